@@ -1,0 +1,171 @@
+"""Seeded synthetic inputs for the two-phase SPH particle loop.
+
+This module builds initial states only: particle lattices, wall layers, the
+oil drop, the seeded jitter and perturbations, and the physical parameters of
+each workload.  It holds none of the method's arithmetic (no kernel, no
+equation of state, no rates), so both the CUDA path and the CPU oracle can
+consume its arrays.
+
+Workloads (oil drop rising in still water, after the paper's Sec. III
+numerical examples, re-sized as synthetic cases):
+
+* ``drop_2d``: 2-D box of 64 x 128 fluid particles, dx = 0.25 mm, three layers
+  of dynamic wall particles on every side (9 380 particles), drop diameter
+  16 dx centred at (W/2, H/4).
+* ``drop_3d``: 3-D box of 64 x 64 x 128 fluid particles with the same
+  spacing, fluids and kernel (656 600 particles with walls).
+
+Fluids: water rho0 = 1000 kg/m^3, mu = 1e-3 Pa s; oil rho0 = 900 kg/m^3,
+mu = 1e-2 Pa s; tension alpha_s = 0.02 N/m; g = 9.81 m/s^2 along -y (2-D)
+or -z (3-D); smoothing length h = 1.3 dx; gamma = 7;
+c0 = 10 sqrt(2 g H) with H the fluid depth; particle mass rho0 dx^dim per
+phase; delta = 0.1 h.
+
+Initial density is the linearised hydrostatic profile
+rho = rho0_phase + rho0_water g (H - y) / c0^2 (a physical initial condition,
+not the method's equation of state).  Random numbers come from
+``numpy.random.Generator(PCG64(seed))``.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+WATER, OIL = 0, 1
+
+
+@dataclass
+class Workload:
+    name: str
+    params: dict
+    x: np.ndarray        # (n, dim) float64 positions
+    u: np.ndarray        # (n, dim) float64 velocities
+    rho: np.ndarray      # (n,) float64 densities
+    phase: np.ndarray    # (n,) uint8, 0 water / 1 oil
+    wall: np.ndarray     # (n,) uint8, 1 for dynamic boundary particles
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n(self) -> int:
+        return len(self.x)
+
+    @property
+    def dim(self) -> int:
+        return int(self.params["dim"])
+
+    def copy(self) -> "Workload":
+        return Workload(self.name, dict(self.params), self.x.copy(), self.u.copy(),
+                        self.rho.copy(), self.phase.copy(), self.wall.copy(), dict(self.meta))
+
+
+def fluid_params(dim: int, dx: float, depth: float, *, rho0=(1000.0, 900.0),
+                 mu=(1e-3, 1e-2), alpha_s=0.02, g=9.81, h_over_dx=1.3,
+                 c0=None, visc_form=0, renorm_every=1, cell_factor=2.05) -> dict:
+    """Physical and numerical parameters of a drop-rise workload.
+
+    ``cell_factor`` sets the neighbour-search cell edge in units of h; it must
+    be at least 2 (the kernel support) and the excess is the displacement skin
+    that lets one cell list serve both stages of a step.
+    """
+    h = h_over_dx * dx
+    if c0 is None:
+        c0 = 10.0 * np.sqrt(2.0 * g * depth)
+    grav = [0.0, 0.0, 0.0]
+    grav[dim - 1] = -g
+    return dict(
+        dim=dim, dx=dx, h=h, c0=float(c0), gamma=7.0, delta=0.1 * h,
+        alpha_s=float(alpha_s), g=grav, rho0=list(map(float, rho0)), mu=list(map(float, mu)),
+        mass=[float(r) * dx ** dim for r in rho0], visc_form=int(visc_form),
+        renorm_every=int(renorm_every), cell_size=cell_factor * h, depth=depth,
+        box_lo=[0.0, 0.0, 0.0], box_hi=[0.0, 0.0, 0.0],
+    )
+
+
+def _lattice(shape, lo_cells: int):
+    """Integer lattice coordinates of a box of `shape` cells extended by
+    `lo_cells` layers on every side, plus a mask of the interior cells."""
+    axes = [np.arange(-lo_cells, s + lo_cells) for s in shape]
+    grids = np.meshgrid(*axes, indexing="ij")
+    # x fastest in memory order does not matter; keep (x, y[, z]) ordering
+    ijk = np.stack([g.ravel(order="F") for g in grids], axis=1)
+    inside = np.ones(len(ijk), bool)
+    for k, s in enumerate(shape):
+        inside &= (ijk[:, k] >= 0) & (ijk[:, k] < s)
+    return ijk, inside
+
+
+def drop_tank(dim: int, shape, dx: float = 2.5e-4, drop_d_dx: float = 16.0,
+              drop_centre_frac=None, wall_layers: int = 3, seed: int = 0,
+              jitter_dx: float = 1e-3, perturb: bool = False, quantise: int | None = None,
+              lid: bool = True, name: str | None = None, **param_kw) -> Workload:
+    """A closed box of fluid lattice `shape` (particles per axis) with an oil
+    drop of diameter `drop_d_dx` * dx and `wall_layers` layers of dynamic wall
+    particles on every side.
+
+    perturb:  add the parity perturbation (u ~ U(-0.01, 0.01) c0 per component
+              on fluid particles, rho *= 1 + U(-1e-3, 1e-3)).
+    lid:      keep the wall layers above the fluid (closed box); without
+              them the fluid has a free surface at y = H.
+    quantise: if given, the jitter is drawn as an integer multiple of
+              dx / quantise in [-quantise/4, quantise/4] (grid-quantised test
+              positions for exact neighbour-set comparisons).
+    """
+    shape = tuple(int(s) for s in shape)
+    assert len(shape) == dim
+    rng = np.random.Generator(np.random.PCG64(seed))
+    depth = shape[dim - 1] * dx
+    p = fluid_params(dim, dx, depth, **param_kw)
+    ijk, inside = _lattice(shape, wall_layers)
+    if not lid:
+        keep = ijk[:, dim - 1] < shape[dim - 1]
+        ijk, inside = ijk[keep], inside[keep]
+    x = (ijk + 0.5) * dx
+    wall = (~inside).astype(np.uint8)
+    fl = inside
+    nfl = int(fl.sum())
+    if quantise:
+        q = int(quantise)
+        jit = rng.integers(-(q // 4), q // 4 + 1, size=(nfl, dim)) * (dx / q)
+    else:
+        jit = rng.uniform(-jitter_dx, jitter_dx, size=(nfl, dim)) * dx
+    x[fl] += jit
+    if drop_centre_frac is None:
+        drop_centre_frac = [0.5] * (dim - 1) + [0.25]
+    centre = np.array([f * s * dx for f, s in zip(drop_centre_frac, shape)])
+    r_drop = 0.5 * drop_d_dx * dx
+    lattice_pos = (ijk + 0.5) * dx
+    in_drop = fl & (np.sum((lattice_pos - centre) ** 2, axis=1) < r_drop ** 2)
+    phase = np.where(in_drop, OIL, WATER).astype(np.uint8)
+    # linearised hydrostatic initial density
+    y = x[:, dim - 1]
+    g = abs(p["g"][dim - 1])
+    p_h = p["rho0"][WATER] * g * (depth - y)
+    rho = np.array(p["rho0"])[phase] + p_h / p["c0"] ** 2
+    u = np.zeros_like(x)
+    if perturb:
+        u[fl] = rng.uniform(-0.01, 0.01, size=(nfl, dim)) * p["c0"]
+        rho *= 1.0 + rng.uniform(-1e-3, 1e-3, size=len(rho))
+    lo = -wall_layers * dx
+    for k in range(dim):
+        p["box_lo"][k] = lo
+        p["box_hi"][k] = shape[k] * dx + wall_layers * dx
+    meta = dict(shape=shape, drop_centre=centre.tolist(), drop_radius=r_drop, seed=seed,
+                n_fluid=nfl, n_wall=int(wall.sum()), n_oil=int(in_drop.sum()))
+    nm = name or f"drop_{dim}d_" + "x".join(map(str, shape))
+    return Workload(nm, p, np.ascontiguousarray(x), u, rho, phase, wall, meta)
+
+
+def drop_2d(seed: int = 0, perturb: bool = False, **kw) -> Workload:
+    """2-D oil drop rise: 64 x 128 fluid particles + 3 wall layers (9 380)."""
+    return drop_tank(2, (64, 128), seed=seed, perturb=perturb, name="drop_2d_64x128", **kw)
+
+
+def drop_3d(seed: int = 1000, perturb: bool = False, **kw) -> Workload:
+    """3-D oil drop rise: 64 x 64 x 128 fluid particles + 3 wall layers (656 600)."""
+    return drop_tank(3, (64, 64, 128), seed=seed, perturb=perturb, name="drop_3d_64x64x128", **kw)
+
+
+def stable_dt(p: dict, cfl: float = 0.25) -> float:
+    """Acoustic time step 0.25 h / c0 used by the drop-rise workloads."""
+    return cfl * p["h"] / p["c0"]
