@@ -1,0 +1,332 @@
+"""Benchmark of the two-phase WCSPH particle loop on one GB300 (or N replicas).
+
+One step = one predictor-corrector step of the whole particle loop (cell
+hash, stable sort, reorder, two renormalisation/colour sweeps, two force
+sweeps, two integrations) over the 3-D oil-drop-rise workload of
+64 x 64 x 128 fluid particles plus three wall layers (656 600 particles).
+
+Prints ONE JSON line (rank 0).  ``value`` is particle-steps/s with the state
+resident in HBM, timed with CUDA events on the simulation's stream around
+graph-replayed steps; ``e2e`` is the same metric through the C ABI with the
+state uploaded from and downloaded to pinned host memory every step.
+``--impl reference`` times the FP64 CPU oracle instead (the reference arm of
+this method, which has no published implementation).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# FP32 peak from unit counts and the maximum SM clock: 152 SMs x 128 FP32
+# lanes x 2 flops (FMA) x 2.07 GHz.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+# Algorithmic flops of one accepted (i, j) pair in the force sweep (FMA = 2,
+# sqrt and divide = 1): pair vector and squared distance, q, (1 - q/2)^3,
+# pressure term, viscous term, continuity term.  Surface-tension pairs are
+# not counted (conservative).
+SWEEP_B_FLOPS_PER_PAIR = {2: 33, 3: 43}
+# Algorithmic flops of one accepted pair in the renormalisation sweep at
+# stage 1: same-phase pairs (kernel value + two compensated sums) and
+# other-phase pairs (colour gradient).
+SWEEP_A_FLOPS_SAME = {2: 24, 3: 27}
+SWEEP_A_FLOPS_OTHER = {2: 14, 3: 21}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="drop_3d", choices=["drop_3d", "drop_2d"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ws, v: float, device=None) -> float:
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def make_workload(name):
+    from paper_1702_07760_gb300 import workloads as WL
+    return WL.drop_3d() if name == "drop_3d" else WL.drop_2d()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "",
+                                 f".clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_oracle_rate(w, budget_s=15.0, max_steps=8):
+    """Times the FP64 oracle on the host cores; returns (particle-steps/s, cores, steps)."""
+    import oracle
+    from paper_1702_07760_gb300 import workloads as WL
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    dt = WL.stable_dt(w.params)
+    x, u, rho = w.x, w.u, w.rho
+    t0 = time.perf_counter()
+    steps = 0
+    while steps < max_steps:
+        x, u, rho = oracle.run(w.params, x, u, rho, w.phase, w.wall, dt, 1, first_step=steps)
+        steps += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    el = time.perf_counter() - t0
+    return w.n * steps / el, oracle.num_threads(), steps
+
+
+def run_reference(args, ws, rank):
+    """The oracle as the reference arm: each step is one oracle step of a
+    bounded sample of the workload (a 32 x 32 x 64 fluid box with the same
+    spacing, fluids, kernel and wall layers)."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_1702_07760_gb300 import workloads as WL
+    w = WL.drop_tank(3, (32, 32, 64), drop_d_dx=8, seed=1000) if args.workload == "drop_3d" else WL.drop_2d()
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    dt = WL.stable_dt(w.params)
+    x, u, rho = w.x, w.u, w.rho
+    for s in range(args.warmup):
+        x, u, rho = oracle.run(w.params, x, u, rho, w.phase, w.wall, dt, 1, first_step=s)
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        x, u, rho = oracle.run(w.params, x, u, rho, w.phase, w.wall, dt, 1, first_step=args.warmup + s)
+    el = time.perf_counter() - t0
+    value = w.n * args.steps / el
+    sample = f"{w.n}-particle sample box ({w.name}) of the 3-D drop-rise workload, one oracle step per bench step"
+    line = {
+        "impl": "reference", "metric": "particle-steps/s", "value": value, "unit": "particle-steps/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "drop_3d_64x64x128" if args.workload == "drop_3d" else w.name,
+                   "sample": sample, "particles": w.n},
+        "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": oracle.num_threads(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+    from paper_1702_07760_gb300 import build as B
+    from paper_1702_07760_gb300 import sph
+    from paper_1702_07760_gb300 import workloads as WL
+
+    B.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    w = make_workload(args.workload)
+    p = w.params
+    dim = w.dim
+    dt = WL.stable_dt(p)
+    n = w.n
+    sim = sph.Simulation.from_workload(w, stream=stream.cuda_stream)
+    pairs0, other0 = sim.pair_stats()
+
+    # ---- timed region A: graph-replayed steps, state resident in HBM ----
+    sim.run(dt, args.warmup, graph=True)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        sim.run(dt, args.steps, graph=True)
+        ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    ms = max_over_ranks(ws, ms, dev)
+    barrier(ws)
+    value = ws * n * args.steps / (ms / 1e3)
+    pairs1, other1 = sim.pair_stats()
+
+    # ---- timed region B: same steps with per-kernel CUDA events ----
+    sim.timing(True)
+    sim.timing_reset()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.run(dt, args.steps, graph=False)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ms_eager = e0.elapsed_time(e1)
+    kt = sim.timing_read()
+    sim.timing(False)
+    tot = sum(v[1] for v in kt.values())
+    kernels = {k: {"launches": v[0], "ms": round(v[1], 4), "share": round(v[1] / tot, 4)} for k, v in kt.items() if v[0]}
+    top = max(kt, key=lambda k: kt[k][1])
+    pairs = 0.5 * (pairs0 + pairs1)
+    other = 0.5 * (other0 + other1)
+    if top == "sweep_b":
+        flops = pairs * SWEEP_B_FLOPS_PER_PAIR[dim]
+    elif top == "sweep_a":
+        # two launches per step: stage 1 (renormalisation + colour) and stage 2 (colour only)
+        flops = 0.5 * ((pairs - other) * SWEEP_A_FLOPS_SAME[dim] + 2 * other * SWEEP_A_FLOPS_OTHER[dim])
+    else:
+        flops = float("nan")
+    avg_ms = kt[top][1] / max(kt[top][0], 1)
+    achieved = flops / (avg_ms / 1e3) / 1e12
+    roofline = {"bound": "alu", "kernel": top, "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz",
+                "flops_per_launch": flops, "avg_launch_ms": avg_ms}
+
+    # ---- e2e: host buffers through the C ABI every step ----
+    e2e = None
+    if not args.no_e2e:
+        ke = max(3, min(args.steps, 20))
+        pin = lambda *s: torch.empty(s, dtype=torch.float64, pin_memory=True).numpy()
+        hx, hu, hr = pin(n, dim), pin(n, dim), pin(n)
+        hx[:] = sim.read("pos")
+        hu[:] = sim.read("vel")
+        hr[:] = sim.read("rho")
+        # one untimed round trip
+        sim.set_state(hx, hu, hr)
+        sim.step(dt)
+        torch.cuda.synchronize()
+        barrier(ws)
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            sim.set_state(hx, hu, hr)
+            sim.step(dt)
+            hx[:] = sim.read("pos")
+            hu[:] = sim.read("vel")
+            hr[:] = sim.read("rho")
+        sim.sync()
+        el = max_over_ranks(ws, time.perf_counter() - t0, dev)
+        nb = n * (2 * dim + 1) * 8
+        e2e = {"value": ws * n * ke / el, "unit": "particle-steps/s", "h2d_bytes_per_step": nb,
+               "d2h_bytes_per_step": nb, "steps": ke}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        rate, cores, steps = cpu_oracle_rate(w)
+        cpu = {"value": rate, "unit": "particle-steps/s", "cores": cores, "kind": "oracle",
+               "sample": f"{steps} FP64 oracle step(s) of the full {n}-particle workload"}
+
+    kernels_per_step = 13  # hash, 3 scan, scatter, rank, gather, 2 sweep_a, 2 sweep_b, predict, correct
+    line = {
+        "metric": "particle-steps/s", "value": value, "unit": "particle-steps/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "drop_3d_64x64x128" if args.workload == "drop_3d" else "drop_2d_64x128",
+                   "particles": n, "fluid_particles": int((w.wall == 0).sum()), "dim": dim, "dt": dt,
+                   "neighbour_pairs": int(pairs), "l2": "step working set (~390 MB) exceeds the 129 MB L2; no flush",
+                   "parallelism": "replicas" if ws > 1 else "single", "graph": True,
+                   "ms_per_step_eager_timed": ms_eager / args.steps},
+        "roofline": roofline,
+        "kernels": kernels,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": kernels_per_step * args.steps,
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    sim.close()
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,183 @@
+/*
+ * sph.h -- C ABI of the GB300 two-phase weakly compressible SPH particle loop.
+ *
+ * Method: Wei et al., "Behavior of Oil under Breaking Waves by a Two-phase SPH
+ * Model", Sec. II.  One time step evaluates, for every particle, the per-phase
+ * density renormalisation (Eq. ct_dist_3), the equation of state (Eqs. state
+ * and beta), the colour-index gradient (Eq. cd) and surface stress tensor
+ * (Eq. csf), the symmetric pressure gradient (Eq. dist_p_1), the harmonic-mean
+ * two-phase viscosity (Eq. visc_2, or Eq. visc_1), the surface-tension force
+ * (F_s/rho, Sec. II-C), gravity, and the two-phase continuity equation
+ * (Eq. ct_dist_2), and advances the state with an explicit midpoint
+ * predictor-corrector.  Dynamic boundary particles (Sec. III) are water
+ * particles whose position and velocity stay fixed while their density
+ * integrates.
+ *
+ * Conventions for every entry point:
+ *   - Return value: SPH_OK (0) or a negative SPH_E* code; the message of the
+ *     last failure on the calling thread is available from sph_last_error().
+ *     The library never aborts the process.
+ *   - Host arrays are owned by the caller and only read (or, for sph_read,
+ *     written) during the call.  Device memory belongs to the handle from
+ *     sph_create until sph_destroy.
+ *   - All GPU work is issued on the CUDA stream given to sph_create, in call
+ *     order.  sph_step and sph_run return once the work is queued; errors
+ *     raised on the device (non-finite values, a particle leaving the box, a
+ *     step too large for the neighbour-search skin) are reported by the next
+ *     call that waits for the stream: sph_run, sph_sync, sph_read,
+ *     sph_neighbours, sph_diag.
+ *   - Particle order: arrays passed in and read out are in the caller's
+ *     original order (particle id = index in the arrays given to sph_create).
+ */
+#ifndef SPH_H
+#define SPH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Error codes */
+#define SPH_OK          0
+#define SPH_EINVAL     -1  /* invalid argument or parameter */
+#define SPH_ENOMEM     -2  /* device or host allocation failed */
+#define SPH_ECUDA      -3  /* a CUDA runtime call failed */
+#define SPH_ENONFINITE -4  /* a NaN or Inf appeared in the state */
+#define SPH_ECFL       -5  /* a particle moved farther in a step than the cell skin allows */
+#define SPH_EDOMAIN    -6  /* a particle left the box of the cell grid */
+
+/* Viscous term forms (Sec. II-C) */
+#define SPH_VISC_DYNAMIC   0  /* Eq. visc_2: (1/rho_i) sum 2 mu_ij (m_j/rho_j) (r.gradW)/(r^2+delta^2) u_ij */
+#define SPH_VISC_KINEMATIC 1  /* Eq. visc_1: sum 2 nu_ij (m_j/rho_j) (r.gradW)/(r^2+delta^2) u_ij, nu = mu/rho0 */
+
+/* Fields for sph_read.  Floating fields are written as double, integer fields
+ * as int32.  "eval" fields hold the last rates evaluation (sph_eval_rates, or
+ * stage 2 of the last sph_step). */
+#define SPH_FIELD_POS        0  /* n*dim  position x (state) */
+#define SPH_FIELD_VEL        1  /* n*dim  velocity u (state) */
+#define SPH_FIELD_RHO        2  /* n      density rho (state) */
+#define SPH_FIELD_RHO_EVAL   3  /* n      density after renormalisation, Eq. ct_dist_3 (eval) */
+#define SPH_FIELD_PRESSURE   4  /* n      pressure P, Eq. state (eval) */
+#define SPH_FIELD_ACC        5  /* n*dim  acceleration Du/Dt, zero on walls (eval) */
+#define SPH_FIELD_DRHO       6  /* n      density rate Drho/Dt, Eq. ct_dist_2 (eval) */
+#define SPH_FIELD_TENSOR     7  /* n*dim*dim surface stress tensor T, Eq. csf (eval) */
+#define SPH_FIELD_CELL       8  /* n      int32 cell id of the last cell-list build */
+#define SPH_FIELD_ORDER      9  /* n      int32 particle id at each sorted position:
+                                   the stable order by (cell id, particle id) */
+
+/* Physical and numerical parameters.  The layout is fixed; unused 3-D
+ * entries are ignored when dim == 2. */
+typedef struct sph_params {
+    int32_t dim;           /* 2 or 3 */
+    int32_t visc_form;     /* SPH_VISC_DYNAMIC or SPH_VISC_KINEMATIC */
+    int32_t renorm_every;  /* Eq. ct_dist_3 at stage 1 of steps with step % renorm_every == 0; 0 = never */
+    int32_t reserved;      /* must be 0 */
+    double h;              /* smoothing length; the Wendland C2 kernel has support 2h */
+    double c0;             /* reference speed of sound C_s0 (Eq. beta) */
+    double gamma;          /* exponent of Eq. state; must be 7 (the paper's value) */
+    double delta;          /* regulariser of the viscous term (the paper uses 0.1 h) */
+    double alpha_s;        /* interfacial surface tension coefficient (Eq. csf) */
+    double cell_size;      /* cell edge of the neighbour grid, >= 2h; the excess
+                              (cell_size - 2h)/2 is the displacement skin within
+                              which one cell list serves both stages of a step */
+    double g[3];           /* gravitational acceleration */
+    double rho0[2];        /* reference density per phase: [0] water, [1] oil */
+    double mu[2];          /* dynamic viscosity per phase */
+    double mass[2];        /* particle mass per phase */
+    double box_lo[3];      /* lower corner of the domain covered by the cell grid */
+    double box_hi[3];      /* upper corner */
+} sph_params;
+
+typedef struct sph_sim *sph_handle;
+
+/* Creates a simulation of n particles and copies the initial state to the GPU.
+ *   x, u   : n*dim doubles, row-major (particle-major), positions and velocities
+ *   rho    : n doubles, densities
+ *   phase  : n bytes, 0 = water, 1 = oil
+ *   wall   : n bytes, 1 = dynamic boundary particle (must be phase 0), else 0
+ *   stream : a cudaStream_t, or NULL for the default stream
+ * Every position must lie inside [box_lo, box_hi].  On success *out holds the
+ * handle; on failure *out is NULL and nothing is leaked. */
+int sph_create(const sph_params *params, int64_t n, const double *x, const double *u,
+               const double *rho, const uint8_t *phase, const uint8_t *wall,
+               void *stream, sph_handle *out);
+
+/* Replaces the state (x, u, rho; same layout as sph_create) of an existing
+ * handle with host data, keeping its parameters, phases and walls.  The step
+ * counter is left as it is. */
+int sph_set_state(sph_handle h, const double *x, const double *u, const double *rho);
+
+/* Builds the cell list at the current positions: cell hash, stable sort by
+ * (cell id, particle id), reorder of every per-particle array, cellStart and
+ * cellEnd (the neighbour search; the paper inherits it from the GPU code
+ * base named at the end of Sec. II-C and does not describe it). */
+int sph_build_cells(sph_handle h);
+
+/* One evaluation of the rates at the current state, on a fresh cell list,
+ * renormalising the density when the current step index calls for it.  Does
+ * not advance the state; the results are read with the *_EVAL fields,
+ * SPH_FIELD_PRESSURE, SPH_FIELD_ACC, SPH_FIELD_DRHO and SPH_FIELD_TENSOR. */
+int sph_eval_rates(sph_handle h);
+
+/* One predictor-corrector step of size dt > 0 (cell build, two rates
+ * evaluations, two integrations).  Queues the work and returns. */
+int sph_step(sph_handle h, double dt);
+
+/* nsteps steps of size dt, then waits for the stream and reports any device
+ * error.  With graph != 0 the per-step launch sequence is captured once into
+ * a CUDA graph and replayed. */
+int sph_run(sph_handle h, double dt, int64_t nsteps, int graph);
+
+/* Waits for the stream and reports any device-side error flag. */
+int sph_sync(sph_handle h);
+
+/* Copies a field (SPH_FIELD_*) into host memory in original particle order.
+ * bytes must be at least the field's size (see the field list). */
+int sph_read(sph_handle h, int field, void *host_out, int64_t bytes);
+
+/* Neighbour sets at the current positions (rebuilds the cell list, which
+ * invalidates the eval fields) as computed by the GPU's own
+ * candidate test (j != i and |r_ij|^2 < (2h)^2 in the kernels' arithmetic),
+ * in CSR form over original particle ids, each row ascending.  start has n+1
+ * entries.  Returns the number of pairs (>= 0), or SPH_EINVAL when cap is too
+ * small (start is filled in that case, so a second call can size list). */
+int64_t sph_neighbours(sph_handle h, int64_t *start, int32_t *list, int64_t cap);
+
+/* Neighbour statistics at the current positions (rebuilds the cell list):
+ * out[0] = number of ordered pairs (i, j), j != i, with |r_ij| < 2h;
+ * out[1] = how many of them join particles of different phase.  These are
+ * the pair counts the interaction sweeps evaluate. */
+int sph_pair_stats(sph_handle h, int64_t out[2]);
+
+/* FP64 diagnostics over the fluid particles (walls excluded):
+ *   out[0] mass, out[1..3] momentum sum m u, out[4] kinetic energy,
+ *   out[5] potential energy -sum m g.x, out[6..8] oil centroid,
+ *   out[9] oil sphericity sqrt(lambda_min/lambda_max) of the covariance of
+ *   oil positions, out[10] max |u|, out[11] number of oil particles. */
+int sph_diag(sph_handle h, double out[12]);
+
+/* Per-kernel timing with CUDA events on the simulation's stream.  While
+ * enabled, every launch is bracketed by events; sph_timing_read returns, for
+ * kernel index k (0 <= k < sph_timing_count()), its name, launch count and
+ * total milliseconds since the last reset. */
+int sph_timing_enable(sph_handle h, int enable);
+int sph_timing_reset(sph_handle h);
+int sph_timing_count(void);
+int sph_timing_read(sph_handle h, int k, const char **name, int64_t *launches, double *total_ms);
+
+/* Number of particles, step counter, grid cells. */
+int64_t sph_num_particles(sph_handle h);
+int64_t sph_step_index(sph_handle h);
+int64_t sph_num_cells(sph_handle h);
+
+void sph_destroy(sph_handle h);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char *sph_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPH_H */

@@ -1,0 +1,756 @@
+// Device kernels of the two-phase WCSPH particle loop (sm_103a).
+//
+// Method: Wei et al., "Behavior of Oil under Breaking Waves by a Two-phase SPH
+// Model", Sec. II.  Layout and arithmetic choices made for the GPU:
+//   * particles live in cell order (stable by original id), structure of
+//     arrays; positions used by the neighbour sweeps are stored as a cell id
+//     plus an FP32 offset from the cell centre, so a pair distance is formed
+//     from two small numbers and an exact multiple of the cell edge;
+//   * the FP64 position and velocity are the integration accumulators;
+//   * density is stored as the deviation drho = rho - rho0(phase) in FP32, so
+//     the equation of state and the renormalisation never subtract two
+//     numbers near rho0;
+//   * one thread per particle scans the 3^dim neighbouring cells; threads of a
+//     warp are consecutive particles of the same or adjacent cells and read
+//     the same candidates, so candidate loads are served as L1 broadcasts.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sphgb {
+
+enum : unsigned {
+    FLAG_DOMAIN = 1u,     // a particle left the cell grid
+    FLAG_NONFINITE = 2u,  // NaN/Inf in the state
+    FLAG_SKIN = 4u,       // predictor displacement beyond the cell skin
+};
+
+// Constants of the physics, FP32 unless they feed an FP64 accumulator.
+struct Phys {
+    float inv_h;        // 1/h
+    float R2;           // (2h)^2, neighbour test
+    float cF;           // -5 alpha_d / h^2: grad W_ij = cF (1-q/2)^3 r_ij
+    float mass[2];      // per-phase particle mass
+    float inv_mass[2];
+    float rho0[2];      // per-phase reference density
+    float inv_rho0[2];
+    float beta[2];      // rho0 c0^2 / gamma
+    float kvis[4];      // [2*ph_i + ph_j]: 2 mu_ij (dynamic form) or 2 nu_ij (kinematic form)
+    float delta2;       // delta^2
+    float alpha_s;      // surface tension coefficient
+    float inv_dim;      // 1/d in Eq. csf
+    int visc_dynamic;   // 1: Eq. visc_2 (factor 1/rho_i), 0: Eq. visc_1
+    int renorm_every;   // Eq. ct_dist_3 at stage 1 of steps with step % renorm_every == 0
+    float gf[3];        // gravity (FP32, added to the FP32 acceleration)
+    double hd;          // h (FP64), skin test
+};
+
+struct Grid {
+    int nx, ny, nz;     // cells per axis (nz = 1 in 2-D)
+    float cs;           // cell edge (FP32) for pair offsets
+    double csd;         // cell edge (FP64) for hashing and offsets
+    double lo[3];       // box lower corner
+};
+
+// All device arrays of one simulation (sorted order unless noted).
+struct Dev {
+    int n;
+    // state (FP64 accumulators + FP32 density deviation)
+    double *x;          // dim * n, SoA
+    double *u;          // dim * n, SoA
+    float *drho;        // n, rho - rho0(phase) of the state
+    int *pid;           // n, original particle id
+    uint8_t *tag;       // n, bit0 oil, bit1 wall
+    int *cell;          // n, cell id (sorted order)
+    // stage arrays
+    float4 *pos;        // n, (offset from cell centre xyz, +/- m/rho: sign = phase)
+    float *vd;          // n, (m/rho) * drho of the stage input
+    float4 *vel;        // n, (u xyz, 0) FP32 copy of the stage velocity
+    float *drho_stage;  // n, drho* of the predictor
+    float *drho_eval;   // n, drho after renormalisation (stage output)
+    float4 *aux;        // n, (m/rho, P/rho^2, interface flag, P)
+    float4 *T4;         // n, T sigma^-2 = T (m/rho)^2: 2-D (xx, xy, yy, 0); 3-D (xx, xy, xz, yy)
+    float2 *T2;         // n, 3-D only: (yz, zz)
+    float4 *acc;        // n, (a xyz, Drho/Dt)
+    // cell list
+    int *cstart;        // ncell + 1
+    unsigned *flags;    // 1 word
+    long long *step;    // device step counter (drives the renormalisation schedule)
+};
+
+__device__ __forceinline__ int phase_of(float w) { return __float_as_uint(w) >> 31; }
+
+// Scans all candidates of the 3^DIM cells around cell (cx, cy, cz) and calls
+// f(j, pj, rx, ry, rz, r2) for every j with |r_ij|^2 < (2h)^2 (j == i
+// included: r = 0).  r_ij = x_i - x_j is formed per axis as
+// (o_i + (c_i - c_j) * cs) - o_j.
+template <int DIM, class F>
+__device__ __forceinline__ void for_each_neighbour(const Grid &g, const int *__restrict__ cstart,
+                                                   const float4 *__restrict__ pos, int cx, int cy,
+                                                   int cz, float4 pi, float R2, F &&f)
+{
+    const int z0 = DIM == 3 ? max(cz - 1, 0) : 0;
+    const int z1 = DIM == 3 ? min(cz + 1, g.nz - 1) : 0;
+    const int y0 = max(cy - 1, 0), y1 = min(cy + 1, g.ny - 1);
+    const int x0 = max(cx - 1, 0), x1 = min(cx + 1, g.nx - 1);
+    for (int z = z0; z <= z1; ++z) {
+        const float bz = DIM == 3 ? pi.z + (float)(cz - z) * g.cs : 0.f;
+        for (int y = y0; y <= y1; ++y) {
+            const float by = pi.y + (float)(cy - y) * g.cs;
+            const int row = (z * g.ny + y) * g.nx;
+            for (int xx = x0; xx <= x1; ++xx) {
+                const float bx = pi.x + (float)(cx - xx) * g.cs;
+                const int jb = __ldg(cstart + row + xx), je = __ldg(cstart + row + xx + 1);
+                for (int j = jb; j < je; ++j) {
+                    const float4 pj = __ldg(pos + j);
+                    const float rx = bx - pj.x, ry = by - pj.y;
+                    const float rz = DIM == 3 ? bz - pj.z : 0.f;
+                    float r2 = rx * rx;
+                    r2 = fmaf(ry, ry, r2);
+                    if (DIM == 3) r2 = fmaf(rz, rz, r2);
+                    if (r2 < R2) f(j, pj, rx, ry, rz, r2);
+                }
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void cell_coords(const Grid &g, int c, int &cx, int &cy, int &cz)
+{
+    cx = c % g.nx;
+    const int r = c / g.nx;
+    cy = r % g.ny;
+    cz = r / g.ny;
+}
+
+// Compensated (Kahan) accumulation.
+__device__ __forceinline__ void kahan_add(float &s, float &c, float v)
+{
+    const float y = v - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
+// Eq. state with gamma = 7 written in the density deviation eps = drho/rho0:
+// P = beta ((1 + eps)^7 - 1) = beta eps (7 + 21 eps + 35 eps^2 + 35 eps^3
+// + 21 eps^4 + 7 eps^5 + eps^6), free of the cancellation of the power form.
+__device__ __forceinline__ float eos_tait7(float beta, float eps)
+{
+    float p = eps + 7.f;
+    p = fmaf(p, eps, 21.f);
+    p = fmaf(p, eps, 35.f);
+    p = fmaf(p, eps, 35.f);
+    p = fmaf(p, eps, 21.f);
+    p = fmaf(p, eps, 7.f);
+    return beta * eps * p;
+}
+
+// ---------------------------------------------------------------------------
+// Cell list: hash, counting sort stable in particle id, reorder.
+
+template <int DIM>
+__global__ void __launch_bounds__(256) k_hash(Dev d, Grid g, int *cell_tmp, int *slot, int *count)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= d.n) return;
+    const int dims[3] = {g.nx, g.ny, g.nz};
+    int c[3] = {0, 0, 0};
+    bool bad = false;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        const double s = floor((d.x[(size_t)a * d.n + k] - g.lo[a]) / g.csd);
+        if (!(s >= 0.0 && s < (double)dims[a])) {
+            bad = true;
+            c[a] = 0;
+        } else {
+            c[a] = (int)s;
+        }
+    }
+    if (bad) atomicOr(d.flags, FLAG_DOMAIN);
+    const int id = c[0] + g.nx * (c[1] + g.ny * c[2]);
+    cell_tmp[k] = id;
+    slot[k] = atomicAdd(count + id, 1);
+}
+
+// Exclusive scan of m ints, 4096 per block (1024 threads x 4).
+constexpr int SCAN_THREADS = 1024, SCAN_ITEMS = 4, SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+// Block-wide exclusive scan of one value per thread; the block total is
+// written to *total (shared memory).
+__device__ __forceinline__ int block_exclusive_scan(int v, int *total)
+{
+    __shared__ int warp_tot[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    int inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) warp_tot[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        const int w = lane < nw ? warp_tot[lane] : 0;
+        int wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += t;
+        }
+        warp_tot[lane] = wi - w;
+        if (lane == nw - 1) *total = wi;
+    }
+    __syncthreads();
+    const int res = warp_tot[wid] + inc - v;
+    __syncthreads();
+    return res;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_tiles(const int *in, int *out, int *tile_sums, int m)
+{
+    __shared__ int s_total;
+    const int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+    int v[SCAN_ITEMS];
+    int sum = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        v[k] = base + k < m ? in[base + k] : 0;
+        sum += v[k];
+    }
+    int ex = block_exclusive_scan(sum, &s_total);
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        if (base + k < m) out[base + k] = ex;
+        ex += v[k];
+    }
+    if (threadIdx.x == 0) tile_sums[blockIdx.x] = s_total;
+}
+
+// Scans the tile sums in place (one block, at most SCAN_TILE tiles) and
+// writes the grand total to out[m].
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_sums(int *tile_sums, int ntiles, int *out, int m)
+{
+    __shared__ int s_total;
+    const int base = threadIdx.x * SCAN_ITEMS;
+    int v[SCAN_ITEMS];
+    int sum = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        v[k] = base + k < ntiles ? tile_sums[base + k] : 0;
+        sum += v[k];
+    }
+    int ex = block_exclusive_scan(sum, &s_total);
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        if (base + k < ntiles) tile_sums[base + k] = ex;
+        ex += v[k];
+    }
+    if (threadIdx.x == 0) out[m] = s_total;
+}
+
+__global__ void __launch_bounds__(256) k_scan_add(int *out, const int *tile_sums, int m)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) out[i] += tile_sums[i / SCAN_TILE];
+}
+
+__global__ void __launch_bounds__(256) k_scatter(int n, const int *cell_tmp, const int *slot, const int *cstart, int *tmp)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    tmp[cstart[cell_tmp[k]] + slot[k]] = k;
+}
+
+// Final position of each particle inside its cell: its rank by original id
+// among the cell's particles, so the order is (cell id, particle id).
+__global__ void __launch_bounds__(256) k_rank(int n, const int *tmp, const int *cell_tmp, const int *pid,
+                                              const int *cstart, int *perm)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int k = tmp[p];
+    const int c = cell_tmp[k];
+    const int b = cstart[c], e = cstart[c + 1];
+    const int me = pid[k];
+    int rank = 0;
+    for (int q = b; q < e; ++q) rank += pid[tmp[q]] < me;
+    perm[b + rank] = k;
+}
+
+// Signed specific volume for the stage position array: m/rho, negative for oil.
+__device__ __forceinline__ float signed_volume(const Phys &ph, int phase, float drho, float &vol)
+{
+    vol = ph.mass[phase] / (ph.rho0[phase] + drho);
+    return phase ? -vol : vol;
+}
+
+template <int DIM>
+__device__ __forceinline__ float4 cell_offset(const Grid &g, int c, const double xa[3])
+{
+    int cc[3];
+    cell_coords(g, c, cc[0], cc[1], cc[2]);
+    float o[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) o[a] = (float)(xa[a] - (g.lo[a] + ((double)cc[a] + 0.5) * g.csd));
+    return make_float4(o[0], o[1], o[2], 0.f);
+}
+
+// Gathers the state into the new order and prepares the stage-1 arrays.
+template <int DIM>
+__global__ void __launch_bounds__(256) k_gather(Dev src, Dev dst, Grid g, Phys ph, const int *perm, const int *cell_tmp)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = src.n;
+    if (k >= n) return;
+    const int o = perm[k];
+    double xa[3] = {0, 0, 0}, ua[3] = {0, 0, 0};
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        xa[a] = src.x[(size_t)a * n + o];
+        ua[a] = src.u[(size_t)a * n + o];
+        dst.x[(size_t)a * n + k] = xa[a];
+        dst.u[(size_t)a * n + k] = ua[a];
+    }
+    const float dr = src.drho[o];
+    const uint8_t tg = src.tag[o];
+    const int c = cell_tmp[o];
+    dst.drho[k] = dr;
+    dst.pid[k] = src.pid[o];
+    dst.tag[k] = tg;
+    dst.cell[k] = c;
+    float4 p = cell_offset<DIM>(g, c, xa);
+    float vol;
+    p.w = signed_volume(ph, tg & 1, dr, vol);
+    dst.pos[k] = p;
+    dst.vd[k] = vol * dr;
+    dst.vel[k] = make_float4((float)ua[0], (float)ua[1], (float)ua[2], 0.f);
+}
+
+// ---------------------------------------------------------------------------
+// Sweep A: per-phase renormalisation (Eq. ct_dist_3), colour-index gradient
+// (Eq. cd) and surface stress tensor (Eq. csf), equation of state (Eq. state).
+//
+// Eq. ct_dist_3 with same-phase masses m_j = m_i is rewritten exactly as a
+// Shepard average of the density deviation:
+//   rho_i - rho0 = sum_j (m_j/rho_j) drho_j W_ij / sum_j (m_j/rho_j) W_ij,
+// both sums Kahan-compensated.  The colour gradient uses the density that
+// entered the stage: grad C_i = (1/V_i) sum_{j other phase} V_j^2 grad W_ij,
+// V = m/rho = 1/sigma.
+template <int DIM>
+__global__ void __launch_bounds__(256) k_sweep_a(Dev d, Grid g, Phys ph, const float *__restrict__ drho_in, int stage1)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d.n) return;
+    const int renorm = stage1 && ph.renorm_every > 0 && (*d.step % ph.renorm_every) == 0;
+    const float4 pi = d.pos[i];
+    const int phi = phase_of(pi.w);
+    int cx, cy, cz;
+    cell_coords(g, d.cell[i], cx, cy, cz);
+    float s1 = 0.f, c1 = 0.f, s2 = 0.f, c2 = 0.f;
+    float gx = 0.f, gy = 0.f, gz = 0.f;
+    const float inv_h = ph.inv_h;
+    const float *__restrict__ vd = d.vd;
+    for_each_neighbour<DIM>(g, d.cstart, d.pos, cx, cy, cz, pi, ph.R2,
+        [&](int j, const float4 &pj, float rx, float ry, float rz, float r2) {
+            const float r = sqrtf(r2);
+            const float t = fmaf(-0.5f * inv_h, r, 1.f);
+            const float t3 = t * t * t;
+            if (phase_of(pj.w) == phi) {
+                if (renorm) {
+                    // W / alpha_d = t^4 (2q + 1)
+                    const float w = t3 * t * fmaf(2.f * inv_h, r, 1.f);
+                    kahan_add(s1, c1, fabsf(pj.w) * w);
+                    kahan_add(s2, c2, __ldg(vd + j) * w);
+                }
+            } else {
+                const float c = pj.w * pj.w * t3;
+                gx = fmaf(c, rx, gx);
+                gy = fmaf(c, ry, gy);
+                if (DIM == 3) gz = fmaf(c, rz, gz);
+            }
+        });
+    const float drho = renorm ? s2 / s1 : drho_in[i];
+    d.drho_eval[i] = drho;
+    const float rho = ph.rho0[phi] + drho;
+    const float vol = ph.mass[phi] / rho;
+    const float P = eos_tait7(ph.beta[phi], drho * ph.inv_rho0[phi]);
+    // grad C_i = sigma_i sum V_j^2 grad W_ij, sigma_i = 1/|V_i| (entry density)
+    const float sc = ph.cF / fabsf(pi.w);
+    gx *= sc;
+    gy *= sc;
+    gz *= sc;
+    const float n2 = gx * gx + gy * gy + gz * gz;
+    float iface = 0.f;
+    float4 t4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float2 t2 = make_float2(0.f, 0.f);
+    if (n2 > 0.f) {
+        iface = 1.f;
+        // T sigma_i^-2 = alpha_s / |g| (|g|^2/d I - g g^T) V_i^2, V_i from the renormalised density
+        const float k = ph.alpha_s * rsqrtf(n2) * vol * vol;
+        const float iso = n2 * ph.inv_dim;
+        if (DIM == 2) {
+            t4 = make_float4(k * (iso - gx * gx), -k * gx * gy, k * (iso - gy * gy), 0.f);
+        } else {
+            t4 = make_float4(k * (iso - gx * gx), -k * gx * gy, -k * gx * gz, k * (iso - gy * gy));
+            t2 = make_float2(-k * gy * gz, k * (iso - gz * gz));
+        }
+    }
+    d.aux[i] = make_float4(vol, P / (rho * rho), iface, P);
+    d.T4[i] = t4;
+    if (DIM == 3) d.T2[i] = t2;
+}
+
+// ---------------------------------------------------------------------------
+// Sweep B: pressure gradient (Eq. dist_p_1), harmonic-mean viscosity
+// (Eq. visc_2 or visc_1), surface tension (F_s/rho), gravity, continuity
+// (Eq. ct_dist_2).  grad_i W_ij = cF t^3 r_ij with t = 1 - q/2; the common
+// factor cF is applied once per particle.
+template <int DIM>
+__global__ void __launch_bounds__(256) k_sweep_b(Dev d, Grid g, Phys ph)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d.n) return;
+    const float4 pi = d.pos[i];
+    const int phi = phase_of(pi.w);
+    const float4 ai = d.aux[i];
+    const float4 ui = d.vel[i];
+    const float4 Ti = d.T4[i];
+    const float2 Ti2 = DIM == 3 ? d.T2[i] : make_float2(0.f, 0.f);
+    int cx, cy, cz;
+    cell_coords(g, d.cell[i], cx, cy, cz);
+    float px = 0.f, py = 0.f, pz = 0.f;    // sum m_j (P_i/rho_i^2 + P_j/rho_j^2) t^3 r_ij
+    float vx = 0.f, vy = 0.f, vz = 0.f;    // sum k_ij V_j t^3 r^2/(r^2+delta^2) u_ij
+    float sx = 0.f, sy = 0.f, sz = 0.f;    // sum (T_i/sigma_i^2 + T_j/sigma_j^2) . t^3 r_ij
+    float dv = 0.f;                        // sum V_j t^3 u_ij . r_ij
+    const float inv_h = ph.inv_h;
+    const float4 *__restrict__ aux = d.aux;
+    const float4 *__restrict__ vel = d.vel;
+    const float4 *__restrict__ T4 = d.T4;
+    const float2 *__restrict__ T2 = d.T2;
+    for_each_neighbour<DIM>(g, d.cstart, d.pos, cx, cy, cz, pi, ph.R2,
+        [&](int j, const float4 &pj, float rx, float ry, float rz, float r2) {
+            const int phj = phase_of(pj.w);
+            const float4 aj = __ldg(aux + j);
+            const float4 uj = __ldg(vel + j);
+            const float r = sqrtf(r2);
+            const float t = fmaf(-0.5f * inv_h, r, 1.f);
+            const float t3 = t * t * t;
+            const float pt = ph.mass[phj] * (ai.y + aj.y) * t3;
+            px = fmaf(pt, rx, px);
+            py = fmaf(pt, ry, py);
+            if (DIM == 3) pz = fmaf(pt, rz, pz);
+            const float ux = ui.x - uj.x, uy = ui.y - uj.y, uz = DIM == 3 ? ui.z - uj.z : 0.f;
+            const float vt = aj.x * t3;
+            const float s = ph.kvis[2 * phi + phj] * vt * __fdividef(r2, r2 + ph.delta2);
+            vx = fmaf(s, ux, vx);
+            vy = fmaf(s, uy, vy);
+            if (DIM == 3) vz = fmaf(s, uz, vz);
+            float ur = ux * rx;
+            ur = fmaf(uy, ry, ur);
+            if (DIM == 3) ur = fmaf(uz, rz, ur);
+            dv = fmaf(vt, ur, dv);
+            if (ai.z + aj.z > 0.f) {
+                const float4 Tj = __ldg(T4 + j);
+                if (DIM == 2) {
+                    const float xx = Ti.x + Tj.x, xy = Ti.y + Tj.y, yy = Ti.z + Tj.z;
+                    sx = fmaf(t3, xx * rx + xy * ry, sx);
+                    sy = fmaf(t3, xy * rx + yy * ry, sy);
+                } else {
+                    const float2 Tj2 = __ldg(T2 + j);
+                    const float xx = Ti.x + Tj.x, xy = Ti.y + Tj.y, xz = Ti.z + Tj.z;
+                    const float yy = Ti.w + Tj.w, yz = Ti2.x + Tj2.x, zz = Ti2.y + Tj2.y;
+                    sx = fmaf(t3, xx * rx + xy * ry + xz * rz, sx);
+                    sy = fmaf(t3, xy * rx + yy * ry + yz * rz, sy);
+                    sz = fmaf(t3, xz * rx + yz * ry + zz * rz, sz);
+                }
+            }
+        });
+    const float rho = ph.rho0[phi] + d.drho_eval[i];
+    float4 out;
+    out.w = rho * ph.cF * dv;
+    if (d.tag[i] & 2) {
+        out.x = out.y = out.z = 0.f;
+    } else {
+        const float vf = ph.visc_dynamic ? ph.cF / rho : ph.cF;
+        const float sf = ph.cF * ph.inv_mass[phi];
+        out.x = -ph.cF * px + vf * vx + sf * sx + ph.gf[0];
+        out.y = -ph.cF * py + vf * vy + sf * sy + ph.gf[1];
+        out.z = DIM == 3 ? -ph.cF * pz + vf * vz + sf * sz + ph.gf[2] : 0.f;
+    }
+    d.acc[i] = out;
+}
+
+// ---------------------------------------------------------------------------
+// Explicit midpoint predictor-corrector.
+
+template <int DIM>
+__global__ void __launch_bounds__(256) k_predict(Dev d, Grid g, Phys ph, double dt)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= d.n) return;
+    const uint8_t tg = d.tag[k];
+    const float4 a = d.acc[k];
+    const float dr = d.drho_eval[k];         // renormalised density becomes the state
+    d.drho[k] = dr;
+    const float drs = fmaf(0.5f * (float)dt, a.w, dr);
+    d.drho_stage[k] = drs;
+    double xs[3] = {0, 0, 0}, us[3] = {0, 0, 0};
+    const double af[3] = {a.x, a.y, a.z};
+    bool finite = isfinite(drs);
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+        const double x = d.x[(size_t)c * d.n + k], u = d.u[(size_t)c * d.n + k];
+        xs[c] = (tg & 2) ? x : x + 0.5 * dt * u;
+        us[c] = (tg & 2) ? u : u + 0.5 * dt * af[c];
+        finite = finite && isfinite(us[c]) && isfinite(xs[c]);
+    }
+    float4 p = cell_offset<DIM>(g, d.cell[k], xs);
+    // one cell list serves both stages while every particle stays within
+    // cell_size - h of its cell centre on each axis
+    const float lim = (float)(g.csd - ph.hd);
+    if (fabsf(p.x) > lim || fabsf(p.y) > lim || fabsf(p.z) > lim) atomicOr(d.flags, FLAG_SKIN);
+    float vol;
+    p.w = signed_volume(ph, tg & 1, drs, vol);
+    d.pos[k] = p;
+    d.vd[k] = vol * drs;
+    d.vel[k] = make_float4((float)us[0], (float)us[1], (float)us[2], 0.f);
+    if (!finite) atomicOr(d.flags, FLAG_NONFINITE);
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(256) k_correct(Dev d, double dt)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= d.n) return;
+    if (k == 0) *d.step += 1;
+    const uint8_t tg = d.tag[k];
+    const float4 a = d.acc[k];
+    const float dr = fmaf((float)dt, a.w, d.drho[k]);
+    d.drho[k] = dr;
+    bool finite = isfinite(dr);
+    if (!(tg & 2)) {
+        const float4 us = d.vel[k];
+        const double usa[3] = {us.x, us.y, us.z};
+        const double af[3] = {a.x, a.y, a.z};
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) {
+            const double x = d.x[(size_t)c * d.n + k] + dt * usa[c];
+            const double u = d.u[(size_t)c * d.n + k] + dt * af[c];
+            d.x[(size_t)c * d.n + k] = x;
+            d.u[(size_t)c * d.n + k] = u;
+            finite = finite && isfinite(x) && isfinite(u);
+        }
+    }
+    if (!finite) atomicOr(d.flags, FLAG_NONFINITE);
+}
+
+// ---------------------------------------------------------------------------
+// Neighbour sets (same candidate test as the sweeps).
+
+template <int DIM>
+__global__ void __launch_bounds__(256) k_nbr_count(Dev d, Grid g, Phys ph, int *count)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d.n) return;
+    const float4 pi = d.pos[i];
+    int cx, cy, cz;
+    cell_coords(g, d.cell[i], cx, cy, cz);
+    int cnt = 0;
+    for_each_neighbour<DIM>(g, d.cstart, d.pos, cx, cy, cz, pi, ph.R2,
+                            [&](int j, const float4 &, float, float, float, float) { cnt += j != i; });
+    count[i] = cnt;
+}
+
+// Totals of ordered neighbour pairs (j != i): [0] all, [1] of different phase.
+template <int DIM>
+__global__ void __launch_bounds__(256) k_pair_stats(Dev d, Grid g, Phys ph, unsigned long long *tot)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int all = 0, other = 0;
+    if (i < d.n) {
+        const float4 pi = d.pos[i];
+        const int phi = phase_of(pi.w);
+        int cx, cy, cz;
+        cell_coords(g, d.cell[i], cx, cy, cz);
+        for_each_neighbour<DIM>(g, d.cstart, d.pos, cx, cy, cz, pi, ph.R2,
+                                [&](int j, const float4 &pj, float, float, float, float) {
+                                    all += j != i;
+                                    other += phase_of(pj.w) != phi;
+                                });
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        all += __shfl_down_sync(0xffffffffu, all, o);
+        other += __shfl_down_sync(0xffffffffu, other, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(tot, (unsigned long long)all);
+        atomicAdd(tot + 1, (unsigned long long)other);
+    }
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(256) k_nbr_fill(Dev d, Grid g, Phys ph, const long long *start, int *list)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d.n) return;
+    const float4 pi = d.pos[i];
+    int cx, cy, cz;
+    cell_coords(g, d.cell[i], cx, cy, cz);
+    long long w = start[i];
+    for_each_neighbour<DIM>(g, d.cstart, d.pos, cx, cy, cz, pi, ph.R2,
+                            [&](int j, const float4 &, float, float, float, float) {
+                                if (j != i) list[w++] = d.pid[j];
+                            });
+}
+
+// ---------------------------------------------------------------------------
+// Output in original order.
+
+enum ReadKind { RK_X, RK_U, RK_RHO, RK_RHO_EVAL, RK_P, RK_ACC, RK_DRHO, RK_T, RK_CELL, RK_ORDER };
+
+template <int DIM>
+__global__ void __launch_bounds__(256) k_unpermute(Dev d, Phys ph, int kind, double *out, int *iout)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= d.n) return;
+    const int n = d.n;
+    const int p = d.pid[k];
+    const int phs = d.tag[k] & 1;
+    switch (kind) {
+    case RK_X:
+        for (int c = 0; c < DIM; ++c) out[(size_t)p * DIM + c] = d.x[(size_t)c * n + k];
+        break;
+    case RK_U:
+        for (int c = 0; c < DIM; ++c) out[(size_t)p * DIM + c] = d.u[(size_t)c * n + k];
+        break;
+    case RK_RHO:
+        out[p] = (double)ph.rho0[phs] + (double)d.drho[k];
+        break;
+    case RK_RHO_EVAL:
+        out[p] = (double)ph.rho0[phs] + (double)d.drho_eval[k];
+        break;
+    case RK_P:
+        out[p] = d.aux[k].w;
+        break;
+    case RK_ACC: {
+        const float4 a = d.acc[k];
+        const float av[3] = {a.x, a.y, a.z};
+        for (int c = 0; c < DIM; ++c) out[(size_t)p * DIM + c] = av[c];
+        break;
+    }
+    case RK_DRHO:
+        out[p] = d.acc[k].w;
+        break;
+    case RK_T: {
+        const float4 t = d.T4[k];
+        const double v2 = (double)d.aux[k].x * (double)d.aux[k].x;
+        double T[9];
+        if (DIM == 2) {
+            T[0] = t.x; T[1] = t.y; T[2] = t.y; T[3] = t.z;
+        } else {
+            const float2 t2 = d.T2[k];
+            T[0] = t.x; T[1] = t.y; T[2] = t.z;
+            T[3] = t.y; T[4] = t.w; T[5] = t2.x;
+            T[6] = t.z; T[7] = t2.x; T[8] = t2.y;
+        }
+        for (int c = 0; c < DIM * DIM; ++c) out[(size_t)p * DIM * DIM + c] = T[c] / v2;
+        break;
+    }
+    case RK_CELL:
+        iout[p] = d.cell[k];
+        break;
+    case RK_ORDER:
+        iout[k] = p;
+        break;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 diagnostics: deterministic two-level reductions.
+
+constexpr int DIAG_THREADS = 256;
+constexpr int DIAG_K = 16;  // accumulated quantities per pass
+
+__device__ __forceinline__ void block_reduce_store(double (&v)[DIAG_K], double *out)
+{
+    __shared__ double sm[DIAG_THREADS];
+#pragma unroll 1
+    for (int q = 0; q < DIAG_K; ++q) {
+        sm[threadIdx.x] = v[q];
+        __syncthreads();
+        for (int s = DIAG_THREADS / 2; s > 0; s >>= 1) {
+            if ((int)threadIdx.x < s) {
+                // max for the speed slot, sum otherwise
+                sm[threadIdx.x] = q == 15 ? fmax(sm[threadIdx.x], sm[threadIdx.x + s])
+                                          : sm[threadIdx.x] + sm[threadIdx.x + s];
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[q] = sm[0];
+        __syncthreads();
+    }
+}
+
+// pass 0: mass, momentum, energies, oil count and sum of oil positions, max|u|
+// pass 1: covariance of oil positions about the centroid `cen`
+template <int DIM>
+__global__ void __launch_bounds__(DIAG_THREADS) k_diag(Dev d, Phys ph, int pass, const double *cen, const double *grav,
+                                                       const double *mass, double *partial)
+{
+    double v[DIAG_K];
+#pragma unroll
+    for (int q = 0; q < DIAG_K; ++q) v[q] = 0.0;
+    const int n = d.n;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const uint8_t tg = d.tag[k];
+        if (tg & 2) continue;
+        const int oil = tg & 1;
+        double x[3] = {0, 0, 0}, u[3] = {0, 0, 0};
+        for (int c = 0; c < DIM; ++c) {
+            x[c] = d.x[(size_t)c * n + k];
+            u[c] = d.u[(size_t)c * n + k];
+        }
+        if (pass == 0) {
+            const double m = mass[oil];
+            const double u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+            v[0] += m;
+            v[1] += m * u[0];
+            v[2] += m * u[1];
+            v[3] += m * u[2];
+            v[4] += 0.5 * m * u2;
+            v[5] -= m * (grav[0] * x[0] + grav[1] * x[1] + grav[2] * x[2]);
+            if (oil) {
+                v[6] += x[0];
+                v[7] += x[1];
+                v[8] += x[2];
+                v[9] += 1.0;
+            }
+            v[15] = fmax(v[15], sqrt(u2));
+        } else if (oil) {
+            const double a = x[0] - cen[0], b = x[1] - cen[1], c = x[2] - cen[2];
+            v[0] += a * a;
+            v[1] += a * b;
+            v[2] += a * c;
+            v[3] += b * b;
+            v[4] += b * c;
+            v[5] += c * c;
+        }
+    }
+    block_reduce_store(v, partial + (size_t)blockIdx.x * DIAG_K);
+}
+
+__global__ void __launch_bounds__(DIAG_K) k_diag_final(const double *partial, int nblocks, double *out)
+{
+    const int q = threadIdx.x;
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) {
+        const double v = partial[(size_t)b * DIAG_K + q];
+        s = q == 15 ? fmax(s, v) : s + v;
+    }
+    out[q] = s;
+}
+
+}  // namespace sphgb

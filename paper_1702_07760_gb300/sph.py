@@ -1,0 +1,228 @@
+"""Thin ctypes binding of the C ABI in ``include/sph.h`` (libsph.so).
+
+Argument marshalling only: every step of the particle loop runs in the CUDA
+library.  Loading fails loudly when the library is missing; there is no CPU
+path.  Arrays are numpy, in the caller's particle order.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsph.so")
+
+SPH_OK = 0
+ERRORS = {-1: "SPH_EINVAL", -2: "SPH_ENOMEM", -3: "SPH_ECUDA", -4: "SPH_ENONFINITE",
+          -5: "SPH_ECFL", -6: "SPH_EDOMAIN"}
+VISC_DYNAMIC, VISC_KINEMATIC = 0, 1
+FIELD = dict(pos=0, vel=1, rho=2, rho_eval=3, pressure=4, acc=5, drho=6, tensor=7, cell=8, order=9)
+
+# entry points declared in include/sph.h
+EXPORTS = ["sph_create", "sph_set_state", "sph_build_cells", "sph_eval_rates", "sph_step", "sph_run",
+           "sph_sync", "sph_read", "sph_neighbours", "sph_pair_stats", "sph_diag", "sph_timing_enable",
+           "sph_timing_reset", "sph_timing_count", "sph_timing_read", "sph_num_particles",
+           "sph_step_index", "sph_num_cells", "sph_destroy", "sph_last_error"]
+
+
+class SphError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class SphParams(C.Structure):
+    _fields_ = [
+        ("dim", C.c_int32), ("visc_form", C.c_int32), ("renorm_every", C.c_int32),
+        ("reserved", C.c_int32), ("h", C.c_double), ("c0", C.c_double), ("gamma", C.c_double),
+        ("delta", C.c_double), ("alpha_s", C.c_double), ("cell_size", C.c_double),
+        ("g", C.c_double * 3), ("rho0", C.c_double * 2), ("mu", C.c_double * 2),
+        ("mass", C.c_double * 2), ("box_lo", C.c_double * 3), ("box_hi", C.c_double * 3),
+    ]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Loads libsph.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libsph.so not found at {path}: run paper_1702_07760_gb300.build.build()")
+    L = C.CDLL(path)
+    P, vp, dp, u8p = C.POINTER, C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_uint8)
+    H = C.c_void_p
+    L.sph_create.argtypes = [P(SphParams), C.c_int64, dp, dp, dp, u8p, u8p, vp, P(H)]
+    L.sph_set_state.argtypes = [H, dp, dp, dp]
+    for f in (L.sph_build_cells, L.sph_eval_rates, L.sph_sync, L.sph_timing_reset):
+        f.argtypes = [H]
+    L.sph_step.argtypes = [H, C.c_double]
+    L.sph_run.argtypes = [H, C.c_double, C.c_int64, C.c_int]
+    L.sph_read.argtypes = [H, C.c_int, vp, C.c_int64]
+    L.sph_neighbours.argtypes = [H, P(C.c_int64), P(C.c_int32), C.c_int64]
+    L.sph_neighbours.restype = C.c_int64
+    L.sph_diag.argtypes = [H, dp]
+    L.sph_pair_stats.argtypes = [H, P(C.c_int64)]
+    L.sph_timing_enable.argtypes = [H, C.c_int]
+    L.sph_timing_count.argtypes = []
+    L.sph_timing_read.argtypes = [H, C.c_int, P(C.c_char_p), P(C.c_int64), P(C.c_double)]
+    for f in (L.sph_num_particles, L.sph_step_index, L.sph_num_cells):
+        f.argtypes = [H]
+        f.restype = C.c_int64
+    L.sph_destroy.argtypes = [H]
+    L.sph_destroy.restype = None
+    L.sph_last_error.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def make_params(p: dict) -> SphParams:
+    s = SphParams()
+    s.dim = int(p["dim"])
+    s.visc_form = int(p.get("visc_form", 0))
+    s.renorm_every = int(p.get("renorm_every", 1))
+    s.reserved = 0
+    s.h, s.c0, s.gamma = p["h"], p["c0"], p.get("gamma", 7.0)
+    s.delta, s.alpha_s, s.cell_size = p["delta"], p["alpha_s"], p["cell_size"]
+    for k in range(3):
+        s.g[k], s.box_lo[k], s.box_hi[k] = p["g"][k], p["box_lo"][k], p["box_hi"][k]
+    for k in range(2):
+        s.rho0[k], s.mu[k], s.mass[k] = p["rho0"][k], p["mu"][k], p["mass"][k]
+    return s
+
+
+def _check(rc: int):
+    if rc != SPH_OK:
+        raise SphError(rc, load().sph_last_error().decode())
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+class Simulation:
+    """One two-phase SPH simulation resident on the GPU."""
+
+    def __init__(self, params: dict, x, u, rho, phase, wall, stream: int | None = None):
+        L = load()
+        self.params = dict(params)
+        self.dim = int(params["dim"])
+        x = np.ascontiguousarray(x, np.float64)
+        u = np.ascontiguousarray(u, np.float64)
+        rho = np.ascontiguousarray(rho, np.float64)
+        phase = np.ascontiguousarray(phase, np.uint8)
+        wall = np.ascontiguousarray(wall, np.uint8)
+        self.n = len(x)
+        self._p = make_params(params)
+        h = C.c_void_p()
+        _check(L.sph_create(C.byref(self._p), self.n, _dp(x), _dp(u), _dp(rho),
+                            phase.ctypes.data_as(C.POINTER(C.c_uint8)),
+                            wall.ctypes.data_as(C.POINTER(C.c_uint8)),
+                            C.c_void_p(stream or 0), C.byref(h)))
+        self._h = h
+
+    @classmethod
+    def from_workload(cls, w, stream=None):
+        return cls(w.params, w.x, w.u, w.rho, w.phase, w.wall, stream)
+
+    # -- stepping ---------------------------------------------------------
+    def set_state(self, x, u, rho):
+        x = np.ascontiguousarray(x, np.float64)
+        u = np.ascontiguousarray(u, np.float64)
+        rho = np.ascontiguousarray(rho, np.float64)
+        _check(load().sph_set_state(self._h, _dp(x), _dp(u), _dp(rho)))
+
+    def build_cells(self):
+        _check(load().sph_build_cells(self._h))
+
+    def eval_rates(self):
+        _check(load().sph_eval_rates(self._h))
+
+    def step(self, dt: float):
+        _check(load().sph_step(self._h, dt))
+
+    def run(self, dt: float, nsteps: int, graph: bool = True):
+        _check(load().sph_run(self._h, dt, int(nsteps), int(bool(graph))))
+
+    def sync(self):
+        _check(load().sph_sync(self._h))
+
+    # -- output -----------------------------------------------------------
+    def read(self, field: str) -> np.ndarray:
+        n, d = self.n, self.dim
+        shapes = dict(pos=(n, d), vel=(n, d), acc=(n, d), tensor=(n, d, d))
+        shape = shapes.get(field, (n,))
+        dtype = np.int32 if field in ("cell", "order") else np.float64
+        out = np.empty(shape, dtype)
+        _check(load().sph_read(self._h, FIELD[field], out.ctypes.data_as(C.c_void_p), out.nbytes))
+        return out
+
+    def neighbours(self):
+        L = load()
+        start = np.zeros(self.n + 1, np.int64)
+        L.sph_neighbours(self._h, start.ctypes.data_as(C.POINTER(C.c_int64)), None, 0)
+        cap = int(start[-1])
+        lst = np.zeros(max(cap, 1), np.int32)
+        r = L.sph_neighbours(self._h, start.ctypes.data_as(C.POINTER(C.c_int64)),
+                             lst.ctypes.data_as(C.POINTER(C.c_int32)), cap)
+        if r < 0:
+            _check(int(r))
+        return start, lst[:cap]
+
+    def pair_stats(self):
+        """(ordered neighbour pairs, of which across phases) at the current positions."""
+        out = np.zeros(2, np.int64)
+        _check(load().sph_pair_stats(self._h, out.ctypes.data_as(C.POINTER(C.c_int64))))
+        return int(out[0]), int(out[1])
+
+    def diagnostics(self) -> dict:
+        out = np.zeros(12)
+        _check(load().sph_diag(self._h, _dp(out)))
+        d = self.dim
+        return dict(mass=out[0], momentum=out[1:1 + d].copy(), e_kin=out[4], e_pot=out[5],
+                    centroid=out[6:6 + d].copy(), sphericity=out[9], u_max=out[10], n_oil=int(out[11]))
+
+    # -- timing -----------------------------------------------------------
+    def timing(self, enable: bool):
+        _check(load().sph_timing_enable(self._h, int(bool(enable))))
+
+    def timing_reset(self):
+        _check(load().sph_timing_reset(self._h))
+
+    def timing_read(self) -> dict:
+        L = load()
+        res = {}
+        for k in range(L.sph_timing_count()):
+            name, cnt, ms = C.c_char_p(), C.c_int64(), C.c_double()
+            _check(L.sph_timing_read(self._h, k, C.byref(name), C.byref(cnt), C.byref(ms)))
+            res[name.value.decode()] = (int(cnt.value), float(ms.value))
+        return res
+
+    @property
+    def step_index(self) -> int:
+        return int(load().sph_step_index(self._h))
+
+    @property
+    def num_cells(self) -> int:
+        return int(load().sph_num_cells(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().sph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

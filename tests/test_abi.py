@@ -1,0 +1,74 @@
+"""CPU checks of the C ABI: the library builds, loads without a GPU, and
+exports every entry point that include/sph.h declares; the binding names the
+same set."""
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_1702_07760_gb300 import build as B
+from paper_1702_07760_gb300 import sph
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared(header="sph.h"):
+    txt = open(os.path.join(ROOT, "include", header)).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(sph_[a-z0-9_]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return sph.load()
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = declared()
+    assert len(names) >= 15
+    for nm in names:
+        assert hasattr(lib, nm), nm
+    out = subprocess.run(["nm", "-D", "--defined-only", sph.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (sph_\w+)", out))
+    assert set(names) <= exported
+
+
+def test_binding_covers_the_header(lib):
+    assert sorted(sph.EXPORTS) == declared()
+
+
+def test_invalid_parameters_are_rejected_without_a_gpu(lib):
+    from paper_1702_07760_gb300 import workloads as WL
+    w = WL.drop_tank(2, (4, 4))
+    bad = dict(w.params, gamma=5.0)
+    with pytest.raises(sph.SphError) as e:
+        sph.Simulation(bad, w.x, w.u, w.rho, w.phase, w.wall)
+    assert e.value.code == -1 and "gamma" in str(e.value)
+    bad = dict(w.params, cell_size=w.params["h"])
+    with pytest.raises(sph.SphError) as e:
+        sph.Simulation(bad, w.x, w.u, w.rho, w.phase, w.wall)
+    assert e.value.code == -1
+    x = w.x.copy()
+    x[0, 0] = w.params["box_hi"][0] + 1.0
+    with pytest.raises(sph.SphError) as e:
+        sph.Simulation(w.params, x, w.u, w.rho, w.phase, w.wall)
+    assert e.value.code == -1 and "outside" in str(e.value)
+    ph = w.phase.copy()
+    wl = w.wall.copy()
+    ph[wl == 1] = 1
+    with pytest.raises(sph.SphError):
+        sph.Simulation(w.params, w.x, w.u, w.rho, ph, wl)
+
+
+def test_kernels_compile_for_sm103a_without_spills():
+    out = subprocess.run(B.nvcc_command("/tmp/libsph_probe.so", ("-Xptxas", "-v")),
+                         capture_output=True, text=True)
+    assert out.returncode == 0, out.stderr[-2000:]
+    info = out.stderr
+    for kern in ("k_sweep_b",):
+        blocks = [b for b in info.split("Function properties for ") if kern in b.split("\n")[0]]
+        assert blocks, kern
+        for b in blocks:
+            assert "0 bytes spill stores" in b, b[:400]

@@ -1,0 +1,231 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances (FP32 interactions against an FP64 oracle):
+* cell ids, sort order and neighbour sets: bit-exact on grid-quantised
+  positions (dyadic jitter, so no pair distance lies within FP32 rounding of
+  the support radius 2h);
+* density after renormalisation and density rate: max over particles of
+  |x_gpu - x_ref| / |x_ref| <= 1e-5 (density), and <= 1e-5 of the field's
+  largest magnitude (density rate);
+* acceleration: max_i |a_gpu,i - a_ref,i| / max_i |a_ref,i| <= 1e-5 (the
+  normwise relative error), and the per-particle error is reported against
+  max(|a_ref,i|, |g|).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1702_07760_gb300 import workloads as WL
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def sphmod():
+    from paper_1702_07760_gb300 import build as B
+    from paper_1702_07760_gb300 import sph
+    B.build()
+    sph.load()
+    return sph
+
+
+def rel_err_field(gpu, ref):
+    """max_i |gpu_i - ref_i| / max_i |ref_i| (vectors: Euclidean norms)."""
+    g = np.atleast_2d(gpu.T).T
+    r = np.atleast_2d(ref.T).T
+    num = np.linalg.norm((g - r).reshape(len(g), -1), axis=1)
+    den = np.linalg.norm(r.reshape(len(r), -1), axis=1)
+    return num.max() / den.max()
+
+
+def rel_err_particle(gpu, ref, floor):
+    g = np.atleast_2d(gpu.T).T
+    r = np.atleast_2d(ref.T).T
+    num = np.linalg.norm((g - r).reshape(len(g), -1), axis=1)
+    den = np.maximum(np.linalg.norm(r.reshape(len(r), -1), axis=1), floor)
+    return (num / den).max()
+
+
+CASES = {
+    "2d_small": lambda: WL.drop_tank(2, (40, 60), drop_d_dx=12, seed=5, perturb=True),
+    "2d_cfg": lambda: WL.drop_2d(seed=0, perturb=True),
+    "3d_small": lambda: WL.drop_tank(3, (20, 20, 36), drop_d_dx=10, seed=7, perturb=True),
+}
+
+
+@pytest.mark.parametrize("case", ["2d_small", "3d_small"])
+def test_cells_order_and_neighbours_bit_exact(sphmod, case):
+    dim = 2 if case.startswith("2d") else 3
+    shape = (37, 53) if dim == 2 else (13, 17, 19)   # ragged sizes, several 256-thread tiles
+    w = WL.drop_tank(dim, shape, drop_d_dx=8, seed=13, quantise=16)
+    sim = sphmod.Simulation.from_workload(w)
+    sim.build_cells()
+    cells = sim.read("cell")
+    order = sim.read("order")
+    ref_cells = oracle.cell_ids(w.params, w.x)
+    assert np.array_equal(cells, ref_cells)
+    assert np.array_equal(order, oracle.sort_perm(ref_cells).astype(np.int32))
+    s_gpu, l_gpu = sim.neighbours()
+    s_ref, l_ref = oracle.neighbours(w.params, w.x, "brute")
+    assert np.array_equal(s_gpu, s_ref)
+    assert np.array_equal(l_gpu, l_ref)
+    sim.close()
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_single_evaluation_matches_oracle(sphmod, case):
+    w = CASES[case]()
+    p = w.params
+    sim = sphmod.Simulation.from_workload(w)
+    sim.eval_rates()
+    got = {k: sim.read(k) for k in ("rho_eval", "pressure", "acc", "drho", "tensor")}
+    ref = oracle.evaluate(p, w.x, w.u, w.rho, w.phase, w.wall, renorm=True)
+    fl = w.wall == 0
+    e_rho = np.abs(got["rho_eval"] / ref["rho"] - 1).max()
+    e_p = rel_err_field(got["pressure"], ref["P"])
+    e_a = rel_err_field(got["acc"][fl], ref["a"][fl])
+    e_a_pp = rel_err_particle(got["acc"][fl], ref["a"][fl], np.linalg.norm(p["g"]))
+    e_dr = rel_err_field(got["drho"], ref["drho"])
+    e_T = rel_err_field(got["tensor"], ref["T"])
+    print(f"\n[{case}] n={w.n} rho {e_rho:.2e} P {e_p:.2e} acc {e_a:.2e} (per particle, floor |g|: "
+          f"{e_a_pp:.2e}) drho {e_dr:.2e} T {e_T:.2e}")
+    assert np.all(got["acc"][~fl] == 0.0)
+    assert e_rho <= TOL
+    assert e_p <= TOL
+    assert e_a <= TOL
+    assert e_dr <= TOL
+    assert e_T <= 1e-4
+    sim.close()
+
+
+def test_one_step_matches_oracle(sphmod):
+    w = WL.drop_2d(seed=2, perturb=True)
+    p = w.params
+    dt = WL.stable_dt(p)
+    sim = sphmod.Simulation.from_workload(w)
+    sim.step(dt)
+    sim.sync()
+    x, u, rho = sim.read("pos"), sim.read("vel"), sim.read("rho")
+    xr, ur, rr = oracle.run(p, w.x, w.u, w.rho, w.phase, w.wall, dt, 1)
+    dx = p["dx"]
+    e_x = np.abs(x - xr).max() / dx
+    e_u = rel_err_field(u - w.u, ur - w.u)        # velocity increment dt * a*
+    e_r = np.abs(rho / rr - 1).max()
+    print(f"\n[one step] |dx|/dx {e_x:.2e} du {e_u:.2e} rho {e_r:.2e}")
+    assert e_x < 1e-9
+    assert e_u < TOL
+    assert e_r < TOL
+    sim.close()
+
+
+def test_graph_replay_is_bit_identical_to_eager(sphmod):
+    w = WL.drop_tank(2, (30, 40), drop_d_dx=10, seed=3, perturb=True)
+    dt = WL.stable_dt(w.params)
+    a = sphmod.Simulation.from_workload(w)
+    b = sphmod.Simulation.from_workload(w)
+    a.run(dt, 9, graph=False)
+    b.run(dt, 9, graph=True)
+    for f in ("pos", "vel", "rho"):
+        assert np.array_equal(a.read(f), b.read(f)), f
+    assert a.step_index == b.step_index == 9
+
+
+def test_restart_is_bit_exact(sphmod):
+    w = WL.drop_tank(2, (30, 40), drop_d_dx=10, seed=4, perturb=True)
+    dt = WL.stable_dt(w.params)
+    a = sphmod.Simulation.from_workload(w)
+    a.run(dt, 20)
+    b = sphmod.Simulation.from_workload(w)
+    b.run(dt, 10)
+    x, u, r = b.read("pos"), b.read("vel"), b.read("rho")
+    c = sphmod.Simulation(w.params, x, u, r, w.phase, w.wall)
+    c.run(dt, 10)
+    for f in ("pos", "vel", "rho"):
+        assert np.array_equal(a.read(f), c.read(f)), f
+
+
+def test_diagnostics_match_oracle(sphmod):
+    w = WL.drop_tank(3, (16, 16, 24), drop_d_dx=8, seed=9, perturb=True)
+    sim = sphmod.Simulation.from_workload(w)
+    d = sim.diagnostics()
+    r = oracle.diagnostics(w.params, w.x, w.u, w.phase, w.wall)
+    assert abs(d["mass"] / r["mass"] - 1) < 1e-12
+    assert np.allclose(d["momentum"], r["momentum"], rtol=1e-10, atol=1e-12 * r["mass"])
+    assert abs(d["e_kin"] / r["e_kin"] - 1) < 1e-10
+    assert abs(d["e_pot"] / r["e_pot"] - 1) < 1e-10
+    assert np.allclose(d["centroid"], r["centroid"], rtol=1e-12)
+    assert abs(d["sphericity"] - r["sphericity"]) < 1e-9
+    assert abs(d["u_max"] - r["u_max"]) < 1e-12
+    assert d["n_oil"] == r["n_oil"]
+
+
+def test_errors_are_reported_not_faulted(sphmod):
+    w = WL.drop_tank(2, (20, 20), drop_d_dx=6, seed=1)
+    dt = WL.stable_dt(w.params)
+    sim = sphmod.Simulation.from_workload(w)
+    # a non-finite velocity made on the host
+    u = w.u.copy()
+    u[np.nonzero(w.wall == 0)[0][0], 0] = np.nan
+    sim.set_state(w.x, u, w.rho)
+    with pytest.raises(sphmod.SphError) as e:
+        sim.run(dt, 2)
+    assert e.value.code == -4
+    # a step too large for the cell skin
+    sim2 = sphmod.Simulation.from_workload(w)
+    u = w.u.copy()
+    u[w.wall == 0] = 0.5
+    sim2.set_state(w.x, u, w.rho)
+    # predictor displacement dt/2 * 0.5 m/s = 1e-5 m > skin (cell_size - 2h)/2 = 8.1e-6 m
+    with pytest.raises(sphmod.SphError) as e:
+        sim2.run(4e-5, 1)
+    assert e.value.code == -5
+    with pytest.raises(sphmod.SphError):
+        sim2.step(-1.0)
+
+
+def test_empty_simulation(sphmod):
+    w = WL.drop_tank(2, (4, 4))
+    sim = sphmod.Simulation(w.params, w.x[:0], w.u[:0], w.rho[:0], w.phase[:0], w.wall[:0])
+    sim.run(1e-6, 3)
+    assert sim.read("pos").shape == (0, 2)
+    assert sim.step_index == 3
+
+
+@pytest.mark.slow
+def test_200_steps_drift_against_oracle(sphmod):
+    """2-D drop rise, 200 steps: FP32 GPU vs FP64 oracle drift report."""
+    w = WL.drop_2d(seed=0)
+    p = w.params
+    dt = WL.stable_dt(p)
+    sim = sphmod.Simulation.from_workload(w)
+    sim.run(dt, 200)
+    x, u, rho = sim.read("pos"), sim.read("vel"), sim.read("rho")
+    xr, ur, rr = oracle.run(p, w.x, w.u, w.rho, w.phase, w.wall, dt, 200)
+    e_x = np.abs(x - xr).max() / p["dx"]
+    e_u = np.abs(u - ur).max() / max(np.abs(ur).max(), 1e-12)
+    e_r = np.abs(rho / rr - 1).max()
+    dg = sim.diagnostics()
+    dr = oracle.diagnostics(p, xr, ur, w.phase, w.wall)
+    e_c = np.linalg.norm(dg["centroid"] - dr["centroid"]) / (2 * w.meta["drop_radius"])
+    print(f"\n[200 steps] max|dx|/dx {e_x:.2e} u {e_u:.2e} rho {e_r:.2e} centroid/D {e_c:.2e}")
+    assert e_x < 1e-4 and e_r < 1e-4 and e_c < 1e-6 and e_u < 1e-2
+
+
+def test_full_size_3d_evaluation(sphmod):
+    """656 600-particle 3-D drop rise, the benchmark's workload and launch
+    configuration: single evaluation against the oracle on every particle."""
+    w = WL.drop_3d(perturb=True)
+    p = w.params
+    sim = sphmod.Simulation.from_workload(w)
+    sim.eval_rates()
+    got_r, got_a, got_d = sim.read("rho_eval"), sim.read("acc"), sim.read("drho")
+    ref = oracle.evaluate(p, w.x, w.u, w.rho, w.phase, w.wall, renorm=True)
+    fl = w.wall == 0
+    e_rho = np.abs(got_r / ref["rho"] - 1).max()
+    e_a = rel_err_field(got_a[fl], ref["a"][fl])
+    e_a_pp = rel_err_particle(got_a[fl], ref["a"][fl], np.linalg.norm(p["g"]))
+    e_dr = rel_err_field(got_d, ref["drho"])
+    print(f"\n[3d full n={w.n}] rho {e_rho:.2e} acc {e_a:.2e} (per particle {e_a_pp:.2e}) drho {e_dr:.2e}")
+    assert e_rho <= TOL and e_a <= TOL and e_dr <= TOL
