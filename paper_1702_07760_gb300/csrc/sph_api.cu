@@ -200,9 +200,11 @@ int sph_sim::check_flags()
     if (timing) collect_timing();
     if (f == 0) return SPH_OK;
     CU(cudaMemsetAsync(flags, 0, sizeof(unsigned), stream));
-    if (f & FLAG_NONFINITE) return fail(SPH_ENONFINITE, "a non-finite value appeared in the particle state");
+    // the most specific cause first: a step too large for the skin often
+    // also sends particles out of the box or produces non-finite values
+    if (f & FLAG_SKIN) return fail(SPH_ECFL, "a particle moved beyond the cell skin within a step; reduce dt or enlarge cell_size");
     if (f & FLAG_DOMAIN) return fail(SPH_EDOMAIN, "a particle left the box covered by the cell grid");
-    return fail(SPH_ECFL, "a particle moved beyond the cell skin within a step; reduce dt or enlarge cell_size");
+    return fail(SPH_ENONFINITE, "a non-finite value appeared in the particle state");
 }
 
 // ---------------------------------------------------------------------------

@@ -172,14 +172,16 @@ def test_errors_are_reported_not_faulted(sphmod):
     with pytest.raises(sphmod.SphError) as e:
         sim.run(dt, 2)
     assert e.value.code == -4
-    # a step too large for the cell skin
+    # one particle fast enough that the predictor carries it 1.2 cell edges:
+    # beyond the skin whatever its offset in the cell
     sim2 = sphmod.Simulation.from_workload(w)
     u = w.u.copy()
-    u[w.wall == 0] = 0.5
+    fl = np.nonzero(w.wall == 0)[0]
+    k = fl[np.argmin(np.linalg.norm(w.x[fl] - w.x[fl].mean(0), axis=1))]
+    u[k, 0] = 2 * 1.2 * w.params["cell_size"] / dt
     sim2.set_state(w.x, u, w.rho)
-    # predictor displacement dt/2 * 0.5 m/s = 1e-5 m > skin (cell_size - 2h)/2 = 8.1e-6 m
     with pytest.raises(sphmod.SphError) as e:
-        sim2.run(4e-5, 1)
+        sim2.run(dt, 1)
     assert e.value.code == -5
     with pytest.raises(sphmod.SphError):
         sim2.step(-1.0)
