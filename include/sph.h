@@ -46,6 +46,7 @@ extern "C" {
 #define SPH_ENONFINITE -4  /* a NaN or Inf appeared in the state */
 #define SPH_ECFL       -5  /* a particle moved farther in a step than the cell skin allows */
 #define SPH_EDOMAIN    -6  /* a particle left the box of the cell grid */
+#define SPH_ECAPACITY  -7  /* a particle has more neighbours than max_neighbours */
 
 /* Viscous term forms (Sec. II-C) */
 #define SPH_VISC_DYNAMIC   0  /* Eq. visc_2: (1/rho_i) sum 2 mu_ij (m_j/rho_j) (r.gradW)/(r^2+delta^2) u_ij */
@@ -72,15 +73,17 @@ typedef struct sph_params {
     int32_t dim;           /* 2 or 3 */
     int32_t visc_form;     /* SPH_VISC_DYNAMIC or SPH_VISC_KINEMATIC */
     int32_t renorm_every;  /* Eq. ct_dist_3 at stage 1 of steps with step % renorm_every == 0; 0 = never */
-    int32_t reserved;      /* must be 0 */
+    int32_t max_neighbours;/* capacity of the per-particle neighbour list (pairs within
+                              cell_size); 0 selects 48 in 2-D and 128 in 3-D */
     double h;              /* smoothing length; the Wendland C2 kernel has support 2h */
     double c0;             /* reference speed of sound C_s0 (Eq. beta) */
     double gamma;          /* exponent of Eq. state; must be 7 (the paper's value) */
     double delta;          /* regulariser of the viscous term (the paper uses 0.1 h) */
     double alpha_s;        /* interfacial surface tension coefficient (Eq. csf) */
-    double cell_size;      /* cell edge of the neighbour grid, >= 2h; the excess
-                              (cell_size - 2h)/2 is the displacement skin within
-                              which one cell list serves both stages of a step */
+    double cell_size;      /* cell edge of the neighbour grid, >= 2h; the list of
+                              each step holds the pairs closer than cell_size, and
+                              the excess (cell_size - 2h)/2 is the displacement
+                              skin within which that list serves both stages */
     double g[3];           /* gravitational acceleration */
     double rho0[2];        /* reference density per phase: [0] water, [1] oil */
     double mu[2];          /* dynamic viscosity per phase */

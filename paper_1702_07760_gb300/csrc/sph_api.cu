@@ -33,11 +33,11 @@ int fail(int code, const std::string &msg)
     } while (0)
 
 enum KernelId {
-    KI_MEMSET, KI_HASH, KI_SCAN, KI_SCATTER, KI_RANK, KI_GATHER, KI_SWEEP_A, KI_SWEEP_B,
+    KI_MEMSET, KI_HASH, KI_SCAN, KI_SCATTER, KI_RANK, KI_GATHER, KI_LIST, KI_SWEEP_A, KI_SWEEP_B,
     KI_PREDICT, KI_CORRECT, KI_COUNT
 };
 const char *k_names[KI_COUNT] = {"count_reset", "cell_hash", "cell_scan", "cell_scatter",
-                                 "cell_rank", "reorder_gather", "sweep_a", "sweep_b",
+                                 "cell_rank", "reorder_gather", "neighbour_list", "sweep_a", "sweep_b",
                                  "predict", "correct"};
 
 struct PendingTiming {
@@ -160,6 +160,10 @@ void sph_sim::enqueue_build_cells()
         if (dim == 2) k_gather<2><<<blocks(n), 256, 0, stream>>>(s, t, grid, phys, perm, cell_tmp);
         else k_gather<3><<<blocks(n), 256, 0, stream>>>(s, t, grid, phys, perm, cell_tmp);
     });
+    launch(KI_LIST, [&] {
+        if (dim == 2) k_build_list<2><<<blocks(n), 256, 0, stream>>>(t, grid, phys);
+        else k_build_list<3><<<blocks(n), 256, 0, stream>>>(t, grid, phys);
+    });
     cur ^= 1;
 }
 
@@ -167,12 +171,12 @@ void sph_sim::enqueue_eval(int stage1, const float *drho_in)
 {
     Dev &d = buf[cur];
     launch(KI_SWEEP_A, [&] {
-        if (dim == 2) k_sweep_a<2><<<blocks(n), 256, 0, stream>>>(d, grid, phys, drho_in, stage1);
-        else k_sweep_a<3><<<blocks(n), 256, 0, stream>>>(d, grid, phys, drho_in, stage1);
+        if (dim == 2) k_sweep_a<2><<<blocks(n), 256, 0, stream>>>(d, phys, drho_in, stage1);
+        else k_sweep_a<3><<<blocks(n), 256, 0, stream>>>(d, phys, drho_in, stage1);
     });
     launch(KI_SWEEP_B, [&] {
-        if (dim == 2) k_sweep_b<2><<<blocks(n), 256, 0, stream>>>(d, grid, phys);
-        else k_sweep_b<3><<<blocks(n), 256, 0, stream>>>(d, grid, phys);
+        if (dim == 2) k_sweep_b<2><<<blocks(n), 256, 0, stream>>>(d, phys);
+        else k_sweep_b<3><<<blocks(n), 256, 0, stream>>>(d, phys);
     });
 }
 
@@ -203,8 +207,9 @@ int sph_sim::check_flags()
     // the most specific cause first: a step too large for the skin often
     // also sends particles out of the box or produces non-finite values
     if (f & FLAG_SKIN) return fail(SPH_ECFL, "a particle moved beyond the cell skin within a step; reduce dt or enlarge cell_size");
-    if (f & FLAG_DOMAIN) return fail(SPH_EDOMAIN, "a particle left the box covered by the cell grid");
-    return fail(SPH_ENONFINITE, "a non-finite value appeared in the particle state");
+    if (f & FLAG_NONFINITE) return fail(SPH_ENONFINITE, "a non-finite value appeared in the particle state");
+    if (f & FLAG_LIST) return fail(SPH_ECAPACITY, "a particle has more neighbours than max_neighbours");
+    return fail(SPH_EDOMAIN, "a particle left the box covered by the cell grid");
 }
 
 // ---------------------------------------------------------------------------
@@ -236,7 +241,8 @@ int validate(const sph_params *P, int64_t n)
     if (P->visc_form != SPH_VISC_DYNAMIC && P->visc_form != SPH_VISC_KINEMATIC)
         return fail(SPH_EINVAL, "visc_form must be SPH_VISC_DYNAMIC or SPH_VISC_KINEMATIC");
     if (P->renorm_every < 0) return fail(SPH_EINVAL, "renorm_every must be >= 0");
-    if (P->reserved != 0) return fail(SPH_EINVAL, "reserved must be 0");
+    if (P->max_neighbours < 0 || P->max_neighbours > 4096)
+        return fail(SPH_EINVAL, "max_neighbours must be in [0, 4096]");
     if (!(P->h > 0) || !std::isfinite(P->h)) return fail(SPH_EINVAL, "h must be positive");
     if (!(P->c0 > 0) || !std::isfinite(P->c0)) return fail(SPH_EINVAL, "c0 must be positive");
     if (P->gamma != 7.0) return fail(SPH_EINVAL, "gamma must be 7 (the exponent of the paper's equation of state)");
@@ -337,8 +343,11 @@ int sph_create(const sph_params *params, int64_t n, const double *x, const doubl
     s->grid.ny = dims[1];
     s->grid.nz = dims[2];
     s->grid.csd = P.cell_size;
-    s->grid.cs = (float)P.cell_size;
     for (int c = 0; c < 3; ++c) s->grid.lo[c] = c < dim ? P.box_lo[c] : 0.0;
+    // largest power of two not above the cell edge
+    int e2 = 0;
+    std::frexp(P.cell_size, &e2);
+    s->grid.q = std::ldexp(1.0, e2 - 1);
     // physics constants
     const double pi = 3.14159265358979323846;
     const double h = P.h;
@@ -346,6 +355,9 @@ int sph_create(const sph_params *params, int64_t n, const double *x, const doubl
     Phys &ph = s->phys;
     ph.inv_h = (float)(1.0 / h);
     ph.R2 = (float)(4.0 * h * h);
+    ph.RL2 = (float)(P.cell_size * P.cell_size);
+    ph.skin = 0.5 * (P.cell_size - 2.0 * h);
+    ph.kmax = P.max_neighbours > 0 ? P.max_neighbours : (dim == 2 ? 48 : 128);
     ph.cF = (float)(-5.0 * alpha_d / (h * h));
     for (int k = 0; k < 2; ++k) {
         ph.mass[k] = (float)P.mass[k];
@@ -367,7 +379,6 @@ int sph_create(const sph_params *params, int64_t n, const double *x, const doubl
     ph.visc_dynamic = P.visc_form == SPH_VISC_DYNAMIC;
     ph.renorm_every = P.renorm_every;
     for (int c = 0; c < 3; ++c) ph.gf[c] = c < dim ? (float)P.g[c] : 0.f;
-    ph.hd = h;
 
     auto cleanup = [&](int code) {
         for (void *p : s->allocs) cudaFree(p);
@@ -396,9 +407,12 @@ int sph_create(const sph_params *params, int64_t n, const double *x, const doubl
     }
     Dev &a0 = s->buf[0];
     if (!err) {
-        err |= s->alloc(&a0.pos, N);
-        err |= s->alloc(&a0.vd, N);
+        err |= s->alloc(&a0.phi, N);
+        err |= s->alloc(&a0.plo, N);
         err |= s->alloc(&a0.vel, N);
+        err |= s->alloc(&a0.nbr, N * (size_t)ph.kmax);
+        err |= s->alloc(&a0.ncnt, N);
+        err |= s->alloc(&a0.nflag, N);
         err |= s->alloc(&a0.drho_stage, N);
         err |= s->alloc(&a0.drho_eval, N);
         err |= s->alloc(&a0.aux, N);
@@ -419,7 +433,8 @@ int sph_create(const sph_params *params, int64_t n, const double *x, const doubl
     }
     if (err) return cleanup(SPH_ENOMEM);
     Dev &a1 = s->buf[1];
-    a1.pos = a0.pos; a1.vd = a0.vd; a1.vel = a0.vel; a1.drho_stage = a0.drho_stage;
+    a1.phi = a0.phi; a1.plo = a0.plo; a1.vel = a0.vel; a1.drho_stage = a0.drho_stage;
+    a1.nbr = a0.nbr; a1.ncnt = a0.ncnt; a1.nflag = a0.nflag;
     a1.drho_eval = a0.drho_eval; a1.aux = a0.aux; a1.T4 = a0.T4; a1.T2 = a0.T2; a1.acc = a0.acc;
     a1.cstart = a0.cstart;
     a0.flags = a1.flags = s->flags;
@@ -681,8 +696,8 @@ int sph_diag(sph_handle s, double out[12])
     CU(cudaMemcpyAsync(grav, consts, sizeof(double) * 3, cudaMemcpyHostToDevice, s->stream));
     CU(cudaMemcpyAsync(mass, s->P.mass, sizeof(double) * 2, cudaMemcpyHostToDevice, s->stream));
     double r0[DIAG_K], r1[DIAG_K];
-    if (s->dim == 2) k_diag<2><<<nb, DIAG_THREADS, 0, s->stream>>>(s->D(), s->phys, 0, cen, grav, mass, partial);
-    else k_diag<3><<<nb, DIAG_THREADS, 0, s->stream>>>(s->D(), s->phys, 0, cen, grav, mass, partial);
+    if (s->dim == 2) k_diag<2><<<nb, DIAG_THREADS, 0, s->stream>>>(s->D(), 0, cen, grav, mass, partial);
+    else k_diag<3><<<nb, DIAG_THREADS, 0, s->stream>>>(s->D(), 0, cen, grav, mass, partial);
     k_diag_final<<<1, DIAG_K, 0, s->stream>>>(partial, nb, res);
     CU(cudaGetLastError());
     CU(cudaMemcpyAsync(r0, res, sizeof(r0), cudaMemcpyDeviceToHost, s->stream));
@@ -697,8 +712,8 @@ int sph_diag(sph_handle s, double out[12])
         double c3[3] = {r0[6] / r0[9], r0[7] / r0[9], r0[8] / r0[9]};
         for (int c = 0; c < s->dim; ++c) out[6 + c] = c3[c];
         CU(cudaMemcpyAsync(cen, c3, sizeof(c3), cudaMemcpyHostToDevice, s->stream));
-        if (s->dim == 2) k_diag<2><<<nb, DIAG_THREADS, 0, s->stream>>>(s->D(), s->phys, 1, cen, grav, mass, partial);
-        else k_diag<3><<<nb, DIAG_THREADS, 0, s->stream>>>(s->D(), s->phys, 1, cen, grav, mass, partial);
+        if (s->dim == 2) k_diag<2><<<nb, DIAG_THREADS, 0, s->stream>>>(s->D(), 1, cen, grav, mass, partial);
+        else k_diag<3><<<nb, DIAG_THREADS, 0, s->stream>>>(s->D(), 1, cen, grav, mass, partial);
         k_diag_final<<<1, DIAG_K, 0, s->stream>>>(partial, nb, res);
         CU(cudaGetLastError());
         CU(cudaMemcpyAsync(r1, res, sizeof(r1), cudaMemcpyDeviceToHost, s->stream));

@@ -3,16 +3,19 @@
 // Method: Wei et al., "Behavior of Oil under Breaking Waves by a Two-phase SPH
 // Model", Sec. II.  Layout and arithmetic choices made for the GPU:
 //   * particles live in cell order (stable by original id), structure of
-//     arrays; positions used by the neighbour sweeps are stored as a cell id
-//     plus an FP32 offset from the cell centre, so a pair distance is formed
-//     from two small numbers and an exact multiple of the cell edge;
+//     arrays;
+//   * a position used by the interaction sweeps is an exactly representable
+//     FP32 multiple of a power-of-two quantum q (an integer lattice index
+//     times q) plus an FP32 offset below q/2, so a pair vector
+//     (hi_i - hi_j) + (lo_i - lo_j) is formed with one rounding;
 //   * the FP64 position and velocity are the integration accumulators;
 //   * density is stored as the deviation drho = rho - rho0(phase) in FP32, so
 //     the equation of state and the renormalisation never subtract two
 //     numbers near rho0;
-//   * one thread per particle scans the 3^dim neighbouring cells; threads of a
-//     warp are consecutive particles of the same or adjacent cells and read
-//     the same candidates, so candidate loads are served as L1 broadcasts.
+//   * once per step a neighbour list (radius = cell edge = 2h + 2 skin) is
+//     built from the cell list and stored column-major, so the four
+//     interaction sweeps of the step read it coalesced and run without the
+//     branch divergence of a candidate scan.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -23,13 +26,15 @@ namespace sphgb {
 enum : unsigned {
     FLAG_DOMAIN = 1u,     // a particle left the cell grid
     FLAG_NONFINITE = 2u,  // NaN/Inf in the state
-    FLAG_SKIN = 4u,       // predictor displacement beyond the cell skin
+    FLAG_SKIN = 4u,       // predictor displacement beyond the skin
+    FLAG_LIST = 8u,       // a particle has more list neighbours than max_neighbours
 };
 
 // Constants of the physics, FP32 unless they feed an FP64 accumulator.
 struct Phys {
     float inv_h;        // 1/h
-    float R2;           // (2h)^2, neighbour test
+    float R2;           // (2h)^2, support test
+    float RL2;          // list radius^2 = cell edge^2
     float cF;           // -5 alpha_d / h^2: grad W_ij = cF (1-q/2)^3 r_ij
     float mass[2];      // per-phase particle mass
     float inv_mass[2];
@@ -40,17 +45,18 @@ struct Phys {
     float delta2;       // delta^2
     float alpha_s;      // surface tension coefficient
     float inv_dim;      // 1/d in Eq. csf
+    float gf[3];        // gravity (FP32, added to the FP32 acceleration)
     int visc_dynamic;   // 1: Eq. visc_2 (factor 1/rho_i), 0: Eq. visc_1
     int renorm_every;   // Eq. ct_dist_3 at stage 1 of steps with step % renorm_every == 0
-    float gf[3];        // gravity (FP32, added to the FP32 acceleration)
-    double hd;          // h (FP64), skin test
+    int kmax;           // neighbour-list capacity per particle
+    double skin;        // (cell edge - 2h) / 2: allowed predictor displacement
 };
 
 struct Grid {
     int nx, ny, nz;     // cells per axis (nz = 1 in 2-D)
-    float cs;           // cell edge (FP32) for pair offsets
-    double csd;         // cell edge (FP64) for hashing and offsets
+    double csd;         // cell edge (FP64) for hashing
     double lo[3];       // box lower corner
+    double q;           // power-of-two position quantum (<= cell edge)
 };
 
 // All device arrays of one simulation (sorted order unless noted).
@@ -64,8 +70,8 @@ struct Dev {
     uint8_t *tag;       // n, bit0 oil, bit1 wall
     int *cell;          // n, cell id (sorted order)
     // stage arrays
-    float4 *pos;        // n, (offset from cell centre xyz, +/- m/rho: sign = phase)
-    float *vd;          // n, (m/rho) * drho of the stage input
+    float4 *phi;        // n, (hi xyz, +/- m/rho of the stage input: sign = phase)
+    float4 *plo;        // n, (lo xyz, (m/rho) * drho of the stage input)
     float4 *vel;        // n, (u xyz, 0) FP32 copy of the stage velocity
     float *drho_stage;  // n, drho* of the predictor
     float *drho_eval;   // n, drho after renormalisation (stage output)
@@ -73,6 +79,10 @@ struct Dev {
     float4 *T4;         // n, T sigma^-2 = T (m/rho)^2: 2-D (xx, xy, yy, 0); 3-D (xx, xy, xz, yy)
     float2 *T2;         // n, 3-D only: (yz, zz)
     float4 *acc;        // n, (a xyz, Drho/Dt)
+    // neighbour list
+    int *nbr;           // kmax * n, entry k of particle i at nbr[k * n + i]
+    int *ncnt;          // n, list length
+    uint8_t *nflag;     // n, bit0: an other-phase particle lies within the list radius
     // cell list
     int *cstart;        // ncell + 1
     unsigned *flags;    // 1 word
@@ -81,39 +91,18 @@ struct Dev {
 
 __device__ __forceinline__ int phase_of(float w) { return __float_as_uint(w) >> 31; }
 
-// Scans all candidates of the 3^DIM cells around cell (cx, cy, cz) and calls
-// f(j, pj, rx, ry, rz, r2) for every j with |r_ij|^2 < (2h)^2 (j == i
-// included: r = 0).  r_ij = x_i - x_j is formed per axis as
-// (o_i + (c_i - c_j) * cs) - o_j.
-template <int DIM, class F>
-__device__ __forceinline__ void for_each_neighbour(const Grid &g, const int *__restrict__ cstart,
-                                                   const float4 *__restrict__ pos, int cx, int cy,
-                                                   int cz, float4 pi, float R2, F &&f)
+// r_ij = x_i - x_j from the split positions; the hi difference is exact.
+template <int DIM>
+__device__ __forceinline__ float pair_vec(const float4 &hi, const float4 &lo, const float4 &hj, const float4 &lj,
+                                          float &rx, float &ry, float &rz)
 {
-    const int z0 = DIM == 3 ? max(cz - 1, 0) : 0;
-    const int z1 = DIM == 3 ? min(cz + 1, g.nz - 1) : 0;
-    const int y0 = max(cy - 1, 0), y1 = min(cy + 1, g.ny - 1);
-    const int x0 = max(cx - 1, 0), x1 = min(cx + 1, g.nx - 1);
-    for (int z = z0; z <= z1; ++z) {
-        const float bz = DIM == 3 ? pi.z + (float)(cz - z) * g.cs : 0.f;
-        for (int y = y0; y <= y1; ++y) {
-            const float by = pi.y + (float)(cy - y) * g.cs;
-            const int row = (z * g.ny + y) * g.nx;
-            for (int xx = x0; xx <= x1; ++xx) {
-                const float bx = pi.x + (float)(cx - xx) * g.cs;
-                const int jb = __ldg(cstart + row + xx), je = __ldg(cstart + row + xx + 1);
-                for (int j = jb; j < je; ++j) {
-                    const float4 pj = __ldg(pos + j);
-                    const float rx = bx - pj.x, ry = by - pj.y;
-                    const float rz = DIM == 3 ? bz - pj.z : 0.f;
-                    float r2 = rx * rx;
-                    r2 = fmaf(ry, ry, r2);
-                    if (DIM == 3) r2 = fmaf(rz, rz, r2);
-                    if (r2 < R2) f(j, pj, rx, ry, rz, r2);
-                }
-            }
-        }
-    }
+    rx = (hi.x - hj.x) + (lo.x - lj.x);
+    ry = (hi.y - hj.y) + (lo.y - lj.y);
+    rz = DIM == 3 ? (hi.z - hj.z) + (lo.z - lj.z) : 0.f;
+    float r2 = rx * rx;
+    r2 = fmaf(ry, ry, r2);
+    if (DIM == 3) r2 = fmaf(rz, rz, r2);
+    return r2;
 }
 
 __device__ __forceinline__ void cell_coords(const Grid &g, int c, int &cx, int &cy, int &cz)
@@ -122,6 +111,34 @@ __device__ __forceinline__ void cell_coords(const Grid &g, int c, int &cx, int &
     const int r = c / g.nx;
     cy = r % g.ny;
     cz = r / g.ny;
+}
+
+// Scans every particle of the 3^DIM cells around cell (cx, cy, cz) and calls
+// f(j, hj, lj, rx, ry, rz, r2) for those with |r_ij|^2 < R2 (j == i included).
+template <int DIM, class F>
+__device__ __forceinline__ void for_each_candidate(const Grid &g, const int *__restrict__ cstart,
+                                                   const float4 *__restrict__ phi, const float4 *__restrict__ plo,
+                                                   int cx, int cy, int cz, const float4 &hi, const float4 &lo,
+                                                   float R2, F &&f)
+{
+    const int z0 = DIM == 3 ? max(cz - 1, 0) : 0;
+    const int z1 = DIM == 3 ? min(cz + 1, g.nz - 1) : 0;
+    const int y0 = max(cy - 1, 0), y1 = min(cy + 1, g.ny - 1);
+    const int x0 = max(cx - 1, 0), x1 = min(cx + 1, g.nx - 1);
+    for (int z = z0; z <= z1; ++z) {
+        for (int y = y0; y <= y1; ++y) {
+            // the cells x0..x1 of a row are contiguous in the sorted order
+            const int row = (z * g.ny + y) * g.nx;
+            const int jb = __ldg(cstart + row + x0), je = __ldg(cstart + row + x1 + 1);
+            for (int j = jb; j < je; ++j) {
+                const float4 hj = __ldg(phi + j);
+                const float4 lj = __ldg(plo + j);
+                float rx, ry, rz;
+                const float r2 = pair_vec<DIM>(hi, lo, hj, lj, rx, ry, rz);
+                if (r2 < R2) f(j, hj, lj, rx, ry, rz, r2);
+            }
+        }
+    }
 }
 
 // Compensated (Kahan) accumulation.
@@ -147,6 +164,32 @@ __device__ __forceinline__ float eos_tait7(float beta, float eps)
     return beta * eps * p;
 }
 
+// Split of an FP64 coordinate (relative to the box corner) into an exact
+// FP32 multiple of q and an FP32 remainder.
+__device__ __forceinline__ void split_coord(double X, double q, float &hi, float &lo)
+{
+    const double k = rint(X / q);
+    hi = (float)(k * q);
+    lo = (float)(X - k * q);
+}
+
+template <int DIM>
+__device__ __forceinline__ void split_position(const Grid &g, const double xa[3], float4 &hi, float4 &lo)
+{
+    float h[3] = {0.f, 0.f, 0.f}, l[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) split_coord(xa[a] - g.lo[a], g.q, h[a], l[a]);
+    hi = make_float4(h[0], h[1], h[2], 0.f);
+    lo = make_float4(l[0], l[1], l[2], 0.f);
+}
+
+// Signed specific volume m/rho, negative for oil.
+__device__ __forceinline__ float signed_volume(const Phys &ph, int phase, float drho, float &vol)
+{
+    vol = ph.mass[phase] / (ph.rho0[phase] + drho);
+    return phase ? -vol : vol;
+}
+
 // ---------------------------------------------------------------------------
 // Cell list: hash, counting sort stable in particle id, reorder.
 
@@ -157,18 +200,20 @@ __global__ void __launch_bounds__(256) k_hash(Dev d, Grid g, int *cell_tmp, int 
     if (k >= d.n) return;
     const int dims[3] = {g.nx, g.ny, g.nz};
     int c[3] = {0, 0, 0};
-    bool bad = false;
+    unsigned bad = 0;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
-        const double s = floor((d.x[(size_t)a * d.n + k] - g.lo[a]) / g.csd);
-        if (!(s >= 0.0 && s < (double)dims[a])) {
-            bad = true;
-            c[a] = 0;
+        const double xa = d.x[(size_t)a * d.n + k];
+        const double s = floor((xa - g.lo[a]) / g.csd);
+        if (isnan(xa)) {
+            bad |= FLAG_NONFINITE;
+        } else if (!(s >= 0.0 && s < (double)dims[a])) {
+            bad |= FLAG_DOMAIN;
         } else {
             c[a] = (int)s;
         }
     }
-    if (bad) atomicOr(d.flags, FLAG_DOMAIN);
+    if (bad) atomicOr(d.flags, bad);
     const int id = c[0] + g.nx * (c[1] + g.ny * c[2]);
     cell_tmp[k] = id;
     slot[k] = atomicAdd(count + id, 1);
@@ -280,24 +325,6 @@ __global__ void __launch_bounds__(256) k_rank(int n, const int *tmp, const int *
     perm[b + rank] = k;
 }
 
-// Signed specific volume for the stage position array: m/rho, negative for oil.
-__device__ __forceinline__ float signed_volume(const Phys &ph, int phase, float drho, float &vol)
-{
-    vol = ph.mass[phase] / (ph.rho0[phase] + drho);
-    return phase ? -vol : vol;
-}
-
-template <int DIM>
-__device__ __forceinline__ float4 cell_offset(const Grid &g, int c, const double xa[3])
-{
-    int cc[3];
-    cell_coords(g, c, cc[0], cc[1], cc[2]);
-    float o[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-    for (int a = 0; a < DIM; ++a) o[a] = (float)(xa[a] - (g.lo[a] + ((double)cc[a] + 0.5) * g.csd));
-    return make_float4(o[0], o[1], o[2], 0.f);
-}
-
 // Gathers the state into the new order and prepares the stage-1 arrays.
 template <int DIM>
 __global__ void __launch_bounds__(256) k_gather(Dev src, Dev dst, Grid g, Phys ph, const int *perm, const int *cell_tmp)
@@ -316,17 +343,50 @@ __global__ void __launch_bounds__(256) k_gather(Dev src, Dev dst, Grid g, Phys p
     }
     const float dr = src.drho[o];
     const uint8_t tg = src.tag[o];
-    const int c = cell_tmp[o];
     dst.drho[k] = dr;
     dst.pid[k] = src.pid[o];
     dst.tag[k] = tg;
-    dst.cell[k] = c;
-    float4 p = cell_offset<DIM>(g, c, xa);
+    dst.cell[k] = cell_tmp[o];
+    float4 hi, lo;
+    split_position<DIM>(g, xa, hi, lo);
     float vol;
-    p.w = signed_volume(ph, tg & 1, dr, vol);
-    dst.pos[k] = p;
-    dst.vd[k] = vol * dr;
+    hi.w = signed_volume(ph, tg & 1, dr, vol);
+    lo.w = vol * dr;
+    dst.phi[k] = hi;
+    dst.plo[k] = lo;
     dst.vel[k] = make_float4((float)ua[0], (float)ua[1], (float)ua[2], 0.f);
+}
+
+// ---------------------------------------------------------------------------
+// Neighbour list: every j != i within the cell edge (2h + 2 skin) at the
+// positions of the build, so the list stays complete while no particle moves
+// farther than the skin.
+template <int DIM>
+__global__ void __launch_bounds__(256) k_build_list(Dev d, Grid g, Phys ph)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d.n) return;
+    const float4 hi = d.phi[i], lo = d.plo[i];
+    const int phi_ = phase_of(hi.w);
+    int cx, cy, cz;
+    cell_coords(g, d.cell[i], cx, cy, cz);
+    int cnt = 0;
+    int other = 0;
+    const int n = d.n, kmax = ph.kmax;
+    int *__restrict__ nbr = d.nbr;
+    for_each_candidate<DIM>(g, d.cstart, d.phi, d.plo, cx, cy, cz, hi, lo, ph.RL2,
+        [&](int j, const float4 &hj, const float4 &, float, float, float, float) {
+            if (j == i) return;
+            if (cnt < kmax) nbr[(size_t)cnt * n + i] = j;
+            ++cnt;
+            other |= phase_of(hj.w) != phi_;
+        });
+    if (cnt > kmax) {
+        atomicOr(d.flags, FLAG_LIST);
+        cnt = kmax;
+    }
+    d.ncnt[i] = cnt;
+    d.nflag[i] = (uint8_t)other;
 }
 
 // ---------------------------------------------------------------------------
@@ -336,49 +396,59 @@ __global__ void __launch_bounds__(256) k_gather(Dev src, Dev dst, Grid g, Phys p
 // Eq. ct_dist_3 with same-phase masses m_j = m_i is rewritten exactly as a
 // Shepard average of the density deviation:
 //   rho_i - rho0 = sum_j (m_j/rho_j) drho_j W_ij / sum_j (m_j/rho_j) W_ij,
-// both sums Kahan-compensated.  The colour gradient uses the density that
-// entered the stage: grad C_i = (1/V_i) sum_{j other phase} V_j^2 grad W_ij,
-// V = m/rho = 1/sigma.
+// over i itself and its same-phase neighbours, both sums Kahan-compensated.
+// The colour gradient uses the density that entered the stage:
+// grad C_i = (1/V_i) sum_{j other phase} V_j^2 grad W_ij, V = m/rho = 1/sigma.
 template <int DIM>
-__global__ void __launch_bounds__(256) k_sweep_a(Dev d, Grid g, Phys ph, const float *__restrict__ drho_in, int stage1)
+__global__ void __launch_bounds__(256) k_sweep_a(Dev d, Phys ph, const float *__restrict__ drho_in, int stage1)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.n) return;
     const int renorm = stage1 && ph.renorm_every > 0 && (*d.step % ph.renorm_every) == 0;
-    const float4 pi = d.pos[i];
-    const int phi = phase_of(pi.w);
-    int cx, cy, cz;
-    cell_coords(g, d.cell[i], cx, cy, cz);
-    float s1 = 0.f, c1 = 0.f, s2 = 0.f, c2 = 0.f;
+    const float4 hi = d.phi[i], lo = d.plo[i];
+    const int phi_ = phase_of(hi.w);
+    // self term: W(0)/alpha_d = 1
+    float s1 = fabsf(hi.w), c1 = 0.f, s2 = lo.w, c2 = 0.f;
     float gx = 0.f, gy = 0.f, gz = 0.f;
-    const float inv_h = ph.inv_h;
-    const float *__restrict__ vd = d.vd;
-    for_each_neighbour<DIM>(g, d.cstart, d.pos, cx, cy, cz, pi, ph.R2,
-        [&](int j, const float4 &pj, float rx, float ry, float rz, float r2) {
+    const bool other = d.nflag[i] & 1;
+    if (renorm || other) {
+        const float inv_h = ph.inv_h;
+        const int n = d.n, cnt = d.ncnt[i];
+        const int *__restrict__ nbr = d.nbr;
+        const float4 *__restrict__ phi = d.phi;
+        const float4 *__restrict__ plo = d.plo;
+        for (int k = 0; k < cnt; ++k) {
+            const int j = __ldg(nbr + (size_t)k * n + i);
+            const float4 hj = __ldg(phi + j);
+            const float4 lj = __ldg(plo + j);
+            float rx, ry, rz;
+            const float r2 = pair_vec<DIM>(hi, lo, hj, lj, rx, ry, rz);
+            if (!(r2 < ph.R2)) continue;
             const float r = sqrtf(r2);
             const float t = fmaf(-0.5f * inv_h, r, 1.f);
             const float t3 = t * t * t;
-            if (phase_of(pj.w) == phi) {
+            if (phase_of(hj.w) == phi_) {
                 if (renorm) {
                     // W / alpha_d = t^4 (2q + 1)
                     const float w = t3 * t * fmaf(2.f * inv_h, r, 1.f);
-                    kahan_add(s1, c1, fabsf(pj.w) * w);
-                    kahan_add(s2, c2, __ldg(vd + j) * w);
+                    kahan_add(s1, c1, fabsf(hj.w) * w);
+                    kahan_add(s2, c2, lj.w * w);
                 }
             } else {
-                const float c = pj.w * pj.w * t3;
+                const float c = hj.w * hj.w * t3;
                 gx = fmaf(c, rx, gx);
                 gy = fmaf(c, ry, gy);
                 if (DIM == 3) gz = fmaf(c, rz, gz);
             }
-        });
+        }
+    }
     const float drho = renorm ? s2 / s1 : drho_in[i];
     d.drho_eval[i] = drho;
-    const float rho = ph.rho0[phi] + drho;
-    const float vol = ph.mass[phi] / rho;
-    const float P = eos_tait7(ph.beta[phi], drho * ph.inv_rho0[phi]);
+    const float rho = ph.rho0[phi_] + drho;
+    const float vol = ph.mass[phi_] / rho;
+    const float P = eos_tait7(ph.beta[phi_], drho * ph.inv_rho0[phi_]);
     // grad C_i = sigma_i sum V_j^2 grad W_ij, sigma_i = 1/|V_i| (entry density)
-    const float sc = ph.cF / fabsf(pi.w);
+    const float sc = ph.cF / fabsf(hi.w);
     gx *= sc;
     gy *= sc;
     gz *= sc;
@@ -389,13 +459,13 @@ __global__ void __launch_bounds__(256) k_sweep_a(Dev d, Grid g, Phys ph, const f
     if (n2 > 0.f) {
         iface = 1.f;
         // T sigma_i^-2 = alpha_s / |g| (|g|^2/d I - g g^T) V_i^2, V_i from the renormalised density
-        const float k = ph.alpha_s * rsqrtf(n2) * vol * vol;
+        const float kk = ph.alpha_s * rsqrtf(n2) * vol * vol;
         const float iso = n2 * ph.inv_dim;
         if (DIM == 2) {
-            t4 = make_float4(k * (iso - gx * gx), -k * gx * gy, k * (iso - gy * gy), 0.f);
+            t4 = make_float4(kk * (iso - gx * gx), -kk * gx * gy, kk * (iso - gy * gy), 0.f);
         } else {
-            t4 = make_float4(k * (iso - gx * gx), -k * gx * gy, -k * gx * gz, k * (iso - gy * gy));
-            t2 = make_float2(-k * gy * gz, k * (iso - gz * gz));
+            t4 = make_float4(kk * (iso - gx * gx), -kk * gx * gy, -kk * gx * gz, kk * (iso - gy * gy));
+            t2 = make_float2(-kk * gy * gz, kk * (iso - gz * gz));
         }
     }
     d.aux[i] = make_float4(vol, P / (rho * rho), iface, P);
@@ -409,73 +479,80 @@ __global__ void __launch_bounds__(256) k_sweep_a(Dev d, Grid g, Phys ph, const f
 // (Eq. ct_dist_2).  grad_i W_ij = cF t^3 r_ij with t = 1 - q/2; the common
 // factor cF is applied once per particle.
 template <int DIM>
-__global__ void __launch_bounds__(256) k_sweep_b(Dev d, Grid g, Phys ph)
+__global__ void __launch_bounds__(256) k_sweep_b(Dev d, Phys ph)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.n) return;
-    const float4 pi = d.pos[i];
-    const int phi = phase_of(pi.w);
+    const float4 hi = d.phi[i], lo = d.plo[i];
+    const int phi_ = phase_of(hi.w);
     const float4 ai = d.aux[i];
     const float4 ui = d.vel[i];
     const float4 Ti = d.T4[i];
     const float2 Ti2 = DIM == 3 ? d.T2[i] : make_float2(0.f, 0.f);
-    int cx, cy, cz;
-    cell_coords(g, d.cell[i], cx, cy, cz);
     float px = 0.f, py = 0.f, pz = 0.f;    // sum m_j (P_i/rho_i^2 + P_j/rho_j^2) t^3 r_ij
     float vx = 0.f, vy = 0.f, vz = 0.f;    // sum k_ij V_j t^3 r^2/(r^2+delta^2) u_ij
     float sx = 0.f, sy = 0.f, sz = 0.f;    // sum (T_i/sigma_i^2 + T_j/sigma_j^2) . t^3 r_ij
     float dv = 0.f;                        // sum V_j t^3 u_ij . r_ij
     const float inv_h = ph.inv_h;
+    const int n = d.n, cnt = d.ncnt[i];
+    const int *__restrict__ nbr = d.nbr;
+    const float4 *__restrict__ phi = d.phi;
+    const float4 *__restrict__ plo = d.plo;
     const float4 *__restrict__ aux = d.aux;
     const float4 *__restrict__ vel = d.vel;
     const float4 *__restrict__ T4 = d.T4;
     const float2 *__restrict__ T2 = d.T2;
-    for_each_neighbour<DIM>(g, d.cstart, d.pos, cx, cy, cz, pi, ph.R2,
-        [&](int j, const float4 &pj, float rx, float ry, float rz, float r2) {
-            const int phj = phase_of(pj.w);
-            const float4 aj = __ldg(aux + j);
-            const float4 uj = __ldg(vel + j);
-            const float r = sqrtf(r2);
-            const float t = fmaf(-0.5f * inv_h, r, 1.f);
-            const float t3 = t * t * t;
-            const float pt = ph.mass[phj] * (ai.y + aj.y) * t3;
-            px = fmaf(pt, rx, px);
-            py = fmaf(pt, ry, py);
-            if (DIM == 3) pz = fmaf(pt, rz, pz);
-            const float ux = ui.x - uj.x, uy = ui.y - uj.y, uz = DIM == 3 ? ui.z - uj.z : 0.f;
-            const float vt = aj.x * t3;
-            const float s = ph.kvis[2 * phi + phj] * vt * __fdividef(r2, r2 + ph.delta2);
-            vx = fmaf(s, ux, vx);
-            vy = fmaf(s, uy, vy);
-            if (DIM == 3) vz = fmaf(s, uz, vz);
-            float ur = ux * rx;
-            ur = fmaf(uy, ry, ur);
-            if (DIM == 3) ur = fmaf(uz, rz, ur);
-            dv = fmaf(vt, ur, dv);
-            if (ai.z + aj.z > 0.f) {
-                const float4 Tj = __ldg(T4 + j);
-                if (DIM == 2) {
-                    const float xx = Ti.x + Tj.x, xy = Ti.y + Tj.y, yy = Ti.z + Tj.z;
-                    sx = fmaf(t3, xx * rx + xy * ry, sx);
-                    sy = fmaf(t3, xy * rx + yy * ry, sy);
-                } else {
-                    const float2 Tj2 = __ldg(T2 + j);
-                    const float xx = Ti.x + Tj.x, xy = Ti.y + Tj.y, xz = Ti.z + Tj.z;
-                    const float yy = Ti.w + Tj.w, yz = Ti2.x + Tj2.x, zz = Ti2.y + Tj2.y;
-                    sx = fmaf(t3, xx * rx + xy * ry + xz * rz, sx);
-                    sy = fmaf(t3, xy * rx + yy * ry + yz * rz, sy);
-                    sz = fmaf(t3, xz * rx + yz * ry + zz * rz, sz);
-                }
+    for (int k = 0; k < cnt; ++k) {
+        const int j = __ldg(nbr + (size_t)k * n + i);
+        const float4 hj = __ldg(phi + j);
+        const float4 lj = __ldg(plo + j);
+        float rx, ry, rz;
+        const float r2 = pair_vec<DIM>(hi, lo, hj, lj, rx, ry, rz);
+        if (!(r2 < ph.R2)) continue;
+        const int phj = phase_of(hj.w);
+        const float4 aj = __ldg(aux + j);
+        const float4 uj = __ldg(vel + j);
+        const float r = sqrtf(r2);
+        const float t = fmaf(-0.5f * inv_h, r, 1.f);
+        const float t3 = t * t * t;
+        const float pt = ph.mass[phj] * (ai.y + aj.y) * t3;
+        px = fmaf(pt, rx, px);
+        py = fmaf(pt, ry, py);
+        if (DIM == 3) pz = fmaf(pt, rz, pz);
+        const float ux = ui.x - uj.x, uy = ui.y - uj.y, uz = DIM == 3 ? ui.z - uj.z : 0.f;
+        const float vt = aj.x * t3;
+        const float s = ph.kvis[2 * phi_ + phj] * vt * __fdividef(r2, r2 + ph.delta2);
+        vx = fmaf(s, ux, vx);
+        vy = fmaf(s, uy, vy);
+        if (DIM == 3) vz = fmaf(s, uz, vz);
+        float ur = ux * rx;
+        ur = fmaf(uy, ry, ur);
+        if (DIM == 3) ur = fmaf(uz, rz, ur);
+        dv = fmaf(vt, ur, dv);
+        if (ai.z + aj.z > 0.f) {
+            const float4 Tj = __ldg(T4 + j);
+            if (DIM == 2) {
+                const float xx = Ti.x + Tj.x, xy = Ti.y + Tj.y, yy = Ti.z + Tj.z;
+                sx = fmaf(t3, xx * rx + xy * ry, sx);
+                sy = fmaf(t3, xy * rx + yy * ry, sy);
+            } else {
+                const float2 Tj2 = __ldg(T2 + j);
+                const float xx = Ti.x + Tj.x, xy = Ti.y + Tj.y, xz = Ti.z + Tj.z;
+                const float yy = Ti.w + Tj.w, yz = Ti2.x + Tj2.x, zz = Ti2.y + Tj2.y;
+                sx = fmaf(t3, xx * rx + xy * ry + xz * rz, sx);
+                sy = fmaf(t3, xy * rx + yy * ry + yz * rz, sy);
+                sz = fmaf(t3, xz * rx + yz * ry + zz * rz, sz);
             }
-        });
-    const float rho = ph.rho0[phi] + d.drho_eval[i];
+        }
+    }
+    const float rho = ph.rho0[phi_] + d.drho_eval[i];
     float4 out;
     out.w = rho * ph.cF * dv;
     if (d.tag[i] & 2) {
         out.x = out.y = out.z = 0.f;
     } else {
         const float vf = ph.visc_dynamic ? ph.cF / rho : ph.cF;
-        const float sf = ph.cF * ph.inv_mass[phi];
+        const float sf = ph.cF * ph.inv_mass[phi_];
         out.x = -ph.cF * px + vf * vx + sf * sx + ph.gf[0];
         out.y = -ph.cF * py + vf * vy + sf * sy + ph.gf[1];
         out.z = DIM == 3 ? -ph.cF * pz + vf * vz + sf * sz + ph.gf[2] : 0.f;
@@ -500,22 +577,26 @@ __global__ void __launch_bounds__(256) k_predict(Dev d, Grid g, Phys ph, double 
     double xs[3] = {0, 0, 0}, us[3] = {0, 0, 0};
     const double af[3] = {a.x, a.y, a.z};
     bool finite = isfinite(drs);
+    double disp2 = 0.0;
 #pragma unroll
     for (int c = 0; c < DIM; ++c) {
         const double x = d.x[(size_t)c * d.n + k], u = d.u[(size_t)c * d.n + k];
-        xs[c] = (tg & 2) ? x : x + 0.5 * dt * u;
+        const double dx = (tg & 2) ? 0.0 : 0.5 * dt * u;
+        xs[c] = x + dx;
         us[c] = (tg & 2) ? u : u + 0.5 * dt * af[c];
+        disp2 += dx * dx;
         finite = finite && isfinite(us[c]) && isfinite(xs[c]);
     }
-    float4 p = cell_offset<DIM>(g, d.cell[k], xs);
-    // one cell list serves both stages while every particle stays within
-    // cell_size - h of its cell centre on each axis
-    const float lim = (float)(g.csd - ph.hd);
-    if (fabsf(p.x) > lim || fabsf(p.y) > lim || fabsf(p.z) > lim) atomicOr(d.flags, FLAG_SKIN);
+    // the neighbour list of the step stays complete while no particle moves
+    // farther than the skin
+    if (disp2 > ph.skin * ph.skin) atomicOr(d.flags, FLAG_SKIN);
+    float4 hi, lo;
+    split_position<DIM>(g, xs, hi, lo);
     float vol;
-    p.w = signed_volume(ph, tg & 1, drs, vol);
-    d.pos[k] = p;
-    d.vd[k] = vol * drs;
+    hi.w = signed_volume(ph, tg & 1, drs, vol);
+    lo.w = vol * drs;
+    d.phi[k] = hi;
+    d.plo[k] = lo;
     d.vel[k] = make_float4((float)us[0], (float)us[1], (float)us[2], 0.f);
     if (!finite) atomicOr(d.flags, FLAG_NONFINITE);
 }
@@ -548,20 +629,35 @@ __global__ void __launch_bounds__(256) k_correct(Dev d, double dt)
 }
 
 // ---------------------------------------------------------------------------
-// Neighbour sets (same candidate test as the sweeps).
+// Neighbour sets and pair statistics by the sweeps' own support test.
 
 template <int DIM>
 __global__ void __launch_bounds__(256) k_nbr_count(Dev d, Grid g, Phys ph, int *count)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.n) return;
-    const float4 pi = d.pos[i];
+    const float4 hi = d.phi[i], lo = d.plo[i];
     int cx, cy, cz;
     cell_coords(g, d.cell[i], cx, cy, cz);
     int cnt = 0;
-    for_each_neighbour<DIM>(g, d.cstart, d.pos, cx, cy, cz, pi, ph.R2,
-                            [&](int j, const float4 &, float, float, float, float) { cnt += j != i; });
+    for_each_candidate<DIM>(g, d.cstart, d.phi, d.plo, cx, cy, cz, hi, lo, ph.R2,
+                            [&](int j, const float4 &, const float4 &, float, float, float, float) { cnt += j != i; });
     count[i] = cnt;
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(256) k_nbr_fill(Dev d, Grid g, Phys ph, const long long *start, int *list)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d.n) return;
+    const float4 hi = d.phi[i], lo = d.plo[i];
+    int cx, cy, cz;
+    cell_coords(g, d.cell[i], cx, cy, cz);
+    long long w = start[i];
+    for_each_candidate<DIM>(g, d.cstart, d.phi, d.plo, cx, cy, cz, hi, lo, ph.R2,
+                            [&](int j, const float4 &, const float4 &, float, float, float, float) {
+                                if (j != i) list[w++] = d.pid[j];
+                            });
 }
 
 // Totals of ordered neighbour pairs (j != i): [0] all, [1] of different phase.
@@ -571,14 +667,14 @@ __global__ void __launch_bounds__(256) k_pair_stats(Dev d, Grid g, Phys ph, unsi
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     int all = 0, other = 0;
     if (i < d.n) {
-        const float4 pi = d.pos[i];
-        const int phi = phase_of(pi.w);
+        const float4 hi = d.phi[i], lo = d.plo[i];
+        const int phi_ = phase_of(hi.w);
         int cx, cy, cz;
         cell_coords(g, d.cell[i], cx, cy, cz);
-        for_each_neighbour<DIM>(g, d.cstart, d.pos, cx, cy, cz, pi, ph.R2,
-                                [&](int j, const float4 &pj, float, float, float, float) {
+        for_each_candidate<DIM>(g, d.cstart, d.phi, d.plo, cx, cy, cz, hi, lo, ph.R2,
+                                [&](int j, const float4 &hj, const float4 &, float, float, float, float) {
                                     all += j != i;
-                                    other += phase_of(pj.w) != phi;
+                                    other += phase_of(hj.w) != phi_;
                                 });
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -589,21 +685,6 @@ __global__ void __launch_bounds__(256) k_pair_stats(Dev d, Grid g, Phys ph, unsi
         atomicAdd(tot, (unsigned long long)all);
         atomicAdd(tot + 1, (unsigned long long)other);
     }
-}
-
-template <int DIM>
-__global__ void __launch_bounds__(256) k_nbr_fill(Dev d, Grid g, Phys ph, const long long *start, int *list)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= d.n) return;
-    const float4 pi = d.pos[i];
-    int cx, cy, cz;
-    cell_coords(g, d.cell[i], cx, cy, cz);
-    long long w = start[i];
-    for_each_neighbour<DIM>(g, d.cstart, d.pos, cx, cy, cz, pi, ph.R2,
-                            [&](int j, const float4 &, float, float, float, float) {
-                                if (j != i) list[w++] = d.pid[j];
-                            });
 }
 
 // ---------------------------------------------------------------------------
@@ -697,7 +778,7 @@ __device__ __forceinline__ void block_reduce_store(double (&v)[DIAG_K], double *
 // pass 0: mass, momentum, energies, oil count and sum of oil positions, max|u|
 // pass 1: covariance of oil positions about the centroid `cen`
 template <int DIM>
-__global__ void __launch_bounds__(DIAG_THREADS) k_diag(Dev d, Phys ph, int pass, const double *cen, const double *grav,
+__global__ void __launch_bounds__(DIAG_THREADS) k_diag(Dev d, int pass, const double *cen, const double *grav,
                                                        const double *mass, double *partial)
 {
     double v[DIAG_K];

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, "libsph.so")
 
 SPH_OK = 0
 ERRORS = {-1: "SPH_EINVAL", -2: "SPH_ENOMEM", -3: "SPH_ECUDA", -4: "SPH_ENONFINITE",
-          -5: "SPH_ECFL", -6: "SPH_EDOMAIN"}
+          -5: "SPH_ECFL", -6: "SPH_EDOMAIN", -7: "SPH_ECAPACITY"}
 VISC_DYNAMIC, VISC_KINEMATIC = 0, 1
 FIELD = dict(pos=0, vel=1, rho=2, rho_eval=3, pressure=4, acc=5, drho=6, tensor=7, cell=8, order=9)
 
@@ -36,7 +36,7 @@ class SphError(RuntimeError):
 class SphParams(C.Structure):
     _fields_ = [
         ("dim", C.c_int32), ("visc_form", C.c_int32), ("renorm_every", C.c_int32),
-        ("reserved", C.c_int32), ("h", C.c_double), ("c0", C.c_double), ("gamma", C.c_double),
+        ("max_neighbours", C.c_int32), ("h", C.c_double), ("c0", C.c_double), ("gamma", C.c_double),
         ("delta", C.c_double), ("alpha_s", C.c_double), ("cell_size", C.c_double),
         ("g", C.c_double * 3), ("rho0", C.c_double * 2), ("mu", C.c_double * 2),
         ("mass", C.c_double * 2), ("box_lo", C.c_double * 3), ("box_hi", C.c_double * 3),
@@ -85,7 +85,7 @@ def make_params(p: dict) -> SphParams:
     s.dim = int(p["dim"])
     s.visc_form = int(p.get("visc_form", 0))
     s.renorm_every = int(p.get("renorm_every", 1))
-    s.reserved = 0
+    s.max_neighbours = int(p.get("max_neighbours", 0))
     s.h, s.c0, s.gamma = p["h"], p["c0"], p.get("gamma", 7.0)
     s.delta, s.alpha_s, s.cell_size = p["delta"], p["alpha_s"], p["cell_size"]
     for k in range(3):
