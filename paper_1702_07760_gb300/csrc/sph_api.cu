@@ -355,7 +355,7 @@ int sph_create(const sph_params *params, int64_t n, const double *x, const doubl
     Phys &ph = s->phys;
     ph.inv_h = (float)(1.0 / h);
     ph.R2 = (float)(4.0 * h * h);
-    ph.RL2 = (float)(P.cell_size * P.cell_size);
+    ph.RL2 = (float)(P.cell_size * P.cell_size * (1.0 + 2e-5));
     ph.skin = 0.5 * (P.cell_size - 2.0 * h);
     ph.kmax = P.max_neighbours > 0 ? P.max_neighbours : (dim == 2 ? 48 : 128);
     ph.cF = (float)(-5.0 * alpha_d / (h * h));
@@ -407,6 +407,7 @@ int sph_create(const sph_params *params, int64_t n, const double *x, const doubl
     }
     Dev &a0 = s->buf[0];
     if (!err) {
+        err |= s->alloc(&a0.pa, N);
         err |= s->alloc(&a0.phi, N);
         err |= s->alloc(&a0.plo, N);
         err |= s->alloc(&a0.vel, N);
@@ -433,7 +434,7 @@ int sph_create(const sph_params *params, int64_t n, const double *x, const doubl
     }
     if (err) return cleanup(SPH_ENOMEM);
     Dev &a1 = s->buf[1];
-    a1.phi = a0.phi; a1.plo = a0.plo; a1.vel = a0.vel; a1.drho_stage = a0.drho_stage;
+    a1.pa = a0.pa; a1.phi = a0.phi; a1.plo = a0.plo; a1.vel = a0.vel; a1.drho_stage = a0.drho_stage;
     a1.nbr = a0.nbr; a1.ncnt = a0.ncnt; a1.nflag = a0.nflag;
     a1.drho_eval = a0.drho_eval; a1.aux = a0.aux; a1.T4 = a0.T4; a1.T2 = a0.T2; a1.acc = a0.acc;
     a1.cstart = a0.cstart;

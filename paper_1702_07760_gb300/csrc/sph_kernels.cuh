@@ -34,7 +34,8 @@ enum : unsigned {
 struct Phys {
     float inv_h;        // 1/h
     float R2;           // (2h)^2, support test
-    float RL2;          // list radius^2 = cell edge^2
+    float RL2;          // list radius^2: cell edge^2 widened by a relative 1e-5 to cover
+                        // the rounding of the FP32 filter positions
     float cF;           // -5 alpha_d / h^2: grad W_ij = cF (1-q/2)^3 r_ij
     float mass[2];      // per-phase particle mass
     float inv_mass[2];
@@ -70,6 +71,7 @@ struct Dev {
     uint8_t *tag;       // n, bit0 oil, bit1 wall
     int *cell;          // n, cell id (sorted order)
     // stage arrays
+    float4 *pa;         // n, (x - box corner as FP32 xyz, phase sign): list-build filter only
     float4 *phi;        // n, (hi xyz, +/- m/rho of the stage input: sign = phase)
     float4 *plo;        // n, (lo xyz, (m/rho) * drho of the stage input)
     float4 *vel;        // n, (u xyz, 0) FP32 copy of the stage velocity
@@ -130,6 +132,7 @@ __device__ __forceinline__ void for_each_candidate(const Grid &g, const int *__r
             // the cells x0..x1 of a row are contiguous in the sorted order
             const int row = (z * g.ny + y) * g.nx;
             const int jb = __ldg(cstart + row + x0), je = __ldg(cstart + row + x1 + 1);
+#pragma unroll 4
             for (int j = jb; j < je; ++j) {
                 const float4 hj = __ldg(phi + j);
                 const float4 lj = __ldg(plo + j);
@@ -354,6 +357,8 @@ __global__ void __launch_bounds__(256) k_gather(Dev src, Dev dst, Grid g, Phys p
     lo.w = vol * dr;
     dst.phi[k] = hi;
     dst.plo[k] = lo;
+    dst.pa[k] = make_float4((float)(xa[0] - g.lo[0]), (float)(xa[1] - g.lo[1]), (float)(xa[2] - g.lo[2]),
+                            (tg & 1) ? -1.f : 1.f);
     dst.vel[k] = make_float4((float)ua[0], (float)ua[1], (float)ua[2], 0.f);
 }
 
@@ -366,21 +371,40 @@ __global__ void __launch_bounds__(256) k_build_list(Dev d, Grid g, Phys ph)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.n) return;
-    const float4 hi = d.phi[i], lo = d.plo[i];
-    const int phi_ = phase_of(hi.w);
+    // the filter needs no more than FP32 absolute positions: their rounding
+    // (~1e-7 of the box) is far below the skin, and RL2 is widened to match
+    const float4 pi = d.pa[i];
+    const int phi_ = phase_of(pi.w);
     int cx, cy, cz;
     cell_coords(g, d.cell[i], cx, cy, cz);
     int cnt = 0;
     int other = 0;
     const int n = d.n, kmax = ph.kmax;
     int *__restrict__ nbr = d.nbr;
-    for_each_candidate<DIM>(g, d.cstart, d.phi, d.plo, cx, cy, cz, hi, lo, ph.RL2,
-        [&](int j, const float4 &hj, const float4 &, float, float, float, float) {
-            if (j == i) return;
-            if (cnt < kmax) nbr[(size_t)cnt * n + i] = j;
-            ++cnt;
-            other |= phase_of(hj.w) != phi_;
-        });
+    const float4 *__restrict__ pa = d.pa;
+    const int z0 = DIM == 3 ? max(cz - 1, 0) : 0;
+    const int z1 = DIM == 3 ? min(cz + 1, g.nz - 1) : 0;
+    const int y0 = max(cy - 1, 0), y1 = min(cy + 1, g.ny - 1);
+    const int x0 = max(cx - 1, 0), x1 = min(cx + 1, g.nx - 1);
+    for (int z = z0; z <= z1; ++z) {
+        for (int y = y0; y <= y1; ++y) {
+            const int row = (z * g.ny + y) * g.nx;
+            const int jb = __ldg(d.cstart + row + x0), je = __ldg(d.cstart + row + x1 + 1);
+#pragma unroll 4
+            for (int j = jb; j < je; ++j) {
+                const float4 pj = __ldg(pa + j);
+                const float rx = pi.x - pj.x, ry = pi.y - pj.y, rz = DIM == 3 ? pi.z - pj.z : 0.f;
+                float r2 = rx * rx;
+                r2 = fmaf(ry, ry, r2);
+                if (DIM == 3) r2 = fmaf(rz, rz, r2);
+                if (r2 < ph.RL2 && j != i) {
+                    if (cnt < kmax) nbr[(size_t)cnt * n + i] = j;
+                    ++cnt;
+                    other |= phase_of(pj.w) != phi_;
+                }
+            }
+        }
+    }
     if (cnt > kmax) {
         atomicOr(d.flags, FLAG_LIST);
         cnt = kmax;
@@ -417,15 +441,18 @@ __global__ void __launch_bounds__(256) k_sweep_a(Dev d, Phys ph, const float *__
         const int *__restrict__ nbr = d.nbr;
         const float4 *__restrict__ phi = d.phi;
         const float4 *__restrict__ plo = d.plo;
-        for (int k = 0; k < cnt; ++k) {
-            const int j = __ldg(nbr + (size_t)k * n + i);
+        const int *__restrict__ np = nbr + i;
+#pragma unroll 4
+        for (int k = 0; k < cnt; ++k, np += n) {
+            const int j = __ldg(np);
             const float4 hj = __ldg(phi + j);
             const float4 lj = __ldg(plo + j);
             float rx, ry, rz;
             const float r2 = pair_vec<DIM>(hi, lo, hj, lj, rx, ry, rz);
-            if (!(r2 < ph.R2)) continue;
+            // beyond the support (list entries in the skin) t clamps to 0 and
+            // every kernel term vanishes
             const float r = sqrtf(r2);
-            const float t = fmaf(-0.5f * inv_h, r, 1.f);
+            const float t = fmaxf(fmaf(-0.5f * inv_h, r, 1.f), 0.f);
             const float t3 = t * t * t;
             if (phase_of(hj.w) == phi_) {
                 if (renorm) {
@@ -502,18 +529,21 @@ __global__ void __launch_bounds__(256) k_sweep_b(Dev d, Phys ph)
     const float4 *__restrict__ vel = d.vel;
     const float4 *__restrict__ T4 = d.T4;
     const float2 *__restrict__ T2 = d.T2;
-    for (int k = 0; k < cnt; ++k) {
-        const int j = __ldg(nbr + (size_t)k * n + i);
+    const int *__restrict__ np = nbr + i;
+#pragma unroll 4
+    for (int k = 0; k < cnt; ++k, np += n) {
+        const int j = __ldg(np);
         const float4 hj = __ldg(phi + j);
         const float4 lj = __ldg(plo + j);
-        float rx, ry, rz;
-        const float r2 = pair_vec<DIM>(hi, lo, hj, lj, rx, ry, rz);
-        if (!(r2 < ph.R2)) continue;
-        const int phj = phase_of(hj.w);
         const float4 aj = __ldg(aux + j);
         const float4 uj = __ldg(vel + j);
+        float rx, ry, rz;
+        const float r2 = pair_vec<DIM>(hi, lo, hj, lj, rx, ry, rz);
+        const int phj = phase_of(hj.w);
+        // beyond the support (list entries in the skin) t clamps to 0 and
+        // every pair term below vanishes
         const float r = sqrtf(r2);
-        const float t = fmaf(-0.5f * inv_h, r, 1.f);
+        const float t = fmaxf(fmaf(-0.5f * inv_h, r, 1.f), 0.f);
         const float t3 = t * t * t;
         const float pt = ph.mass[phj] * (ai.y + aj.y) * t3;
         px = fmaf(pt, rx, px);
