@@ -259,7 +259,7 @@ int validate(const sph_params *P, int64_t n)
         if (!(P->box_hi[k] > P->box_lo[k])) return fail(SPH_EINVAL, "box_hi must exceed box_lo");
         if (!std::isfinite(P->g[k])) return fail(SPH_EINVAL, "g must be finite");
     }
-    if (n < 0 || n > (int64_t)0x7fffffff) return fail(SPH_EINVAL, "n must be in [0, 2^31)");
+    if (n < 0 || n > ((int64_t)1 << 29)) return fail(SPH_EINVAL, "n must be in [0, 2^29]");
     return SPH_OK;
 }
 
@@ -408,15 +408,12 @@ int sph_create(const sph_params *params, int64_t n, const double *x, const doubl
     Dev &a0 = s->buf[0];
     if (!err) {
         err |= s->alloc(&a0.pa, N);
-        err |= s->alloc(&a0.phi, N);
-        err |= s->alloc(&a0.plo, N);
-        err |= s->alloc(&a0.vel, N);
+        err |= s->alloc(&a0.pd, 4 * N);
         err |= s->alloc(&a0.nbr, N * (size_t)ph.kmax);
         err |= s->alloc(&a0.ncnt, N);
         err |= s->alloc(&a0.nflag, N);
         err |= s->alloc(&a0.drho_stage, N);
         err |= s->alloc(&a0.drho_eval, N);
-        err |= s->alloc(&a0.aux, N);
         err |= s->alloc(&a0.T4, N);
         err |= s->alloc(&a0.T2, N);
         err |= s->alloc(&a0.acc, N);
@@ -434,9 +431,9 @@ int sph_create(const sph_params *params, int64_t n, const double *x, const doubl
     }
     if (err) return cleanup(SPH_ENOMEM);
     Dev &a1 = s->buf[1];
-    a1.pa = a0.pa; a1.phi = a0.phi; a1.plo = a0.plo; a1.vel = a0.vel; a1.drho_stage = a0.drho_stage;
+    a1.pa = a0.pa; a1.pd = a0.pd; a1.drho_stage = a0.drho_stage;
     a1.nbr = a0.nbr; a1.ncnt = a0.ncnt; a1.nflag = a0.nflag;
-    a1.drho_eval = a0.drho_eval; a1.aux = a0.aux; a1.T4 = a0.T4; a1.T2 = a0.T2; a1.acc = a0.acc;
+    a1.drho_eval = a0.drho_eval; a1.T4 = a0.T4; a1.T2 = a0.T2; a1.acc = a0.acc;
     a1.cstart = a0.cstart;
     a0.flags = a1.flags = s->flags;
     a0.step = a1.step = s->dstep;

@@ -72,12 +72,14 @@ struct Dev {
     int *cell;          // n, cell id (sorted order)
     // stage arrays
     float4 *pa;         // n, (x - box corner as FP32 xyz, phase sign): list-build filter only
-    float4 *phi;        // n, (hi xyz, +/- m/rho of the stage input: sign = phase)
-    float4 *plo;        // n, (lo xyz, (m/rho) * drho of the stage input)
-    float4 *vel;        // n, (u xyz, 0) FP32 copy of the stage velocity
+    // pd: one 64-byte record per particle, read whole by the interaction sweeps
+    //   pd[4j + PD_HI]  (hi xyz, +/- m/rho of the stage input: sign = phase)
+    //   pd[4j + PD_LO]  (lo xyz, (m/rho) * drho of the stage input)
+    //   pd[4j + PD_AUX] (m/rho, P/rho^2, interface flag, P) after sweep A
+    //   pd[4j + PD_VEL] (u xyz, 0) FP32 copy of the stage velocity
+    float4 *pd;
     float *drho_stage;  // n, drho* of the predictor
     float *drho_eval;   // n, drho after renormalisation (stage output)
-    float4 *aux;        // n, (m/rho, P/rho^2, interface flag, P)
     float4 *T4;         // n, T sigma^-2 = T (m/rho)^2: 2-D (xx, xy, yy, 0); 3-D (xx, xy, xz, yy)
     float2 *T2;         // n, 3-D only: (yz, zz)
     float4 *acc;        // n, (a xyz, Drho/Dt)
@@ -90,6 +92,8 @@ struct Dev {
     unsigned *flags;    // 1 word
     long long *step;    // device step counter (drives the renormalisation schedule)
 };
+
+enum { PD_HI = 0, PD_LO = 1, PD_AUX = 2, PD_VEL = 3 };
 
 __device__ __forceinline__ int phase_of(float w) { return __float_as_uint(w) >> 31; }
 
@@ -119,8 +123,7 @@ __device__ __forceinline__ void cell_coords(const Grid &g, int c, int &cx, int &
 // f(j, hj, lj, rx, ry, rz, r2) for those with |r_ij|^2 < R2 (j == i included).
 template <int DIM, class F>
 __device__ __forceinline__ void for_each_candidate(const Grid &g, const int *__restrict__ cstart,
-                                                   const float4 *__restrict__ phi, const float4 *__restrict__ plo,
-                                                   int cx, int cy, int cz, const float4 &hi, const float4 &lo,
+                                                   const float4 *__restrict__ pd, int cx, int cy, int cz, const float4 &hi, const float4 &lo,
                                                    float R2, F &&f)
 {
     const int z0 = DIM == 3 ? max(cz - 1, 0) : 0;
@@ -134,8 +137,8 @@ __device__ __forceinline__ void for_each_candidate(const Grid &g, const int *__r
             const int jb = __ldg(cstart + row + x0), je = __ldg(cstart + row + x1 + 1);
 #pragma unroll 4
             for (int j = jb; j < je; ++j) {
-                const float4 hj = __ldg(phi + j);
-                const float4 lj = __ldg(plo + j);
+                const float4 hj = __ldg(pd + 4 * j + PD_HI);
+                const float4 lj = __ldg(pd + 4 * j + PD_LO);
                 float rx, ry, rz;
                 const float r2 = pair_vec<DIM>(hi, lo, hj, lj, rx, ry, rz);
                 if (r2 < R2) f(j, hj, lj, rx, ry, rz, r2);
@@ -355,11 +358,11 @@ __global__ void __launch_bounds__(256) k_gather(Dev src, Dev dst, Grid g, Phys p
     float vol;
     hi.w = signed_volume(ph, tg & 1, dr, vol);
     lo.w = vol * dr;
-    dst.phi[k] = hi;
-    dst.plo[k] = lo;
+    dst.pd[4 * k + PD_HI] = hi;
+    dst.pd[4 * k + PD_LO] = lo;
     dst.pa[k] = make_float4((float)(xa[0] - g.lo[0]), (float)(xa[1] - g.lo[1]), (float)(xa[2] - g.lo[2]),
                             (tg & 1) ? -1.f : 1.f);
-    dst.vel[k] = make_float4((float)ua[0], (float)ua[1], (float)ua[2], 0.f);
+    dst.pd[4 * k + PD_VEL] = make_float4((float)ua[0], (float)ua[1], (float)ua[2], 0.f);
 }
 
 // ---------------------------------------------------------------------------
@@ -429,7 +432,7 @@ __global__ void __launch_bounds__(256) k_sweep_a(Dev d, Phys ph, const float *__
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.n) return;
     const int renorm = stage1 && ph.renorm_every > 0 && (*d.step % ph.renorm_every) == 0;
-    const float4 hi = d.phi[i], lo = d.plo[i];
+    const float4 hi = d.pd[4 * i + PD_HI], lo = d.pd[4 * i + PD_LO];
     const int phi_ = phase_of(hi.w);
     // self term: W(0)/alpha_d = 1
     float s1 = fabsf(hi.w), c1 = 0.f, s2 = lo.w, c2 = 0.f;
@@ -439,19 +442,19 @@ __global__ void __launch_bounds__(256) k_sweep_a(Dev d, Phys ph, const float *__
         const float inv_h = ph.inv_h;
         const int n = d.n, cnt = d.ncnt[i];
         const int *__restrict__ nbr = d.nbr;
-        const float4 *__restrict__ phi = d.phi;
-        const float4 *__restrict__ plo = d.plo;
+        const float4 *__restrict__ pd = d.pd;
         const int *__restrict__ np = nbr + i;
 #pragma unroll 4
         for (int k = 0; k < cnt; ++k, np += n) {
             const int j = __ldg(np);
-            const float4 hj = __ldg(phi + j);
-            const float4 lj = __ldg(plo + j);
+            const float4 *q = pd + 4 * j;
+            const float4 hj = __ldg(q + PD_HI);
+            const float4 lj = __ldg(q + PD_LO);
             float rx, ry, rz;
             const float r2 = pair_vec<DIM>(hi, lo, hj, lj, rx, ry, rz);
             // beyond the support (list entries in the skin) t clamps to 0 and
             // every kernel term vanishes
-            const float r = sqrtf(r2);
+            const float r = r2 * rsqrtf(fmaxf(r2, 1e-30f));
             const float t = fmaxf(fmaf(-0.5f * inv_h, r, 1.f), 0.f);
             const float t3 = t * t * t;
             if (phase_of(hj.w) == phi_) {
@@ -495,7 +498,7 @@ __global__ void __launch_bounds__(256) k_sweep_a(Dev d, Phys ph, const float *__
             t2 = make_float2(-kk * gy * gz, kk * (iso - gz * gz));
         }
     }
-    d.aux[i] = make_float4(vol, P / (rho * rho), iface, P);
+    d.pd[4 * i + PD_AUX] = make_float4(vol, P / (rho * rho), iface, P);
     d.T4[i] = t4;
     if (DIM == 3) d.T2[i] = t2;
 }
@@ -510,10 +513,10 @@ __global__ void __launch_bounds__(256) k_sweep_b(Dev d, Phys ph)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.n) return;
-    const float4 hi = d.phi[i], lo = d.plo[i];
+    const float4 hi = d.pd[4 * i + PD_HI], lo = d.pd[4 * i + PD_LO];
     const int phi_ = phase_of(hi.w);
-    const float4 ai = d.aux[i];
-    const float4 ui = d.vel[i];
+    const float4 ai = d.pd[4 * i + PD_AUX];
+    const float4 ui = d.pd[4 * i + PD_VEL];
     const float4 Ti = d.T4[i];
     const float2 Ti2 = DIM == 3 ? d.T2[i] : make_float2(0.f, 0.f);
     float px = 0.f, py = 0.f, pz = 0.f;    // sum m_j (P_i/rho_i^2 + P_j/rho_j^2) t^3 r_ij
@@ -522,36 +525,37 @@ __global__ void __launch_bounds__(256) k_sweep_b(Dev d, Phys ph)
     float dv = 0.f;                        // sum V_j t^3 u_ij . r_ij
     const float inv_h = ph.inv_h;
     const int n = d.n, cnt = d.ncnt[i];
+    // per-phase constants of the pair terms as registers (selected per pair)
+    const float m_wat = ph.mass[0], m_oil = ph.mass[1];
+    const float kv_wat = ph.kvis[2 * phi_], kv_oil = ph.kvis[2 * phi_ + 1];
     const int *__restrict__ nbr = d.nbr;
-    const float4 *__restrict__ phi = d.phi;
-    const float4 *__restrict__ plo = d.plo;
-    const float4 *__restrict__ aux = d.aux;
-    const float4 *__restrict__ vel = d.vel;
+    const float4 *__restrict__ pd = d.pd;
     const float4 *__restrict__ T4 = d.T4;
     const float2 *__restrict__ T2 = d.T2;
     const int *__restrict__ np = nbr + i;
 #pragma unroll 4
     for (int k = 0; k < cnt; ++k, np += n) {
         const int j = __ldg(np);
-        const float4 hj = __ldg(phi + j);
-        const float4 lj = __ldg(plo + j);
-        const float4 aj = __ldg(aux + j);
-        const float4 uj = __ldg(vel + j);
+        const float4 *q = pd + 4 * j;
+        const float4 hj = __ldg(q + PD_HI);
+        const float4 lj = __ldg(q + PD_LO);
+        const float4 aj = __ldg(q + PD_AUX);
+        const float4 uj = __ldg(q + PD_VEL);
         float rx, ry, rz;
         const float r2 = pair_vec<DIM>(hi, lo, hj, lj, rx, ry, rz);
-        const int phj = phase_of(hj.w);
+        const bool oj = hj.w < 0.f;
         // beyond the support (list entries in the skin) t clamps to 0 and
         // every pair term below vanishes
-        const float r = sqrtf(r2);
+        const float r = r2 * rsqrtf(fmaxf(r2, 1e-30f));
         const float t = fmaxf(fmaf(-0.5f * inv_h, r, 1.f), 0.f);
         const float t3 = t * t * t;
-        const float pt = ph.mass[phj] * (ai.y + aj.y) * t3;
+        const float pt = (oj ? m_oil : m_wat) * (ai.y + aj.y) * t3;
         px = fmaf(pt, rx, px);
         py = fmaf(pt, ry, py);
         if (DIM == 3) pz = fmaf(pt, rz, pz);
         const float ux = ui.x - uj.x, uy = ui.y - uj.y, uz = DIM == 3 ? ui.z - uj.z : 0.f;
         const float vt = aj.x * t3;
-        const float s = ph.kvis[2 * phi_ + phj] * vt * __fdividef(r2, r2 + ph.delta2);
+        const float s = (oj ? kv_oil : kv_wat) * vt * __fdividef(r2, r2 + ph.delta2);
         vx = fmaf(s, ux, vx);
         vy = fmaf(s, uy, vy);
         if (DIM == 3) vz = fmaf(s, uz, vz);
@@ -625,9 +629,9 @@ __global__ void __launch_bounds__(256) k_predict(Dev d, Grid g, Phys ph, double 
     float vol;
     hi.w = signed_volume(ph, tg & 1, drs, vol);
     lo.w = vol * drs;
-    d.phi[k] = hi;
-    d.plo[k] = lo;
-    d.vel[k] = make_float4((float)us[0], (float)us[1], (float)us[2], 0.f);
+    d.pd[4 * k + PD_HI] = hi;
+    d.pd[4 * k + PD_LO] = lo;
+    d.pd[4 * k + PD_VEL] = make_float4((float)us[0], (float)us[1], (float)us[2], 0.f);
     if (!finite) atomicOr(d.flags, FLAG_NONFINITE);
 }
 
@@ -643,7 +647,7 @@ __global__ void __launch_bounds__(256) k_correct(Dev d, double dt)
     d.drho[k] = dr;
     bool finite = isfinite(dr);
     if (!(tg & 2)) {
-        const float4 us = d.vel[k];
+        const float4 us = d.pd[4 * k + PD_VEL];
         const double usa[3] = {us.x, us.y, us.z};
         const double af[3] = {a.x, a.y, a.z};
 #pragma unroll
@@ -666,11 +670,11 @@ __global__ void __launch_bounds__(256) k_nbr_count(Dev d, Grid g, Phys ph, int *
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.n) return;
-    const float4 hi = d.phi[i], lo = d.plo[i];
+    const float4 hi = d.pd[4 * i + PD_HI], lo = d.pd[4 * i + PD_LO];
     int cx, cy, cz;
     cell_coords(g, d.cell[i], cx, cy, cz);
     int cnt = 0;
-    for_each_candidate<DIM>(g, d.cstart, d.phi, d.plo, cx, cy, cz, hi, lo, ph.R2,
+    for_each_candidate<DIM>(g, d.cstart, d.pd, cx, cy, cz, hi, lo, ph.R2,
                             [&](int j, const float4 &, const float4 &, float, float, float, float) { cnt += j != i; });
     count[i] = cnt;
 }
@@ -680,11 +684,11 @@ __global__ void __launch_bounds__(256) k_nbr_fill(Dev d, Grid g, Phys ph, const 
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.n) return;
-    const float4 hi = d.phi[i], lo = d.plo[i];
+    const float4 hi = d.pd[4 * i + PD_HI], lo = d.pd[4 * i + PD_LO];
     int cx, cy, cz;
     cell_coords(g, d.cell[i], cx, cy, cz);
     long long w = start[i];
-    for_each_candidate<DIM>(g, d.cstart, d.phi, d.plo, cx, cy, cz, hi, lo, ph.R2,
+    for_each_candidate<DIM>(g, d.cstart, d.pd, cx, cy, cz, hi, lo, ph.R2,
                             [&](int j, const float4 &, const float4 &, float, float, float, float) {
                                 if (j != i) list[w++] = d.pid[j];
                             });
@@ -697,11 +701,11 @@ __global__ void __launch_bounds__(256) k_pair_stats(Dev d, Grid g, Phys ph, unsi
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     int all = 0, other = 0;
     if (i < d.n) {
-        const float4 hi = d.phi[i], lo = d.plo[i];
+        const float4 hi = d.pd[4 * i + PD_HI], lo = d.pd[4 * i + PD_LO];
         const int phi_ = phase_of(hi.w);
         int cx, cy, cz;
         cell_coords(g, d.cell[i], cx, cy, cz);
-        for_each_candidate<DIM>(g, d.cstart, d.phi, d.plo, cx, cy, cz, hi, lo, ph.R2,
+        for_each_candidate<DIM>(g, d.cstart, d.pd, cx, cy, cz, hi, lo, ph.R2,
                                 [&](int j, const float4 &hj, const float4 &, float, float, float, float) {
                                     all += j != i;
                                     other += phase_of(hj.w) != phi_;
@@ -744,7 +748,7 @@ __global__ void __launch_bounds__(256) k_unpermute(Dev d, Phys ph, int kind, dou
         out[p] = (double)ph.rho0[phs] + (double)d.drho_eval[k];
         break;
     case RK_P:
-        out[p] = d.aux[k].w;
+        out[p] = d.pd[4 * k + PD_AUX].w;
         break;
     case RK_ACC: {
         const float4 a = d.acc[k];
@@ -757,7 +761,7 @@ __global__ void __launch_bounds__(256) k_unpermute(Dev d, Phys ph, int kind, dou
         break;
     case RK_T: {
         const float4 t = d.T4[k];
-        const double v2 = (double)d.aux[k].x * (double)d.aux[k].x;
+        const double v2 = (double)d.pd[4 * k + PD_AUX].x * (double)d.pd[4 * k + PD_AUX].x;
         double T[9];
         if (DIM == 2) {
             T[0] = t.x; T[1] = t.y; T[2] = t.y; T[3] = t.z;
