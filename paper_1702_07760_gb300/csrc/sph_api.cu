@@ -171,12 +171,12 @@ void sph_sim::enqueue_eval(int stage1, const float *drho_in)
 {
     Dev &d = buf[cur];
     launch(KI_SWEEP_A, [&] {
-        if (dim == 2) k_sweep_a<2><<<blocks(n), 256, 0, stream>>>(d, phys, drho_in, stage1);
-        else k_sweep_a<3><<<blocks(n), 256, 0, stream>>>(d, phys, drho_in, stage1);
+        if (dim == 2) k_sweep_a<2><<<blocks(n), 256, 0, stream>>>(d, grid, phys, drho_in, stage1);
+        else k_sweep_a<3><<<blocks(n), 256, 0, stream>>>(d, grid, phys, drho_in, stage1);
     });
     launch(KI_SWEEP_B, [&] {
-        if (dim == 2) k_sweep_b<2><<<blocks(n), 256, 0, stream>>>(d, phys);
-        else k_sweep_b<3><<<blocks(n), 256, 0, stream>>>(d, phys);
+        if (dim == 2) k_sweep_b<2><<<blocks(n), 256, 0, stream>>>(d, grid, phys);
+        else k_sweep_b<3><<<blocks(n), 256, 0, stream>>>(d, grid, phys);
     });
 }
 
@@ -259,7 +259,7 @@ int validate(const sph_params *P, int64_t n)
         if (!(P->box_hi[k] > P->box_lo[k])) return fail(SPH_EINVAL, "box_hi must exceed box_lo");
         if (!std::isfinite(P->g[k])) return fail(SPH_EINVAL, "g must be finite");
     }
-    if (n < 0 || n > ((int64_t)1 << 29)) return fail(SPH_EINVAL, "n must be in [0, 2^29]");
+    if (n < 0 || n > ((int64_t)1 << 26)) return fail(SPH_EINVAL, "n must be in [0, 2^26]");
     return SPH_OK;
 }
 
@@ -343,11 +343,8 @@ int sph_create(const sph_params *params, int64_t n, const double *x, const doubl
     s->grid.ny = dims[1];
     s->grid.nz = dims[2];
     s->grid.csd = P.cell_size;
+    s->grid.cs = (float)P.cell_size;
     for (int c = 0; c < 3; ++c) s->grid.lo[c] = c < dim ? P.box_lo[c] : 0.0;
-    // largest power of two not above the cell edge
-    int e2 = 0;
-    std::frexp(P.cell_size, &e2);
-    s->grid.q = std::ldexp(1.0, e2 - 1);
     // physics constants
     const double pi = 3.14159265358979323846;
     const double h = P.h;
@@ -355,7 +352,7 @@ int sph_create(const sph_params *params, int64_t n, const double *x, const doubl
     Phys &ph = s->phys;
     ph.inv_h = (float)(1.0 / h);
     ph.R2 = (float)(4.0 * h * h);
-    ph.RL2 = (float)(P.cell_size * P.cell_size * (1.0 + 2e-5));
+    ph.RL2 = (float)(P.cell_size * P.cell_size);
     ph.skin = 0.5 * (P.cell_size - 2.0 * h);
     ph.kmax = P.max_neighbours > 0 ? P.max_neighbours : (dim == 2 ? 48 : 128);
     ph.cF = (float)(-5.0 * alpha_d / (h * h));
@@ -407,8 +404,11 @@ int sph_create(const sph_params *params, int64_t n, const double *x, const doubl
     }
     Dev &a0 = s->buf[0];
     if (!err) {
-        err |= s->alloc(&a0.pa, N);
-        err |= s->alloc(&a0.pd, 4 * N);
+        err |= s->alloc(&a0.pos, N);
+        err |= s->alloc(&a0.vd, N);
+        err |= s->alloc(&a0.posv, N);
+        err |= s->alloc(&a0.velp, N);
+        err |= s->alloc(&a0.pres, N);
         err |= s->alloc(&a0.nbr, N * (size_t)ph.kmax);
         err |= s->alloc(&a0.ncnt, N);
         err |= s->alloc(&a0.nflag, N);
@@ -431,7 +431,8 @@ int sph_create(const sph_params *params, int64_t n, const double *x, const doubl
     }
     if (err) return cleanup(SPH_ENOMEM);
     Dev &a1 = s->buf[1];
-    a1.pa = a0.pa; a1.pd = a0.pd; a1.drho_stage = a0.drho_stage;
+    a1.pos = a0.pos; a1.vd = a0.vd; a1.posv = a0.posv; a1.velp = a0.velp; a1.pres = a0.pres;
+    a1.drho_stage = a0.drho_stage;
     a1.nbr = a0.nbr; a1.ncnt = a0.ncnt; a1.nflag = a0.nflag;
     a1.drho_eval = a0.drho_eval; a1.T4 = a0.T4; a1.T2 = a0.T2; a1.acc = a0.acc;
     a1.cstart = a0.cstart;

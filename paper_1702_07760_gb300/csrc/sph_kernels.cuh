@@ -4,10 +4,11 @@
 // Model", Sec. II.  Layout and arithmetic choices made for the GPU:
 //   * particles live in cell order (stable by original id), structure of
 //     arrays;
-//   * a position used by the interaction sweeps is an exactly representable
-//     FP32 multiple of a power-of-two quantum q (an integer lattice index
-//     times q) plus an FP32 offset below q/2, so a pair vector
-//     (hi_i - hi_j) + (lo_i - lo_j) is formed with one rounding;
+//   * a position used by the interaction sweeps is the particle's cell (an
+//     integer index of the cell grid) plus an FP32 offset from the cell
+//     centre; a pair vector is (o_i - o_j) + (c_i - c_j) * cell edge, the
+//     cell difference (-1, 0 or 1 per axis) being packed into the pair's
+//     neighbour-list entry;
 //   * the FP64 position and velocity are the integration accumulators;
 //   * density is stored as the deviation drho = rho - rho0(phase) in FP32, so
 //     the equation of state and the renormalisation never subtract two
@@ -15,7 +16,8 @@
 //   * once per step a neighbour list (radius = cell edge = 2h + 2 skin) is
 //     built from the cell list and stored column-major, so the four
 //     interaction sweeps of the step read it coalesced and run without the
-//     branch divergence of a candidate scan.
+//     branch divergence of a candidate scan; a sweep gathers two 16-byte
+//     records per neighbour.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -34,8 +36,7 @@ enum : unsigned {
 struct Phys {
     float inv_h;        // 1/h
     float R2;           // (2h)^2, support test
-    float RL2;          // list radius^2: cell edge^2 widened by a relative 1e-5 to cover
-                        // the rounding of the FP32 filter positions
+    float RL2;          // list radius^2 = cell edge^2
     float cF;           // -5 alpha_d / h^2: grad W_ij = cF (1-q/2)^3 r_ij
     float mass[2];      // per-phase particle mass
     float inv_mass[2];
@@ -55,9 +56,9 @@ struct Phys {
 
 struct Grid {
     int nx, ny, nz;     // cells per axis (nz = 1 in 2-D)
-    double csd;         // cell edge (FP64) for hashing
+    float cs;           // cell edge (FP32): pair vectors
+    double csd;         // cell edge (FP64): hashing and offsets
     double lo[3];       // box lower corner
-    double q;           // power-of-two position quantum (<= cell edge)
 };
 
 // All device arrays of one simulation (sorted order unless noted).
@@ -71,20 +72,19 @@ struct Dev {
     uint8_t *tag;       // n, bit0 oil, bit1 wall
     int *cell;          // n, cell id (sorted order)
     // stage arrays
-    float4 *pa;         // n, (x - box corner as FP32 xyz, phase sign): list-build filter only
-    // pd: one 64-byte record per particle, read whole by the interaction sweeps
-    //   pd[4j + PD_HI]  (hi xyz, +/- m/rho of the stage input: sign = phase)
-    //   pd[4j + PD_LO]  (lo xyz, (m/rho) * drho of the stage input)
-    //   pd[4j + PD_AUX] (m/rho, P/rho^2, interface flag, P) after sweep A
-    //   pd[4j + PD_VEL] (u xyz, 0) FP32 copy of the stage velocity
-    float4 *pd;
+    float4 *pos;        // n, (offset from the cell centre xyz, +/- m/rho of the stage input; sign = phase)
+    float *vd;          // n, (m/rho) * drho of the stage input
+    float4 *posv;       // n, (offset xyz, +/- m/rho after renormalisation with its lowest
+                        //     mantissa bit replaced by the interface flag): sweep A output
+    float4 *velp;       // n, (u xyz of the stage, P/rho^2 from sweep A)
+    float *pres;        // n, P from sweep A
     float *drho_stage;  // n, drho* of the predictor
     float *drho_eval;   // n, drho after renormalisation (stage output)
     float4 *T4;         // n, T sigma^-2 = T (m/rho)^2: 2-D (xx, xy, yy, 0); 3-D (xx, xy, xz, yy)
     float2 *T2;         // n, 3-D only: (yz, zz)
     float4 *acc;        // n, (a xyz, Drho/Dt)
     // neighbour list
-    int *nbr;           // kmax * n, entry k of particle i at nbr[k * n + i]
+    unsigned *nbr;      // kmax * n, entry k of particle i at nbr[k * n + i]
     int *ncnt;          // n, list length
     uint8_t *nflag;     // n, bit0: an other-phase particle lies within the list radius
     // cell list
@@ -93,18 +93,33 @@ struct Dev {
     long long *step;    // device step counter (drives the renormalisation schedule)
 };
 
-enum { PD_HI = 0, PD_LO = 1, PD_AUX = 2, PD_VEL = 3 };
+// Neighbour-list entry: particle index in the low 26 bits; per axis a, two
+// bits at 26 + 2a holding (c_i - c_j) + 1 in {0, 1, 2}.
+constexpr int NBR_IDX_BITS = 26;
+constexpr unsigned NBR_IDX_MASK = (1u << NBR_IDX_BITS) - 1u;
 
 __device__ __forceinline__ int phase_of(float w) { return __float_as_uint(w) >> 31; }
 
-// r_ij = x_i - x_j from the split positions; the hi difference is exact.
+// Per-phase constant without indexing the parameter block at run time (an
+// indexed parameter load would go through the constant cache per thread).
+__device__ __forceinline__ float by_phase(int phase, const float (&a)[2]) { return phase ? a[1] : a[0]; }
+
+// (c_i - c_j) * cs for axis a of an entry, exact: the code e in {0, 1, 2}
+// becomes the float e - 1 through the 2^23 + 2^22 mantissa trick.
+__device__ __forceinline__ float entry_shift(unsigned e, int a, float cs)
+{
+    const unsigned code = (e >> (NBR_IDX_BITS + 2 * a)) & 3u;
+    return (__uint_as_float(0x4B400000u | code) - 12582913.f) * cs;
+}
+
+// r_ij = x_i - x_j from cell offsets and the cell-centre difference (s).
 template <int DIM>
-__device__ __forceinline__ float pair_vec(const float4 &hi, const float4 &lo, const float4 &hj, const float4 &lj,
+__device__ __forceinline__ float pair_vec(const float4 &oi, const float4 &oj, float sx, float sy, float sz,
                                           float &rx, float &ry, float &rz)
 {
-    rx = (hi.x - hj.x) + (lo.x - lj.x);
-    ry = (hi.y - hj.y) + (lo.y - lj.y);
-    rz = DIM == 3 ? (hi.z - hj.z) + (lo.z - lj.z) : 0.f;
+    rx = (oi.x - oj.x) + sx;
+    ry = (oi.y - oj.y) + sy;
+    rz = DIM == 3 ? (oi.z - oj.z) + sz : 0.f;
     float r2 = rx * rx;
     r2 = fmaf(ry, ry, r2);
     if (DIM == 3) r2 = fmaf(rz, rz, r2);
@@ -120,28 +135,37 @@ __device__ __forceinline__ void cell_coords(const Grid &g, int c, int &cx, int &
 }
 
 // Scans every particle of the 3^DIM cells around cell (cx, cy, cz) and calls
-// f(j, hj, lj, rx, ry, rz, r2) for those with |r_ij|^2 < R2 (j == i included).
+// f(j, oj, rx, ry, rz, r2, code) for those with |r_ij|^2 < R2 (j == i
+// included); code is the shift part of a neighbour-list entry.
 template <int DIM, class F>
 __device__ __forceinline__ void for_each_candidate(const Grid &g, const int *__restrict__ cstart,
-                                                   const float4 *__restrict__ pd, int cx, int cy, int cz, const float4 &hi, const float4 &lo,
-                                                   float R2, F &&f)
+                                                   const float4 *__restrict__ pos, int cx, int cy, int cz,
+                                                   const float4 &oi, float R2, F &&f)
 {
     const int z0 = DIM == 3 ? max(cz - 1, 0) : 0;
     const int z1 = DIM == 3 ? min(cz + 1, g.nz - 1) : 0;
     const int y0 = max(cy - 1, 0), y1 = min(cy + 1, g.ny - 1);
     const int x0 = max(cx - 1, 0), x1 = min(cx + 1, g.nx - 1);
+    const float cs = g.cs;
     for (int z = z0; z <= z1; ++z) {
+        const float sz = (float)(cz - z) * cs;
         for (int y = y0; y <= y1; ++y) {
+            const float sy = (float)(cy - y) * cs;
             // the cells x0..x1 of a row are contiguous in the sorted order
             const int row = (z * g.ny + y) * g.nx;
             const int jb = __ldg(cstart + row + x0), je = __ldg(cstart + row + x1 + 1);
+            const int b1 = __ldg(cstart + row + cx), b2 = __ldg(cstart + row + cx + 1);
+            const unsigned cyz = ((unsigned)(cy - y + 1) << (NBR_IDX_BITS + 2)) |
+                                 ((unsigned)(DIM == 3 ? cz - z + 1 : 1) << (NBR_IDX_BITS + 4));
 #pragma unroll 4
             for (int j = jb; j < je; ++j) {
-                const float4 hj = __ldg(pd + 4 * j + PD_HI);
-                const float4 lj = __ldg(pd + 4 * j + PD_LO);
+                const float4 oj = __ldg(pos + j);
+                // x cell of j: cx - 1, cx or cx + 1
+                const float sx = j < b1 ? cs : (j < b2 ? 0.f : -cs);
+                const unsigned ex = j < b1 ? 2u : (j < b2 ? 1u : 0u);
                 float rx, ry, rz;
-                const float r2 = pair_vec<DIM>(hi, lo, hj, lj, rx, ry, rz);
-                if (r2 < R2) f(j, hj, lj, rx, ry, rz, r2);
+                const float r2 = pair_vec<DIM>(oi, oj, sx, sy, sz, rx, ry, rz);
+                if (r2 < R2) f(j, oj, rx, ry, rz, r2, cyz | (ex << NBR_IDX_BITS));
             }
         }
     }
@@ -170,29 +194,22 @@ __device__ __forceinline__ float eos_tait7(float beta, float eps)
     return beta * eps * p;
 }
 
-// Split of an FP64 coordinate (relative to the box corner) into an exact
-// FP32 multiple of q and an FP32 remainder.
-__device__ __forceinline__ void split_coord(double X, double q, float &hi, float &lo)
-{
-    const double k = rint(X / q);
-    hi = (float)(k * q);
-    lo = (float)(X - k * q);
-}
-
+// FP32 offset of an FP64 position from the centre of cell c.
 template <int DIM>
-__device__ __forceinline__ void split_position(const Grid &g, const double xa[3], float4 &hi, float4 &lo)
+__device__ __forceinline__ float4 cell_offset(const Grid &g, int c, const double xa[3])
 {
-    float h[3] = {0.f, 0.f, 0.f}, l[3] = {0.f, 0.f, 0.f};
+    int cc[3];
+    cell_coords(g, c, cc[0], cc[1], cc[2]);
+    float o[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-    for (int a = 0; a < DIM; ++a) split_coord(xa[a] - g.lo[a], g.q, h[a], l[a]);
-    hi = make_float4(h[0], h[1], h[2], 0.f);
-    lo = make_float4(l[0], l[1], l[2], 0.f);
+    for (int a = 0; a < DIM; ++a) o[a] = (float)(xa[a] - (g.lo[a] + ((double)cc[a] + 0.5) * g.csd));
+    return make_float4(o[0], o[1], o[2], 0.f);
 }
 
 // Signed specific volume m/rho, negative for oil.
 __device__ __forceinline__ float signed_volume(const Phys &ph, int phase, float drho, float &vol)
 {
-    vol = ph.mass[phase] / (ph.rho0[phase] + drho);
+    vol = by_phase(phase, ph.mass) / (by_phase(phase, ph.rho0) + drho);
     return phase ? -vol : vol;
 }
 
@@ -349,20 +366,17 @@ __global__ void __launch_bounds__(256) k_gather(Dev src, Dev dst, Grid g, Phys p
     }
     const float dr = src.drho[o];
     const uint8_t tg = src.tag[o];
+    const int c = cell_tmp[o];
     dst.drho[k] = dr;
     dst.pid[k] = src.pid[o];
     dst.tag[k] = tg;
-    dst.cell[k] = cell_tmp[o];
-    float4 hi, lo;
-    split_position<DIM>(g, xa, hi, lo);
+    dst.cell[k] = c;
+    float4 p = cell_offset<DIM>(g, c, xa);
     float vol;
-    hi.w = signed_volume(ph, tg & 1, dr, vol);
-    lo.w = vol * dr;
-    dst.pd[4 * k + PD_HI] = hi;
-    dst.pd[4 * k + PD_LO] = lo;
-    dst.pa[k] = make_float4((float)(xa[0] - g.lo[0]), (float)(xa[1] - g.lo[1]), (float)(xa[2] - g.lo[2]),
-                            (tg & 1) ? -1.f : 1.f);
-    dst.pd[4 * k + PD_VEL] = make_float4((float)ua[0], (float)ua[1], (float)ua[2], 0.f);
+    p.w = signed_volume(ph, tg & 1, dr, vol);
+    dst.pos[k] = p;
+    dst.vd[k] = vol * dr;
+    dst.velp[k] = make_float4((float)ua[0], (float)ua[1], (float)ua[2], 0.f);
 }
 
 // ---------------------------------------------------------------------------
@@ -374,40 +388,21 @@ __global__ void __launch_bounds__(256) k_build_list(Dev d, Grid g, Phys ph)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.n) return;
-    // the filter needs no more than FP32 absolute positions: their rounding
-    // (~1e-7 of the box) is far below the skin, and RL2 is widened to match
-    const float4 pi = d.pa[i];
-    const int phi_ = phase_of(pi.w);
+    const float4 oi = d.pos[i];
+    const int phi_ = phase_of(oi.w);
     int cx, cy, cz;
     cell_coords(g, d.cell[i], cx, cy, cz);
     int cnt = 0;
     int other = 0;
     const int n = d.n, kmax = ph.kmax;
-    int *__restrict__ nbr = d.nbr;
-    const float4 *__restrict__ pa = d.pa;
-    const int z0 = DIM == 3 ? max(cz - 1, 0) : 0;
-    const int z1 = DIM == 3 ? min(cz + 1, g.nz - 1) : 0;
-    const int y0 = max(cy - 1, 0), y1 = min(cy + 1, g.ny - 1);
-    const int x0 = max(cx - 1, 0), x1 = min(cx + 1, g.nx - 1);
-    for (int z = z0; z <= z1; ++z) {
-        for (int y = y0; y <= y1; ++y) {
-            const int row = (z * g.ny + y) * g.nx;
-            const int jb = __ldg(d.cstart + row + x0), je = __ldg(d.cstart + row + x1 + 1);
-#pragma unroll 4
-            for (int j = jb; j < je; ++j) {
-                const float4 pj = __ldg(pa + j);
-                const float rx = pi.x - pj.x, ry = pi.y - pj.y, rz = DIM == 3 ? pi.z - pj.z : 0.f;
-                float r2 = rx * rx;
-                r2 = fmaf(ry, ry, r2);
-                if (DIM == 3) r2 = fmaf(rz, rz, r2);
-                if (r2 < ph.RL2 && j != i) {
-                    if (cnt < kmax) nbr[(size_t)cnt * n + i] = j;
-                    ++cnt;
-                    other |= phase_of(pj.w) != phi_;
-                }
-            }
-        }
-    }
+    unsigned *__restrict__ nbr = d.nbr;
+    for_each_candidate<DIM>(g, d.cstart, d.pos, cx, cy, cz, oi, ph.RL2,
+        [&](int j, const float4 &oj, float, float, float, float, unsigned code) {
+            if (j == i) return;
+            if (cnt < kmax) nbr[(size_t)cnt * n + i] = (unsigned)j | code;
+            ++cnt;
+            other |= phase_of(oj.w) != phi_;
+        });
     if (cnt > kmax) {
         atomicOr(d.flags, FLAG_LIST);
         cnt = kmax;
@@ -427,45 +422,45 @@ __global__ void __launch_bounds__(256) k_build_list(Dev d, Grid g, Phys ph)
 // The colour gradient uses the density that entered the stage:
 // grad C_i = (1/V_i) sum_{j other phase} V_j^2 grad W_ij, V = m/rho = 1/sigma.
 template <int DIM>
-__global__ void __launch_bounds__(256) k_sweep_a(Dev d, Phys ph, const float *__restrict__ drho_in, int stage1)
+__global__ void __launch_bounds__(256) k_sweep_a(Dev d, Grid g, Phys ph, const float *__restrict__ drho_in, int stage1)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.n) return;
     const int renorm = stage1 && ph.renorm_every > 0 && (*d.step % ph.renorm_every) == 0;
-    const float4 hi = d.pd[4 * i + PD_HI], lo = d.pd[4 * i + PD_LO];
-    const int phi_ = phase_of(hi.w);
+    const float4 oi = d.pos[i];
+    const int phi_ = phase_of(oi.w);
     // self term: W(0)/alpha_d = 1
-    float s1 = fabsf(hi.w), c1 = 0.f, s2 = lo.w, c2 = 0.f;
+    float s1 = fabsf(oi.w), c1 = 0.f, s2 = d.vd[i], c2 = 0.f;
     float gx = 0.f, gy = 0.f, gz = 0.f;
     const bool other = d.nflag[i] & 1;
     if (renorm || other) {
-        const float inv_h = ph.inv_h;
+        const float inv_h = ph.inv_h, cs = g.cs;
         const int n = d.n, cnt = d.ncnt[i];
-        const int *__restrict__ nbr = d.nbr;
-        const float4 *__restrict__ pd = d.pd;
-        const int *__restrict__ np = nbr + i;
+        const unsigned *__restrict__ np = d.nbr + i;
+        const float4 *__restrict__ pos = d.pos;
+        const float *__restrict__ vd = d.vd;
 #pragma unroll 4
         for (int k = 0; k < cnt; ++k, np += n) {
-            const int j = __ldg(np);
-            const float4 *q = pd + 4 * j;
-            const float4 hj = __ldg(q + PD_HI);
-            const float4 lj = __ldg(q + PD_LO);
+            const unsigned e = __ldg(np);
+            const int j = (int)(e & NBR_IDX_MASK);
+            const float4 oj = __ldg(pos + j);
             float rx, ry, rz;
-            const float r2 = pair_vec<DIM>(hi, lo, hj, lj, rx, ry, rz);
+            const float r2 = pair_vec<DIM>(oi, oj, entry_shift(e, 0, cs), entry_shift(e, 1, cs),
+                                           DIM == 3 ? entry_shift(e, 2, cs) : 0.f, rx, ry, rz);
             // beyond the support (list entries in the skin) t clamps to 0 and
             // every kernel term vanishes
             const float r = r2 * rsqrtf(fmaxf(r2, 1e-30f));
             const float t = fmaxf(fmaf(-0.5f * inv_h, r, 1.f), 0.f);
             const float t3 = t * t * t;
-            if (phase_of(hj.w) == phi_) {
+            if (phase_of(oj.w) == phi_) {
                 if (renorm) {
                     // W / alpha_d = t^4 (2q + 1)
                     const float w = t3 * t * fmaf(2.f * inv_h, r, 1.f);
-                    kahan_add(s1, c1, fabsf(hj.w) * w);
-                    kahan_add(s2, c2, lj.w * w);
+                    kahan_add(s1, c1, fabsf(oj.w) * w);
+                    kahan_add(s2, c2, __ldg(vd + j) * w);
                 }
             } else {
-                const float c = hj.w * hj.w * t3;
+                const float c = oj.w * oj.w * t3;
                 gx = fmaf(c, rx, gx);
                 gy = fmaf(c, ry, gy);
                 if (DIM == 3) gz = fmaf(c, rz, gz);
@@ -474,20 +469,20 @@ __global__ void __launch_bounds__(256) k_sweep_a(Dev d, Phys ph, const float *__
     }
     const float drho = renorm ? s2 / s1 : drho_in[i];
     d.drho_eval[i] = drho;
-    const float rho = ph.rho0[phi_] + drho;
-    const float vol = ph.mass[phi_] / rho;
-    const float P = eos_tait7(ph.beta[phi_], drho * ph.inv_rho0[phi_]);
+    const float rho = by_phase(phi_, ph.rho0) + drho;
+    const float vol = by_phase(phi_, ph.mass) / rho;
+    const float P = eos_tait7(by_phase(phi_, ph.beta), drho * by_phase(phi_, ph.inv_rho0));
     // grad C_i = sigma_i sum V_j^2 grad W_ij, sigma_i = 1/|V_i| (entry density)
-    const float sc = ph.cF / fabsf(hi.w);
+    const float sc = ph.cF / fabsf(oi.w);
     gx *= sc;
     gy *= sc;
     gz *= sc;
     const float n2 = gx * gx + gy * gy + gz * gz;
-    float iface = 0.f;
+    unsigned iface = 0u;
     float4 t4 = make_float4(0.f, 0.f, 0.f, 0.f);
     float2 t2 = make_float2(0.f, 0.f);
     if (n2 > 0.f) {
-        iface = 1.f;
+        iface = 1u;
         // T sigma_i^-2 = alpha_s / |g| (|g|^2/d I - g g^T) V_i^2, V_i from the renormalised density
         const float kk = ph.alpha_s * rsqrtf(n2) * vol * vol;
         const float iso = n2 * ph.inv_dim;
@@ -498,7 +493,13 @@ __global__ void __launch_bounds__(256) k_sweep_a(Dev d, Phys ph, const float *__
             t2 = make_float2(-kk * gy * gz, kk * (iso - gz * gz));
         }
     }
-    d.pd[4 * i + PD_AUX] = make_float4(vol, P / (rho * rho), iface, P);
+    // signed volume (sign = phase) whose lowest mantissa bit carries the
+    // interface flag: at most one unit in the last place, the size of the
+    // rounding of m/rho itself
+    const float vs = phi_ ? -vol : vol;
+    d.posv[i] = make_float4(oi.x, oi.y, oi.z, __uint_as_float((__float_as_uint(vs) & ~1u) | iface));
+    d.velp[i].w = P / (rho * rho);
+    d.pres[i] = P;
     d.T4[i] = t4;
     if (DIM == 3) d.T2[i] = t2;
 }
@@ -509,53 +510,53 @@ __global__ void __launch_bounds__(256) k_sweep_a(Dev d, Phys ph, const float *__
 // (Eq. ct_dist_2).  grad_i W_ij = cF t^3 r_ij with t = 1 - q/2; the common
 // factor cF is applied once per particle.
 template <int DIM>
-__global__ void __launch_bounds__(256) k_sweep_b(Dev d, Phys ph)
+__global__ void __launch_bounds__(256) k_sweep_b(Dev d, Grid g, Phys ph)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.n) return;
-    const float4 hi = d.pd[4 * i + PD_HI], lo = d.pd[4 * i + PD_LO];
-    const int phi_ = phase_of(hi.w);
-    const float4 ai = d.pd[4 * i + PD_AUX];
-    const float4 ui = d.pd[4 * i + PD_VEL];
+    const float4 oi = d.posv[i];
+    const int phi_ = phase_of(oi.w);
+    const unsigned iface_i = __float_as_uint(oi.w) & 1u;
+    const float4 ui = d.velp[i];             // w: P_i / rho_i^2
     const float4 Ti = d.T4[i];
     const float2 Ti2 = DIM == 3 ? d.T2[i] : make_float2(0.f, 0.f);
     float px = 0.f, py = 0.f, pz = 0.f;    // sum m_j (P_i/rho_i^2 + P_j/rho_j^2) t^3 r_ij
     float vx = 0.f, vy = 0.f, vz = 0.f;    // sum k_ij V_j t^3 r^2/(r^2+delta^2) u_ij
     float sx = 0.f, sy = 0.f, sz = 0.f;    // sum (T_i/sigma_i^2 + T_j/sigma_j^2) . t^3 r_ij
     float dv = 0.f;                        // sum V_j t^3 u_ij . r_ij
-    const float inv_h = ph.inv_h;
+    const float inv_h = ph.inv_h, cs = g.cs;
     const int n = d.n, cnt = d.ncnt[i];
     // per-phase constants of the pair terms as registers (selected per pair)
     const float m_wat = ph.mass[0], m_oil = ph.mass[1];
-    const float kv_wat = ph.kvis[2 * phi_], kv_oil = ph.kvis[2 * phi_ + 1];
-    const int *__restrict__ nbr = d.nbr;
-    const float4 *__restrict__ pd = d.pd;
+    const float kv_wat = phi_ ? ph.kvis[2] : ph.kvis[0], kv_oil = phi_ ? ph.kvis[3] : ph.kvis[1];
+    const unsigned *__restrict__ np = d.nbr + i;
+    const float4 *__restrict__ posv = d.posv;
+    const float4 *__restrict__ velp = d.velp;
     const float4 *__restrict__ T4 = d.T4;
     const float2 *__restrict__ T2 = d.T2;
-    const int *__restrict__ np = nbr + i;
-#pragma unroll 4
+#pragma unroll (DIM == 3 ? 4 : 8)
     for (int k = 0; k < cnt; ++k, np += n) {
-        const int j = __ldg(np);
-        const float4 *q = pd + 4 * j;
-        const float4 hj = __ldg(q + PD_HI);
-        const float4 lj = __ldg(q + PD_LO);
-        const float4 aj = __ldg(q + PD_AUX);
-        const float4 uj = __ldg(q + PD_VEL);
+        const unsigned e = __ldg(np);
+        const int j = (int)(e & NBR_IDX_MASK);
+        const float4 oj = __ldg(posv + j);
+        const float4 uj = __ldg(velp + j);
         float rx, ry, rz;
-        const float r2 = pair_vec<DIM>(hi, lo, hj, lj, rx, ry, rz);
-        const bool oj = hj.w < 0.f;
+        const float r2 = pair_vec<DIM>(oi, oj, entry_shift(e, 0, cs), entry_shift(e, 1, cs),
+                                       DIM == 3 ? entry_shift(e, 2, cs) : 0.f, rx, ry, rz);
+        const bool oil_j = oj.w < 0.f;
+        const float vol_j = fabsf(oj.w);
         // beyond the support (list entries in the skin) t clamps to 0 and
         // every pair term below vanishes
         const float r = r2 * rsqrtf(fmaxf(r2, 1e-30f));
         const float t = fmaxf(fmaf(-0.5f * inv_h, r, 1.f), 0.f);
         const float t3 = t * t * t;
-        const float pt = (oj ? m_oil : m_wat) * (ai.y + aj.y) * t3;
+        const float pt = (oil_j ? m_oil : m_wat) * (ui.w + uj.w) * t3;
         px = fmaf(pt, rx, px);
         py = fmaf(pt, ry, py);
         if (DIM == 3) pz = fmaf(pt, rz, pz);
         const float ux = ui.x - uj.x, uy = ui.y - uj.y, uz = DIM == 3 ? ui.z - uj.z : 0.f;
-        const float vt = aj.x * t3;
-        const float s = (oj ? kv_oil : kv_wat) * vt * __fdividef(r2, r2 + ph.delta2);
+        const float vt = vol_j * t3;
+        const float s = (oil_j ? kv_oil : kv_wat) * vt * __fdividef(r2, r2 + ph.delta2);
         vx = fmaf(s, ux, vx);
         vy = fmaf(s, uy, vy);
         if (DIM == 3) vz = fmaf(s, uz, vz);
@@ -563,7 +564,7 @@ __global__ void __launch_bounds__(256) k_sweep_b(Dev d, Phys ph)
         ur = fmaf(uy, ry, ur);
         if (DIM == 3) ur = fmaf(uz, rz, ur);
         dv = fmaf(vt, ur, dv);
-        if (ai.z + aj.z > 0.f) {
+        if ((iface_i | (__float_as_uint(oj.w) & 1u)) != 0u) {
             const float4 Tj = __ldg(T4 + j);
             if (DIM == 2) {
                 const float xx = Ti.x + Tj.x, xy = Ti.y + Tj.y, yy = Ti.z + Tj.z;
@@ -579,14 +580,14 @@ __global__ void __launch_bounds__(256) k_sweep_b(Dev d, Phys ph)
             }
         }
     }
-    const float rho = ph.rho0[phi_] + d.drho_eval[i];
+    const float rho = by_phase(phi_, ph.rho0) + d.drho_eval[i];
     float4 out;
     out.w = rho * ph.cF * dv;
     if (d.tag[i] & 2) {
         out.x = out.y = out.z = 0.f;
     } else {
         const float vf = ph.visc_dynamic ? ph.cF / rho : ph.cF;
-        const float sf = ph.cF * ph.inv_mass[phi_];
+        const float sf = ph.cF * by_phase(phi_, ph.inv_mass);
         out.x = -ph.cF * px + vf * vx + sf * sx + ph.gf[0];
         out.y = -ph.cF * py + vf * vy + sf * sy + ph.gf[1];
         out.z = DIM == 3 ? -ph.cF * pz + vf * vz + sf * sz + ph.gf[2] : 0.f;
@@ -624,14 +625,12 @@ __global__ void __launch_bounds__(256) k_predict(Dev d, Grid g, Phys ph, double 
     // the neighbour list of the step stays complete while no particle moves
     // farther than the skin
     if (disp2 > ph.skin * ph.skin) atomicOr(d.flags, FLAG_SKIN);
-    float4 hi, lo;
-    split_position<DIM>(g, xs, hi, lo);
+    float4 p = cell_offset<DIM>(g, d.cell[k], xs);
     float vol;
-    hi.w = signed_volume(ph, tg & 1, drs, vol);
-    lo.w = vol * drs;
-    d.pd[4 * k + PD_HI] = hi;
-    d.pd[4 * k + PD_LO] = lo;
-    d.pd[4 * k + PD_VEL] = make_float4((float)us[0], (float)us[1], (float)us[2], 0.f);
+    p.w = signed_volume(ph, tg & 1, drs, vol);
+    d.pos[k] = p;
+    d.vd[k] = vol * drs;
+    d.velp[k] = make_float4((float)us[0], (float)us[1], (float)us[2], 0.f);
     if (!finite) atomicOr(d.flags, FLAG_NONFINITE);
 }
 
@@ -647,7 +646,7 @@ __global__ void __launch_bounds__(256) k_correct(Dev d, double dt)
     d.drho[k] = dr;
     bool finite = isfinite(dr);
     if (!(tg & 2)) {
-        const float4 us = d.pd[4 * k + PD_VEL];
+        const float4 us = d.velp[k];
         const double usa[3] = {us.x, us.y, us.z};
         const double af[3] = {a.x, a.y, a.z};
 #pragma unroll
@@ -670,12 +669,12 @@ __global__ void __launch_bounds__(256) k_nbr_count(Dev d, Grid g, Phys ph, int *
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.n) return;
-    const float4 hi = d.pd[4 * i + PD_HI], lo = d.pd[4 * i + PD_LO];
+    const float4 oi = d.pos[i];
     int cx, cy, cz;
     cell_coords(g, d.cell[i], cx, cy, cz);
     int cnt = 0;
-    for_each_candidate<DIM>(g, d.cstart, d.pd, cx, cy, cz, hi, lo, ph.R2,
-                            [&](int j, const float4 &, const float4 &, float, float, float, float) { cnt += j != i; });
+    for_each_candidate<DIM>(g, d.cstart, d.pos, cx, cy, cz, oi, ph.R2,
+                            [&](int j, const float4 &, float, float, float, float, unsigned) { cnt += j != i; });
     count[i] = cnt;
 }
 
@@ -684,12 +683,12 @@ __global__ void __launch_bounds__(256) k_nbr_fill(Dev d, Grid g, Phys ph, const 
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.n) return;
-    const float4 hi = d.pd[4 * i + PD_HI], lo = d.pd[4 * i + PD_LO];
+    const float4 oi = d.pos[i];
     int cx, cy, cz;
     cell_coords(g, d.cell[i], cx, cy, cz);
     long long w = start[i];
-    for_each_candidate<DIM>(g, d.cstart, d.pd, cx, cy, cz, hi, lo, ph.R2,
-                            [&](int j, const float4 &, const float4 &, float, float, float, float) {
+    for_each_candidate<DIM>(g, d.cstart, d.pos, cx, cy, cz, oi, ph.R2,
+                            [&](int j, const float4 &, float, float, float, float, unsigned) {
                                 if (j != i) list[w++] = d.pid[j];
                             });
 }
@@ -701,14 +700,14 @@ __global__ void __launch_bounds__(256) k_pair_stats(Dev d, Grid g, Phys ph, unsi
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     int all = 0, other = 0;
     if (i < d.n) {
-        const float4 hi = d.pd[4 * i + PD_HI], lo = d.pd[4 * i + PD_LO];
-        const int phi_ = phase_of(hi.w);
+        const float4 oi = d.pos[i];
+        const int phi_ = phase_of(oi.w);
         int cx, cy, cz;
         cell_coords(g, d.cell[i], cx, cy, cz);
-        for_each_candidate<DIM>(g, d.cstart, d.pd, cx, cy, cz, hi, lo, ph.R2,
-                                [&](int j, const float4 &hj, const float4 &, float, float, float, float) {
+        for_each_candidate<DIM>(g, d.cstart, d.pos, cx, cy, cz, oi, ph.R2,
+                                [&](int j, const float4 &oj, float, float, float, float, unsigned) {
                                     all += j != i;
-                                    other += phase_of(hj.w) != phi_;
+                                    other += phase_of(oj.w) != phi_;
                                 });
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -742,13 +741,13 @@ __global__ void __launch_bounds__(256) k_unpermute(Dev d, Phys ph, int kind, dou
         for (int c = 0; c < DIM; ++c) out[(size_t)p * DIM + c] = d.u[(size_t)c * n + k];
         break;
     case RK_RHO:
-        out[p] = (double)ph.rho0[phs] + (double)d.drho[k];
+        out[p] = (double)by_phase(phs, ph.rho0) + (double)d.drho[k];
         break;
     case RK_RHO_EVAL:
-        out[p] = (double)ph.rho0[phs] + (double)d.drho_eval[k];
+        out[p] = (double)by_phase(phs, ph.rho0) + (double)d.drho_eval[k];
         break;
     case RK_P:
-        out[p] = d.pd[4 * k + PD_AUX].w;
+        out[p] = d.pres[k];
         break;
     case RK_ACC: {
         const float4 a = d.acc[k];
@@ -761,7 +760,9 @@ __global__ void __launch_bounds__(256) k_unpermute(Dev d, Phys ph, int kind, dou
         break;
     case RK_T: {
         const float4 t = d.T4[k];
-        const double v2 = (double)d.pd[4 * k + PD_AUX].x * (double)d.pd[4 * k + PD_AUX].x;
+        // T sigma^-2 was formed with V = m/rho of the renormalised density
+        const double v = (double)(by_phase(phs, ph.mass) / (by_phase(phs, ph.rho0) + d.drho_eval[k]));
+        const double v2 = v * v;
         double T[9];
         if (DIM == 2) {
             T[0] = t.x; T[1] = t.y; T[2] = t.y; T[3] = t.z;
