@@ -209,7 +209,7 @@ static int cmp_i32(const void *a, const void *b)
 }
 
 /* Same sets through a cell list: particles sorted by cell, every i scans the
- * 3^dim cells around its own.  Requires cell_size >= 2h.                   */
+ * cells within w = ceil(2h / cell_size) of its own on each axis.           */
 int64_t or_neighbours_cells(const or_params *p, int64_t n, const double *x,
                             int64_t *start, int32_t *list, int64_t cap)
 {
@@ -229,6 +229,8 @@ int64_t or_neighbours_cells(const or_params *p, int64_t n, const double *x,
     for (int64_t c = 0; c < ncell; ++c) cstart[c + 1] += cstart[c];
     double R2 = 4.0 * p->h * p->h;
     int dim = p->dim;
+    const int w = (int)ceil(2.0 * p->h / p->cell_size);
+    const int wz = dim == 3 ? w : 0;
 
     /* pass 1: counts */
 #pragma omp parallel for schedule(dynamic, 256)
@@ -236,9 +238,9 @@ int64_t or_neighbours_cells(const or_params *p, int64_t n, const double *x,
         int32_t ci = cell[i];
         int32_t cx = ci % dims[0], cy = (ci / dims[0]) % dims[1], cz = ci / (dims[0] * dims[1]);
         int64_t cnt = 0;
-        for (int dz = (dim == 3 ? -1 : 0); dz <= (dim == 3 ? 1 : 0); ++dz)
-            for (int dy = -1; dy <= 1; ++dy)
-                for (int dx = -1; dx <= 1; ++dx) {
+        for (int dz = -wz; dz <= wz; ++dz)
+            for (int dy = -w; dy <= w; ++dy)
+                for (int dx = -w; dx <= w; ++dx) {
                     int32_t X = cx + dx, Y = cy + dy, Z = cz + dz;
                     if (X < 0 || Y < 0 || Z < 0 || X >= dims[0] || Y >= dims[1] || Z >= dims[2]) continue;
                     int64_t c = X + (int64_t)dims[0] * (Y + (int64_t)dims[1] * Z);
@@ -261,16 +263,16 @@ int64_t or_neighbours_cells(const or_params *p, int64_t n, const double *x,
     for (int64_t i = 0; i < n; ++i) {
         int32_t ci = cell[i];
         int32_t cx = ci % dims[0], cy = (ci / dims[0]) % dims[1], cz = ci / (dims[0] * dims[1]);
-        int64_t w = start[i];
-        for (int dz = (dim == 3 ? -1 : 0); dz <= (dim == 3 ? 1 : 0); ++dz)
-            for (int dy = -1; dy <= 1; ++dy)
-                for (int dx = -1; dx <= 1; ++dx) {
+        int64_t wr = start[i];
+        for (int dz = -wz; dz <= wz; ++dz)
+            for (int dy = -w; dy <= w; ++dy)
+                for (int dx = -w; dx <= w; ++dx) {
                     int32_t X = cx + dx, Y = cy + dy, Z = cz + dz;
                     if (X < 0 || Y < 0 || Z < 0 || X >= dims[0] || Y >= dims[1] || Z >= dims[2]) continue;
                     int64_t c = X + (int64_t)dims[0] * (Y + (int64_t)dims[1] * Z);
                     for (int64_t k = cstart[c]; k < cstart[c + 1]; ++k) {
                         int64_t j = perm[k];
-                        if (j != i && dist2(dim, x, i, j) < R2) list[w++] = (int32_t)j;
+                        if (j != i && dist2(dim, x, i, j) < R2) list[wr++] = (int32_t)j;
                     }
                 }
         qsort(list + start[i], (size_t)(start[i + 1] - start[i]), sizeof(int32_t), cmp_i32);
