@@ -80,10 +80,11 @@ typedef struct sph_params {
     double gamma;          /* exponent of Eq. state; must be 7 (the paper's value) */
     double delta;          /* regulariser of the viscous term (the paper uses 0.1 h) */
     double alpha_s;        /* interfacial surface tension coefficient (Eq. csf) */
-    double cell_size;      /* cell edge of the neighbour grid, >= 2h; the list of
-                              each step holds the pairs closer than cell_size, and
-                              the excess (cell_size - 2h)/2 is the displacement
-                              skin within which that list serves both stages */
+    double cell_size;      /* edge of the cell grid used for hashing, sorting and the
+                              neighbour search; >= h + skin (half the list radius) */
+    double skin;           /* the neighbour list of a step holds the pairs closer
+                              than 2h + 2 skin, so it serves both stages while no
+                              particle moves farther than skin in a half step */
     double g[3];           /* gravitational acceleration */
     double rho0[2];        /* reference density per phase: [0] water, [1] oil */
     double mu[2];          /* dynamic viscosity per phase */

@@ -248,8 +248,9 @@ int validate(const sph_params *P, int64_t n)
     if (P->gamma != 7.0) return fail(SPH_EINVAL, "gamma must be 7 (the exponent of the paper's equation of state)");
     if (!(P->delta >= 0)) return fail(SPH_EINVAL, "delta must be >= 0");
     if (!(P->alpha_s >= 0)) return fail(SPH_EINVAL, "alpha_s must be >= 0");
-    if (!(P->cell_size >= 2 * P->h) || !std::isfinite(P->cell_size))
-        return fail(SPH_EINVAL, "cell_size must be >= 2h");
+    if (!(P->skin >= 0) || !std::isfinite(P->skin)) return fail(SPH_EINVAL, "skin must be >= 0");
+    if (!(P->cell_size >= P->h + P->skin) || !std::isfinite(P->cell_size))
+        return fail(SPH_EINVAL, "cell_size must be >= h + skin (half the list radius 2h + 2 skin)");
     for (int k = 0; k < 2; ++k) {
         if (!(P->rho0[k] > 0)) return fail(SPH_EINVAL, "rho0 must be positive");
         if (!(P->mass[k] > 0)) return fail(SPH_EINVAL, "mass must be positive");
@@ -342,8 +343,12 @@ int sph_create(const sph_params *params, int64_t n, const double *x, const doubl
     s->grid.nx = dims[0];
     s->grid.ny = dims[1];
     s->grid.nz = dims[2];
+    const double RL = 2.0 * P.h + 2.0 * P.skin;
+    s->grid.f = P.cell_size >= RL ? 1 : 2;
     s->grid.csd = P.cell_size;
     s->grid.cs = (float)P.cell_size;
+    s->grid.Ed = s->grid.f * P.cell_size;
+    s->grid.Es = (float)s->grid.Ed;
     for (int c = 0; c < 3; ++c) s->grid.lo[c] = c < dim ? P.box_lo[c] : 0.0;
     // physics constants
     const double pi = 3.14159265358979323846;
@@ -352,8 +357,9 @@ int sph_create(const sph_params *params, int64_t n, const double *x, const doubl
     Phys &ph = s->phys;
     ph.inv_h = (float)(1.0 / h);
     ph.R2 = (float)(4.0 * h * h);
-    ph.RL2 = (float)(P.cell_size * P.cell_size);
-    ph.skin = 0.5 * (P.cell_size - 2.0 * h);
+    ph.RL2 = (float)(RL * RL);
+    ph.RP = (float)(RL * (1.0 + 1e-4));
+    ph.skin = P.skin;
     ph.kmax = P.max_neighbours > 0 ? P.max_neighbours : (dim == 2 ? 48 : 128);
     ph.cF = (float)(-5.0 * alpha_d / (h * h));
     for (int k = 0; k < 2; ++k) {

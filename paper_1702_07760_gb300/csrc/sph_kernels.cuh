@@ -5,16 +5,18 @@
 //   * particles live in cell order (stable by original id), structure of
 //     arrays;
 //   * a position used by the interaction sweeps is the particle's cell (an
-//     integer index of the cell grid) plus an FP32 offset from the cell
-//     centre; a pair vector is (o_i - o_j) + (c_i - c_j) * cell edge, the
-//     cell difference (-1, 0 or 1 per axis) being packed into the pair's
-//     neighbour-list entry;
+//     integer index of the cell grid) plus an FP32 offset from the centre of
+//     its super-cell (a block of f x f x f cells whose edge E = f * cell edge
+//     is at least the list radius); a pair vector is
+//     (o_i - o_j) + (S_i - S_j) * E, the super-cell difference (-1, 0 or 1
+//     per axis) being packed into the pair's neighbour-list entry;
 //   * the FP64 position and velocity are the integration accumulators;
 //   * density is stored as the deviation drho = rho - rho0(phase) in FP32, so
 //     the equation of state and the renormalisation never subtract two
 //     numbers near rho0;
-//   * once per step a neighbour list (radius = cell edge = 2h + 2 skin) is
-//     built from the cell list and stored column-major, so the four
+//   * once per step a neighbour list (radius 2h + 2 skin) is built from the
+//     cell list, scanning per particle only the cells of the +/-f stencil that
+//     the radius can reach, and stored column-major, so the four
 //     interaction sweeps of the step read it coalesced and run without the
 //     branch divergence of a candidate scan; a sweep gathers two 16-byte
 //     records per neighbour.
@@ -36,7 +38,8 @@ enum : unsigned {
 struct Phys {
     float inv_h;        // 1/h
     float R2;           // (2h)^2, support test
-    float RL2;          // list radius^2 = cell edge^2
+    float RL2;          // list radius^2, (2h + 2 skin)^2
+    float RP;           // list radius widened by 1e-4 (conservative stencil pruning)
     float cF;           // -5 alpha_d / h^2: grad W_ij = cF (1-q/2)^3 r_ij
     float mass[2];      // per-phase particle mass
     float inv_mass[2];
@@ -51,13 +54,16 @@ struct Phys {
     int visc_dynamic;   // 1: Eq. visc_2 (factor 1/rho_i), 0: Eq. visc_1
     int renorm_every;   // Eq. ct_dist_3 at stage 1 of steps with step % renorm_every == 0
     int kmax;           // neighbour-list capacity per particle
-    double skin;        // (cell edge - 2h) / 2: allowed predictor displacement
+    double skin;        // allowed predictor displacement (the list's margin)
 };
 
 struct Grid {
     int nx, ny, nz;     // cells per axis (nz = 1 in 2-D)
-    float cs;           // cell edge (FP32): pair vectors
-    double csd;         // cell edge (FP64): hashing and offsets
+    int f;              // cells per super-cell edge: 1 or 2 (also the stencil half-width)
+    float cs;           // cell edge (FP32)
+    float Es;           // super-cell edge (FP32): pair vectors
+    double csd;         // cell edge (FP64): hashing
+    double Ed;          // super-cell edge (FP64): offsets
     double lo[3];       // box lower corner
 };
 
@@ -72,7 +78,7 @@ struct Dev {
     uint8_t *tag;       // n, bit0 oil, bit1 wall
     int *cell;          // n, cell id (sorted order)
     // stage arrays
-    float4 *pos;        // n, (offset from the cell centre xyz, +/- m/rho of the stage input; sign = phase)
+    float4 *pos;        // n, (offset from the super-cell centre xyz, +/- m/rho of the stage input; sign = phase)
     float *vd;          // n, (m/rho) * drho of the stage input
     float4 *posv;       // n, (offset xyz, +/- m/rho after renormalisation with its lowest
                         //     mantissa bit replaced by the interface flag): sweep A output
@@ -94,7 +100,7 @@ struct Dev {
 };
 
 // Neighbour-list entry: particle index in the low 26 bits; per axis a, two
-// bits at 26 + 2a holding (c_i - c_j) + 1 in {0, 1, 2}.
+// bits at 26 + 2a holding (S_i - S_j) + 1 in {0, 1, 2} (super-cells).
 constexpr int NBR_IDX_BITS = 26;
 constexpr unsigned NBR_IDX_MASK = (1u << NBR_IDX_BITS) - 1u;
 
@@ -104,15 +110,15 @@ __device__ __forceinline__ int phase_of(float w) { return __float_as_uint(w) >> 
 // indexed parameter load would go through the constant cache per thread).
 __device__ __forceinline__ float by_phase(int phase, const float (&a)[2]) { return phase ? a[1] : a[0]; }
 
-// (c_i - c_j) * cs for axis a of an entry, exact: the code e in {0, 1, 2}
+// (S_i - S_j) * E for axis a of an entry, exact: the code e in {0, 1, 2}
 // becomes the float e - 1 through the 2^23 + 2^22 mantissa trick.
-__device__ __forceinline__ float entry_shift(unsigned e, int a, float cs)
+__device__ __forceinline__ float entry_shift(unsigned e, int a, float E)
 {
     const unsigned code = (e >> (NBR_IDX_BITS + 2 * a)) & 3u;
-    return (__uint_as_float(0x4B400000u | code) - 12582913.f) * cs;
+    return (__uint_as_float(0x4B400000u | code) - 12582913.f) * E;
 }
 
-// r_ij = x_i - x_j from cell offsets and the cell-centre difference (s).
+// r_ij = x_i - x_j from super-cell offsets and the centre difference (s).
 template <int DIM>
 __device__ __forceinline__ float pair_vec(const float4 &oi, const float4 &oj, float sx, float sy, float sz,
                                           float &rx, float &ry, float &rz)
@@ -134,38 +140,68 @@ __device__ __forceinline__ void cell_coords(const Grid &g, int c, int &cx, int &
     cz = r / g.ny;
 }
 
-// Scans every particle of the 3^DIM cells around cell (cx, cy, cz) and calls
+// Gap along one axis between a particle at p (from its cell's lower corner)
+// and the cell d cells away: 0 for d = 0.
+__device__ __forceinline__ float axis_gap(float p, int d, float e)
+{
+    return d > 0 ? (float)d * e - p : (d < 0 ? p - (float)(d + 1) * e : 0.f);
+}
+
+// Scans the particles of the cells within +/-f of cell c that a sphere of
+// radius Rp around the particle can reach (pruned per row), and calls
 // f(j, oj, rx, ry, rz, r2, code) for those with |r_ij|^2 < R2 (j == i
 // included); code is the shift part of a neighbour-list entry.
 template <int DIM, class F>
 __device__ __forceinline__ void for_each_candidate(const Grid &g, const int *__restrict__ cstart,
-                                                   const float4 *__restrict__ pos, int cx, int cy, int cz,
-                                                   const float4 &oi, float R2, F &&f)
+                                                   const float4 *__restrict__ pos, int c, const float4 &oi,
+                                                   float R2, float Rp, F &&fn)
 {
-    const int z0 = DIM == 3 ? max(cz - 1, 0) : 0;
-    const int z1 = DIM == 3 ? min(cz + 1, g.nz - 1) : 0;
-    const int y0 = max(cy - 1, 0), y1 = min(cy + 1, g.ny - 1);
-    const int x0 = max(cx - 1, 0), x1 = min(cx + 1, g.nx - 1);
-    const float cs = g.cs;
+    int cx, cy, cz;
+    cell_coords(g, c, cx, cy, cz);
+    const int fm = g.f - 1, hw = g.f;
+    const int Sx = cx >> fm, Sy = cy >> fm, Sz = cz >> fm;
+    const float e = g.cs, E = g.Es;
+    // position inside the cell from its lower corner: the super-cell centre
+    // lies e/2 above the corner for f = 1, and e above (even cell) or at the
+    // corner (odd cell) for f = 2
+    const float px = oi.x + (hw == 1 ? 0.5f * e : ((cx & 1) ? 0.f : e));
+    const float py = oi.y + (hw == 1 ? 0.5f * e : ((cy & 1) ? 0.f : e));
+    const float pz = DIM == 3 ? oi.z + (hw == 1 ? 0.5f * e : ((cz & 1) ? 0.f : e)) : 0.f;
+    const float Rp2 = Rp * Rp;
+    const int z0 = DIM == 3 ? max(cz - hw, 0) : 0, z1 = DIM == 3 ? min(cz + hw, g.nz - 1) : 0;
+    const int y0 = max(cy - hw, 0), y1 = min(cy + hw, g.ny - 1);
     for (int z = z0; z <= z1; ++z) {
-        const float sz = (float)(cz - z) * cs;
+        const float gz = DIM == 3 ? axis_gap(pz, z - cz, e) : 0.f;
+        if (gz >= Rp) continue;
+        const int dSz = DIM == 3 ? Sz - (z >> fm) : 0;
+        const float sz = (float)dSz * E;
         for (int y = y0; y <= y1; ++y) {
-            const float sy = (float)(cy - y) * cs;
-            // the cells x0..x1 of a row are contiguous in the sorted order
+            const float gy = axis_gap(py, y - cy, e);
+            const float rem = Rp2 - gy * gy - gz * gz;
+            if (rem <= 0.f) continue;
+            const int dSy = Sy - (y >> fm);
+            const float sy = (float)dSy * E;
+            const float xr = sqrtf(rem);
+            const int xlo = max(max(cx + (int)floorf((px - xr) / e), cx - hw), 0);
+            const int xhi = min(min(cx + (int)floorf((px + xr) / e), cx + hw), g.nx - 1);
+            if (xlo > xhi) continue;
+            // the cells xlo..xhi of a row are contiguous in the sorted order
             const int row = (z * g.ny + y) * g.nx;
-            const int jb = __ldg(cstart + row + x0), je = __ldg(cstart + row + x1 + 1);
-            const int b1 = __ldg(cstart + row + cx), b2 = __ldg(cstart + row + cx + 1);
-            const unsigned cyz = ((unsigned)(cy - y + 1) << (NBR_IDX_BITS + 2)) |
-                                 ((unsigned)(DIM == 3 ? cz - z + 1 : 1) << (NBR_IDX_BITS + 4));
+            const int jb = __ldg(cstart + row + xlo), je = __ldg(cstart + row + xhi + 1);
+            // super-cell Sx covers cells [Sx*f, Sx*f + f)
+            const int b1 = __ldg(cstart + row + min(max(Sx * hw, xlo), xhi + 1));
+            const int b2 = __ldg(cstart + row + min(max(Sx * hw + hw, xlo), xhi + 1));
+            const unsigned cyz = ((unsigned)(dSy + 1) << (NBR_IDX_BITS + 2)) |
+                                 ((unsigned)(dSz + 1) << (NBR_IDX_BITS + 4));
 #pragma unroll 4
             for (int j = jb; j < je; ++j) {
                 const float4 oj = __ldg(pos + j);
-                // x cell of j: cx - 1, cx or cx + 1
-                const float sx = j < b1 ? cs : (j < b2 ? 0.f : -cs);
+                // super-cell of j along x: Sx - 1, Sx or Sx + 1
+                const float sx = j < b1 ? E : (j < b2 ? 0.f : -E);
                 const unsigned ex = j < b1 ? 2u : (j < b2 ? 1u : 0u);
                 float rx, ry, rz;
                 const float r2 = pair_vec<DIM>(oi, oj, sx, sy, sz, rx, ry, rz);
-                if (r2 < R2) f(j, oj, rx, ry, rz, r2, cyz | (ex << NBR_IDX_BITS));
+                if (r2 < R2) fn(j, oj, rx, ry, rz, r2, cyz | (ex << NBR_IDX_BITS));
             }
         }
     }
@@ -194,15 +230,16 @@ __device__ __forceinline__ float eos_tait7(float beta, float eps)
     return beta * eps * p;
 }
 
-// FP32 offset of an FP64 position from the centre of cell c.
+// FP32 offset of an FP64 position from the centre of the super-cell of cell c.
 template <int DIM>
 __device__ __forceinline__ float4 cell_offset(const Grid &g, int c, const double xa[3])
 {
     int cc[3];
     cell_coords(g, c, cc[0], cc[1], cc[2]);
+    const int fm = g.f - 1;
     float o[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-    for (int a = 0; a < DIM; ++a) o[a] = (float)(xa[a] - (g.lo[a] + ((double)cc[a] + 0.5) * g.csd));
+    for (int a = 0; a < DIM; ++a) o[a] = (float)(xa[a] - (g.lo[a] + ((double)(cc[a] >> fm) + 0.5) * g.Ed));
     return make_float4(o[0], o[1], o[2], 0.f);
 }
 
@@ -384,19 +421,17 @@ __global__ void __launch_bounds__(256) k_gather(Dev src, Dev dst, Grid g, Phys p
 // positions of the build, so the list stays complete while no particle moves
 // farther than the skin.
 template <int DIM>
-__global__ void __launch_bounds__(256) k_build_list(Dev d, Grid g, Phys ph)
+__global__ void __launch_bounds__(256, 4) k_build_list(Dev d, Grid g, Phys ph)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.n) return;
     const float4 oi = d.pos[i];
     const int phi_ = phase_of(oi.w);
-    int cx, cy, cz;
-    cell_coords(g, d.cell[i], cx, cy, cz);
     int cnt = 0;
     int other = 0;
     const int n = d.n, kmax = ph.kmax;
     unsigned *__restrict__ nbr = d.nbr;
-    for_each_candidate<DIM>(g, d.cstart, d.pos, cx, cy, cz, oi, ph.RL2,
+    for_each_candidate<DIM>(g, d.cstart, d.pos, d.cell[i], oi, ph.RL2, ph.RP,
         [&](int j, const float4 &oj, float, float, float, float, unsigned code) {
             if (j == i) return;
             if (cnt < kmax) nbr[(size_t)cnt * n + i] = (unsigned)j | code;
@@ -434,7 +469,7 @@ __global__ void __launch_bounds__(256) k_sweep_a(Dev d, Grid g, Phys ph, const f
     float gx = 0.f, gy = 0.f, gz = 0.f;
     const bool other = d.nflag[i] & 1;
     if (renorm || other) {
-        const float inv_h = ph.inv_h, cs = g.cs;
+        const float inv_h = ph.inv_h, cs = g.Es;
         const int n = d.n, cnt = d.ncnt[i];
         const unsigned *__restrict__ np = d.nbr + i;
         const float4 *__restrict__ pos = d.pos;
@@ -510,7 +545,7 @@ __global__ void __launch_bounds__(256) k_sweep_a(Dev d, Grid g, Phys ph, const f
 // (Eq. ct_dist_2).  grad_i W_ij = cF t^3 r_ij with t = 1 - q/2; the common
 // factor cF is applied once per particle.
 template <int DIM>
-__global__ void __launch_bounds__(256) k_sweep_b(Dev d, Grid g, Phys ph)
+__global__ void __launch_bounds__(256, 4) k_sweep_b(Dev d, Grid g, Phys ph)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.n) return;
@@ -524,7 +559,7 @@ __global__ void __launch_bounds__(256) k_sweep_b(Dev d, Grid g, Phys ph)
     float vx = 0.f, vy = 0.f, vz = 0.f;    // sum k_ij V_j t^3 r^2/(r^2+delta^2) u_ij
     float sx = 0.f, sy = 0.f, sz = 0.f;    // sum (T_i/sigma_i^2 + T_j/sigma_j^2) . t^3 r_ij
     float dv = 0.f;                        // sum V_j t^3 u_ij . r_ij
-    const float inv_h = ph.inv_h, cs = g.cs;
+    const float inv_h = ph.inv_h, cs = g.Es;
     const int n = d.n, cnt = d.ncnt[i];
     // per-phase constants of the pair terms as registers (selected per pair)
     const float m_wat = ph.mass[0], m_oil = ph.mass[1];
@@ -534,7 +569,7 @@ __global__ void __launch_bounds__(256) k_sweep_b(Dev d, Grid g, Phys ph)
     const float4 *__restrict__ velp = d.velp;
     const float4 *__restrict__ T4 = d.T4;
     const float2 *__restrict__ T2 = d.T2;
-#pragma unroll (DIM == 3 ? 4 : 8)
+#pragma unroll 4
     for (int k = 0; k < cnt; ++k, np += n) {
         const unsigned e = __ldg(np);
         const int j = (int)(e & NBR_IDX_MASK);
@@ -670,10 +705,8 @@ __global__ void __launch_bounds__(256) k_nbr_count(Dev d, Grid g, Phys ph, int *
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.n) return;
     const float4 oi = d.pos[i];
-    int cx, cy, cz;
-    cell_coords(g, d.cell[i], cx, cy, cz);
     int cnt = 0;
-    for_each_candidate<DIM>(g, d.cstart, d.pos, cx, cy, cz, oi, ph.R2,
+    for_each_candidate<DIM>(g, d.cstart, d.pos, d.cell[i], oi, ph.R2, ph.RP,
                             [&](int j, const float4 &, float, float, float, float, unsigned) { cnt += j != i; });
     count[i] = cnt;
 }
@@ -684,10 +717,8 @@ __global__ void __launch_bounds__(256) k_nbr_fill(Dev d, Grid g, Phys ph, const 
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.n) return;
     const float4 oi = d.pos[i];
-    int cx, cy, cz;
-    cell_coords(g, d.cell[i], cx, cy, cz);
     long long w = start[i];
-    for_each_candidate<DIM>(g, d.cstart, d.pos, cx, cy, cz, oi, ph.R2,
+    for_each_candidate<DIM>(g, d.cstart, d.pos, d.cell[i], oi, ph.R2, ph.RP,
                             [&](int j, const float4 &, float, float, float, float, unsigned) {
                                 if (j != i) list[w++] = d.pid[j];
                             });
@@ -702,9 +733,7 @@ __global__ void __launch_bounds__(256) k_pair_stats(Dev d, Grid g, Phys ph, unsi
     if (i < d.n) {
         const float4 oi = d.pos[i];
         const int phi_ = phase_of(oi.w);
-        int cx, cy, cz;
-        cell_coords(g, d.cell[i], cx, cy, cz);
-        for_each_candidate<DIM>(g, d.cstart, d.pos, cx, cy, cz, oi, ph.R2,
+        for_each_candidate<DIM>(g, d.cstart, d.pos, d.cell[i], oi, ph.R2, ph.RP,
                                 [&](int j, const float4 &oj, float, float, float, float, unsigned) {
                                     all += j != i;
                                     other += phase_of(oj.w) != phi_;

@@ -37,7 +37,7 @@ class SphParams(C.Structure):
     _fields_ = [
         ("dim", C.c_int32), ("visc_form", C.c_int32), ("renorm_every", C.c_int32),
         ("max_neighbours", C.c_int32), ("h", C.c_double), ("c0", C.c_double), ("gamma", C.c_double),
-        ("delta", C.c_double), ("alpha_s", C.c_double), ("cell_size", C.c_double),
+        ("delta", C.c_double), ("alpha_s", C.c_double), ("cell_size", C.c_double), ("skin", C.c_double),
         ("g", C.c_double * 3), ("rho0", C.c_double * 2), ("mu", C.c_double * 2),
         ("mass", C.c_double * 2), ("box_lo", C.c_double * 3), ("box_hi", C.c_double * 3),
     ]
@@ -87,7 +87,7 @@ def make_params(p: dict) -> SphParams:
     s.renorm_every = int(p.get("renorm_every", 1))
     s.max_neighbours = int(p.get("max_neighbours", 0))
     s.h, s.c0, s.gamma = p["h"], p["c0"], p.get("gamma", 7.0)
-    s.delta, s.alpha_s, s.cell_size = p["delta"], p["alpha_s"], p["cell_size"]
+    s.delta, s.alpha_s, s.cell_size, s.skin = p["delta"], p["alpha_s"], p["cell_size"], p["skin"]
     for k in range(3):
         s.g[k], s.box_lo[k], s.box_hi[k] = p["g"][k], p["box_lo"][k], p["box_hi"][k]
     for k in range(2):

@@ -61,23 +61,25 @@ class Workload:
 
 def fluid_params(dim: int, dx: float, depth: float, *, rho0=(1000.0, 900.0),
                  mu=(1e-3, 1e-2), alpha_s=0.02, g=9.81, h_over_dx=1.3,
-                 c0=None, visc_form=0, renorm_every=1, cell_factor=2.05) -> dict:
+                 c0=None, visc_form=0, renorm_every=1, skin_h=0.025, cell_h=None) -> dict:
     """Physical and numerical parameters of a drop-rise workload.
 
-    ``cell_factor`` sets the neighbour-search cell edge in units of h; it must
-    be at least 2 (the kernel support) and the excess is the displacement skin
-    that lets one cell list serve both stages of a step.
+    ``skin_h`` is the neighbour-list margin in units of h (the list holds pairs
+    closer than 2h + 2 skin); ``cell_h`` is the hashing-cell edge in units of
+    h, by default half the list radius, h + skin.
     """
     h = h_over_dx * dx
     if c0 is None:
         c0 = 10.0 * np.sqrt(2.0 * g * depth)
     grav = [0.0, 0.0, 0.0]
     grav[dim - 1] = -g
+    skin = skin_h * h
+    cell = (cell_h * h) if cell_h is not None else h + skin
     return dict(
         dim=dim, dx=dx, h=h, c0=float(c0), gamma=7.0, delta=0.1 * h,
         alpha_s=float(alpha_s), g=grav, rho0=list(map(float, rho0)), mu=list(map(float, mu)),
         mass=[float(r) * dx ** dim for r in rho0], visc_form=int(visc_form),
-        renorm_every=int(renorm_every), cell_size=cell_factor * h, depth=depth,
+        renorm_every=int(renorm_every), cell_size=cell, skin=skin, depth=depth,
         box_lo=[0.0, 0.0, 0.0], box_hi=[0.0, 0.0, 0.0],
     )
 
