@@ -73,8 +73,12 @@ typedef struct sph_params {
     int32_t dim;           /* 2 or 3 */
     int32_t visc_form;     /* SPH_VISC_DYNAMIC or SPH_VISC_KINEMATIC */
     int32_t renorm_every;  /* Eq. ct_dist_3 at stage 1 of steps with step % renorm_every == 0; 0 = never */
-    int32_t max_neighbours;/* capacity of the per-particle neighbour list (pairs within
-                              cell_size); 0 selects 48 in 2-D and 128 in 3-D */
+    int32_t max_neighbours;/* capacity of the per-particle neighbour list (pairs closer
+                              than 2h + 2 skin); 0 selects 48 in 2-D and 128 in 3-D */
+    int32_t rebuild_every; /* 0: the cell and neighbour lists are rebuilt when a particle
+                              may move farther than skin from where it was at the last
+                              build; k > 0: rebuilt every k steps */
+    int32_t reserved;      /* must be 0 */
     double h;              /* smoothing length; the Wendland C2 kernel has support 2h */
     double c0;             /* reference speed of sound C_s0 (Eq. beta) */
     double gamma;          /* exponent of Eq. state; must be 7 (the paper's value) */
@@ -82,9 +86,9 @@ typedef struct sph_params {
     double alpha_s;        /* interfacial surface tension coefficient (Eq. csf) */
     double cell_size;      /* edge of the cell grid used for hashing, sorting and the
                               neighbour search; >= h + skin (half the list radius) */
-    double skin;           /* the neighbour list of a step holds the pairs closer
-                              than 2h + 2 skin, so it serves both stages while no
-                              particle moves farther than skin in a half step */
+    double skin;           /* the neighbour list holds the pairs closer than 2h + 2 skin,
+                              so it stays complete while no particle has moved farther
+                              than skin since the list was built */
     double g[3];           /* gravitational acceleration */
     double rho0[2];        /* reference density per phase: [0] water, [1] oil */
     double mu[2];          /* dynamic viscosity per phase */
@@ -169,6 +173,10 @@ int sph_timing_enable(sph_handle h, int enable);
 int sph_timing_reset(sph_handle h);
 int sph_timing_count(void);
 int sph_timing_read(sph_handle h, int k, const char **name, int64_t *launches, double *total_ms);
+
+/* Number of cell and neighbour-list builds performed so far (waits for the
+ * stream), or a negative error code. */
+int64_t sph_list_builds(sph_handle h);
 
 /* Number of particles, step counter, grid cells. */
 int64_t sph_num_particles(sph_handle h);

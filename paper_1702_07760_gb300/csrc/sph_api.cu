@@ -33,12 +33,12 @@ int fail(int code, const std::string &msg)
     } while (0)
 
 enum KernelId {
-    KI_MEMSET, KI_HASH, KI_SCAN, KI_SCATTER, KI_RANK, KI_GATHER, KI_LIST, KI_SWEEP_A, KI_SWEEP_B,
+    KI_MEMSET, KI_HASH, KI_SCAN, KI_SCATTER, KI_RANK, KI_GATHER, KI_COPY, KI_LIST, KI_SWEEP_A, KI_SWEEP_B,
     KI_PREDICT, KI_CORRECT, KI_COUNT
 };
 const char *k_names[KI_COUNT] = {"count_reset", "cell_hash", "cell_scan", "cell_scatter",
-                                 "cell_rank", "reorder_gather", "neighbour_list", "sweep_a", "sweep_b",
-                                 "predict", "correct"};
+                                 "cell_rank", "reorder_gather", "reorder_copy", "neighbour_list",
+                                 "sweep_a", "sweep_b", "predict", "correct"};
 
 struct PendingTiming {
     int id;
@@ -62,7 +62,10 @@ struct sph_sim {
     int *cell_tmp = nullptr, *slot = nullptr, *count = nullptr, *tmp = nullptr, *perm = nullptr,
         *tile_sums = nullptr;
     unsigned *flags = nullptr;
+    unsigned *rebuild = nullptr;
     long long *dstep = nullptr;
+    long long *dbuilds = nullptr;
+    double last_dt = 0.0;
     double *diag_partial = nullptr, *diag_small = nullptr;
     double *read_buf = nullptr;
     int *read_ibuf = nullptr;
@@ -74,7 +77,7 @@ struct sph_sim {
     std::vector<cudaEvent_t> free_events;
     int64_t t_launches[KI_COUNT] = {};
     double t_ms[KI_COUNT] = {};
-    // graph of two steps (gexec[0]), replayed while dt matches gdt[0]
+    // graph of one step (gexec[0]), replayed while dt matches gdt[0]
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     double gdt[2] = {0.0, 0.0};
 
@@ -134,42 +137,50 @@ struct sph_sim {
 
     int blocks(int work, int threads = 256) const { return (work + threads - 1) / threads; }
 
-    void enqueue_build_cells();
+    void enqueue_build_cells(bool force);
     void enqueue_eval(int stage1, const float *drho_in);
     void enqueue_step(double dt);
     int check_flags();
 };
 
-void sph_sim::enqueue_build_cells()
+// Cell hash, stable sort, reorder and neighbour list.  Every kernel returns
+// at once unless the device flag `rebuild` is set (by the corrector when a
+// particle may leave the skin, or here when force is true), so the same
+// launch sequence serves every step of a captured graph.
+void sph_sim::enqueue_build_cells(bool force)
 {
-    Dev &s = buf[cur];
-    Dev &t = buf[cur ^ 1];
-    launch(KI_MEMSET, [&] { cudaMemsetAsync(count, 0, sizeof(int) * (size_t)ncell, stream); });
+    Dev &s = buf[0];
+    Dev &t = buf[1];
+    if (force) cudaMemsetAsync(rebuild, 0xff, sizeof(unsigned), stream);
+    launch(KI_MEMSET, [&] { k_zero<<<blocks(ncell), 256, 0, stream>>>(count, ncell, rebuild); });
     launch(KI_HASH, [&] {
         if (dim == 2) k_hash<2><<<blocks(n), 256, 0, stream>>>(s, grid, cell_tmp, slot, count);
         else k_hash<3><<<blocks(n), 256, 0, stream>>>(s, grid, cell_tmp, slot, count);
     });
     launch(KI_SCAN, [&] {
-        k_scan_tiles<<<ntiles, SCAN_THREADS, 0, stream>>>(count, s.cstart, tile_sums, ncell);
-        k_scan_sums<<<1, SCAN_THREADS, 0, stream>>>(tile_sums, ntiles, s.cstart, ncell);
-        k_scan_add<<<blocks(ncell), 256, 0, stream>>>(s.cstart, tile_sums, ncell);
+        k_scan_tiles<<<ntiles, SCAN_THREADS, 0, stream>>>(count, s.cstart, tile_sums, ncell, rebuild);
+        k_scan_sums<<<1, SCAN_THREADS, 0, stream>>>(tile_sums, ntiles, s.cstart, ncell, rebuild);
+        k_scan_add<<<blocks(ncell), 256, 0, stream>>>(s.cstart, tile_sums, ncell, rebuild);
     });
-    launch(KI_SCATTER, [&] { k_scatter<<<blocks(n), 256, 0, stream>>>(n, cell_tmp, slot, s.cstart, tmp); });
-    launch(KI_RANK, [&] { k_rank<<<blocks(n), 256, 0, stream>>>(n, tmp, cell_tmp, s.pid, s.cstart, perm); });
+    launch(KI_SCATTER, [&] { k_scatter<<<blocks(n), 256, 0, stream>>>(n, cell_tmp, slot, s.cstart, tmp, rebuild); });
+    launch(KI_RANK, [&] { k_rank<<<blocks(n), 256, 0, stream>>>(n, tmp, cell_tmp, s.pid, s.cstart, perm, rebuild); });
     launch(KI_GATHER, [&] {
         if (dim == 2) k_gather<2><<<blocks(n), 256, 0, stream>>>(s, t, grid, phys, perm, cell_tmp);
         else k_gather<3><<<blocks(n), 256, 0, stream>>>(s, t, grid, phys, perm, cell_tmp);
     });
-    launch(KI_LIST, [&] {
-        if (dim == 2) k_build_list<2><<<blocks(n), 256, 0, stream>>>(t, grid, phys);
-        else k_build_list<3><<<blocks(n), 256, 0, stream>>>(t, grid, phys);
+    launch(KI_COPY, [&] {
+        if (dim == 2) k_copy_back<2><<<blocks(n), 256, 0, stream>>>(t, s);
+        else k_copy_back<3><<<blocks(n), 256, 0, stream>>>(t, s);
     });
-    cur ^= 1;
+    launch(KI_LIST, [&] {
+        if (dim == 2) k_build_list<2><<<blocks(n), 256, 0, stream>>>(s, grid, phys);
+        else k_build_list<3><<<blocks(n), 256, 0, stream>>>(s, grid, phys);
+    });
 }
 
 void sph_sim::enqueue_eval(int stage1, const float *drho_in)
 {
-    Dev &d = buf[cur];
+    Dev &d = buf[0];
     launch(KI_SWEEP_A, [&] {
         if (dim == 2) k_sweep_a<2><<<blocks(n), 256, 0, stream>>>(d, grid, phys, drho_in, stage1);
         else k_sweep_a<3><<<blocks(n), 256, 0, stream>>>(d, grid, phys, drho_in, stage1);
@@ -182,8 +193,8 @@ void sph_sim::enqueue_eval(int stage1, const float *drho_in)
 
 void sph_sim::enqueue_step(double dt)
 {
-    enqueue_build_cells();
-    Dev &d = buf[cur];
+    enqueue_build_cells(false);
+    Dev &d = buf[0];
     enqueue_eval(1, d.drho);
     launch(KI_PREDICT, [&] {
         if (dim == 2) k_predict<2><<<blocks(n), 256, 0, stream>>>(d, grid, phys, dt);
@@ -191,8 +202,8 @@ void sph_sim::enqueue_step(double dt)
     });
     enqueue_eval(0, d.drho_stage);
     launch(KI_CORRECT, [&] {
-        if (dim == 2) k_correct<2><<<blocks(n), 256, 0, stream>>>(d, dt);
-        else k_correct<3><<<blocks(n), 256, 0, stream>>>(d, dt);
+        if (dim == 2) k_correct<2><<<blocks(n), 256, 0, stream>>>(d, grid, phys, dt);
+        else k_correct<3><<<blocks(n), 256, 0, stream>>>(d, grid, phys, dt);
     });
 }
 
@@ -243,6 +254,8 @@ int validate(const sph_params *P, int64_t n)
     if (P->renorm_every < 0) return fail(SPH_EINVAL, "renorm_every must be >= 0");
     if (P->max_neighbours < 0 || P->max_neighbours > 4096)
         return fail(SPH_EINVAL, "max_neighbours must be in [0, 4096]");
+    if (P->rebuild_every < 0) return fail(SPH_EINVAL, "rebuild_every must be >= 0");
+    if (P->reserved != 0) return fail(SPH_EINVAL, "reserved must be 0");
     if (!(P->h > 0) || !std::isfinite(P->h)) return fail(SPH_EINVAL, "h must be positive");
     if (!(P->c0 > 0) || !std::isfinite(P->c0)) return fail(SPH_EINVAL, "c0 must be positive");
     if (P->gamma != 7.0) return fail(SPH_EINVAL, "gamma must be 7 (the exponent of the paper's equation of state)");
@@ -381,6 +394,7 @@ int sph_create(const sph_params *params, int64_t n, const double *x, const doubl
     ph.inv_dim = (float)(1.0 / dim);
     ph.visc_dynamic = P.visc_form == SPH_VISC_DYNAMIC;
     ph.renorm_every = P.renorm_every;
+    ph.rebuild_every = P.rebuild_every;
     for (int c = 0; c < 3; ++c) ph.gf[c] = c < dim ? (float)P.g[c] : 0.f;
 
     auto cleanup = [&](int code) {
@@ -406,10 +420,11 @@ int sph_create(const sph_params *params, int64_t n, const double *x, const doubl
         err |= s->alloc(&d.drho, N);
         err |= s->alloc(&d.pid, N);
         err |= s->alloc(&d.tag, N);
-        err |= s->alloc(&d.cell, N);
     }
     Dev &a0 = s->buf[0];
     if (!err) {
+        err |= s->alloc(&a0.cell, N);
+        err |= s->alloc(&a0.pos0, N);
         err |= s->alloc(&a0.pos, N);
         err |= s->alloc(&a0.vd, N);
         err |= s->alloc(&a0.posv, N);
@@ -425,7 +440,9 @@ int sph_create(const sph_params *params, int64_t n, const double *x, const doubl
         err |= s->alloc(&a0.acc, N);
         err |= s->alloc(&a0.cstart, (size_t)ncell + 1);
         err |= s->alloc(&s->flags, 1);
+        err |= s->alloc(&s->rebuild, 1);
         err |= s->alloc(&s->dstep, 1);
+        err |= s->alloc(&s->dbuilds, 1);
         err |= s->alloc(&s->cell_tmp, N);
         err |= s->alloc(&s->slot, N);
         err |= s->alloc(&s->count, (size_t)ncell);
@@ -437,6 +454,7 @@ int sph_create(const sph_params *params, int64_t n, const double *x, const doubl
     }
     if (err) return cleanup(SPH_ENOMEM);
     Dev &a1 = s->buf[1];
+    a1.cell = a0.cell; a1.pos0 = a0.pos0;
     a1.pos = a0.pos; a1.vd = a0.vd; a1.posv = a0.posv; a1.velp = a0.velp; a1.pres = a0.pres;
     a1.drho_stage = a0.drho_stage;
     a1.nbr = a0.nbr; a1.ncnt = a0.ncnt; a1.nflag = a0.nflag;
@@ -444,12 +462,15 @@ int sph_create(const sph_params *params, int64_t n, const double *x, const doubl
     a1.cstart = a0.cstart;
     a0.flags = a1.flags = s->flags;
     a0.step = a1.step = s->dstep;
+    a0.rebuild = a1.rebuild = s->rebuild;
+    a0.builds = a1.builds = s->dbuilds;
 
     cudaStream_t st = s->stream;
     auto cuda_fail = [&](cudaError_t e) { return cleanup(fail(SPH_ECUDA, cudaGetErrorString(e))); };
     cudaError_t e = cudaMemsetAsync(s->flags, 0, sizeof(unsigned), st);
     if (e != cudaSuccess) return cuda_fail(e);
     if ((e = cudaMemsetAsync(s->dstep, 0, sizeof(long long), st)) != cudaSuccess) return cuda_fail(e);
+    if ((e = cudaMemsetAsync(s->dbuilds, 0, sizeof(long long), st)) != cudaSuccess) return cuda_fail(e);
     if (n > 0) {
         std::vector<uint8_t> tag((size_t)n);
         for (int64_t i = 0; i < n; ++i) tag[i] = (uint8_t)(phase[i] | (wall[i] << 1));
@@ -485,6 +506,7 @@ int sph_set_state(sph_handle s, const double *x, const double *u, const double *
     CU(cudaMemcpyAsync(dr, rho, sizeof(double) * n, cudaMemcpyHostToDevice, s->stream));
     k_load_state<<<s->blocks(s->n), 256, 0, s->stream>>>(s->D(), s->phys, s->dim, dx, du, dr);
     CU(cudaGetLastError());
+    CU(cudaMemsetAsync(s->rebuild, 0xff, sizeof(unsigned), s->stream));
     CU(cudaStreamSynchronize(s->stream));
     return SPH_OK;
 }
@@ -493,7 +515,7 @@ int sph_build_cells(sph_handle s)
 {
     if (!s) return fail(SPH_EINVAL, "handle is NULL");
     if (s->n == 0) return SPH_OK;
-    s->enqueue_build_cells();
+    s->enqueue_build_cells(true);
     CU(cudaGetLastError());
     return SPH_OK;
 }
@@ -502,7 +524,7 @@ int sph_eval_rates(sph_handle s)
 {
     if (!s) return fail(SPH_EINVAL, "handle is NULL");
     if (s->n == 0) return SPH_OK;
-    s->enqueue_build_cells();
+    s->enqueue_build_cells(true);
     s->enqueue_eval(1, s->D().drho);
     CU(cudaGetLastError());
     return SPH_OK;
@@ -513,6 +535,9 @@ int sph_step(sph_handle s, double dt)
     if (!s) return fail(SPH_EINVAL, "handle is NULL");
     if (!(dt > 0) || !std::isfinite(dt)) return fail(SPH_EINVAL, "dt must be positive and finite");
     if (s->n > 0) {
+        // the rebuild test looks half a step ahead with the previous dt
+        if (dt != s->last_dt) CU(cudaMemsetAsync(s->rebuild, 0xff, sizeof(unsigned), s->stream));
+        s->last_dt = dt;
         s->enqueue_step(dt);
         CU(cudaGetLastError());
     }
@@ -530,45 +555,32 @@ int sph_run(sph_handle s, double dt, int64_t nsteps, int graph)
         return SPH_OK;
     }
     const bool use_graph = graph && !s->timing;
-    int64_t left = nsteps;
-    auto eager = [&]() -> int {
-        s->enqueue_step(dt);
-        CU(cudaGetLastError());
-        s->step += 1;
-        left -= 1;
-        return SPH_OK;
-    };
+    if (dt != s->last_dt) CU(cudaMemsetAsync(s->rebuild, 0xff, sizeof(unsigned), s->stream));
+    s->last_dt = dt;
     if (use_graph) {
-        // Every step swaps the double-buffered state, so one graph holds two
-        // steps and starts and ends on buffer 0.
-        if (s->cur != 0 && left > 0) {
-            int rc = eager();
-            if (rc) return rc;
+        if (!s->gexec[0] || s->gdt[0] != dt) {
+            cudaGraph_t gr = nullptr;
+            CU(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
+            s->enqueue_step(dt);
+            cudaError_t e = cudaStreamEndCapture(s->stream, &gr);
+            if (e != cudaSuccess) return fail(SPH_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+            if (s->gexec[0]) cudaGraphExecDestroy(s->gexec[0]);
+            s->gexec[0] = nullptr;
+            e = cudaGraphInstantiate(&s->gexec[0], gr, 0);
+            cudaGraphDestroy(gr);
+            if (e != cudaSuccess) return fail(SPH_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+            s->gdt[0] = dt;
         }
-        while (left >= 2) {
-            if (!s->gexec[0] || s->gdt[0] != dt) {
-                cudaGraph_t gr = nullptr;
-                CU(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
-                s->enqueue_step(dt);
-                s->enqueue_step(dt);
-                cudaError_t e = cudaStreamEndCapture(s->stream, &gr);
-                if (e != cudaSuccess) return fail(SPH_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-                if (s->gexec[0]) cudaGraphExecDestroy(s->gexec[0]);
-                s->gexec[0] = nullptr;
-                e = cudaGraphInstantiate(&s->gexec[0], gr, 0);
-                cudaGraphDestroy(gr);
-                if (e != cudaSuccess) return fail(SPH_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
-                s->gdt[0] = dt;
-                // capture queued nothing; the two swaps it made are undone
-            }
+        for (int64_t k = 0; k < nsteps; ++k) {
             CU(cudaGraphLaunch(s->gexec[0], s->stream));
-            s->step += 2;
-            left -= 2;
+            s->step += 1;
         }
-    }
-    while (left > 0) {
-        int rc = eager();
-        if (rc) return rc;
+    } else {
+        for (int64_t k = 0; k < nsteps; ++k) {
+            s->enqueue_step(dt);
+            CU(cudaGetLastError());
+            s->step += 1;
+        }
     }
     return s->check_flags();
 }
@@ -624,7 +636,7 @@ int64_t sph_neighbours(sph_handle s, int64_t *start, int32_t *list, int64_t cap)
         start[0] = 0;
         return 0;
     }
-    s->enqueue_build_cells();
+    s->enqueue_build_cells(true);
     Dev &d = s->D();
     int *cnt = s->tmp;  // scratch, free after the build
     if (s->dim == 2) k_nbr_count<2><<<s->blocks(n), 256, 0, s->stream>>>(d, s->grid, s->phys, cnt);
@@ -671,7 +683,7 @@ int sph_pair_stats(sph_handle s, int64_t out[2])
     if (!s || !out) return fail(SPH_EINVAL, "NULL argument");
     out[0] = out[1] = 0;
     if (s->n == 0) return SPH_OK;
-    s->enqueue_build_cells();
+    s->enqueue_build_cells(true);
     unsigned long long *tot = reinterpret_cast<unsigned long long *>(s->diag_small + 48);
     CU(cudaMemsetAsync(tot, 0, 2 * sizeof(unsigned long long), s->stream));
     if (s->dim == 2) k_pair_stats<2><<<s->blocks(s->n), 256, 0, s->stream>>>(s->D(), s->grid, s->phys, tot);
@@ -771,6 +783,15 @@ int sph_timing_read(sph_handle s, int k, const char **name, int64_t *launches, d
     if (launches) *launches = s->t_launches[k];
     if (total_ms) *total_ms = s->t_ms[k];
     return SPH_OK;
+}
+
+int64_t sph_list_builds(sph_handle s)
+{
+    if (!s) return fail(SPH_EINVAL, "handle is NULL");
+    long long b = 0;
+    CU(cudaMemcpyAsync(&b, s->dbuilds, sizeof(b), cudaMemcpyDeviceToHost, s->stream));
+    CU(cudaStreamSynchronize(s->stream));
+    return b;
 }
 
 int64_t sph_num_particles(sph_handle s) { return s ? s->n : 0; }

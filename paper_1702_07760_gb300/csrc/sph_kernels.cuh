@@ -54,7 +54,8 @@ struct Phys {
     int visc_dynamic;   // 1: Eq. visc_2 (factor 1/rho_i), 0: Eq. visc_1
     int renorm_every;   // Eq. ct_dist_3 at stage 1 of steps with step % renorm_every == 0
     int kmax;           // neighbour-list capacity per particle
-    double skin;        // allowed predictor displacement (the list's margin)
+    int rebuild_every;  // 0: rebuild when a particle may leave the skin; k: every k steps
+    double skin;        // allowed displacement since the last build (the list's margin)
 };
 
 struct Grid {
@@ -79,6 +80,7 @@ struct Dev {
     int *cell;          // n, cell id (sorted order)
     // stage arrays
     float4 *pos;        // n, (offset from the super-cell centre xyz, +/- m/rho of the stage input; sign = phase)
+    float4 *pos0;       // n, offset at the last list build (xyz): displacement since the build
     float *vd;          // n, (m/rho) * drho of the stage input
     float4 *posv;       // n, (offset xyz, +/- m/rho after renormalisation with its lowest
                         //     mantissa bit replaced by the interface flag): sweep A output
@@ -96,7 +98,9 @@ struct Dev {
     // cell list
     int *cstart;        // ncell + 1
     unsigned *flags;    // 1 word
+    unsigned *rebuild;  // 1 word: nonzero when the cell and neighbour lists must be rebuilt
     long long *step;    // device step counter (drives the renormalisation schedule)
+    long long *builds;  // number of list builds performed
 };
 
 // Neighbour-list entry: particle index in the low 26 bits; per axis a, two
@@ -257,7 +261,7 @@ template <int DIM>
 __global__ void __launch_bounds__(256) k_hash(Dev d, Grid g, int *cell_tmp, int *slot, int *count)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= d.n) return;
+    if (k >= d.n || !*d.rebuild) return;
     const int dims[3] = {g.nx, g.ny, g.nz};
     int c[3] = {0, 0, 0};
     unsigned bad = 0;
@@ -314,9 +318,11 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int *total)
     return res;
 }
 
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan_tiles(const int *in, int *out, int *tile_sums, int m)
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_tiles(const int *in, int *out, int *tile_sums, int m,
+                                                              const unsigned *rebuild)
 {
     __shared__ int s_total;
+    if (!*rebuild) return;
     const int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
     int v[SCAN_ITEMS];
     int sum = 0;
@@ -336,9 +342,11 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_tiles(const int *in, int 
 
 // Scans the tile sums in place (one block, at most SCAN_TILE tiles) and
 // writes the grand total to out[m].
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan_sums(int *tile_sums, int ntiles, int *out, int m)
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_sums(int *tile_sums, int ntiles, int *out, int m,
+                                                             const unsigned *rebuild)
 {
     __shared__ int s_total;
+    if (!*rebuild) return;
     const int base = threadIdx.x * SCAN_ITEMS;
     int v[SCAN_ITEMS];
     int sum = 0;
@@ -356,26 +364,33 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_sums(int *tile_sums, int 
     if (threadIdx.x == 0) out[m] = s_total;
 }
 
-__global__ void __launch_bounds__(256) k_scan_add(int *out, const int *tile_sums, int m)
+__global__ void __launch_bounds__(256) k_scan_add(int *out, const int *tile_sums, int m, const unsigned *rebuild)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < m) out[i] += tile_sums[i / SCAN_TILE];
+    if (i < m && *rebuild) out[i] += tile_sums[i / SCAN_TILE];
 }
 
-__global__ void __launch_bounds__(256) k_scatter(int n, const int *cell_tmp, const int *slot, const int *cstart, int *tmp)
+__global__ void __launch_bounds__(256) k_zero(int *a, int m, const unsigned *rebuild)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m && *rebuild) a[i] = 0;
+}
+
+__global__ void __launch_bounds__(256) k_scatter(int n, const int *cell_tmp, const int *slot, const int *cstart, int *tmp,
+                                                 const unsigned *rebuild)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
+    if (k >= n || !*rebuild) return;
     tmp[cstart[cell_tmp[k]] + slot[k]] = k;
 }
 
 // Final position of each particle inside its cell: its rank by original id
 // among the cell's particles, so the order is (cell id, particle id).
 __global__ void __launch_bounds__(256) k_rank(int n, const int *tmp, const int *cell_tmp, const int *pid,
-                                              const int *cstart, int *perm)
+                                              const int *cstart, int *perm, const unsigned *rebuild)
 {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n) return;
+    if (p >= n || !*rebuild) return;
     const int k = tmp[p];
     const int c = cell_tmp[k];
     const int b = cstart[c], e = cstart[c + 1];
@@ -385,13 +400,27 @@ __global__ void __launch_bounds__(256) k_rank(int n, const int *tmp, const int *
     perm[b + rank] = k;
 }
 
-// Gathers the state into the new order and prepares the stage-1 arrays.
+// Stage-1 records of particle k from its FP64 state.
+template <int DIM>
+__device__ __forceinline__ void stage_records(const Dev &d, const Grid &g, const Phys &ph, int k, int c,
+                                              const double xa[3], const double ua[3], float dr, int oil)
+{
+    float4 p = cell_offset<DIM>(g, c, xa);
+    float vol;
+    p.w = signed_volume(ph, oil, dr, vol);
+    d.pos[k] = p;
+    d.vd[k] = vol * dr;
+    d.velp[k] = make_float4((float)ua[0], (float)ua[1], (float)ua[2], 0.f);
+}
+
+// Gathers the state into the new order (into the scratch set `dst`) and
+// prepares the stage-1 records and the build offsets.
 template <int DIM>
 __global__ void __launch_bounds__(256) k_gather(Dev src, Dev dst, Grid g, Phys ph, const int *perm, const int *cell_tmp)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = src.n;
-    if (k >= n) return;
+    if (k >= n || !*src.rebuild) return;
     const int o = perm[k];
     double xa[3] = {0, 0, 0}, ua[3] = {0, 0, 0};
 #pragma unroll
@@ -407,13 +436,26 @@ __global__ void __launch_bounds__(256) k_gather(Dev src, Dev dst, Grid g, Phys p
     dst.drho[k] = dr;
     dst.pid[k] = src.pid[o];
     dst.tag[k] = tg;
-    dst.cell[k] = c;
-    float4 p = cell_offset<DIM>(g, c, xa);
-    float vol;
-    p.w = signed_volume(ph, tg & 1, dr, vol);
-    dst.pos[k] = p;
-    dst.vd[k] = vol * dr;
-    dst.velp[k] = make_float4((float)ua[0], (float)ua[1], (float)ua[2], 0.f);
+    src.cell[k] = c;
+    stage_records<DIM>(src, g, ph, k, c, xa, ua, dr, tg & 1);
+    src.pos0[k] = src.pos[k];
+}
+
+// Copies the gathered state back into the primary set.
+template <int DIM>
+__global__ void __launch_bounds__(256) k_copy_back(Dev src, Dev dst)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = src.n;
+    if (k >= n || !*dst.rebuild) return;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        dst.x[(size_t)a * n + k] = src.x[(size_t)a * n + k];
+        dst.u[(size_t)a * n + k] = src.u[(size_t)a * n + k];
+    }
+    dst.drho[k] = src.drho[k];
+    dst.pid[k] = src.pid[k];
+    dst.tag[k] = src.tag[k];
 }
 
 // ---------------------------------------------------------------------------
@@ -424,7 +466,8 @@ template <int DIM>
 __global__ void __launch_bounds__(256, 4) k_build_list(Dev d, Grid g, Phys ph)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= d.n) return;
+    if (i >= d.n || !*d.rebuild) return;
+    if (i == 0) *d.builds += 1;
     const float4 oi = d.pos[i];
     const int phi_ = phase_of(oi.w);
     int cnt = 0;
@@ -462,6 +505,8 @@ __global__ void __launch_bounds__(256) k_sweep_a(Dev d, Grid g, Phys ph, const f
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.n) return;
     const int renorm = stage1 && ph.renorm_every > 0 && (*d.step % ph.renorm_every) == 0;
+    // the lists built for this step are in place; the corrector decides the next build
+    if (stage1 && i == 0) *d.rebuild = 0u;
     const float4 oi = d.pos[i];
     const int phi_ = phase_of(oi.w);
     // self term: W(0)/alpha_d = 1
@@ -647,20 +692,19 @@ __global__ void __launch_bounds__(256) k_predict(Dev d, Grid g, Phys ph, double 
     double xs[3] = {0, 0, 0}, us[3] = {0, 0, 0};
     const double af[3] = {a.x, a.y, a.z};
     bool finite = isfinite(drs);
-    double disp2 = 0.0;
 #pragma unroll
     for (int c = 0; c < DIM; ++c) {
         const double x = d.x[(size_t)c * d.n + k], u = d.u[(size_t)c * d.n + k];
-        const double dx = (tg & 2) ? 0.0 : 0.5 * dt * u;
-        xs[c] = x + dx;
+        xs[c] = (tg & 2) ? x : x + 0.5 * dt * u;
         us[c] = (tg & 2) ? u : u + 0.5 * dt * af[c];
-        disp2 += dx * dx;
         finite = finite && isfinite(us[c]) && isfinite(xs[c]);
     }
-    // the neighbour list of the step stays complete while no particle moves
-    // farther than the skin
-    if (disp2 > ph.skin * ph.skin) atomicOr(d.flags, FLAG_SKIN);
     float4 p = cell_offset<DIM>(g, d.cell[k], xs);
+    // the neighbour list stays complete while no particle is farther than the
+    // skin from where it was at the build
+    const float4 p0 = d.pos0[k];
+    const float ex = p.x - p0.x, ey = p.y - p0.y, ez = p.z - p0.z;
+    if (ex * ex + ey * ey + ez * ez > (float)(ph.skin * ph.skin)) atomicOr(d.flags, FLAG_SKIN);
     float vol;
     p.w = signed_volume(ph, tg & 1, drs, vol);
     d.pos[k] = p;
@@ -670,30 +714,51 @@ __global__ void __launch_bounds__(256) k_predict(Dev d, Grid g, Phys ph, double 
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(256) k_correct(Dev d, double dt)
+__global__ void __launch_bounds__(256) k_correct(Dev d, Grid g, Phys ph, double dt)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= d.n) return;
-    if (k == 0) *d.step += 1;
+    if (k == 0) {
+        const long long next = *d.step + 1;
+        *d.step = next;
+        if (ph.rebuild_every > 0 && next % ph.rebuild_every == 0) *d.rebuild = 1u;
+    }
     const uint8_t tg = d.tag[k];
     const float4 a = d.acc[k];
     const float dr = fmaf((float)dt, a.w, d.drho[k]);
     d.drho[k] = dr;
     bool finite = isfinite(dr);
-    if (!(tg & 2)) {
-        const float4 us = d.velp[k];
-        const double usa[3] = {us.x, us.y, us.z};
-        const double af[3] = {a.x, a.y, a.z};
+    double xa[3] = {0, 0, 0}, ua[3] = {0, 0, 0};
+    const float4 us = d.velp[k];
+    const double usa[3] = {us.x, us.y, us.z};
+    const double af[3] = {a.x, a.y, a.z};
 #pragma unroll
-        for (int c = 0; c < DIM; ++c) {
-            const double x = d.x[(size_t)c * d.n + k] + dt * usa[c];
-            const double u = d.u[(size_t)c * d.n + k] + dt * af[c];
-            d.x[(size_t)c * d.n + k] = x;
-            d.u[(size_t)c * d.n + k] = u;
-            finite = finite && isfinite(x) && isfinite(u);
+    for (int c = 0; c < DIM; ++c) {
+        xa[c] = d.x[(size_t)c * d.n + k];
+        ua[c] = d.u[(size_t)c * d.n + k];
+        if (!(tg & 2)) {
+            xa[c] += dt * usa[c];
+            ua[c] += dt * af[c];
+            d.x[(size_t)c * d.n + k] = xa[c];
+            d.u[(size_t)c * d.n + k] = ua[c];
         }
+        finite = finite && isfinite(xa[c]) && isfinite(ua[c]);
     }
     if (!finite) atomicOr(d.flags, FLAG_NONFINITE);
+    // stage-1 records of the next step (replaced by the gather if it rebuilds)
+    stage_records<DIM>(d, g, ph, k, d.cell[k], xa, ua, dr, tg & 1);
+    if (ph.rebuild_every == 0 && !(tg & 2)) {
+        // next step's stage positions: x^{n+1} and x^{n+1} + dt/2 u^{n+1};
+        // rebuild before either can be farther than the skin from the build
+        const float4 p = d.pos[k], p0 = d.pos0[k];
+        const float hx = 0.5f * (float)dt * (float)ua[0], hy = 0.5f * (float)dt * (float)ua[1],
+                    hz = 0.5f * (float)dt * (float)ua[2];
+        const float ex = p.x - p0.x, ey = p.y - p0.y, ez = p.z - p0.z;
+        const float d1 = ex * ex + ey * ey + ez * ez;
+        const float d2 = (ex + hx) * (ex + hx) + (ey + hy) * (ey + hy) + (ez + hz) * (ez + hz);
+        const float lim = (float)(0.98 * ph.skin);
+        if (fmaxf(d1, d2) > lim * lim) atomicOr(d.rebuild, 1u);
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -24,7 +24,7 @@ FIELD = dict(pos=0, vel=1, rho=2, rho_eval=3, pressure=4, acc=5, drho=6, tensor=
 EXPORTS = ["sph_create", "sph_set_state", "sph_build_cells", "sph_eval_rates", "sph_step", "sph_run",
            "sph_sync", "sph_read", "sph_neighbours", "sph_pair_stats", "sph_diag", "sph_timing_enable",
            "sph_timing_reset", "sph_timing_count", "sph_timing_read", "sph_num_particles",
-           "sph_step_index", "sph_num_cells", "sph_destroy", "sph_last_error"]
+           "sph_step_index", "sph_num_cells", "sph_list_builds", "sph_destroy", "sph_last_error"]
 
 
 class SphError(RuntimeError):
@@ -36,7 +36,7 @@ class SphError(RuntimeError):
 class SphParams(C.Structure):
     _fields_ = [
         ("dim", C.c_int32), ("visc_form", C.c_int32), ("renorm_every", C.c_int32),
-        ("max_neighbours", C.c_int32), ("h", C.c_double), ("c0", C.c_double), ("gamma", C.c_double),
+        ("max_neighbours", C.c_int32), ("rebuild_every", C.c_int32), ("reserved", C.c_int32), ("h", C.c_double), ("c0", C.c_double), ("gamma", C.c_double),
         ("delta", C.c_double), ("alpha_s", C.c_double), ("cell_size", C.c_double), ("skin", C.c_double),
         ("g", C.c_double * 3), ("rho0", C.c_double * 2), ("mu", C.c_double * 2),
         ("mass", C.c_double * 2), ("box_lo", C.c_double * 3), ("box_hi", C.c_double * 3),
@@ -70,7 +70,7 @@ def load(path: str = LIB_PATH):
     L.sph_timing_enable.argtypes = [H, C.c_int]
     L.sph_timing_count.argtypes = []
     L.sph_timing_read.argtypes = [H, C.c_int, P(C.c_char_p), P(C.c_int64), P(C.c_double)]
-    for f in (L.sph_num_particles, L.sph_step_index, L.sph_num_cells):
+    for f in (L.sph_num_particles, L.sph_step_index, L.sph_num_cells, L.sph_list_builds):
         f.argtypes = [H]
         f.restype = C.c_int64
     L.sph_destroy.argtypes = [H]
@@ -86,6 +86,8 @@ def make_params(p: dict) -> SphParams:
     s.visc_form = int(p.get("visc_form", 0))
     s.renorm_every = int(p.get("renorm_every", 1))
     s.max_neighbours = int(p.get("max_neighbours", 0))
+    s.rebuild_every = int(p.get("rebuild_every", 0))
+    s.reserved = 0
     s.h, s.c0, s.gamma = p["h"], p["c0"], p.get("gamma", 7.0)
     s.delta, s.alpha_s, s.cell_size, s.skin = p["delta"], p["alpha_s"], p["cell_size"], p["skin"]
     for k in range(3):
@@ -205,6 +207,13 @@ class Simulation:
     @property
     def step_index(self) -> int:
         return int(load().sph_step_index(self._h))
+
+    @property
+    def list_builds(self) -> int:
+        r = int(load().sph_list_builds(self._h))
+        if r < 0:
+            _check(r)
+        return r
 
     @property
     def num_cells(self) -> int:

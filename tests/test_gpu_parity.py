@@ -133,17 +133,40 @@ def test_graph_replay_is_bit_identical_to_eager(sphmod):
 
 
 def test_restart_is_bit_exact(sphmod):
+    """With a list build every step the particle order after a restart is
+    the one the uninterrupted run has, so the runs agree bit for bit."""
     w = WL.drop_tank(2, (30, 40), drop_d_dx=10, seed=4, perturb=True)
-    dt = WL.stable_dt(w.params)
-    a = sphmod.Simulation.from_workload(w)
+    p = dict(w.params, rebuild_every=1)
+    dt = WL.stable_dt(p)
+    a = sphmod.Simulation(p, w.x, w.u, w.rho, w.phase, w.wall)
     a.run(dt, 20)
-    b = sphmod.Simulation.from_workload(w)
+    b = sphmod.Simulation(p, w.x, w.u, w.rho, w.phase, w.wall)
     b.run(dt, 10)
     x, u, r = b.read("pos"), b.read("vel"), b.read("rho")
-    c = sphmod.Simulation(w.params, x, u, r, w.phase, w.wall)
+    c = sphmod.Simulation(p, x, u, r, w.phase, w.wall)
     c.run(dt, 10)
     for f in ("pos", "vel", "rho"):
         assert np.array_equal(a.read(f), c.read(f)), f
+    assert a.list_builds == 20
+
+
+def test_adaptive_list_rebuild_matches_every_step_build(sphmod):
+    """The displacement-driven rebuild skips builds and changes only the
+    summation order (FP32 rounding), never the neighbour sets."""
+    w = WL.drop_tank(2, (40, 60), drop_d_dx=12, seed=6, perturb=True)
+    dt = WL.stable_dt(w.params)
+    every = sphmod.Simulation(dict(w.params, rebuild_every=1), w.x, w.u, w.rho, w.phase, w.wall)
+    adapt = sphmod.Simulation(w.params, w.x, w.u, w.rho, w.phase, w.wall)
+    every.run(dt, 30)
+    adapt.run(dt, 30)
+    assert every.list_builds == 30
+    assert 1 <= adapt.list_builds < 30
+    dx = w.params["dx"]
+    assert np.abs(every.read("pos") - adapt.read("pos")).max() < 1e-6 * dx
+    rel = np.abs(every.read("rho") / adapt.read("rho") - 1).max()
+    assert rel < 1e-6
+    ue, ua = every.read("vel"), adapt.read("vel")
+    assert np.abs(ue - ua).max() < 1e-5 * np.abs(ue).max()
 
 
 def test_diagnostics_match_oracle(sphmod):
