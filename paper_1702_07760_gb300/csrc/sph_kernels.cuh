@@ -103,6 +103,12 @@ struct Dev {
     long long *builds;  // number of list builds performed
 };
 
+// Neighbour-list entries a sweep loads ahead of use (one chunk in flight
+// while the previous chunk is processed).
+#ifndef SPH_LIST_CHUNK
+#define SPH_LIST_CHUNK 8
+#endif
+
 // Neighbour-list entry: particle index in the low 26 bits; per axis a, two
 // bits at 26 + 2a holding (S_i - S_j) + 1 in {0, 1, 2} (super-cells).
 constexpr int NBR_IDX_BITS = 26;
@@ -516,35 +522,50 @@ __global__ void __launch_bounds__(256) k_sweep_a(Dev d, Grid g, Phys ph, const f
     if (renorm || other) {
         const float inv_h = ph.inv_h, cs = g.Es;
         const int n = d.n, cnt = d.ncnt[i];
-        const unsigned *__restrict__ np = d.nbr + i;
+        const unsigned *__restrict__ col = d.nbr + i;
         const float4 *__restrict__ pos = d.pos;
         const float *__restrict__ vd = d.vd;
-#pragma unroll 4
-        for (int k = 0; k < cnt; ++k, np += n) {
-            const unsigned e = __ldg(np);
-            const int j = (int)(e & NBR_IDX_MASK);
-            const float4 oj = __ldg(pos + j);
-            float rx, ry, rz;
-            const float r2 = pair_vec<DIM>(oi, oj, entry_shift(e, 0, cs), entry_shift(e, 1, cs),
-                                           DIM == 3 ? entry_shift(e, 2, cs) : 0.f, rx, ry, rz);
-            // beyond the support (list entries in the skin) t clamps to 0 and
-            // every kernel term vanishes
-            const float r = r2 * rsqrtf(fmaxf(r2, 1e-30f));
-            const float t = fmaxf(fmaf(-0.5f * inv_h, r, 1.f), 0.f);
-            const float t3 = t * t * t;
-            if (phase_of(oj.w) == phi_) {
-                if (renorm) {
-                    // W / alpha_d = t^4 (2q + 1)
-                    const float w = t3 * t * fmaf(2.f * inv_h, r, 1.f);
-                    kahan_add(s1, c1, fabsf(oj.w) * w);
-                    kahan_add(s2, c2, __ldg(vd + j) * w);
-                }
-            } else {
-                const float c = oj.w * oj.w * t3;
-                gx = fmaf(c, rx, gx);
-                gy = fmaf(c, ry, gy);
-                if (DIM == 3) gz = fmaf(c, rz, gz);
+        constexpr int CH = SPH_LIST_CHUNK;
+        unsigned ec[CH];
+#pragma unroll
+        for (int c = 0; c < CH; ++c) ec[c] = c < cnt ? __ldg(col + (size_t)c * n) : 0u;
+        for (int k0 = 0; k0 < cnt; k0 += CH) {
+            unsigned en[CH];
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                const int kk = k0 + CH + c;
+                en[c] = kk < cnt ? __ldg(col + (size_t)kk * n) : 0u;
             }
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                if (k0 + c >= cnt) break;
+                const unsigned e = ec[c];
+                const int j = (int)(e & NBR_IDX_MASK);
+                const float4 oj = __ldg(pos + j);
+                float rx, ry, rz;
+                const float r2 = pair_vec<DIM>(oi, oj, entry_shift(e, 0, cs), entry_shift(e, 1, cs),
+                                               DIM == 3 ? entry_shift(e, 2, cs) : 0.f, rx, ry, rz);
+                // beyond the support (list entries in the skin) t clamps to 0 and
+                // every kernel term vanishes
+                const float r = r2 * rsqrtf(fmaxf(r2, 1e-30f));
+                const float t = fmaxf(fmaf(-0.5f * inv_h, r, 1.f), 0.f);
+                const float t3 = t * t * t;
+                if (phase_of(oj.w) == phi_) {
+                    if (renorm) {
+                        // W / alpha_d = t^4 (2q + 1)
+                        const float w = t3 * t * fmaf(2.f * inv_h, r, 1.f);
+                        kahan_add(s1, c1, fabsf(oj.w) * w);
+                        kahan_add(s2, c2, __ldg(vd + j) * w);
+                    }
+                } else {
+                    const float cc = oj.w * oj.w * t3;
+                    gx = fmaf(cc, rx, gx);
+                    gy = fmaf(cc, ry, gy);
+                    if (DIM == 3) gz = fmaf(cc, rz, gz);
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < CH; ++c) ec[c] = en[c];
         }
     }
     const float drho = renorm ? s2 / s1 : drho_in[i];
@@ -609,56 +630,71 @@ __global__ void __launch_bounds__(256, 4) k_sweep_b(Dev d, Grid g, Phys ph)
     // per-phase constants of the pair terms as registers (selected per pair)
     const float m_wat = ph.mass[0], m_oil = ph.mass[1];
     const float kv_wat = phi_ ? ph.kvis[2] : ph.kvis[0], kv_oil = phi_ ? ph.kvis[3] : ph.kvis[1];
-    const unsigned *__restrict__ np = d.nbr + i;
+    const unsigned *__restrict__ col = d.nbr + i;
     const float4 *__restrict__ posv = d.posv;
     const float4 *__restrict__ velp = d.velp;
     const float4 *__restrict__ T4 = d.T4;
     const float2 *__restrict__ T2 = d.T2;
-#pragma unroll 4
-    for (int k = 0; k < cnt; ++k, np += n) {
-        const unsigned e = __ldg(np);
-        const int j = (int)(e & NBR_IDX_MASK);
-        const float4 oj = __ldg(posv + j);
-        const float4 uj = __ldg(velp + j);
-        float rx, ry, rz;
-        const float r2 = pair_vec<DIM>(oi, oj, entry_shift(e, 0, cs), entry_shift(e, 1, cs),
-                                       DIM == 3 ? entry_shift(e, 2, cs) : 0.f, rx, ry, rz);
-        const bool oil_j = oj.w < 0.f;
-        const float vol_j = fabsf(oj.w);
-        // beyond the support (list entries in the skin) t clamps to 0 and
-        // every pair term below vanishes
-        const float r = r2 * rsqrtf(fmaxf(r2, 1e-30f));
-        const float t = fmaxf(fmaf(-0.5f * inv_h, r, 1.f), 0.f);
-        const float t3 = t * t * t;
-        const float pt = (oil_j ? m_oil : m_wat) * (ui.w + uj.w) * t3;
-        px = fmaf(pt, rx, px);
-        py = fmaf(pt, ry, py);
-        if (DIM == 3) pz = fmaf(pt, rz, pz);
-        const float ux = ui.x - uj.x, uy = ui.y - uj.y, uz = DIM == 3 ? ui.z - uj.z : 0.f;
-        const float vt = vol_j * t3;
-        const float s = (oil_j ? kv_oil : kv_wat) * vt * __fdividef(r2, r2 + ph.delta2);
-        vx = fmaf(s, ux, vx);
-        vy = fmaf(s, uy, vy);
-        if (DIM == 3) vz = fmaf(s, uz, vz);
-        float ur = ux * rx;
-        ur = fmaf(uy, ry, ur);
-        if (DIM == 3) ur = fmaf(uz, rz, ur);
-        dv = fmaf(vt, ur, dv);
-        if ((iface_i | (__float_as_uint(oj.w) & 1u)) != 0u) {
-            const float4 Tj = __ldg(T4 + j);
-            if (DIM == 2) {
-                const float xx = Ti.x + Tj.x, xy = Ti.y + Tj.y, yy = Ti.z + Tj.z;
-                sx = fmaf(t3, xx * rx + xy * ry, sx);
-                sy = fmaf(t3, xy * rx + yy * ry, sy);
-            } else {
-                const float2 Tj2 = __ldg(T2 + j);
-                const float xx = Ti.x + Tj.x, xy = Ti.y + Tj.y, xz = Ti.z + Tj.z;
-                const float yy = Ti.w + Tj.w, yz = Ti2.x + Tj2.x, zz = Ti2.y + Tj2.y;
-                sx = fmaf(t3, xx * rx + xy * ry + xz * rz, sx);
-                sy = fmaf(t3, xy * rx + yy * ry + yz * rz, sy);
-                sz = fmaf(t3, xz * rx + yz * ry + zz * rz, sz);
+    constexpr int CH = SPH_LIST_CHUNK;
+    unsigned ec[CH];
+#pragma unroll
+    for (int c = 0; c < CH; ++c) ec[c] = c < cnt ? __ldg(col + (size_t)c * n) : 0u;
+    for (int k0 = 0; k0 < cnt; k0 += CH) {
+        unsigned en[CH];
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+            const int kk = k0 + CH + c;
+            en[c] = kk < cnt ? __ldg(col + (size_t)kk * n) : 0u;
+        }
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+            if (k0 + c >= cnt) break;
+            const unsigned e = ec[c];
+            const int j = (int)(e & NBR_IDX_MASK);
+            const float4 oj = __ldg(posv + j);
+            const float4 uj = __ldg(velp + j);
+            float rx, ry, rz;
+            const float r2 = pair_vec<DIM>(oi, oj, entry_shift(e, 0, cs), entry_shift(e, 1, cs),
+                                           DIM == 3 ? entry_shift(e, 2, cs) : 0.f, rx, ry, rz);
+            const bool oil_j = oj.w < 0.f;
+            const float vol_j = fabsf(oj.w);
+            // beyond the support (list entries in the skin) t clamps to 0 and
+            // every pair term below vanishes
+            const float r = r2 * rsqrtf(fmaxf(r2, 1e-30f));
+            const float t = fmaxf(fmaf(-0.5f * inv_h, r, 1.f), 0.f);
+            const float t3 = t * t * t;
+            const float pt = (oil_j ? m_oil : m_wat) * (ui.w + uj.w) * t3;
+            px = fmaf(pt, rx, px);
+            py = fmaf(pt, ry, py);
+            if (DIM == 3) pz = fmaf(pt, rz, pz);
+            const float ux = ui.x - uj.x, uy = ui.y - uj.y, uz = DIM == 3 ? ui.z - uj.z : 0.f;
+            const float vt = vol_j * t3;
+            const float s = (oil_j ? kv_oil : kv_wat) * vt * __fdividef(r2, r2 + ph.delta2);
+            vx = fmaf(s, ux, vx);
+            vy = fmaf(s, uy, vy);
+            if (DIM == 3) vz = fmaf(s, uz, vz);
+            float ur = ux * rx;
+            ur = fmaf(uy, ry, ur);
+            if (DIM == 3) ur = fmaf(uz, rz, ur);
+            dv = fmaf(vt, ur, dv);
+            if ((iface_i | (__float_as_uint(oj.w) & 1u)) != 0u) {
+                const float4 Tj = __ldg(T4 + j);
+                if (DIM == 2) {
+                    const float xx = Ti.x + Tj.x, xy = Ti.y + Tj.y, yy = Ti.z + Tj.z;
+                    sx = fmaf(t3, xx * rx + xy * ry, sx);
+                    sy = fmaf(t3, xy * rx + yy * ry, sy);
+                } else {
+                    const float2 Tj2 = __ldg(T2 + j);
+                    const float xx = Ti.x + Tj.x, xy = Ti.y + Tj.y, xz = Ti.z + Tj.z;
+                    const float yy = Ti.w + Tj.w, yz = Ti2.x + Tj2.x, zz = Ti2.y + Tj2.y;
+                    sx = fmaf(t3, xx * rx + xy * ry + xz * rz, sx);
+                    sy = fmaf(t3, xy * rx + yy * ry + yz * rz, sy);
+                    sz = fmaf(t3, xz * rx + yz * ry + zz * rz, sz);
+                }
             }
         }
+#pragma unroll
+        for (int c = 0; c < CH; ++c) ec[c] = en[c];
     }
     const float rho = by_phase(phi_, ph.rho0) + d.drho_eval[i];
     float4 out;
