@@ -293,7 +293,9 @@ def run_ours(args, ws, rank, local):
         cpu = {"value": rate, "unit": "particle-steps/s", "cores": cores, "kind": "oracle",
                "sample": f"{steps} FP64 oracle step(s) of the full {n}-particle workload"}
 
-    kernels_per_step = 13  # hash, 3 scan, scatter, rank, gather, 2 sweep_a, 2 sweep_b, predict, correct
+    # count reset, hash, 3 scan, scatter, rank, gather, copy-back, list (these return at once on
+    # steps without a rebuild), 2 sweep_a, 2 sweep_b, predict, correct
+    kernels_per_step = 16
     line = {
         "metric": "particle-steps/s", "value": value, "unit": "particle-steps/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,

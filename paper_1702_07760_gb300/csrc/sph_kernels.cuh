@@ -106,7 +106,7 @@ struct Dev {
 // Neighbour-list entries a sweep loads ahead of use (one chunk in flight
 // while the previous chunk is processed).
 #ifndef SPH_LIST_CHUNK
-#define SPH_LIST_CHUNK 8
+#define SPH_LIST_CHUNK 4
 #endif
 
 // Neighbour-list entry: particle index in the low 26 bits; per axis a, two
