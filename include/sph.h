@@ -185,6 +185,28 @@ int64_t sph_num_cells(sph_handle h);
 
 void sph_destroy(sph_handle h);
 
+/* Allocation-free cell sort (no counterpart in the paper: it serves callers
+ * that cannot allocate device memory -- code running while a CUDA stream is
+ * captured, where cudaMalloc is not permitted, or a host whose device memory
+ * is owned by another allocator).  Computes, for n particles whose positions
+ * x_dev are a device array of n * dim doubles (particle-major), the cell id
+ * of each particle on the grid of params (cell_size, box_lo, box_hi) into
+ * cell_dev (n int32, device) and the particle ids in the stable order by
+ * (cell id, particle id) into order_dev (n int32, device): the same values as
+ * SPH_FIELD_CELL and SPH_FIELD_ORDER after sph_build_cells.  The caller owns
+ * all three arrays.  No device memory is allocated: the scratch is one
+ * file-scope device array of about 21 MB that every GPU loading the library
+ * holds until the process exits, limiting n to 2^20 particles and the grid to
+ * 2^20 cells (larger sizes return SPH_EINVAL).  The first call on a device
+ * looks up that array's device address (once per device, with the device
+ * current), so make it before any stream capture.  Every call on a device
+ * shares the array and keeps the last call's contents (the parts that must
+ * start at zero are cleared by each call); calls that overlap on the GPU race.
+ * The call waits for the stream and returns SPH_EDOMAIN when a particle lies
+ * outside the box. */
+int sph_cell_sort_noalloc(const sph_params *params, int64_t n, const double *x_dev, int32_t *cell_dev,
+                          int32_t *order_dev, void *stream);
+
 /* Message of the last failure on the calling thread ("" if none). */
 const char *sph_last_error(void);
 

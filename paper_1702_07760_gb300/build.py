@@ -9,7 +9,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libsph.so")
-SOURCES = ["sph_api.cu"]
+SOURCES = ["sph_api.cu", "sph_noalloc.cu"]
 HEADERS = ["sph_kernels.cuh"]
 
 

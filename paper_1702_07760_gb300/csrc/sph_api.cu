@@ -225,6 +225,11 @@ int sph_sim::check_flags()
 
 // ---------------------------------------------------------------------------
 
+namespace sphgb {
+// Records the message returned by sph_last_error() for this thread.
+int set_error(int code, const std::string &msg) { return fail(code, msg); }
+}  // namespace sphgb
+
 namespace {
 
 __global__ void k_load_state(Dev d, Phys ph, int dim, const double *x, const double *u, const double *rho)

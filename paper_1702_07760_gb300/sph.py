@@ -24,7 +24,8 @@ FIELD = dict(pos=0, vel=1, rho=2, rho_eval=3, pressure=4, acc=5, drho=6, tensor=
 EXPORTS = ["sph_create", "sph_set_state", "sph_build_cells", "sph_eval_rates", "sph_step", "sph_run",
            "sph_sync", "sph_read", "sph_neighbours", "sph_pair_stats", "sph_diag", "sph_timing_enable",
            "sph_timing_reset", "sph_timing_count", "sph_timing_read", "sph_num_particles",
-           "sph_step_index", "sph_num_cells", "sph_list_builds", "sph_destroy", "sph_last_error"]
+           "sph_step_index", "sph_num_cells", "sph_list_builds", "sph_destroy", "sph_last_error",
+           "sph_cell_sort_noalloc"]
 
 
 class SphError(RuntimeError):
@@ -76,6 +77,7 @@ def load(path: str = LIB_PATH):
     L.sph_destroy.argtypes = [H]
     L.sph_destroy.restype = None
     L.sph_last_error.restype = C.c_char_p
+    L.sph_cell_sort_noalloc.argtypes = [P(SphParams), C.c_int64, vp, vp, vp, vp]
     _lib = L
     return L
 
@@ -104,6 +106,14 @@ def _check(rc: int):
 
 def _dp(a):
     return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def cell_sort_noalloc(params: dict, n: int, x_dev: int, cell_dev: int, order_dev: int, stream: int = 0):
+    """Allocation-free cell sort on device arrays given by address (see
+    sph_cell_sort_noalloc in include/sph.h)."""
+    p = make_params(params)
+    _check(load().sph_cell_sort_noalloc(C.byref(p), int(n), C.c_void_p(x_dev), C.c_void_p(cell_dev),
+                                        C.c_void_p(order_dev), C.c_void_p(stream)))
 
 
 class Simulation:
