@@ -294,8 +294,8 @@ def run_ours(args, ws, rank, local):
                "sample": f"{steps} FP64 oracle step(s) of the full {n}-particle workload"}
 
     # count reset, hash, 3 scan, scatter, rank, gather, copy-back, list (these return at once on
-    # steps without a rebuild), 2 sweep_a, 2 sweep_b, predict, correct
-    kernels_per_step = 16
+    # steps without a rebuild), 2 sweep_a, 2 sweep_b (with the predictor / corrector)
+    kernels_per_step = 14
     line = {
         "metric": "particle-steps/s", "value": value, "unit": "particle-steps/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,

@@ -34,11 +34,12 @@ int fail(int code, const std::string &msg)
 
 enum KernelId {
     KI_MEMSET, KI_HASH, KI_SCAN, KI_SCATTER, KI_RANK, KI_GATHER, KI_COPY, KI_LIST, KI_SWEEP_A, KI_SWEEP_B,
-    KI_PREDICT, KI_CORRECT, KI_COUNT
+    KI_COUNT
 };
+// sweep_b includes the predictor (stage 1) or the corrector (stage 2)
 const char *k_names[KI_COUNT] = {"count_reset", "cell_hash", "cell_scan", "cell_scatter",
                                  "cell_rank", "reorder_gather", "reorder_copy", "neighbour_list",
-                                 "sweep_a", "sweep_b", "predict", "correct"};
+                                 "sweep_a", "sweep_b"};
 
 struct PendingTiming {
     int id;
@@ -138,7 +139,7 @@ struct sph_sim {
     int blocks(int work, int threads = 256) const { return (work + threads - 1) / threads; }
 
     void enqueue_build_cells(bool force);
-    void enqueue_eval(int stage1, const float *drho_in);
+    void enqueue_eval(int stage, const float *drho_in, double dt);
     void enqueue_step(double dt);
     int check_flags();
 };
@@ -178,16 +179,27 @@ void sph_sim::enqueue_build_cells(bool force)
     });
 }
 
-void sph_sim::enqueue_eval(int stage1, const float *drho_in)
+// One rates evaluation: sweep A then sweep B of stage 0 (rates only), 1
+// (predictor fused) or 2 (corrector fused).
+void sph_sim::enqueue_eval(int stage, const float *drho_in, double dt)
 {
     Dev &d = buf[0];
+    float4 *vel_s = stage == 2 ? d.velq : d.velp;
+    const int stage1 = stage != 2;
     launch(KI_SWEEP_A, [&] {
-        if (dim == 2) k_sweep_a<2><<<blocks(n), 256, 0, stream>>>(d, grid, phys, drho_in, stage1);
-        else k_sweep_a<3><<<blocks(n), 256, 0, stream>>>(d, grid, phys, drho_in, stage1);
+        if (dim == 2) k_sweep_a<2><<<blocks(n), 256, 0, stream>>>(d, grid, phys, drho_in, stage1, vel_s);
+        else k_sweep_a<3><<<blocks(n), 256, 0, stream>>>(d, grid, phys, drho_in, stage1, vel_s);
     });
     launch(KI_SWEEP_B, [&] {
-        if (dim == 2) k_sweep_b<2><<<blocks(n), 256, 0, stream>>>(d, grid, phys);
-        else k_sweep_b<3><<<blocks(n), 256, 0, stream>>>(d, grid, phys);
+        if (dim == 2) {
+            if (stage == 0) k_sweep_b<2, 0><<<blocks(n), 256, 0, stream>>>(d, grid, phys, dt);
+            else if (stage == 1) k_sweep_b<2, 1><<<blocks(n), 256, 0, stream>>>(d, grid, phys, dt);
+            else k_sweep_b<2, 2><<<blocks(n), 256, 0, stream>>>(d, grid, phys, dt);
+        } else {
+            if (stage == 0) k_sweep_b<3, 0><<<blocks(n), 256, 0, stream>>>(d, grid, phys, dt);
+            else if (stage == 1) k_sweep_b<3, 1><<<blocks(n), 256, 0, stream>>>(d, grid, phys, dt);
+            else k_sweep_b<3, 2><<<blocks(n), 256, 0, stream>>>(d, grid, phys, dt);
+        }
     });
 }
 
@@ -195,16 +207,8 @@ void sph_sim::enqueue_step(double dt)
 {
     enqueue_build_cells(false);
     Dev &d = buf[0];
-    enqueue_eval(1, d.drho);
-    launch(KI_PREDICT, [&] {
-        if (dim == 2) k_predict<2><<<blocks(n), 256, 0, stream>>>(d, grid, phys, dt);
-        else k_predict<3><<<blocks(n), 256, 0, stream>>>(d, grid, phys, dt);
-    });
-    enqueue_eval(0, d.drho_stage);
-    launch(KI_CORRECT, [&] {
-        if (dim == 2) k_correct<2><<<blocks(n), 256, 0, stream>>>(d, grid, phys, dt);
-        else k_correct<3><<<blocks(n), 256, 0, stream>>>(d, grid, phys, dt);
-    });
+    enqueue_eval(1, d.drho, dt);
+    enqueue_eval(2, d.drho_stage, dt);
 }
 
 int sph_sim::check_flags()
@@ -434,6 +438,7 @@ int sph_create(const sph_params *params, int64_t n, const double *x, const doubl
         err |= s->alloc(&a0.vd, N);
         err |= s->alloc(&a0.posv, N);
         err |= s->alloc(&a0.velp, N);
+        err |= s->alloc(&a0.velq, N);
         err |= s->alloc(&a0.pres, N);
         err |= s->alloc(&a0.nbr, N * (size_t)ph.kmax);
         err |= s->alloc(&a0.ncnt, N);
@@ -460,7 +465,7 @@ int sph_create(const sph_params *params, int64_t n, const double *x, const doubl
     if (err) return cleanup(SPH_ENOMEM);
     Dev &a1 = s->buf[1];
     a1.cell = a0.cell; a1.pos0 = a0.pos0;
-    a1.pos = a0.pos; a1.vd = a0.vd; a1.posv = a0.posv; a1.velp = a0.velp; a1.pres = a0.pres;
+    a1.pos = a0.pos; a1.vd = a0.vd; a1.posv = a0.posv; a1.velp = a0.velp; a1.velq = a0.velq; a1.pres = a0.pres;
     a1.drho_stage = a0.drho_stage;
     a1.nbr = a0.nbr; a1.ncnt = a0.ncnt; a1.nflag = a0.nflag;
     a1.drho_eval = a0.drho_eval; a1.T4 = a0.T4; a1.T2 = a0.T2; a1.acc = a0.acc;
@@ -530,7 +535,7 @@ int sph_eval_rates(sph_handle s)
     if (!s) return fail(SPH_EINVAL, "handle is NULL");
     if (s->n == 0) return SPH_OK;
     s->enqueue_build_cells(true);
-    s->enqueue_eval(1, s->D().drho);
+    s->enqueue_eval(0, s->D().drho, 0.0);
     CU(cudaGetLastError());
     return SPH_OK;
 }

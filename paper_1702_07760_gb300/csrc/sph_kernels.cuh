@@ -84,7 +84,9 @@ struct Dev {
     float *vd;          // n, (m/rho) * drho of the stage input
     float4 *posv;       // n, (offset xyz, +/- m/rho after renormalisation with its lowest
                         //     mantissa bit replaced by the interface flag): sweep A output
-    float4 *velp;       // n, (u xyz of the stage, P/rho^2 from sweep A)
+    float4 *velp;       // n, stage 1: (u^n xyz, P/rho^2 from sweep A)
+    float4 *velq;       // n, stage 2: (u* xyz, P/rho^2 from sweep A); a separate buffer so
+                        //     the stage-1 force sweep can write it while neighbours read velp
     float *pres;        // n, P from sweep A
     float *drho_stage;  // n, drho* of the predictor
     float *drho_eval;   // n, drho after renormalisation (stage output)
@@ -496,6 +498,95 @@ __global__ void __launch_bounds__(256, 4) k_build_list(Dev d, Grid g, Phys ph)
 }
 
 // ---------------------------------------------------------------------------
+// Explicit midpoint predictor-corrector, run per particle at the end of the
+// force sweep of each stage (the particle's own acceleration is then final).
+
+// Predictor: x* = x^n + dt/2 u^n, u* = u^n + dt/2 a^n, rho* = rho^n + dt/2 Drho^n;
+// the renormalised density becomes the state rho^n.  Writes the stage-2
+// records (pos, vd, velq).
+template <int DIM>
+__device__ __forceinline__ void predict_particle(const Dev &d, const Grid &g, const Phys &ph, int k, float4 a,
+                                                 double dt)
+{
+    const uint8_t tg = d.tag[k];
+    const float dr = d.drho_eval[k];
+    d.drho[k] = dr;
+    const float drs = fmaf(0.5f * (float)dt, a.w, dr);
+    d.drho_stage[k] = drs;
+    double xs[3] = {0, 0, 0}, us[3] = {0, 0, 0};
+    const double af[3] = {a.x, a.y, a.z};
+    bool finite = isfinite(drs);
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+        const double x = d.x[(size_t)c * d.n + k], u = d.u[(size_t)c * d.n + k];
+        xs[c] = (tg & 2) ? x : x + 0.5 * dt * u;
+        us[c] = (tg & 2) ? u : u + 0.5 * dt * af[c];
+        finite = finite && isfinite(us[c]) && isfinite(xs[c]);
+    }
+    float4 p = cell_offset<DIM>(g, d.cell[k], xs);
+    // the neighbour list stays complete while no particle is farther than the
+    // skin from where it was at the build
+    const float4 p0 = d.pos0[k];
+    const float ex = p.x - p0.x, ey = p.y - p0.y, ez = p.z - p0.z;
+    if (ex * ex + ey * ey + ez * ez > (float)(ph.skin * ph.skin)) atomicOr(d.flags, FLAG_SKIN);
+    float vol;
+    p.w = signed_volume(ph, tg & 1, drs, vol);
+    d.pos[k] = p;
+    d.vd[k] = vol * drs;
+    d.velq[k] = make_float4((float)us[0], (float)us[1], (float)us[2], 0.f);
+    if (!finite) atomicOr(d.flags, FLAG_NONFINITE);
+}
+
+// Corrector: x^{n+1} = x^n + dt u*, u^{n+1} = u^n + dt a*, rho^{n+1} = rho^n +
+// dt Drho*, in the FP64 accumulators (walls keep x and u).  Writes the
+// stage-1 records of the next step and decides whether it rebuilds the lists.
+template <int DIM>
+__device__ __forceinline__ void correct_particle(const Dev &d, const Grid &g, const Phys &ph, int k, float4 a,
+                                                 double dt)
+{
+    if (k == 0) {
+        const long long next = *d.step + 1;
+        *d.step = next;
+        if (ph.rebuild_every > 0 && next % ph.rebuild_every == 0) *d.rebuild = 1u;
+    }
+    const uint8_t tg = d.tag[k];
+    const float dr = fmaf((float)dt, a.w, d.drho[k]);
+    d.drho[k] = dr;
+    bool finite = isfinite(dr);
+    double xa[3] = {0, 0, 0}, ua[3] = {0, 0, 0};
+    const float4 us = d.velq[k];
+    const double usa[3] = {us.x, us.y, us.z};
+    const double af[3] = {a.x, a.y, a.z};
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+        xa[c] = d.x[(size_t)c * d.n + k];
+        ua[c] = d.u[(size_t)c * d.n + k];
+        if (!(tg & 2)) {
+            xa[c] += dt * usa[c];
+            ua[c] += dt * af[c];
+            d.x[(size_t)c * d.n + k] = xa[c];
+            d.u[(size_t)c * d.n + k] = ua[c];
+        }
+        finite = finite && isfinite(xa[c]) && isfinite(ua[c]);
+    }
+    if (!finite) atomicOr(d.flags, FLAG_NONFINITE);
+    // stage-1 records of the next step (replaced by the gather if it rebuilds)
+    stage_records<DIM>(d, g, ph, k, d.cell[k], xa, ua, dr, tg & 1);
+    if (ph.rebuild_every == 0 && !(tg & 2)) {
+        // next step's stage positions: x^{n+1} and x^{n+1} + dt/2 u^{n+1};
+        // rebuild before either can be farther than the skin from the build
+        const float4 p = d.pos[k], p0 = d.pos0[k];
+        const float hx = 0.5f * (float)dt * (float)ua[0], hy = 0.5f * (float)dt * (float)ua[1],
+                    hz = 0.5f * (float)dt * (float)ua[2];
+        const float ex = p.x - p0.x, ey = p.y - p0.y, ez = p.z - p0.z;
+        const float d1 = ex * ex + ey * ey + ez * ez;
+        const float d2 = (ex + hx) * (ex + hx) + (ey + hy) * (ey + hy) + (ez + hz) * (ez + hz);
+        const float lim = (float)(0.98 * ph.skin);
+        if (fmaxf(d1, d2) > lim * lim) atomicOr(d.rebuild, 1u);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Sweep A: per-phase renormalisation (Eq. ct_dist_3), colour-index gradient
 // (Eq. cd) and surface stress tensor (Eq. csf), equation of state (Eq. state).
 //
@@ -506,7 +597,8 @@ __global__ void __launch_bounds__(256, 4) k_build_list(Dev d, Grid g, Phys ph)
 // The colour gradient uses the density that entered the stage:
 // grad C_i = (1/V_i) sum_{j other phase} V_j^2 grad W_ij, V = m/rho = 1/sigma.
 template <int DIM>
-__global__ void __launch_bounds__(256) k_sweep_a(Dev d, Grid g, Phys ph, const float *__restrict__ drho_in, int stage1)
+__global__ void __launch_bounds__(256) k_sweep_a(Dev d, Grid g, Phys ph, const float *__restrict__ drho_in, int stage1,
+                                                 float4 *vel_s)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.n) return;
@@ -599,7 +691,7 @@ __global__ void __launch_bounds__(256) k_sweep_a(Dev d, Grid g, Phys ph, const f
     // rounding of m/rho itself
     const float vs = phi_ ? -vol : vol;
     d.posv[i] = make_float4(oi.x, oi.y, oi.z, __uint_as_float((__float_as_uint(vs) & ~1u) | iface));
-    d.velp[i].w = P / (rho * rho);
+    vel_s[i].w = P / (rho * rho);
     d.pres[i] = P;
     d.T4[i] = t4;
     if (DIM == 3) d.T2[i] = t2;
@@ -610,15 +702,17 @@ __global__ void __launch_bounds__(256) k_sweep_a(Dev d, Grid g, Phys ph, const f
 // (Eq. visc_2 or visc_1), surface tension (F_s/rho), gravity, continuity
 // (Eq. ct_dist_2).  grad_i W_ij = cF t^3 r_ij with t = 1 - q/2; the common
 // factor cF is applied once per particle.
-template <int DIM>
-__global__ void __launch_bounds__(256, 4) k_sweep_b(Dev d, Grid g, Phys ph)
+// STAGE 0: rates only; 1: then the predictor; 2: then the corrector.
+template <int DIM, int STAGE>
+__global__ void __launch_bounds__(256, 4) k_sweep_b(Dev d, Grid g, Phys ph, double dt)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.n) return;
     const float4 oi = d.posv[i];
     const int phi_ = phase_of(oi.w);
     const unsigned iface_i = __float_as_uint(oi.w) & 1u;
-    const float4 ui = d.velp[i];             // w: P_i / rho_i^2
+    const float4 *__restrict__ vel_s = STAGE == 2 ? d.velq : d.velp;
+    const float4 ui = vel_s[i];              // w: P_i / rho_i^2
     const float4 Ti = d.T4[i];
     const float2 Ti2 = DIM == 3 ? d.T2[i] : make_float2(0.f, 0.f);
     float px = 0.f, py = 0.f, pz = 0.f;    // sum m_j (P_i/rho_i^2 + P_j/rho_j^2) t^3 r_ij
@@ -632,7 +726,6 @@ __global__ void __launch_bounds__(256, 4) k_sweep_b(Dev d, Grid g, Phys ph)
     const float kv_wat = phi_ ? ph.kvis[2] : ph.kvis[0], kv_oil = phi_ ? ph.kvis[3] : ph.kvis[1];
     const unsigned *__restrict__ col = d.nbr + i;
     const float4 *__restrict__ posv = d.posv;
-    const float4 *__restrict__ velp = d.velp;
     const float4 *__restrict__ T4 = d.T4;
     const float2 *__restrict__ T2 = d.T2;
     constexpr int CH = SPH_LIST_CHUNK;
@@ -652,7 +745,7 @@ __global__ void __launch_bounds__(256, 4) k_sweep_b(Dev d, Grid g, Phys ph)
             const unsigned e = ec[c];
             const int j = (int)(e & NBR_IDX_MASK);
             const float4 oj = __ldg(posv + j);
-            const float4 uj = __ldg(velp + j);
+            const float4 uj = __ldg(vel_s + j);
             float rx, ry, rz;
             const float r2 = pair_vec<DIM>(oi, oj, entry_shift(e, 0, cs), entry_shift(e, 1, cs),
                                            DIM == 3 ? entry_shift(e, 2, cs) : 0.f, rx, ry, rz);
@@ -709,94 +802,11 @@ __global__ void __launch_bounds__(256, 4) k_sweep_b(Dev d, Grid g, Phys ph)
         out.z = DIM == 3 ? -ph.cF * pz + vf * vz + sf * sz + ph.gf[2] : 0.f;
     }
     d.acc[i] = out;
+    if (STAGE == 1) predict_particle<DIM>(d, g, ph, i, out, dt);
+    if (STAGE == 2) correct_particle<DIM>(d, g, ph, i, out, dt);
 }
 
 // ---------------------------------------------------------------------------
-// Explicit midpoint predictor-corrector.
-
-template <int DIM>
-__global__ void __launch_bounds__(256) k_predict(Dev d, Grid g, Phys ph, double dt)
-{
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= d.n) return;
-    const uint8_t tg = d.tag[k];
-    const float4 a = d.acc[k];
-    const float dr = d.drho_eval[k];         // renormalised density becomes the state
-    d.drho[k] = dr;
-    const float drs = fmaf(0.5f * (float)dt, a.w, dr);
-    d.drho_stage[k] = drs;
-    double xs[3] = {0, 0, 0}, us[3] = {0, 0, 0};
-    const double af[3] = {a.x, a.y, a.z};
-    bool finite = isfinite(drs);
-#pragma unroll
-    for (int c = 0; c < DIM; ++c) {
-        const double x = d.x[(size_t)c * d.n + k], u = d.u[(size_t)c * d.n + k];
-        xs[c] = (tg & 2) ? x : x + 0.5 * dt * u;
-        us[c] = (tg & 2) ? u : u + 0.5 * dt * af[c];
-        finite = finite && isfinite(us[c]) && isfinite(xs[c]);
-    }
-    float4 p = cell_offset<DIM>(g, d.cell[k], xs);
-    // the neighbour list stays complete while no particle is farther than the
-    // skin from where it was at the build
-    const float4 p0 = d.pos0[k];
-    const float ex = p.x - p0.x, ey = p.y - p0.y, ez = p.z - p0.z;
-    if (ex * ex + ey * ey + ez * ez > (float)(ph.skin * ph.skin)) atomicOr(d.flags, FLAG_SKIN);
-    float vol;
-    p.w = signed_volume(ph, tg & 1, drs, vol);
-    d.pos[k] = p;
-    d.vd[k] = vol * drs;
-    d.velp[k] = make_float4((float)us[0], (float)us[1], (float)us[2], 0.f);
-    if (!finite) atomicOr(d.flags, FLAG_NONFINITE);
-}
-
-template <int DIM>
-__global__ void __launch_bounds__(256) k_correct(Dev d, Grid g, Phys ph, double dt)
-{
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= d.n) return;
-    if (k == 0) {
-        const long long next = *d.step + 1;
-        *d.step = next;
-        if (ph.rebuild_every > 0 && next % ph.rebuild_every == 0) *d.rebuild = 1u;
-    }
-    const uint8_t tg = d.tag[k];
-    const float4 a = d.acc[k];
-    const float dr = fmaf((float)dt, a.w, d.drho[k]);
-    d.drho[k] = dr;
-    bool finite = isfinite(dr);
-    double xa[3] = {0, 0, 0}, ua[3] = {0, 0, 0};
-    const float4 us = d.velp[k];
-    const double usa[3] = {us.x, us.y, us.z};
-    const double af[3] = {a.x, a.y, a.z};
-#pragma unroll
-    for (int c = 0; c < DIM; ++c) {
-        xa[c] = d.x[(size_t)c * d.n + k];
-        ua[c] = d.u[(size_t)c * d.n + k];
-        if (!(tg & 2)) {
-            xa[c] += dt * usa[c];
-            ua[c] += dt * af[c];
-            d.x[(size_t)c * d.n + k] = xa[c];
-            d.u[(size_t)c * d.n + k] = ua[c];
-        }
-        finite = finite && isfinite(xa[c]) && isfinite(ua[c]);
-    }
-    if (!finite) atomicOr(d.flags, FLAG_NONFINITE);
-    // stage-1 records of the next step (replaced by the gather if it rebuilds)
-    stage_records<DIM>(d, g, ph, k, d.cell[k], xa, ua, dr, tg & 1);
-    if (ph.rebuild_every == 0 && !(tg & 2)) {
-        // next step's stage positions: x^{n+1} and x^{n+1} + dt/2 u^{n+1};
-        // rebuild before either can be farther than the skin from the build
-        const float4 p = d.pos[k], p0 = d.pos0[k];
-        const float hx = 0.5f * (float)dt * (float)ua[0], hy = 0.5f * (float)dt * (float)ua[1],
-                    hz = 0.5f * (float)dt * (float)ua[2];
-        const float ex = p.x - p0.x, ey = p.y - p0.y, ez = p.z - p0.z;
-        const float d1 = ex * ex + ey * ey + ez * ez;
-        const float d2 = (ex + hx) * (ex + hx) + (ey + hy) * (ey + hy) + (ez + hz) * (ez + hz);
-        const float lim = (float)(0.98 * ph.skin);
-        if (fmaxf(d1, d2) > lim * lim) atomicOr(d.rebuild, 1u);
-    }
-}
-
 // ---------------------------------------------------------------------------
 // Neighbour sets and pair statistics by the sweeps' own support test.
 
