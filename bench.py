@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--workload", default="drop_3d", choices=["drop_3d", "drop_2d"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-steps", type=int, default=500,
+                    help="steps of the 256-instance batched comparison (0 skips it)")
     return ap.parse_args()
 
 
@@ -195,6 +197,75 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_batched(sph, WL, stream, steps, torch):
+    """256 uneven 2-D drop-rise instances advanced together (one persistent
+    launch per call, captured in a CUDA graph, launch shape autotuned) against
+    the same instances simulated one after another with the per-kernel path:
+    throughput, speedup and the drop-centroid error ||c_batch - c_plain|| / D
+    at equal physical time."""
+    ws_ = WL.drop_batch_2d(k=256, seed=3000)
+    dt, scales = WL.batch_dt(ws_)
+    n = sum(w.n for w in ws_)
+    bt = sph.Simulation.batch(ws_, stream=stream.cuda_stream)
+    bt.set_dt_scales(scales)
+    shape = bt.autotune(dt, trial_steps=10)
+    x0, u0, r0 = bt.read("pos"), bt.read("vel"), bt.read("rho")
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        a, b = ev(), ev()
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b)
+
+    # first pass captures the graph (untimed); the timed pass replays it from the same state
+    bt.run_persistent(dt, steps, graph=True)
+    xa = bt.read("pos")
+    bt.set_state(x0, u0, r0)
+    ms_persist = timed(lambda: bt.run_persistent(dt, steps, graph=True))
+    deterministic = bool(np.array_equal(xa, bt.read("pos")))
+    diag_b = bt.diagnostics_instances()
+    # the same batch through the per-kernel launch sequence (graph per step)
+    bt.set_state(x0, u0, r0)
+    kl = min(steps, 100)
+    bt.run(dt, 3, graph=True)
+    ms_launch = timed(lambda: bt.run(dt, kl, graph=True)) * steps / kl
+    bt.close()
+    # plain: every instance alone, one after another
+    sims = [sph.Simulation.from_workload(w, stream=stream.cuda_stream) for w in ws_]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for q, sm in enumerate(sims):
+        sm.run(dt * scales[q], steps, graph=True)
+    torch.cuda.synchronize()
+    ms_plain = (time.perf_counter() - t0) * 1e3
+    errs = []
+    for q, (sm, w) in enumerate(zip(sims, ws_)):
+        c = sm.diagnostics()["centroid"]
+        errs.append(float(np.linalg.norm(diag_b[q]["centroid"] - c) / (2 * w.meta["drop_radius"])))
+        sm.close()
+    return {
+        "workload": "drop_batch_2d: 256 instances, D/dx log-uniform [8, 40], tank 4D x 8D + 3 wall layers",
+        "instances": 256, "particles": n, "steps": steps, "dt_max": dt,
+        "launch_shape": {"block": shape[0], "grid_blocks": shape[1], "dynamic_chunks": shape[2],
+                         "tuned_ms_per_step": shape[3]},
+        "persistent_graph_ms_per_step": ms_persist / steps,
+        "per_kernel_graph_ms_per_step": ms_launch / steps,
+        "plain_sequential_ms_per_step": ms_plain / steps,
+        "value_persistent": n * steps / (ms_persist / 1e3),
+        "unit": "particle-steps/s",
+        "speedup_persistent_vs_plain": ms_plain / ms_persist,
+        "speedup_per_kernel_batch_vs_plain": ms_plain / ms_launch,
+        "centroid_err_max_over_D": max(errs), "centroid_err_mean_over_D": float(np.mean(errs)),
+        "replay_bit_identical": deterministic,
+        "plain_timing": "host clock around 256 sequential 500-step graph runs (each ends in a sync)",
+    }
+
+
 def run_ours(args, ws, rank, local):
     import torch
     from paper_1702_07760_gb300 import build as B
@@ -305,6 +376,10 @@ def run_ours(args, ws, rank, local):
         cpu = {"value": rate, "unit": "particle-steps/s", "cores": cores, "kind": "oracle",
                "sample": f"{steps} FP64 oracle step(s) of the full {n}-particle workload"}
 
+    batched = None
+    if rank == 0 and ws == 1 and args.batch_steps > 0:
+        batched = run_batched(sph, WL, stream, args.batch_steps, torch)
+
     # count reset, hash, 3 scan, scatter, rank, gather, copy-back, list (these return at once on
     # steps without a rebuild), 2 sweep_a, 2 sweep_b (with the predictor / corrector)
     kernels_per_step = 14
@@ -322,6 +397,7 @@ def run_ours(args, ws, rank, local):
         "kernels": kernels,
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "batched": batched,
         "gpu_launches": kernels_per_step * args.steps,
         "clocks": clk,
     }

@@ -47,6 +47,7 @@ extern "C" {
 #define SPH_ECFL       -5  /* a particle moved farther in a step than the cell skin allows */
 #define SPH_EDOMAIN    -6  /* a particle left the box of the cell grid */
 #define SPH_ECAPACITY  -7  /* a particle has more neighbours than max_neighbours */
+#define SPH_ETIMEOUT   -8  /* a grid barrier of the persistent kernel gave up after one second */
 
 /* Viscous term forms (Sec. II-C) */
 #define SPH_VISC_DYNAMIC   0  /* Eq. visc_2: (1/rho_i) sum 2 mu_ij (m_j/rho_j) (r.gradW)/(r^2+delta^2) u_ij */
@@ -111,6 +112,28 @@ int sph_create(const sph_params *params, int64_t n, const double *x, const doubl
                const double *rho, const uint8_t *phase, const uint8_t *wall,
                void *stream, sph_handle *out);
 
+/* Creates ONE handle over k >= 1 independent instances (a batch of separate
+ * problems advanced together by every launch; the paper runs one problem at
+ * a time, so this packing is this library's).  params[q] holds instance q's
+ * parameters; all instances must share dim, h, gamma, delta, g, cell_size,
+ * skin, visc_form, renorm_every, rebuild_every and max_neighbours, and may
+ * differ in c0, alpha_s, rho0, mu, mass and box.  counts[q] particles belong
+ * to instance q; x, u, rho, phase and wall hold the instances one after
+ * another (instance 0's particles first), each in its own frame and box.
+ * The boxes are packed side by side in one cell grid (a shelf packing in the
+ * x-y plane) with gaps of 2h + 2 skin + 2 cell_size, so no two instances
+ * interact; every read returns positions in each instance's own frame.
+ * Particle ids run over the whole batch.  k <= 65535, total n <= 2^26.  A
+ * particle that leaves its own box but not the packed grid is not reported
+ * as SPH_EDOMAIN: walls keep particles inside in the intended use. */
+int sph_create_batch(int k, const sph_params *params, const int64_t *counts, const double *x,
+                     const double *u, const double *rho, const uint8_t *phase, const uint8_t *wall,
+                     void *stream, sph_handle *out);
+
+/* Per-instance step sizes: instance q advances by dt * scales[q] whenever the
+ * handle advances by dt (each scale in (0, 1]).  Default 1. */
+int sph_set_dt_scales(sph_handle h, const double *scales);
+
 /* Replaces the state (x, u, rho; same layout as sph_create) of an existing
  * handle with host data, keeping its parameters, phases and walls.  The step
  * counter is left as it is. */
@@ -137,8 +160,51 @@ int sph_step(sph_handle h, double dt);
  * a CUDA graph and replayed. */
 int sph_run(sph_handle h, double dt, int64_t nsteps, int graph);
 
+/* The same nsteps steps as sph_run in ONE cooperative kernel launch: every
+ * phase of the step (cell build when due, both sweeps of both stages) is a
+ * grid-stride loop over the particles, phases separated by a grid-wide
+ * barrier.  The results are bit-identical to sph_run's (same per-particle
+ * arithmetic and summation order).  Every barrier wait gives up after one
+ * second; the launch then returns early, the state is left partly advanced
+ * and the call returns SPH_ETIMEOUT.  The launch uses the shape set by
+ * sph_set_launch_shape or chosen by sph_autotune (default: 256 threads, as
+ * many blocks per SM as fit).  With graph != 0 the launch is captured into a
+ * CUDA graph (re-captured when dt, nsteps or the shape changes).  Waits for
+ * the stream.  nsteps < 2^31. */
+int sph_run_persistent(sph_handle h, double dt, int64_t nsteps, int graph);
+
+/* Launch shape of sph_run_persistent: block in {128, 256, 512} threads,
+ * grid_blocks blocks (clamped to what can be co-resident; 0 = as many as
+ * can), and how each phase's particles are shared out: dynamic_chunks = 1
+ * hands chunks of consecutive particles to warps from a grid-wide counter,
+ * 0 gives each thread a fixed grid-stride share.  Shapes of at most 512
+ * threads per SM run a build of the kernel with up to 128 registers a
+ * thread, the others one with 64.  sph_get_launch_shape returns the shape
+ * with the grid it gives on the current device.  Default: 256, 0, 1. */
+int sph_set_launch_shape(sph_handle h, int block, int grid_blocks, int dynamic_chunks);
+int sph_get_launch_shape(sph_handle h, int *block, int *grid_blocks, int *dynamic_chunks);
+
+/* Times sph_run_persistent over trial_steps steps of size dt for every block
+ * size in {128, 256, 512} with grids of every co-resident multiple of the SM
+ * count, and, where the particles are fewer than twice such a grid's
+ * threads, of 1/2, 1/4, 1/8 and 1/19 of the SM count, each with both ways of
+ * sharing out particles; keeps the fastest shape and writes it and its
+ * milliseconds per step to the non-NULL outputs.
+ * Each trial starts from the state at entry; afterwards the state, the step
+ * counter and the build counter are put back as they were (the next step
+ * rebuilds the lists). */
+int sph_autotune(sph_handle h, double dt, int trial_steps, int *best_block, int *best_grid_blocks,
+                 int *best_dynamic_chunks, double *best_ms_per_step);
+
 /* Waits for the stream and reports any device-side error flag. */
 int sph_sync(sph_handle h);
+
+/* Test support for the barrier time-out (no counterpart in the paper): puts
+ * the persistent kernel's grid barrier in a state that no arrival completes,
+ * so that the next sph_run_persistent waits out its one-second limit in every
+ * block and returns SPH_ETIMEOUT, after which the barrier is reset and runs
+ * work again.  The state advanced by that call is undefined. */
+int sph_test_stall_barrier(sph_handle h);
 
 /* Copies a field (SPH_FIELD_*) into host memory in original particle order.
  * bytes must be at least the field's size (see the field list). */
@@ -165,6 +231,11 @@ int sph_pair_stats(sph_handle h, int64_t out[2]);
  *   oil positions, out[10] max |u|, out[11] number of oil particles. */
 int sph_diag(sph_handle h, double out[12]);
 
+/* sph_diag for every instance of a batch: out holds 12 doubles per instance
+ * (instance q at out[12 q], same layout as sph_diag, positions in the
+ * instance's own frame).  sph_diag on a batch reports instance 0. */
+int sph_diag_instances(sph_handle h, double *out);
+
 /* Per-kernel timing with CUDA events on the simulation's stream.  While
  * enabled, every launch is bracketed by events; sph_timing_read returns, for
  * kernel index k (0 <= k < sph_timing_count()), its name, launch count and
@@ -178,10 +249,12 @@ int sph_timing_read(sph_handle h, int k, const char **name, int64_t *launches, d
  * stream), or a negative error code. */
 int64_t sph_list_builds(sph_handle h);
 
-/* Number of particles, step counter, grid cells. */
+/* Number of particles (all instances), step counter, grid cells. */
 int64_t sph_num_particles(sph_handle h);
 int64_t sph_step_index(sph_handle h);
 int64_t sph_num_cells(sph_handle h);
+/* Number of instances (1 unless created by sph_create_batch). */
+int64_t sph_num_instances(sph_handle h);
 
 void sph_destroy(sph_handle h);
 

@@ -1,6 +1,8 @@
 // Host side of the C ABI declared in include/sph.h: parameter validation,
-// device memory, the per-step launch sequence, CUDA-graph replay, reads in
-// original particle order, FP64 diagnostics and per-kernel event timing.
+// device memory, the per-step launch sequence, CUDA-graph replay, the
+// persistent cooperative form and its launch-shape autotuner, batches of
+// independent instances, reads in original particle order, FP64 diagnostics
+// and per-kernel event timing.
 #include "sph.h"
 #include "sph_kernels.cuh"
 
@@ -10,6 +12,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <numeric>
 #include <string>
 #include <vector>
 
@@ -34,17 +37,47 @@ int fail(int code, const std::string &msg)
 
 enum KernelId {
     KI_MEMSET, KI_HASH, KI_SCAN, KI_SCATTER, KI_RANK, KI_GATHER, KI_COPY, KI_LIST, KI_SWEEP_A, KI_SWEEP_B,
-    KI_COUNT
+    KI_PERSISTENT, KI_COUNT
 };
-// sweep_b includes the predictor (stage 1) or the corrector (stage 2)
+// sweep_b includes the predictor (stage 1) or the corrector (stage 2);
+// persistent_steps is one cooperative launch running whole steps
 const char *k_names[KI_COUNT] = {"count_reset", "cell_hash", "cell_scan", "cell_scatter",
                                  "cell_rank", "reorder_gather", "reorder_copy", "neighbour_list",
-                                 "sweep_a", "sweep_b"};
+                                 "sweep_a", "sweep_b", "persistent_steps"};
 
 struct PendingTiming {
     int id;
     cudaEvent_t a, b;
 };
+
+// Block sizes the persistent kernel is compiled for.  Each size has two
+// register budgets: 64 registers a thread (up to 1024 resident threads an
+// SM) and 128 (up to 512 threads); a shape with at most 512 threads an SM
+// takes the second.
+constexpr int PERSIST_BS[3] = {128, 256, 512};
+
+template <int DIM, int BS, int TPSM>
+__global__ void __launch_bounds__(BS, TPSM / BS) k_persistent_bs(Dev d, Dev scratch, Grid g, Phys ph, Sort s,
+                                                                  GridBarrier *bar, double dt, int nsteps, int dyn)
+{
+    persistent_steps<DIM>(d, scratch, g, ph, s, bar, dt, nsteps, dyn);
+}
+
+using PersistFn = void (*)(Dev, Dev, Grid, Phys, Sort, GridBarrier *, double, int, int);
+
+template <int DIM, int TPSM>
+PersistFn persist_fn_t(int bs)
+{
+    if (bs == 128) return k_persistent_bs<DIM, 128, TPSM>;
+    if (bs == 256) return k_persistent_bs<DIM, 256, TPSM>;
+    return k_persistent_bs<DIM, 512, TPSM>;
+}
+
+PersistFn persist_fn(int dim, int bs, bool wide)
+{
+    if (dim == 2) return wide ? persist_fn_t<2, 512>(bs) : persist_fn_t<2, 1024>(bs);
+    return wide ? persist_fn_t<3, 512>(bs) : persist_fn_t<3, 1024>(bs);
+}
 
 }  // namespace
 
@@ -52,22 +85,27 @@ struct sph_sim {
     sph_params P{};
     int dim = 0;
     int n = 0;
+    int ninst = 1;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     Grid grid{};
     Phys phys{};
     int ncell = 0;
     int ntiles = 0;
-    Dev buf[2]{};
-    int cur = 0;
-    int *cell_tmp = nullptr, *slot = nullptr, *count = nullptr, *tmp = nullptr, *perm = nullptr,
-        *tile_sums = nullptr;
+    Dev buf[2]{};                         // buf[0]: the state; buf[1]: reorder scratch
+    Sort sort{};
+    std::vector<Inst> hinst;
+    Inst *dinst = nullptr;
+    std::vector<int64_t> first;           // instance q owns original ids [first[q], first[q+1])
+    long long *dfirst = nullptr;
     unsigned *flags = nullptr;
     unsigned *rebuild = nullptr;
     long long *dstep = nullptr;
     long long *dbuilds = nullptr;
+    GridBarrier *bar = nullptr;
+    unsigned long long *pair_tot = nullptr;
     double last_dt = 0.0;
-    double *diag_partial = nullptr, *diag_small = nullptr;
+    double *diag_out = nullptr, *diag_grav = nullptr;
     double *read_buf = nullptr;
     int *read_ibuf = nullptr;
     int64_t step = 0;
@@ -78,11 +116,18 @@ struct sph_sim {
     std::vector<cudaEvent_t> free_events;
     int64_t t_launches[KI_COUNT] = {};
     double t_ms[KI_COUNT] = {};
-    // graph of one step (gexec[0]), replayed while dt matches gdt[0]
-    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-    double gdt[2] = {0.0, 0.0};
+    // per-launch graph of one step, replayed while dt matches
+    cudaGraphExec_t gexec = nullptr;
+    double gdt = 0.0;
+    // persistent form: launch shape and its graph
+    int pbs = 256, pgrid = 0;             // block size, grid blocks (0: as many as fit)
+    int pdyn = 1;                         // particle loops: 1 dynamic chunks, 0 grid-stride
+    cudaGraphExec_t pexec = nullptr;
+    double pdt = 0.0;
+    int64_t psteps = 0;
+    int pshape = 0;
 
-    Dev &D() { return buf[cur]; }
+    Dev &D() { return buf[0]; }
 
     template <class T>
     int alloc(T **p, size_t count_) {
@@ -141,6 +186,8 @@ struct sph_sim {
     void enqueue_build_cells(bool force);
     void enqueue_eval(int stage, const float *drho_in, double dt);
     void enqueue_step(double dt);
+    int persistent_shape(int bs, int grid_req, int *grid_out, PersistFn *fn_out);
+    int launch_persistent(double dt, int nsteps);
     int check_flags();
 };
 
@@ -153,21 +200,21 @@ void sph_sim::enqueue_build_cells(bool force)
     Dev &s = buf[0];
     Dev &t = buf[1];
     if (force) cudaMemsetAsync(rebuild, 0xff, sizeof(unsigned), stream);
-    launch(KI_MEMSET, [&] { k_zero<<<blocks(ncell), 256, 0, stream>>>(count, ncell, rebuild); });
+    launch(KI_MEMSET, [&] { k_zero<<<blocks(ncell), 256, 0, stream>>>(sort.count, ncell, rebuild); });
     launch(KI_HASH, [&] {
-        if (dim == 2) k_hash<2><<<blocks(n), 256, 0, stream>>>(s, grid, cell_tmp, slot, count);
-        else k_hash<3><<<blocks(n), 256, 0, stream>>>(s, grid, cell_tmp, slot, count);
+        if (dim == 2) k_hash<2><<<blocks(n), 256, 0, stream>>>(s, grid, sort);
+        else k_hash<3><<<blocks(n), 256, 0, stream>>>(s, grid, sort);
     });
     launch(KI_SCAN, [&] {
-        k_scan_tiles<<<ntiles, SCAN_THREADS, 0, stream>>>(count, s.cstart, tile_sums, ncell, rebuild);
-        k_scan_sums<<<1, SCAN_THREADS, 0, stream>>>(tile_sums, ntiles, s.cstart, ncell, rebuild);
-        k_scan_add<<<blocks(ncell), 256, 0, stream>>>(s.cstart, tile_sums, ncell, rebuild);
+        k_scan_tiles<<<ntiles, SCAN_THREADS, 0, stream>>>(sort.count, s.cstart, sort.tile_sums, ncell, rebuild);
+        k_scan_sums<<<1, SCAN_THREADS, 0, stream>>>(sort.tile_sums, ntiles, s.cstart, ncell, rebuild);
+        k_scan_add<<<blocks(ncell), 256, 0, stream>>>(s.cstart, sort.tile_sums, ncell, rebuild);
     });
-    launch(KI_SCATTER, [&] { k_scatter<<<blocks(n), 256, 0, stream>>>(n, cell_tmp, slot, s.cstart, tmp, rebuild); });
-    launch(KI_RANK, [&] { k_rank<<<blocks(n), 256, 0, stream>>>(n, tmp, cell_tmp, s.pid, s.cstart, perm, rebuild); });
+    launch(KI_SCATTER, [&] { k_scatter<<<blocks(n), 256, 0, stream>>>(n, sort, s.cstart, rebuild); });
+    launch(KI_RANK, [&] { k_rank<<<blocks(n), 256, 0, stream>>>(n, sort, s.pid, s.cstart, rebuild); });
     launch(KI_GATHER, [&] {
-        if (dim == 2) k_gather<2><<<blocks(n), 256, 0, stream>>>(s, t, grid, phys, perm, cell_tmp);
-        else k_gather<3><<<blocks(n), 256, 0, stream>>>(s, t, grid, phys, perm, cell_tmp);
+        if (dim == 2) k_gather<2><<<blocks(n), 256, 0, stream>>>(s, t, grid, sort);
+        else k_gather<3><<<blocks(n), 256, 0, stream>>>(s, t, grid, sort);
     });
     launch(KI_COPY, [&] {
         if (dim == 2) k_copy_back<2><<<blocks(n), 256, 0, stream>>>(t, s);
@@ -211,6 +258,48 @@ void sph_sim::enqueue_step(double dt)
     enqueue_eval(2, d.drho_stage, dt);
 }
 
+// Grid and kernel build of a persistent launch of grid_req blocks of bs
+// threads (0: as many as can be co-resident); never more blocks than fit.
+int sph_sim::persistent_shape(int bs, int grid_req, int *grid_out, PersistFn *fn_out)
+{
+    int dev = 0, sms = 0, fit = 0;
+    CU(cudaGetDevice(&dev));
+    CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const bool wide = grid_req > 0 && bs * ((grid_req + sms - 1) / sms) <= 512;
+    PersistFn fn = persist_fn(dim, bs, wide);
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, (const void *)fn, bs, 0));
+    if (fit < 1) return fail(SPH_ECUDA, "the persistent kernel does not fit an SM");
+    *grid_out = grid_req > 0 ? std::min(grid_req, fit * sms) : fit * sms;
+    if (fn_out) *fn_out = fn;
+    return SPH_OK;
+}
+
+// Cooperative launch (all blocks co-resident, or the launch fails), through
+// cudaLaunchKernelEx so that it can be captured into a graph.
+int sph_sim::launch_persistent(double dt, int nsteps)
+{
+    int gsz = 0;
+    PersistFn fn = nullptr;
+    int rc = persistent_shape(pbs, pgrid, &gsz, &fn);
+    if (rc) return rc;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(gsz);
+    cfg.blockDim = dim3(pbs);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaSuccess;
+    launch(KI_PERSISTENT, [&] {
+        e = cudaLaunchKernelEx(&cfg, fn, buf[0], buf[1], grid, phys, sort, bar, dt, nsteps, pdyn);
+    });
+    if (e != cudaSuccess) return fail(SPH_ECUDA, std::string("persistent launch: ") + cudaGetErrorString(e));
+    return SPH_OK;
+}
+
 int sph_sim::check_flags()
 {
     unsigned f = 0;
@@ -219,6 +308,12 @@ int sph_sim::check_flags()
     if (timing) collect_timing();
     if (f == 0) return SPH_OK;
     CU(cudaMemsetAsync(flags, 0, sizeof(unsigned), stream));
+    if (f & FLAG_TIMEOUT) {
+        // a block gave up at a barrier: start the next launch from a clean barrier
+        CU(cudaMemsetAsync(bar, 0, sizeof(GridBarrier), stream));
+        CU(cudaStreamSynchronize(stream));
+        return fail(SPH_ETIMEOUT, "a grid barrier of the persistent kernel waited longer than one second");
+    }
     // the most specific cause first: a step too large for the skin often
     // also sends particles out of the box or produces non-finite values
     if (f & FLAG_SKIN) return fail(SPH_ECFL, "a particle moved beyond the cell skin within a step; reduce dt or enlarge cell_size");
@@ -236,16 +331,19 @@ int set_error(int code, const std::string &msg) { return fail(code, msg); }
 
 namespace {
 
-__global__ void k_load_state(Dev d, Phys ph, int dim, const double *x, const double *u, const double *rho)
+// Copies the caller's state (original order, each instance in its own frame)
+// into the sorted device state.
+__global__ void k_load_state(Dev d, int dim, const double *x, const double *u, const double *rho)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= d.n) return;
     const int p = d.pid[k];
+    const Inst &I = d.inst[d.iid[k]];
     for (int c = 0; c < dim; ++c) {
-        d.x[(size_t)c * d.n + k] = x[(size_t)p * dim + c];
+        d.x[(size_t)c * d.n + k] = x[(size_t)p * dim + c] + I.offset[c];
         d.u[(size_t)c * d.n + k] = u[(size_t)p * dim + c];
     }
-    d.drho[k] = (float)(rho[p] - (double)ph.rho0[d.tag[k] & 1]);
+    d.drho[k] = (float)(rho[p] - (double)by_phase(d.tag[k] & 1, I.rho0));
 }
 
 __global__ void k_iota(int *p, int n)
@@ -254,7 +352,7 @@ __global__ void k_iota(int *p, int n)
     if (k < n) p[k] = k;
 }
 
-int validate(const sph_params *P, int64_t n)
+int validate(const sph_params *P)
 {
     if (!P) return fail(SPH_EINVAL, "params is NULL");
     if (P->dim != 2 && P->dim != 3) return fail(SPH_EINVAL, "dim must be 2 or 3");
@@ -282,11 +380,47 @@ int validate(const sph_params *P, int64_t n)
         if (!(P->box_hi[k] > P->box_lo[k])) return fail(SPH_EINVAL, "box_hi must exceed box_lo");
         if (!std::isfinite(P->g[k])) return fail(SPH_EINVAL, "g must be finite");
     }
-    if (n < 0 || n > ((int64_t)1 << 26)) return fail(SPH_EINVAL, "n must be in [0, 2^26]");
     return SPH_OK;
 }
 
+// Parameters every instance of a batch must share (they are compiled into
+// the shared constants or the shared cell grid).
+bool same_shared(const sph_params &a, const sph_params &b)
+{
+    bool same = a.dim == b.dim && a.visc_form == b.visc_form && a.renorm_every == b.renorm_every &&
+                a.max_neighbours == b.max_neighbours && a.rebuild_every == b.rebuild_every && a.h == b.h &&
+                a.gamma == b.gamma && a.delta == b.delta && a.cell_size == b.cell_size && a.skin == b.skin;
+    for (int c = 0; c < 3; ++c) same = same && a.g[c] == b.g[c];
+    return same;
+}
+
 double harmonic(double a, double b) { return a + b > 0 ? 2.0 * a * b / (a + b) : 0.0; }
+
+// Per-instance constants: masses, reference densities, the Tait stiffness
+// rho0 c0^2 / gamma (Eq. eos), the harmonic-mean viscosity pairs (Sec. II-C)
+// and the surface-tension coefficient.
+Inst make_inst(const sph_params &P)
+{
+    Inst I{};
+    for (int k = 0; k < 2; ++k) {
+        I.mass[k] = (float)P.mass[k];
+        I.mass64[k] = P.mass[k];
+        I.inv_mass[k] = (float)(1.0 / P.mass[k]);
+        I.rho0[k] = (float)P.rho0[k];
+        I.inv_rho0[k] = (float)(1.0 / P.rho0[k]);
+        I.beta[k] = (float)(P.rho0[k] * P.c0 * P.c0 / P.gamma);
+    }
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) {
+            const double kv = P.visc_form == SPH_VISC_DYNAMIC
+                                  ? 2.0 * harmonic(P.mu[a], P.mu[b])
+                                  : 2.0 * harmonic(P.mu[a] / P.rho0[a], P.mu[b] / P.rho0[b]);
+            I.kvis[2 * a + b] = (float)kv;
+        }
+    I.alpha_s = (float)P.alpha_s;
+    I.dt_scale = 1.0;
+    return I;
+}
 
 // Eigenvalues of a symmetric 3x3 matrix by the trigonometric closed form.
 void eig3(const double A[6], double &lmin, double &lmax)
@@ -311,44 +445,132 @@ void eig3(const double A[6], double &lmin, double &lmax)
     lmin = q + 2.0 * p * std::cos(phi + 2.0 * pi / 3.0);
 }
 
-}  // namespace
+// Places instance boxes (extents w[q] along x, hgt[q] along y) on shelves in
+// the x-y plane, tallest first, at least `gap` apart, each lower corner on a
+// multiple of `align`; returns the corners and the extent of the packing.
+void shelf_pack(const std::vector<double> &w, const std::vector<double> &hgt, double gap, double align,
+                std::vector<double> &ox, std::vector<double> &oy, double &width, double &height)
+{
+    auto up = [align](double v) { return std::ceil(v / align - 1e-9) * align; };
+    const size_t k = w.size();
+    std::vector<size_t> order(k);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return hgt[a] > hgt[b]; });
+    double area = 0.0, wmax = 0.0;
+    for (size_t q = 0; q < k; ++q) {
+        area += (w[q] + gap) * (hgt[q] + gap);
+        wmax = std::max(wmax, w[q] + gap);
+    }
+    const double limit = std::max(wmax, 1.2 * std::sqrt(area));
+    ox.assign(k, 0.0);
+    oy.assign(k, 0.0);
+    double x = 0.0, y = 0.0, row_h = 0.0;
+    width = 0.0;
+    for (size_t idx = 0; idx < k; ++idx) {
+        const size_t q = order[idx];
+        if (x > 0.0 && x + w[q] > limit) {
+            y = up(y + row_h + gap);
+            x = 0.0;
+            row_h = 0.0;
+        }
+        ox[q] = x;
+        oy[q] = y;
+        x = up(x + w[q] + gap);
+        row_h = std::max(row_h, hgt[q]);
+        width = std::max(width, ox[q] + w[q]);
+    }
+    height = y + row_h;
+}
 
-extern "C" {
-
-const char *sph_last_error(void) { return g_err.c_str(); }
-
-int sph_create(const sph_params *params, int64_t n, const double *x, const double *u, const double *rho,
-               const uint8_t *phase, const uint8_t *wall, void *stream, sph_handle *out)
+// Shared creation path of sph_create and sph_create_batch.
+int create_sim(const sph_params *params, int k, const int64_t *counts, const double *x, const double *u,
+               const double *rho, const uint8_t *phase, const uint8_t *wall, void *stream, sph_handle *out)
 {
     if (!out) return fail(SPH_EINVAL, "out is NULL");
     *out = nullptr;
-    int rc = validate(params, n);
-    if (rc) return rc;
+    if (k < 1 || k > 65535) return fail(SPH_EINVAL, "the number of instances must be in [1, 65535]");
+    int64_t n = 0;
+    for (int q = 0; q < k; ++q) {
+        int rc = validate(params + q);
+        if (rc) return rc;
+        if (!same_shared(params[0], params[q]))
+            return fail(SPH_EINVAL, "instances of a batch must share dim, h, gamma, delta, g, cell_size, skin, "
+                                    "visc_form, renorm_every, rebuild_every and max_neighbours");
+        if (counts[q] < 0) return fail(SPH_EINVAL, "instance particle counts must be >= 0");
+        n += counts[q];
+        if (n > ((int64_t)1 << 26)) return fail(SPH_EINVAL, "n must be in [0, 2^26]");
+    }
     if (n > 0 && (!x || !u || !rho || !phase || !wall)) return fail(SPH_EINVAL, "an input array is NULL");
-    const sph_params &P = *params;
-    const int dim = P.dim;
+    const sph_params &P0 = params[0];
+    const int dim = P0.dim;
     // host-side checks of the particle data
-    for (int64_t i = 0; i < n; ++i) {
-        if (phase[i] > 1) return fail(SPH_EINVAL, "phase must be 0 (water) or 1 (oil)");
-        if (wall[i] > 1) return fail(SPH_EINVAL, "wall must be 0 or 1");
-        if (wall[i] && phase[i] != 0) return fail(SPH_EINVAL, "wall particles must be water (phase 0)");
-        if (!(rho[i] > 0) || !std::isfinite(rho[i])) return fail(SPH_EINVAL, "rho must be positive and finite");
-        for (int c = 0; c < dim; ++c) {
-            const double xc = x[i * dim + c];
-            if (!std::isfinite(xc) || !std::isfinite(u[i * dim + c]))
-                return fail(SPH_EINVAL, "x and u must be finite");
-            if (xc < P.box_lo[c] || xc > P.box_hi[c]) return fail(SPH_EINVAL, "a particle lies outside the box");
-        }
+    {
+        int64_t i = 0;
+        for (int q = 0; q < k; ++q)
+            for (int64_t c = 0; c < counts[q]; ++c, ++i) {
+                if (phase[i] > 1) return fail(SPH_EINVAL, "phase must be 0 (water) or 1 (oil)");
+                if (wall[i] > 1) return fail(SPH_EINVAL, "wall must be 0 or 1");
+                if (wall[i] && phase[i] != 0) return fail(SPH_EINVAL, "wall particles must be water (phase 0)");
+                if (!(rho[i] > 0) || !std::isfinite(rho[i])) return fail(SPH_EINVAL, "rho must be positive and finite");
+                for (int a = 0; a < dim; ++a) {
+                    const double xc = x[i * dim + a];
+                    if (!std::isfinite(xc) || !std::isfinite(u[i * dim + a]))
+                        return fail(SPH_EINVAL, "x and u must be finite");
+                    if (xc < params[q].box_lo[a] || xc > params[q].box_hi[a])
+                        return fail(SPH_EINVAL, "a particle lies outside the box");
+                }
+            }
     }
     sph_sim *s = new sph_sim();
-    s->P = P;
+    s->P = P0;
     s->dim = dim;
     s->n = (int)n;
+    s->ninst = k;
+    // instance placement in the shared grid: a single instance keeps its own
+    // box; a batch is shelf-packed in the x-y plane with gaps wider than the
+    // list radius plus two cells, so no neighbour pair joins two instances.
+    // Each instance's box corner sits on a super-cell boundary of the shared
+    // grid, so its particles see the same cell geometry (and the same pair
+    // arithmetic, up to FP64 rounding of the shifted positions) as alone.
+    const double RL = 2.0 * P0.h + 2.0 * P0.skin;
+    s->hinst.resize(k);
+    double box_lo[3] = {0, 0, 0}, box_hi[3] = {0, 0, 0};
+    if (k == 1) {
+        s->hinst[0] = make_inst(P0);
+        for (int a = 0; a < dim; ++a) {
+            box_lo[a] = P0.box_lo[a];
+            box_hi[a] = P0.box_hi[a];
+        }
+    } else {
+        std::vector<double> w(k), hg(k), ox, oy;
+        double zmax = 0.0;
+        for (int q = 0; q < k; ++q) {
+            w[q] = params[q].box_hi[0] - params[q].box_lo[0];
+            hg[q] = params[q].box_hi[1] - params[q].box_lo[1];
+            if (dim == 3) zmax = std::max(zmax, params[q].box_hi[2] - params[q].box_lo[2]);
+        }
+        double width = 0.0, height = 0.0;
+        const double gap = RL + 2.0 * P0.cell_size;
+        const double E = (P0.cell_size >= RL ? 1.0 : 2.0) * P0.cell_size;
+        shelf_pack(w, hg, gap, E, ox, oy, width, height);
+        for (int q = 0; q < k; ++q) {
+            Inst I = make_inst(params[q]);
+            I.offset[0] = ox[q] - params[q].box_lo[0];
+            I.offset[1] = oy[q] - params[q].box_lo[1];
+            I.offset[2] = dim == 3 ? -params[q].box_lo[2] : 0.0;
+            s->hinst[q] = I;
+        }
+        box_hi[0] = width;
+        box_hi[1] = height;
+        box_hi[2] = dim == 3 ? zmax : 0.0;
+    }
+    s->first.assign(k + 1, 0);
+    for (int q = 0; q < k; ++q) s->first[q + 1] = s->first[q] + counts[q];
     // grid
     int dims[3] = {1, 1, 1};
     int64_t ncell = 1;
     for (int c = 0; c < dim; ++c) {
-        const double m = std::floor((P.box_hi[c] - P.box_lo[c]) / P.cell_size) + 1.0;
+        const double m = std::floor((box_hi[c] - box_lo[c]) / P0.cell_size) + 1.0;
         if (m > 1e9) {
             delete s;
             return fail(SPH_EINVAL, "cell grid too large");
@@ -365,46 +587,30 @@ int sph_create(const sph_params *params, int64_t n, const double *x, const doubl
     s->grid.nx = dims[0];
     s->grid.ny = dims[1];
     s->grid.nz = dims[2];
-    const double RL = 2.0 * P.h + 2.0 * P.skin;
-    s->grid.f = P.cell_size >= RL ? 1 : 2;
-    s->grid.csd = P.cell_size;
-    s->grid.cs = (float)P.cell_size;
-    s->grid.Ed = s->grid.f * P.cell_size;
+    s->grid.f = P0.cell_size >= RL ? 1 : 2;
+    s->grid.csd = P0.cell_size;
+    s->grid.cs = (float)P0.cell_size;
+    s->grid.Ed = s->grid.f * P0.cell_size;
     s->grid.Es = (float)s->grid.Ed;
-    for (int c = 0; c < 3; ++c) s->grid.lo[c] = c < dim ? P.box_lo[c] : 0.0;
-    // physics constants
+    for (int c = 0; c < 3; ++c) s->grid.lo[c] = box_lo[c];
+    // constants shared by all instances
     const double pi = 3.14159265358979323846;
-    const double h = P.h;
+    const double h = P0.h;
     const double alpha_d = dim == 2 ? 7.0 / (4.0 * pi * h * h) : 21.0 / (16.0 * pi * h * h * h);
     Phys &ph = s->phys;
     ph.inv_h = (float)(1.0 / h);
     ph.R2 = (float)(4.0 * h * h);
     ph.RL2 = (float)(RL * RL);
     ph.RP = (float)(RL * (1.0 + 1e-4));
-    ph.skin = P.skin;
-    ph.kmax = P.max_neighbours > 0 ? P.max_neighbours : (dim == 2 ? 48 : 128);
+    ph.skin = P0.skin;
+    ph.kmax = P0.max_neighbours > 0 ? P0.max_neighbours : (dim == 2 ? 48 : 128);
     ph.cF = (float)(-5.0 * alpha_d / (h * h));
-    for (int k = 0; k < 2; ++k) {
-        ph.mass[k] = (float)P.mass[k];
-        ph.inv_mass[k] = (float)(1.0 / P.mass[k]);
-        ph.rho0[k] = (float)P.rho0[k];
-        ph.inv_rho0[k] = (float)(1.0 / P.rho0[k]);
-        ph.beta[k] = (float)(P.rho0[k] * P.c0 * P.c0 / P.gamma);
-    }
-    for (int a = 0; a < 2; ++a)
-        for (int b = 0; b < 2; ++b) {
-            const double kv = P.visc_form == SPH_VISC_DYNAMIC
-                                  ? 2.0 * harmonic(P.mu[a], P.mu[b])
-                                  : 2.0 * harmonic(P.mu[a] / P.rho0[a], P.mu[b] / P.rho0[b]);
-            ph.kvis[2 * a + b] = (float)kv;
-        }
-    ph.delta2 = (float)(P.delta * P.delta);
-    ph.alpha_s = (float)P.alpha_s;
+    ph.delta2 = (float)(P0.delta * P0.delta);
     ph.inv_dim = (float)(1.0 / dim);
-    ph.visc_dynamic = P.visc_form == SPH_VISC_DYNAMIC;
-    ph.renorm_every = P.renorm_every;
-    ph.rebuild_every = P.rebuild_every;
-    for (int c = 0; c < 3; ++c) ph.gf[c] = c < dim ? (float)P.g[c] : 0.f;
+    ph.visc_dynamic = P0.visc_form == SPH_VISC_DYNAMIC;
+    ph.renorm_every = P0.renorm_every;
+    ph.rebuild_every = P0.rebuild_every;
+    for (int c = 0; c < 3; ++c) ph.gf[c] = c < dim ? (float)P0.g[c] : 0.f;
 
     auto cleanup = [&](int code) {
         for (void *p : s->allocs) cudaFree(p);
@@ -429,6 +635,7 @@ int sph_create(const sph_params *params, int64_t n, const double *x, const doubl
         err |= s->alloc(&d.drho, N);
         err |= s->alloc(&d.pid, N);
         err |= s->alloc(&d.tag, N);
+        err |= s->alloc(&d.iid, N);
     }
     Dev &a0 = s->buf[0];
     if (!err) {
@@ -453,50 +660,101 @@ int sph_create(const sph_params *params, int64_t n, const double *x, const doubl
         err |= s->alloc(&s->rebuild, 1);
         err |= s->alloc(&s->dstep, 1);
         err |= s->alloc(&s->dbuilds, 1);
-        err |= s->alloc(&s->cell_tmp, N);
-        err |= s->alloc(&s->slot, N);
-        err |= s->alloc(&s->count, (size_t)ncell);
-        err |= s->alloc(&s->tmp, N);
-        err |= s->alloc(&s->perm, N);
-        err |= s->alloc(&s->tile_sums, (size_t)s->ntiles);
-        err |= s->alloc(&s->diag_partial, (size_t)1024 * DIAG_K);
-        err |= s->alloc(&s->diag_small, 64);
+        err |= s->alloc(&s->bar, 1);
+        err |= s->alloc(&s->pair_tot, 2);
+        err |= s->alloc(&s->dinst, (size_t)k);
+        err |= s->alloc(&s->dfirst, (size_t)k + 1);
+        err |= s->alloc(&s->sort.cell_tmp, N);
+        err |= s->alloc(&s->sort.slot, N);
+        err |= s->alloc(&s->sort.count, (size_t)ncell);
+        err |= s->alloc(&s->sort.tmp, N);
+        err |= s->alloc(&s->sort.perm, N);
+        err |= s->alloc(&s->sort.tile_sums, (size_t)s->ntiles);
+        err |= s->alloc(&s->diag_out, (size_t)k * DIAG_STRIDE);
+        err |= s->alloc(&s->diag_grav, 4);
+        err |= s->alloc(&s->read_buf, N * 9 + 16);
+        err |= s->alloc(&s->read_ibuf, N);
     }
     if (err) return cleanup(SPH_ENOMEM);
+    s->sort.ncell = (int)ncell;
     Dev &a1 = s->buf[1];
     a1.cell = a0.cell; a1.pos0 = a0.pos0;
     a1.pos = a0.pos; a1.vd = a0.vd; a1.posv = a0.posv; a1.velp = a0.velp; a1.velq = a0.velq; a1.pres = a0.pres;
-    a1.drho_stage = a0.drho_stage;
     a1.nbr = a0.nbr; a1.ncnt = a0.ncnt; a1.nflag = a0.nflag;
-    a1.drho_eval = a0.drho_eval; a1.T4 = a0.T4; a1.T2 = a0.T2; a1.acc = a0.acc;
-    a1.cstart = a0.cstart;
+    a1.drho_stage = a0.drho_stage; a1.drho_eval = a0.drho_eval;
+    a1.T4 = a0.T4; a1.T2 = a0.T2; a1.acc = a0.acc; a1.cstart = a0.cstart;
     a0.flags = a1.flags = s->flags;
     a0.step = a1.step = s->dstep;
     a0.rebuild = a1.rebuild = s->rebuild;
     a0.builds = a1.builds = s->dbuilds;
+    a0.inst = a1.inst = s->dinst;
 
     cudaStream_t st = s->stream;
     auto cuda_fail = [&](cudaError_t e) { return cleanup(fail(SPH_ECUDA, cudaGetErrorString(e))); };
-    cudaError_t e = cudaMemsetAsync(s->flags, 0, sizeof(unsigned), st);
-    if (e != cudaSuccess) return cuda_fail(e);
+    cudaError_t e = cudaSuccess;
+    if ((e = cudaMemsetAsync(s->flags, 0, sizeof(unsigned), st)) != cudaSuccess) return cuda_fail(e);
     if ((e = cudaMemsetAsync(s->dstep, 0, sizeof(long long), st)) != cudaSuccess) return cuda_fail(e);
     if ((e = cudaMemsetAsync(s->dbuilds, 0, sizeof(long long), st)) != cudaSuccess) return cuda_fail(e);
+    if ((e = cudaMemsetAsync(s->bar, 0, sizeof(GridBarrier), st)) != cudaSuccess) return cuda_fail(e);
+    if ((e = cudaMemcpyAsync(s->dinst, s->hinst.data(), sizeof(Inst) * k, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return cuda_fail(e);
+    std::vector<long long> fl(s->first.begin(), s->first.end());
+    if ((e = cudaMemcpyAsync(s->dfirst, fl.data(), sizeof(long long) * (k + 1), cudaMemcpyHostToDevice, st)) !=
+        cudaSuccess)
+        return cuda_fail(e);
+    double grav[4] = {0, 0, 0, 0};
+    for (int c = 0; c < dim; ++c) grav[c] = P0.g[c];
+    if ((e = cudaMemcpyAsync(s->diag_grav, grav, sizeof(grav), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return cuda_fail(e);
     if (n > 0) {
         std::vector<uint8_t> tag((size_t)n);
-        for (int64_t i = 0; i < n; ++i) tag[i] = (uint8_t)(phase[i] | (wall[i] << 1));
+        std::vector<uint16_t> iid((size_t)n);
+        int64_t i = 0;
+        for (int q = 0; q < k; ++q)
+            for (int64_t c = 0; c < counts[q]; ++c, ++i) {
+                tag[i] = (uint8_t)(phase[i] | (wall[i] << 1));
+                iid[i] = (uint16_t)q;
+            }
         if ((e = cudaMemcpyAsync(a0.tag, tag.data(), (size_t)n, cudaMemcpyHostToDevice, st)) != cudaSuccess)
             return cuda_fail(e);
+        if ((e = cudaMemcpyAsync(a0.iid, iid.data(), sizeof(uint16_t) * n, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            return cuda_fail(e);
         k_iota<<<s->blocks((int)n), 256, 0, st>>>(a0.pid, (int)n);
-        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e);
     }
-    s->cur = 0;
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e);
     *out = s;
-    rc = sph_set_state(s, x, u, rho);
+    int rc = sph_set_state(s, x, u, rho);
     if (rc) {
         *out = nullptr;
         return cleanup(rc);
     }
     return SPH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *sph_last_error(void) { return g_err.c_str(); }
+
+int sph_create(const sph_params *params, int64_t n, const double *x, const double *u, const double *rho,
+               const uint8_t *phase, const uint8_t *wall, void *stream, sph_handle *out)
+{
+    if (n < 0) {
+        if (out) *out = nullptr;
+        return fail(SPH_EINVAL, "n must be in [0, 2^26]");
+    }
+    return create_sim(params, 1, &n, x, u, rho, phase, wall, stream, out);
+}
+
+int sph_create_batch(int k, const sph_params *params, const int64_t *counts, const double *x, const double *u,
+                     const double *rho, const uint8_t *phase, const uint8_t *wall, void *stream, sph_handle *out)
+{
+    if (!params || !counts) {
+        if (out) *out = nullptr;
+        return fail(SPH_EINVAL, "params or counts is NULL");
+    }
+    return create_sim(params, k, counts, x, u, rho, phase, wall, stream, out);
 }
 
 int sph_set_state(sph_handle s, const double *x, const double *u, const double *rho)
@@ -505,17 +763,25 @@ int sph_set_state(sph_handle s, const double *x, const double *u, const double *
     if (s->n == 0) return SPH_OK;
     if (!x || !u || !rho) return fail(SPH_EINVAL, "an input array is NULL");
     const size_t n = (size_t)s->n, dim = (size_t)s->dim;
-    // staging area: x, u (n*dim each) and rho (n) as doubles
-    if (!s->read_buf) {
-        if (s->alloc(&s->read_buf, n * 9 + 16)) return SPH_ENOMEM;
-        if (s->alloc(&s->read_ibuf, n)) return SPH_ENOMEM;
-    }
     double *dx = s->read_buf, *du = s->read_buf + n * dim, *dr = s->read_buf + 2 * n * dim;
     CU(cudaMemcpyAsync(dx, x, sizeof(double) * n * dim, cudaMemcpyHostToDevice, s->stream));
     CU(cudaMemcpyAsync(du, u, sizeof(double) * n * dim, cudaMemcpyHostToDevice, s->stream));
     CU(cudaMemcpyAsync(dr, rho, sizeof(double) * n, cudaMemcpyHostToDevice, s->stream));
-    k_load_state<<<s->blocks(s->n), 256, 0, s->stream>>>(s->D(), s->phys, s->dim, dx, du, dr);
+    k_load_state<<<s->blocks(s->n), 256, 0, s->stream>>>(s->D(), s->dim, dx, du, dr);
     CU(cudaGetLastError());
+    CU(cudaMemsetAsync(s->rebuild, 0xff, sizeof(unsigned), s->stream));
+    CU(cudaStreamSynchronize(s->stream));
+    return SPH_OK;
+}
+
+int sph_set_dt_scales(sph_handle s, const double *scales)
+{
+    if (!s || !scales) return fail(SPH_EINVAL, "NULL argument");
+    for (int q = 0; q < s->ninst; ++q)
+        if (!(scales[q] > 0 && scales[q] <= 1.0)) return fail(SPH_EINVAL, "dt scales must be in (0, 1]");
+    for (int q = 0; q < s->ninst; ++q) s->hinst[q].dt_scale = scales[q];
+    CU(cudaMemcpyAsync(s->dinst, s->hinst.data(), sizeof(Inst) * s->ninst, cudaMemcpyHostToDevice, s->stream));
+    // the rebuild test looks half a step ahead with the previous step size
     CU(cudaMemsetAsync(s->rebuild, 0xff, sizeof(unsigned), s->stream));
     CU(cudaStreamSynchronize(s->stream));
     return SPH_OK;
@@ -568,21 +834,21 @@ int sph_run(sph_handle s, double dt, int64_t nsteps, int graph)
     if (dt != s->last_dt) CU(cudaMemsetAsync(s->rebuild, 0xff, sizeof(unsigned), s->stream));
     s->last_dt = dt;
     if (use_graph) {
-        if (!s->gexec[0] || s->gdt[0] != dt) {
+        if (!s->gexec || s->gdt != dt) {
             cudaGraph_t gr = nullptr;
             CU(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
             s->enqueue_step(dt);
             cudaError_t e = cudaStreamEndCapture(s->stream, &gr);
             if (e != cudaSuccess) return fail(SPH_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-            if (s->gexec[0]) cudaGraphExecDestroy(s->gexec[0]);
-            s->gexec[0] = nullptr;
-            e = cudaGraphInstantiate(&s->gexec[0], gr, 0);
+            if (s->gexec) cudaGraphExecDestroy(s->gexec);
+            s->gexec = nullptr;
+            e = cudaGraphInstantiate(&s->gexec, gr, 0);
             cudaGraphDestroy(gr);
             if (e != cudaSuccess) return fail(SPH_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
-            s->gdt[0] = dt;
+            s->gdt = dt;
         }
         for (int64_t k = 0; k < nsteps; ++k) {
-            CU(cudaGraphLaunch(s->gexec[0], s->stream));
+            CU(cudaGraphLaunch(s->gexec, s->stream));
             s->step += 1;
         }
     } else {
@@ -593,6 +859,181 @@ int sph_run(sph_handle s, double dt, int64_t nsteps, int graph)
         }
     }
     return s->check_flags();
+}
+
+int sph_run_persistent(sph_handle s, double dt, int64_t nsteps, int graph)
+{
+    if (!s) return fail(SPH_EINVAL, "handle is NULL");
+    if (!(dt > 0) || !std::isfinite(dt)) return fail(SPH_EINVAL, "dt must be positive and finite");
+    if (nsteps < 0 || nsteps > 0x7fffffff) return fail(SPH_EINVAL, "nsteps must be in [0, 2^31)");
+    if (s->n == 0 || nsteps == 0) {
+        s->step += nsteps;
+        return SPH_OK;
+    }
+    if (dt != s->last_dt) CU(cudaMemsetAsync(s->rebuild, 0xff, sizeof(unsigned), s->stream));
+    s->last_dt = dt;
+    const int shape = (s->pbs * 100000 + s->pgrid) * 2 + s->pdyn;
+    if (graph && !s->timing) {
+        if (!s->pexec || s->pdt != dt || s->psteps != nsteps || s->pshape != shape) {
+            cudaGraph_t gr = nullptr;
+            CU(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
+            int rc = s->launch_persistent(dt, (int)nsteps);
+            cudaError_t e = cudaStreamEndCapture(s->stream, &gr);
+            if (rc) {
+                if (gr) cudaGraphDestroy(gr);
+                return rc;
+            }
+            if (e != cudaSuccess) return fail(SPH_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+            if (s->pexec) cudaGraphExecDestroy(s->pexec);
+            s->pexec = nullptr;
+            e = cudaGraphInstantiate(&s->pexec, gr, 0);
+            cudaGraphDestroy(gr);
+            if (e != cudaSuccess) return fail(SPH_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+            s->pdt = dt;
+            s->psteps = nsteps;
+            s->pshape = shape;
+        }
+        CU(cudaGraphLaunch(s->pexec, s->stream));
+    } else {
+        int rc = s->launch_persistent(dt, (int)nsteps);
+        if (rc) return rc;
+    }
+    s->step += nsteps;
+    return s->check_flags();
+}
+
+int sph_set_launch_shape(sph_handle s, int block, int grid_blocks, int dynamic_chunks)
+{
+    if (!s) return fail(SPH_EINVAL, "handle is NULL");
+    if (block != 128 && block != 256 && block != 512) return fail(SPH_EINVAL, "block must be 128, 256 or 512");
+    if (grid_blocks < 0) return fail(SPH_EINVAL, "grid_blocks must be >= 0");
+    if (dynamic_chunks != 0 && dynamic_chunks != 1) return fail(SPH_EINVAL, "dynamic_chunks must be 0 or 1");
+    int gsz = 0;
+    int rc = s->persistent_shape(block, grid_blocks, &gsz, nullptr);
+    if (rc) return rc;
+    s->pbs = block;
+    s->pgrid = grid_blocks;
+    s->pdyn = dynamic_chunks;
+    return SPH_OK;
+}
+
+int sph_get_launch_shape(sph_handle s, int *block, int *grid_blocks, int *dynamic_chunks)
+{
+    if (!s) return fail(SPH_EINVAL, "handle is NULL");
+    int gsz = 0;
+    int rc = s->persistent_shape(s->pbs, s->pgrid, &gsz, nullptr);
+    if (rc) return rc;
+    if (block) *block = s->pbs;
+    if (grid_blocks) *grid_blocks = gsz;
+    if (dynamic_chunks) *dynamic_chunks = s->pdyn;
+    return SPH_OK;
+}
+
+int sph_autotune(sph_handle s, double dt, int trial_steps, int *best_block, int *best_grid_blocks,
+                 int *best_dynamic_chunks, double *best_ms_per_step)
+{
+    if (!s) return fail(SPH_EINVAL, "handle is NULL");
+    if (!(dt > 0) || !std::isfinite(dt) || trial_steps < 1)
+        return fail(SPH_EINVAL, "dt must be positive and trial_steps >= 1");
+    if (s->n == 0) return SPH_OK;
+    // the trials advance the state: keep it and put it back afterwards
+    const size_t n = (size_t)s->n, dim = (size_t)s->dim;
+    std::vector<double> x(n * dim), u(n * dim), rho(n);
+    int rc = sph_read(s, SPH_FIELD_POS, x.data(), (int64_t)(x.size() * 8));
+    if (!rc) rc = sph_read(s, SPH_FIELD_VEL, u.data(), (int64_t)(u.size() * 8));
+    if (!rc) rc = sph_read(s, SPH_FIELD_RHO, rho.data(), (int64_t)(rho.size() * 8));
+    if (rc) return rc;
+    long long dstep = 0, dbuilds = 0;
+    CU(cudaMemcpyAsync(&dstep, s->dstep, sizeof(dstep), cudaMemcpyDeviceToHost, s->stream));
+    CU(cudaMemcpyAsync(&dbuilds, s->dbuilds, sizeof(dbuilds), cudaMemcpyDeviceToHost, s->stream));
+    CU(cudaStreamSynchronize(s->stream));
+    int dev = 0, sms = 0;
+    CU(cudaGetDevice(&dev));
+    CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    // candidate shapes: every co-resident multiple of the SM count and, for
+    // inputs smaller than twice such a grid's threads, fractions of the SM
+    // count (fewer blocks make each grid barrier cheaper)
+    struct Shape {
+        int bs, grid, dyn;
+    };
+    std::vector<Shape> shapes;
+    for (int bs : PERSIST_BS) {
+        int maxg = 0;
+        rc = s->persistent_shape(bs, 0, &maxg, nullptr);
+        if (rc) return rc;
+        std::vector<int> grids;
+        for (int g = sms; g <= maxg; g += sms) grids.push_back(g);
+        for (int div : {2, 4, 8, 19})
+            if (sms / div >= 1 && (int64_t)(sms / div) * bs <= 2 * (int64_t)n) grids.push_back(sms / div);
+        for (int g : grids)
+            for (int dyn : {1, 0}) shapes.push_back({bs, g, dyn});
+    }
+    const int64_t host_step = s->step;
+    const double host_last_dt = s->last_dt;
+    const bool timing = s->timing;
+    s->timing = false;
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    double best = 1e300;
+    int bb = s->pbs, bg = s->pgrid, bd = s->pdyn;
+    for (const Shape &sh : shapes) {
+        s->pbs = sh.bs;
+        s->pgrid = sh.grid;
+        s->pdyn = sh.dyn;
+        rc = sph_set_state(s, x.data(), u.data(), rho.data());
+        if (!rc) rc = sph_run_persistent(s, dt, 1, 0);  // warm-up, includes a list build
+        if (rc) break;
+        cudaEventRecord(e0, s->stream);
+        rc = s->launch_persistent(dt, trial_steps);
+        cudaEventRecord(e1, s->stream);
+        if (!rc) rc = s->check_flags();
+        if (rc) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double per = ms / trial_steps;
+        if (per < best) {
+            best = per;
+            bb = sh.bs;
+            bg = sh.grid;
+            bd = sh.dyn;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    s->timing = timing;
+    s->pbs = bb;
+    s->pgrid = bg;
+    s->pdyn = bd;
+    // the state and counters as they were before the trials (the next step
+    // rebuilds the lists)
+    int rc2 = sph_set_state(s, x.data(), u.data(), rho.data());
+    CU(cudaMemcpyAsync(s->dstep, &dstep, sizeof(dstep), cudaMemcpyHostToDevice, s->stream));
+    CU(cudaMemcpyAsync(s->dbuilds, &dbuilds, sizeof(dbuilds), cudaMemcpyHostToDevice, s->stream));
+    CU(cudaStreamSynchronize(s->stream));
+    s->step = host_step;
+    s->last_dt = host_last_dt;
+    if (rc) return rc;
+    if (rc2) return rc2;
+    if (best_block) *best_block = bb;
+    if (best_grid_blocks) *best_grid_blocks = bg;
+    if (best_dynamic_chunks) *best_dynamic_chunks = bd;
+    if (best_ms_per_step) *best_ms_per_step = best;
+    return SPH_OK;
+}
+
+int sph_test_stall_barrier(sph_handle s)
+{
+    if (!s) return fail(SPH_EINVAL, "handle is NULL");
+    // with `count` at a value no arrival can reach from below, no block is the
+    // last to arrive: every block waits out its one-second limit and returns
+    int gsz = 0;
+    int rc = s->persistent_shape(s->pbs, s->pgrid, &gsz, nullptr);
+    if (rc) return rc;
+    const unsigned count = (unsigned)gsz;
+    CU(cudaMemcpyAsync(&s->bar->count, &count, sizeof(count), cudaMemcpyHostToDevice, s->stream));
+    CU(cudaStreamSynchronize(s->stream));
+    return SPH_OK;
 }
 
 int sph_sync(sph_handle s)
@@ -624,12 +1065,8 @@ int sph_read(sph_handle s, int field, void *host_out, int64_t bytes)
     }
     if (bytes < (int64_t)need) return fail(SPH_EINVAL, "output buffer too small for the field");
     if (n == 0) return SPH_OK;
-    if (!s->read_buf) {
-        if (s->alloc(&s->read_buf, n * 9 + 16)) return SPH_ENOMEM;
-        if (s->alloc(&s->read_ibuf, n)) return SPH_ENOMEM;
-    }
-    if (s->dim == 2) k_unpermute<2><<<s->blocks(s->n), 256, 0, s->stream>>>(s->D(), s->phys, kind, s->read_buf, s->read_ibuf);
-    else k_unpermute<3><<<s->blocks(s->n), 256, 0, s->stream>>>(s->D(), s->phys, kind, s->read_buf, s->read_ibuf);
+    if (s->dim == 2) k_unpermute<2><<<s->blocks(s->n), 256, 0, s->stream>>>(s->D(), kind, s->read_buf, s->read_ibuf);
+    else k_unpermute<3><<<s->blocks(s->n), 256, 0, s->stream>>>(s->D(), kind, s->read_buf, s->read_ibuf);
     CU(cudaGetLastError());
     if (integer) CU(cudaMemcpyAsync(host_out, s->read_ibuf, need, cudaMemcpyDeviceToHost, s->stream));
     else CU(cudaMemcpyAsync(host_out, s->read_buf, need, cudaMemcpyDeviceToHost, s->stream));
@@ -648,7 +1085,7 @@ int64_t sph_neighbours(sph_handle s, int64_t *start, int32_t *list, int64_t cap)
     }
     s->enqueue_build_cells(true);
     Dev &d = s->D();
-    int *cnt = s->tmp;  // scratch, free after the build
+    int *cnt = s->read_ibuf;
     if (s->dim == 2) k_nbr_count<2><<<s->blocks(n), 256, 0, s->stream>>>(d, s->grid, s->phys, cnt);
     else k_nbr_count<3><<<s->blocks(n), 256, 0, s->stream>>>(d, s->grid, s->phys, cnt);
     CU(cudaGetLastError());
@@ -694,73 +1131,82 @@ int sph_pair_stats(sph_handle s, int64_t out[2])
     out[0] = out[1] = 0;
     if (s->n == 0) return SPH_OK;
     s->enqueue_build_cells(true);
-    unsigned long long *tot = reinterpret_cast<unsigned long long *>(s->diag_small + 48);
-    CU(cudaMemsetAsync(tot, 0, 2 * sizeof(unsigned long long), s->stream));
-    if (s->dim == 2) k_pair_stats<2><<<s->blocks(s->n), 256, 0, s->stream>>>(s->D(), s->grid, s->phys, tot);
-    else k_pair_stats<3><<<s->blocks(s->n), 256, 0, s->stream>>>(s->D(), s->grid, s->phys, tot);
+    CU(cudaMemsetAsync(s->pair_tot, 0, 2 * sizeof(unsigned long long), s->stream));
+    if (s->dim == 2) k_pair_stats<2><<<s->blocks(s->n), 256, 0, s->stream>>>(s->D(), s->grid, s->phys, s->pair_tot);
+    else k_pair_stats<3><<<s->blocks(s->n), 256, 0, s->stream>>>(s->D(), s->grid, s->phys, s->pair_tot);
     CU(cudaGetLastError());
     unsigned long long h[2];
-    CU(cudaMemcpyAsync(h, tot, sizeof(h), cudaMemcpyDeviceToHost, s->stream));
+    CU(cudaMemcpyAsync(h, s->pair_tot, sizeof(h), cudaMemcpyDeviceToHost, s->stream));
     CU(cudaStreamSynchronize(s->stream));
     out[0] = (int64_t)h[0];
     out[1] = (int64_t)h[1];
     return s->check_flags();
 }
 
+int sph_diag_instances(sph_handle s, double *out)
+{
+    if (!s || !out) return fail(SPH_EINVAL, "NULL argument");
+    const int k = s->ninst;
+    for (int q = 0; q < 12 * k; ++q) out[q] = 0.0;
+    if (s->n == 0) return SPH_OK;
+    const size_t n = (size_t)s->n, dim = (size_t)s->dim;
+    double *x = s->read_buf, *u = s->read_buf + n * dim;
+    // original-order positions (instance frames), velocities and tags
+    if (s->dim == 2) {
+        k_unpermute<2><<<s->blocks(s->n), 256, 0, s->stream>>>(s->D(), RK_X, x, s->read_ibuf);
+        k_unpermute<2><<<s->blocks(s->n), 256, 0, s->stream>>>(s->D(), RK_U, u, s->read_ibuf);
+        k_unpermute<2><<<s->blocks(s->n), 256, 0, s->stream>>>(s->D(), RK_TAG, x, s->read_ibuf);
+        k_diag_inst<2><<<k, DIAG_THREADS, 0, s->stream>>>(s->dfirst, x, u, s->read_ibuf, s->dinst, s->diag_grav,
+                                                           s->diag_out);
+    } else {
+        k_unpermute<3><<<s->blocks(s->n), 256, 0, s->stream>>>(s->D(), RK_X, x, s->read_ibuf);
+        k_unpermute<3><<<s->blocks(s->n), 256, 0, s->stream>>>(s->D(), RK_U, u, s->read_ibuf);
+        k_unpermute<3><<<s->blocks(s->n), 256, 0, s->stream>>>(s->D(), RK_TAG, x, s->read_ibuf);
+        k_diag_inst<3><<<k, DIAG_THREADS, 0, s->stream>>>(s->dfirst, x, u, s->read_ibuf, s->dinst, s->diag_grav,
+                                                           s->diag_out);
+    }
+    CU(cudaGetLastError());
+    std::vector<double> r((size_t)k * DIAG_STRIDE);
+    CU(cudaMemcpyAsync(r.data(), s->diag_out, sizeof(double) * r.size(), cudaMemcpyDeviceToHost, s->stream));
+    CU(cudaStreamSynchronize(s->stream));
+    for (int q = 0; q < k; ++q) {
+        const double *v = r.data() + (size_t)q * DIAG_STRIDE;
+        double *o = out + (size_t)q * 12;
+        o[0] = v[0];
+        for (int c = 0; c < s->dim; ++c) o[1 + c] = v[1 + c];
+        o[4] = v[4];
+        o[5] = v[5];
+        o[10] = v[10];
+        o[11] = v[9];
+        if (v[9] > 0) {
+            for (int c = 0; c < s->dim; ++c) o[6 + c] = v[6 + c];
+            const double no = v[9];
+            double lmin, lmax;
+            if (s->dim == 2) {
+                const double a = v[11] / no, b = v[12] / no, d = v[14] / no;
+                const double tr = a + d, det = a * d - b * b;
+                const double disc = std::sqrt(std::max(0.25 * tr * tr - det, 0.0));
+                lmin = 0.5 * tr - disc;
+                lmax = 0.5 * tr + disc;
+            } else {
+                double A[6];
+                for (int c = 0; c < 6; ++c) A[c] = v[11 + c] / no;
+                eig3(A, lmin, lmax);
+            }
+            o[9] = lmax > 0 ? std::sqrt(std::max(lmin, 0.0) / lmax) : 0.0;
+        }
+    }
+    return s->check_flags();
+}
+
 int sph_diag(sph_handle s, double out[12])
 {
     if (!s || !out) return fail(SPH_EINVAL, "NULL argument");
-    for (int k = 0; k < 12; ++k) out[k] = 0.0;
-    if (s->n == 0) return SPH_OK;
-    const int nb = std::min(1024, std::max(1, s->blocks(s->n, DIAG_THREADS)));
-    double *partial = s->diag_partial;
-    double *res = s->diag_small;          // 16
-    double *cen = s->diag_small + 16;     // 3
-    double *grav = s->diag_small + 24;    // 3
-    double *mass = s->diag_small + 32;    // 2
-    double consts[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-    for (int c = 0; c < s->dim; ++c) consts[c] = s->P.g[c];
-    CU(cudaMemcpyAsync(grav, consts, sizeof(double) * 3, cudaMemcpyHostToDevice, s->stream));
-    CU(cudaMemcpyAsync(mass, s->P.mass, sizeof(double) * 2, cudaMemcpyHostToDevice, s->stream));
-    double r0[DIAG_K], r1[DIAG_K];
-    if (s->dim == 2) k_diag<2><<<nb, DIAG_THREADS, 0, s->stream>>>(s->D(), 0, cen, grav, mass, partial);
-    else k_diag<3><<<nb, DIAG_THREADS, 0, s->stream>>>(s->D(), 0, cen, grav, mass, partial);
-    k_diag_final<<<1, DIAG_K, 0, s->stream>>>(partial, nb, res);
-    CU(cudaGetLastError());
-    CU(cudaMemcpyAsync(r0, res, sizeof(r0), cudaMemcpyDeviceToHost, s->stream));
-    CU(cudaStreamSynchronize(s->stream));
-    out[0] = r0[0];
-    for (int c = 0; c < s->dim; ++c) out[1 + c] = r0[1 + c];
-    out[4] = r0[4];
-    out[5] = r0[5];
-    out[10] = r0[15];
-    out[11] = r0[9];
-    if (r0[9] > 0) {
-        double c3[3] = {r0[6] / r0[9], r0[7] / r0[9], r0[8] / r0[9]};
-        for (int c = 0; c < s->dim; ++c) out[6 + c] = c3[c];
-        CU(cudaMemcpyAsync(cen, c3, sizeof(c3), cudaMemcpyHostToDevice, s->stream));
-        if (s->dim == 2) k_diag<2><<<nb, DIAG_THREADS, 0, s->stream>>>(s->D(), 1, cen, grav, mass, partial);
-        else k_diag<3><<<nb, DIAG_THREADS, 0, s->stream>>>(s->D(), 1, cen, grav, mass, partial);
-        k_diag_final<<<1, DIAG_K, 0, s->stream>>>(partial, nb, res);
-        CU(cudaGetLastError());
-        CU(cudaMemcpyAsync(r1, res, sizeof(r1), cudaMemcpyDeviceToHost, s->stream));
-        CU(cudaStreamSynchronize(s->stream));
-        double lmin, lmax;
-        const double no = r0[9];
-        if (s->dim == 2) {
-            const double a = r1[0] / no, b = r1[1] / no, d = r1[3] / no;
-            const double tr = a + d, det = a * d - b * b;
-            const double disc = std::sqrt(std::max(0.25 * tr * tr - det, 0.0));
-            lmin = 0.5 * tr - disc;
-            lmax = 0.5 * tr + disc;
-        } else {
-            double A[6];
-            for (int k = 0; k < 6; ++k) A[k] = r1[k] / no;
-            eig3(A, lmin, lmax);
-        }
-        out[9] = lmax > 0 ? std::sqrt(std::max(lmin, 0.0) / lmax) : 0.0;
-    }
-    return s->check_flags();
+    if (s->ninst == 1) return sph_diag_instances(s, out);
+    std::vector<double> all((size_t)12 * s->ninst);
+    const int rc = sph_diag_instances(s, all.data());
+    for (int c = 0; c < 12; ++c) out[c] = all[c];
+    return rc;
 }
 
 int sph_timing_enable(sph_handle s, int enable)
@@ -807,6 +1253,7 @@ int64_t sph_list_builds(sph_handle s)
 int64_t sph_num_particles(sph_handle s) { return s ? s->n : 0; }
 int64_t sph_step_index(sph_handle s) { return s ? s->step : 0; }
 int64_t sph_num_cells(sph_handle s) { return s ? s->ncell : 0; }
+int64_t sph_num_instances(sph_handle s) { return s ? s->ninst : 0; }
 
 void sph_destroy(sph_handle s)
 {
@@ -814,8 +1261,8 @@ void sph_destroy(sph_handle s)
     if (s->stream) cudaStreamSynchronize(s->stream);
     s->collect_timing();
     for (auto e : s->free_events) cudaEventDestroy(e);
-    for (int k = 0; k < 2; ++k)
-        if (s->gexec[k]) cudaGraphExecDestroy(s->gexec[k]);
+    if (s->gexec) cudaGraphExecDestroy(s->gexec);
+    if (s->pexec) cudaGraphExecDestroy(s->pexec);
     for (void *p : s->allocs) cudaFree(p);
     if (s->own_stream) cudaStreamDestroy(s->stream);
     delete s;

@@ -14,12 +14,23 @@
 //   * density is stored as the deviation drho = rho - rho0(phase) in FP32, so
 //     the equation of state and the renormalisation never subtract two
 //     numbers near rho0;
-//   * once per step a neighbour list (radius 2h + 2 skin) is built from the
-//     cell list, scanning per particle only the cells of the +/-f stencil that
-//     the radius can reach, and stored column-major, so the four
-//     interaction sweeps of the step read it coalesced and run without the
-//     branch divergence of a candidate scan; a sweep gathers two 16-byte
-//     records per neighbour.
+//   * a neighbour list (radius 2h + 2 skin) is built from the cell list,
+//     scanning per particle only the cells of the +/-f stencil that the
+//     radius can reach, and stored column-major, so the four interaction
+//     sweeps of a step read it coalesced and run without the branch
+//     divergence of a candidate scan; a sweep gathers two 16-byte records per
+//     neighbour.  The list is rebuilt only when a particle may have moved
+//     farther than the skin since the last build;
+//   * several independent simulations ("instances") can share one particle
+//     set: they sit in disjoint regions of one box and each particle carries
+//     the index of its instance, whose constants (densities, masses,
+//     viscosities, tension, time-step scale) come from a small table.
+//
+// Every phase is a device function of one particle (or cell, or tile), used
+// both by one-kernel-per-phase launches and by a persistent kernel that runs
+// whole steps with grid barriers between phases.  The template flag NC
+// selects read-only cached loads, which are valid only for data no phase of
+// the same launch writes; the persistent kernel uses plain loads.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -32,23 +43,18 @@ enum : unsigned {
     FLAG_NONFINITE = 2u,  // NaN/Inf in the state
     FLAG_SKIN = 4u,       // predictor displacement beyond the skin
     FLAG_LIST = 8u,       // a particle has more list neighbours than max_neighbours
+    FLAG_TIMEOUT = 16u,   // a grid barrier of the persistent kernel gave up waiting
 };
+constexpr unsigned FLAG_ERRORS = 31u;
 
-// Constants of the physics, FP32 unless they feed an FP64 accumulator.
+// Constants shared by all instances, FP32 unless they feed an FP64 accumulator.
 struct Phys {
     float inv_h;        // 1/h
     float R2;           // (2h)^2, support test
     float RL2;          // list radius^2, (2h + 2 skin)^2
     float RP;           // list radius widened by 1e-4 (conservative stencil pruning)
     float cF;           // -5 alpha_d / h^2: grad W_ij = cF (1-q/2)^3 r_ij
-    float mass[2];      // per-phase particle mass
-    float inv_mass[2];
-    float rho0[2];      // per-phase reference density
-    float inv_rho0[2];
-    float beta[2];      // rho0 c0^2 / gamma
-    float kvis[4];      // [2*ph_i + ph_j]: 2 mu_ij (dynamic form) or 2 nu_ij (kinematic form)
     float delta2;       // delta^2
-    float alpha_s;      // surface tension coefficient
     float inv_dim;      // 1/d in Eq. csf
     float gf[3];        // gravity (FP32, added to the FP32 acceleration)
     int visc_dynamic;   // 1: Eq. visc_2 (factor 1/rho_i), 0: Eq. visc_1
@@ -56,6 +62,21 @@ struct Phys {
     int kmax;           // neighbour-list capacity per particle
     int rebuild_every;  // 0: rebuild when a particle may leave the skin; k: every k steps
     double skin;        // allowed displacement since the last build (the list's margin)
+};
+
+// Constants of one instance.
+struct Inst {
+    float mass[2];      // per-phase particle mass
+    float inv_mass[2];
+    float rho0[2];      // per-phase reference density
+    float inv_rho0[2];
+    float beta[2];      // rho0 c0^2 / gamma
+    float kvis[4];      // [2*ph_i + ph_j]: 2 mu_ij (dynamic form) or 2 nu_ij (kinematic form)
+    float alpha_s;      // surface tension coefficient
+    float pad;
+    double dt_scale;    // this instance's step is dt * dt_scale
+    double offset[3];   // placement of the instance's frame in the shared box
+    double mass64[2];   // per-phase particle mass in FP64 (diagnostics)
 };
 
 struct Grid {
@@ -77,7 +98,9 @@ struct Dev {
     float *drho;        // n, rho - rho0(phase) of the state
     int *pid;           // n, original particle id
     uint8_t *tag;       // n, bit0 oil, bit1 wall
+    uint16_t *iid;      // n, instance index
     int *cell;          // n, cell id (sorted order)
+    const Inst *inst;   // instance table
     // stage arrays
     float4 *pos;        // n, (offset from the super-cell centre xyz, +/- m/rho of the stage input; sign = phase)
     float4 *pos0;       // n, offset at the last list build (xyz): displacement since the build
@@ -105,6 +128,17 @@ struct Dev {
     long long *builds;  // number of list builds performed
 };
 
+// Scratch of the cell-list build.
+struct Sort {
+    int *count;         // ncell, particles per cell
+    int *cell_tmp;      // n, cell id in the pre-sort order
+    int *slot;          // n, arrival slot within the cell
+    int *tmp;           // n, pre-sort index at each (unordered) sorted position
+    int *perm;          // n, pre-sort index at each sorted position
+    int *tile_sums;     // scan tiles
+    int ncell;
+};
+
 // Neighbour-list entries a sweep loads ahead of use (one chunk in flight
 // while the previous chunk is processed).
 #ifndef SPH_LIST_CHUNK
@@ -116,10 +150,29 @@ struct Dev {
 constexpr int NBR_IDX_BITS = 26;
 constexpr unsigned NBR_IDX_MASK = (1u << NBR_IDX_BITS) - 1u;
 
+// Load through the read-only cache when NC (data constant for the launch).
+template <bool NC, class T>
+__device__ __forceinline__ T ld(const T *p)
+{
+    if constexpr (NC) return __ldg(p);
+    else return *p;
+}
+
+// Read-only pointer, __restrict__ only where the pointee is not written
+// anywhere in the launch (NC): the persistent kernel writes every array in
+// some phase and must not let the compiler route its loads through the
+// non-coherent read-only path.
+template <bool NC, class T>
+struct RO {
+    using type = const T *__restrict__;
+};
+template <class T>
+struct RO<false, T> {
+    using type = const T *;
+};
+
 __device__ __forceinline__ int phase_of(float w) { return __float_as_uint(w) >> 31; }
 
-// Per-phase constant without indexing the parameter block at run time (an
-// indexed parameter load would go through the constant cache per thread).
 __device__ __forceinline__ float by_phase(int phase, const float (&a)[2]) { return phase ? a[1] : a[0]; }
 
 // (S_i - S_j) * E for axis a of an entry, exact: the code e in {0, 1, 2}
@@ -161,11 +214,11 @@ __device__ __forceinline__ float axis_gap(float p, int d, float e)
 
 // Scans the particles of the cells within +/-f of cell c that a sphere of
 // radius Rp around the particle can reach (pruned per row), and calls
-// f(j, oj, rx, ry, rz, r2, code) for those with |r_ij|^2 < R2 (j == i
+// fn(j, oj, rx, ry, rz, r2, code) for those with |r_ij|^2 < R2 (j == i
 // included); code is the shift part of a neighbour-list entry.
-template <int DIM, class F>
-__device__ __forceinline__ void for_each_candidate(const Grid &g, const int *__restrict__ cstart,
-                                                   const float4 *__restrict__ pos, int c, const float4 &oi,
+template <int DIM, bool NC, class F>
+__device__ __forceinline__ void for_each_candidate(const Grid &g, typename RO<NC, int>::type cstart,
+                                                   typename RO<NC, float4>::type pos, int c, const float4 &oi,
                                                    float R2, float Rp, F &&fn)
 {
     int cx, cy, cz;
@@ -199,15 +252,15 @@ __device__ __forceinline__ void for_each_candidate(const Grid &g, const int *__r
             if (xlo > xhi) continue;
             // the cells xlo..xhi of a row are contiguous in the sorted order
             const int row = (z * g.ny + y) * g.nx;
-            const int jb = __ldg(cstart + row + xlo), je = __ldg(cstart + row + xhi + 1);
+            const int jb = ld<NC>(cstart + row + xlo), je = ld<NC>(cstart + row + xhi + 1);
             // super-cell Sx covers cells [Sx*f, Sx*f + f)
-            const int b1 = __ldg(cstart + row + min(max(Sx * hw, xlo), xhi + 1));
-            const int b2 = __ldg(cstart + row + min(max(Sx * hw + hw, xlo), xhi + 1));
+            const int b1 = ld<NC>(cstart + row + min(max(Sx * hw, xlo), xhi + 1));
+            const int b2 = ld<NC>(cstart + row + min(max(Sx * hw + hw, xlo), xhi + 1));
             const unsigned cyz = ((unsigned)(dSy + 1) << (NBR_IDX_BITS + 2)) |
                                  ((unsigned)(dSz + 1) << (NBR_IDX_BITS + 4));
 #pragma unroll 4
             for (int j = jb; j < je; ++j) {
-                const float4 oj = __ldg(pos + j);
+                const float4 oj = ld<NC>(pos + j);
                 // super-cell of j along x: Sx - 1, Sx or Sx + 1
                 const float sx = j < b1 ? E : (j < b2 ? 0.f : -E);
                 const unsigned ex = j < b1 ? 2u : (j < b2 ? 1u : 0u);
@@ -256,9 +309,9 @@ __device__ __forceinline__ float4 cell_offset(const Grid &g, int c, const double
 }
 
 // Signed specific volume m/rho, negative for oil.
-__device__ __forceinline__ float signed_volume(const Phys &ph, int phase, float drho, float &vol)
+__device__ __forceinline__ float signed_volume(const Inst &I, int phase, float drho, float &vol)
 {
-    vol = by_phase(phase, ph.mass) / (by_phase(phase, ph.rho0) + drho);
+    vol = by_phase(phase, I.mass) / (by_phase(phase, I.rho0) + drho);
     return phase ? -vol : vol;
 }
 
@@ -266,32 +319,30 @@ __device__ __forceinline__ float signed_volume(const Phys &ph, int phase, float 
 // Cell list: hash, counting sort stable in particle id, reorder.
 
 template <int DIM>
-__global__ void __launch_bounds__(256) k_hash(Dev d, Grid g, int *cell_tmp, int *slot, int *count)
+__device__ __forceinline__ void hash_one(const Dev &d, const Grid &g, const Sort &s, int k)
 {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= d.n || !*d.rebuild) return;
     const int dims[3] = {g.nx, g.ny, g.nz};
     int c[3] = {0, 0, 0};
     unsigned bad = 0;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
         const double xa = d.x[(size_t)a * d.n + k];
-        const double s = floor((xa - g.lo[a]) / g.csd);
+        const double sc = floor((xa - g.lo[a]) / g.csd);
         if (isnan(xa)) {
             bad |= FLAG_NONFINITE;
-        } else if (!(s >= 0.0 && s < (double)dims[a])) {
+        } else if (!(sc >= 0.0 && sc < (double)dims[a])) {
             bad |= FLAG_DOMAIN;
         } else {
-            c[a] = (int)s;
+            c[a] = (int)sc;
         }
     }
     if (bad) atomicOr(d.flags, bad);
     const int id = c[0] + g.nx * (c[1] + g.ny * c[2]);
-    cell_tmp[k] = id;
-    slot[k] = atomicAdd(count + id, 1);
+    s.cell_tmp[k] = id;
+    s.slot[k] = atomicAdd(s.count + id, 1);
 }
 
-// Exclusive scan of m ints, 4096 per block (1024 threads x 4).
+// Exclusive scan of the cell counts in tiles of SCAN_TILE cells.
 constexpr int SCAN_THREADS = 1024, SCAN_ITEMS = 4, SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 
 // Block-wide exclusive scan of one value per thread; the block total is
@@ -326,110 +377,88 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int *total)
     return res;
 }
 
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan_tiles(const int *in, int *out, int *tile_sums, int m,
-                                                              const unsigned *rebuild)
+// Scans tile `tile` of `in` (m values) into `out` with whatever block size
+// runs it (each thread takes SCAN_TILE / blockDim consecutive values) and
+// returns the tile total (the same in every thread).
+__device__ __forceinline__ int scan_tile(const int *in, int *out, int m, int tile)
 {
     __shared__ int s_total;
-    if (!*rebuild) return;
-    const int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
-    int v[SCAN_ITEMS];
+    const int per = SCAN_TILE / blockDim.x;
+    const int base = tile * SCAN_TILE + threadIdx.x * per;
     int sum = 0;
-#pragma unroll
-    for (int k = 0; k < SCAN_ITEMS; ++k) {
-        v[k] = base + k < m ? in[base + k] : 0;
-        sum += v[k];
-    }
+    for (int k = 0; k < per; ++k) sum += base + k < m ? in[base + k] : 0;
     int ex = block_exclusive_scan(sum, &s_total);
-#pragma unroll
-    for (int k = 0; k < SCAN_ITEMS; ++k) {
-        if (base + k < m) out[base + k] = ex;
-        ex += v[k];
+    for (int k = 0; k < per; ++k) {
+        if (base + k < m) {
+            const int v = in[base + k];
+            out[base + k] = ex;
+            ex += v;
+        }
     }
-    if (threadIdx.x == 0) tile_sums[blockIdx.x] = s_total;
+    const int t = s_total;
+    __syncthreads();
+    return t;
 }
 
-// Scans the tile sums in place (one block, at most SCAN_TILE tiles) and
-// writes the grand total to out[m].
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan_sums(int *tile_sums, int ntiles, int *out, int m,
-                                                             const unsigned *rebuild)
+// Exclusive scan of the tile totals in place (one block); writes the grand
+// total to out[m].
+__device__ __forceinline__ void scan_tile_sums(int *tile_sums, int ntiles, int *out, int m)
 {
     __shared__ int s_total;
-    if (!*rebuild) return;
-    const int base = threadIdx.x * SCAN_ITEMS;
-    int v[SCAN_ITEMS];
+    const int per = (ntiles + blockDim.x - 1) / blockDim.x;
+    const int base = threadIdx.x * per;
     int sum = 0;
-#pragma unroll
-    for (int k = 0; k < SCAN_ITEMS; ++k) {
-        v[k] = base + k < ntiles ? tile_sums[base + k] : 0;
-        sum += v[k];
-    }
+    for (int k = 0; k < per; ++k) sum += base + k < ntiles ? tile_sums[base + k] : 0;
     int ex = block_exclusive_scan(sum, &s_total);
-#pragma unroll
-    for (int k = 0; k < SCAN_ITEMS; ++k) {
-        if (base + k < ntiles) tile_sums[base + k] = ex;
-        ex += v[k];
+    for (int k = 0; k < per; ++k) {
+        if (base + k < ntiles) {
+            const int v = tile_sums[base + k];
+            tile_sums[base + k] = ex;
+            ex += v;
+        }
     }
     if (threadIdx.x == 0) out[m] = s_total;
+    __syncthreads();
 }
 
-__global__ void __launch_bounds__(256) k_scan_add(int *out, const int *tile_sums, int m, const unsigned *rebuild)
+__device__ __forceinline__ void scatter_one(const Sort &s, const int *cstart, int k)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < m && *rebuild) out[i] += tile_sums[i / SCAN_TILE];
-}
-
-__global__ void __launch_bounds__(256) k_zero(int *a, int m, const unsigned *rebuild)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < m && *rebuild) a[i] = 0;
-}
-
-__global__ void __launch_bounds__(256) k_scatter(int n, const int *cell_tmp, const int *slot, const int *cstart, int *tmp,
-                                                 const unsigned *rebuild)
-{
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n || !*rebuild) return;
-    tmp[cstart[cell_tmp[k]] + slot[k]] = k;
+    s.tmp[cstart[s.cell_tmp[k]] + s.slot[k]] = k;
 }
 
 // Final position of each particle inside its cell: its rank by original id
 // among the cell's particles, so the order is (cell id, particle id).
-__global__ void __launch_bounds__(256) k_rank(int n, const int *tmp, const int *cell_tmp, const int *pid,
-                                              const int *cstart, int *perm, const unsigned *rebuild)
+__device__ __forceinline__ void rank_one(const Sort &s, const int *pid, const int *cstart, int p)
 {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n || !*rebuild) return;
-    const int k = tmp[p];
-    const int c = cell_tmp[k];
+    const int k = s.tmp[p];
+    const int c = s.cell_tmp[k];
     const int b = cstart[c], e = cstart[c + 1];
     const int me = pid[k];
     int rank = 0;
-    for (int q = b; q < e; ++q) rank += pid[tmp[q]] < me;
-    perm[b + rank] = k;
+    for (int q = b; q < e; ++q) rank += pid[s.tmp[q]] < me;
+    s.perm[b + rank] = k;
 }
 
 // Stage-1 records of particle k from its FP64 state.
 template <int DIM>
-__device__ __forceinline__ void stage_records(const Dev &d, const Grid &g, const Phys &ph, int k, int c,
+__device__ __forceinline__ void stage_records(const Dev &d, const Grid &g, const Inst &I, int k, int c,
                                               const double xa[3], const double ua[3], float dr, int oil)
 {
     float4 p = cell_offset<DIM>(g, c, xa);
     float vol;
-    p.w = signed_volume(ph, oil, dr, vol);
+    p.w = signed_volume(I, oil, dr, vol);
     d.pos[k] = p;
     d.vd[k] = vol * dr;
     d.velp[k] = make_float4((float)ua[0], (float)ua[1], (float)ua[2], 0.f);
 }
 
-// Gathers the state into the new order (into the scratch set `dst`) and
-// prepares the stage-1 records and the build offsets.
+// Gathers the state of sorted position k into the scratch set `dst` and
+// prepares its stage-1 records and build offset.
 template <int DIM>
-__global__ void __launch_bounds__(256) k_gather(Dev src, Dev dst, Grid g, Phys ph, const int *perm, const int *cell_tmp)
+__device__ __forceinline__ void gather_one(const Dev &src, const Dev &dst, const Grid &g, const Sort &s, int k)
 {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = src.n;
-    if (k >= n || !*src.rebuild) return;
-    const int o = perm[k];
+    const int o = s.perm[k];
     double xa[3] = {0, 0, 0}, ua[3] = {0, 0, 0};
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
@@ -440,22 +469,21 @@ __global__ void __launch_bounds__(256) k_gather(Dev src, Dev dst, Grid g, Phys p
     }
     const float dr = src.drho[o];
     const uint8_t tg = src.tag[o];
-    const int c = cell_tmp[o];
+    const uint16_t ii = src.iid[o];
+    const int c = s.cell_tmp[o];
     dst.drho[k] = dr;
     dst.pid[k] = src.pid[o];
     dst.tag[k] = tg;
+    dst.iid[k] = ii;
     src.cell[k] = c;
-    stage_records<DIM>(src, g, ph, k, c, xa, ua, dr, tg & 1);
+    stage_records<DIM>(src, g, src.inst[ii], k, c, xa, ua, dr, tg & 1);
     src.pos0[k] = src.pos[k];
 }
 
-// Copies the gathered state back into the primary set.
 template <int DIM>
-__global__ void __launch_bounds__(256) k_copy_back(Dev src, Dev dst)
+__device__ __forceinline__ void copy_one(const Dev &src, const Dev &dst, int k)
 {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = src.n;
-    if (k >= n || !*dst.rebuild) return;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
         dst.x[(size_t)a * n + k] = src.x[(size_t)a * n + k];
@@ -464,25 +492,22 @@ __global__ void __launch_bounds__(256) k_copy_back(Dev src, Dev dst)
     dst.drho[k] = src.drho[k];
     dst.pid[k] = src.pid[k];
     dst.tag[k] = src.tag[k];
+    dst.iid[k] = src.iid[k];
 }
 
-// ---------------------------------------------------------------------------
-// Neighbour list: every j != i within the cell edge (2h + 2 skin) at the
+// Neighbour list of particle i: every j != i within 2h + 2 skin at the
 // positions of the build, so the list stays complete while no particle moves
 // farther than the skin.
-template <int DIM>
-__global__ void __launch_bounds__(256, 4) k_build_list(Dev d, Grid g, Phys ph)
+template <int DIM, bool NC>
+__device__ __forceinline__ void list_one(const Dev &d, const Grid &g, const Phys &ph, int i)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= d.n || !*d.rebuild) return;
-    if (i == 0) *d.builds += 1;
     const float4 oi = d.pos[i];
     const int phi_ = phase_of(oi.w);
     int cnt = 0;
     int other = 0;
     const int n = d.n, kmax = ph.kmax;
     unsigned *__restrict__ nbr = d.nbr;
-    for_each_candidate<DIM>(g, d.cstart, d.pos, d.cell[i], oi, ph.RL2, ph.RP,
+    for_each_candidate<DIM, NC>(g, d.cstart, d.pos, d.cell[i], oi, ph.RL2, ph.RP,
         [&](int j, const float4 &oj, float, float, float, float, unsigned code) {
             if (j == i) return;
             if (cnt < kmax) nbr[(size_t)cnt * n + i] = (unsigned)j | code;
@@ -505,8 +530,8 @@ __global__ void __launch_bounds__(256, 4) k_build_list(Dev d, Grid g, Phys ph)
 // the renormalised density becomes the state rho^n.  Writes the stage-2
 // records (pos, vd, velq).
 template <int DIM>
-__device__ __forceinline__ void predict_particle(const Dev &d, const Grid &g, const Phys &ph, int k, float4 a,
-                                                 double dt)
+__device__ __forceinline__ void predict_particle(const Dev &d, const Grid &g, const Phys &ph, const Inst &I, int k,
+                                                 float4 a, double dt)
 {
     const uint8_t tg = d.tag[k];
     const float dr = d.drho_eval[k];
@@ -530,7 +555,7 @@ __device__ __forceinline__ void predict_particle(const Dev &d, const Grid &g, co
     const float ex = p.x - p0.x, ey = p.y - p0.y, ez = p.z - p0.z;
     if (ex * ex + ey * ey + ez * ez > (float)(ph.skin * ph.skin)) atomicOr(d.flags, FLAG_SKIN);
     float vol;
-    p.w = signed_volume(ph, tg & 1, drs, vol);
+    p.w = signed_volume(I, tg & 1, drs, vol);
     d.pos[k] = p;
     d.vd[k] = vol * drs;
     d.velq[k] = make_float4((float)us[0], (float)us[1], (float)us[2], 0.f);
@@ -541,8 +566,8 @@ __device__ __forceinline__ void predict_particle(const Dev &d, const Grid &g, co
 // dt Drho*, in the FP64 accumulators (walls keep x and u).  Writes the
 // stage-1 records of the next step and decides whether it rebuilds the lists.
 template <int DIM>
-__device__ __forceinline__ void correct_particle(const Dev &d, const Grid &g, const Phys &ph, int k, float4 a,
-                                                 double dt)
+__device__ __forceinline__ void correct_particle(const Dev &d, const Grid &g, const Phys &ph, const Inst &I, int k,
+                                                 float4 a, double dt)
 {
     if (k == 0) {
         const long long next = *d.step + 1;
@@ -571,7 +596,7 @@ __device__ __forceinline__ void correct_particle(const Dev &d, const Grid &g, co
     }
     if (!finite) atomicOr(d.flags, FLAG_NONFINITE);
     // stage-1 records of the next step (replaced by the gather if it rebuilds)
-    stage_records<DIM>(d, g, ph, k, d.cell[k], xa, ua, dr, tg & 1);
+    stage_records<DIM>(d, g, I, k, d.cell[k], xa, ua, dr, tg & 1);
     if (ph.rebuild_every == 0 && !(tg & 2)) {
         // next step's stage positions: x^{n+1} and x^{n+1} + dt/2 u^{n+1};
         // rebuild before either can be farther than the skin from the build
@@ -596,17 +621,13 @@ __device__ __forceinline__ void correct_particle(const Dev &d, const Grid &g, co
 // over i itself and its same-phase neighbours, both sums Kahan-compensated.
 // The colour gradient uses the density that entered the stage:
 // grad C_i = (1/V_i) sum_{j other phase} V_j^2 grad W_ij, V = m/rho = 1/sigma.
-template <int DIM>
-__global__ void __launch_bounds__(256) k_sweep_a(Dev d, Grid g, Phys ph, const float *__restrict__ drho_in, int stage1,
-                                                 float4 *vel_s)
+template <int DIM, bool NC>
+__device__ __forceinline__ void sweep_a_one(const Dev &d, const Grid &g, const Phys &ph, const float *drho_in,
+                                            int renorm, float4 *vel_s, int i)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= d.n) return;
-    const int renorm = stage1 && ph.renorm_every > 0 && (*d.step % ph.renorm_every) == 0;
-    // the lists built for this step are in place; the corrector decides the next build
-    if (stage1 && i == 0) *d.rebuild = 0u;
     const float4 oi = d.pos[i];
     const int phi_ = phase_of(oi.w);
+    const Inst &I = d.inst[d.iid[i]];
     // self term: W(0)/alpha_d = 1
     float s1 = fabsf(oi.w), c1 = 0.f, s2 = d.vd[i], c2 = 0.f;
     float gx = 0.f, gy = 0.f, gz = 0.f;
@@ -614,26 +635,26 @@ __global__ void __launch_bounds__(256) k_sweep_a(Dev d, Grid g, Phys ph, const f
     if (renorm || other) {
         const float inv_h = ph.inv_h, cs = g.Es;
         const int n = d.n, cnt = d.ncnt[i];
-        const unsigned *__restrict__ col = d.nbr + i;
-        const float4 *__restrict__ pos = d.pos;
-        const float *__restrict__ vd = d.vd;
+        typename RO<NC, unsigned>::type col = d.nbr + i;
+        typename RO<NC, float4>::type pos = d.pos;
+        typename RO<NC, float>::type vd = d.vd;
         constexpr int CH = SPH_LIST_CHUNK;
         unsigned ec[CH];
 #pragma unroll
-        for (int c = 0; c < CH; ++c) ec[c] = c < cnt ? __ldg(col + (size_t)c * n) : 0u;
+        for (int c = 0; c < CH; ++c) ec[c] = c < cnt ? ld<NC>(col + (size_t)c * n) : 0u;
         for (int k0 = 0; k0 < cnt; k0 += CH) {
             unsigned en[CH];
 #pragma unroll
             for (int c = 0; c < CH; ++c) {
                 const int kk = k0 + CH + c;
-                en[c] = kk < cnt ? __ldg(col + (size_t)kk * n) : 0u;
+                en[c] = kk < cnt ? ld<NC>(col + (size_t)kk * n) : 0u;
             }
 #pragma unroll
             for (int c = 0; c < CH; ++c) {
                 if (k0 + c >= cnt) break;
                 const unsigned e = ec[c];
                 const int j = (int)(e & NBR_IDX_MASK);
-                const float4 oj = __ldg(pos + j);
+                const float4 oj = ld<NC>(pos + j);
                 float rx, ry, rz;
                 const float r2 = pair_vec<DIM>(oi, oj, entry_shift(e, 0, cs), entry_shift(e, 1, cs),
                                                DIM == 3 ? entry_shift(e, 2, cs) : 0.f, rx, ry, rz);
@@ -647,7 +668,7 @@ __global__ void __launch_bounds__(256) k_sweep_a(Dev d, Grid g, Phys ph, const f
                         // W / alpha_d = t^4 (2q + 1)
                         const float w = t3 * t * fmaf(2.f * inv_h, r, 1.f);
                         kahan_add(s1, c1, fabsf(oj.w) * w);
-                        kahan_add(s2, c2, __ldg(vd + j) * w);
+                        kahan_add(s2, c2, ld<NC>(vd + j) * w);
                     }
                 } else {
                     const float cc = oj.w * oj.w * t3;
@@ -662,9 +683,9 @@ __global__ void __launch_bounds__(256) k_sweep_a(Dev d, Grid g, Phys ph, const f
     }
     const float drho = renorm ? s2 / s1 : drho_in[i];
     d.drho_eval[i] = drho;
-    const float rho = by_phase(phi_, ph.rho0) + drho;
-    const float vol = by_phase(phi_, ph.mass) / rho;
-    const float P = eos_tait7(by_phase(phi_, ph.beta), drho * by_phase(phi_, ph.inv_rho0));
+    const float rho = by_phase(phi_, I.rho0) + drho;
+    const float vol = by_phase(phi_, I.mass) / rho;
+    const float P = eos_tait7(by_phase(phi_, I.beta), drho * by_phase(phi_, I.inv_rho0));
     // grad C_i = sigma_i sum V_j^2 grad W_ij, sigma_i = 1/|V_i| (entry density)
     const float sc = ph.cF / fabsf(oi.w);
     gx *= sc;
@@ -677,7 +698,7 @@ __global__ void __launch_bounds__(256) k_sweep_a(Dev d, Grid g, Phys ph, const f
     if (n2 > 0.f) {
         iface = 1u;
         // T sigma_i^-2 = alpha_s / |g| (|g|^2/d I - g g^T) V_i^2, V_i from the renormalised density
-        const float kk = ph.alpha_s * rsqrtf(n2) * vol * vol;
+        const float kk = I.alpha_s * rsqrtf(n2) * vol * vol;
         const float iso = n2 * ph.inv_dim;
         if (DIM == 2) {
             t4 = make_float4(kk * (iso - gx * gx), -kk * gx * gy, kk * (iso - gy * gy), 0.f);
@@ -703,15 +724,14 @@ __global__ void __launch_bounds__(256) k_sweep_a(Dev d, Grid g, Phys ph, const f
 // (Eq. ct_dist_2).  grad_i W_ij = cF t^3 r_ij with t = 1 - q/2; the common
 // factor cF is applied once per particle.
 // STAGE 0: rates only; 1: then the predictor; 2: then the corrector.
-template <int DIM, int STAGE>
-__global__ void __launch_bounds__(256, 4) k_sweep_b(Dev d, Grid g, Phys ph, double dt)
+template <int DIM, int STAGE, bool NC>
+__device__ __forceinline__ void sweep_b_one(const Dev &d, const Grid &g, const Phys &ph, double dt, int i)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= d.n) return;
     const float4 oi = d.posv[i];
     const int phi_ = phase_of(oi.w);
+    const Inst &I = d.inst[d.iid[i]];
     const unsigned iface_i = __float_as_uint(oi.w) & 1u;
-    const float4 *__restrict__ vel_s = STAGE == 2 ? d.velq : d.velp;
+    typename RO<NC, float4>::type vel_s = STAGE == 2 ? d.velq : d.velp;
     const float4 ui = vel_s[i];              // w: P_i / rho_i^2
     const float4 Ti = d.T4[i];
     const float2 Ti2 = DIM == 3 ? d.T2[i] : make_float2(0.f, 0.f);
@@ -722,30 +742,30 @@ __global__ void __launch_bounds__(256, 4) k_sweep_b(Dev d, Grid g, Phys ph, doub
     const float inv_h = ph.inv_h, cs = g.Es;
     const int n = d.n, cnt = d.ncnt[i];
     // per-phase constants of the pair terms as registers (selected per pair)
-    const float m_wat = ph.mass[0], m_oil = ph.mass[1];
-    const float kv_wat = phi_ ? ph.kvis[2] : ph.kvis[0], kv_oil = phi_ ? ph.kvis[3] : ph.kvis[1];
-    const unsigned *__restrict__ col = d.nbr + i;
-    const float4 *__restrict__ posv = d.posv;
-    const float4 *__restrict__ T4 = d.T4;
-    const float2 *__restrict__ T2 = d.T2;
+    const float m_wat = I.mass[0], m_oil = I.mass[1];
+    const float kv_wat = phi_ ? I.kvis[2] : I.kvis[0], kv_oil = phi_ ? I.kvis[3] : I.kvis[1];
+    typename RO<NC, unsigned>::type col = d.nbr + i;
+    typename RO<NC, float4>::type posv = d.posv;
+    typename RO<NC, float4>::type T4 = d.T4;
+    typename RO<NC, float2>::type T2 = d.T2;
     constexpr int CH = SPH_LIST_CHUNK;
     unsigned ec[CH];
 #pragma unroll
-    for (int c = 0; c < CH; ++c) ec[c] = c < cnt ? __ldg(col + (size_t)c * n) : 0u;
+    for (int c = 0; c < CH; ++c) ec[c] = c < cnt ? ld<NC>(col + (size_t)c * n) : 0u;
     for (int k0 = 0; k0 < cnt; k0 += CH) {
         unsigned en[CH];
 #pragma unroll
         for (int c = 0; c < CH; ++c) {
             const int kk = k0 + CH + c;
-            en[c] = kk < cnt ? __ldg(col + (size_t)kk * n) : 0u;
+            en[c] = kk < cnt ? ld<NC>(col + (size_t)kk * n) : 0u;
         }
 #pragma unroll
         for (int c = 0; c < CH; ++c) {
             if (k0 + c >= cnt) break;
             const unsigned e = ec[c];
             const int j = (int)(e & NBR_IDX_MASK);
-            const float4 oj = __ldg(posv + j);
-            const float4 uj = __ldg(vel_s + j);
+            const float4 oj = ld<NC>(posv + j);
+            const float4 uj = ld<NC>(vel_s + j);
             float rx, ry, rz;
             const float r2 = pair_vec<DIM>(oi, oj, entry_shift(e, 0, cs), entry_shift(e, 1, cs),
                                            DIM == 3 ? entry_shift(e, 2, cs) : 0.f, rx, ry, rz);
@@ -771,13 +791,13 @@ __global__ void __launch_bounds__(256, 4) k_sweep_b(Dev d, Grid g, Phys ph, doub
             if (DIM == 3) ur = fmaf(uz, rz, ur);
             dv = fmaf(vt, ur, dv);
             if ((iface_i | (__float_as_uint(oj.w) & 1u)) != 0u) {
-                const float4 Tj = __ldg(T4 + j);
+                const float4 Tj = ld<NC>(T4 + j);
                 if (DIM == 2) {
                     const float xx = Ti.x + Tj.x, xy = Ti.y + Tj.y, yy = Ti.z + Tj.z;
                     sx = fmaf(t3, xx * rx + xy * ry, sx);
                     sy = fmaf(t3, xy * rx + yy * ry, sy);
                 } else {
-                    const float2 Tj2 = __ldg(T2 + j);
+                    const float2 Tj2 = ld<NC>(T2 + j);
                     const float xx = Ti.x + Tj.x, xy = Ti.y + Tj.y, xz = Ti.z + Tj.z;
                     const float yy = Ti.w + Tj.w, yz = Ti2.x + Tj2.x, zz = Ti2.y + Tj2.y;
                     sx = fmaf(t3, xx * rx + xy * ry + xz * rz, sx);
@@ -789,24 +809,296 @@ __global__ void __launch_bounds__(256, 4) k_sweep_b(Dev d, Grid g, Phys ph, doub
 #pragma unroll
         for (int c = 0; c < CH; ++c) ec[c] = en[c];
     }
-    const float rho = by_phase(phi_, ph.rho0) + d.drho_eval[i];
+    const float rho = by_phase(phi_, I.rho0) + d.drho_eval[i];
     float4 out;
     out.w = rho * ph.cF * dv;
     if (d.tag[i] & 2) {
         out.x = out.y = out.z = 0.f;
     } else {
         const float vf = ph.visc_dynamic ? ph.cF / rho : ph.cF;
-        const float sf = ph.cF * by_phase(phi_, ph.inv_mass);
+        const float sf = ph.cF * by_phase(phi_, I.inv_mass);
         out.x = -ph.cF * px + vf * vx + sf * sx + ph.gf[0];
         out.y = -ph.cF * py + vf * vy + sf * sy + ph.gf[1];
         out.z = DIM == 3 ? -ph.cF * pz + vf * vz + sf * sz + ph.gf[2] : 0.f;
     }
     d.acc[i] = out;
-    if (STAGE == 1) predict_particle<DIM>(d, g, ph, i, out, dt);
-    if (STAGE == 2) correct_particle<DIM>(d, g, ph, i, out, dt);
+    if (STAGE == 1) predict_particle<DIM>(d, g, ph, I, i, out, dt * I.dt_scale);
+    if (STAGE == 2) correct_particle<DIM>(d, g, ph, I, i, out, dt * I.dt_scale);
+}
+
+__device__ __forceinline__ int renorm_now(const Dev &d, const Phys &ph, int stage1)
+{
+    return stage1 && ph.renorm_every > 0 && (*d.step % ph.renorm_every) == 0;
 }
 
 // ---------------------------------------------------------------------------
+// One kernel per phase.  The cell-list kernels return at once unless the
+// device flag `rebuild` is set.
+
+template <int DIM>
+__global__ void __launch_bounds__(256) k_hash(Dev d, Grid g, Sort s)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= d.n || !*d.rebuild) return;
+    hash_one<DIM>(d, g, s, k);
+}
+
+__global__ void __launch_bounds__(256) k_zero(int *a, int m, const unsigned *rebuild)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m && *rebuild) a[i] = 0;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_tiles(const int *in, int *out, int *tile_sums, int m,
+                                                              const unsigned *rebuild)
+{
+    if (!*rebuild) return;
+    const int t = scan_tile(in, out, m, blockIdx.x);
+    if (threadIdx.x == 0) tile_sums[blockIdx.x] = t;
+}
+
+// Scans the tile sums in place (one block) and writes the grand total to out[m].
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_sums(int *tile_sums, int ntiles, int *out, int m,
+                                                             const unsigned *rebuild)
+{
+    if (!*rebuild) return;
+    scan_tile_sums(tile_sums, ntiles, out, m);
+}
+
+__global__ void __launch_bounds__(256) k_scan_add(int *out, const int *tile_sums, int m, const unsigned *rebuild)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m && *rebuild) out[i] += tile_sums[i / SCAN_TILE];
+}
+
+__global__ void __launch_bounds__(256) k_scatter(int n, Sort s, const int *cstart, const unsigned *rebuild)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n || !*rebuild) return;
+    scatter_one(s, cstart, k);
+}
+
+__global__ void __launch_bounds__(256) k_rank(int n, Sort s, const int *pid, const int *cstart,
+                                              const unsigned *rebuild)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n || !*rebuild) return;
+    rank_one(s, pid, cstart, p);
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(256) k_gather(Dev src, Dev dst, Grid g, Sort s)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= src.n || !*src.rebuild) return;
+    gather_one<DIM>(src, dst, g, s, k);
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(256) k_copy_back(Dev src, Dev dst)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= src.n || !*dst.rebuild) return;
+    copy_one<DIM>(src, dst, k);
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(256, 4) k_build_list(Dev d, Grid g, Phys ph)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d.n || !*d.rebuild) return;
+    if (i == 0) *d.builds += 1;
+    list_one<DIM, true>(d, g, ph, i);
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(256) k_sweep_a(Dev d, Grid g, Phys ph, const float *__restrict__ drho_in, int stage1,
+                                                 float4 *vel_s)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d.n) return;
+    const int renorm = renorm_now(d, ph, stage1);
+    // the lists built for this step are in place; the corrector decides the next build
+    if (stage1 && i == 0) *d.rebuild = 0u;
+    sweep_a_one<DIM, true>(d, g, ph, drho_in, renorm, vel_s, i);
+}
+
+template <int DIM, int STAGE>
+__global__ void __launch_bounds__(256, 4) k_sweep_b(Dev d, Grid g, Phys ph, double dt)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d.n) return;
+    sweep_b_one<DIM, STAGE, true>(d, g, ph, dt, i);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent form: one cooperative launch runs whole steps, every phase a
+// grid-stride loop, phases separated by a grid barrier that gives up after
+// one second (the launch then sets FLAG_TIMEOUT and returns).
+
+struct GridBarrier {
+    unsigned count;     // blocks arrived at the current barrier
+    unsigned gen;       // barrier generation
+    unsigned snapshot;  // error flags seen by the last arriving block
+    unsigned work;      // next 32-particle chunk of the current phase (reset by each barrier)
+};
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned atom_add_acq_rel_gpu(unsigned *p, unsigned v)
+{
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+__device__ __forceinline__ void st_release_gpu(unsigned *p, unsigned v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid-wide barrier.  Thread 0 of each block arrives with a release-acquire
+// add (the block's writes, ordered before it by the block barrier, become
+// visible to whoever acquires later); the last block to arrive records the
+// error flags, resets the arrival and chunk counters and publishes a new
+// generation with a release store, which the others poll with acquire loads.
+// Returns the error flags as they stood when the last block arrived (the same
+// value in every block), plus FLAG_TIMEOUT if this block gave up waiting.
+__device__ __forceinline__ unsigned grid_sync(GridBarrier *b, unsigned *flags)
+{
+    __shared__ unsigned s_snap;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // the generation cannot advance before this block has arrived
+        const unsigned g0 = ld_acquire_gpu(&b->gen);
+        const unsigned arrived = atom_add_acq_rel_gpu(&b->count, 1u);
+        unsigned mine = 0u;
+        if (arrived == gridDim.x - 1) {
+            b->snapshot = *(volatile unsigned *)flags;
+            atomicExch(&b->work, 0u);
+            atomicExch(&b->count, 0u);
+            st_release_gpu(&b->gen, g0 + 1u);
+        } else {
+            const unsigned long long t0 = global_ns();
+            while (ld_acquire_gpu(&b->gen) == g0) {
+                __nanosleep(32);
+                if (global_ns() - t0 > 1000000000ull) {
+                    atomicOr(flags, FLAG_TIMEOUT);
+                    mine = FLAG_TIMEOUT;
+                    break;
+                }
+            }
+        }
+        s_snap = *(volatile unsigned *)&b->snapshot | mine;
+    }
+    __syncthreads();
+    return s_snap;
+}
+
+// Calls f(i) for every particle i < n, handing out chunks of consecutive
+// particles (32 a sub-chunk, one particle a lane) to warps from a grid-wide
+// counter: warps that finish early take more chunks, so a phase ends with at
+// most one chunk in flight per warp instead of a fixed share per thread.  The
+// barrier before the phase resets the counter.
+template <class F>
+__device__ __forceinline__ void for_each_chunk(GridBarrier *bar, int n, F &&f)
+{
+    const int lane = threadIdx.x & 31;
+    // tickets of m x 32 particles, m chosen so each thread takes about eight
+    // tickets a phase (few atomics on large inputs, a short tail on small ones)
+    const int m = max(1, n / (int)(gridDim.x * blockDim.x * 8u));
+    for (;;) {
+        unsigned c = 0u;
+        if (lane == 0) c = atomicAdd(&bar->work, 1u);
+        c = __shfl_sync(0xffffffffu, c, 0);
+        const long long base = (long long)c * 32 * m;
+        if (base >= n) break;
+        for (int k = 0; k < m; ++k) {
+            const long long i = base + 32 * k + lane;
+            if (i < n) f((int)i);
+        }
+    }
+}
+
+// Particle loop of one phase: dynamic chunks (above) or, with dyn == 0, a
+// fixed grid-stride share per thread.
+template <class F>
+__device__ __forceinline__ void for_each_particle(GridBarrier *bar, int n, int dyn, F &&f)
+{
+    if (dyn) {
+        for_each_chunk(bar, n, f);
+    } else {
+        const int stride = gridDim.x * blockDim.x;
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) f(i);
+    }
+}
+
+// Body of the persistent kernel (instantiated per block size by the host
+// file): nsteps whole steps; returns early, in every block, once an error
+// flag is raised or a barrier times out.
+template <int DIM>
+__device__ __forceinline__ void persistent_steps(Dev d, Dev scratch, Grid g, Phys ph, Sort s, GridBarrier *bar,
+                                                 double dt, int nsteps, int dyn)
+{
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int stride = gridDim.x * blockDim.x;
+    const int n = d.n;
+    if (grid_sync(bar, d.flags) & FLAG_ERRORS) return;
+    for (int step = 0; step < nsteps; ++step) {
+        // every block reads the flag after the barrier that closed the last step
+        if (*(volatile unsigned *)d.rebuild) {
+            for (int c = tid; c < s.ncell; c += stride) s.count[c] = 0;
+            if (grid_sync(bar, d.flags) & FLAG_ERRORS) return;
+            for (int k = tid; k < n; k += stride) hash_one<DIM>(d, g, s, k);
+            if (grid_sync(bar, d.flags) & FLAG_ERRORS) return;
+            const int ntiles = (s.ncell + SCAN_TILE - 1) / SCAN_TILE;
+            for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+                const int tot = scan_tile(s.count, d.cstart, s.ncell, t);
+                if (threadIdx.x == 0) s.tile_sums[t] = tot;
+            }
+            if (grid_sync(bar, d.flags) & FLAG_ERRORS) return;
+            if (blockIdx.x == 0) scan_tile_sums(s.tile_sums, ntiles, d.cstart, s.ncell);
+            if (grid_sync(bar, d.flags) & FLAG_ERRORS) return;
+            for (int c = tid; c < s.ncell; c += stride) d.cstart[c] += s.tile_sums[c / SCAN_TILE];
+            if (grid_sync(bar, d.flags) & FLAG_ERRORS) return;
+            for (int k = tid; k < n; k += stride) scatter_one(s, d.cstart, k);
+            if (grid_sync(bar, d.flags) & FLAG_ERRORS) return;
+            for (int p = tid; p < n; p += stride) rank_one(s, d.pid, d.cstart, p);
+            if (grid_sync(bar, d.flags) & FLAG_ERRORS) return;
+            for (int k = tid; k < n; k += stride) gather_one<DIM>(d, scratch, g, s, k);
+            if (grid_sync(bar, d.flags) & FLAG_ERRORS) return;
+            for (int k = tid; k < n; k += stride) copy_one<DIM>(scratch, d, k);
+            if (grid_sync(bar, d.flags) & FLAG_ERRORS) return;
+            if (tid == 0) *d.builds += 1;
+            for_each_particle(bar, n, dyn, [&](int i) { list_one<DIM, false>(d, g, ph, i); });
+            if (grid_sync(bar, d.flags) & FLAG_ERRORS) return;
+        }
+        const int renorm = renorm_now(d, ph, 1);
+        if (grid_sync(bar, d.flags) & FLAG_ERRORS) return;  // all blocks read rebuild and step
+        if (tid == 0) *d.rebuild = 0u;
+        for_each_particle(bar, n, dyn, [&](int i) { sweep_a_one<DIM, false>(d, g, ph, d.drho, renorm, d.velp, i); });
+        if (grid_sync(bar, d.flags) & FLAG_ERRORS) return;
+        for_each_particle(bar, n, dyn, [&](int i) { sweep_b_one<DIM, 1, false>(d, g, ph, dt, i); });
+        if (grid_sync(bar, d.flags) & FLAG_ERRORS) return;
+        for_each_particle(bar, n, dyn, [&](int i) { sweep_a_one<DIM, false>(d, g, ph, d.drho_stage, 0, d.velq, i); });
+        if (grid_sync(bar, d.flags) & FLAG_ERRORS) return;
+        for_each_particle(bar, n, dyn, [&](int i) { sweep_b_one<DIM, 2, false>(d, g, ph, dt, i); });
+        if (grid_sync(bar, d.flags) & FLAG_ERRORS) return;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Neighbour sets and pair statistics by the sweeps' own support test.
 
@@ -817,8 +1109,8 @@ __global__ void __launch_bounds__(256) k_nbr_count(Dev d, Grid g, Phys ph, int *
     if (i >= d.n) return;
     const float4 oi = d.pos[i];
     int cnt = 0;
-    for_each_candidate<DIM>(g, d.cstart, d.pos, d.cell[i], oi, ph.R2, ph.RP,
-                            [&](int j, const float4 &, float, float, float, float, unsigned) { cnt += j != i; });
+    for_each_candidate<DIM, true>(g, d.cstart, d.pos, d.cell[i], oi, ph.R2, ph.RP,
+                                  [&](int j, const float4 &, float, float, float, float, unsigned) { cnt += j != i; });
     count[i] = cnt;
 }
 
@@ -829,10 +1121,10 @@ __global__ void __launch_bounds__(256) k_nbr_fill(Dev d, Grid g, Phys ph, const 
     if (i >= d.n) return;
     const float4 oi = d.pos[i];
     long long w = start[i];
-    for_each_candidate<DIM>(g, d.cstart, d.pos, d.cell[i], oi, ph.R2, ph.RP,
-                            [&](int j, const float4 &, float, float, float, float, unsigned) {
-                                if (j != i) list[w++] = d.pid[j];
-                            });
+    for_each_candidate<DIM, true>(g, d.cstart, d.pos, d.cell[i], oi, ph.R2, ph.RP,
+                                  [&](int j, const float4 &, float, float, float, float, unsigned) {
+                                      if (j != i) list[w++] = d.pid[j];
+                                  });
 }
 
 // Totals of ordered neighbour pairs (j != i): [0] all, [1] of different phase.
@@ -844,11 +1136,11 @@ __global__ void __launch_bounds__(256) k_pair_stats(Dev d, Grid g, Phys ph, unsi
     if (i < d.n) {
         const float4 oi = d.pos[i];
         const int phi_ = phase_of(oi.w);
-        for_each_candidate<DIM>(g, d.cstart, d.pos, d.cell[i], oi, ph.R2, ph.RP,
-                                [&](int j, const float4 &oj, float, float, float, float, unsigned) {
-                                    all += j != i;
-                                    other += phase_of(oj.w) != phi_;
-                                });
+        for_each_candidate<DIM, true>(g, d.cstart, d.pos, d.cell[i], oi, ph.R2, ph.RP,
+                                      [&](int j, const float4 &oj, float, float, float, float, unsigned) {
+                                          all += j != i;
+                                          other += phase_of(oj.w) != phi_;
+                                      });
     }
     for (int o = 16; o > 0; o >>= 1) {
         all += __shfl_down_sync(0xffffffffu, all, o);
@@ -861,30 +1153,31 @@ __global__ void __launch_bounds__(256) k_pair_stats(Dev d, Grid g, Phys ph, unsi
 }
 
 // ---------------------------------------------------------------------------
-// Output in original order.
+// Output in original order; positions in each instance's own frame.
 
-enum ReadKind { RK_X, RK_U, RK_RHO, RK_RHO_EVAL, RK_P, RK_ACC, RK_DRHO, RK_T, RK_CELL, RK_ORDER };
+enum ReadKind { RK_X, RK_U, RK_RHO, RK_RHO_EVAL, RK_P, RK_ACC, RK_DRHO, RK_T, RK_CELL, RK_ORDER, RK_TAG };
 
 template <int DIM>
-__global__ void __launch_bounds__(256) k_unpermute(Dev d, Phys ph, int kind, double *out, int *iout)
+__global__ void __launch_bounds__(256) k_unpermute(Dev d, int kind, double *out, int *iout)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= d.n) return;
     const int n = d.n;
     const int p = d.pid[k];
     const int phs = d.tag[k] & 1;
+    const Inst &I = d.inst[d.iid[k]];
     switch (kind) {
     case RK_X:
-        for (int c = 0; c < DIM; ++c) out[(size_t)p * DIM + c] = d.x[(size_t)c * n + k];
+        for (int c = 0; c < DIM; ++c) out[(size_t)p * DIM + c] = d.x[(size_t)c * n + k] - I.offset[c];
         break;
     case RK_U:
         for (int c = 0; c < DIM; ++c) out[(size_t)p * DIM + c] = d.u[(size_t)c * n + k];
         break;
     case RK_RHO:
-        out[p] = (double)by_phase(phs, ph.rho0) + (double)d.drho[k];
+        out[p] = (double)by_phase(phs, I.rho0) + (double)d.drho[k];
         break;
     case RK_RHO_EVAL:
-        out[p] = (double)by_phase(phs, ph.rho0) + (double)d.drho_eval[k];
+        out[p] = (double)by_phase(phs, I.rho0) + (double)d.drho_eval[k];
         break;
     case RK_P:
         out[p] = d.pres[k];
@@ -901,7 +1194,7 @@ __global__ void __launch_bounds__(256) k_unpermute(Dev d, Phys ph, int kind, dou
     case RK_T: {
         const float4 t = d.T4[k];
         // T sigma^-2 was formed with V = m/rho of the renormalised density
-        const double v = (double)(by_phase(phs, ph.mass) / (by_phase(phs, ph.rho0) + d.drho_eval[k]));
+        const double v = (double)(by_phase(phs, I.mass) / (by_phase(phs, I.rho0) + d.drho_eval[k]));
         const double v2 = v * v;
         double T[9];
         if (DIM == 2) {
@@ -921,92 +1214,98 @@ __global__ void __launch_bounds__(256) k_unpermute(Dev d, Phys ph, int kind, dou
     case RK_ORDER:
         iout[k] = p;
         break;
+    case RK_TAG:
+        iout[p] = d.tag[k];
+        break;
     }
 }
 
 // ---------------------------------------------------------------------------
-// FP64 diagnostics: deterministic two-level reductions.
-
+// FP64 diagnostics of each instance: one block per instance reduces, in a
+// fixed tree order, over the instance's fluid particles taken in original
+// order from arrays written by k_unpermute (positions in the instance frame,
+// velocities, tags).  Per instance, DIAG_STRIDE doubles:
+//   [0] mass, [1..3] momentum sum m u, [4] kinetic energy, [5] potential
+//   energy -sum m g.x, [6..8] oil centroid, [9] oil count, [10] max |u|,
+//   [11..16] oil position covariance about the centroid (xx xy xz yy yz zz).
 constexpr int DIAG_THREADS = 256;
-constexpr int DIAG_K = 16;  // accumulated quantities per pass
+constexpr int DIAG_STRIDE = 20;
 
-__device__ __forceinline__ void block_reduce_store(double (&v)[DIAG_K], double *out)
+__device__ __forceinline__ double block_reduce(double v, double *sm, bool is_max)
+{
+    sm[threadIdx.x] = v;
+    __syncthreads();
+    for (int s = DIAG_THREADS / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s)
+            sm[threadIdx.x] = is_max ? fmax(sm[threadIdx.x], sm[threadIdx.x + s]) : sm[threadIdx.x] + sm[threadIdx.x + s];
+        __syncthreads();
+    }
+    const double r = sm[0];
+    __syncthreads();
+    return r;
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(DIAG_THREADS) k_diag_inst(const long long *first, const double *x, const double *u,
+                                                            const int *tag, const Inst *inst, const double *grav,
+                                                            double *out)
 {
     __shared__ double sm[DIAG_THREADS];
-#pragma unroll 1
-    for (int q = 0; q < DIAG_K; ++q) {
-        sm[threadIdx.x] = v[q];
-        __syncthreads();
-        for (int s = DIAG_THREADS / 2; s > 0; s >>= 1) {
-            if ((int)threadIdx.x < s) {
-                // max for the speed slot, sum otherwise
-                sm[threadIdx.x] = q == 15 ? fmax(sm[threadIdx.x], sm[threadIdx.x + s])
-                                          : sm[threadIdx.x] + sm[threadIdx.x + s];
-            }
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) out[q] = sm[0];
-        __syncthreads();
-    }
-}
-
-// pass 0: mass, momentum, energies, oil count and sum of oil positions, max|u|
-// pass 1: covariance of oil positions about the centroid `cen`
-template <int DIM>
-__global__ void __launch_bounds__(DIAG_THREADS) k_diag(Dev d, int pass, const double *cen, const double *grav,
-                                                       const double *mass, double *partial)
-{
-    double v[DIAG_K];
-#pragma unroll
-    for (int q = 0; q < DIAG_K; ++q) v[q] = 0.0;
-    const int n = d.n;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        const uint8_t tg = d.tag[k];
+    const int q = blockIdx.x;
+    const long long b = first[q], e = first[q + 1];
+    const Inst &I = inst[q];
+    double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};  // m, mu xyz, ekin, epot, oil sum xyz, oil count
+    double umax = 0.0;
+    for (long long k = b + threadIdx.x; k < e; k += DIAG_THREADS) {
+        const int tg = tag[k];
         if (tg & 2) continue;
         const int oil = tg & 1;
-        double x[3] = {0, 0, 0}, u[3] = {0, 0, 0};
+        const double m = oil ? I.mass64[1] : I.mass64[0];
+        double u2 = 0.0, gx = 0.0;
         for (int c = 0; c < DIM; ++c) {
-            x[c] = d.x[(size_t)c * n + k];
-            u[c] = d.u[(size_t)c * n + k];
+            const double uc = u[k * DIM + c], xc = x[k * DIM + c];
+            acc[1 + c] += m * uc;
+            u2 += uc * uc;
+            gx += grav[c] * xc;
+            if (oil) acc[6 + c] += xc;
         }
-        if (pass == 0) {
-            const double m = mass[oil];
-            const double u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-            v[0] += m;
-            v[1] += m * u[0];
-            v[2] += m * u[1];
-            v[3] += m * u[2];
-            v[4] += 0.5 * m * u2;
-            v[5] -= m * (grav[0] * x[0] + grav[1] * x[1] + grav[2] * x[2]);
-            if (oil) {
-                v[6] += x[0];
-                v[7] += x[1];
-                v[8] += x[2];
-                v[9] += 1.0;
-            }
-            v[15] = fmax(v[15], sqrt(u2));
-        } else if (oil) {
-            const double a = x[0] - cen[0], b = x[1] - cen[1], c = x[2] - cen[2];
-            v[0] += a * a;
-            v[1] += a * b;
-            v[2] += a * c;
-            v[3] += b * b;
-            v[4] += b * c;
-            v[5] += c * c;
-        }
+        acc[0] += m;
+        acc[4] += 0.5 * m * u2;
+        acc[5] -= m * gx;
+        acc[9] += oil;
+        umax = fmax(umax, sqrt(u2));
     }
-    block_reduce_store(v, partial + (size_t)blockIdx.x * DIAG_K);
-}
-
-__global__ void __launch_bounds__(DIAG_K) k_diag_final(const double *partial, int nblocks, double *out)
-{
-    const int q = threadIdx.x;
-    double s = 0.0;
-    for (int b = 0; b < nblocks; ++b) {
-        const double v = partial[(size_t)b * DIAG_K + q];
-        s = q == 15 ? fmax(s, v) : s + v;
+    double tot[10];
+#pragma unroll 1
+    for (int c = 0; c < 10; ++c) tot[c] = block_reduce(acc[c], sm, false);
+    const double vmax = block_reduce(umax, sm, true);
+    double cen[3] = {0, 0, 0};
+    if (tot[9] > 0)
+        for (int c = 0; c < DIM; ++c) cen[c] = tot[6 + c] / tot[9];
+    double cv[6] = {0, 0, 0, 0, 0, 0};
+    for (long long k = b + threadIdx.x; k < e; k += DIAG_THREADS) {
+        const int tg = tag[k];
+        if ((tg & 2) || !(tg & 1)) continue;
+        double r[3] = {0, 0, 0};
+        for (int c = 0; c < DIM; ++c) r[c] = x[k * DIM + c] - cen[c];
+        cv[0] += r[0] * r[0];
+        cv[1] += r[0] * r[1];
+        cv[2] += r[0] * r[2];
+        cv[3] += r[1] * r[1];
+        cv[4] += r[1] * r[2];
+        cv[5] += r[2] * r[2];
     }
-    out[q] = s;
+    double ctot[6];
+#pragma unroll 1
+    for (int c = 0; c < 6; ++c) ctot[c] = block_reduce(cv[c], sm, false);
+    if (threadIdx.x == 0) {
+        double *o = out + (size_t)q * DIAG_STRIDE;
+        for (int c = 0; c < 6; ++c) o[c] = tot[c];
+        for (int c = 0; c < 3; ++c) o[6 + c] = cen[c];
+        o[9] = tot[9];
+        o[10] = vmax;
+        for (int c = 0; c < 6; ++c) o[11 + c] = ctot[c];
+    }
 }
 
 }  // namespace sphgb

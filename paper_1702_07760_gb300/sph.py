@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, "libsph.so")
 
 SPH_OK = 0
 ERRORS = {-1: "SPH_EINVAL", -2: "SPH_ENOMEM", -3: "SPH_ECUDA", -4: "SPH_ENONFINITE",
-          -5: "SPH_ECFL", -6: "SPH_EDOMAIN", -7: "SPH_ECAPACITY"}
+          -5: "SPH_ECFL", -6: "SPH_EDOMAIN", -7: "SPH_ECAPACITY", -8: "SPH_ETIMEOUT"}
 VISC_DYNAMIC, VISC_KINEMATIC = 0, 1
 FIELD = dict(pos=0, vel=1, rho=2, rho_eval=3, pressure=4, acc=5, drho=6, tensor=7, cell=8, order=9)
 
@@ -25,7 +25,9 @@ EXPORTS = ["sph_create", "sph_set_state", "sph_build_cells", "sph_eval_rates", "
            "sph_sync", "sph_read", "sph_neighbours", "sph_pair_stats", "sph_diag", "sph_timing_enable",
            "sph_timing_reset", "sph_timing_count", "sph_timing_read", "sph_num_particles",
            "sph_step_index", "sph_num_cells", "sph_list_builds", "sph_destroy", "sph_last_error",
-           "sph_cell_sort_noalloc"]
+           "sph_cell_sort_noalloc", "sph_create_batch", "sph_set_dt_scales", "sph_run_persistent",
+           "sph_set_launch_shape", "sph_get_launch_shape", "sph_autotune", "sph_diag_instances",
+           "sph_num_instances", "sph_test_stall_barrier"]
 
 
 class SphError(RuntimeError):
@@ -78,6 +80,16 @@ def load(path: str = LIB_PATH):
     L.sph_destroy.restype = None
     L.sph_last_error.restype = C.c_char_p
     L.sph_cell_sort_noalloc.argtypes = [P(SphParams), C.c_int64, vp, vp, vp, vp]
+    L.sph_create_batch.argtypes = [C.c_int, P(SphParams), P(C.c_int64), dp, dp, dp, u8p, u8p, vp, P(H)]
+    L.sph_set_dt_scales.argtypes = [H, dp]
+    L.sph_run_persistent.argtypes = [H, C.c_double, C.c_int64, C.c_int]
+    L.sph_set_launch_shape.argtypes = [H, C.c_int, C.c_int, C.c_int]
+    L.sph_get_launch_shape.argtypes = [H, P(C.c_int), P(C.c_int), P(C.c_int)]
+    L.sph_autotune.argtypes = [H, C.c_double, C.c_int, P(C.c_int), P(C.c_int), P(C.c_int), dp]
+    L.sph_diag_instances.argtypes = [H, dp]
+    L.sph_num_instances.argtypes = [H]
+    L.sph_test_stall_barrier.argtypes = [H]
+    L.sph_num_instances.restype = C.c_int64
     _lib = L
     return L
 
@@ -141,6 +153,44 @@ class Simulation:
     def from_workload(cls, w, stream=None):
         return cls(w.params, w.x, w.u, w.rho, w.phase, w.wall, stream)
 
+    @classmethod
+    def batch(cls, workloads, stream: int | None = None) -> "Simulation":
+        """One handle over independent instances (sph_create_batch): the
+        workloads' particles one after another, each in its own frame."""
+        L = load()
+        self = cls.__new__(cls)
+        k = len(workloads)
+        self.params = dict(workloads[0].params)
+        self.dim = int(self.params["dim"])
+        ps = (SphParams * k)(*[make_params(w.params) for w in workloads])
+        counts = np.array([w.n for w in workloads], np.int64)
+        x = np.ascontiguousarray(np.concatenate([w.x for w in workloads]), np.float64)
+        u = np.ascontiguousarray(np.concatenate([w.u for w in workloads]), np.float64)
+        rho = np.ascontiguousarray(np.concatenate([w.rho for w in workloads]), np.float64)
+        phase = np.ascontiguousarray(np.concatenate([w.phase for w in workloads]), np.uint8)
+        wall = np.ascontiguousarray(np.concatenate([w.wall for w in workloads]), np.uint8)
+        self.n = len(x)
+        self._p = ps
+        self.first = np.concatenate([[0], np.cumsum(counts)])
+        h = C.c_void_p()
+        self._h = None
+        _check(L.sph_create_batch(k, ps, counts.ctypes.data_as(C.POINTER(C.c_int64)), _dp(x), _dp(u),
+                                  _dp(rho), phase.ctypes.data_as(C.POINTER(C.c_uint8)),
+                                  wall.ctypes.data_as(C.POINTER(C.c_uint8)), C.c_void_p(stream or 0),
+                                  C.byref(h)))
+        self._h = h
+        return self
+
+    @property
+    def num_instances(self) -> int:
+        return int(load().sph_num_instances(self._h))
+
+    def set_dt_scales(self, scales):
+        sc = np.ascontiguousarray(scales, np.float64)
+        if len(sc) != self.num_instances:
+            raise ValueError("one scale per instance")
+        _check(load().sph_set_dt_scales(self._h, _dp(sc)))
+
     # -- stepping ---------------------------------------------------------
     def set_state(self, x, u, rho):
         x = np.ascontiguousarray(x, np.float64)
@@ -159,6 +209,30 @@ class Simulation:
 
     def run(self, dt: float, nsteps: int, graph: bool = True):
         _check(load().sph_run(self._h, dt, int(nsteps), int(bool(graph))))
+
+    def run_persistent(self, dt: float, nsteps: int, graph: bool = True):
+        """nsteps steps in one cooperative launch (sph_run_persistent)."""
+        _check(load().sph_run_persistent(self._h, dt, int(nsteps), int(bool(graph))))
+
+    def set_launch_shape(self, block: int, grid_blocks: int = 0, dynamic_chunks: bool = True):
+        _check(load().sph_set_launch_shape(self._h, int(block), int(grid_blocks), int(bool(dynamic_chunks))))
+
+    def launch_shape(self):
+        """(block, grid blocks, dynamic chunks) of the persistent launch on this device."""
+        b, g, d = C.c_int(), C.c_int(), C.c_int()
+        _check(load().sph_get_launch_shape(self._h, C.byref(b), C.byref(g), C.byref(d)))
+        return b.value, g.value, bool(d.value)
+
+    def autotune(self, dt: float, trial_steps: int = 20):
+        """Fastest persistent launch shape: (block, grid blocks, dynamic chunks, ms per step)."""
+        b, g, d, ms = C.c_int(), C.c_int(), C.c_int(), C.c_double()
+        _check(load().sph_autotune(self._h, dt, int(trial_steps), C.byref(b), C.byref(g), C.byref(d),
+                                   C.byref(ms)))
+        return b.value, g.value, bool(d.value), ms.value
+
+    def test_stall_barrier(self):
+        """Makes the next run_persistent time out at its first barrier (test support)."""
+        _check(load().sph_test_stall_barrier(self._h))
 
     def sync(self):
         _check(load().sph_sync(self._h))
@@ -191,12 +265,22 @@ class Simulation:
         _check(load().sph_pair_stats(self._h, out.ctypes.data_as(C.POINTER(C.c_int64))))
         return int(out[0]), int(out[1])
 
+    @staticmethod
+    def _diag_dict(out, d):
+        return dict(mass=out[0], momentum=out[1:1 + d].copy(), e_kin=out[4], e_pot=out[5],
+                    centroid=out[6:6 + d].copy(), sphericity=out[9], u_max=out[10], n_oil=int(out[11]))
+
     def diagnostics(self) -> dict:
         out = np.zeros(12)
         _check(load().sph_diag(self._h, _dp(out)))
-        d = self.dim
-        return dict(mass=out[0], momentum=out[1:1 + d].copy(), e_kin=out[4], e_pot=out[5],
-                    centroid=out[6:6 + d].copy(), sphericity=out[9], u_max=out[10], n_oil=int(out[11]))
+        return self._diag_dict(out, self.dim)
+
+    def diagnostics_instances(self) -> list:
+        """diagnostics() of every instance of a batch, positions in each instance's frame."""
+        k = self.num_instances
+        out = np.zeros(12 * k)
+        _check(load().sph_diag_instances(self._h, _dp(out)))
+        return [self._diag_dict(out[12 * q:12 * q + 12], self.dim) for q in range(k)]
 
     # -- timing -----------------------------------------------------------
     def timing(self, enable: bool):

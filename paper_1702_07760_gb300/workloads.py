@@ -171,3 +171,42 @@ def drop_3d(seed: int = 1000, perturb: bool = False, **kw) -> Workload:
 def stable_dt(p: dict, cfl: float = 0.25) -> float:
     """Acoustic time step 0.25 h / c0 used by the drop-rise workloads."""
     return cfl * p["h"] / p["c0"]
+
+
+def drop_batch_2d(k: int = 256, seed: int = 3000, dx: float = 2.5e-4, wall_layers: int = 3,
+                  d_range=(8.0, 40.0), mu_ratio_range=(1.0, 100.0), sigma_range=(0.01, 0.05),
+                  rho_ratio_range=(0.80, 0.95), perturb: bool = False) -> list:
+    """k independent 2-D drop-rise instances of uneven size for the batched form.
+
+    Per instance q, drawn in order from ``Generator(PCG64(seed))``: the drop
+    diameter D/dx log-uniform in d_range, the oil/water viscosity ratio
+    log-uniform in mu_ratio_range, the tension alpha_s uniform in sigma_range
+    and the oil/water density ratio uniform in rho_ratio_range.  The tank is
+    4D x 8D of fluid lattice (2 048 to 51 200 fluid particles for D/dx in
+    [8, 40]) in a closed box of wall layers, the drop at (W/2, H/4); its
+    jitter is seeded with seed + 1 + q.  Water is rho0 = 1000, mu = 1e-3.
+    All instances share dx (so h, delta and the cell size); c0 = 10 sqrt(2 g H)
+    follows each tank's depth, so each has its own acoustic step.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for q in range(k):
+        ddx = float(np.exp(rng.uniform(np.log(d_range[0]), np.log(d_range[1]))))
+        mu_ratio = float(np.exp(rng.uniform(np.log(mu_ratio_range[0]), np.log(mu_ratio_range[1]))))
+        sigma = float(rng.uniform(*sigma_range))
+        rho_ratio = float(rng.uniform(*rho_ratio_range))
+        shape = (max(4, int(round(4 * ddx))), max(8, int(round(8 * ddx))))
+        w = drop_tank(2, shape, dx=dx, drop_d_dx=ddx, wall_layers=wall_layers, seed=seed + 1 + q,
+                      perturb=perturb, rho0=(1000.0, 1000.0 * rho_ratio), mu=(1e-3, 1e-3 * mu_ratio),
+                      alpha_s=sigma, name=f"drop_batch_{seed}_{q}")
+        w.meta.update(drop_d_dx=ddx, mu_ratio=mu_ratio, sigma=sigma, rho_ratio=rho_ratio)
+        out.append(w)
+    return out
+
+
+def batch_dt(workloads, cfl: float = 0.25):
+    """Common step dt (the largest instance step) and each instance's scale
+    dt_q / dt in (0, 1] for a batch advanced together."""
+    dts = np.array([stable_dt(w.params, cfl) for w in workloads])
+    dt = float(dts.max())
+    return dt, dts / dt

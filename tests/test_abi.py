@@ -72,3 +72,26 @@ def test_kernels_compile_for_sm103a_without_spills():
         assert blocks, kern
         for b in blocks:
             assert "0 bytes spill stores" in b, b[:400]
+
+
+def test_batch_validation_without_a_gpu(lib):
+    """sph_create_batch checks the shared parameters and every instance's
+    particles before it touches the device."""
+    from paper_1702_07760_gb300 import workloads as WL
+    ws = WL.drop_batch_2d(k=3, seed=5, d_range=(4.0, 5.0))
+    # instances differing in a shared parameter (h through dx)
+    odd = WL.drop_tank(2, (8, 16), dx=3e-4)
+    with pytest.raises(sph.SphError) as e:
+        sph.Simulation.batch(ws + [odd])
+    assert e.value.code == -1 and "share" in str(e.value)
+    # a particle outside its own instance's box
+    bad = ws[1].copy()
+    bad.x[0, 1] = bad.params["box_hi"][1] + 1e-3
+    with pytest.raises(sph.SphError) as e:
+        sph.Simulation.batch([ws[0], bad, ws[2]])
+    assert e.value.code == -1 and "outside" in str(e.value)
+    bad = ws[2].copy()
+    bad.params = dict(bad.params, gamma=6.0)
+    with pytest.raises(sph.SphError) as e:
+        sph.Simulation.batch([ws[0], bad])
+    assert e.value.code == -1

@@ -1,0 +1,179 @@
+"""The persistent single-launch form and batches of independent instances.
+
+* sph_run_persistent runs the same per-particle arithmetic in the same
+  summation order as the per-kernel launches, so the two agree bit for bit,
+  with or without graph capture and with list rebuilds inside the launch.
+* A batch places each instance's box on a super-cell boundary of the shared
+  grid, so every instance sees the cell geometry it has alone: its rates
+  match the oracle run on that instance alone, and its trajectory matches the
+  instance simulated alone up to FP64 rounding of the shifted positions.
+* The barrier time-out is exercised with a barrier that no arrival completes
+  (a bounded wait that runs out), never with a fault.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1702_07760_gb300 import workloads as WL
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def sphmod():
+    from paper_1702_07760_gb300 import build as B
+    from paper_1702_07760_gb300 import sph
+    B.build()
+    sph.load()
+    return sph
+
+
+def _small_batch(k=5, seed=77):
+    """k small uneven 2-D instances (D/dx in [5, 9]) with varied fluids."""
+    return WL.drop_batch_2d(k=k, seed=seed, d_range=(5.0, 9.0), perturb=True)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("graph", [False, True])
+def test_persistent_matches_per_launch(sphmod, dim, graph):
+    if dim == 2:
+        w = WL.drop_tank(2, (45, 70), drop_d_dx=12, seed=31, perturb=True)
+    else:
+        w = WL.drop_tank(3, (14, 15, 22), drop_d_dx=8, seed=32, perturb=True)
+    dt = WL.stable_dt(w.params)
+    a = sphmod.Simulation.from_workload(w)
+    b = sphmod.Simulation.from_workload(w)
+    a.run(dt, 25, graph=True)
+    b.run_persistent(dt, 10, graph=graph)
+    b.run_persistent(dt, 15, graph=graph)
+    for f in ("pos", "vel", "rho", "order"):
+        assert np.array_equal(a.read(f), b.read(f)), f
+    assert a.list_builds == b.list_builds >= 2
+    assert a.step_index == b.step_index == 25
+
+
+def test_persistent_launch_shapes_agree(sphmod):
+    w = WL.drop_tank(2, (33, 41), drop_d_dx=10, seed=33, perturb=True)
+    dt = WL.stable_dt(w.params)
+    ref = sphmod.Simulation.from_workload(w)
+    ref.run(dt, 12)
+    for block, grid, dyn in [(128, 152, True), (256, 456, False), (512, 0, True), (128, 8, False), (512, 19, True)]:
+        s = sphmod.Simulation.from_workload(w)
+        s.set_launch_shape(block, grid, dyn)
+        b, g, d = s.launch_shape()
+        assert b == block and d == dyn and (g == grid or (grid == 0 and g >= 152))
+        s.run_persistent(dt, 12)
+        assert np.array_equal(ref.read("pos"), s.read("pos")), (block, grid)
+        s.close()
+    with pytest.raises(sphmod.SphError):
+        ref.set_launch_shape(192, 1)
+
+
+def test_autotune_keeps_the_state(sphmod):
+    w = WL.drop_tank(2, (30, 44), drop_d_dx=10, seed=34, perturb=True)
+    dt = WL.stable_dt(w.params)
+    s = sphmod.Simulation.from_workload(w)
+    s.run(dt, 5)
+    x0, u0, r0 = s.read("pos"), s.read("vel"), s.read("rho")
+    builds = s.list_builds
+    block, grid, dyn, ms = s.autotune(dt, trial_steps=3)
+    assert block in (128, 256, 512) and grid >= 1 and ms > 0
+    assert s.launch_shape() == (block, grid, dyn)
+    assert np.array_equal(s.read("pos"), x0) and np.array_equal(s.read("vel"), u0)
+    assert np.array_equal(s.read("rho"), r0)
+    assert s.step_index == 5 and s.list_builds == builds
+    # the run after tuning equals one from the same state without tuning
+    t = sphmod.Simulation(w.params, x0, u0, r0, w.phase, w.wall)
+    s.run_persistent(dt, 6)
+    t.run(dt, 6)
+    assert np.allclose(s.read("pos"), t.read("pos"), rtol=0, atol=1e-9 * w.params["dx"])
+
+
+def test_barrier_timeout_is_reported_and_recovers(sphmod):
+    w = WL.drop_tank(2, (20, 24), drop_d_dx=6, seed=35)
+    dt = WL.stable_dt(w.params)
+    s = sphmod.Simulation.from_workload(w)
+    s.set_launch_shape(256, 152)
+    s.test_stall_barrier()
+    with pytest.raises(sphmod.SphError) as e:
+        s.run_persistent(dt, 3, graph=False)
+    assert e.value.code == -8
+    # the barrier is reset: the next launch runs normally
+    s.set_state(w.x, w.u, w.rho)
+    s.run_persistent(dt, 4, graph=False)
+    ref = sphmod.Simulation.from_workload(w)
+    ref.run(dt, 4)
+    assert np.allclose(s.read("pos"), ref.read("pos"), rtol=0, atol=1e-9 * w.params["dx"])
+
+
+def test_batch_rates_match_oracle_per_instance(sphmod):
+    ws = _small_batch()
+    sim = sphmod.Simulation.batch(ws)
+    assert sim.num_instances == len(ws)
+    sim.eval_rates()
+    got = {k: sim.read(k) for k in ("rho_eval", "acc", "drho", "pos")}
+    first = np.concatenate([[0], np.cumsum([w.n for w in ws])])
+    for q, w in enumerate(ws):
+        sl = slice(first[q], first[q + 1])
+        # read back in the instance's frame (shifted and unshifted in FP64)
+        assert np.abs(got["pos"][sl] - w.x).max() < 1e-11 * w.params["dx"]
+        ref = oracle.evaluate(w.params, w.x, w.u, w.rho, w.phase, w.wall, renorm=True)
+        fl = w.wall == 0
+        e_rho = np.abs(got["rho_eval"][sl] / ref["rho"] - 1).max()
+        a = got["acc"][sl]
+        e_a = np.linalg.norm(a[fl] - ref["a"][fl], axis=1).max() / np.linalg.norm(ref["a"][fl], axis=1).max()
+        d = got["drho"][sl]
+        e_dr = np.abs(d - ref["drho"]).max() / np.abs(ref["drho"]).max()
+        print(f"\n[instance {q} n={w.n}] rho {e_rho:.2e} acc {e_a:.2e} drho {e_dr:.2e}")
+        assert e_rho <= TOL and e_a <= TOL and e_dr <= TOL
+
+
+def test_batch_persistent_matches_instances_alone(sphmod):
+    ws = _small_batch(k=6, seed=78)
+    dt, scales = WL.batch_dt(ws)
+    nsteps = 40
+    batch = sphmod.Simulation.batch(ws)
+    batch.set_dt_scales(scales)
+    batch.run_persistent(dt, nsteps)
+    x = batch.read("pos")
+    diags = batch.diagnostics_instances()
+    first = np.concatenate([[0], np.cumsum([w.n for w in ws])])
+    for q, w in enumerate(ws):
+        alone = sphmod.Simulation.from_workload(w)
+        alone.run(dt * scales[q], nsteps)
+        xa = alone.read("pos")
+        dxq = w.params["dx"]
+        err = np.abs(x[first[q]:first[q + 1]] - xa).max() / dxq
+        da = alone.diagnostics()
+        c_err = np.linalg.norm(diags[q]["centroid"] - da["centroid"]) / (2 * w.meta["drop_radius"])
+        print(f"\n[instance {q}] max|x - x_alone|/dx {err:.2e} centroid/D {c_err:.2e}")
+        assert err < 1e-5
+        assert c_err < 1e-6
+        assert abs(diags[q]["mass"] / da["mass"] - 1) < 1e-12
+        assert diags[q]["n_oil"] == da["n_oil"] == w.meta["n_oil"]
+        alone.close()
+
+
+def test_batch_diagnostics_match_oracle(sphmod):
+    ws = _small_batch(k=4, seed=79)
+    sim = sphmod.Simulation.batch(ws)
+    for d, w in zip(sim.diagnostics_instances(), ws):
+        r = oracle.diagnostics(w.params, w.x, w.u, w.phase, w.wall)
+        assert abs(d["mass"] / r["mass"] - 1) < 1e-12
+        assert np.allclose(d["centroid"], r["centroid"], rtol=1e-12)
+        assert abs(d["e_kin"] / r["e_kin"] - 1) < 1e-10
+        assert abs(d["e_pot"] / r["e_pot"] - 1) < 1e-10
+        assert abs(d["sphericity"] - r["sphericity"]) < 1e-9
+        assert d["n_oil"] == r["n_oil"]
+
+
+def test_batch_of_one_equals_plain(sphmod):
+    w = WL.drop_tank(2, (26, 30), drop_d_dx=8, seed=36, perturb=True)
+    dt = WL.stable_dt(w.params)
+    a = sphmod.Simulation.batch([w])
+    b = sphmod.Simulation.from_workload(w)
+    a.run(dt, 7)
+    b.run(dt, 7)
+    assert np.array_equal(a.read("pos"), b.read("pos"))
