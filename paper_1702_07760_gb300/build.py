@@ -1,4 +1,7 @@
-"""Builds the CUDA library libsph.so in-tree for sm_103a with nvcc."""
+"""Builds the CUDA library libsph.so in-tree for sm_103a with nvcc.
+
+Each translation unit is compiled to an object in parallel (under _build/),
+then linked into one shared library."""
 from __future__ import annotations
 
 import os
@@ -9,32 +12,55 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libsph.so")
-SOURCES = ["sph_api.cu", "sph_noalloc.cu"]
-HEADERS = ["sph_kernels.cuh"]
+OBJ_DIR = os.path.join(ROOT, "_build")
+SOURCES = ["sph_api.cu", "sph_noalloc.cu", "mpnn.cu"]
+HEADERS = ["sph_kernels.cuh", "umma.cuh"]
+PUBLIC_HEADERS = ["sph.h", "sph_surrogate.h"]
+FLAGS = ["-O3", "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-Xcompiler", "-fPIC"]
+
+
+def _includes():
+    return ["-I", os.path.join(ROOT, "include"), "-I", CSRC]
 
 
 def nvcc_command(out: str = LIB, extra=()):
-    return [
-        "nvcc", "-O3", "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo",
-        "-Xcompiler", "-fPIC", "-shared", "-I", os.path.join(ROOT, "include"), "-I", CSRC,
-        *extra, "-o", out, *[os.path.join(CSRC, s) for s in SOURCES],
-    ]
+    """One nvcc invocation compiling and linking every source (used to inspect
+    ptxas output)."""
+    return ["nvcc", *FLAGS, "-shared", *_includes(), *extra, "-o", out,
+            *[os.path.join(CSRC, s) for s in SOURCES]]
 
 
 def stale() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = [os.path.join(CSRC, f) for f in SOURCES + HEADERS] + [os.path.join(ROOT, "include", "sph.h")]
+    deps = [os.path.join(CSRC, f) for f in SOURCES + HEADERS] + \
+        [os.path.join(ROOT, "include", h) for h in PUBLIC_HEADERS]
     return any(os.path.getmtime(d) > t for d in deps)
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    if force or stale():
-        tmp = LIB + f".tmp{os.getpid()}"
-        cmd = nvcc_command(tmp, ("-Xptxas", "-v") if verbose else ())
-        subprocess.check_call(cmd)
-        os.replace(tmp, LIB)
+    if not (force or stale()):
+        return LIB
+    os.makedirs(OBJ_DIR, exist_ok=True)
+    extra = ["-Xptxas", "-v"] if verbose else []
+    procs, objs = [], []
+    for s in SOURCES:
+        obj = os.path.join(OBJ_DIR, os.path.splitext(s)[0] + f".{os.getpid()}.o")
+        objs.append(obj)
+        procs.append(subprocess.Popen(["nvcc", *FLAGS, *_includes(), *extra, "-c", "-o", obj,
+                                       os.path.join(CSRC, s)]))
+    codes = [p.wait() for p in procs]
+    if any(codes):
+        for o in objs:
+            if os.path.exists(o):
+                os.remove(o)
+        raise subprocess.CalledProcessError(max(codes, key=abs), "nvcc")
+    tmp = LIB + f".tmp{os.getpid()}"
+    subprocess.check_call(["nvcc", "-shared", "-gencode", "arch=compute_103a,code=sm_103a", "-o", tmp, *objs])
+    for o in objs:
+        os.remove(o)
+    os.replace(tmp, LIB)
     return LIB
 
 

@@ -836,20 +836,20 @@ __device__ __forceinline__ int renorm_now(const Dev &d, const Phys &ph, int stag
 // device flag `rebuild` is set.
 
 template <int DIM>
-__global__ void __launch_bounds__(256) k_hash(Dev d, Grid g, Sort s)
+static __global__ void __launch_bounds__(256) k_hash(Dev d, Grid g, Sort s)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= d.n || !*d.rebuild) return;
     hash_one<DIM>(d, g, s, k);
 }
 
-__global__ void __launch_bounds__(256) k_zero(int *a, int m, const unsigned *rebuild)
+static __global__ void __launch_bounds__(256) k_zero(int *a, int m, const unsigned *rebuild)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < m && *rebuild) a[i] = 0;
 }
 
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan_tiles(const int *in, int *out, int *tile_sums, int m,
+static __global__ void __launch_bounds__(SCAN_THREADS) k_scan_tiles(const int *in, int *out, int *tile_sums, int m,
                                                               const unsigned *rebuild)
 {
     if (!*rebuild) return;
@@ -858,27 +858,27 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_tiles(const int *in, int 
 }
 
 // Scans the tile sums in place (one block) and writes the grand total to out[m].
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan_sums(int *tile_sums, int ntiles, int *out, int m,
+static __global__ void __launch_bounds__(SCAN_THREADS) k_scan_sums(int *tile_sums, int ntiles, int *out, int m,
                                                              const unsigned *rebuild)
 {
     if (!*rebuild) return;
     scan_tile_sums(tile_sums, ntiles, out, m);
 }
 
-__global__ void __launch_bounds__(256) k_scan_add(int *out, const int *tile_sums, int m, const unsigned *rebuild)
+static __global__ void __launch_bounds__(256) k_scan_add(int *out, const int *tile_sums, int m, const unsigned *rebuild)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < m && *rebuild) out[i] += tile_sums[i / SCAN_TILE];
 }
 
-__global__ void __launch_bounds__(256) k_scatter(int n, Sort s, const int *cstart, const unsigned *rebuild)
+static __global__ void __launch_bounds__(256) k_scatter(int n, Sort s, const int *cstart, const unsigned *rebuild)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n || !*rebuild) return;
     scatter_one(s, cstart, k);
 }
 
-__global__ void __launch_bounds__(256) k_rank(int n, Sort s, const int *pid, const int *cstart,
+static __global__ void __launch_bounds__(256) k_rank(int n, Sort s, const int *pid, const int *cstart,
                                               const unsigned *rebuild)
 {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -887,7 +887,7 @@ __global__ void __launch_bounds__(256) k_rank(int n, Sort s, const int *pid, con
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(256) k_gather(Dev src, Dev dst, Grid g, Sort s)
+static __global__ void __launch_bounds__(256) k_gather(Dev src, Dev dst, Grid g, Sort s)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= src.n || !*src.rebuild) return;
@@ -895,7 +895,7 @@ __global__ void __launch_bounds__(256) k_gather(Dev src, Dev dst, Grid g, Sort s
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(256) k_copy_back(Dev src, Dev dst)
+static __global__ void __launch_bounds__(256) k_copy_back(Dev src, Dev dst)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= src.n || !*dst.rebuild) return;
@@ -903,7 +903,7 @@ __global__ void __launch_bounds__(256) k_copy_back(Dev src, Dev dst)
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(256, 4) k_build_list(Dev d, Grid g, Phys ph)
+static __global__ void __launch_bounds__(256, 4) k_build_list(Dev d, Grid g, Phys ph)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.n || !*d.rebuild) return;
@@ -912,7 +912,7 @@ __global__ void __launch_bounds__(256, 4) k_build_list(Dev d, Grid g, Phys ph)
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(256) k_sweep_a(Dev d, Grid g, Phys ph, const float *__restrict__ drho_in, int stage1,
+static __global__ void __launch_bounds__(256) k_sweep_a(Dev d, Grid g, Phys ph, const float *__restrict__ drho_in, int stage1,
                                                  float4 *vel_s)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -924,7 +924,7 @@ __global__ void __launch_bounds__(256) k_sweep_a(Dev d, Grid g, Phys ph, const f
 }
 
 template <int DIM, int STAGE>
-__global__ void __launch_bounds__(256, 4) k_sweep_b(Dev d, Grid g, Phys ph, double dt)
+static __global__ void __launch_bounds__(256, 4) k_sweep_b(Dev d, Grid g, Phys ph, double dt)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.n) return;
@@ -1103,7 +1103,7 @@ __device__ __forceinline__ void persistent_steps(Dev d, Dev scratch, Grid g, Phy
 // Neighbour sets and pair statistics by the sweeps' own support test.
 
 template <int DIM>
-__global__ void __launch_bounds__(256) k_nbr_count(Dev d, Grid g, Phys ph, int *count)
+static __global__ void __launch_bounds__(256) k_nbr_count(Dev d, Grid g, Phys ph, int *count)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.n) return;
@@ -1115,7 +1115,7 @@ __global__ void __launch_bounds__(256) k_nbr_count(Dev d, Grid g, Phys ph, int *
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(256) k_nbr_fill(Dev d, Grid g, Phys ph, const long long *start, int *list)
+static __global__ void __launch_bounds__(256) k_nbr_fill(Dev d, Grid g, Phys ph, const long long *start, int *list)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.n) return;
@@ -1129,7 +1129,7 @@ __global__ void __launch_bounds__(256) k_nbr_fill(Dev d, Grid g, Phys ph, const 
 
 // Totals of ordered neighbour pairs (j != i): [0] all, [1] of different phase.
 template <int DIM>
-__global__ void __launch_bounds__(256) k_pair_stats(Dev d, Grid g, Phys ph, unsigned long long *tot)
+static __global__ void __launch_bounds__(256) k_pair_stats(Dev d, Grid g, Phys ph, unsigned long long *tot)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     int all = 0, other = 0;
@@ -1158,7 +1158,7 @@ __global__ void __launch_bounds__(256) k_pair_stats(Dev d, Grid g, Phys ph, unsi
 enum ReadKind { RK_X, RK_U, RK_RHO, RK_RHO_EVAL, RK_P, RK_ACC, RK_DRHO, RK_T, RK_CELL, RK_ORDER, RK_TAG };
 
 template <int DIM>
-__global__ void __launch_bounds__(256) k_unpermute(Dev d, int kind, double *out, int *iout)
+static __global__ void __launch_bounds__(256) k_unpermute(Dev d, int kind, double *out, int *iout)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= d.n) return;
@@ -1246,7 +1246,7 @@ __device__ __forceinline__ double block_reduce(double v, double *sm, bool is_max
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(DIAG_THREADS) k_diag_inst(const long long *first, const double *x, const double *u,
+static __global__ void __launch_bounds__(DIAG_THREADS) k_diag_inst(const long long *first, const double *x, const double *u,
                                                             const int *tag, const Inst *inst, const double *grav,
                                                             double *out)
 {

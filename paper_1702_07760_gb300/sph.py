@@ -20,14 +20,14 @@ ERRORS = {-1: "SPH_EINVAL", -2: "SPH_ENOMEM", -3: "SPH_ECUDA", -4: "SPH_ENONFINI
 VISC_DYNAMIC, VISC_KINEMATIC = 0, 1
 FIELD = dict(pos=0, vel=1, rho=2, rho_eval=3, pressure=4, acc=5, drho=6, tensor=7, cell=8, order=9)
 
-# entry points declared in include/sph.h
+# entry points declared in include/sph.h and include/sph_surrogate.h
 EXPORTS = ["sph_create", "sph_set_state", "sph_build_cells", "sph_eval_rates", "sph_step", "sph_run",
            "sph_sync", "sph_read", "sph_neighbours", "sph_pair_stats", "sph_diag", "sph_timing_enable",
            "sph_timing_reset", "sph_timing_count", "sph_timing_read", "sph_num_particles",
            "sph_step_index", "sph_num_cells", "sph_list_builds", "sph_destroy", "sph_last_error",
            "sph_cell_sort_noalloc", "sph_create_batch", "sph_set_dt_scales", "sph_run_persistent",
            "sph_set_launch_shape", "sph_get_launch_shape", "sph_autotune", "sph_diag_instances",
-           "sph_num_instances", "sph_test_stall_barrier"]
+           "sph_num_instances", "sph_test_stall_barrier", "sph_mm_bf16"]
 
 
 class SphError(RuntimeError):
@@ -89,6 +89,8 @@ def load(path: str = LIB_PATH):
     L.sph_diag_instances.argtypes = [H, dp]
     L.sph_num_instances.argtypes = [H]
     L.sph_test_stall_barrier.argtypes = [H]
+    L.sph_mm_bf16.argtypes = [vp, C.c_int, vp, C.c_int, vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                              vp, vp]
     L.sph_num_instances.restype = C.c_int64
     _lib = L
     return L
@@ -126,6 +128,14 @@ def cell_sort_noalloc(params: dict, n: int, x_dev: int, cell_dev: int, order_dev
     p = make_params(params)
     _check(load().sph_cell_sort_noalloc(C.byref(p), int(n), C.c_void_p(x_dev), C.c_void_p(cell_dev),
                                         C.c_void_p(order_dev), C.c_void_p(stream)))
+
+
+def mm_bf16(a_ptr: int, lda: int, b_ptr: int, ldb: int, c_ptr: int, ldc: int, M: int, N: int, K: int,
+            k_split: int = 0, accumulate: bool = False, stream: int = 0, err_ptr: int = 0):
+    """C = A B^T on the tensor cores for device arrays given by address (see
+    sph_mm_bf16 in include/sph_surrogate.h)."""
+    _check(load().sph_mm_bf16(C.c_void_p(a_ptr), lda, C.c_void_p(b_ptr), ldb, C.c_void_p(c_ptr), ldc, M, N, K,
+                              k_split, int(bool(accumulate)), C.c_void_p(stream), C.c_void_p(err_ptr)))
 
 
 class Simulation:
