@@ -31,6 +31,69 @@ extern "C" {
 int sph_mm_bf16(const void *A, int lda, const void *B, int ldb, float *C, int ldc, int M, int N, int K,
                 int k_split, int accumulate, void *stream, unsigned *err_dev);
 
+/* State snapshots in original particle order, in device memory owned by the
+ * caller: x and u of n * dim doubles (particle-major, each instance in its
+ * own frame), rho of n doubles.  sph_snapshot queues the copy; 
+ * sph_load_snapshot replaces the handle's state (the next step rebuilds the
+ * lists) without changing the step counter. */
+int sph_snapshot(sph_handle h, double *x_dev, double *u_dev, double *rho_dev);
+int sph_load_snapshot(sph_handle h, const double *x_dev, const double *u_dev, const double *rho_dev);
+
+/* Attaches the learned surrogate to a single-instance handle (or replaces
+ * its parameters).  weights: nweights host doubles in the flat format of
+ * paper_1702_07760_gb300/surrogate_layout.py (held on the device as FP32
+ * master weights, with BF16 copies for the tensor cores); norm: the
+ * normalisation block of that format (6 dim + 14 doubles: mu_in, sd_in,
+ * mu_out, sd_out, k_ref, the jump time T = k dt, sd_edge_u, sd_edge_rho).
+ * Resets the Adam state.  The network, for every particle, maps the state
+ * and the plain method's rates at that state (acceleration a, density rate)
+ * to its increments over the jump: encoder, two rounds of edge messages over
+ * the neighbour pairs closer than 2h (edge inputs: relative position,
+ * distance, phase change, velocity and density differences; summed, scaled
+ * by 1/k_ref) with a residual node update, decoder giving corrections to the
+ * explicit jump: du = T a + c_u, drho = T Drho/Dt + c_rho, and
+ * dx = T (u + du / 2) + c_x. */
+int sph_surrogate_init(sph_handle h, const double *weights, int64_t nweights, const double *norm, int64_t nnorm);
+
+/* Copies the current FP32 master weights to host doubles. */
+int sph_surrogate_get_weights(sph_handle h, double *weights, int64_t nweights);
+
+/* Network increments at the current state, in original particle order:
+ * out[p * (2 dim + 1) + c] holds dx (dim), du (dim) and drho (1); walls get
+ * zero dx and du.  Evaluates the rates at the current state first (which
+ * rebuilds the lists and overwrites the eval fields).  Waits for the
+ * stream. */
+int sph_surrogate_predict(sph_handle h, double *out_host, int64_t bytes);
+
+/* Advances the state by one rates evaluation and one network evaluation
+ * standing for k_steps plain steps: x += dx and u += du on fluid particles,
+ * rho += drho on all; adds k_steps to the step counters.  Queues the work. */
+int sph_surrogate_advance(sph_handle h, int k_steps);
+
+/* One training step on the pair (current state, state after k plain
+ * steps): x1, u1, rho1 are device arrays in the snapshot layout.  Computes
+ * the masked mean squared error of the normalised targets (position
+ * increment minus T (u + u1) / 2, velocity increment minus T a, density
+ * deviation increment minus T (Drho/Dt) / rho0; all channels of fluid
+ * particles, the density channel of walls) and its gradient with
+ * the hand-written backward pass; with update != 0 applies one Adam step
+ * (beta1 0.9, beta2 0.999, eps 1e-8) of learning rate lr.  Writes the loss
+ * to *loss_out and, if grad_out is not NULL, the FP32 gradient (ngrad =
+ * number of parameters) as host doubles.  Waits for the stream. */
+int sph_surrogate_train_step(sph_handle h, const double *x1_dev, const double *u1_dev, const double *rho1_dev,
+                             double lr, int update, double *loss_out, double *grad_out, int64_t ngrad);
+
+/* n_macro macro-steps of k_steps plain steps each.  A macro-step is one
+ * surrogate evaluation, except every judge_every-th (0: never), where both
+ * the surrogate and k_steps plain steps (of size dt, graph-replayed) start
+ * from the same state: the plain result is kept, and the distance between
+ * the two oil centroids over d_ref is the judged error.  An error above tol
+ * rejects the surrogate: plain steps replace it until the next judged
+ * macro-step.  Reports the judged count, the rejected count and the largest
+ * judged error.  Waits for the stream. */
+int sph_surrogate_run(sph_handle h, double dt, int k_steps, int64_t n_macro, int judge_every, double tol,
+                      double d_ref, int64_t *n_judged, int64_t *n_rejected, double *max_err);
+
 #ifdef __cplusplus
 }
 #endif

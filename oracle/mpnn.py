@@ -26,6 +26,7 @@ from __future__ import annotations
 
 import numpy as np
 
+import oracle as SPH
 from paper_1702_07760_gb300 import surrogate_layout as SL
 
 
@@ -38,10 +39,12 @@ def dsilu(z):
     return s * (1.0 + z * (1.0 - s))
 
 
-def graph(p: dict, x: np.ndarray, phase: np.ndarray):
+def graph(p: dict, x: np.ndarray, phase: np.ndarray, u=None, rho=None, norm=None):
     """Edges (receiver i, sender j), j != i, |x_i - x_j| < 2h, sorted by
     (i, j), by brute force over all pairs; edge features
-    [r_ij / 2h, |r_ij| / 2h, phase_i != phase_j]."""
+    [r_ij / 2h, |r_ij| / 2h, phase_i != phase_j, (u_i - u_j) / sd_edge_u,
+    (delta_i - delta_j) / sd_edge_rho] with delta = (rho - rho0) / rho0.
+    Without u, rho and norm the state-difference channels are zero."""
     x = np.asarray(x, float)
     n = len(x)
     two_h = 2.0 * p["h"]
@@ -58,17 +61,35 @@ def graph(p: dict, x: np.ndarray, phase: np.ndarray):
     r = x[recv] - x[send]
     dist = np.sqrt(np.einsum("ij,ij->i", r, r))
     diff = (phase[recv] != phase[send]).astype(float)
-    E = np.concatenate([r / two_h, (dist / two_h)[:, None], diff[:, None]], axis=1)
+    dim = x.shape[1]
+    if u is None:
+        du = np.zeros((len(recv), dim))
+        dd = np.zeros(len(recv))
+    else:
+        _, _, _, _, _, _, su, sr = SL.split_norm(norm, dim)
+        delta = (rho - np.asarray(p["rho0"], float)[phase]) / np.asarray(p["rho0"], float)[phase]
+        du = (u[recv] - u[send]) / su
+        dd = (delta[recv] - delta[send]) / sr
+    E = np.concatenate([r / two_h, (dist / two_h)[:, None], diff[:, None], du, dd[:, None]], axis=1)
     return recv, send, E
 
 
-def node_features(p: dict, u, rho, phase, wall, norm: np.ndarray):
-    """Normalised node inputs [u, (rho - rho0)/rho0, oil, wall]."""
+def rates(p: dict, x, u, rho, phase, wall):
+    """The plain method's acceleration and density rate at the state (the
+    FP64 SPH oracle, with the density renormalisation of stage 1)."""
+    ref = SPH.evaluate(p, x, u, rho, phase, wall, renorm=True)
+    return ref["a"], ref["drho"]
+
+
+def node_features(p: dict, u, rho, phase, wall, norm: np.ndarray, a, drho_dt):
+    """Normalised node inputs [u, (rho - rho0)/rho0, oil, wall, T a,
+    T (Drho/Dt) / rho0]."""
     dim = int(p["dim"])
-    mu_in, sd_in, _, _, _ = SL.split_norm(norm, dim)
+    mu_in, sd_in, _, _, _, T, _, _ = SL.split_norm(norm, dim)
     rho0 = np.asarray(p["rho0"], float)[phase]
     raw = np.concatenate([np.asarray(u, float), ((rho - rho0) / rho0)[:, None],
-                          phase[:, None].astype(float), wall[:, None].astype(float)], axis=1)
+                          phase[:, None].astype(float), wall[:, None].astype(float),
+                          T * np.asarray(a, float), (T * np.asarray(drho_dt, float) / rho0)[:, None]], axis=1)
     return (raw - mu_in) / sd_in
 
 
@@ -175,17 +196,33 @@ def adam(theta, grad, m, v, step: int, lr: float, beta1=0.9, beta2=0.999, eps=1e
     return theta - lr * mhat / (np.sqrt(vhat) + eps), m, v
 
 
+def targets(p: dict, x0, u0, rho0_state, x1, u1, rho1, phase, norm, a, drho_dt):
+    """Normalised training targets between two states T apart: the position
+    increment's departure from the trapezoid rule T (u0 + u1) / 2, and the
+    velocity and density deviation increments' departures from the explicit
+    jump T a and T (Drho/Dt) / rho0."""
+    dim = int(p["dim"])
+    _, _, mu_out, sd_out, _, T, _, _ = SL.split_norm(norm, dim)
+    ref = np.asarray(p["rho0"], float)[phase]
+    D = np.concatenate([(x1 - x0) - T * 0.5 * (u0 + u1), u1 - u0 - T * np.asarray(a, float),
+                        ((rho1 - rho0_state) / ref - T * np.asarray(drho_dt, float) / ref)[:, None]], axis=1)
+    return (D - mu_out) / sd_out
+
+
 def predict(flat, p: dict, x, u, rho, phase, wall, norm):
     """De-normalised increments over k plain steps for the state (x, u, rho):
     (dx (N, d), du (N, d), drho (N,)); walls get zero dx and du."""
     dim = int(p["dim"])
-    recv, send, E = graph(p, x, phase)
-    X = node_features(p, u, rho, phase, wall, norm)
-    _, _, mu_out, sd_out, k_ref = SL.split_norm(norm, dim)
+    a, drho_dt = rates(p, x, u, rho, phase, wall)
+    recv, send, E = graph(p, x, phase, u, rho, norm)
+    X = node_features(p, u, rho, phase, wall, norm, a, drho_dt)
+    _, _, mu_out, sd_out, k_ref, T, _, _ = SL.split_norm(norm, dim)
     y, _ = forward(flat, dim, X, E, recv, send, k_ref)
     D = y * sd_out + mu_out
-    dx, du, drel = D[:, :dim].copy(), D[:, dim:2 * dim].copy(), D[:, 2 * dim]
+    ref = np.asarray(p["rho0"], float)[phase]
+    du = T * np.asarray(a, float) + D[:, dim:2 * dim]
+    dx = T * (np.asarray(u, float) + 0.5 * du) + D[:, :dim]
+    drel = T * np.asarray(drho_dt, float) / ref + D[:, 2 * dim]
     dx[wall.astype(bool)] = 0.0
     du[wall.astype(bool)] = 0.0
-    rho0 = np.asarray(p["rho0"], float)[phase]
-    return dx, du, drel * rho0
+    return dx, du, drel * ref

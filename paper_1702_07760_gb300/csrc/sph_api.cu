@@ -4,6 +4,7 @@
 // independent instances, reads in original particle order, FP64 diagnostics
 // and per-kernel event timing.
 #include "sph.h"
+#include "sph_internal.h"
 #include "sph_kernels.cuh"
 
 #include <cuda_runtime.h>
@@ -126,6 +127,9 @@ struct sph_sim {
     double pdt = 0.0;
     int64_t psteps = 0;
     int pshape = 0;
+    // extension owned by the learned surrogate
+    void *ext = nullptr;
+    void (*ext_free)(void *) = nullptr;
 
     Dev &D() { return buf[0]; }
 
@@ -328,6 +332,14 @@ namespace sphgb {
 // Records the message returned by sph_last_error() for this thread.
 int set_error(int code, const std::string &msg) { return fail(code, msg); }
 }  // namespace sphgb
+
+namespace {
+__global__ void k_load_state(Dev d, int dim, const double *x, const double *u, const double *rho);
+__global__ void k_add_step(long long *step, long long k)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) *step += k;
+}
+}  // namespace
 
 namespace {
 
@@ -732,6 +744,86 @@ int create_sim(const sph_params *params, int k, const int64_t *counts, const dou
 }
 
 }  // namespace
+
+namespace sphgb {
+
+SimView sim_view(sph_sim *s)
+{
+    SimView v{};
+    v.d = s->buf[0];
+    v.g = s->grid;
+    v.ph = s->phys;
+    v.stream = s->stream;
+    v.dim = s->dim;
+    v.n = s->n;
+    v.ninst = s->ninst;
+    v.h = s->P.h;
+    v.rho0 = s->P.rho0;
+    return v;
+}
+
+void sim_build_lists(sph_sim *s)
+{
+    if (s->n > 0) s->enqueue_build_cells(true);
+}
+
+int sim_check(sph_sim *s) { return s->check_flags(); }
+
+int sim_moved(sph_sim *s, int64_t steps)
+{
+    if (s->n > 0) {
+        k_add_step<<<1, 32, 0, s->stream>>>(s->dstep, (long long)steps);
+        CU(cudaGetLastError());
+        CU(cudaMemsetAsync(s->rebuild, 0xff, sizeof(unsigned), s->stream));
+    }
+    s->step += steps;
+    return SPH_OK;
+}
+
+int sim_snapshot_device(sph_sim *s, double *x, double *u, double *rho)
+{
+    if (s->n == 0) return SPH_OK;
+    const int nb = s->blocks(s->n);
+    if (s->dim == 2) {
+        k_unpermute<2><<<nb, 256, 0, s->stream>>>(s->D(), RK_X, x, s->read_ibuf);
+        k_unpermute<2><<<nb, 256, 0, s->stream>>>(s->D(), RK_U, u, s->read_ibuf);
+        k_unpermute<2><<<nb, 256, 0, s->stream>>>(s->D(), RK_RHO, rho, s->read_ibuf);
+    } else {
+        k_unpermute<3><<<nb, 256, 0, s->stream>>>(s->D(), RK_X, x, s->read_ibuf);
+        k_unpermute<3><<<nb, 256, 0, s->stream>>>(s->D(), RK_U, u, s->read_ibuf);
+        k_unpermute<3><<<nb, 256, 0, s->stream>>>(s->D(), RK_RHO, rho, s->read_ibuf);
+    }
+    CU(cudaGetLastError());
+    return SPH_OK;
+}
+
+int sim_load_device(sph_sim *s, const double *x, const double *u, const double *rho)
+{
+    if (s->n == 0) return SPH_OK;
+    k_load_state<<<s->blocks(s->n), 256, 0, s->stream>>>(s->D(), s->dim, x, u, rho);
+    CU(cudaGetLastError());
+    CU(cudaMemsetAsync(s->rebuild, 0xff, sizeof(unsigned), s->stream));
+    return SPH_OK;
+}
+
+int sim_centroid(sph_sim *s, double c[3])
+{
+    std::vector<double> all((size_t)12 * s->ninst);
+    const int rc = sph_diag_instances(s, all.data());
+    for (int k = 0; k < 3; ++k) c[k] = all[6 + k];
+    return rc;
+}
+
+void *sim_ext(sph_sim *s) { return s->ext; }
+
+void sim_set_ext(sph_sim *s, void *p, void (*free_fn)(void *))
+{
+    if (s->ext && s->ext_free) s->ext_free(s->ext);
+    s->ext = p;
+    s->ext_free = free_fn;
+}
+
+}  // namespace sphgb
 
 extern "C" {
 
@@ -1259,6 +1351,7 @@ void sph_destroy(sph_handle s)
 {
     if (!s) return;
     if (s->stream) cudaStreamSynchronize(s->stream);
+    if (s->ext && s->ext_free) s->ext_free(s->ext);
     s->collect_timing();
     for (auto e : s->free_events) cudaEventDestroy(e);
     if (s->gexec) cudaGraphExecDestroy(s->gexec);

@@ -154,6 +154,12 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 
 __device__ __forceinline__ float silu(float z) { return z / (1.f + __expf(-z)); }
 
+__device__ __forceinline__ float dsilu(float z)
+{
+    const float s = 1.f / (1.f + __expf(-z));
+    return s * (1.f + z * (1.f - s));
+}
+
 // Arguments of one contraction C = A B^T (+ epilogue).
 struct GemmArgs {
     const __nv_bfloat16 *A;
@@ -173,8 +179,11 @@ struct GemmArgs {
     int ldz;
     const float *residual;      // added after the activation (or NULL)
     int ldr;
-    int act;                    // 0 none, 1 SiLU
+    int act;                    // 0 none, 1 SiLU, 2 multiply by SiLU'(dact) (backward)
+    const float *dact;          // pre-activation for act == 2
+    int lddact;
     int atomic;                 // 1: atomicAdd the raw accumulator into Cf (split K)
+    int n_store;                // columns stored (0: N)
     unsigned *err;              // error word (ERR_TIMEOUT)
 };
 
@@ -300,18 +309,21 @@ __global__ void __launch_bounds__(THREADS, 1) k_gemm(GemmArgs g)
                     for (int j = 0; j < 16; ++j) v[j] = 0.f;
                 }
                 if (row >= g.M) continue;
+                const int nst = g.n_store > 0 ? g.n_store : BN;
                 if (g.atomic) {
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) atomicAdd(g.Cf + (size_t)row * g.ldcf + c0 + j, v[j]);
+                    for (int j = 0; j < 16; ++j)
+                        if (c0 + j < nst) atomicAdd(g.Cf + (size_t)row * g.ldcf + c0 + j, v[j]);
                     continue;
                 }
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
+                    if (c0 + j >= nst) continue;
                     float z = v[j];
                     if (g.bias) z += g.bias[c0 + j];
                     if (g.row_scale) z += g.row_scale[row] * g.row_bias[c0 + j];
                     if (g.Z) g.Z[(size_t)row * g.ldz + c0 + j] = z;
-                    float y = g.act == 1 ? silu(z) : z;
+                    float y = g.act == 1 ? silu(z) : g.act == 2 ? z * dsilu(g.dact[(size_t)row * g.lddact + c0 + j]) : z;
                     if (g.residual) y += g.residual[(size_t)row * g.ldr + c0 + j];
                     if (g.Cf) g.Cf[(size_t)row * g.ldcf + c0 + j] = y;
                     if (g.Cb) g.Cb[(size_t)row * g.ldcb + c0 + j] = __float2bfloat16_rn(y);

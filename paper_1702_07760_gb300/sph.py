@@ -27,7 +27,9 @@ EXPORTS = ["sph_create", "sph_set_state", "sph_build_cells", "sph_eval_rates", "
            "sph_step_index", "sph_num_cells", "sph_list_builds", "sph_destroy", "sph_last_error",
            "sph_cell_sort_noalloc", "sph_create_batch", "sph_set_dt_scales", "sph_run_persistent",
            "sph_set_launch_shape", "sph_get_launch_shape", "sph_autotune", "sph_diag_instances",
-           "sph_num_instances", "sph_test_stall_barrier", "sph_mm_bf16"]
+           "sph_num_instances", "sph_test_stall_barrier", "sph_mm_bf16", "sph_snapshot", "sph_load_snapshot",
+           "sph_surrogate_init", "sph_surrogate_get_weights", "sph_surrogate_predict", "sph_surrogate_advance",
+           "sph_surrogate_train_step", "sph_surrogate_run"]
 
 
 class SphError(RuntimeError):
@@ -91,6 +93,15 @@ def load(path: str = LIB_PATH):
     L.sph_test_stall_barrier.argtypes = [H]
     L.sph_mm_bf16.argtypes = [vp, C.c_int, vp, C.c_int, vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                               vp, vp]
+    L.sph_snapshot.argtypes = [H, vp, vp, vp]
+    L.sph_load_snapshot.argtypes = [H, vp, vp, vp]
+    L.sph_surrogate_init.argtypes = [H, dp, C.c_int64, dp, C.c_int64]
+    L.sph_surrogate_get_weights.argtypes = [H, dp, C.c_int64]
+    L.sph_surrogate_predict.argtypes = [H, dp, C.c_int64]
+    L.sph_surrogate_advance.argtypes = [H, C.c_int]
+    L.sph_surrogate_train_step.argtypes = [H, vp, vp, vp, C.c_double, C.c_int, dp, dp, C.c_int64]
+    L.sph_surrogate_run.argtypes = [H, C.c_double, C.c_int, C.c_int64, C.c_int, C.c_double, C.c_double,
+                                    P(C.c_int64), P(C.c_int64), dp]
     L.sph_num_instances.restype = C.c_int64
     _lib = L
     return L
@@ -246,6 +257,51 @@ class Simulation:
 
     def sync(self):
         _check(load().sph_sync(self._h))
+
+    # -- snapshots and the learned surrogate ------------------------------
+    def snapshot_to(self, x_ptr: int, u_ptr: int, rho_ptr: int):
+        """Queues a copy of the state (original order) into device arrays given by address."""
+        _check(load().sph_snapshot(self._h, C.c_void_p(x_ptr), C.c_void_p(u_ptr), C.c_void_p(rho_ptr)))
+
+    def load_snapshot(self, x_ptr: int, u_ptr: int, rho_ptr: int):
+        _check(load().sph_load_snapshot(self._h, C.c_void_p(x_ptr), C.c_void_p(u_ptr), C.c_void_p(rho_ptr)))
+
+    def surrogate_init(self, weights, norm):
+        w = np.ascontiguousarray(weights, np.float64)
+        nm = np.ascontiguousarray(norm, np.float64)
+        _check(load().sph_surrogate_init(self._h, _dp(w), len(w), _dp(nm), len(nm)))
+        self._nweights = len(w)
+
+    def surrogate_weights(self) -> np.ndarray:
+        w = np.zeros(self._nweights)
+        _check(load().sph_surrogate_get_weights(self._h, _dp(w), len(w)))
+        return w
+
+    def surrogate_predict(self) -> np.ndarray:
+        """(n, 2 dim + 1) increments dx, du, drho in original order."""
+        out = np.zeros((self.n, 2 * self.dim + 1))
+        _check(load().sph_surrogate_predict(self._h, _dp(out), out.nbytes))
+        return out
+
+    def surrogate_advance(self, k_steps: int):
+        _check(load().sph_surrogate_advance(self._h, int(k_steps)))
+
+    def surrogate_train_step(self, x1_ptr: int, u1_ptr: int, rho1_ptr: int, lr: float = 1e-3,
+                             update: bool = True, want_grad: bool = False):
+        """(loss, gradient or None) of one training step towards the state after k steps."""
+        loss = C.c_double()
+        g = np.zeros(self._nweights) if want_grad else None
+        _check(load().sph_surrogate_train_step(self._h, C.c_void_p(x1_ptr), C.c_void_p(u1_ptr),
+                                               C.c_void_p(rho1_ptr), float(lr), int(bool(update)), C.byref(loss),
+                                               _dp(g) if want_grad else None, self._nweights if want_grad else 0))
+        return loss.value, g
+
+    def surrogate_run(self, dt: float, k_steps: int, n_macro: int, judge_every: int, tol: float, d_ref: float):
+        """(judged, rejected, largest judged centroid error / d_ref)."""
+        a, b, e = C.c_int64(), C.c_int64(), C.c_double()
+        _check(load().sph_surrogate_run(self._h, float(dt), int(k_steps), int(n_macro), int(judge_every),
+                                        float(tol), float(d_ref), C.byref(a), C.byref(b), C.byref(e)))
+        return a.value, b.value, e.value
 
     # -- output -----------------------------------------------------------
     def read(self, field: str) -> np.ndarray:

@@ -8,12 +8,14 @@ format, so a weight file trained by one can be evaluated by the other.
 Network (message passing over the particle graph, width H = 128; the paper
 has no learned component, the architecture is this library's):
 
-* node input, d + 3 channels: velocity u (d), density deviation
-  (rho - rho0) / rho0, oil flag, wall flag; each normalised as
-  (raw - mu_in) / sd_in;
-* edge input for the pair (receiver i, sender j), |r_ij| < 2h, d + 2
-  channels: r_ij / 2h (d), |r_ij| / 2h, and 1 when i and j are of different
-  phase;
+* node input, 2d + 4 channels: velocity u (d), density deviation
+  (rho - rho0) / rho0, oil flag, wall flag, and the explicit increments of
+  the plain method's rates at the current state over the jump T = k dt:
+  T a (d) and T (Drho/Dt) / rho0; each normalised as (raw - mu_in) / sd_in;
+* edge input for the pair (receiver i, sender j), |r_ij| < 2h, 2d + 3
+  channels: r_ij / 2h (d), |r_ij| / 2h, 1 when i and j are of different
+  phase, (u_i - u_j) / sd_edge_u (d) and the difference of the density
+  deviations ((rho_i - rho0_i)/rho0_i - (rho_j - rho0_j)/rho0_j) / sd_edge_rho;
 * encoder ``enc1`` (d+3 -> H), SiLU, ``enc2`` (H -> H);
 * two rounds r of: edge MLP on [h_i, h_j, e_ij] whose first layer is stored
   split as ``w1`` (acting on h_i, with bias ``b1``), ``w2`` (on h_j) and
@@ -21,13 +23,16 @@ has no learned component, the architecture is this library's):
   over j and scaled by 1 / k_ref; node MLP ``n1`` (on [h, M], 2H -> H), SiLU,
   ``n2`` (H -> H), added to h;
 * decoder ``dec1`` (H -> H), SiLU, ``dec2`` (H -> 2d + 1): normalised
-  increments over k plain steps of position (d), velocity (d) and density
-  deviation (1), de-normalised as y * sd_out + mu_out.
+  outputs de-normalised as D = y * sd_out + mu_out, corrections to the
+  explicit jump: velocity increment du = T a + D[d:2d], density deviation
+  increment T (Drho/Dt) / rho0 + D[2d] (times rho0 for drho), position
+  increment dx = T (u + du / 2) + D[:d] (the trapezoid rule plus a
+  correction).
 
 Flat order: the tensors below in list order, each row-major (weights
 [out, in]).  The normalisation block is a separate array of
-4 d + 9 values: mu_in (d+3), sd_in (d+3), mu_out (2d+1), sd_out (2d+1),
-k_ref (1).
+6 d + 14 values: mu_in (2d+4), sd_in (2d+4), mu_out (2d+1), sd_out (2d+1),
+k_ref, T, sd_edge_u, sd_edge_rho.
 """
 from __future__ import annotations
 
@@ -38,11 +43,11 @@ ROUNDS = 2
 
 
 def n_in(dim: int) -> int:
-    return dim + 3
+    return 2 * dim + 4
 
 
 def n_edge(dim: int) -> int:
-    return dim + 2
+    return 2 * dim + 3
 
 
 def n_out(dim: int) -> int:
@@ -110,18 +115,22 @@ def init_weights(dim: int, seed: int = 0, width: int = H, out_scale: float = 0.1
 
 
 def norm_size(dim: int) -> int:
-    return 2 * n_in(dim) + 2 * n_out(dim) + 1
+    return 2 * n_in(dim) + 2 * n_out(dim) + 4
 
 
-def make_norm(dim: int, mu_in, sd_in, mu_out, sd_out, k_ref: float) -> np.ndarray:
+def make_norm(dim: int, mu_in, sd_in, mu_out, sd_out, k_ref: float, t_jump: float, sd_edge_u: float,
+              sd_edge_rho: float) -> np.ndarray:
     """Pack the normalisation block."""
     v = np.concatenate([np.asarray(mu_in, float), np.asarray(sd_in, float), np.asarray(mu_out, float),
-                        np.asarray(sd_out, float), [float(k_ref)]])
+                        np.asarray(sd_out, float), [float(k_ref), float(t_jump), float(sd_edge_u),
+                                                    float(sd_edge_rho)]])
     assert len(v) == norm_size(dim)
     return v
 
 
 def split_norm(norm: np.ndarray, dim: int):
+    """(mu_in, sd_in, mu_out, sd_out, k_ref, t_jump, sd_edge_u, sd_edge_rho)."""
     a, b = n_in(dim), n_out(dim)
-    return (norm[:a], norm[a:2 * a], norm[2 * a:2 * a + b], norm[2 * a + b:2 * a + 2 * b],
-            float(norm[2 * a + 2 * b]))
+    o = 2 * a + 2 * b
+    return (norm[:a], norm[a:2 * a], norm[2 * a:2 * a + b], norm[2 * a + b:o], float(norm[o]),
+            float(norm[o + 1]), float(norm[o + 2]), float(norm[o + 3]))

@@ -29,7 +29,8 @@ def _case(dim=2, seed=3):
     rng = np.random.Generator(np.random.PCG64(seed))
     n_in, n_out = SL.n_in(dim), SL.n_out(dim)
     norm = SL.make_norm(dim, rng.normal(0, 0.1, n_in), rng.uniform(0.5, 2, n_in),
-                        rng.normal(0, 0.1, n_out), rng.uniform(0.5, 2, n_out), k_ref=10.0)
+                        rng.normal(0, 0.1, n_out), rng.uniform(0.5, 2, n_out), k_ref=10.0, t_jump=8e-5,
+                        sd_edge_u=0.02 * w.params["c0"], sd_edge_rho=1e-3)
     return w, norm
 
 
@@ -53,8 +54,8 @@ def _textbook(flat, dim, X, E, recv, send, k_ref, width=SL.H):
 def test_forward_equals_textbook_edge_mlp(dim):
     w, norm = _case(dim)
     flat = SL.init_weights(dim, seed=5, out_scale=1.0)
-    recv, send, E = O.graph(w.params, w.x, w.phase)
-    X = O.node_features(w.params, w.u, w.rho, w.phase, w.wall, norm)
+    recv, send, E = O.graph(w.params, w.x, w.phase, w.u, w.rho, norm)
+    X = O.node_features(w.params, w.u, w.rho, w.phase, w.wall, norm, *O.rates(w.params, w.x, w.u, w.rho, w.phase, w.wall))
     y, _ = O.forward(flat, dim, X, E, recv, send, 10.0)
     yt = _textbook(flat, dim, X, E, recv, send, 10.0).numpy()
     assert len(recv) > 10 * len(X)
@@ -65,8 +66,8 @@ def test_forward_equals_textbook_edge_mlp(dim):
 def test_backward_equals_autograd_of_textbook_form(dim):
     w, norm = _case(dim, seed=4)
     flat = SL.init_weights(dim, seed=6, out_scale=1.0)
-    recv, send, E = O.graph(w.params, w.x, w.phase)
-    X = O.node_features(w.params, w.u, w.rho, w.phase, w.wall, norm)
+    recv, send, E = O.graph(w.params, w.x, w.phase, w.u, w.rho, norm)
+    X = O.node_features(w.params, w.u, w.rho, w.phase, w.wall, norm, *O.rates(w.params, w.x, w.u, w.rho, w.phase, w.wall))
     rng = np.random.Generator(np.random.PCG64(9))
     t = rng.normal(size=(len(X), SL.n_out(dim)))
     mask = O.output_mask(dim, w.wall)
@@ -108,8 +109,8 @@ def test_backward_matches_central_differences():
     dim, width = 2, 6
     w, norm = _case(2, seed=7)
     flat = SL.init_weights(dim, seed=8, width=width, out_scale=1.0)
-    recv, send, E = O.graph(w.params, w.x, w.phase)
-    X = O.node_features(w.params, w.u, w.rho, w.phase, w.wall, norm)
+    recv, send, E = O.graph(w.params, w.x, w.phase, w.u, w.rho, norm)
+    X = O.node_features(w.params, w.u, w.rho, w.phase, w.wall, norm, *O.rates(w.params, w.x, w.u, w.rho, w.phase, w.wall))
     rng = np.random.Generator(np.random.PCG64(10))
     t = rng.normal(size=(len(X), SL.n_out(dim)))
     mask = O.output_mask(dim, w.wall)
@@ -120,12 +121,17 @@ def test_backward_matches_central_differences():
     y, cache = O.forward(flat, dim, X, E, recv, send, 10.0, width)
     _, dy = O.loss(y, t, mask)
     g = O.backward(flat, dim, cache, dy)
-    eps = 1e-6
+    # central differences with Richardson extrapolation (truncation error O(eps^4))
+    eps = 1e-5
     idx = rng.choice(len(flat), size=120, replace=False)
     for k in idx:
         e = np.zeros_like(flat)
-        e[k] = eps
-        fd = (f(flat + e) - f(flat - e)) / (2 * eps)
+        e[k] = 1.0
+
+        def cd(h):
+            return (f(flat + h * e) - f(flat - h * e)) / (2 * h)
+
+        fd = (4.0 * cd(eps / 2) - cd(eps)) / 3.0
         assert abs(fd - g[k]) <= 1e-6 * max(abs(fd), 1e-3 * np.abs(g).max()), (k, fd, g[k])
 
 
@@ -135,7 +141,9 @@ def test_translation_invariance_and_permutation_equivariance():
     flat = SL.init_weights(dim, seed=12, out_scale=1.0)
     dx, du, dr = O.predict(flat, w.params, w.x, w.u, w.rho, w.phase, w.wall, norm)
     shift = np.array([3.7e-3, -1.1e-3])
-    dx2, du2, dr2 = O.predict(flat, w.params, w.x + shift, w.u, w.rho, w.phase, w.wall, norm)
+    p2 = dict(w.params, box_lo=[w.params["box_lo"][0] + shift[0], w.params["box_lo"][1] + shift[1], 0.0],
+              box_hi=[w.params["box_hi"][0] + shift[0], w.params["box_hi"][1] + shift[1], 0.0])
+    dx2, du2, dr2 = O.predict(flat, p2, w.x + shift, w.u, w.rho, w.phase, w.wall, norm)
     assert np.allclose(dx, dx2, rtol=0, atol=1e-9 * np.abs(dx).max())
     assert np.allclose(dr, dr2, rtol=0, atol=1e-9 * np.abs(dr).max())
     perm = np.random.Generator(np.random.PCG64(13)).permutation(w.n)
@@ -151,21 +159,27 @@ def test_zero_weights_give_the_output_bias():
     flat = np.zeros(SL.size(dim))
     b = np.arange(1, SL.n_out(dim) + 1, dtype=float)
     flat[SL.offsets(dim)["dec2.b"]:SL.offsets(dim)["dec2.b"] + len(b)] = b
-    recv, send, E = O.graph(w.params, w.x, w.phase)
-    X = O.node_features(w.params, w.u, w.rho, w.phase, w.wall, norm)
+    recv, send, E = O.graph(w.params, w.x, w.phase, w.u, w.rho, norm)
+    X = O.node_features(w.params, w.u, w.rho, w.phase, w.wall, norm, *O.rates(w.params, w.x, w.u, w.rho, w.phase, w.wall))
     y, _ = O.forward(flat, dim, X, E, recv, send, 10.0)
     assert np.all(y == b)
 
 
 @pytest.mark.parametrize("dim", [2, 3])
 def test_graph_equals_cell_list_neighbours(dim):
-    w, _ = _case(dim, seed=15)
-    recv, send, E = O.graph(w.params, w.x, w.phase)
+    w, norm = _case(dim, seed=15)
+    recv, send, E = O.graph(w.params, w.x, w.phase, w.u, w.rho, norm)
     start, lst = oracle.neighbours(w.params, w.x, "cells")
     r2 = np.repeat(np.arange(w.n), np.diff(start))
     assert np.array_equal(recv, r2) and np.array_equal(send, lst)
     assert np.all(E[:, dim] < 1.0) and np.all(E[:, dim] > 0.0)
     assert np.allclose(np.linalg.norm(E[:, :dim], axis=1), E[:, dim], rtol=1e-14)
+    # the state-difference channels are antisymmetric in (i, j)
+    key = {(a, b): k for k, (a, b) in enumerate(zip(recv, send))}
+    rev = np.array([key[(b, a)] for a, b in zip(recv, send)])
+    flip = np.r_[np.arange(dim), np.arange(dim + 2, 2 * dim + 3)]
+    keep = np.array([dim, dim + 1])
+    assert np.array_equal(E[rev][:, flip], -E[:, flip]) and np.array_equal(E[rev][:, keep], E[:, keep])
 
 
 def test_adam_matches_torch():
