@@ -44,7 +44,7 @@ SWEEP_A_FLOPS_OTHER = {2: 14, 3: 21}
 # DRAM bytes (read + write) per launch of the force sweep on the 3-D workload,
 # from the ncu capture summarised in profiles/sweeps_drop_3d_64x64x128.md; valid
 # only for the kernel source it was taken on (first 16 hex digits of its sha256).
-PROFILED_TRAFFIC = {"sweep_b": {"source_sha256": "a310baa690210eff", "bytes": 331.0e6, "workload": "drop_3d"}}
+PROFILED_TRAFFIC = {"sweep_b": {"source_sha256": "911cb5d2142081aa", "bytes": 332.9e6, "workload": "drop_3d"}}
 
 
 def parse():
@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=500,
                     help="steps of the 256-instance batched comparison (0 skips it)")
+    ap.add_argument("--surrogate-iters", type=int, default=600,
+                    help="training iterations of the learned k-step surrogate (0 skips it)")
     return ap.parse_args()
 
 
@@ -266,6 +268,103 @@ def run_batched(sph, WL, stream, steps, torch):
     }
 
 
+def run_surrogate(sph, WL, stream, iters, torch, macro=25, k=8):
+    """The learned k-step surrogate: trained on plain trajectories of narrower
+    tanks of the same depth (so the same c0, dt and jump T = k dt), then
+    advancing the 656 600-particle drop for `macro` jumps of k steps against
+    the plain method over the same physical time: time per k steps and the
+    drop-centroid error ||c_surrogate - c_plain|| / D."""
+    from paper_1702_07760_gb300 import surrogate as SUR
+    from paper_1702_07760_gb300 import surrogate_layout as SL
+
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        a, b = ev(), ev()
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b)
+
+    train_tanks = [WL.drop_tank(3, (32, 32, 128), drop_d_dx=d, seed=4000 + d, name=f"drop_3d_32x32x128_d{d}")
+                   for d in (12, 20)]
+    w_eval = WL.drop_3d()
+    dt = WL.stable_dt(w_eval.params)
+    assert all(abs(WL.stable_dt(t.params) - dt) < 1e-15 for t in train_tanks)
+    T = k * dt
+    t0 = time.perf_counter()
+    sets = []
+    for tw in train_tanks:
+        s = sph.Simulation.from_workload(tw, stream=stream.cuda_stream)
+        sets.append((s, SUR.record(s, dt, k, 40, torch)))
+    rec_s = time.perf_counter() - t0
+    norm = SUR.fit_norm(train_tanks[0].params, train_tanks[0].phase, train_tanks[0].wall, [sets[0][1]],
+                        k_ref=80.0, t_jump=T)
+    # one handle trains on both trajectories in turn (the weights move between handles)
+    flat = SL.init_weights(3, seed=7)
+    hist = []
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    per = max(iters // 4, 1)
+    for rnd in range(4):
+        s, snaps = sets[rnd % 2]
+        s.surrogate_init(flat, norm)
+        hist += list(SUR.train(s, [snaps], iters=per, lr=1e-3 * (0.5 ** rnd), lr_final=2e-4 * (0.5 ** rnd),
+                               seed=rnd))
+        flat = s.surrogate_weights()
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t1
+    train_nodes = sum(s.n for s, _ in sets) / 2
+    for s, _ in sets:
+        s.close()
+    # evaluation on the full workload
+    plain = sph.Simulation.from_workload(w_eval, stream=stream.cuda_stream)
+    plain.run(dt, k, graph=True)          # graph capture, untimed
+    plain.close()
+    plain = sph.Simulation.from_workload(w_eval, stream=stream.cuda_stream)
+    ms_plain = timed(lambda: plain.run(dt, macro * k, graph=True))
+    c_plain = plain.diagnostics()["centroid"]
+    u_plain = plain.read("vel")
+    plain.close()
+    sur = sph.Simulation.from_workload(w_eval, stream=stream.cuda_stream)
+    sur.surrogate_init(flat, norm)
+    sur.surrogate_advance(k)               # warm-up (allocations), then restart
+    sur.close()
+    sur = sph.Simulation.from_workload(w_eval, stream=stream.cuda_stream)
+    sur.surrogate_init(flat, norm)
+    ms_sur = timed(lambda: [sur.surrogate_advance(k) for _ in range(macro)])
+    sur.sync()
+    c_sur = sur.diagnostics()["centroid"]
+    u_sur = sur.read("vel")
+    sur.close()
+    D = 2 * w_eval.meta["drop_radius"]
+    fl = w_eval.wall == 0
+    judged = sph.Simulation.from_workload(w_eval, stream=stream.cuda_stream)
+    judged.surrogate_init(flat, norm)
+    t2 = time.perf_counter()
+    nj, nr, worst = judged.surrogate_run(dt, k, macro, 5, 0.02, D)
+    ms_judged = (time.perf_counter() - t2) * 1e3
+    c_j = judged.diagnostics()["centroid"]
+    judged.close()
+    return {
+        "train": {"workloads": [t.name for t in train_tanks], "particles": int(train_nodes), "iterations": iters,
+                  "snapshots": "2 x 40, every k = 8 steps", "record_s": rec_s, "train_s": train_s,
+                  "ms_per_iteration": train_s / max(iters, 1) * 1e3,
+                  "loss_first_50": float(np.mean(hist[:50])), "loss_last_50": float(np.mean(hist[-50:]))},
+        "eval_workload": "drop_3d_64x64x128 (656 600 particles, D = 16 dx)", "k": k, "macro_steps": macro,
+        "plain_ms_per_k_steps": ms_plain / macro, "surrogate_ms_per_jump": ms_sur / macro,
+        "speedup_vs_plain": ms_plain / ms_sur,
+        "centroid_err_over_D": float(np.linalg.norm(c_sur - c_plain) / D),
+        "velocity_rms_err_rel": float(np.sqrt(((u_sur[fl] - u_plain[fl]) ** 2).mean() / (u_plain[fl] ** 2).mean())),
+        "judged": {"judge_every": 5, "tol": 0.02, "judged": nj, "rejected": nr, "max_err": worst,
+                   "ms_per_k_steps_host_clock": ms_judged / macro,
+                   "centroid_err_over_D": float(np.linalg.norm(c_j - c_plain) / D)},
+    }
+
+
 def run_ours(args, ws, rank, local):
     import torch
     from paper_1702_07760_gb300 import build as B
@@ -379,6 +478,9 @@ def run_ours(args, ws, rank, local):
     batched = None
     if rank == 0 and ws == 1 and args.batch_steps > 0:
         batched = run_batched(sph, WL, stream, args.batch_steps, torch)
+    surrogate = None
+    if rank == 0 and ws == 1 and args.surrogate_iters > 0:
+        surrogate = run_surrogate(sph, WL, stream, args.surrogate_iters, torch)
 
     # count reset, hash, 3 scan, scatter, rank, gather, copy-back, list (these return at once on
     # steps without a rebuild), 2 sweep_a, 2 sweep_b (with the predictor / corrector)
@@ -398,6 +500,7 @@ def run_ours(args, ws, rank, local):
         "cpu_baseline": cpu,
         "e2e": e2e,
         "batched": batched,
+        "surrogate": surrogate,
         "gpu_launches": kernels_per_step * args.steps,
         "clocks": clk,
     }

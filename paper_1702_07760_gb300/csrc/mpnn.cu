@@ -237,24 +237,71 @@ __device__ __forceinline__ void store4(bf16 *p, const float (&v)[4])
     *(uint2 *)p = raw;
 }
 
+constexpr int GRP = 2;   // valid edges whose row gathers are in flight together
+
+// Lane-parallel decoding of up to 32 list entries of receiver i (entry
+// k0 + lane on each lane): the edge features and the sender of every valid
+// entry go to the warp's shared-memory slots; returns the ballot of valid
+// entries.
+template <int DIM>
+__device__ __forceinline__ unsigned stage_entries(const Dev &d, const Grid &g, float R2, float inv2h,
+                                                  const float4 &oi, int phi, const float4 &nfi, const float4 *NF,
+                                                  int i, int k0, int cnt, float (*slot)[2 * DIM + 4])
+{
+    constexpr int NE = 2 * DIM + 3;
+    const int lane = threadIdx.x & 31;
+    const int k = k0 + lane;
+    bool valid = false;
+    if (k < cnt) {
+        int j;
+        float ef[NE];
+        valid = edge_features<DIM>(d, g, R2, inv2h, oi, phi, nfi, NF, d.nbr[(size_t)k * d.n + i], j, ef);
+        if (valid) {
+#pragma unroll
+            for (int c = 0; c < NE; ++c) slot[lane][c] = ef[c];
+            slot[lane][NE] = __int_as_float(j);
+        }
+    }
+    const unsigned mask = __ballot_sync(0xffffffffu, valid);
+    __syncwarp();
+    return mask;
+}
+
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+
 // Forward edge phase: one warp per receiver i, four features per lane.
 // S_i = (1/k_ref) sum_j SiLU(P_i + Q_j + W3 e_ij) over list entries with
-// |r_ij| < 2h; degs_i = deg_i / k_ref.
+// |r_ij| < 2h; degs_i = deg_i / k_ref.  Entries are decoded 32 at a time,
+// one per lane; the sender rows Q_j of every valid entry of the batch are
+// then copied to shared memory with cp.async (all in flight together) and
+// the arithmetic reads them from there.
+constexpr int EWF = 128;   // threads of the forward edge kernel (4 warps, one node each)
+
 template <int DIM>
-__global__ void __launch_bounds__(EW) k_edge_fwd(Dev d, Grid g, float R2, float inv2h, const float4 *NF,
-                                                 const bf16 *PQ, const float *W3, float inv_kref, bf16 *S,
-                                                 float *degs)
+__global__ void __launch_bounds__(EWF, 6) k_edge_fwd(Dev d, Grid g, float R2, float inv2h, const float4 *NF,
+                                                   const bf16 *PQ, const float *W3, float inv_kref, bf16 *S,
+                                                   float *degs)
 {
+    constexpr int NE = 2 * DIM + 3;
+    __shared__ float slots[EWF / 32][32][NE + 1];
+    __shared__ __align__(16) uint2 qrows[EWF / 32][32][32];   // [warp][entry][lane]: 4 BF16 features
+    __shared__ float4 sw[NE][32];   // W3 column c for the four features of lane l
+    for (int t = threadIdx.x; t < NE * 32; t += EWF) {
+        const int c = t / 32, l = t % 32;
+        sw[c][l] = make_float4(W3[(4 * l) * NE + c], W3[(4 * l + 1) * NE + c], W3[(4 * l + 2) * NE + c],
+                               W3[(4 * l + 3) * NE + c]);
+    }
+    __syncthreads();
+    const int wid = threadIdx.x >> 5;
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (i >= d.n) return;
-    constexpr int NE = 2 * DIM + 3;
     const int f0 = lane * 4;
-    float w[4][NE];
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-#pragma unroll
-        for (int c = 0; c < NE; ++c) w[q][c] = W3[(f0 + q) * NE + c];
     float P[4];
     load4(PQ + (size_t)i * 2 * H + f0, P);
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
@@ -263,21 +310,36 @@ __global__ void __launch_bounds__(EW) k_edge_fwd(Dev d, Grid g, float R2, float 
     const float4 nfi = NF[i];
     const int phi = phase_of(oi.w);
     const int cnt = d.ncnt[i];
-    for (int k = 0; k < cnt; ++k) {
-        const unsigned e = d.nbr[(size_t)k * d.n + i];
-        int j;
-        float ef[NE];
-        if (!edge_features<DIM>(d, g, R2, inv2h, oi, phi, nfi, NF, e, j, ef)) continue;
-        ++deg;
-        float Q[4];
-        load4(PQ + (size_t)j * 2 * H + H + f0, Q);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            float z = P[q] + Q[q];
-#pragma unroll
-            for (int c = 0; c < NE; ++c) z = fmaf(w[q][c], ef[c], z);
-            acc[q] += silu(z);
+    float(*slot)[NE + 1] = slots[wid];
+    uint2(*qr)[32] = qrows[wid];
+    for (int k0 = 0; k0 < cnt; k0 += 32) {
+        const unsigned valid = stage_entries<DIM>(d, g, R2, inv2h, oi, phi, nfi, NF, i, k0, cnt, slot);
+        deg += __popc(valid);
+        for (unsigned m = valid; m; m &= m - 1) {
+            const int sl = __ffs(m) - 1;
+            cp_async8(&qr[sl][lane], PQ + (size_t)__float_as_int(slot[sl][NE]) * 2 * H + H + f0);
         }
+        asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+        __syncwarp();
+        for (unsigned m = valid; m; m &= m - 1) {
+            const int sl = __ffs(m) - 1;
+            const uint2 raw = qr[sl][lane];
+            const __nv_bfloat162 qa = *(const __nv_bfloat162 *)&raw.x, qb = *(const __nv_bfloat162 *)&raw.y;
+            float z[4] = {P[0] + __low2float(qa), P[1] + __high2float(qa), P[2] + __low2float(qb),
+                          P[3] + __high2float(qb)};
+#pragma unroll
+            for (int c = 0; c < NE; ++c) {
+                const float ec = slot[sl][c];
+                const float4 wc = sw[c][lane];
+                z[0] = fmaf(wc.x, ec, z[0]);
+                z[1] = fmaf(wc.y, ec, z[1]);
+                z[2] = fmaf(wc.z, ec, z[2]);
+                z[3] = fmaf(wc.w, ec, z[3]);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[q] += silu(z[q]);
+        }
+        __syncwarp();
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) acc[q] *= inv_kref;
@@ -290,12 +352,20 @@ __global__ void __launch_bounds__(EW) k_edge_fwd(Dev d, Grid g, float R2, float 
 // symmetric, so node i gathers its own sender terms), dW3 += dZ_ij e_ij and
 // db1 += dP_i, reduced per block and added with atomics.
 template <int DIM>
-__global__ void __launch_bounds__(EW) k_edge_bwd(Dev d, Grid g, float R2, float inv2h, const float4 *NF,
+__global__ void __launch_bounds__(EW, 2) k_edge_bwd(Dev d, Grid g, float R2, float inv2h, const float4 *NF,
                                                  const bf16 *PQ, const float *W3, float inv_kref, const float *dS,
                                                  bf16 *dPQ, float *gW3, float *gb1)
 {
     constexpr int NE = 2 * DIM + 3;
+    __shared__ float slots[EW / 32][32][NE + 1];
     __shared__ float red[EW / 32][H * (NE + 1)];
+    __shared__ float4 sw[NE][32];
+    for (int t = threadIdx.x; t < NE * 32; t += EW) {
+        const int c = t / 32, l = t % 32;
+        sw[c][l] = make_float4(W3[(4 * l) * NE + c], W3[(4 * l + 1) * NE + c], W3[(4 * l + 2) * NE + c],
+                               W3[(4 * l + 3) * NE + c]);
+    }
+    __syncthreads();
     const int wid = threadIdx.x >> 5;
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -307,46 +377,67 @@ __global__ void __launch_bounds__(EW) k_edge_bwd(Dev d, Grid g, float R2, float 
 #pragma unroll
         for (int c = 0; c < NE; ++c) gw[q][c] = 0.f;
     if (i < d.n) {
-        float w[4][NE];
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-#pragma unroll
-            for (int c = 0; c < NE; ++c) w[q][c] = W3[(f0 + q) * NE + c];
         float Pi[4], Qi[4], dSi[4];
         load4(PQ + (size_t)i * 2 * H + f0, Pi);
         load4(PQ + (size_t)i * 2 * H + H + f0, Qi);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) dSi[q] = dS[(size_t)i * H + f0 + q] * inv_kref;
+        const float4 ds4 = *(const float4 *)(dS + (size_t)i * H + f0);
+        dSi[0] = ds4.x * inv_kref;
+        dSi[1] = ds4.y * inv_kref;
+        dSi[2] = ds4.z * inv_kref;
+        dSi[3] = ds4.w * inv_kref;
         const float4 oi = d.pos[i];
         const float4 nfi = NF[i];
         const int phi = phase_of(oi.w);
         const int cnt = d.ncnt[i];
-        for (int k = 0; k < cnt; ++k) {
-            const unsigned e = d.nbr[(size_t)k * d.n + i];
-            int j;
-            float ef[NE];
-            if (!edge_features<DIM>(d, g, R2, inv2h, oi, phi, nfi, NF, e, j, ef)) continue;
-            float Pj[4], Qj[4];
-            load4(PQ + (size_t)j * 2 * H + f0, Pj);
-            load4(PQ + (size_t)j * 2 * H + H + f0, Qj);
+        float(*slot)[NE + 1] = slots[wid];
+        for (int k0 = 0; k0 < cnt; k0 += 32) {
+            unsigned mask = stage_entries<DIM>(d, g, R2, inv2h, oi, phi, nfi, NF, i, k0, cnt, slot);
+            while (mask) {
+                constexpr int GB = 2;
+                int sl[GB];
+                float Pj[GB][4], Qj[GB][4];
+                float4 dSj[GB];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                float zij = Pi[q] + Qj[q], zji = Pj[q] + Qi[q];
-#pragma unroll
-                for (int c = 0; c < NE; ++c) {
-                    // e_ji: the relative position and the state differences change
-                    // sign, the distance and the phase flag do not
-                    const float ec = ef[c];
-                    zij = fmaf(w[q][c], ec, zij);
-                    zji = fmaf(w[q][c], (c < DIM || c >= DIM + 2) ? -ec : ec, zji);
+                for (int t = 0; t < GB; ++t) {
+                    sl[t] = mask ? __ffs(mask) - 1 : -1;
+                    if (mask) mask &= mask - 1;
+                    if (sl[t] >= 0) {
+                        const size_t j = (size_t)__float_as_int(slot[sl[t]][NE]);
+                        load4(PQ + j * 2 * H + f0, Pj[t]);
+                        load4(PQ + j * 2 * H + H + f0, Qj[t]);
+                        dSj[t] = *(const float4 *)(dS + j * H + f0);
+                    }
                 }
-                const float dzij = dSi[q] * dsilu(zij);
-                const float dzji = dS[(size_t)j * H + f0 + q] * inv_kref * dsilu(zji);
-                dP[q] += dzij;
-                dQ[q] += dzji;
 #pragma unroll
-                for (int c = 0; c < NE; ++c) gw[q][c] = fmaf(dzij, ef[c], gw[q][c]);
+                for (int t = 0; t < GB; ++t) {
+                    if (sl[t] < 0) break;
+                    float ef[NE];
+#pragma unroll
+                    for (int c = 0; c < NE; ++c) ef[c] = slot[sl[t]][c];
+                    const float dsj[4] = {dSj[t].x, dSj[t].y, dSj[t].z, dSj[t].w};
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        float zij = Pi[q] + Qj[t][q], zji = Pj[t][q] + Qi[q];
+#pragma unroll
+                        for (int c = 0; c < NE; ++c) {
+                            // e_ji: the relative position and the state differences change
+                            // sign, the distance and the phase flag do not
+                            const float ec = ef[c];
+                            const float4 wc4 = sw[c][lane];
+                            const float wq = q == 0 ? wc4.x : q == 1 ? wc4.y : q == 2 ? wc4.z : wc4.w;
+                            zij = fmaf(wq, ec, zij);
+                            zji = fmaf(wq, (c < DIM || c >= DIM + 2) ? -ec : ec, zji);
+                        }
+                        const float dzij = dSi[q] * dsilu(zij);
+                        const float dzji = dsj[q] * inv_kref * dsilu(zji);
+                        dP[q] += dzij;
+                        dQ[q] += dzji;
+#pragma unroll
+                        for (int c = 0; c < NE; ++c) gw[q][c] = fmaf(dzij, ef[c], gw[q][c]);
+                    }
+                }
             }
+            __syncwarp();
         }
         store4(dPQ + (size_t)i * 2 * H + f0, dP);
         store4(dPQ + (size_t)i * 2 * H + H + f0, dQ);
@@ -710,8 +801,10 @@ int alloc_backward(Surrogate &S)
     return SPH_OK;
 }
 
-// Forward pass at the simulation's current state (lists built by the caller).
-int forward(Surrogate &S, const SimView &v)
+// Forward pass at the simulation's current state (rates evaluated by the
+// caller); the pre-activations the backward pass needs are stored only when
+// training.
+int forward(Surrogate &S, const SimView &v, bool training)
 {
     const Layout &L = S.L;
     const float *T = S.theta;
@@ -726,7 +819,7 @@ int forward(Surrogate &S, const SimView &v)
         Epi e;
         e.bias = T + L.enc1b;
         e.act = 1;
-        e.Z = S.Z0;
+        e.Z = training ? S.Z0 : nullptr;
         e.ldz = H;
         e.Cb = S.A0;
         e.ldcb = H;
@@ -751,11 +844,11 @@ int forward(Surrogate &S, const SimView &v)
             if ((rc = mm(S, st, S.A1[r], 2 * H, S.Wpq[r], H, n, 2 * H, H, e))) return rc;
         }
         if (v.dim == 2)
-            k_edge_fwd<2><<<nb(n * 32, EW), EW, 0, st>>>(v.d, v.g, R2, inv2h, S.NF, S.PQ[r], T + L.w3[r], invk,
-                                                         S.S[r], S.degs);
+            k_edge_fwd<2><<<nb(n * 32, EWF), EWF, 0, st>>>(v.d, v.g, R2, inv2h, S.NF, S.PQ[r], T + L.w3[r], invk,
+                                                           S.S[r], S.degs);
         else
-            k_edge_fwd<3><<<nb(n * 32, EW), EW, 0, st>>>(v.d, v.g, R2, inv2h, S.NF, S.PQ[r], T + L.w3[r], invk,
-                                                         S.S[r], S.degs);
+            k_edge_fwd<3><<<nb(n * 32, EWF), EWF, 0, st>>>(v.d, v.g, R2, inv2h, S.NF, S.PQ[r], T + L.w3[r], invk,
+                                                           S.S[r], S.degs);
         CUR(cudaGetLastError());
         {
             Epi e;
@@ -769,7 +862,7 @@ int forward(Surrogate &S, const SimView &v)
             Epi e;
             e.bias = T + L.n1b[r];
             e.act = 1;
-            e.Z = S.Z1[r];
+            e.Z = training ? S.Z1[r] : nullptr;
             e.ldz = H;
             e.Cb = S.G1[r];
             e.ldcb = H;
@@ -791,7 +884,7 @@ int forward(Surrogate &S, const SimView &v)
         Epi e;
         e.bias = T + L.dec1b;
         e.act = 1;
-        e.Z = S.Z2;
+        e.Z = training ? S.Z2 : nullptr;
         e.ldz = H;
         e.Cb = S.A2;
         e.ldcb = H;
@@ -1066,7 +1159,7 @@ int sph_surrogate_predict(sph_handle h, double *out, int64_t bytes)
     int rc0 = sph_eval_rates(h);
     if (rc0) return rc0;
     const SimView v = sim_view(h);
-    int rc = forward(*S, v);
+    int rc = forward(*S, v, false);
     if (rc) return rc;
     double *dout = nullptr;
     CUR(cudaMallocAsync((void **)&dout, need, v.stream));
@@ -1089,7 +1182,7 @@ int sph_surrogate_advance(sph_handle h, int k_steps)
     int rc0 = sph_eval_rates(h);
     if (rc0) return rc0;
     const SimView v = sim_view(h);
-    int rc = forward(*S, v);
+    int rc = forward(*S, v, false);
     if (rc) return rc;
     if (v.dim == 2) k_apply<2><<<nb(v.n), 256, 0, v.stream>>>(v.d, S->norm_d, S->t_jump, S->Y);
     else k_apply<3><<<nb(v.n), 256, 0, v.stream>>>(v.d, S->norm_d, S->t_jump, S->Y);
@@ -1112,7 +1205,7 @@ int sph_surrogate_train_step(sph_handle h, const double *x1, const double *u1, c
     int rc0 = sph_eval_rates(h);
     if (rc0) return rc0;
     const SimView v = sim_view(h);
-    if ((rc = forward(*S, v))) return rc;
+    if ((rc = forward(*S, v, true))) return rc;
     // count of (node, channel) terms: every channel of fluid nodes, the density channel of walls
     // (computed on the device side by the loss kernel's mask; the host needs the wall count)
     std::vector<uint8_t> tags(v.n);

@@ -206,6 +206,58 @@ __device__ __forceinline__ void load_chunk(uint8_t *dst, const __nv_bfloat16 *X,
     }
 }
 
+__device__ __forceinline__ bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+// 16 consecutive FP32 values: four 16-byte accesses when the chunk is whole
+// and aligned, else element by element (the first `count` values).
+__device__ __forceinline__ void store16(float *p, const float (&v)[16], bool full, int count)
+{
+    if (full && aligned16(p)) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) ((float4 *)p)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+            if (j < count) p[j] = v[j];
+    }
+}
+
+__device__ __forceinline__ void load16(const float *p, float (&v)[16], bool full, int count)
+{
+    if (full && aligned16(p)) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float4 t = ((const float4 *)p)[q];
+            v[4 * q] = t.x;
+            v[4 * q + 1] = t.y;
+            v[4 * q + 2] = t.z;
+            v[4 * q + 3] = t.w;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = j < count ? p[j] : 0.f;
+    }
+}
+
+__device__ __forceinline__ void store16_bf16(__nv_bfloat16 *p, const float (&v)[16], bool full, int count)
+{
+    if (full && aligned16(p)) {
+        uint4 w[2];
+        uint32_t *u = (uint32_t *)w;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const __nv_bfloat162 b = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+            u[q] = *(const uint32_t *)&b;
+        }
+        ((uint4 *)p)[0] = w[0];
+        ((uint4 *)p)[1] = w[1];
+    } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+            if (j < count) p[j] = __float2bfloat16_rn(v[j]);
+    }
+}
+
 template <int BN>
 __global__ void __launch_bounds__(THREADS, 1) k_gemm(GemmArgs g)
 {
@@ -214,8 +266,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_gemm(GemmArgs g)
     constexpr int B_BYTES = BN * BK * 2;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint8_t *bufA[2] = {smem, smem + A_BYTES + B_BYTES};
-    uint8_t *bufB[2] = {smem + A_BYTES, smem + 2 * A_BYTES + B_BYTES};
+    // buffer b: A at smem + b * (A_BYTES + B_BYTES), B right after it
+    auto bufA = [&](int b) { return smem + b * (A_BYTES + B_BYTES); };
+    auto bufB = [&](int b) { return smem + b * (A_BYTES + B_BYTES) + A_BYTES; };
     __shared__ __align__(8) uint64_t mbar[2];
     __shared__ uint32_t tmem_base;
 
@@ -244,8 +297,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_gemm(GemmArgs g)
     if (nchunks > 0) {
         {
             const int kc = min(BK, k_end - k_begin);
-            load_chunk<BM>(bufA[0], g.A, g.lda, row0, g.M, k_begin, kc / 8);
-            load_chunk<BN>(bufB[0], g.B, g.ldb, 0, g.N, k_begin, kc / 8);
+            load_chunk<BM>(bufA(0), g.A, g.lda, row0, g.M, k_begin, kc / 8);
+            load_chunk<BN>(bufB(0), g.B, g.ldb, 0, g.N, k_begin, kc / 8);
             cp_async_commit();
         }
         for (int c = 0; c < nchunks; ++c) {
@@ -259,8 +312,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_gemm(GemmArgs g)
                 }
                 const int k0 = k_begin + (c + 1) * BK;
                 const int kc = min(BK, k_end - k0);
-                load_chunk<BM>(bufA[b ^ 1], g.A, g.lda, row0, g.M, k0, kc / 8);
-                load_chunk<BN>(bufB[b ^ 1], g.B, g.ldb, 0, g.N, k0, kc / 8);
+                load_chunk<BM>(bufA(b ^ 1), g.A, g.lda, row0, g.M, k0, kc / 8);
+                load_chunk<BN>(bufB(b ^ 1), g.B, g.ldb, 0, g.N, k0, kc / 8);
                 cp_async_commit();
                 cp_async_wait<1>();
             } else {
@@ -273,7 +326,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_gemm(GemmArgs g)
                 const int k0 = k_begin + c * BK;
                 const int kc = min(BK, k_end - k0);
                 const int KG = kc / 8;
-                const uint32_t a0 = smem_u32(bufA[b]), b0 = smem_u32(bufB[b]);
+                const uint32_t a0 = smem_u32(bufA(b)), b0 = smem_u32(bufB(b));
                 for (int kk = 0; kk < kc / 16; ++kk) {
                     const uint64_t ad = desc_kmajor(a0 + kk * 256, 128, KG * 128);
                     const uint64_t bd = desc_kmajor(b0 + kk * 256, 128, KG * 128);
@@ -310,24 +363,44 @@ __global__ void __launch_bounds__(THREADS, 1) k_gemm(GemmArgs g)
                 }
                 if (row >= g.M) continue;
                 const int nst = g.n_store > 0 ? g.n_store : BN;
+                // whole 16-column chunks go through 16-byte vector accesses
+                const bool full = c0 + 16 <= nst;
                 if (g.atomic) {
+                    float *dst = g.Cf + (size_t)row * g.ldcf + c0;
+                    if (full && aligned16(dst)) {
 #pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        if (c0 + j < nst) atomicAdd(g.Cf + (size_t)row * g.ldcf + c0 + j, v[j]);
+                        for (int q = 0; q < 4; ++q)
+                            atomicAdd((float4 *)dst + q, make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]));
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            if (c0 + j < nst) atomicAdd(dst + j, v[j]);
+                    }
                     continue;
                 }
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    if (c0 + j >= nst) continue;
-                    float z = v[j];
-                    if (g.bias) z += g.bias[c0 + j];
-                    if (g.row_scale) z += g.row_scale[row] * g.row_bias[c0 + j];
-                    if (g.Z) g.Z[(size_t)row * g.ldz + c0 + j] = z;
-                    float y = g.act == 1 ? silu(z) : g.act == 2 ? z * dsilu(g.dact[(size_t)row * g.lddact + c0 + j]) : z;
-                    if (g.residual) y += g.residual[(size_t)row * g.ldr + c0 + j];
-                    if (g.Cf) g.Cf[(size_t)row * g.ldcf + c0 + j] = y;
-                    if (g.Cb) g.Cb[(size_t)row * g.ldcb + c0 + j] = __float2bfloat16_rn(y);
+                    if (g.bias) v[j] += g.bias[c0 + j];
+                    if (g.row_scale) v[j] += g.row_scale[row] * g.row_bias[c0 + j];
                 }
+                if (g.Z) store16(g.Z + (size_t)row * g.ldz + c0, v, full, nst - c0);
+                if (g.act == 1) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) v[j] = silu(v[j]);
+                } else if (g.act == 2) {
+                    float a[16];
+                    load16(g.dact + (size_t)row * g.lddact + c0, a, full, nst - c0);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) v[j] *= dsilu(a[j]);
+                }
+                if (g.residual) {
+                    float r[16];
+                    load16(g.residual + (size_t)row * g.ldr + c0, r, full, nst - c0);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) v[j] += r[j];
+                }
+                if (g.Cf) store16(g.Cf + (size_t)row * g.ldcf + c0, v, full, nst - c0);
+                if (g.Cb) store16_bf16(g.Cb + (size_t)row * g.ldcb + c0, v, full, nst - c0);
             }
         }
     }
