@@ -18,6 +18,7 @@
 #include "umma.cuh"
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -100,7 +101,8 @@ struct Surrogate {
     bf16 *Wd2T, *Wd1T, *Wn2T[2], *Wn1T[2], *We2T[2], *WpqT[2], *Wenc2T;
     float *bpq[2], *bd2;
     // forward activations (rows: nodes in sorted order, padded to npad, zero beyond n)
-    bf16 *X16, *A0, *A1[2], *PQ[2], *S[2], *G1[2], *hLb, *A2;
+    bf16 *X16, *A0, *A1[2], *S[2], *G1[2], *hLb, *A2;
+    __half *PQ[2];               // [P | Q] node terms of the edge MLP's first layer, FP16
     float *Z0, *h[3], *degs, *Z1[2], *Z2, *Y;
     float4 *NF;                  // per node: u / sd_edge_u (xyz), density deviation / sd_edge_rho
     // backward
@@ -135,11 +137,13 @@ int dalloc(Surrogate &S, T **p, size_t count)
 // ---------------------------------------------------------------------------
 // Kernels
 
-__device__ __forceinline__ float silu(float z) { return z / (1.f + __expf(-z)); }
+// SiLU and its derivative with the fast reciprocal (relative error ~1e-6,
+// far below the BF16 rounding of the network's operands).
+__device__ __forceinline__ float silu(float z) { return __fdividef(z, 1.f + __expf(-z)); }
 
 __device__ __forceinline__ float dsilu(float z)
 {
-    const float s = 1.f / (1.f + __expf(-z));
+    const float s = __fdividef(1.f, 1.f + __expf(-z));
     return s * (1.f + z * (1.f - s));
 }
 
@@ -228,6 +232,16 @@ __device__ __forceinline__ void load4(const bf16 *p, float (&v)[4])
     v[3] = __high2float(b);
 }
 
+__device__ __forceinline__ void load4(const __half *p, float (&v)[4])
+{
+    const uint2 raw = *(const uint2 *)p;
+    const float2 a = __half22float2(*(const __half2 *)&raw.x), b = __half22float2(*(const __half2 *)&raw.y);
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = b.x;
+    v[3] = b.y;
+}
+
 __device__ __forceinline__ void store4(bf16 *p, const float (&v)[4])
 {
     __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]), b = __floats2bfloat162_rn(v[2], v[3]);
@@ -239,6 +253,11 @@ __device__ __forceinline__ void store4(bf16 *p, const float (&v)[4])
 
 constexpr int GRP = 2;   // valid edges whose row gathers are in flight together
 
+// Width of a staged entry: 2 DIM + 3 edge features and the sender index,
+// padded to whole 16-byte vectors.
+template <int DIM>
+__host__ __device__ constexpr int slot_width() { return ((2 * DIM + 4) + 3) / 4 * 4; }
+
 // Lane-parallel decoding of up to 32 list entries of receiver i (entry
 // k0 + lane on each lane): the edge features and the sender of every valid
 // entry go to the warp's shared-memory slots; returns the ballot of valid
@@ -246,7 +265,7 @@ constexpr int GRP = 2;   // valid edges whose row gathers are in flight together
 template <int DIM>
 __device__ __forceinline__ unsigned stage_entries(const Dev &d, const Grid &g, float R2, float inv2h,
                                                   const float4 &oi, int phi, const float4 &nfi, const float4 *NF,
-                                                  int i, int k0, int cnt, float (*slot)[2 * DIM + 4])
+                                                  int i, int k0, int cnt, float (*slot)[slot_width<DIM>()])
 {
     constexpr int NE = 2 * DIM + 3;
     const int lane = threadIdx.x & 31;
@@ -274,71 +293,123 @@ __device__ __forceinline__ void cp_async8(void *smem, const void *gmem)
                  : "memory");
 }
 
+// Lane-parallel decoding as in stage_entries, storing each feature as a
+// duplicated FP16 pair (the operand of the packed arithmetic below) and the
+// sender index after them.
+template <int DIM>
+__device__ __forceinline__ unsigned stage_entries_h2(const Dev &d, const Grid &g, float R2, float inv2h,
+                                                     const float4 &oi, int phi, const float4 &nfi, const float4 *NF,
+                                                     int i, int k0, int cnt, uint32_t (*slot)[slot_width<DIM>()])
+{
+    constexpr int NE = 2 * DIM + 3;
+    const int lane = threadIdx.x & 31;
+    const int k = k0 + lane;
+    bool valid = false;
+    if (k < cnt) {
+        int j;
+        float ef[NE];
+        valid = edge_features<DIM>(d, g, R2, inv2h, oi, phi, nfi, NF, d.nbr[(size_t)k * d.n + i], j, ef);
+        if (valid) {
+#pragma unroll
+            for (int c = 0; c < NE; ++c) {
+                const __half2 e2 = __float2half2_rn(ef[c]);
+                slot[lane][c] = *(const uint32_t *)&e2;
+            }
+            slot[lane][NE] = (uint32_t)j;
+        }
+    }
+    const unsigned mask = __ballot_sync(0xffffffffu, valid);
+    __syncwarp();
+    return mask;
+}
+
+__device__ __forceinline__ __half2 tanh_h2(__half2 x)
+{
+    uint32_t r;
+    asm("tanh.approx.f16x2 %0, %1;" : "=r"(r) : "r"(*(const uint32_t *)&x));
+    return *(const __half2 *)&r;
+}
+
 // Forward edge phase: one warp per receiver i, four features per lane.
 // S_i = (1/k_ref) sum_j SiLU(P_i + Q_j + W3 e_ij) over list entries with
 // |r_ij| < 2h; degs_i = deg_i / k_ref.  Entries are decoded 32 at a time,
 // one per lane; the sender rows Q_j of every valid entry of the batch are
-// then copied to shared memory with cp.async (all in flight together) and
-// the arithmetic reads them from there.
+// then copied to shared memory with cp.async (all in flight together).  The
+// pre-activation and SiLU run on feature pairs in FP16 (packed FMA, and
+// SiLU(z) = h + h tanh(h) with h = z/2); each batch's sum is added to an
+// FP32 accumulator.
 constexpr int EWF = 128;   // threads of the forward edge kernel (4 warps, one node each)
 
 template <int DIM>
-__global__ void __launch_bounds__(EWF, 6) k_edge_fwd(Dev d, Grid g, float R2, float inv2h, const float4 *NF,
-                                                   const bf16 *PQ, const float *W3, float inv_kref, bf16 *S,
+__global__ void __launch_bounds__(EWF, 4) k_edge_fwd(Dev d, Grid g, float R2, float inv2h, const float4 *NF,
+                                                   const __half *PQ, const float *W3, float inv_kref, bf16 *S,
                                                    float *degs)
 {
     constexpr int NE = 2 * DIM + 3;
-    __shared__ float slots[EWF / 32][32][NE + 1];
-    __shared__ __align__(16) uint2 qrows[EWF / 32][32][32];   // [warp][entry][lane]: 4 BF16 features
-    __shared__ float4 sw[NE][32];   // W3 column c for the four features of lane l
-    for (int t = threadIdx.x; t < NE * 32; t += EWF) {
-        const int c = t / 32, l = t % 32;
-        sw[c][l] = make_float4(W3[(4 * l) * NE + c], W3[(4 * l + 1) * NE + c], W3[(4 * l + 2) * NE + c],
-                               W3[(4 * l + 3) * NE + c]);
-    }
-    __syncthreads();
+    constexpr int SWD = slot_width<DIM>();
+    __shared__ __align__(16) uint32_t slots[EWF / 32][32][SWD];
+    __shared__ __align__(16) uint2 qrows[EWF / 32][32][32];   // [warp][entry][lane]: 4 FP16 features
     const int wid = threadIdx.x >> 5;
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (i >= d.n) return;
     const int f0 = lane * 4;
-    float P[4];
-    load4(PQ + (size_t)i * 2 * H + f0, P);
+    __half2 w2[NE][2];   // W3 column c for features (f0, f0+1) and (f0+2, f0+3)
+#pragma unroll
+    for (int c = 0; c < NE; ++c) {
+        w2[c][0] = __floats2half2_rn(W3[f0 * NE + c], W3[(f0 + 1) * NE + c]);
+        w2[c][1] = __floats2half2_rn(W3[(f0 + 2) * NE + c], W3[(f0 + 3) * NE + c]);
+    }
+    const uint2 praw = *(const uint2 *)(PQ + (size_t)i * 2 * H + f0);
+    const __half2 P0 = *(const __half2 *)&praw.x, P1 = *(const __half2 *)&praw.y;
+    const __half2 half2c = __float2half2_rn(0.5f);
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
     int deg = 0;
     const float4 oi = d.pos[i];
     const float4 nfi = NF[i];
     const int phi = phase_of(oi.w);
     const int cnt = d.ncnt[i];
-    float(*slot)[NE + 1] = slots[wid];
+    uint32_t(*slot)[SWD] = slots[wid];
     uint2(*qr)[32] = qrows[wid];
     for (int k0 = 0; k0 < cnt; k0 += 32) {
-        const unsigned valid = stage_entries<DIM>(d, g, R2, inv2h, oi, phi, nfi, NF, i, k0, cnt, slot);
+        const unsigned valid = stage_entries_h2<DIM>(d, g, R2, inv2h, oi, phi, nfi, NF, i, k0, cnt, slot);
         deg += __popc(valid);
         for (unsigned m = valid; m; m &= m - 1) {
             const int sl = __ffs(m) - 1;
-            cp_async8(&qr[sl][lane], PQ + (size_t)__float_as_int(slot[sl][NE]) * 2 * H + H + f0);
+            cp_async8(&qr[sl][lane], PQ + (size_t)slot[sl][NE] * 2 * H + H + f0);
         }
         asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
         __syncwarp();
+        __half2 s0 = __float2half2_rn(0.f), s1 = s0;
         for (unsigned m = valid; m; m &= m - 1) {
             const int sl = __ffs(m) - 1;
             const uint2 raw = qr[sl][lane];
-            const __nv_bfloat162 qa = *(const __nv_bfloat162 *)&raw.x, qb = *(const __nv_bfloat162 *)&raw.y;
-            float z[4] = {P[0] + __low2float(qa), P[1] + __high2float(qa), P[2] + __low2float(qb),
-                          P[3] + __high2float(qb)};
+            __half2 z0 = __hadd2(P0, *(const __half2 *)&raw.x);
+            __half2 z1 = __hadd2(P1, *(const __half2 *)&raw.y);
+            uint32_t e[SWD];
 #pragma unroll
-            for (int c = 0; c < NE; ++c) {
-                const float ec = slot[sl][c];
-                const float4 wc = sw[c][lane];
-                z[0] = fmaf(wc.x, ec, z[0]);
-                z[1] = fmaf(wc.y, ec, z[1]);
-                z[2] = fmaf(wc.z, ec, z[2]);
-                z[3] = fmaf(wc.w, ec, z[3]);
+            for (int v4 = 0; v4 < SWD / 4; ++v4) {
+                const uint4 t4 = *(const uint4 *)&slot[sl][4 * v4];
+                e[4 * v4] = t4.x;
+                e[4 * v4 + 1] = t4.y;
+                e[4 * v4 + 2] = t4.z;
+                e[4 * v4 + 3] = t4.w;
             }
 #pragma unroll
-            for (int q = 0; q < 4; ++q) acc[q] += silu(z[q]);
+            for (int c = 0; c < NE; ++c) {
+                const __half2 ec = *(const __half2 *)&e[c];
+                z0 = __hfma2(w2[c][0], ec, z0);
+                z1 = __hfma2(w2[c][1], ec, z1);
+            }
+            const __half2 h0 = __hmul2(z0, half2c), h1 = __hmul2(z1, half2c);
+            s0 = __hadd2(s0, __hfma2(h0, tanh_h2(h0), h0));
+            s1 = __hadd2(s1, __hfma2(h1, tanh_h2(h1), h1));
         }
+        const float2 a0 = __half22float2(s0), a1 = __half22float2(s1);
+        acc[0] += a0.x;
+        acc[1] += a0.y;
+        acc[2] += a1.x;
+        acc[3] += a1.y;
         __syncwarp();
     }
 #pragma unroll
@@ -353,11 +424,12 @@ __global__ void __launch_bounds__(EWF, 6) k_edge_fwd(Dev d, Grid g, float R2, fl
 // db1 += dP_i, reduced per block and added with atomics.
 template <int DIM>
 __global__ void __launch_bounds__(EW, 2) k_edge_bwd(Dev d, Grid g, float R2, float inv2h, const float4 *NF,
-                                                 const bf16 *PQ, const float *W3, float inv_kref, const float *dS,
+                                                 const __half *PQ, const float *W3, float inv_kref, const float *dS,
                                                  bf16 *dPQ, float *gW3, float *gb1)
 {
     constexpr int NE = 2 * DIM + 3;
-    __shared__ float slots[EW / 32][32][NE + 1];
+    constexpr int SWD = slot_width<DIM>();
+    __shared__ __align__(16) float slots[EW / 32][32][SWD];
     __shared__ float red[EW / 32][H * (NE + 1)];
     __shared__ float4 sw[NE][32];
     for (int t = threadIdx.x; t < NE * 32; t += EW) {
@@ -389,7 +461,7 @@ __global__ void __launch_bounds__(EW, 2) k_edge_bwd(Dev d, Grid g, float R2, flo
         const float4 nfi = NF[i];
         const int phi = phase_of(oi.w);
         const int cnt = d.ncnt[i];
-        float(*slot)[NE + 1] = slots[wid];
+        float(*slot)[SWD] = slots[wid];
         for (int k0 = 0; k0 < cnt; k0 += 32) {
             unsigned mask = stage_entries<DIM>(d, g, R2, inv2h, oi, phi, nfi, NF, i, k0, cnt, slot);
             while (mask) {
@@ -638,6 +710,7 @@ struct Epi {
     int atomic = 0;
     int k_split = 0;
     int n_store = 0;
+    int cb_half = 0;
 };
 
 int mm(Surrogate &S, cudaStream_t st, const bf16 *A, int lda, const bf16 *B, int ldb, int M, int N, int K,
@@ -668,6 +741,7 @@ int mm(Surrogate &S, cudaStream_t st, const bf16 *A, int lda, const bf16 *B, int
     g.lddact = e.lddact;
     g.atomic = e.atomic;
     g.n_store = e.n_store;
+    g.cb_half = e.cb_half;
     g.err = S.err;
     cudaError_t err = umma::gemm(g, st);
     if (err != cudaSuccess) return set_error(SPH_ECUDA, std::string("gemm: ") + cudaGetErrorString(err));
@@ -839,7 +913,8 @@ int forward(Surrogate &S, const SimView &v, bool training)
         {
             Epi e;
             e.bias = S.bpq[r];
-            e.Cb = S.PQ[r];
+            e.Cb = (bf16 *)S.PQ[r];
+            e.cb_half = 1;
             e.ldcb = 2 * H;
             if ((rc = mm(S, st, S.A1[r], 2 * H, S.Wpq[r], H, n, 2 * H, H, e))) return rc;
         }

@@ -13,11 +13,12 @@
 // releases its TMEM.  The epilogue reads the accumulator with tcgen05.ld
 // (each warp its 32-lane quarter), adds a column bias and an optional
 // row-scaled bias, stores the pre-activation, applies SiLU, adds a residual
-// and writes FP32 and/or BF16 outputs, or adds into FP32 with atomics when K
-// is split across CTAs.
+// and writes FP32 and/or BF16 (or FP16) outputs, or adds into FP32 with
+// atomics when K is split across CTAs.
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -184,6 +185,7 @@ struct GemmArgs {
     int lddact;
     int atomic;                 // 1: atomicAdd the raw accumulator into Cf (split K)
     int n_store;                // columns stored (0: N)
+    int cb_half;                // 1: Cb holds FP16 (__half) instead of BF16
     unsigned *err;              // error word (ERR_TIMEOUT)
 };
 
@@ -236,6 +238,25 @@ __device__ __forceinline__ void load16(const float *p, float (&v)[16], bool full
     } else {
 #pragma unroll
         for (int j = 0; j < 16; ++j) v[j] = j < count ? p[j] : 0.f;
+    }
+}
+
+__device__ __forceinline__ void store16_half(__half *p, const float (&v)[16], bool full, int count)
+{
+    if (full && aligned16(p)) {
+        uint4 w[2];
+        uint32_t *u = (uint32_t *)w;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const __half2 b = __floats2half2_rn(v[2 * q], v[2 * q + 1]);
+            u[q] = *(const uint32_t *)&b;
+        }
+        ((uint4 *)p)[0] = w[0];
+        ((uint4 *)p)[1] = w[1];
+    } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+            if (j < count) p[j] = __float2half_rn(v[j]);
     }
 }
 
@@ -400,7 +421,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_gemm(GemmArgs g)
                     for (int j = 0; j < 16; ++j) v[j] += r[j];
                 }
                 if (g.Cf) store16(g.Cf + (size_t)row * g.ldcf + c0, v, full, nst - c0);
-                if (g.Cb) store16_bf16(g.Cb + (size_t)row * g.ldcb + c0, v, full, nst - c0);
+                if (g.Cb) {
+                    if (g.cb_half) store16_half((__half *)g.Cb + (size_t)row * g.ldcb + c0, v, full, nst - c0);
+                    else store16_bf16(g.Cb + (size_t)row * g.ldcb + c0, v, full, nst - c0);
+                }
             }
         }
     }
