@@ -89,8 +89,15 @@ int sph_surrogate_train_step(sph_handle h, const double *x1_dev, const double *u
  * from the same state: the plain result is kept, and the distance between
  * the two oil centroids over d_ref is the judged error.  An error above tol
  * rejects the surrogate: plain steps replace it until the next judged
- * macro-step.  Reports the judged count, the rejected count and the largest
- * judged error.  Waits for the stream. */
+ * macro-step.  After every unjudged jump the device error flags are read; a
+ * jump that left a non-finite value, a particle outside the box or an
+ * over-full neighbour list is rejected too: the state returns to the last
+ * verified one (the start, or the result of the last judged or plain
+ * stretch), the macro-steps since then are redone with plain steps, and
+ * plain steps continue until the next judged macro-step.  Reports the
+ * judged count, the rejected count (both kinds) and the largest judged
+ * error (1e30 for a judged jump that broke the state).  Waits for the
+ * stream. */
 int sph_surrogate_run(sph_handle h, double dt, int k_steps, int64_t n_macro, int judge_every, double tol,
                       double d_ref, int64_t *n_judged, int64_t *n_rejected, double *max_err);
 

@@ -112,6 +112,7 @@ struct Surrogate {
     unsigned *err = nullptr;
     // judge snapshots (original order)
     double *sx = nullptr, *su = nullptr, *sr = nullptr;
+    double *vx = nullptr, *vu = nullptr, *vr = nullptr;   // last verified state
     std::vector<void *> allocs;
 
     ~Surrogate()
@@ -1344,37 +1345,62 @@ int sph_surrogate_run(sph_handle h, double dt, int k_steps, int64_t n_macro, int
     const SimView v = sim_view(h);
     const size_t nd = (size_t)v.n * v.dim;
     if (!S->sx) {
-        int e = dalloc(*S, &S->sx, nd) | dalloc(*S, &S->su, nd) | dalloc(*S, &S->sr, (size_t)v.n);
+        int e = dalloc(*S, &S->sx, nd) | dalloc(*S, &S->su, nd) | dalloc(*S, &S->sr, (size_t)v.n) |
+                dalloc(*S, &S->vx, nd) | dalloc(*S, &S->vu, nd) | dalloc(*S, &S->vr, (size_t)v.n);
         if (e) return SPH_ENOMEM;
         CUR(cudaDeviceSynchronize());
     }
-    int64_t judged = 0, rejected = 0;
+    // a state the plain method produced or accepted, and the macro-step it belongs to
+    auto verify = [&](int64_t m, int64_t &mv) {
+        mv = m;
+        return sim_snapshot_device(h, S->vx, S->vu, S->vr);
+    };
+    // errors that mean "the jump produced an unusable state" rather than a failure of the library
+    auto state_error = [](int rc) {
+        return rc == SPH_ENONFINITE || rc == SPH_EDOMAIN || rc == SPH_ECAPACITY || rc == SPH_ECFL;
+    };
+    int64_t judged = 0, rejected = 0, mv = 0;
     double worst = 0.0;
     bool fallback = false;
-    int rc = 0;
+    int rc = verify(0, mv);
+    if (rc) return rc;
     for (int64_t mstep = 0; mstep < n_macro; ++mstep) {
         const bool judge = judge_every > 0 && (mstep % judge_every) == 0;
         if (judge) {
             // surrogate jump and plain steps from the same state; the plain result is kept
             if ((rc = sim_snapshot_device(h, S->sx, S->su, S->sr))) return rc;
             if ((rc = sph_surrogate_advance(h, k_steps))) return rc;
-            double cs[3], cp[3];
-            if ((rc = sim_centroid(h, cs))) return rc;
+            double cs[3] = {0, 0, 0}, cp[3];
+            const int crc = sim_centroid(h, cs);
+            if (crc && !state_error(crc)) return crc;
             if ((rc = sim_load_device(h, S->sx, S->su, S->sr))) return rc;
             if ((rc = sim_moved(h, -k_steps))) return rc;
             if ((rc = sph_run(h, dt, k_steps, 1))) return rc;
             if ((rc = sim_centroid(h, cp))) return rc;
             double e2 = 0.0;
             for (int c = 0; c < v.dim; ++c) e2 += (cs[c] - cp[c]) * (cs[c] - cp[c]);
-            const double err = std::sqrt(e2) / d_ref;
+            const double err = crc ? 1.0e30 : std::sqrt(e2) / d_ref;
             worst = std::max(worst, err);
             ++judged;
             fallback = err > tol;
             rejected += fallback ? 1 : 0;
+            if ((rc = verify(mstep + 1, mv))) return rc;
         } else if (fallback) {
             if ((rc = sph_run(h, dt, k_steps, 1))) return rc;
         } else {
             if ((rc = sph_surrogate_advance(h, k_steps))) return rc;
+            const int crc = sim_check(h);
+            if (crc && !state_error(crc)) return crc;
+            if (crc) {
+                // the jump broke the state: back to the last verified state, plain steps from there
+                const int64_t redo = (mstep + 1 - mv) * k_steps;
+                if ((rc = sim_load_device(h, S->vx, S->vu, S->vr))) return rc;
+                if ((rc = sim_moved(h, -redo))) return rc;
+                if ((rc = sph_run(h, dt, redo, 1))) return rc;
+                ++rejected;
+                fallback = true;
+                if ((rc = verify(mstep + 1, mv))) return rc;
+            }
         }
     }
     if ((rc = check_err(*S, v.stream))) return rc;

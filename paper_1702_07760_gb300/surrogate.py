@@ -116,3 +116,68 @@ def train(sim, snap_sets, iters: int, lr: float = 1e-3, lr_final: float = 5e-5, 
         if log_every and it % log_every == 0:
             print(f"[train] it {it} loss {loss:.4e} lr {lr_t:.2e}", flush=True)
     return np.array(hist)
+
+
+def _time_main(argv=None):
+    """Times surrogate jumps (and optionally training steps) on a drop-rise
+    workload with seeded random weights and a fixed normalisation:
+
+        python -m paper_1702_07760_gb300.surrogate --workload drop_3d --jumps 3 --train-steps 0
+    """
+    import argparse
+    import json
+    import time
+
+    import torch
+
+    from . import build as B
+    from . import sph
+    from . import workloads as WL
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="drop_3d", choices=["drop_3d", "drop_3d_32x32x128", "drop_2d"])
+    ap.add_argument("--jumps", type=int, default=3)
+    ap.add_argument("--train-steps", type=int, default=0)
+    a = ap.parse_args(argv)
+    B.build()
+    sph.load()
+    torch.cuda.set_device(0)
+    if a.workload == "drop_3d":
+        w = WL.drop_3d()
+    elif a.workload == "drop_2d":
+        w = WL.drop_2d()
+    else:
+        w = WL.drop_tank(3, (32, 32, 128), drop_d_dx=16, seed=5, name="drop_3d_32x32x128")
+    dim = w.dim
+    dt = WL.stable_dt(w.params)
+    n_in, n_out = SL.n_in(dim), SL.n_out(dim)
+    norm = SL.make_norm(dim, np.zeros(n_in), np.ones(n_in), np.zeros(n_out), np.full(n_out, 1e-6),
+                        80.0 if dim == 3 else 20.0, 8 * dt, 1e-3, 1e-4)
+    sim = sph.Simulation.from_workload(w)
+    sim.surrogate_init(SL.init_weights(dim, seed=1, out_scale=1e-3), norm)
+    out = {"workload": a.workload, "particles": w.n}
+    if a.jumps:
+        sim.surrogate_advance(8)
+        sim.sync()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(a.jumps):
+            sim.surrogate_advance(8)
+        sim.sync()
+        out["ms_per_jump"] = (time.perf_counter() - t0) / a.jumps * 1e3
+    if a.train_steps:
+        tx, tu, tr = (torch.tensor(v, dtype=torch.float64, device="cuda") for v in (w.x, w.u, w.rho))
+        ptr = (tx.data_ptr(), tu.data_ptr(), tr.data_ptr())
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(a.train_steps):
+            sim.load_snapshot(*ptr)
+            sim.surrogate_train_step(*ptr, lr=1e-6)
+        torch.cuda.synchronize()
+        out["ms_per_train_step"] = (time.perf_counter() - t0) / a.train_steps * 1e3
+    sim.close()
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    _time_main()

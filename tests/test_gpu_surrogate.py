@@ -162,6 +162,29 @@ def test_judged_run_falls_back_to_plain(env):
     assert judged == 2 and rejected == 0 and sim2.step_index == 48
 
 
+def test_judged_run_rolls_back_a_broken_jump(env):
+    """A network whose position corrections are scaled to metres throws
+    particles out of the box; the run detects it after the next jump, returns
+    to the last verified state (the start) and redoes the stretch with plain
+    steps, ending where a plain run ends."""
+    torch, sph = env
+    w = WL.drop_tank(2, (24, 30), drop_d_dx=8, seed=82)
+    dim = 2
+    _, norm, flat = _case(dim, 83)
+    norm = norm.copy()
+    o = 2 * SL.n_in(dim) + SL.n_out(dim)
+    norm[o:o + dim] = 1.0   # sd_out of the position corrections
+    dt = WL.stable_dt(w.params)
+    sim = sph.Simulation.from_workload(w)
+    sim.surrogate_init(flat, norm)
+    judged, rejected, err = sim.surrogate_run(dt, 8, 4, 0, 0.02, 2 * w.meta["drop_radius"])
+    assert judged == 0 and rejected == 1
+    plain = sph.Simulation.from_workload(w)
+    plain.run(dt, 32)
+    assert sim.step_index == plain.step_index == 32
+    assert np.abs(sim.read("pos") - plain.read("pos")).max() < 1e-6 * w.params["dx"]
+
+
 def test_training_beats_the_explicit_jump(env):
     """Trained on pairs from a plain trajectory, the network's increments
     over k = 8 steps are closer to the plain method's than the explicit jump
