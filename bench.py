@@ -504,9 +504,9 @@ def run_ours(args, ws, rank, local):
         for _ in range(ke):
             sim.set_state(hx, hu, hr)
             sim.step(dt)
-            hx[:] = sim.read("pos")
-            hu[:] = sim.read("vel")
-            hr[:] = sim.read("rho")
+            sim.read("pos", out=hx)
+            sim.read("vel", out=hu)
+            sim.read("rho", out=hr)
         sim.sync()
         el = max_over_ranks(ws, time.perf_counter() - t0, dev)
         nb = n * (2 * dim + 1) * 8

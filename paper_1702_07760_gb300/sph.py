@@ -304,12 +304,18 @@ class Simulation:
         return a.value, b.value, e.value
 
     # -- output -----------------------------------------------------------
-    def read(self, field: str) -> np.ndarray:
+    def read(self, field: str, out: np.ndarray | None = None) -> np.ndarray:
+        """Copies a field in original particle order into `out` (a C-contiguous
+        array of the field's shape and type, e.g. in pinned host memory) or a
+        new array."""
         n, d = self.n, self.dim
         shapes = dict(pos=(n, d), vel=(n, d), acc=(n, d), tensor=(n, d, d))
         shape = shapes.get(field, (n,))
         dtype = np.int32 if field in ("cell", "order") else np.float64
-        out = np.empty(shape, dtype)
+        if out is None:
+            out = np.empty(shape, dtype)
+        elif out.shape != shape or out.dtype != dtype or not out.flags["C_CONTIGUOUS"]:
+            raise ValueError(f"out must be a C-contiguous {dtype.__name__} array of shape {shape}")
         _check(load().sph_read(self._h, FIELD[field], out.ctypes.data_as(C.c_void_p), out.nbytes))
         return out
 

@@ -52,6 +52,9 @@ CASES = {
     "2d_small": lambda: WL.drop_tank(2, (40, 60), drop_d_dx=12, seed=5, perturb=True),
     "2d_cfg": lambda: WL.drop_2d(seed=0, perturb=True),
     "3d_small": lambda: WL.drop_tank(3, (20, 20, 36), drop_d_dx=10, seed=7, perturb=True),
+    # kinematic viscosity form (Eq. visc_1): nu = mu / rho0 per phase
+    "2d_kinematic": lambda: WL.drop_tank(2, (40, 60), drop_d_dx=12, seed=8, perturb=True, visc_form=1),
+    "3d_kinematic": lambda: WL.drop_tank(3, (20, 20, 36), drop_d_dx=10, seed=9, perturb=True, visc_form=1),
 }
 
 
@@ -100,8 +103,9 @@ def test_single_evaluation_matches_oracle(sphmod, case):
     sim.close()
 
 
-def test_one_step_matches_oracle(sphmod):
-    w = WL.drop_2d(seed=2, perturb=True)
+@pytest.mark.parametrize("visc_form", [0, 1])
+def test_one_step_matches_oracle(sphmod, visc_form):
+    w = WL.drop_2d(seed=2, perturb=True, visc_form=visc_form)
     p = w.params
     dt = WL.stable_dt(p)
     sim = sphmod.Simulation.from_workload(w)
@@ -113,7 +117,7 @@ def test_one_step_matches_oracle(sphmod):
     e_x = np.abs(x - xr).max() / dx
     e_u = rel_err_field(u - w.u, ur - w.u)        # velocity increment dt * a*
     e_r = np.abs(rho / rr - 1).max()
-    print(f"\n[one step] |dx|/dx {e_x:.2e} du {e_u:.2e} rho {e_r:.2e}")
+    print(f"\n[one step, visc_form {visc_form}] |dx|/dx {e_x:.2e} du {e_u:.2e} rho {e_r:.2e}")
     assert e_x < 1e-9
     assert e_u < TOL
     assert e_r < TOL
