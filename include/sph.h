@@ -136,7 +136,13 @@ int sph_set_dt_scales(sph_handle h, const double *scales);
 
 /* Replaces the state (x, u, rho; same layout as sph_create) of an existing
  * handle with host data, keeping its parameters, phases and walls.  The step
- * counter is left as it is. */
+ * counter is left as it is.  After a step has run (and with rebuild_every ==
+ * 0) the cell order and neighbour list are kept when every particle of the
+ * new state is within the corrector's skin test of its position at the last
+ * list build (now and half a step of the last dt ahead); otherwise, or with a
+ * non-finite position, the next step rebuilds them.  Either way the result
+ * of the following steps is that of a handle created at the new state, up to
+ * the particle order in which the sums are taken.  Synchronises the stream. */
 int sph_set_state(sph_handle h, const double *x, const double *u, const double *rho);
 
 /* Builds the cell list at the current positions: cell hash, stable sort by

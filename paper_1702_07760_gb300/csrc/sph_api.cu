@@ -188,6 +188,7 @@ struct sph_sim {
     int blocks(int work, int threads = 256) const { return (work + threads - 1) / threads; }
 
     void enqueue_build_cells(bool force);
+    void enqueue_load(const double *x, const double *u, const double *rho, double check_dt);
     void enqueue_eval(int stage, const float *drho_in, double dt);
     void enqueue_step(double dt);
     int persistent_shape(int bs, int grid_req, int *grid_out, PersistFn *fn_out);
@@ -334,7 +335,9 @@ int set_error(int code, const std::string &msg) { return fail(code, msg); }
 }  // namespace sphgb
 
 namespace {
-__global__ void k_load_state(Dev d, int dim, const double *x, const double *u, const double *rho);
+template <int DIM>
+__global__ void k_load_state(Dev d, Grid g, Phys ph, const double *x, const double *u, const double *rho,
+                             double check_dt);
 __global__ void k_add_step(long long *step, long long k)
 {
     if (threadIdx.x == 0 && blockIdx.x == 0) *step += k;
@@ -344,19 +347,53 @@ __global__ void k_add_step(long long *step, long long k)
 namespace {
 
 // Copies the caller's state (original order, each instance in its own frame)
-// into the sorted device state.
-__global__ void k_load_state(Dev d, int dim, const double *x, const double *u, const double *rho)
+// into the sorted device state.  With check_dt > 0 the cell order and the
+// neighbour list are kept when they still hold the new state: the particle's
+// stage-1 records are written in its current cell, and the rebuild flag is
+// raised if it is farther than the skin allows from where it was at the last
+// build, by the test the corrector applies (positions now and half a step of
+// check_dt ahead; a wall only now).  Non-finite positions always raise it.
+// With check_dt == 0 the caller forces the rebuild.
+template <int DIM>
+__global__ void k_load_state(Dev d, Grid g, Phys ph, const double *x, const double *u, const double *rho,
+                             double check_dt)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= d.n) return;
     const int p = d.pid[k];
     const Inst &I = d.inst[d.iid[k]];
-    for (int c = 0; c < dim; ++c) {
-        d.x[(size_t)c * d.n + k] = x[(size_t)p * dim + c] + I.offset[c];
-        d.u[(size_t)c * d.n + k] = u[(size_t)p * dim + c];
+    const uint8_t tg = d.tag[k];
+    double xa[3] = {0, 0, 0}, ua[3] = {0, 0, 0};
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+        xa[c] = x[(size_t)p * DIM + c] + I.offset[c];
+        ua[c] = u[(size_t)p * DIM + c];
+        d.x[(size_t)c * d.n + k] = xa[c];
+        d.u[(size_t)c * d.n + k] = ua[c];
     }
-    d.drho[k] = (float)(rho[p] - (double)by_phase(d.tag[k] & 1, I.rho0));
+    const float dr = (float)(rho[p] - (double)by_phase(tg & 1, I.rho0));
+    d.drho[k] = dr;
+    if (!(check_dt > 0)) return;
+    stage_records<DIM>(d, g, I, k, d.cell[k], xa, ua, dr, tg & 1);
+    const float4 q = d.pos[k], q0 = d.pos0[k];
+    const float ex = q.x - q0.x, ey = q.y - q0.y, ez = q.z - q0.z;
+    const float dts = (tg & 2) ? 0.f : (float)(check_dt * I.dt_scale);
+    const float hx = 0.5f * dts * (float)ua[0], hy = 0.5f * dts * (float)ua[1], hz = 0.5f * dts * (float)ua[2];
+    const float d1 = ex * ex + ey * ey + ez * ez;
+    const float d2 = (ex + hx) * (ex + hx) + (ey + hy) * (ey + hy) + (ez + hz) * (ez + hz);
+    const float lim = (float)(0.98 * ph.skin);
+    if (!(d1 <= lim * lim) || !(d2 <= lim * lim)) atomicOr(d.rebuild, 1u);
 }
+
+}  // namespace
+
+void sph_sim::enqueue_load(const double *x, const double *u, const double *rho, double check_dt)
+{
+    if (dim == 2) k_load_state<2><<<blocks(n), 256, 0, stream>>>(D(), grid, phys, x, u, rho, check_dt);
+    else k_load_state<3><<<blocks(n), 256, 0, stream>>>(D(), grid, phys, x, u, rho, check_dt);
+}
+
+namespace {
 
 __global__ void k_iota(int *p, int n)
 {
@@ -800,7 +837,7 @@ int sim_snapshot_device(sph_sim *s, double *x, double *u, double *rho)
 int sim_load_device(sph_sim *s, const double *x, const double *u, const double *rho)
 {
     if (s->n == 0) return SPH_OK;
-    k_load_state<<<s->blocks(s->n), 256, 0, s->stream>>>(s->D(), s->dim, x, u, rho);
+    s->enqueue_load(x, u, rho, 0.0);
     CU(cudaGetLastError());
     CU(cudaMemsetAsync(s->rebuild, 0xff, sizeof(unsigned), s->stream));
     return SPH_OK;
@@ -859,9 +896,12 @@ int sph_set_state(sph_handle s, const double *x, const double *u, const double *
     CU(cudaMemcpyAsync(dx, x, sizeof(double) * n * dim, cudaMemcpyHostToDevice, s->stream));
     CU(cudaMemcpyAsync(du, u, sizeof(double) * n * dim, cudaMemcpyHostToDevice, s->stream));
     CU(cudaMemcpyAsync(dr, rho, sizeof(double) * n, cudaMemcpyHostToDevice, s->stream));
-    k_load_state<<<s->blocks(s->n), 256, 0, s->stream>>>(s->D(), s->dim, dx, du, dr);
+    // the lists are kept when they still hold the new state (tested against the
+    // skin with the last step size; a fixed rebuild cadence or no step yet rebuilds)
+    const double check_dt = s->P.rebuild_every == 0 ? s->last_dt : 0.0;
+    s->enqueue_load(dx, du, dr, check_dt);
     CU(cudaGetLastError());
-    CU(cudaMemsetAsync(s->rebuild, 0xff, sizeof(unsigned), s->stream));
+    if (!(check_dt > 0)) CU(cudaMemsetAsync(s->rebuild, 0xff, sizeof(unsigned), s->stream));
     CU(cudaStreamSynchronize(s->stream));
     return SPH_OK;
 }

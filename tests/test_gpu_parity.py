@@ -154,6 +154,62 @@ def test_restart_is_bit_exact(sphmod):
     assert a.list_builds == 20
 
 
+def test_set_state_keeps_valid_lists(sphmod):
+    """Loading back the state a handle holds keeps its cell order and list
+    (no rebuild) and leaves the trajectory bit for bit unchanged."""
+    w = WL.drop_tank(2, (40, 60), drop_d_dx=12, seed=14, perturb=True)
+    dt = WL.stable_dt(w.params)
+    a = sphmod.Simulation.from_workload(w)
+    b = sphmod.Simulation.from_workload(w)
+    a.run(dt, 12, graph=False)
+    b.run(dt, 12, graph=False)
+    for k in range(4):
+        x, u, r = b.read("pos"), b.read("vel"), b.read("rho")
+        b.set_state(x, u, r)
+        b.step(dt)
+        a.step(dt)
+        assert np.array_equal(a.read("pos"), b.read("pos")), k
+        assert a.list_builds == b.list_builds
+    for f in ("vel", "rho", "order"):
+        assert np.array_equal(a.read(f), b.read(f)), f
+
+
+@pytest.mark.parametrize("move", ["far", "skin", "nan"])
+def test_set_state_rebuilds_when_the_skin_is_exceeded(sphmod, move):
+    """A loaded state with a particle beyond the skin test (or non-finite)
+    rebuilds; the run then equals one created at that state."""
+    w = WL.drop_tank(2, (40, 60), drop_d_dx=12, seed=15, perturb=True)
+    p = w.params
+    dt = WL.stable_dt(p)
+    s = sphmod.Simulation.from_workload(w)
+    s.run(dt, 6, graph=False)
+    x, u, r = s.read("pos"), s.read("vel"), s.read("rho")
+    fluid = np.flatnonzero(w.wall == 0)
+    if move == "far":
+        x2 = x.copy()                         # two distant fluid particles trade places
+        i, j = fluid[0], fluid[-1]
+        x2[[i, j]] = x2[[j, i]]
+    else:
+        x2 = x.copy()
+        # every particle is within 0.98 skin of its build position, so a move of
+        # 2 skin ends beyond the test whatever the direction of the earlier drift
+        x2[fluid[len(fluid) // 2], 0] += 2.0 * p["skin"] if move == "skin" else np.nan
+    builds = s.list_builds
+    s.set_state(x2, u, r)
+    if move == "nan":
+        with pytest.raises(sphmod.SphError):
+            s.step(dt)
+            s.sync()
+        return
+    s.step(dt)
+    s.sync()
+    assert s.list_builds == builds + 1
+    t = sphmod.Simulation(p, x2, u, r, w.phase, w.wall)
+    t.step(dt)
+    assert np.allclose(s.read("pos"), t.read("pos"), rtol=0, atol=1e-9 * p["dx"])
+    assert np.allclose(s.read("rho"), t.read("rho"), rtol=1e-6, atol=0)
+
+
 def test_adaptive_list_rebuild_matches_every_step_build(sphmod):
     """The displacement-driven rebuild skips builds and changes only the
     summation order (FP32 rounding), never the neighbour sets."""
