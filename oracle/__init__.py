@@ -27,7 +27,7 @@ class OrParams(C.Structure):
         ("dim", C.c_int32),
         ("visc_form", C.c_int32),
         ("renorm_every", C.c_int32),
-        ("reserved", C.c_int32),
+        ("periodic", C.c_int32),
         ("h", C.c_double),
         ("c0", C.c_double),
         ("gamma", C.c_double),
@@ -40,6 +40,17 @@ class OrParams(C.Structure):
         ("mass", C.c_double * 2),
         ("box_lo", C.c_double * 3),
         ("box_hi", C.c_double * 3),
+    ]
+
+
+class OrPiston(C.Structure):
+    _fields_ = [
+        ("axis", C.c_int32),
+        ("ncomp", C.c_int32),
+        ("t_end", C.c_double),
+        ("amp", C.c_double * 8),
+        ("omega", C.c_double * 8),
+        ("phase", C.c_double * 8),
     ]
 
 
@@ -81,10 +92,14 @@ def lib():
         L.or_eval.argtypes = [P(OrParams), C.c_int64, dp, dp, dp, u8p, u8p, C.c_int,
                               dp, dp, dp, dp, dp, dp]
         L.or_step.restype = C.c_int
-        L.or_step.argtypes = [P(OrParams), C.c_int64, dp, dp, dp, u8p, u8p, C.c_double, C.c_int64]
+        L.or_step.argtypes = [P(OrParams), C.c_int64, dp, dp, dp, u8p, u8p, C.c_double, C.c_int64,
+                              P(OrPiston), C.c_double]
         L.or_run.restype = C.c_int
         L.or_run.argtypes = [P(OrParams), C.c_int64, dp, dp, dp, u8p, u8p, C.c_double,
-                             C.c_int64, C.c_int64]
+                             C.c_int64, C.c_int64, P(OrPiston), C.c_double]
+        for f in (L.or_piston_disp, L.or_piston_vel):
+            f.restype = C.c_double
+            f.argtypes = [P(OrPiston), C.c_double]
         L.or_diag.argtypes = [P(OrParams), C.c_int64, dp, dp, u8p, u8p, dp]
         L.or_num_threads.restype = C.c_int
         L.or_set_num_threads.argtypes = [C.c_int]
@@ -98,6 +113,7 @@ def make_params(p: dict) -> OrParams:
     o.dim = int(p["dim"])
     o.visc_form = int(p.get("visc_form", 0))
     o.renorm_every = int(p.get("renorm_every", 1))
+    o.periodic = int(p.get("periodic", 0))
     o.h = p["h"]
     o.c0 = p["c0"]
     o.gamma = p.get("gamma", 7.0)
@@ -113,6 +129,29 @@ def make_params(p: dict) -> OrParams:
         o.mu[k] = p["mu"][k]
         o.mass[k] = p["mass"][k]
     return o
+
+
+def make_piston(m: dict | None) -> OrPiston | None:
+    """The oracle's piston struct from a dict with axis, amp, omega, phase
+    (equal-length sequences, at most 8) and t_end; None for no motion."""
+    if m is None:
+        return None
+    o = OrPiston()
+    o.axis = int(m["axis"])
+    o.ncomp = len(m["amp"])
+    assert o.ncomp <= 8 and len(m["omega"]) == len(m["phase"]) == o.ncomp
+    o.t_end = float(m["t_end"])
+    for c in range(o.ncomp):
+        o.amp[c], o.omega[c], o.phase[c] = m["amp"][c], m["omega"][c], m["phase"][c]
+    return o
+
+
+def piston_disp(m: dict, t: float) -> float:
+    return lib().or_piston_disp(C.byref(make_piston(m)), t)
+
+
+def piston_vel(m: dict, t: float) -> float:
+    return lib().or_piston_vel(C.byref(make_piston(m)), t)
 
 
 def _d(a):
@@ -195,15 +234,19 @@ def evaluate(p: dict, x, u, rho, phase, wall, renorm: bool):
     return out
 
 
-def run(p: dict, x, u, rho, phase, wall, dt: float, nsteps: int, first_step: int = 0):
-    """nsteps predictor-corrector steps; returns new (x, u, rho) copies."""
+def run(p: dict, x, u, rho, phase, wall, dt: float, nsteps: int, first_step: int = 0,
+        piston: dict | None = None, t0: float = 0.0):
+    """nsteps predictor-corrector steps from time t0; returns new (x, u, rho)
+    copies.  Particles with wall == 2 follow the piston motion (if given)."""
     x = np.array(x, np.float64, copy=True, order="C")
     u = np.array(u, np.float64, copy=True, order="C")
     rho = np.array(rho, np.float64, copy=True, order="C")
     phase = np.ascontiguousarray(phase, np.uint8)
     wall = np.ascontiguousarray(wall, np.uint8)
+    m = make_piston(piston)
     rc = lib().or_run(C.byref(make_params(p)), len(x), _d(x), _d(u), _d(rho),
-                      _c(phase, C.c_uint8), _c(wall, C.c_uint8), dt, first_step, nsteps)
+                      _c(phase, C.c_uint8), _c(wall, C.c_uint8), dt, first_step, nsteps,
+                      C.byref(m) if m is not None else None, t0)
     if rc != 0:
         raise RuntimeError(f"oracle step failed ({rc})")
     return x, u, rho

@@ -30,11 +30,23 @@
  *   - T = 0 exactly when grad C = 0 (no threshold: |T| <= alpha_s |grad C|
  *     tends to zero with grad C).
  *   - time integration is the explicit midpoint predictor-corrector.
+ *   - a periodic axis (the cross-tank boundary condition of the flume runs,
+ *     Sec. "Laboratory experiment & numerical setup") is a box side of a
+ *     whole number of cells; r_ij is taken as the minimum image along it and
+ *     positions are wrapped into the box after every step.
+ *   - the piston wavemaker (same section) is a set of boundary particles
+ *     that move rigidly along one axis with a prescribed displacement X(t);
+ *     the predictor puts them at X(t + dt/2) with velocity X'(t + dt/2) and
+ *     the corrector at X(t + dt) with velocity X'(t + dt).  Like the other
+ *     boundary particles their density integrates and their acceleration is
+ *     not computed.
  *
  * Parity status: every function here is pinned by a CPU test (kernel
  * normalisation, partition of unity, EOS closed form, renormalisation
  * invariants, pairwise antisymmetry, brute-force neighbour sets, exact
- * kinematics, hydrostatic column, Laplace jump).
+ * kinematics, hydrostatic column, Laplace jump; periodic box against the
+ * replicated box, translation invariance and the periodic lattice at rest;
+ * the paper's wave-maker formula and exact piston kinematics).
  */
 #include <math.h>
 #include <stdint.h>
@@ -49,7 +61,7 @@ typedef struct {
     int32_t dim;          /* 2 or 3 */
     int32_t visc_form;    /* 0: dynamic form (Eq. visc_2), 1: kinematic form (Eq. visc_1) */
     int32_t renorm_every; /* Eq. ct_dist_3 at stage 1 of steps n % k == 0; 0 = never */
-    int32_t reserved;
+    int32_t periodic;     /* bit k set: axis k is periodic with period box_hi - box_lo */
     double h;             /* smoothing length */
     double c0;            /* reference speed of sound C_s0 */
     double gamma;         /* exponent of the equation of state */
@@ -63,6 +75,66 @@ typedef struct {
     double box_lo[3];
     double box_hi[3];
 } or_params;
+
+/* Prescribed piston motion along `axis`: for t <= t_end
+ *   X(t) = sum_c amp_c (sin(omega_c t + phase_c) - sin(phase_c)),
+ *   X'(t) = sum_c amp_c omega_c cos(omega_c t + phase_c);
+ * after t_end the piston stays at X(t_end) with zero velocity.  The paper's
+ * stroke x(t) = S/2 - S/2 cos(2 pi f t), 0 <= t <= 1/(2f), is one component
+ * with amp = S/2, omega = 2 pi f, phase = -pi/2 and t_end = 1/(2f).        */
+typedef struct {
+    int32_t axis;
+    int32_t ncomp;        /* 0..8; 0 = no motion */
+    double t_end;
+    double amp[8];
+    double omega[8];
+    double phase[8];
+} or_piston;
+
+double or_piston_disp(const or_piston *m, double t)
+{
+    double te = t < m->t_end ? t : m->t_end;
+    double X = 0.0;
+    for (int c = 0; c < m->ncomp; ++c) X += m->amp[c] * (sin(m->omega[c] * te + m->phase[c]) - sin(m->phase[c]));
+    return X;
+}
+
+double or_piston_vel(const or_piston *m, double t)
+{
+    if (t > m->t_end) return 0.0;
+    double U = 0.0;
+    for (int c = 0; c < m->ncomp; ++c) U += m->amp[c] * m->omega[c] * cos(m->omega[c] * t + m->phase[c]);
+    return U;
+}
+
+/* Period of axis k (0 when the axis is not periodic). */
+static double period(const or_params *p, int k)
+{
+    return (p->periodic >> k) & 1 ? p->box_hi[k] - p->box_lo[k] : 0.0;
+}
+
+/* r_ij = x_i - x_j, minimum image along periodic axes; returns |r_ij|^2. */
+static double pair_r(const or_params *p, const double *x, int64_t i, int64_t j, double *rij)
+{
+    double s = 0.0;
+    for (int k = 0; k < p->dim; ++k) {
+        double d = x[i * p->dim + k] - x[j * p->dim + k];
+        double L = period(p, k);
+        if (L > 0.0) d -= L * nearbyint(d / L);
+        rij[k] = d;
+        s += d * d;
+    }
+    return s;
+}
+
+/* Coordinate k of a position wrapped into [box_lo, box_hi) when axis k is
+ * periodic; unchanged otherwise. */
+static double wrapped(const or_params *p, int k, double v)
+{
+    double L = period(p, k);
+    if (L > 0.0) v -= L * floor((v - p->box_lo[k]) / L);
+    return v;
+}
 
 /* ------------------------------------------------------------------------ */
 /* Smoothing kernel: Wendland C2, W(q) = alpha_d (1 - q/2)^4 (2q + 1), q=r/h */
@@ -120,15 +192,18 @@ double or_eos_inverse(const or_params *p, int phase, double pressure)
 
 /* ------------------------------------------------------------------------ */
 /* Cell grid used by the neighbour search.  A cell is the integer part of
- * (x - box_lo) / cell_size on each axis; the grid has
- * floor((box_hi - box_lo) / cell_size) + 1 cells per axis and the linear id
- * is ix + nx * (iy + ny * iz).                                              */
+ * (x - box_lo) / cell_size on each axis (x wrapped into the box along a
+ * periodic axis); the grid has floor((box_hi - box_lo) / cell_size) + 1
+ * cells per axis, or (box_hi - box_lo) / cell_size rounded along a periodic
+ * axis, and the linear id is ix + nx * (iy + ny * iz).                      */
 
 void or_grid_dims(const or_params *p, int32_t *dims)
 {
     for (int k = 0; k < 3; ++k) dims[k] = 1;
-    for (int k = 0; k < p->dim; ++k)
-        dims[k] = (int32_t)floor((p->box_hi[k] - p->box_lo[k]) / p->cell_size) + 1;
+    for (int k = 0; k < p->dim; ++k) {
+        double m = (p->box_hi[k] - p->box_lo[k]) / p->cell_size;
+        dims[k] = period(p, k) > 0.0 ? (int32_t)nearbyint(m) : (int32_t)floor(m) + 1;
+    }
 }
 
 /* Returns the number of particles outside the box (their id is -1). */
@@ -141,7 +216,8 @@ int64_t or_cell_ids(const or_params *p, int64_t n, const double *x, int32_t *cel
         int32_t c[3] = {0, 0, 0};
         int ok = 1;
         for (int k = 0; k < p->dim; ++k) {
-            double s = floor((x[i * p->dim + k] - p->box_lo[k]) / p->cell_size);
+            double s = floor((wrapped(p, k, x[i * p->dim + k]) - p->box_lo[k]) / p->cell_size);
+            if (period(p, k) > 0.0 && s >= (double)dims[k]) s = dims[k] - 1;  /* rounding at box_hi */
             if (!(s >= 0.0 && s < (double)dims[k])) ok = 0;
             else c[k] = (int32_t)s;
         }
@@ -175,14 +251,10 @@ void or_sort_perm(int64_t n, const int32_t *cell, int64_t *perm)
  * ascending j.  Both functions return the number of entries, or -1 when the
  * caller's list capacity is too small (start[] is then still filled).      */
 
-static double dist2(int dim, const double *x, int64_t i, int64_t j)
+static double dist2(const or_params *p, const double *x, int64_t i, int64_t j)
 {
-    double s = 0.0;
-    for (int k = 0; k < dim; ++k) {
-        double d = x[i * dim + k] - x[j * dim + k];
-        s += d * d;
-    }
-    return s;
+    double rij[3];
+    return pair_r(p, x, i, j, rij);
 }
 
 int64_t or_neighbours_brute(const or_params *p, int64_t n, const double *x,
@@ -193,7 +265,7 @@ int64_t or_neighbours_brute(const or_params *p, int64_t n, const double *x,
     for (int64_t i = 0; i < n; ++i) {
         start[i] = total;
         for (int64_t j = 0; j < n; ++j) {
-            if (j == i || dist2(p->dim, x, i, j) >= R2) continue;
+            if (j == i || dist2(p, x, i, j) >= R2) continue;
             if (total < cap) list[total] = (int32_t)j;
             ++total;
         }
@@ -209,7 +281,9 @@ static int cmp_i32(const void *a, const void *b)
 }
 
 /* Same sets through a cell list: particles sorted by cell, every i scans the
- * cells within w = ceil(2h / cell_size) of its own on each axis.           */
+ * cells within w = ceil(2h / cell_size) of its own on each axis (wrapping
+ * around a periodic axis).  Returns -3 when a periodic axis has fewer than
+ * 2w + 1 cells.                                                             */
 int64_t or_neighbours_cells(const or_params *p, int64_t n, const double *x,
                             int64_t *start, int32_t *list, int64_t cap)
 {
@@ -231,6 +305,16 @@ int64_t or_neighbours_cells(const or_params *p, int64_t n, const double *x,
     int dim = p->dim;
     const int w = (int)ceil(2.0 * p->h / p->cell_size);
     const int wz = dim == 3 ? w : 0;
+    /* a periodic axis needs 2w + 1 distinct cells, else a cell would be
+     * scanned twice */
+    int per[3] = {0, 0, 0};
+    for (int k = 0; k < dim; ++k) {
+        per[k] = period(p, k) > 0.0;
+        if (per[k] && dims[k] < 2 * w + 1) {
+            free(cell); free(perm); free(cstart); free(count);
+            return -3;
+        }
+    }
 
     /* pass 1: counts */
 #pragma omp parallel for schedule(dynamic, 256)
@@ -242,11 +326,14 @@ int64_t or_neighbours_cells(const or_params *p, int64_t n, const double *x,
             for (int dy = -w; dy <= w; ++dy)
                 for (int dx = -w; dx <= w; ++dx) {
                     int32_t X = cx + dx, Y = cy + dy, Z = cz + dz;
+                    if (per[0]) X = (X + dims[0]) % dims[0];
+                    if (per[1]) Y = (Y + dims[1]) % dims[1];
+                    if (per[2]) Z = (Z + dims[2]) % dims[2];
                     if (X < 0 || Y < 0 || Z < 0 || X >= dims[0] || Y >= dims[1] || Z >= dims[2]) continue;
                     int64_t c = X + (int64_t)dims[0] * (Y + (int64_t)dims[1] * Z);
                     for (int64_t k = cstart[c]; k < cstart[c + 1]; ++k) {
                         int64_t j = perm[k];
-                        if (j != i && dist2(dim, x, i, j) < R2) ++cnt;
+                        if (j != i && dist2(p, x, i, j) < R2) ++cnt;
                     }
                 }
         count[i] = cnt;
@@ -268,11 +355,14 @@ int64_t or_neighbours_cells(const or_params *p, int64_t n, const double *x,
             for (int dy = -w; dy <= w; ++dy)
                 for (int dx = -w; dx <= w; ++dx) {
                     int32_t X = cx + dx, Y = cy + dy, Z = cz + dz;
+                    if (per[0]) X = (X + dims[0]) % dims[0];
+                    if (per[1]) Y = (Y + dims[1]) % dims[1];
+                    if (per[2]) Z = (Z + dims[2]) % dims[2];
                     if (X < 0 || Y < 0 || Z < 0 || X >= dims[0] || Y >= dims[1] || Z >= dims[2]) continue;
                     int64_t c = X + (int64_t)dims[0] * (Y + (int64_t)dims[1] * Z);
                     for (int64_t k = cstart[c]; k < cstart[c + 1]; ++k) {
                         int64_t j = perm[k];
-                        if (j != i && dist2(dim, x, i, j) < R2) list[wr++] = (int32_t)j;
+                        if (j != i && dist2(p, x, i, j) < R2) list[wr++] = (int32_t)j;
                     }
                 }
         qsort(list + start[i], (size_t)(start[i + 1] - start[i]), sizeof(int32_t), cmp_i32);
@@ -289,7 +379,7 @@ static int build_neighbours(const or_params *p, int64_t n, const double *x,
     /* first call with zero capacity only sizes the lists */
     int64_t cap = 0;
     int64_t r = or_neighbours_cells(p, n, x, start, NULL, 0);
-    if (r == -2) { free(start); return -2; }
+    if (r == -2 || r == -3) { free(start); return (int)r; }
     cap = start[n];
     int32_t *list = malloc(sizeof(int32_t) * (size_t)(cap ? cap : 1));
     r = or_neighbours_cells(p, n, x, start, list, cap);
@@ -343,7 +433,7 @@ int or_eval(const or_params *p, int64_t n, const double *x, const double *u,
         for (int64_t k = start[i]; k < start[i + 1]; ++k) {
             int64_t j = list[k];
             if (phase[j] != ph) continue;
-            double r = sqrt(dist2(d, x, i, j));
+            double r = sqrt(dist2(p, x, i, j));
             double Wij = or_W(d, p->h, r);
             num += p->mass[phase[j]] * Wij;
             den += p->mass[phase[j]] / rho_in[j] * Wij;
@@ -363,8 +453,7 @@ int or_eval(const or_params *p, int64_t n, const double *x, const double *u,
             int64_t j = list[k];
             if (phase[j] == phase[i]) continue;
             double rij[3], gw[3];
-            for (int c = 0; c < d; ++c) rij[c] = x[i * d + c] - x[j * d + c];
-            double r = sqrt(dist2(d, x, i, j));
+            double r = sqrt(pair_r(p, x, i, j, rij));
             grad_W(d, p->h, rij, r, gw);
             double sigma_j = rho_in[j] / p->mass[phase[j]];
             for (int c = 0; c < d; ++c) gc[c] += sigma_i * (1.0 / (sigma_j * sigma_j)) * gw[c];
@@ -401,11 +490,8 @@ int or_eval(const or_params *p, int64_t n, const double *x, const double *u,
             int pj = phase[j];
             double m_j = p->mass[pj];
             double rij[3] = {0, 0, 0}, uij[3] = {0, 0, 0}, gw[3];
-            for (int c = 0; c < d; ++c) {
-                rij[c] = x[i * d + c] - x[j * d + c];
-                uij[c] = u[i * d + c] - u[j * d + c];
-            }
-            double r2 = dist2(d, x, i, j);
+            for (int c = 0; c < d; ++c) uij[c] = u[i * d + c] - u[j * d + c];
+            double r2 = pair_r(p, x, i, j, rij);
             double r = sqrt(r2);
             grad_W(d, p->h, rij, r, gw);
             double rdotgw = 0.0, udotgw = 0.0;
@@ -453,17 +539,21 @@ int or_eval(const or_params *p, int64_t n, const double *x, const double *u,
 }
 
 /* ------------------------------------------------------------------------ */
-/* One predictor-corrector (explicit midpoint) step of size dt, in place.
+/* One predictor-corrector (explicit midpoint) step of size dt from time t,
+ * in place.
  *   stage 1 at (x^n, u^n, rho^n), with the renormalisation when
  *     renorm_every > 0 and step_index % renorm_every == 0 (the renormalised
  *     density replaces rho^n);
  *   x* = x^n + dt/2 u^n, u* = u^n + dt/2 a^n, rho* = rho^n + dt/2 Drho^n;
  *   stage 2 at (x*, u*, rho*);
  *   x^{n+1} = x^n + dt u*, u^{n+1} = u^n + dt a*, rho^{n+1} = rho^n + dt Drho*.
- * Dynamic boundary particles keep x and u; their density integrates.
+ * Boundary particles (wall 1) keep x and u; piston particles (wall 2) move
+ * with the prescribed motion m (NULL: at rest, like wall 1); the density of
+ * both integrates.  Positions are then wrapped along periodic axes.
  * Returns 0, or -2 when a particle left the box.                           */
 int or_step(const or_params *p, int64_t n, double *x, double *u, double *rho,
-            const uint8_t *phase, const uint8_t *wall, double dt, int64_t step_index)
+            const uint8_t *phase, const uint8_t *wall, double dt, int64_t step_index,
+            const or_piston *m, double t)
 {
     const int d = p->dim;
     size_t nv = (size_t)n * d, nt = (size_t)n * d * d;
@@ -473,6 +563,13 @@ int or_step(const or_params *p, int64_t n, double *x, double *u, double *rho,
     double *xs = malloc(sizeof(double) * nv), *us = malloc(sizeof(double) * nv);
     double *rs = malloc(sizeof(double) * n);
     int renorm = p->renorm_every > 0 && step_index % p->renorm_every == 0;
+    int moving = m != NULL && m->ncomp > 0;
+    /* piston displacement over each stage and its velocity at the stage end */
+    double X0 = moving ? or_piston_disp(m, t) : 0.0;
+    double dX_half = moving ? or_piston_disp(m, t + 0.5 * dt) - X0 : 0.0;
+    double dX_full = moving ? or_piston_disp(m, t + dt) - X0 : 0.0;
+    double U_half = moving ? or_piston_vel(m, t + 0.5 * dt) : 0.0;
+    double U_full = moving ? or_piston_vel(m, t + dt) : 0.0;
 
     int rc = or_eval(p, n, x, u, rho, phase, wall, renorm, rho_s, P, gc, T, a, dr);
     if (rc == 0) {
@@ -481,8 +578,13 @@ int or_step(const or_params *p, int64_t n, double *x, double *u, double *rho,
             rs[i] = rho[i] + 0.5 * dt * dr[i];
             for (int c = 0; c < d; ++c) {
                 size_t k = (size_t)i * d + c;
-                xs[k] = wall[i] ? x[k] : x[k] + 0.5 * dt * u[k];
-                us[k] = wall[i] ? u[k] : u[k] + 0.5 * dt * a[k];
+                if (wall[i] == 2 && moving) {
+                    xs[k] = c == m->axis ? x[k] + dX_half : x[k];
+                    us[k] = c == m->axis ? U_half : 0.0;
+                } else {
+                    xs[k] = wall[i] ? x[k] : x[k] + 0.5 * dt * u[k];
+                    us[k] = wall[i] ? u[k] : u[k] + 0.5 * dt * a[k];
+                }
             }
         }
         rc = or_eval(p, n, xs, us, rs, phase, wall, 0, rho_s, P, gc, T, a, dr);
@@ -490,11 +592,16 @@ int or_step(const or_params *p, int64_t n, double *x, double *u, double *rho,
     if (rc == 0) {
         for (int64_t i = 0; i < n; ++i) {
             rho[i] = rho[i] + dt * dr[i];
-            if (wall[i]) continue;
             for (int c = 0; c < d; ++c) {
                 size_t k = (size_t)i * d + c;
-                x[k] = x[k] + dt * us[k];
-                u[k] = u[k] + dt * a[k];
+                if (wall[i] == 2 && moving) {
+                    if (c == m->axis) x[k] = x[k] + dX_full;
+                    u[k] = c == m->axis ? U_full : 0.0;
+                } else if (!wall[i]) {
+                    x[k] = x[k] + dt * us[k];
+                    u[k] = u[k] + dt * a[k];
+                }
+                x[k] = wrapped(p, c, x[k]);
             }
         }
     }
@@ -503,13 +610,16 @@ int or_step(const or_params *p, int64_t n, double *x, double *u, double *rho,
     return rc;
 }
 
+/* nsteps steps from time t0; the time advances by repeated addition of dt. */
 int or_run(const or_params *p, int64_t n, double *x, double *u, double *rho,
            const uint8_t *phase, const uint8_t *wall, double dt,
-           int64_t first_step, int64_t nsteps)
+           int64_t first_step, int64_t nsteps, const or_piston *m, double t0)
 {
+    double t = t0;
     for (int64_t s = 0; s < nsteps; ++s) {
-        int rc = or_step(p, n, x, u, rho, phase, wall, dt, first_step + s);
+        int rc = or_step(p, n, x, u, rho, phase, wall, dt, first_step + s, m, t);
         if (rc != 0) return rc;
+        t += dt;
     }
     return 0;
 }

@@ -1,0 +1,231 @@
+"""Pins of the oracle's periodic axes and piston wavemaker (the flume set-up of
+Sec. "Laboratory experiment & numerical setup": a cross-tank periodic
+boundary and a piston-type wave maker).
+
+* A periodic box gives the rates of the middle copy of the same particles
+  replicated three times along that axis in an ordinary (non-periodic) box:
+  the minimum image is checked against plain geometry.
+* Translating every particle along a periodic axis changes nothing.
+* A full periodic lattice at uniform density is at rest (a = 0, Drho = 0).
+* The stroke reproduces the paper's wave-maker formula at printed times, and
+  piston particles land exactly on the prescribed displacement.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1702_07760_gb300 import workloads as WL
+
+
+def periodic_patch(dim, shape, axis, seed=5, jitter=0.05, drop=True):
+    """Free two-phase patch, periodic along `axis` with period shape[axis]*dx,
+    open with room along the other axes; cell_size divides the period."""
+    w = WL.drop_tank(dim, shape, wall_layers=0, seed=seed, jitter_dx=jitter,
+                     drop_d_dx=min(shape) * 0.5 if drop else 0.0)
+    p = w.params
+    p["g"] = [0.0, 0.0, 0.0]
+    dx, h = p["dx"], p["h"]
+    L = shape[axis] * dx
+    m = int(L // (2 * h))
+    p["cell_size"] = L / m
+    for k in range(dim):
+        if k == axis:
+            p["box_lo"][k], p["box_hi"][k] = 0.0, L
+        else:
+            p["box_lo"][k] -= 4 * h
+            p["box_hi"][k] += 4 * h
+    p["periodic"] = 1 << axis
+    # a shear flow along the axis, so the viscous and continuity terms see
+    # pairs across the boundary with different velocities
+    rng = np.random.Generator(np.random.PCG64(seed + 1))
+    w.u[:] = rng.uniform(-0.02, 0.02, w.u.shape) * p["c0"]
+    w.rho[:] *= 1 + rng.uniform(-1e-3, 1e-3, w.n)
+    return w, L
+
+
+def field_err(a, b):
+    a = np.asarray(a).reshape(len(a), -1)
+    b = np.asarray(b).reshape(len(b), -1)
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+@pytest.mark.parametrize("dim,shape,axis", [(2, (24, 14), 0), (3, (10, 12, 10), 1)])
+def test_periodic_box_equals_middle_of_replicated_box(dim, shape, axis):
+    w, L = periodic_patch(dim, shape, axis)
+    p = w.params
+    per = oracle.evaluate(p, w.x, w.u, w.rho, w.phase, w.wall, renorm=True)
+    # three copies side by side in an ordinary box
+    shift = np.zeros(dim)
+    shift[axis] = L
+    xr = np.concatenate([w.x - shift, w.x, w.x + shift])
+    rep = lambda a: np.concatenate([a, a, a])
+    q = dict(p, periodic=0, box_lo=list(p["box_lo"]), box_hi=list(p["box_hi"]))
+    q["box_lo"][axis] = -L - 4 * p["h"]
+    q["box_hi"][axis] = 2 * L + 4 * p["h"]
+    q["cell_size"] = 2.0 * p["h"]
+    ref = oracle.evaluate(q, xr, rep(w.u), rep(w.rho), rep(w.phase), rep(w.wall), renorm=True)
+    mid = slice(w.n, 2 * w.n)
+    # pairs across the boundary exist
+    s, lst = oracle.neighbours(p, w.x, "brute")
+    i = np.repeat(np.arange(w.n), np.diff(s))
+    assert (np.abs(w.x[i, axis] - w.x[lst, axis]) > 0.5 * L).sum() > 10
+    for k in ("rho", "P", "drho", "a", "gradC", "T"):
+        e = field_err(per[k], ref[k][mid])
+        assert e < 1e-11, (k, e)
+    assert np.abs(per["gradC"]).max() > 0  # the drop interface is present
+
+
+@pytest.mark.parametrize("dim,shape,axis", [(2, (24, 14), 0), (3, (10, 12, 10), 1)])
+def test_periodic_translation_invariance(dim, shape, axis):
+    w, L = periodic_patch(dim, shape, axis, seed=9)
+    p = w.params
+    a = oracle.evaluate(p, w.x, w.u, w.rho, w.phase, w.wall, renorm=True)
+    x2 = w.x.copy()
+    x2[:, axis] = np.mod(x2[:, axis] + 0.37 * L, L)
+    b = oracle.evaluate(p, x2, w.u, w.rho, w.phase, w.wall, renorm=True)
+    for k in ("rho", "drho", "a", "T"):
+        assert field_err(b[k], a[k]) < 1e-11, k
+
+
+@pytest.mark.parametrize("dim,shape,axis", [(2, (24, 14), 0), (3, (10, 12, 10), 1)])
+def test_periodic_neighbours_brute_vs_cells(dim, shape, axis):
+    w, L = periodic_patch(dim, shape, axis, seed=11)
+    sb, lb = oracle.neighbours(w.params, w.x, "brute")
+    sc, lc = oracle.neighbours(w.params, w.x, "cells")
+    assert np.array_equal(sb, sc) and np.array_equal(lb, lc)
+    # every particle strictly inside the patch has the same count with and
+    # without the boundary, whichever side it sits on
+    interior = np.all([(w.x[:, k] > w.params["box_lo"][k] + 6 * w.params["h"]) &
+                       (w.x[:, k] < w.params["box_hi"][k] - 6 * w.params["h"])
+                       for k in range(dim) if k != axis], axis=0)
+    cnt = np.diff(sb)[interior]
+    assert cnt.min() >= (8 if dim == 2 else 40)
+
+
+def test_periodic_cells_too_few_is_an_error():
+    w, L = periodic_patch(2, (24, 14), 0)
+    p = dict(w.params, cell_size=L / 2.0)  # 2 cells across the period
+    with pytest.raises(RuntimeError):
+        oracle.neighbours(p, w.x, "cells")
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_full_periodic_lattice_is_at_rest(dim):
+    """Every particle of a perfect lattice periodic on all axes sees the same
+    neighbourhood: the pressure gradient cancels and the state is steady."""
+    shape = (12, 12) if dim == 2 else (8, 8, 8)
+    w = WL.drop_tank(dim, shape, wall_layers=0, seed=1, jitter_dx=0.0, drop_d_dx=0.0)
+    p = w.params
+    p["g"] = [0.0, 0.0, 0.0]
+    dx = p["dx"]
+    L = [s * dx for s in shape]
+    p["cell_size"] = min(L) / int(min(L) // (2 * p["h"]))
+    for k in range(dim):
+        p["box_lo"][k], p["box_hi"][k] = 0.0, L[k]
+    p["periodic"] = (1 << dim) - 1
+    rho = np.full(w.n, 1010.0)
+    u = np.zeros_like(w.u)
+    r = oracle.evaluate(p, w.x, u, rho, w.phase, w.wall, renorm=True)
+    P = oracle.eos(p, 0, 1010.0)
+    scale = P / 1010.0 ** 2 * 1000 * dx ** dim / p["h"] ** (dim + 1)   # one pair term's size
+    assert np.abs(r["a"]).max() < 1e-11 * scale
+    assert np.abs(r["drho"]).max() == 0.0
+    assert np.abs(r["rho"] / 1010.0 - 1).max() < 1e-14
+    # a step keeps it in place
+    x1, u1, r1 = oracle.run(p, w.x, u, rho, w.phase, w.wall, 1e-6, 3)
+    assert np.abs(x1 - w.x).max() < 1e-12 * dx
+
+
+def test_periodic_step_wraps_positions():
+    w, L = periodic_patch(2, (24, 14), 0, seed=13)
+    p = w.params
+    u = np.zeros_like(w.u)
+    u[:, 0] = 0.3 * p["c0"]           # uniform drift along the periodic axis
+    dt = 0.25 * p["h"] / p["c0"]
+    x1, u1, _ = oracle.run(p, w.x, u, w.rho, w.phase, w.wall, dt, 12)
+    assert x1[:, 0].min() >= 0.0 and x1[:, 0].max() < L
+    # every particle moved by about the drift (the forces are small), some of
+    # them across the boundary
+    drift = 12 * dt * 0.3 * p["c0"]
+    moved = np.mod(x1[:, 0] - w.x[:, 0], L)
+    assert np.abs(moved / drift - 1).max() < 0.05
+    assert (x1[:, 0] < w.x[:, 0]).sum() > 0
+
+
+# --------------------------------------------------------------------------
+# Piston wavemaker
+
+STROKE = 0.4572          # 18 inches
+FREQ = 0.75              # Hz
+
+
+def paper_stroke():
+    """The wave-maker signal of the flume experiment as one component."""
+    return dict(axis=0, amp=[STROKE / 2], omega=[2 * math.pi * FREQ], phase=[-math.pi / 2],
+                t_end=1 / (2 * FREQ))
+
+
+def test_piston_stroke_matches_the_papers_formula():
+    m = paper_stroke()
+    for t, cm in [(0.0, 0.0), (1 / 3, 22.86), (2 / 3, 45.72)]:
+        assert abs(oracle.piston_disp(m, t) * 100 - cm) < 1e-12
+    for t in np.linspace(0.0, 2 / 3, 17):
+        formula = STROKE / 2 - STROKE / 2 * math.cos(2 * math.pi * FREQ * t)
+        assert abs(oracle.piston_disp(m, t) - formula) < 1e-15
+    # holds its end position afterwards, at rest
+    assert oracle.piston_disp(m, 1.5) == oracle.piston_disp(m, 2 / 3)
+    assert oracle.piston_vel(m, 1.5) == 0.0
+    # velocity is the derivative of the displacement
+    for t in np.linspace(0.05, 0.6, 12):
+        e = 1e-6
+        fd = (oracle.piston_disp(m, t + e) - oracle.piston_disp(m, t - e)) / (2 * e)
+        assert abs(fd - oracle.piston_vel(m, t)) < 1e-7
+
+
+def piston_tank(seed=21):
+    """2-D closed tank whose left wall layers form the piston."""
+    w = WL.drop_tank(2, (40, 24), drop_d_dx=8, seed=seed, perturb=False)
+    piston = (w.wall == 1) & (w.x[:, 0] < 0.0)
+    wall = w.wall.copy()
+    wall[piston] = 2
+    return w, wall, piston
+
+
+def test_piston_particles_follow_the_prescribed_motion():
+    w, wall, piston = piston_tank()
+    p = w.params
+    dt = WL.stable_dt(p)
+    # a fast stroke, so the piston moves visibly in a few steps
+    m = dict(axis=0, amp=[2 * p["dx"]], omega=[2 * math.pi / (40 * dt)], phase=[-math.pi / 2],
+             t_end=20 * dt)
+    n = 12
+    x, u, rho = oracle.run(p, w.x, w.u, w.rho, w.phase, wall, dt, n, piston=m, t0=0.0)
+    t = 0.0
+    for _ in range(n):
+        t += dt
+    X, U = oracle.piston_disp(m, t), oracle.piston_vel(m, t)
+    assert X > 0.5 * p["dx"]
+    assert np.abs(x[piston, 0] - (w.x[piston, 0] + X)).max() < 1e-15 * 10
+    assert np.array_equal(x[piston, 1], w.x[piston, 1])
+    assert np.abs(u[piston, 0] - U).max() < 1e-15 and np.all(u[piston, 1] == 0)
+    # the fixed walls stayed; the fluid next to the piston was pushed along +x
+    fixed = wall == 1
+    assert np.array_equal(x[fixed], w.x[fixed])
+    fl = wall == 0
+    near = fl & (w.x[:, 0] < 4 * p["dx"])
+    assert u[near, 0].mean() > 0
+    # the piston's density integrates like a wall's
+    assert not np.array_equal(rho[piston], w.rho[piston])
+
+
+def test_piston_at_rest_is_a_wall():
+    w, wall, piston = piston_tank(seed=22)
+    p = w.params
+    dt = WL.stable_dt(p)
+    m0 = dict(axis=0, amp=[0.0], omega=[1.0], phase=[0.0], t_end=1.0)
+    a = oracle.run(p, w.x, w.u, w.rho, w.phase, wall, dt, 5, piston=m0)
+    b = oracle.run(p, w.x, w.u, w.rho, w.phase, w.wall, dt, 5)
+    for ra, rb in zip(a, b):
+        assert np.array_equal(ra, rb)
