@@ -79,7 +79,12 @@ typedef struct sph_params {
     int32_t rebuild_every; /* 0: the cell and neighbour lists are rebuilt when a particle
                               may move farther than skin from where it was at the last
                               build; k > 0: rebuilt every k steps */
-    int32_t reserved;      /* must be 0 */
+    int32_t periodic;      /* bit a set: axis a is periodic with period box_hi[a] - box_lo[a]
+                              (the cross-tank boundary of the flume runs, Sec. "Laboratory
+                              experiment & numerical setup").  The period must hold a whole
+                              number of super-cells, at least three: cell_size when
+                              cell_size >= 2h + 2 skin, else 2 cell_size.  Positions are read
+                              back wrapped into the box.  Not allowed in a batch. */
     double h;              /* smoothing length; the Wendland C2 kernel has support 2h */
     double c0;             /* reference speed of sound C_s0 (Eq. beta) */
     double gamma;          /* exponent of Eq. state; must be 7 (the paper's value) */
@@ -104,7 +109,9 @@ typedef struct sph_sim *sph_handle;
  *   x, u   : n*dim doubles, row-major (particle-major), positions and velocities
  *   rho    : n doubles, densities
  *   phase  : n bytes, 0 = water, 1 = oil
- *   wall   : n bytes, 1 = dynamic boundary particle (must be phase 0), else 0
+ *   wall   : n bytes, 0 = fluid, 1 = dynamic boundary particle, 2 = piston
+ *            particle (a boundary particle moved by sph_set_piston); boundary
+ *            and piston particles must be phase 0
  *   stream : a cudaStream_t, or NULL for the default stream
  * Every position must lie inside [box_lo, box_hi].  On success *out holds the
  * handle; on failure *out is NULL and nothing is leaked. */
@@ -129,6 +136,45 @@ int sph_create(const sph_params *params, int64_t n, const double *x, const doubl
 int sph_create_batch(int k, const sph_params *params, const int64_t *counts, const double *x,
                      const double *u, const double *rho, const uint8_t *phase, const uint8_t *wall,
                      void *stream, sph_handle *out);
+
+/* As sph_create, with x, u, rho, phase and wall in device memory (e.g. torch
+ * tensors); they are copied, so the caller keeps them.  Waits for `stream`. */
+int sph_create_dev(const sph_params *params, int64_t n, const double *x_dev, const double *u_dev,
+                   const double *rho_dev, const uint8_t *phase_dev, const uint8_t *wall_dev, void *stream,
+                   sph_handle *out);
+
+/* Prescribed motion of the piston particles (wall == 2), the piston-type wave
+ * maker of Sec. "Laboratory experiment & numerical setup": they move rigidly
+ * along `axis` with displacement, for t <= t_end,
+ *   X(t) = sum_{c < ncomp} amp[c] (sin(omega[c] t + phase[c]) - sin(phase[c]))
+ * and velocity X'(t); after t_end they rest at X(t_end) (t_end may be
+ * infinite).  The paper's stroke x(t) = S/2 - S/2 cos(2 pi f t), 0 <= t <=
+ * 1/(2f), is ncomp = 1, amp = S/2, omega = 2 pi f, phase = -pi/2, t_end =
+ * 1/(2f).  A step from time t puts them at X(t + dt/2) - X(t) from where they
+ * are, velocity X'(t + dt/2), for the second stage, and at X(t + dt) - X(t),
+ * velocity X'(t + dt), at its end; their density integrates like a fixed
+ * boundary particle's.  The state's velocity of a piston particle should be
+ * X'(t) along the axis at the current time.  ncomp = 0 stops the motion
+ * (pistons then stay where they are).  Single-instance handles only; at most
+ * 8 components.  The time is the handle's clock (sph_get_time). */
+int sph_set_piston(sph_handle h, int axis, int ncomp, const double *amp, const double *omega, const double *phase,
+                   double t_end);
+
+/* The handle's clock: 0 at creation, advanced by dt by every step (by
+ * repeated addition).  Reading waits for the stream. */
+int sph_get_time(sph_handle h, double *t);
+int sph_set_time(sph_handle h, double t);
+
+/* A time step for the current state: the smallest over instances q of
+ *   min(0.25 h / c0, 0.125 h^2 / nu_max, 0.25 sqrt(rho0_min h^3 / (2 pi alpha_s)),
+ *       0.25 sqrt(h / |a|_max)) / dt_scale[q],
+ * nu_max = max over phases of mu / rho0, rho0_min the smaller reference
+ * density, |a|_max the largest acceleration of a fluid particle in the last
+ * rates evaluation (that term is left out before the first one; the tension
+ * term when alpha_s = 0).  The paper fixes only c0 >= 10 u_max (Sec. II-A);
+ * the four bounds are the usual acoustic, viscous, capillary and body-force
+ * limits of weakly compressible SPH.  Waits for the stream. */
+int sph_suggest_dt(sph_handle h, double *dt);
 
 /* Per-instance step sizes: instance q advances by dt * scales[q] whenever the
  * handle advances by dt (each scale in (0, 1]).  Default 1. */

@@ -264,6 +264,30 @@ def diagnostics(p: dict, x, u, phase, wall):
                 centroid=out[6:6 + d].copy(), sphericity=out[9], u_max=out[10], n_oil=int(out[11]))
 
 
+def suggest_dt(p: dict, a=None, wall=None) -> float:
+    """Time-step advice for one instance: the smallest of the acoustic bound
+    0.25 h / c0, the viscous bound 0.125 h^2 / max(mu / rho0), the capillary
+    bound 0.25 sqrt(min(rho0) h^3 / (2 pi alpha_s)) (alpha_s > 0) and the
+    body-force bound 0.25 sqrt(h / max |a|) over the fluid particles of `a`
+    (when given).  Parity unpinned as a rule: the paper fixes only
+    c0 >= 10 u_max (Sec. II-A); the tests check that the advised step is
+    stable where a few times larger is not."""
+    h = p["h"]
+    d = 0.25 * h / p["c0"]
+    nu = max(p["mu"][0] / p["rho0"][0], p["mu"][1] / p["rho0"][1])
+    if nu > 0:
+        d = min(d, 0.125 * h * h / nu)
+    if p["alpha_s"] > 0:
+        d = min(d, 0.25 * np.sqrt(min(p["rho0"]) * h ** 3 / (2 * np.pi * p["alpha_s"])))
+    if a is not None:
+        a = np.asarray(a)
+        fl = np.ones(len(a), bool) if wall is None else np.asarray(wall) == 0
+        amax = np.linalg.norm(a[fl], axis=1).max() if fl.any() else 0.0
+        if amax > 0:
+            d = min(d, 0.25 * np.sqrt(h / amax))
+    return float(d)
+
+
 def set_threads(k: int) -> None:
     lib().or_set_num_threads(int(k))
 

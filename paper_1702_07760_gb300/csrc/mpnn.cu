@@ -92,6 +92,7 @@ struct Surrogate {
     int dim = 0, n = 0, npad = 0;
     Layout L;
     float k_ref = 1.f, t_jump = 0.f, sd_edge_u = 1.f, sd_edge_rho = 1.f;
+    double t_jump64 = 0.0;       // the jump's time span (the device clock advances by it)
     std::vector<float> norm;     // mu_in, sd_in, mu_out, sd_out
     float *norm_d = nullptr;
     float *theta = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
@@ -1166,6 +1167,7 @@ int sph_surrogate_init(sph_handle h, const double *weights, int64_t nweights, co
     if (!h || !weights || !norm) return set_error(SPH_EINVAL, "NULL argument");
     const SimView v = sim_view(h);
     if (v.ninst != 1) return set_error(SPH_EINVAL, "the surrogate runs on single-instance handles");
+    if (v.npiston > 0) return set_error(SPH_EINVAL, "the surrogate does not move piston particles");
     const Layout L = make_layout(v.dim);
     if (nweights != L.total) return set_error(SPH_EINVAL, "weights: wrong number of parameters for this dim");
     if (nnorm != 2 * L.nin + 2 * L.nout + 4) return set_error(SPH_EINVAL, "norm: wrong length for this dim");
@@ -1196,6 +1198,7 @@ int sph_surrogate_init(sph_handle h, const double *weights, int64_t nweights, co
     }
     S->k_ref = (float)norm[o];
     S->t_jump = (float)norm[o + 1];
+    S->t_jump64 = norm[o + 1];
     S->sd_edge_u = (float)norm[o + 2];
     S->sd_edge_rho = (float)norm[o + 3];
     S->norm.assign(norm, norm + o);
@@ -1254,7 +1257,7 @@ int sph_surrogate_advance(sph_handle h, int k_steps)
     if (!S) return set_error(SPH_EINVAL, "no surrogate on this handle");
     if (k_steps < 1) return set_error(SPH_EINVAL, "k_steps must be >= 1");
     const SimView v0 = sim_view(h);
-    if (v0.n == 0) return sim_moved(h, k_steps);
+    if (v0.n == 0) return sim_moved(h, k_steps, S->t_jump64);
     int rc0 = sph_eval_rates(h);
     if (rc0) return rc0;
     const SimView v = sim_view(h);
@@ -1263,7 +1266,7 @@ int sph_surrogate_advance(sph_handle h, int k_steps)
     if (v.dim == 2) k_apply<2><<<nb(v.n), 256, 0, v.stream>>>(v.d, S->norm_d, S->t_jump, S->Y);
     else k_apply<3><<<nb(v.n), 256, 0, v.stream>>>(v.d, S->norm_d, S->t_jump, S->Y);
     CUR(cudaGetLastError());
-    return sim_moved(h, k_steps);
+    return sim_moved(h, k_steps, S->t_jump64);
 }
 
 int sph_surrogate_train_step(sph_handle h, const double *x1, const double *u1, const double *rho1, double lr,
@@ -1374,7 +1377,7 @@ int sph_surrogate_run(sph_handle h, double dt, int k_steps, int64_t n_macro, int
             const int crc = sim_centroid(h, cs);
             if (crc && !state_error(crc)) return crc;
             if ((rc = sim_load_device(h, S->sx, S->su, S->sr))) return rc;
-            if ((rc = sim_moved(h, -k_steps))) return rc;
+            if ((rc = sim_moved(h, -k_steps, -S->t_jump64))) return rc;
             if ((rc = sph_run(h, dt, k_steps, 1))) return rc;
             if ((rc = sim_centroid(h, cp))) return rc;
             double e2 = 0.0;
@@ -1395,7 +1398,7 @@ int sph_surrogate_run(sph_handle h, double dt, int k_steps, int64_t n_macro, int
                 // the jump broke the state: back to the last verified state, plain steps from there
                 const int64_t redo = (mstep + 1 - mv) * k_steps;
                 if ((rc = sim_load_device(h, S->vx, S->vu, S->vr))) return rc;
-                if ((rc = sim_moved(h, -redo))) return rc;
+                if ((rc = sim_moved(h, -redo, -(double)(mstep + 1 - mv) * S->t_jump64))) return rc;
                 if ((rc = sph_run(h, dt, redo, 1))) return rc;
                 ++rejected;
                 fallback = true;

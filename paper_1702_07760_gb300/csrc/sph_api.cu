@@ -103,6 +103,13 @@ struct sph_sim {
     unsigned *rebuild = nullptr;
     long long *dstep = nullptr;
     long long *dbuilds = nullptr;
+    double *clock = nullptr;              // device time, see Dev::clock
+    Motion *motion = nullptr;             // device copy of the piston motion
+    int64_t npiston = 0;                  // particles with wall == 2
+    bool moving = false;                  // a piston motion is set
+    bool evaluated = false;               // acc holds a rates evaluation
+    unsigned *amax = nullptr;             // per instance, max |a|^2 (FP32 bits) for sph_suggest_dt
+    std::vector<sph_params> inst_params;  // each instance's parameters as given
     GridBarrier *bar = nullptr;
     unsigned long long *pair_tot = nullptr;
     double last_dt = 0.0;
@@ -338,9 +345,12 @@ namespace {
 template <int DIM>
 __global__ void k_load_state(Dev d, Grid g, Phys ph, const double *x, const double *u, const double *rho,
                              double check_dt);
-__global__ void k_add_step(long long *step, long long k)
+__global__ void k_add_step(long long *step, long long k, double *clock, double elapsed)
 {
-    if (threadIdx.x == 0 && blockIdx.x == 0) *step += k;
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        *step += k;
+        clock[1] += elapsed;
+    }
 }
 }  // namespace
 
@@ -395,6 +405,17 @@ void sph_sim::enqueue_load(const double *x, const double *u, const double *rho, 
 
 namespace {
 
+// Largest |a|^2 over the fluid particles of each instance, from the last
+// rates evaluation (non-negative FP32 values order like their bit patterns).
+__global__ void k_amax(Dev d, unsigned *amax)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= d.n || (d.tag[k] & 2)) return;
+    const float4 a = d.acc[k];
+    const float a2 = a.x * a.x + a.y * a.y + a.z * a.z;
+    if (a2 > 0.f) atomicMax(amax + d.iid[k], __float_as_uint(a2));
+}
+
 __global__ void k_iota(int *p, int n)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -411,7 +432,7 @@ int validate(const sph_params *P)
     if (P->max_neighbours < 0 || P->max_neighbours > 4096)
         return fail(SPH_EINVAL, "max_neighbours must be in [0, 4096]");
     if (P->rebuild_every < 0) return fail(SPH_EINVAL, "rebuild_every must be >= 0");
-    if (P->reserved != 0) return fail(SPH_EINVAL, "reserved must be 0");
+    if (P->periodic & ~((1 << P->dim) - 1)) return fail(SPH_EINVAL, "periodic may only set the bits of the dim axes");
     if (!(P->h > 0) || !std::isfinite(P->h)) return fail(SPH_EINVAL, "h must be positive");
     if (!(P->c0 > 0) || !std::isfinite(P->c0)) return fail(SPH_EINVAL, "c0 must be positive");
     if (P->gamma != 7.0) return fail(SPH_EINVAL, "gamma must be 7 (the exponent of the paper's equation of state)");
@@ -437,6 +458,7 @@ int validate(const sph_params *P)
 bool same_shared(const sph_params &a, const sph_params &b)
 {
     bool same = a.dim == b.dim && a.visc_form == b.visc_form && a.renorm_every == b.renorm_every &&
+                a.periodic == b.periodic &&
                 a.max_neighbours == b.max_neighbours && a.rebuild_every == b.rebuild_every && a.h == b.h &&
                 a.gamma == b.gamma && a.delta == b.delta && a.cell_size == b.cell_size && a.skin == b.skin;
     for (int c = 0; c < 3; ++c) same = same && a.g[c] == b.g[c];
@@ -551,6 +573,7 @@ int create_sim(const sph_params *params, int k, const int64_t *counts, const dou
     }
     if (n > 0 && (!x || !u || !rho || !phase || !wall)) return fail(SPH_EINVAL, "an input array is NULL");
     const sph_params &P0 = params[0];
+    if (k > 1 && P0.periodic) return fail(SPH_EINVAL, "periodic axes are not supported in a batch");
     const int dim = P0.dim;
     // host-side checks of the particle data
     {
@@ -558,7 +581,7 @@ int create_sim(const sph_params *params, int k, const int64_t *counts, const dou
         for (int q = 0; q < k; ++q)
             for (int64_t c = 0; c < counts[q]; ++c, ++i) {
                 if (phase[i] > 1) return fail(SPH_EINVAL, "phase must be 0 (water) or 1 (oil)");
-                if (wall[i] > 1) return fail(SPH_EINVAL, "wall must be 0 or 1");
+                if (wall[i] > 2) return fail(SPH_EINVAL, "wall must be 0 (fluid), 1 (boundary) or 2 (piston)");
                 if (wall[i] && phase[i] != 0) return fail(SPH_EINVAL, "wall particles must be water (phase 0)");
                 if (!(rho[i] > 0) || !std::isfinite(rho[i])) return fail(SPH_EINVAL, "rho must be positive and finite");
                 for (int a = 0; a < dim; ++a) {
@@ -572,6 +595,7 @@ int create_sim(const sph_params *params, int k, const int64_t *counts, const dou
     }
     sph_sim *s = new sph_sim();
     s->P = P0;
+    s->inst_params.assign(params, params + k);
     s->dim = dim;
     s->n = (int)n;
     s->ninst = k;
@@ -618,8 +642,20 @@ int create_sim(const sph_params *params, int k, const int64_t *counts, const dou
     // grid
     int dims[3] = {1, 1, 1};
     int64_t ncell = 1;
+    const int fcell = P0.cell_size >= RL ? 1 : 2;   // cells per super-cell edge
     for (int c = 0; c < dim; ++c) {
-        const double m = std::floor((box_hi[c] - box_lo[c]) / P0.cell_size) + 1.0;
+        const double len = box_hi[c] - box_lo[c];
+        double m = std::floor(len / P0.cell_size) + 1.0;
+        if ((P0.periodic >> c) & 1) {
+            // the cells must tile the period, in whole super-cells, at least
+            // three of them (so a stencil never meets a cell twice)
+            m = std::nearbyint(len / P0.cell_size);
+            if (std::fabs(m * P0.cell_size - len) > 1e-9 * len || (int64_t)m % fcell != 0 || m < 3 * fcell) {
+                delete s;
+                return fail(SPH_EINVAL, "a periodic axis must span a whole number of super-cells (cell_size, or "
+                                        "2 cell_size when cell_size < 2h + 2 skin), at least three");
+            }
+        }
         if (m > 1e9) {
             delete s;
             return fail(SPH_EINVAL, "cell grid too large");
@@ -642,6 +678,7 @@ int create_sim(const sph_params *params, int k, const int64_t *counts, const dou
     s->grid.Ed = s->grid.f * P0.cell_size;
     s->grid.Es = (float)s->grid.Ed;
     for (int c = 0; c < 3; ++c) s->grid.lo[c] = box_lo[c];
+    for (int c = 0; c < 3; ++c) s->grid.per[c] = c < dim ? (P0.periodic >> c) & 1 : 0;
     // constants shared by all instances
     const double pi = 3.14159265358979323846;
     const double h = P0.h;
@@ -723,6 +760,9 @@ int create_sim(const sph_params *params, int k, const int64_t *counts, const dou
         err |= s->alloc(&s->diag_grav, 4);
         err |= s->alloc(&s->read_buf, N * 9 + 16);
         err |= s->alloc(&s->read_ibuf, N);
+        err |= s->alloc(&s->clock, 2);
+        err |= s->alloc(&s->amax, (size_t)k);
+        err |= s->alloc(&s->motion, 1);
     }
     if (err) return cleanup(SPH_ENOMEM);
     s->sort.ncell = (int)ncell;
@@ -737,6 +777,12 @@ int create_sim(const sph_params *params, int k, const int64_t *counts, const dou
     a0.rebuild = a1.rebuild = s->rebuild;
     a0.builds = a1.builds = s->dbuilds;
     a0.inst = a1.inst = s->dinst;
+    a0.clock = a1.clock = s->clock;
+    a0.motion = a1.motion = s->motion;
+    for (int c = 0; c < 3; ++c) {
+        a0.period[c] = a1.period[c] = s->grid.per[c] ? box_hi[c] - box_lo[c] : 0.0;
+        a0.plo[c] = a1.plo[c] = box_lo[c];
+    }
 
     cudaStream_t st = s->stream;
     auto cuda_fail = [&](cudaError_t e) { return cleanup(fail(SPH_ECUDA, cudaGetErrorString(e))); };
@@ -745,6 +791,8 @@ int create_sim(const sph_params *params, int k, const int64_t *counts, const dou
     if ((e = cudaMemsetAsync(s->dstep, 0, sizeof(long long), st)) != cudaSuccess) return cuda_fail(e);
     if ((e = cudaMemsetAsync(s->dbuilds, 0, sizeof(long long), st)) != cudaSuccess) return cuda_fail(e);
     if ((e = cudaMemsetAsync(s->bar, 0, sizeof(GridBarrier), st)) != cudaSuccess) return cuda_fail(e);
+    if ((e = cudaMemsetAsync(s->clock, 0, 2 * sizeof(double), st)) != cudaSuccess) return cuda_fail(e);
+    if ((e = cudaMemsetAsync(s->motion, 0, sizeof(Motion), st)) != cudaSuccess) return cuda_fail(e);
     if ((e = cudaMemcpyAsync(s->dinst, s->hinst.data(), sizeof(Inst) * k, cudaMemcpyHostToDevice, st)) != cudaSuccess)
         return cuda_fail(e);
     std::vector<long long> fl(s->first.begin(), s->first.end());
@@ -761,7 +809,9 @@ int create_sim(const sph_params *params, int k, const int64_t *counts, const dou
         int64_t i = 0;
         for (int q = 0; q < k; ++q)
             for (int64_t c = 0; c < counts[q]; ++c, ++i) {
-                tag[i] = (uint8_t)(phase[i] | (wall[i] << 1));
+                // bit 0 oil, bit 1 boundary (fixed or piston), bit 2 piston
+                tag[i] = (uint8_t)(phase[i] | (wall[i] ? 2 : 0) | (wall[i] == 2 ? 4 : 0));
+                s->npiston += wall[i] == 2;
                 iid[i] = (uint16_t)q;
             }
         if ((e = cudaMemcpyAsync(a0.tag, tag.data(), (size_t)n, cudaMemcpyHostToDevice, st)) != cudaSuccess)
@@ -796,6 +846,7 @@ SimView sim_view(sph_sim *s)
     v.ninst = s->ninst;
     v.h = s->P.h;
     v.rho0 = s->P.rho0;
+    v.npiston = s->npiston;
     return v;
 }
 
@@ -806,10 +857,10 @@ void sim_build_lists(sph_sim *s)
 
 int sim_check(sph_sim *s) { return s->check_flags(); }
 
-int sim_moved(sph_sim *s, int64_t steps)
+int sim_moved(sph_sim *s, int64_t steps, double elapsed)
 {
     if (s->n > 0) {
-        k_add_step<<<1, 32, 0, s->stream>>>(s->dstep, (long long)steps);
+        k_add_step<<<1, 32, 0, s->stream>>>(s->dstep, (long long)steps, s->clock, elapsed);
         CU(cudaGetLastError());
         CU(cudaMemsetAsync(s->rebuild, 0xff, sizeof(unsigned), s->stream));
     }
@@ -906,6 +957,109 @@ int sph_set_state(sph_handle s, const double *x, const double *u, const double *
     return SPH_OK;
 }
 
+int sph_create_dev(const sph_params *params, int64_t n, const double *x_dev, const double *u_dev,
+                   const double *rho_dev, const uint8_t *phase_dev, const uint8_t *wall_dev, void *stream,
+                   sph_handle *out)
+{
+    if (out) *out = nullptr;
+    if (n < 0 || n > ((int64_t)1 << 26)) return fail(SPH_EINVAL, "n must be in [0, 2^26]");
+    if (!params) return fail(SPH_EINVAL, "params is NULL");
+    if (params->dim != 2 && params->dim != 3) return fail(SPH_EINVAL, "dim must be 2 or 3");
+    if (n > 0 && (!x_dev || !u_dev || !rho_dev || !phase_dev || !wall_dev))
+        return fail(SPH_EINVAL, "an input array is NULL");
+    // the creation path validates and packs on the host: stage the arrays there
+    const size_t nv = (size_t)n * params->dim;
+    std::vector<double> x(nv), u(nv), rho((size_t)n);
+    std::vector<uint8_t> phase((size_t)n), wall((size_t)n);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n > 0) {
+        CU(cudaMemcpyAsync(x.data(), x_dev, nv * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CU(cudaMemcpyAsync(u.data(), u_dev, nv * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CU(cudaMemcpyAsync(rho.data(), rho_dev, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CU(cudaMemcpyAsync(phase.data(), phase_dev, (size_t)n, cudaMemcpyDeviceToHost, st));
+        CU(cudaMemcpyAsync(wall.data(), wall_dev, (size_t)n, cudaMemcpyDeviceToHost, st));
+        CU(cudaStreamSynchronize(st));
+    }
+    return create_sim(params, 1, &n, x.data(), u.data(), rho.data(), phase.data(), wall.data(), stream, out);
+}
+
+int sph_set_piston(sph_handle s, int axis, int ncomp, const double *amp, const double *omega, const double *phase,
+                   double t_end)
+{
+    if (!s) return fail(SPH_EINVAL, "handle is NULL");
+    if (s->ninst != 1) return fail(SPH_EINVAL, "a piston motion needs a single-instance handle");
+    if (axis < 0 || axis >= s->dim) return fail(SPH_EINVAL, "axis must be in [0, dim)");
+    if (ncomp < 0 || ncomp > MOTION_MAX) return fail(SPH_EINVAL, "ncomp must be in [0, 8]");
+    if (ncomp > 0 && (!amp || !omega || !phase)) return fail(SPH_EINVAL, "a component array is NULL");
+    if (std::isnan(t_end) || t_end < 0) return fail(SPH_EINVAL, "t_end must be >= 0 (may be infinite)");
+    Motion m{};
+    m.axis = axis;
+    m.ncomp = ncomp;
+    m.t_end = t_end;
+    for (int c = 0; c < ncomp; ++c) {
+        if (!std::isfinite(amp[c]) || !std::isfinite(omega[c]) || !std::isfinite(phase[c]))
+            return fail(SPH_EINVAL, "the motion components must be finite");
+        m.amp[c] = amp[c];
+        m.omega[c] = omega[c];
+        m.phase[c] = phase[c];
+    }
+    CU(cudaMemcpyAsync(s->motion, &m, sizeof(Motion), cudaMemcpyHostToDevice, s->stream));
+    CU(cudaStreamSynchronize(s->stream));
+    s->moving = ncomp > 0;
+    return SPH_OK;
+}
+
+int sph_get_time(sph_handle s, double *t)
+{
+    if (!s || !t) return fail(SPH_EINVAL, "NULL argument");
+    double c[2];
+    CU(cudaMemcpyAsync(c, s->clock, sizeof(c), cudaMemcpyDeviceToHost, s->stream));
+    CU(cudaStreamSynchronize(s->stream));
+    *t = c[0] + c[1];
+    return s->check_flags();
+}
+
+int sph_set_time(sph_handle s, double t)
+{
+    if (!s) return fail(SPH_EINVAL, "handle is NULL");
+    if (!std::isfinite(t)) return fail(SPH_EINVAL, "t must be finite");
+    const double c[2] = {t, 0.0};
+    CU(cudaMemcpyAsync(s->clock, c, sizeof(c), cudaMemcpyHostToDevice, s->stream));
+    CU(cudaStreamSynchronize(s->stream));
+    return SPH_OK;
+}
+
+int sph_suggest_dt(sph_handle s, double *dt)
+{
+    if (!s || !dt) return fail(SPH_EINVAL, "NULL argument");
+    const int k = s->ninst;
+    std::vector<float> amax((size_t)k, 0.f);
+    if (s->evaluated && s->n > 0) {
+        CU(cudaMemsetAsync(s->amax, 0, sizeof(unsigned) * k, s->stream));
+        k_amax<<<s->blocks(s->n), 256, 0, s->stream>>>(s->D(), s->amax);
+        CU(cudaGetLastError());
+        CU(cudaMemcpyAsync(amax.data(), s->amax, sizeof(float) * k, cudaMemcpyDeviceToHost, s->stream));
+        CU(cudaStreamSynchronize(s->stream));
+        int rc = s->check_flags();
+        if (rc) return rc;
+    }
+    const double h = s->P.h, pi = 3.14159265358979323846;
+    double best = INFINITY;
+    for (int q = 0; q < k; ++q) {
+        const sph_params &P = s->inst_params[q];
+        double d = 0.25 * h / P.c0;                                           // acoustic (CFL)
+        const double nu = std::max(P.mu[0] / P.rho0[0], P.mu[1] / P.rho0[1]);
+        if (nu > 0) d = std::min(d, 0.125 * h * h / nu);                      // viscous diffusion
+        if (P.alpha_s > 0)                                                    // capillary waves
+            d = std::min(d, 0.25 * std::sqrt(std::min(P.rho0[0], P.rho0[1]) * h * h * h / (2.0 * pi * P.alpha_s)));
+        const double a = std::sqrt((double)amax[q]);
+        if (a > 0) d = std::min(d, 0.25 * std::sqrt(h / a));                  // body force
+        best = std::min(best, d / s->hinst[q].dt_scale);
+    }
+    *dt = best;
+    return SPH_OK;
+}
+
 int sph_set_dt_scales(sph_handle s, const double *scales)
 {
     if (!s || !scales) return fail(SPH_EINVAL, "NULL argument");
@@ -934,6 +1088,7 @@ int sph_eval_rates(sph_handle s)
     if (s->n == 0) return SPH_OK;
     s->enqueue_build_cells(true);
     s->enqueue_eval(0, s->D().drho, 0.0);
+    s->evaluated = true;
     CU(cudaGetLastError());
     return SPH_OK;
 }
@@ -948,6 +1103,7 @@ int sph_step(sph_handle s, double dt)
         s->last_dt = dt;
         s->enqueue_step(dt);
         CU(cudaGetLastError());
+        s->evaluated = true;
     }
     s->step += 1;
     return SPH_OK;
@@ -990,6 +1146,7 @@ int sph_run(sph_handle s, double dt, int64_t nsteps, int graph)
             s->step += 1;
         }
     }
+    if (nsteps > 0) s->evaluated = true;
     return s->check_flags();
 }
 
@@ -1031,6 +1188,7 @@ int sph_run_persistent(sph_handle s, double dt, int64_t nsteps, int graph)
         if (rc) return rc;
     }
     s->step += nsteps;
+    s->evaluated = true;
     return s->check_flags();
 }
 
@@ -1076,6 +1234,8 @@ int sph_autotune(sph_handle s, double dt, int trial_steps, int *best_block, int 
     if (!rc) rc = sph_read(s, SPH_FIELD_RHO, rho.data(), (int64_t)(rho.size() * 8));
     if (rc) return rc;
     long long dstep = 0, dbuilds = 0;
+    double clock[2] = {0, 0};
+    CU(cudaMemcpyAsync(clock, s->clock, sizeof(clock), cudaMemcpyDeviceToHost, s->stream));
     CU(cudaMemcpyAsync(&dstep, s->dstep, sizeof(dstep), cudaMemcpyDeviceToHost, s->stream));
     CU(cudaMemcpyAsync(&dbuilds, s->dbuilds, sizeof(dbuilds), cudaMemcpyDeviceToHost, s->stream));
     CU(cudaStreamSynchronize(s->stream));
@@ -1140,6 +1300,8 @@ int sph_autotune(sph_handle s, double dt, int trial_steps, int *best_block, int 
     // the state and counters as they were before the trials (the next step
     // rebuilds the lists)
     int rc2 = sph_set_state(s, x.data(), u.data(), rho.data());
+    CU(cudaMemcpyAsync(s->clock, clock, sizeof(clock), cudaMemcpyHostToDevice, s->stream));
+    CU(cudaMemsetAsync(s->rebuild, 0xff, sizeof(unsigned), s->stream));
     CU(cudaMemcpyAsync(s->dstep, &dstep, sizeof(dstep), cudaMemcpyHostToDevice, s->stream));
     CU(cudaMemcpyAsync(s->dbuilds, &dbuilds, sizeof(dbuilds), cudaMemcpyHostToDevice, s->stream));
     CU(cudaStreamSynchronize(s->stream));

@@ -19,6 +19,7 @@ struct SimView {
     int dim, n, ninst;
     double h;
     const double *rho0;    // per-phase reference density of instance 0 (host)
+    int64_t npiston;       // particles with a prescribed (piston) motion
 };
 
 int set_error(int code, const std::string &msg);
@@ -27,9 +28,10 @@ SimView sim_view(sph_sim *s);
 void sim_build_lists(sph_sim *s);
 // Waits for the stream and reports device error flags.
 int sim_check(sph_sim *s);
-// Adds `steps` to the host and device step counters and marks the lists for
-// a rebuild (the state moved by more than the skin allows).
-int sim_moved(sph_sim *s, int64_t steps);
+// Adds `steps` to the host and device step counters and `elapsed` to the
+// device clock, and marks the lists for a rebuild (the state moved by more
+// than the skin allows).
+int sim_moved(sph_sim *s, int64_t steps, double elapsed);
 // Original-order state <-> device arrays (x, u: n * dim; rho: n).
 int sim_snapshot_device(sph_sim *s, double *x, double *u, double *rho);
 int sim_load_device(sph_sim *s, const double *x, const double *u, const double *rho);

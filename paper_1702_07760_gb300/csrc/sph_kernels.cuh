@@ -87,6 +87,7 @@ struct Grid {
     double csd;         // cell edge (FP64): hashing
     double Ed;          // super-cell edge (FP64): offsets
     double lo[3];       // box lower corner
+    int per[3];         // 1: the axis is periodic (its cell count is a multiple of f, >= 3f)
 };
 
 // All device arrays of one simulation (sorted order unless noted).
@@ -126,7 +127,51 @@ struct Dev {
     unsigned *rebuild;  // 1 word: nonzero when the cell and neighbour lists must be rebuilt
     long long *step;    // device step counter (drives the renormalisation schedule)
     long long *builds;  // number of list builds performed
+    // time and boundary motion
+    double *clock;      // 2 words: [0] time t_n of the current step, [1] the step size
+                        //   of the last completed step, added into [0] when the next starts
+    const struct Motion *motion;  // prescribed piston motion (particles with tag bit 2)
+    // periodic axes: period (0 when the axis is not periodic) and lower bound
+    double period[3];
+    double plo[3];
 };
+
+// Prescribed displacement X(t) of the piston particles along `axis`: for
+// t <= t_end, X(t) = sum_c amp_c (sin(omega_c t + phase_c) - sin(phase_c)) and
+// X'(t) = sum_c amp_c omega_c cos(omega_c t + phase_c); afterwards the piston
+// rests at X(t_end).  (The flume runs drive a piston-type wave maker with a
+// cosine stroke: one component with phase -pi/2.)
+constexpr int MOTION_MAX = 8;
+struct Motion {
+    int axis;
+    int ncomp;
+    double t_end;
+    double amp[MOTION_MAX];
+    double omega[MOTION_MAX];
+    double phase[MOTION_MAX];
+};
+
+__device__ __forceinline__ double motion_disp(const Motion &m, double t)
+{
+    const double te = t < m.t_end ? t : m.t_end;
+    double X = 0.0;
+    for (int c = 0; c < m.ncomp; ++c) X += m.amp[c] * (sin(m.omega[c] * te + m.phase[c]) - sin(m.phase[c]));
+    return X;
+}
+
+__device__ __forceinline__ double motion_vel(const Motion &m, double t)
+{
+    if (t > m.t_end) return 0.0;
+    double U = 0.0;
+    for (int c = 0; c < m.ncomp; ++c) U += m.amp[c] * m.omega[c] * cos(m.omega[c] * t + m.phase[c]);
+    return U;
+}
+
+// Coordinate wrapped into [lo, lo + L) along a periodic axis (L > 0).
+__device__ __forceinline__ double wrap_coord(double v, double lo, double L)
+{
+    return L > 0.0 ? v - L * floor((v - lo) / L) : v;
+}
 
 // Scratch of the cell-list build.
 struct Sort {
@@ -215,7 +260,10 @@ __device__ __forceinline__ float axis_gap(float p, int d, float e)
 // Scans the particles of the cells within +/-f of cell c that a sphere of
 // radius Rp around the particle can reach (pruned per row), and calls
 // fn(j, oj, rx, ry, rz, r2, code) for those with |r_ij|^2 < R2 (j == i
-// included); code is the shift part of a neighbour-list entry.
+// included); code is the shift part of a neighbour-list entry.  Along a
+// periodic axis the stencil wraps around the box: cells are visited at their
+// unwrapped position (so the super-cell difference S_i - S_j, and with it
+// r_ij, is that of the nearest image) and read at the wrapped one.
 template <int DIM, bool NC, class F>
 __device__ __forceinline__ void for_each_candidate(const Grid &g, typename RO<NC, int>::type cstart,
                                                    typename RO<NC, float4>::type pos, int c, const float4 &oi,
@@ -233,40 +281,57 @@ __device__ __forceinline__ void for_each_candidate(const Grid &g, typename RO<NC
     const float py = oi.y + (hw == 1 ? 0.5f * e : ((cy & 1) ? 0.f : e));
     const float pz = DIM == 3 ? oi.z + (hw == 1 ? 0.5f * e : ((cz & 1) ? 0.f : e)) : 0.f;
     const float Rp2 = Rp * Rp;
-    const int z0 = DIM == 3 ? max(cz - hw, 0) : 0, z1 = DIM == 3 ? min(cz + hw, g.nz - 1) : 0;
-    const int y0 = max(cy - hw, 0), y1 = min(cy + hw, g.ny - 1);
+    int z0 = 0, z1 = 0;
+    if (DIM == 3) {
+        z0 = g.per[2] ? cz - hw : max(cz - hw, 0);
+        z1 = g.per[2] ? cz + hw : min(cz + hw, g.nz - 1);
+    }
+    const int y0 = g.per[1] ? cy - hw : max(cy - hw, 0), y1 = g.per[1] ? cy + hw : min(cy + hw, g.ny - 1);
     for (int z = z0; z <= z1; ++z) {
         const float gz = DIM == 3 ? axis_gap(pz, z - cz, e) : 0.f;
         if (gz >= Rp) continue;
         const int dSz = DIM == 3 ? Sz - (z >> fm) : 0;
+        const int zw = DIM == 3 ? (z < 0 ? z + g.nz : (z >= g.nz ? z - g.nz : z)) : 0;
         const float sz = (float)dSz * E;
         for (int y = y0; y <= y1; ++y) {
             const float gy = axis_gap(py, y - cy, e);
             const float rem = Rp2 - gy * gy - gz * gz;
             if (rem <= 0.f) continue;
             const int dSy = Sy - (y >> fm);
+            const int yw = y < 0 ? y + g.ny : (y >= g.ny ? y - g.ny : y);
             const float sy = (float)dSy * E;
             const float xr = sqrtf(rem);
-            const int xlo = max(max(cx + (int)floorf((px - xr) / e), cx - hw), 0);
-            const int xhi = min(min(cx + (int)floorf((px + xr) / e), cx + hw), g.nx - 1);
+            int xlo = max(cx + (int)floorf((px - xr) / e), cx - hw);
+            int xhi = min(cx + (int)floorf((px + xr) / e), cx + hw);
+            if (!g.per[0]) {
+                xlo = max(xlo, 0);
+                xhi = min(xhi, g.nx - 1);
+            }
             if (xlo > xhi) continue;
-            // the cells xlo..xhi of a row are contiguous in the sorted order
-            const int row = (z * g.ny + y) * g.nx;
-            const int jb = ld<NC>(cstart + row + xlo), je = ld<NC>(cstart + row + xhi + 1);
-            // super-cell Sx covers cells [Sx*f, Sx*f + f)
-            const int b1 = ld<NC>(cstart + row + min(max(Sx * hw, xlo), xhi + 1));
-            const int b2 = ld<NC>(cstart + row + min(max(Sx * hw + hw, xlo), xhi + 1));
+            const int row = (zw * g.ny + yw) * g.nx;
             const unsigned cyz = ((unsigned)(dSy + 1) << (NBR_IDX_BITS + 2)) |
                                  ((unsigned)(dSz + 1) << (NBR_IDX_BITS + 4));
+            // the unwrapped range xlo..xhi in pieces of one image each (one
+            // piece unless x is periodic); the cells of a piece are
+            // contiguous in the sorted order
+            for (int img = -1; img <= 1; ++img) {
+                const int off = img * g.nx;
+                const int a = max(xlo, off), b = min(xhi, off + g.nx - 1);
+                if (a > b) continue;
+                const int jb = ld<NC>(cstart + row + a - off), je = ld<NC>(cstart + row + b - off + 1);
+                // super-cell Sx covers the unwrapped cells [Sx*f, Sx*f + f)
+                const int b1 = ld<NC>(cstart + row + min(max(Sx * hw, a), b + 1) - off);
+                const int b2 = ld<NC>(cstart + row + min(max(Sx * hw + hw, a), b + 1) - off);
 #pragma unroll 4
-            for (int j = jb; j < je; ++j) {
-                const float4 oj = ld<NC>(pos + j);
-                // super-cell of j along x: Sx - 1, Sx or Sx + 1
-                const float sx = j < b1 ? E : (j < b2 ? 0.f : -E);
-                const unsigned ex = j < b1 ? 2u : (j < b2 ? 1u : 0u);
-                float rx, ry, rz;
-                const float r2 = pair_vec<DIM>(oi, oj, sx, sy, sz, rx, ry, rz);
-                if (r2 < R2) fn(j, oj, rx, ry, rz, r2, cyz | (ex << NBR_IDX_BITS));
+                for (int j = jb; j < je; ++j) {
+                    const float4 oj = ld<NC>(pos + j);
+                    // super-cell of j along x: Sx - 1, Sx or Sx + 1
+                    const float sx = j < b1 ? E : (j < b2 ? 0.f : -E);
+                    const unsigned ex = j < b1 ? 2u : (j < b2 ? 1u : 0u);
+                    float rx, ry, rz;
+                    const float r2 = pair_vec<DIM>(oi, oj, sx, sy, sz, rx, ry, rz);
+                    if (r2 < R2) fn(j, oj, rx, ry, rz, r2, cyz | (ex << NBR_IDX_BITS));
+                }
             }
         }
     }
@@ -326,8 +391,14 @@ __device__ __forceinline__ void hash_one(const Dev &d, const Grid &g, const Sort
     unsigned bad = 0;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
-        const double xa = d.x[(size_t)a * d.n + k];
-        const double sc = floor((xa - g.lo[a]) / g.csd);
+        double xa = d.x[(size_t)a * d.n + k];
+        if (g.per[a] && isfinite(xa)) {
+            // a periodic coordinate is wrapped into the box at every build
+            xa = wrap_coord(xa, g.lo[a], d.period[a]);
+            d.x[(size_t)a * d.n + k] = xa;
+        }
+        double sc = floor((xa - g.lo[a]) / g.csd);
+        if (g.per[a] && sc >= (double)dims[a]) sc = dims[a] - 1;  // rounding at the upper side
         if (isnan(xa)) {
             bad |= FLAG_NONFINITE;
         } else if (!(sc >= 0.0 && sc < (double)dims[a])) {
@@ -548,6 +619,17 @@ __device__ __forceinline__ void predict_particle(const Dev &d, const Grid &g, co
         us[c] = (tg & 2) ? u : u + 0.5 * dt * af[c];
         finite = finite && isfinite(us[c]) && isfinite(xs[c]);
     }
+    if (tg & 4) {
+        // piston: at X(t + dt/2) with velocity X'(t + dt/2) along its axis
+        const Motion &m = *d.motion;
+        const double t = d.clock[0];
+        const double dX = motion_disp(m, t + 0.5 * dt) - motion_disp(m, t), U = motion_vel(m, t + 0.5 * dt);
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) {
+            if (c == m.axis) xs[c] += dX;
+            us[c] = c == m.axis ? U : 0.0;
+        }
+    }
     float4 p = cell_offset<DIM>(g, d.cell[k], xs);
     // the neighbour list stays complete while no particle is farther than the
     // skin from where it was at the build
@@ -594,10 +676,23 @@ __device__ __forceinline__ void correct_particle(const Dev &d, const Grid &g, co
         }
         finite = finite && isfinite(xa[c]) && isfinite(ua[c]);
     }
+    if (tg & 4) {
+        // piston: at X(t + dt) with velocity X'(t + dt) along its axis
+        const Motion &m = *d.motion;
+        const double t = d.clock[0];
+        const double dX = motion_disp(m, t + dt) - motion_disp(m, t), U = motion_vel(m, t + dt);
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) {
+            if (c == m.axis) xa[c] += dX;
+            ua[c] = c == m.axis ? U : 0.0;
+            d.x[(size_t)c * d.n + k] = xa[c];
+            d.u[(size_t)c * d.n + k] = ua[c];
+        }
+    }
     if (!finite) atomicOr(d.flags, FLAG_NONFINITE);
     // stage-1 records of the next step (replaced by the gather if it rebuilds)
     stage_records<DIM>(d, g, I, k, d.cell[k], xa, ua, dr, tg & 1);
-    if (ph.rebuild_every == 0 && !(tg & 2)) {
+    if (ph.rebuild_every == 0 && (!(tg & 2) || (tg & 4))) {
         // next step's stage positions: x^{n+1} and x^{n+1} + dt/2 u^{n+1};
         // rebuild before either can be farther than the skin from the build
         const float4 p = d.pos[k], p0 = d.pos0[k];
@@ -823,7 +918,12 @@ __device__ __forceinline__ void sweep_b_one(const Dev &d, const Grid &g, const P
     }
     d.acc[i] = out;
     if (STAGE == 1) predict_particle<DIM>(d, g, ph, I, i, out, dt * I.dt_scale);
-    if (STAGE == 2) correct_particle<DIM>(d, g, ph, I, i, out, dt * I.dt_scale);
+    if (STAGE == 2) {
+        correct_particle<DIM>(d, g, ph, I, i, out, dt * I.dt_scale);
+        // the clock advances when the next step starts (every particle of
+        // this launch reads clock[0] as t_n)
+        if (i == 0) d.clock[1] = dt;
+    }
 }
 
 __device__ __forceinline__ int renorm_now(const Dev &d, const Phys &ph, int stage1)
@@ -919,7 +1019,11 @@ static __global__ void __launch_bounds__(256) k_sweep_a(Dev d, Grid g, Phys ph, 
     if (i >= d.n) return;
     const int renorm = renorm_now(d, ph, stage1);
     // the lists built for this step are in place; the corrector decides the next build
-    if (stage1 && i == 0) *d.rebuild = 0u;
+    if (stage1 && i == 0) {
+        *d.rebuild = 0u;
+        d.clock[0] += d.clock[1];
+        d.clock[1] = 0.0;
+    }
     sweep_a_one<DIM, true>(d, g, ph, drho_in, renorm, vel_s, i);
 }
 
@@ -1087,7 +1191,11 @@ __device__ __forceinline__ void persistent_steps(Dev d, Dev scratch, Grid g, Phy
         }
         const int renorm = renorm_now(d, ph, 1);
         if (grid_sync(bar, d.flags) & FLAG_ERRORS) return;  // all blocks read rebuild and step
-        if (tid == 0) *d.rebuild = 0u;
+        if (tid == 0) {
+            *d.rebuild = 0u;
+            d.clock[0] += d.clock[1];
+            d.clock[1] = 0.0;
+        }
         for_each_particle(bar, n, dyn, [&](int i) { sweep_a_one<DIM, false>(d, g, ph, d.drho, renorm, d.velp, i); });
         if (grid_sync(bar, d.flags) & FLAG_ERRORS) return;
         for_each_particle(bar, n, dyn, [&](int i) { sweep_b_one<DIM, 1, false>(d, g, ph, dt, i); });
@@ -1168,7 +1276,10 @@ static __global__ void __launch_bounds__(256) k_unpermute(Dev d, int kind, doubl
     const Inst &I = d.inst[d.iid[k]];
     switch (kind) {
     case RK_X:
-        for (int c = 0; c < DIM; ++c) out[(size_t)p * DIM + c] = d.x[(size_t)c * n + k] - I.offset[c];
+        // periodic coordinates in the box (between builds they may lie up to
+        // the skin beyond it)
+        for (int c = 0; c < DIM; ++c)
+            out[(size_t)p * DIM + c] = wrap_coord(d.x[(size_t)c * n + k], d.plo[c], d.period[c]) - I.offset[c];
         break;
     case RK_U:
         for (int c = 0; c < DIM; ++c) out[(size_t)p * DIM + c] = d.u[(size_t)c * n + k];

@@ -197,6 +197,7 @@ int sph_cell_sort_noalloc(const sph_params *P, int64_t n, const double *x_dev, i
 {
     if (!P) return na_fail(SPH_EINVAL, "params is NULL");
     if (P->dim != 2 && P->dim != 3) return na_fail(SPH_EINVAL, "dim must be 2 or 3");
+    if (P->periodic != 0) return na_fail(SPH_EINVAL, "the allocation-free sort has no periodic axes");
     if (n < 0 || n > NA_MAX_PARTICLES)
         return na_fail(SPH_EINVAL, "n exceeds the allocation-free limit of 2^20 particles");
     if (!(P->cell_size > 0) || !std::isfinite(P->cell_size)) return na_fail(SPH_EINVAL, "cell_size must be positive");

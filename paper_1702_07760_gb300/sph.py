@@ -29,7 +29,8 @@ EXPORTS = ["sph_create", "sph_set_state", "sph_build_cells", "sph_eval_rates", "
            "sph_set_launch_shape", "sph_get_launch_shape", "sph_autotune", "sph_diag_instances",
            "sph_num_instances", "sph_test_stall_barrier", "sph_mm_bf16", "sph_snapshot", "sph_load_snapshot",
            "sph_surrogate_init", "sph_surrogate_get_weights", "sph_surrogate_predict", "sph_surrogate_advance",
-           "sph_surrogate_train_step", "sph_surrogate_run"]
+           "sph_surrogate_train_step", "sph_surrogate_run", "sph_create_dev", "sph_set_piston", "sph_get_time",
+           "sph_set_time", "sph_suggest_dt"]
 
 
 class SphError(RuntimeError):
@@ -41,7 +42,7 @@ class SphError(RuntimeError):
 class SphParams(C.Structure):
     _fields_ = [
         ("dim", C.c_int32), ("visc_form", C.c_int32), ("renorm_every", C.c_int32),
-        ("max_neighbours", C.c_int32), ("rebuild_every", C.c_int32), ("reserved", C.c_int32), ("h", C.c_double), ("c0", C.c_double), ("gamma", C.c_double),
+        ("max_neighbours", C.c_int32), ("rebuild_every", C.c_int32), ("periodic", C.c_int32), ("h", C.c_double), ("c0", C.c_double), ("gamma", C.c_double),
         ("delta", C.c_double), ("alpha_s", C.c_double), ("cell_size", C.c_double), ("skin", C.c_double),
         ("g", C.c_double * 3), ("rho0", C.c_double * 2), ("mu", C.c_double * 2),
         ("mass", C.c_double * 2), ("box_lo", C.c_double * 3), ("box_hi", C.c_double * 3),
@@ -103,6 +104,11 @@ def load(path: str = LIB_PATH):
     L.sph_surrogate_run.argtypes = [H, C.c_double, C.c_int, C.c_int64, C.c_int, C.c_double, C.c_double,
                                     P(C.c_int64), P(C.c_int64), dp]
     L.sph_num_instances.restype = C.c_int64
+    L.sph_create_dev.argtypes = [P(SphParams), C.c_int64, vp, vp, vp, vp, vp, vp, P(H)]
+    L.sph_set_piston.argtypes = [H, C.c_int, C.c_int, dp, dp, dp, C.c_double]
+    L.sph_get_time.argtypes = [H, dp]
+    L.sph_set_time.argtypes = [H, C.c_double]
+    L.sph_suggest_dt.argtypes = [H, dp]
     _lib = L
     return L
 
@@ -114,7 +120,7 @@ def make_params(p: dict) -> SphParams:
     s.renorm_every = int(p.get("renorm_every", 1))
     s.max_neighbours = int(p.get("max_neighbours", 0))
     s.rebuild_every = int(p.get("rebuild_every", 0))
-    s.reserved = 0
+    s.periodic = int(p.get("periodic", 0))
     s.h, s.c0, s.gamma = p["h"], p["c0"], p.get("gamma", 7.0)
     s.delta, s.alpha_s, s.cell_size, s.skin = p["delta"], p["alpha_s"], p["cell_size"], p["skin"]
     for k in range(3):
@@ -173,6 +179,47 @@ class Simulation:
     @classmethod
     def from_workload(cls, w, stream=None):
         return cls(w.params, w.x, w.u, w.rho, w.phase, w.wall, stream)
+
+    @classmethod
+    def from_device(cls, params: dict, n: int, x_ptr: int, u_ptr: int, rho_ptr: int, phase_ptr: int,
+                    wall_ptr: int, stream: int | None = None) -> "Simulation":
+        """sph_create_dev: the initial state from device arrays given by
+        address (x, u: n*dim float64; rho: n float64; phase, wall: n uint8)."""
+        self = cls.__new__(cls)
+        self.params = dict(params)
+        self.dim = int(params["dim"])
+        self.n = int(n)
+        self._p = make_params(params)
+        self._h = None
+        h = C.c_void_p()
+        _check(load().sph_create_dev(C.byref(self._p), self.n, C.c_void_p(x_ptr), C.c_void_p(u_ptr),
+                                     C.c_void_p(rho_ptr), C.c_void_p(phase_ptr), C.c_void_p(wall_ptr),
+                                     C.c_void_p(stream or 0), C.byref(h)))
+        self._h = h
+        return self
+
+    def set_piston(self, axis: int, amp, omega, phase, t_end: float):
+        """Prescribed motion of the particles with wall == 2 (sph_set_piston)."""
+        a = np.ascontiguousarray(amp, np.float64)
+        w = np.ascontiguousarray(omega, np.float64)
+        f = np.ascontiguousarray(phase, np.float64)
+        if not (len(a) == len(w) == len(f)):
+            raise ValueError("amp, omega and phase must have equal lengths")
+        _check(load().sph_set_piston(self._h, int(axis), len(a), _dp(a), _dp(w), _dp(f), float(t_end)))
+
+    @property
+    def time(self) -> float:
+        t = C.c_double()
+        _check(load().sph_get_time(self._h, C.byref(t)))
+        return t.value
+
+    def set_time(self, t: float):
+        _check(load().sph_set_time(self._h, float(t)))
+
+    def suggest_dt(self) -> float:
+        dt = C.c_double()
+        _check(load().sph_suggest_dt(self._h, C.byref(dt)))
+        return dt.value
 
     @classmethod
     def batch(cls, workloads, stream: int | None = None) -> "Simulation":

@@ -210,3 +210,144 @@ def batch_dt(workloads, cfl: float = 0.25):
     dts = np.array([stable_dt(w.params, cfl) for w in workloads])
     dt = float(dts.max())
     return dt, dts / dt
+
+
+# --------------------------------------------------------------------------
+# Breaking-wave flume (the set-up of Sec. "Laboratory experiment & numerical
+# setup", re-sized as a synthetic case): a long tank, periodic across its
+# width, a piston-type wave maker at one end, a 1:10 plane slope at the
+# other, and a thin oil slick on the surface where the wave group focuses.
+# The piston signal comes from linear wave theory (dispersion relation and
+# the piston transfer function), which is input design, not SPH.
+
+def dispersion_k(omega: float, depth: float, g: float = 9.81) -> float:
+    """Wavenumber k of linear water waves, omega^2 = g k tanh(k d) (Newton)."""
+    k = max(omega * omega / g, omega / np.sqrt(g * depth))
+    for _ in range(100):
+        t = np.tanh(k * depth)
+        f = g * k * t - omega * omega
+        df = g * t + g * k * depth * (1.0 - t * t)
+        step = f / df
+        k -= step
+        if abs(step) < 1e-15 * k:
+            break
+    return float(k)
+
+
+def piston_transfer(k: float, depth: float) -> float:
+    """Wave height over piston stroke, H/S = 2 (cosh 2kd - 1) / (sinh 2kd + 2kd),
+    for a piston wave maker in linear theory."""
+    a = 2.0 * k * depth
+    return float(2.0 * (np.cosh(a) - 1.0) / (np.sinh(a) + a))
+
+
+def group_velocity(omega: float, k: float, depth: float) -> float:
+    a = 2.0 * k * depth
+    return float(0.5 * omega / k * (1.0 + a / np.sinh(a)))
+
+
+def focused_group(seed: int, depth: float, x_focus: float, ncomp: int = 5, f_lo: float = 0.8,
+                  f_hi: float = 1.4, crest: float | None = None, g: float = 9.81) -> dict:
+    """Piston motion that focuses `ncomp` linear components (frequencies evenly
+    spaced in [f_lo, f_hi] Hz, seeded amplitudes summing to `crest`, default
+    0.16 depth) at distance x_focus from the piston at time t_f.
+
+    Component c of the surface elevation is a_c cos(k_c (x - x_f) - w_c (t - t_f));
+    the piston makes it with displacement (a_c / F_c) sin(w_c t + phi_c),
+    phi_c = k_c x_f - w_c t_f, F_c the transfer function.  t_f is the first time
+    after the slowest group arrives at which the piston's initial velocity is
+    zero, so the motion starts from rest."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    crest = 0.16 * depth if crest is None else crest
+    f = np.linspace(f_lo, f_hi, ncomp)
+    w = rng.uniform(0.5, 1.5, ncomp)
+    a = crest * w / w.sum()
+    omega = 2.0 * np.pi * f
+    k = np.array([dispersion_k(o, depth, g) for o in omega])
+    F = np.array([piston_transfer(kk, depth) for kk in k])
+    amp = a / F
+    u0 = lambda tf: float(np.sum(amp * omega * np.cos(k * x_focus - omega * tf)))
+    t0 = x_focus / min(group_velocity(o, kk, depth) for o, kk in zip(omega, k))
+    ts = t0 + np.arange(0.0, 4.0, 1e-3)
+    vals = np.array([u0(t) for t in ts])
+    idx = np.flatnonzero(np.sign(vals[:-1]) != np.sign(vals[1:]))[0]
+    lo_t, hi_t = ts[idx], ts[idx + 1]
+    for _ in range(80):
+        mid = 0.5 * (lo_t + hi_t)
+        if np.sign(u0(mid)) == np.sign(u0(lo_t)):
+            lo_t = mid
+        else:
+            hi_t = mid
+    t_f = 0.5 * (lo_t + hi_t)
+    return dict(axis=0, amp=amp.tolist(), omega=omega.tolist(), phase=(k * x_focus - omega * t_f).tolist(),
+                t_end=float("inf"), t_focus=t_f, elevation=a.tolist(), k=k.tolist())
+
+
+def wave_tank(dx: float = 5e-3, length: float = 4.0, width: float = 0.3, depth: float = 0.5,
+              height: float = 0.6, slope: float = 0.1, slope_toe: float = 3.0, x_focus: float = 2.5,
+              oil_len: float = 0.3, wall_layers: int = 3, seed: int = 2000, jitter_dx: float = 1e-3,
+              name: str | None = None, **param_kw) -> Workload:
+    """3-D flume (x along the tank, y across, z up), periodic in y.
+
+    Fluid: the lattice of length x width x depth (cells of dx) above the slope.
+    Boundary particles (wall_layers each): the bed below z = 0, the end wall
+    beyond x = length, and a plane slope z = slope (x - slope_toe) for
+    x > slope_toe (the layers just under it).  The wall layers before x = 0
+    are the piston (wall = 2), driven by ``meta["piston"]`` (a focused group,
+    see ``focused_group``); the piston and end wall rise to `height`.  Oil:
+    the top particle layer over |x - x_focus| < oil_len / 2."""
+    nx, ny = int(round(length / dx)), int(round(width / dx))
+    nz, nzw = int(round(depth / dx)), int(round(height / dx))
+    L = wall_layers
+    rng = np.random.Generator(np.random.PCG64(seed))
+    p = fluid_params(3, dx, depth, **param_kw)
+    # cells tile the period in whole super-cells (two cells of at least h + skin)
+    RL = 2.0 * p["h"] + 2.0 * p["skin"]
+    msc = int(np.floor(width / RL))
+    p["cell_size"] = width / msc / 2.0
+    p["periodic"] = 2
+    i, j, k = np.meshgrid(np.arange(-L, nx + L), np.arange(ny), np.arange(-L, nzw), indexing="ij")
+    i, j, k = i.ravel(order="F"), j.ravel(order="F"), k.ravel(order="F")
+    xc, zc = (i + 0.5) * dx, (k + 0.5) * dx
+    zs = np.where(xc > slope_toe, slope * (xc - slope_toe), -np.inf)
+    bed = k < 0
+    piston = (i < 0) & (k >= 0)
+    endw = (i >= nx) & (k >= 0)
+    inside = (i >= 0) & (i < nx) & (k >= 0)
+    slope_layer = inside & (zc < zs) & (zc >= zs - L * dx)
+    fluid = inside & (k < nz) & (zc >= zs)
+    keep = bed | piston | endw | slope_layer | fluid
+    i, j, k, xc, zc = i[keep], j[keep], k[keep], xc[keep], zc[keep]
+    wall = np.zeros(len(i), np.uint8)
+    wall[(bed | endw | slope_layer)[keep]] = 1
+    wall[piston[keep]] = 2
+    fl = fluid[keep]
+    x = np.stack([xc, (j + 0.5) * dx, zc], axis=1)
+    nfl = int(fl.sum())
+    x[fl] += rng.uniform(-jitter_dx, jitter_dx, size=(nfl, 3)) * dx
+    # stay inside the period after the jitter
+    x[:, 1] = np.mod(x[:, 1], width)
+    oil = fl & (k == nz - 1) & (np.abs(xc - x_focus) < 0.5 * oil_len)
+    phase = np.where(oil, OIL, WATER).astype(np.uint8)
+    g = abs(p["g"][2])
+    rho = np.array(p["rho0"])[phase] + p["rho0"][WATER] * g * (depth - x[:, 2]) / p["c0"] ** 2
+    rho = np.where(wall > 0, p["rho0"][WATER] + p["rho0"][WATER] * g * np.maximum(depth - x[:, 2], 0.0)
+                   / p["c0"] ** 2, rho)
+    u = np.zeros_like(x)
+    motion = focused_group(seed + 1, depth, x_focus)
+    reach = 2.0 * float(np.sum(np.abs(motion["amp"])))      # bound on |X(t)|
+    p["box_lo"] = [-L * dx - reach - dx, 0.0, -L * dx]
+    p["box_hi"] = [length + L * dx + dx, width, height + 0.4 * depth]
+    meta = dict(piston=motion, n_fluid=nfl, n_wall=int((wall == 1).sum()), n_piston=int((wall == 2).sum()),
+                n_oil=int(oil.sum()), depth=depth, length=length, width=width, seed=seed)
+    nm = name or f"wave_tank_{nx}x{ny}x{nz}"
+    return Workload(nm, p, np.ascontiguousarray(x), u, rho, phase, wall, meta)
+
+
+def wave_tank_small(seed: int = 2100, **kw) -> Workload:
+    """A scaled flume with the same features (dx = 5 mm, 0.6 x 0.06 x 0.1 m
+    water, about 31 k particles) for parity against the oracle."""
+    args = dict(length=0.6, width=0.06, depth=0.1, height=0.15, slope_toe=0.45, x_focus=0.3, oil_len=0.1,
+                seed=seed, name="wave_tank_small")
+    args.update(kw)
+    return wave_tank(**args)

@@ -98,3 +98,36 @@ def test_batch_validation_without_a_gpu(lib):
     with pytest.raises(sph.SphError) as e:
         sph.Simulation.batch([ws[0], bad])
     assert e.value.code == -1
+
+
+def test_periodic_and_piston_validation_without_a_gpu(lib):
+    """Periodic axes and piston flags are checked before the device is touched."""
+    from paper_1702_07760_gb300 import workloads as WL
+    w = WL.wave_tank_small()
+    p = w.params
+    # a period that is not a whole number of super-cells
+    with pytest.raises(sph.SphError) as e:
+        sph.Simulation(dict(p, cell_size=p["cell_size"] * 1.07), w.x, w.u, w.rho, w.phase, w.wall)
+    assert e.value.code == -1 and "periodic" in str(e.value)
+    # a periodic bit beyond dim
+    with pytest.raises(sph.SphError) as e:
+        sph.Simulation(dict(p, periodic=8), w.x, w.u, w.rho, w.phase, w.wall)
+    assert e.value.code == -1
+    # wall flags other than 0, 1, 2; an oil piston
+    wl = w.wall.copy()
+    wl[0] = 3
+    with pytest.raises(sph.SphError) as e:
+        sph.Simulation(p, w.x, w.u, w.rho, w.phase, wl)
+    assert e.value.code == -1 and "piston" in str(e.value)
+    ph = w.phase.copy()
+    ph[w.wall == 2] = 1
+    with pytest.raises(sph.SphError):
+        sph.Simulation(p, w.x, w.u, w.rho, ph, w.wall)
+    # no periodic axes in a batch
+    ws = WL.drop_batch_2d(k=2, seed=5, d_range=(4.0, 5.0))
+    per = [v.copy() for v in ws]
+    for v in per:
+        v.params = dict(v.params, periodic=1)
+    with pytest.raises(sph.SphError) as e:
+        sph.Simulation.batch(per)
+    assert e.value.code == -1 and "batch" in str(e.value)

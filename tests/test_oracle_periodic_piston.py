@@ -229,3 +229,35 @@ def test_piston_at_rest_is_a_wall():
     b = oracle.run(p, w.x, w.u, w.rho, w.phase, w.wall, dt, 5)
     for ra, rb in zip(a, b):
         assert np.array_equal(ra, rb)
+
+
+# --------------------------------------------------------------------------
+# Time-step advice (a rule, not the paper's: its one constraint is c0 >= 10 u_max)
+
+def test_suggested_dt_is_stable_and_ten_times_it_is_not():
+    w = WL.drop_tank(2, (20, 30), drop_d_dx=8, seed=3, perturb=True)
+    p = w.params
+    r = oracle.evaluate(p, w.x, w.u, w.rho, w.phase, w.wall, renorm=True)
+    dt = oracle.suggest_dt(p, r["a"], w.wall)
+    # the acoustic bound is the active one for these fluids
+    assert dt == 0.25 * p["h"] / p["c0"]
+    x, u, rho = oracle.run(p, w.x, w.u, w.rho, w.phase, w.wall, dt, 80)
+    assert np.abs(u).max() < 0.05 * p["c0"]
+    blown = False
+    try:
+        x, u, rho = oracle.run(p, w.x, w.u, w.rho, w.phase, w.wall, 10 * dt, 9)
+        blown = not np.isfinite(u).all() or np.abs(u).max() > 0.2 * p["c0"]
+    except RuntimeError:
+        blown = True      # particles thrown out of the box
+    assert blown
+
+
+def test_suggested_dt_bounds_order():
+    """Each bound takes over when its own parameter is pushed: a large
+    viscosity, a large tension, a large acceleration."""
+    p = WL.drop_tank(2, (10, 10), drop_d_dx=4).params
+    base = oracle.suggest_dt(p)
+    assert oracle.suggest_dt(dict(p, mu=[1e-3, 1e3])) < base
+    assert oracle.suggest_dt(dict(p, alpha_s=1e4)) < base
+    assert oracle.suggest_dt(p, a=np.array([[1e9, 0.0]]), wall=np.zeros(1, np.uint8)) < base
+    assert oracle.suggest_dt(p, a=np.array([[1e9, 0.0]]), wall=np.ones(1, np.uint8)) == base
