@@ -9,6 +9,14 @@ density, density rate and acceleration; positions after a step within 1e-9 dx
 (the FP64 integration of FP32 rates over one step), after a few steps within
 1e-6 dx.  Positions are compared through the minimum image along a periodic
 axis.
+
+In the flume, still water half a metre deep, the acceleration is the small
+difference between a pressure gradient and gravity, while each pressure pair
+term is of order (P/rho)/h, about 75 g at the bed.  The FP32 sums round at
+the size of those terms, so there the acceleration error is stated relative
+to a_P = max_i (|P_i| / rho_i) / h, the scale of one pressure pair term:
+1e-5 a_P (the drop tanks, 32 mm deep, have a_P of a few g and meet 1e-5 of
+their largest acceleration).
 """
 import math
 
@@ -132,6 +140,11 @@ def test_periodic_steps_match_oracle(sphmod, dim):
     sim.close()
 
 
+def pressure_scale(p, ref):
+    """a_P = max_i |P_i| / rho_i / h from an oracle evaluation."""
+    return float(np.max(np.abs(ref["P"]) / ref["rho"]) / p["h"])
+
+
 def piston_tank(seed):
     w = WL.drop_tank(2, (40, 24), drop_d_dx=8, seed=seed, perturb=True)
     wall = w.wall.copy()
@@ -146,14 +159,15 @@ def test_piston_steps_match_oracle(sphmod, persistent):
     w = piston_tank(seed=70)
     p = w.params
     dt = WL.stable_dt(p)
-    m = dict(axis=0, amp=[2 * p["dx"]], omega=[2 * math.pi / (40 * dt)], phase=[-math.pi / 2],
-             t_end=20 * dt)
-    n = 25
+    # a stroke of one dx at up to 0.05 c0 (WCSPH keeps |u| <= 0.1 c0)
+    om = 0.1 * p["c0"] / p["dx"]
+    m = dict(axis=0, amp=[0.5 * p["dx"]], omega=[om], phase=[-math.pi / 2], t_end=math.pi / om)
+    n = int(math.ceil(m["t_end"] / dt)) + 5
     sim = sphmod.Simulation.from_workload(w)
     sim.set_piston(m["axis"], m["amp"], m["omega"], m["phase"], m["t_end"])
     if persistent:
-        sim.run_persistent(dt, 10)
-        sim.run_persistent(dt, n - 10)
+        sim.run_persistent(dt, 40)
+        sim.run_persistent(dt, n - 40)
     else:
         sim.run(dt, n)
     xr, ur, rr = oracle.run(p, w.x, w.u, w.rho, w.phase, w.wall, dt, n, piston=m)
@@ -164,7 +178,7 @@ def test_piston_steps_match_oracle(sphmod, persistent):
         t += dt
     assert sim.time == t
     X = oracle.piston_disp(m, t)
-    assert X > 1.5 * p["dx"]        # the stroke is complete (rest after t_end)
+    assert abs(X - p["dx"]) < 1e-12  # the stroke is complete (rest after t_end)
     assert np.abs(x[pis] - xr[pis]).max() < 1e-12 * p["dx"]
     assert np.abs(u[pis] - ur[pis]).max() < 1e-12 * p["c0"]
     e_x = np.abs(x - xr).max() / p["dx"]
@@ -182,12 +196,22 @@ def test_flume_small_matches_oracle(sphmod):
     dt = WL.stable_dt(p)
     sim = sphmod.Simulation.from_workload(w)
     sim.set_piston(m["axis"], m["amp"], m["omega"], m["phase"], m["t_end"])
+    # rates at the initial state
+    sim.eval_rates()
+    ref = oracle.evaluate(p, w.x, w.u, w.rho, w.phase, w.wall, renorm=True)
+    aP = pressure_scale(p, ref)
+    fl = w.wall == 0
+    e_rho = np.abs(sim.read("rho_eval") / ref["rho"] - 1).max()
+    e_a = np.abs(sim.read("acc")[fl] - ref["a"][fl]).max() / aP
+    e_T = rel_field(sim.read("tensor"), ref["T"])
+    print(f"\n[flume small n={w.n}, rates] a_P = {aP / 9.81:.1f} g; rho {e_rho:.2e} acc/a_P {e_a:.2e} T {e_T:.2e}")
+    assert e_rho < TOL and e_a < TOL and e_T < 1e-4
     sim.step(dt)
     xr, ur, rr = oracle.run(p, w.x, w.u, w.rho, w.phase, w.wall, dt, 1, piston=m)
     e_x = np.abs(min_image(sim.read("pos") - xr, p)).max() / p["dx"]
-    e_u = rel_field(sim.read("vel") - w.u, ur - w.u)
+    e_u = np.abs(sim.read("vel") - ur).max() / (dt * aP)
     e_r = np.abs(sim.read("rho") / rr - 1).max()
-    print(f"\n[flume small n={w.n}, 1 step] |dx|/dx {e_x:.2e} du {e_u:.2e} rho {e_r:.2e}")
+    print(f"[flume small, 1 step] |dx|/dx {e_x:.2e} du/(dt a_P) {e_u:.2e} rho {e_r:.2e}")
     assert e_x < 1e-9 and e_u < TOL and e_r < TOL
     # moving piston: state from the oracle's step, clock at 0.3 s
     t0 = 0.3
@@ -224,10 +248,12 @@ def test_flume_full_size_step_matches_oracle(sphmod):
     x, u, rho = sim.read("pos"), sim.read("vel"), sim.read("rho")
     sim.close()
     xr, ur, rr = oracle.run(p, w.x, w.u, w.rho, w.phase, w.wall, dt, 1, piston=m)
+    aP = pressure_scale(p, oracle.evaluate(p, w.x, w.u, w.rho, w.phase, w.wall, renorm=True))
     e_x = np.abs(min_image(x - xr, p)).max() / p["dx"]
-    e_u = rel_field(u - w.u, ur - w.u)
+    e_u = np.abs(u - ur).max() / (dt * aP)
     e_r = np.abs(rho / rr - 1).max()
-    print(f"\n[flume full n={w.n}, 1 step] |dx|/dx {e_x:.2e} du {e_u:.2e} rho {e_r:.2e}")
+    print(f"\n[flume full n={w.n}, 1 step] a_P = {aP / 9.81:.1f} g; |dx|/dx {e_x:.2e} du/(dt a_P) {e_u:.2e} "
+          f"rho {e_r:.2e}")
     assert e_x < 1e-9 and e_u < TOL and e_r < TOL
 
 
@@ -246,7 +272,7 @@ def test_time_and_suggested_dt(sphmod):
     sim.set_time(1.25)
     assert sim.time == 1.25
     # a strong body force makes the acceleration bound the active one
-    q = dict(p, g=[0.0, -2.0e4, 0.0])
+    q = dict(p, g=[0.0, -2.0e5, 0.0])
     s2 = sphmod.Simulation(q, w.x, w.u, w.rho, w.phase, w.wall)
     s2.eval_rates()
     ref = oracle.evaluate(q, w.x, w.u, w.rho, w.phase, w.wall, renorm=True)
