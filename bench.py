@@ -60,6 +60,8 @@ def parse():
                     help="steps of the 256-instance batched comparison (0 skips it)")
     ap.add_argument("--surrogate-iters", type=int, default=1000,
                     help="training iterations of the learned k-step surrogate (0 skips it)")
+    ap.add_argument("--flume-steps", type=int, default=200,
+                    help="timed steps of the 4.9 M-particle breaking-wave flume (0 skips it)")
     return ap.parse_args()
 
 
@@ -266,6 +268,37 @@ def run_batched(sph, WL, stream, steps, torch):
         "replay_bit_identical": deterministic,
         "plain_timing": "host clock around 256 sequential 500-step graph runs (each ends in a sync)",
     }
+
+
+def run_flume(sph, WL, stream, steps, torch):
+    """The breaking-wave flume (4.0 x 0.3 x 0.5 m of water at dx = 5 mm,
+    periodic across, piston wave maker driving a focused group, 1:10 slope,
+    oil slick at the focus): graph-replayed steps timed with CUDA events."""
+    w = WL.wave_tank()
+    m = w.meta["piston"]
+    dt = WL.stable_dt(w.params)
+    sim = sph.Simulation.from_workload(w, stream=stream.cuda_stream)
+    sim.set_piston(m["axis"], m["amp"], m["omega"], m["phase"], m["t_end"])
+    sim.run(dt, 5, graph=True)
+    b0 = sim.list_builds
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        a.record(stream)
+        sim.run(dt, steps, graph=True)
+        b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    out = {
+        "workload": "wave_tank_800x60x100: flume 4.0 x 0.3 x 0.6 m, depth 0.5 m, dx 5 mm, periodic in y, "
+                    "piston (5-component focused group, 0.8-1.4 Hz, focus 2.5 m), 1:10 slope, oil slick",
+        "particles": w.n, "fluid_particles": w.meta["n_fluid"], "piston_particles": w.meta["n_piston"],
+        "steps": steps, "dt": dt, "ms_per_step": ms / steps, "value": w.n * steps / (ms / 1e3),
+        "unit": "particle-steps/s", "list_builds_in_timed_steps": sim.list_builds - b0,
+        "time_simulated_s": sim.time, "suggested_dt": sim.suggest_dt(),
+    }
+    sim.close()
+    return out
 
 
 def run_surrogate(sph, WL, stream, iters, torch, macro=25, k=8):
@@ -525,6 +558,9 @@ def run_ours(args, ws, rank, local):
     surrogate = None
     if rank == 0 and ws == 1 and args.surrogate_iters > 0:
         surrogate = run_surrogate(sph, WL, stream, args.surrogate_iters, torch)
+    flume = None
+    if rank == 0 and ws == 1 and args.flume_steps > 0:
+        flume = run_flume(sph, WL, stream, args.flume_steps, torch)
 
     # count reset, hash, 3 scan, scatter, rank, gather, copy-back, list (these return at once on
     # steps without a rebuild), 2 sweep_a, 2 sweep_b (with the predictor / corrector)
@@ -545,6 +581,7 @@ def run_ours(args, ws, rank, local):
         "e2e": e2e,
         "batched": batched,
         "surrogate": surrogate,
+        "flume": flume,
         "gpu_launches": kernels_per_step * args.steps,
         "clocks": clk,
     }
