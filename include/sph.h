@@ -48,6 +48,8 @@ extern "C" {
 #define SPH_EDOMAIN    -6  /* a particle left the box of the cell grid */
 #define SPH_ECAPACITY  -7  /* a particle has more neighbours than max_neighbours */
 #define SPH_ETIMEOUT   -8  /* a grid barrier of the persistent kernel gave up after one second */
+#define SPH_EFALLBACK  -9  /* the judge rejected a surrogate jump; the state holds the plain
+                              method's result (sph_surrogate_advance_judged), not a failure */
 
 /* Viscous term forms (Sec. II-C) */
 #define SPH_VISC_DYNAMIC   0  /* Eq. visc_2: (1/rho_i) sum 2 mu_ij (m_j/rho_j) (r.gradW)/(r^2+delta^2) u_ij */
@@ -75,7 +77,8 @@ typedef struct sph_params {
     int32_t visc_form;     /* SPH_VISC_DYNAMIC or SPH_VISC_KINEMATIC */
     int32_t renorm_every;  /* Eq. ct_dist_3 at stage 1 of steps with step % renorm_every == 0; 0 = never */
     int32_t max_neighbours;/* capacity of the per-particle neighbour list (pairs closer
-                              than 2h + 2 skin); 0 selects 48 in 2-D and 128 in 3-D */
+                              than 2h + 2 skin), rounded up to a multiple of 4; 0 selects
+                              48 in 2-D and 128 in 3-D */
     int32_t rebuild_every; /* 0: the cell and neighbour lists are rebuilt when a particle
                               may move farther than skin from where it was at the last
                               build; k > 0: rebuilt every k steps */

@@ -83,6 +83,15 @@ int sph_surrogate_advance(sph_handle h, int k_steps);
 int sph_surrogate_train_step(sph_handle h, const double *x1_dev, const double *u1_dev, const double *rho1_dev,
                              double lr, int update, double *loss_out, double *grad_out, int64_t ngrad);
 
+/* One judged macro-step: the surrogate jump and k_steps plain steps (of size
+ * dt, graph-replayed) from the same state; the plain result is kept.  *err
+ * (if not NULL) receives |c_jump - c_plain| / d_ref for the oil centroids
+ * (1e30 when the jump left a non-finite value, a particle outside the box or
+ * an over-full neighbour list).  Returns SPH_OK when err <= tol and
+ * SPH_EFALLBACK when the judge rejects the jump (the state is still the
+ * plain result).  Waits for the stream. */
+int sph_surrogate_advance_judged(sph_handle h, double dt, int k_steps, double tol, double d_ref, double *err);
+
 /* n_macro macro-steps of k_steps plain steps each.  A macro-step is one
  * surrogate evaluation, except every judge_every-th (0: never), where both
  * the surrogate and k_steps plain steps (of size dt, graph-replayed) start

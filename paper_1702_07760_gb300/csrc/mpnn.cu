@@ -1338,6 +1338,68 @@ int sph_load_snapshot(sph_handle h, const double *x_dev, const double *u_dev, co
     return sim_load_device(h, x_dev, u_dev, rho_dev);
 }
 
+namespace {
+
+// Errors that mean "the jump produced an unusable state" rather than a
+// failure of the library.
+bool state_error(int rc)
+{
+    return rc == SPH_ENONFINITE || rc == SPH_EDOMAIN || rc == SPH_ECAPACITY || rc == SPH_ECFL;
+}
+
+// Snapshot buffers of the judged run (allocated once per surrogate).
+int judge_buffers(Surrogate &S, const SimView &v)
+{
+    if (S.sx) return SPH_OK;
+    const size_t nd = (size_t)v.n * v.dim;
+    int e = dalloc(S, &S.sx, nd) | dalloc(S, &S.su, nd) | dalloc(S, &S.sr, (size_t)v.n) |
+            dalloc(S, &S.vx, nd) | dalloc(S, &S.vu, nd) | dalloc(S, &S.vr, (size_t)v.n);
+    if (e) return SPH_ENOMEM;
+    CUR(cudaDeviceSynchronize());
+    return SPH_OK;
+}
+
+// One judged macro-step: the surrogate jump and k plain steps from the same
+// state; the plain result is kept.  *err = |c_jump - c_plain| / d_ref for the
+// oil centroids (1e30 when the jump broke the state).
+int judged_jump(sph_handle h, Surrogate &S, const SimView &v, double dt, int k_steps, double d_ref, double *err)
+{
+    int rc;
+    if ((rc = sim_snapshot_device(h, S.sx, S.su, S.sr))) return rc;
+    if ((rc = sph_surrogate_advance(h, k_steps))) return rc;
+    double cs[3] = {0, 0, 0}, cp[3];
+    const int crc = sim_centroid(h, cs);
+    if (crc && !state_error(crc)) return crc;
+    if ((rc = sim_load_device(h, S.sx, S.su, S.sr))) return rc;
+    if ((rc = sim_moved(h, -k_steps, -S.t_jump64))) return rc;
+    if ((rc = sph_run(h, dt, k_steps, 1))) return rc;
+    if ((rc = sim_centroid(h, cp))) return rc;
+    double e2 = 0.0;
+    for (int c = 0; c < v.dim; ++c) e2 += (cs[c] - cp[c]) * (cs[c] - cp[c]);
+    *err = crc ? 1.0e30 : std::sqrt(e2) / d_ref;
+    return SPH_OK;
+}
+
+}  // namespace
+
+int sph_surrogate_advance_judged(sph_handle h, double dt, int k_steps, double tol, double d_ref, double *err)
+{
+    Surrogate *S = get(h);
+    if (!S) return set_error(SPH_EINVAL, "no surrogate on this handle");
+    if (!(dt > 0) || k_steps < 1 || !(tol > 0) || !(d_ref > 0))
+        return set_error(SPH_EINVAL, "bad dt, k_steps, tol or d_ref");
+    const SimView v = sim_view(h);
+    int rc = judge_buffers(*S, v);
+    if (rc) return rc;
+    double e = 0.0;
+    if ((rc = judged_jump(h, *S, v, dt, k_steps, d_ref, &e))) return rc;
+    if (err) *err = e;
+    if ((rc = check_err(*S, v.stream))) return rc;
+    if ((rc = sim_check(h))) return rc;
+    return e > tol ? set_error(SPH_EFALLBACK, "the judge rejected the surrogate jump; the state holds the plain steps")
+                   : SPH_OK;
+}
+
 int sph_surrogate_run(sph_handle h, double dt, int k_steps, int64_t n_macro, int judge_every, double tol,
                       double d_ref, int64_t *n_judged, int64_t *n_rejected, double *max_err)
 {
@@ -1346,21 +1408,11 @@ int sph_surrogate_run(sph_handle h, double dt, int k_steps, int64_t n_macro, int
     if (!(dt > 0) || k_steps < 1 || n_macro < 0 || judge_every < 0 || !(tol > 0) || !(d_ref > 0))
         return set_error(SPH_EINVAL, "bad dt, k_steps, n_macro, judge_every, tol or d_ref");
     const SimView v = sim_view(h);
-    const size_t nd = (size_t)v.n * v.dim;
-    if (!S->sx) {
-        int e = dalloc(*S, &S->sx, nd) | dalloc(*S, &S->su, nd) | dalloc(*S, &S->sr, (size_t)v.n) |
-                dalloc(*S, &S->vx, nd) | dalloc(*S, &S->vu, nd) | dalloc(*S, &S->vr, (size_t)v.n);
-        if (e) return SPH_ENOMEM;
-        CUR(cudaDeviceSynchronize());
-    }
+    if (int e = judge_buffers(*S, v)) return e;
     // a state the plain method produced or accepted, and the macro-step it belongs to
     auto verify = [&](int64_t m, int64_t &mv) {
         mv = m;
         return sim_snapshot_device(h, S->vx, S->vu, S->vr);
-    };
-    // errors that mean "the jump produced an unusable state" rather than a failure of the library
-    auto state_error = [](int rc) {
-        return rc == SPH_ENONFINITE || rc == SPH_EDOMAIN || rc == SPH_ECAPACITY || rc == SPH_ECFL;
     };
     int64_t judged = 0, rejected = 0, mv = 0;
     double worst = 0.0;
@@ -1371,18 +1423,8 @@ int sph_surrogate_run(sph_handle h, double dt, int k_steps, int64_t n_macro, int
         const bool judge = judge_every > 0 && (mstep % judge_every) == 0;
         if (judge) {
             // surrogate jump and plain steps from the same state; the plain result is kept
-            if ((rc = sim_snapshot_device(h, S->sx, S->su, S->sr))) return rc;
-            if ((rc = sph_surrogate_advance(h, k_steps))) return rc;
-            double cs[3] = {0, 0, 0}, cp[3];
-            const int crc = sim_centroid(h, cs);
-            if (crc && !state_error(crc)) return crc;
-            if ((rc = sim_load_device(h, S->sx, S->su, S->sr))) return rc;
-            if ((rc = sim_moved(h, -k_steps, -S->t_jump64))) return rc;
-            if ((rc = sph_run(h, dt, k_steps, 1))) return rc;
-            if ((rc = sim_centroid(h, cp))) return rc;
-            double e2 = 0.0;
-            for (int c = 0; c < v.dim; ++c) e2 += (cs[c] - cp[c]) * (cs[c] - cp[c]);
-            const double err = crc ? 1.0e30 : std::sqrt(e2) / d_ref;
+            double err = 0.0;
+            if ((rc = judged_jump(h, *S, v, dt, k_steps, d_ref, &err))) return rc;
             worst = std::max(worst, err);
             ++judged;
             fallback = err > tol;

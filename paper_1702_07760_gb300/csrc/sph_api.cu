@@ -387,10 +387,10 @@ __global__ void k_load_state(Dev d, Grid g, Phys ph, const double *x, const doub
     stage_records<DIM>(d, g, I, k, d.cell[k], xa, ua, dr, tg & 1);
     const float4 q = d.pos[k], q0 = d.pos0[k];
     const float ex = q.x - q0.x, ey = q.y - q0.y, ez = q.z - q0.z;
-    const float dts = (tg & 2) ? 0.f : (float)(check_dt * I.dt_scale);
-    const float hx = 0.5f * dts * (float)ua[0], hy = 0.5f * dts * (float)ua[1], hz = 0.5f * dts * (float)ua[2];
-    const float d1 = ex * ex + ey * ey + ez * ez;
-    const float d2 = (ex + hx) * (ex + hx) + (ey + hy) * (ey + hy) + (ez + hz) * (ez + hz);
+    const float hdt = ((tg & 2) && !(tg & 4)) ? 0.f : 0.5f * (float)(check_dt * I.dt_scale);
+    const float hx = __fmul_rn(hdt, (float)ua[0]), hy = __fmul_rn(hdt, (float)ua[1]), hz = __fmul_rn(hdt, (float)ua[2]);
+    const float d1 = sq3(ex, ey, ez);
+    const float d2 = sq3(ex + hx, ey + hy, ez + hz);
     const float lim = (float)(0.98 * ph.skin);
     if (!(d1 <= lim * lim) || !(d2 <= lim * lim)) atomicOr(d.rebuild, 1u);
 }
@@ -690,6 +690,7 @@ int create_sim(const sph_params *params, int k, const int64_t *counts, const dou
     ph.RP = (float)(RL * (1.0 + 1e-4));
     ph.skin = P0.skin;
     ph.kmax = P0.max_neighbours > 0 ? P0.max_neighbours : (dim == 2 ? 48 : 128);
+    ph.kmax = (ph.kmax + SPH_LIST_CHUNK - 1) / SPH_LIST_CHUNK * SPH_LIST_CHUNK;  // lists hold whole chunks
     ph.cF = (float)(-5.0 * alpha_d / (h * h));
     ph.delta2 = (float)(P0.delta * P0.delta);
     ph.inv_dim = (float)(1.0 / dim);

@@ -228,6 +228,17 @@ __device__ __forceinline__ float entry_shift(unsigned e, int a, float E)
     return (__uint_as_float(0x4B400000u | code) - 12582913.f) * E;
 }
 
+// Products that feed a sum are written as explicit FMAs or round-to-nearest
+// multiplies throughout the sweeps and the integration, so ptxas has no
+// multiply-add left to fuse: every build of a function (per-kernel launches
+// and the persistent kernel, at any register budget) rounds identically.
+
+// x^2 + y^2 + z^2 with a fixed rounding sequence.
+__device__ __forceinline__ float sq3(float x, float y, float z)
+{
+    return fmaf(z, z, fmaf(y, y, __fmul_rn(x, x)));
+}
+
 // r_ij = x_i - x_j from super-cell offsets and the centre difference (s).
 template <int DIM>
 __device__ __forceinline__ float pair_vec(const float4 &oi, const float4 &oj, float sx, float sy, float sz,
@@ -236,10 +247,36 @@ __device__ __forceinline__ float pair_vec(const float4 &oi, const float4 &oj, fl
     rx = (oi.x - oj.x) + sx;
     ry = (oi.y - oj.y) + sy;
     rz = DIM == 3 ? (oi.z - oj.z) + sz : 0.f;
-    float r2 = rx * rx;
+    float r2 = __fmul_rn(rx, rx);
     r2 = fmaf(ry, ry, r2);
     if (DIM == 3) r2 = fmaf(rz, rz, r2);
     return r2;
+}
+
+// r_ij = x_i - x_j for list entry e (returns |r_ij|^2): the offset difference
+// plus the super-cell centre difference (S_i - S_j) E of each axis, whose
+// codes (S_i - S_j + 1) sit at bits 26 (x), 28 (y) and 30 (z).  Each code
+// becomes an exact float through the 1.5 * 2^23 mantissa trick and is fused
+// into the difference with one FMA: the same value as (o_i - o_j) + (S_i - S_j) E.
+template <int DIM>
+__device__ __forceinline__ float entry_vec(const float4 &oi, const float4 &oj, unsigned e, float E, float &rx,
+                                          float &ry, float &rz)
+{
+    const unsigned es = e >> NBR_IDX_BITS;
+    rx = fmaf(__uint_as_float(0x4B400000u | (es & 3u)) - 12582913.f, E, oi.x - oj.x);
+    ry = fmaf(__uint_as_float(0x4B400000u | ((es >> 2) & 3u)) - 12582913.f, E, oi.y - oj.y);
+    rz = DIM == 3 ? fmaf(__uint_as_float(0x4B400000u | (es >> 4)) - 12582913.f, E, oi.z - oj.z) : 0.f;
+    float r2 = __fmul_rn(rx, rx);
+    r2 = fmaf(ry, ry, r2);
+    if (DIM == 3) r2 = fmaf(rz, rz, r2);
+    return r2;
+}
+
+// Padding entry of particle i's list: i itself one super-cell away along x
+// and y, |r| = sqrt(2) E > 2h, so every pair term it feeds is zero.
+__device__ __forceinline__ unsigned pad_entry(int i)
+{
+    return (unsigned)i | (2u << NBR_IDX_BITS) | (2u << (NBR_IDX_BITS + 2)) | (1u << (NBR_IDX_BITS + 4));
 }
 
 __device__ __forceinline__ void cell_coords(const Grid &g, int c, int &cx, int &cy, int &cz)
@@ -369,7 +406,7 @@ __device__ __forceinline__ float4 cell_offset(const Grid &g, int c, const double
     const int fm = g.f - 1;
     float o[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-    for (int a = 0; a < DIM; ++a) o[a] = (float)(xa[a] - (g.lo[a] + ((double)(cc[a] >> fm) + 0.5) * g.Ed));
+    for (int a = 0; a < DIM; ++a) o[a] = (float)(xa[a] - fma((double)(cc[a] >> fm) + 0.5, g.Ed, g.lo[a]));
     return make_float4(o[0], o[1], o[2], 0.f);
 }
 
@@ -589,6 +626,9 @@ __device__ __forceinline__ void list_one(const Dev &d, const Grid &g, const Phys
         atomicOr(d.flags, FLAG_LIST);
         cnt = kmax;
     }
+    // whole chunks (kmax is a multiple of the chunk), so the sweeps need no
+    // per-entry bound test
+    for (; cnt % SPH_LIST_CHUNK; ++cnt) nbr[(size_t)cnt * n + i] = pad_entry(i);
     d.ncnt[i] = cnt;
     d.nflag[i] = (uint8_t)other;
 }
@@ -615,8 +655,8 @@ __device__ __forceinline__ void predict_particle(const Dev &d, const Grid &g, co
 #pragma unroll
     for (int c = 0; c < DIM; ++c) {
         const double x = d.x[(size_t)c * d.n + k], u = d.u[(size_t)c * d.n + k];
-        xs[c] = (tg & 2) ? x : x + 0.5 * dt * u;
-        us[c] = (tg & 2) ? u : u + 0.5 * dt * af[c];
+        xs[c] = (tg & 2) ? x : fma(0.5 * dt, u, x);
+        us[c] = (tg & 2) ? u : fma(0.5 * dt, af[c], u);
         finite = finite && isfinite(us[c]) && isfinite(xs[c]);
     }
     if (tg & 4) {
@@ -635,7 +675,7 @@ __device__ __forceinline__ void predict_particle(const Dev &d, const Grid &g, co
     // skin from where it was at the build
     const float4 p0 = d.pos0[k];
     const float ex = p.x - p0.x, ey = p.y - p0.y, ez = p.z - p0.z;
-    if (ex * ex + ey * ey + ez * ez > (float)(ph.skin * ph.skin)) atomicOr(d.flags, FLAG_SKIN);
+    if (sq3(ex, ey, ez) > (float)(ph.skin * ph.skin)) atomicOr(d.flags, FLAG_SKIN);
     float vol;
     p.w = signed_volume(I, tg & 1, drs, vol);
     d.pos[k] = p;
@@ -669,8 +709,8 @@ __device__ __forceinline__ void correct_particle(const Dev &d, const Grid &g, co
         xa[c] = d.x[(size_t)c * d.n + k];
         ua[c] = d.u[(size_t)c * d.n + k];
         if (!(tg & 2)) {
-            xa[c] += dt * usa[c];
-            ua[c] += dt * af[c];
+            xa[c] = fma(dt, usa[c], xa[c]);
+            ua[c] = fma(dt, af[c], ua[c]);
             d.x[(size_t)c * d.n + k] = xa[c];
             d.u[(size_t)c * d.n + k] = ua[c];
         }
@@ -696,11 +736,12 @@ __device__ __forceinline__ void correct_particle(const Dev &d, const Grid &g, co
         // next step's stage positions: x^{n+1} and x^{n+1} + dt/2 u^{n+1};
         // rebuild before either can be farther than the skin from the build
         const float4 p = d.pos[k], p0 = d.pos0[k];
-        const float hx = 0.5f * (float)dt * (float)ua[0], hy = 0.5f * (float)dt * (float)ua[1],
-                    hz = 0.5f * (float)dt * (float)ua[2];
+        const float hdt = 0.5f * (float)dt;
+        const float hx = __fmul_rn(hdt, (float)ua[0]), hy = __fmul_rn(hdt, (float)ua[1]),
+                    hz = __fmul_rn(hdt, (float)ua[2]);
         const float ex = p.x - p0.x, ey = p.y - p0.y, ez = p.z - p0.z;
-        const float d1 = ex * ex + ey * ey + ez * ez;
-        const float d2 = (ex + hx) * (ex + hx) + (ey + hy) * (ey + hy) + (ez + hz) * (ez + hz);
+        const float d1 = sq3(ex, ey, ez);
+        const float d2 = sq3(ex + hx, ey + hy, ez + hz);
         const float lim = (float)(0.98 * ph.skin);
         if (fmaxf(d1, d2) > lim * lim) atomicOr(d.rebuild, 1u);
     }
@@ -733,26 +774,23 @@ __device__ __forceinline__ void sweep_a_one(const Dev &d, const Grid &g, const P
         typename RO<NC, unsigned>::type col = d.nbr + i;
         typename RO<NC, float4>::type pos = d.pos;
         typename RO<NC, float>::type vd = d.vd;
+        // the list holds whole chunks (padding entries feed zero terms)
         constexpr int CH = SPH_LIST_CHUNK;
-        unsigned ec[CH];
+        unsigned ec[CH];  // the first chunk lies inside the list storage (kmax >= CH) even when empty
 #pragma unroll
-        for (int c = 0; c < CH; ++c) ec[c] = c < cnt ? ld<NC>(col + (size_t)c * n) : 0u;
+        for (int c = 0; c < CH; ++c) ec[c] = ld<NC>(col + (size_t)c * n);
         for (int k0 = 0; k0 < cnt; k0 += CH) {
             unsigned en[CH];
+            const bool more = k0 + CH < cnt;
+#pragma unroll
+            for (int c = 0; c < CH; ++c) en[c] = more ? ld<NC>(col + (size_t)(k0 + CH + c) * n) : 0u;
 #pragma unroll
             for (int c = 0; c < CH; ++c) {
-                const int kk = k0 + CH + c;
-                en[c] = kk < cnt ? ld<NC>(col + (size_t)kk * n) : 0u;
-            }
-#pragma unroll
-            for (int c = 0; c < CH; ++c) {
-                if (k0 + c >= cnt) break;
                 const unsigned e = ec[c];
                 const int j = (int)(e & NBR_IDX_MASK);
                 const float4 oj = ld<NC>(pos + j);
                 float rx, ry, rz;
-                const float r2 = pair_vec<DIM>(oi, oj, entry_shift(e, 0, cs), entry_shift(e, 1, cs),
-                                               DIM == 3 ? entry_shift(e, 2, cs) : 0.f, rx, ry, rz);
+                const float r2 = entry_vec<DIM>(oi, oj, e, cs, rx, ry, rz);
                 // beyond the support (list entries in the skin) t clamps to 0 and
                 // every kernel term vanishes
                 const float r = r2 * rsqrtf(fmaxf(r2, 1e-30f));
@@ -762,8 +800,8 @@ __device__ __forceinline__ void sweep_a_one(const Dev &d, const Grid &g, const P
                     if (renorm) {
                         // W / alpha_d = t^4 (2q + 1)
                         const float w = t3 * t * fmaf(2.f * inv_h, r, 1.f);
-                        kahan_add(s1, c1, fabsf(oj.w) * w);
-                        kahan_add(s2, c2, ld<NC>(vd + j) * w);
+                        kahan_add(s1, c1, __fmul_rn(fabsf(oj.w), w));
+                        kahan_add(s2, c2, __fmul_rn(ld<NC>(vd + j), w));
                     }
                 } else {
                     const float cc = oj.w * oj.w * t3;
@@ -786,7 +824,7 @@ __device__ __forceinline__ void sweep_a_one(const Dev &d, const Grid &g, const P
     gx *= sc;
     gy *= sc;
     gz *= sc;
-    const float n2 = gx * gx + gy * gy + gz * gz;
+    const float n2 = sq3(gx, gy, gz);
     unsigned iface = 0u;
     float4 t4 = make_float4(0.f, 0.f, 0.f, 0.f);
     float2 t2 = make_float2(0.f, 0.f);
@@ -796,10 +834,10 @@ __device__ __forceinline__ void sweep_a_one(const Dev &d, const Grid &g, const P
         const float kk = I.alpha_s * rsqrtf(n2) * vol * vol;
         const float iso = n2 * ph.inv_dim;
         if (DIM == 2) {
-            t4 = make_float4(kk * (iso - gx * gx), -kk * gx * gy, kk * (iso - gy * gy), 0.f);
+            t4 = make_float4(kk * fmaf(-gx, gx, iso), -kk * gx * gy, kk * fmaf(-gy, gy, iso), 0.f);
         } else {
-            t4 = make_float4(kk * (iso - gx * gx), -kk * gx * gy, -kk * gx * gz, kk * (iso - gy * gy));
-            t2 = make_float2(-kk * gy * gz, kk * (iso - gz * gz));
+            t4 = make_float4(kk * fmaf(-gx, gx, iso), -kk * gx * gy, -kk * gx * gz, kk * fmaf(-gy, gy, iso));
+            t2 = make_float2(-kk * gy * gz, kk * fmaf(-gz, gz, iso));
         }
     }
     // signed volume (sign = phase) whose lowest mantissa bit carries the
@@ -807,7 +845,7 @@ __device__ __forceinline__ void sweep_a_one(const Dev &d, const Grid &g, const P
     // rounding of m/rho itself
     const float vs = phi_ ? -vol : vol;
     d.posv[i] = make_float4(oi.x, oi.y, oi.z, __uint_as_float((__float_as_uint(vs) & ~1u) | iface));
-    vel_s[i].w = P / (rho * rho);
+    vel_s[i].w = by_phase(phi_, I.mass) * P / (rho * rho);  // m_i P_i / rho_i^2
     d.pres[i] = P;
     d.T4[i] = t4;
     if (DIM == 3) d.T2[i] = t2;
@@ -827,7 +865,7 @@ __device__ __forceinline__ void sweep_b_one(const Dev &d, const Grid &g, const P
     const Inst &I = d.inst[d.iid[i]];
     const unsigned iface_i = __float_as_uint(oi.w) & 1u;
     typename RO<NC, float4>::type vel_s = STAGE == 2 ? d.velq : d.velp;
-    const float4 ui = vel_s[i];              // w: P_i / rho_i^2
+    const float4 ui = vel_s[i];              // w: m_i P_i / rho_i^2
     const float4 Ti = d.T4[i];
     const float2 Ti2 = DIM == 3 ? d.T2[i] : make_float2(0.f, 0.f);
     float px = 0.f, py = 0.f, pz = 0.f;    // sum m_j (P_i/rho_i^2 + P_j/rho_j^2) t^3 r_ij
@@ -836,34 +874,33 @@ __device__ __forceinline__ void sweep_b_one(const Dev &d, const Grid &g, const P
     float dv = 0.f;                        // sum V_j t^3 u_ij . r_ij
     const float inv_h = ph.inv_h, cs = g.Es;
     const int n = d.n, cnt = d.ncnt[i];
-    // per-phase constants of the pair terms as registers (selected per pair)
-    const float m_wat = I.mass[0], m_oil = I.mass[1];
+    // per-phase constants of the pair terms as registers (selected per pair):
+    // m_j P_i / rho_i^2 for a water and an oil neighbour, and the viscous factors
+    const float Pi = ui.w * by_phase(phi_, I.inv_mass);
+    const float mP_wat = I.mass[0] * Pi, mP_oil = I.mass[1] * Pi;
     const float kv_wat = phi_ ? I.kvis[2] : I.kvis[0], kv_oil = phi_ ? I.kvis[3] : I.kvis[1];
     typename RO<NC, unsigned>::type col = d.nbr + i;
     typename RO<NC, float4>::type posv = d.posv;
     typename RO<NC, float4>::type T4 = d.T4;
     typename RO<NC, float2>::type T2 = d.T2;
+    // the list holds whole chunks (padding entries feed zero terms)
     constexpr int CH = SPH_LIST_CHUNK;
-    unsigned ec[CH];
+    unsigned ec[CH];  // the first chunk lies inside the list storage (kmax >= CH) even when empty
 #pragma unroll
-    for (int c = 0; c < CH; ++c) ec[c] = c < cnt ? ld<NC>(col + (size_t)c * n) : 0u;
+    for (int c = 0; c < CH; ++c) ec[c] = ld<NC>(col + (size_t)c * n);
     for (int k0 = 0; k0 < cnt; k0 += CH) {
         unsigned en[CH];
+        const bool more = k0 + CH < cnt;
+#pragma unroll
+        for (int c = 0; c < CH; ++c) en[c] = more ? ld<NC>(col + (size_t)(k0 + CH + c) * n) : 0u;
 #pragma unroll
         for (int c = 0; c < CH; ++c) {
-            const int kk = k0 + CH + c;
-            en[c] = kk < cnt ? ld<NC>(col + (size_t)kk * n) : 0u;
-        }
-#pragma unroll
-        for (int c = 0; c < CH; ++c) {
-            if (k0 + c >= cnt) break;
             const unsigned e = ec[c];
             const int j = (int)(e & NBR_IDX_MASK);
             const float4 oj = ld<NC>(posv + j);
             const float4 uj = ld<NC>(vel_s + j);
             float rx, ry, rz;
-            const float r2 = pair_vec<DIM>(oi, oj, entry_shift(e, 0, cs), entry_shift(e, 1, cs),
-                                           DIM == 3 ? entry_shift(e, 2, cs) : 0.f, rx, ry, rz);
+            const float r2 = entry_vec<DIM>(oi, oj, e, cs, rx, ry, rz);
             const bool oil_j = oj.w < 0.f;
             const float vol_j = fabsf(oj.w);
             // beyond the support (list entries in the skin) t clamps to 0 and
@@ -871,7 +908,8 @@ __device__ __forceinline__ void sweep_b_one(const Dev &d, const Grid &g, const P
             const float r = r2 * rsqrtf(fmaxf(r2, 1e-30f));
             const float t = fmaxf(fmaf(-0.5f * inv_h, r, 1.f), 0.f);
             const float t3 = t * t * t;
-            const float pt = (oil_j ? m_oil : m_wat) * (ui.w + uj.w) * t3;
+            // m_j (P_i/rho_i^2 + P_j/rho_j^2) t^3 with the record's m_j P_j / rho_j^2
+            const float pt = ((oil_j ? mP_oil : mP_wat) + uj.w) * t3;
             px = fmaf(pt, rx, px);
             py = fmaf(pt, ry, py);
             if (DIM == 3) pz = fmaf(pt, rz, pz);
@@ -881,7 +919,7 @@ __device__ __forceinline__ void sweep_b_one(const Dev &d, const Grid &g, const P
             vx = fmaf(s, ux, vx);
             vy = fmaf(s, uy, vy);
             if (DIM == 3) vz = fmaf(s, uz, vz);
-            float ur = ux * rx;
+            float ur = __fmul_rn(ux, rx);
             ur = fmaf(uy, ry, ur);
             if (DIM == 3) ur = fmaf(uz, rz, ur);
             dv = fmaf(vt, ur, dv);
@@ -889,15 +927,15 @@ __device__ __forceinline__ void sweep_b_one(const Dev &d, const Grid &g, const P
                 const float4 Tj = ld<NC>(T4 + j);
                 if (DIM == 2) {
                     const float xx = Ti.x + Tj.x, xy = Ti.y + Tj.y, yy = Ti.z + Tj.z;
-                    sx = fmaf(t3, xx * rx + xy * ry, sx);
-                    sy = fmaf(t3, xy * rx + yy * ry, sy);
+                    sx = fmaf(t3, fmaf(xy, ry, __fmul_rn(xx, rx)), sx);
+                    sy = fmaf(t3, fmaf(yy, ry, __fmul_rn(xy, rx)), sy);
                 } else {
                     const float2 Tj2 = ld<NC>(T2 + j);
                     const float xx = Ti.x + Tj.x, xy = Ti.y + Tj.y, xz = Ti.z + Tj.z;
                     const float yy = Ti.w + Tj.w, yz = Ti2.x + Tj2.x, zz = Ti2.y + Tj2.y;
-                    sx = fmaf(t3, xx * rx + xy * ry + xz * rz, sx);
-                    sy = fmaf(t3, xy * rx + yy * ry + yz * rz, sy);
-                    sz = fmaf(t3, xz * rx + yz * ry + zz * rz, sz);
+                    sx = fmaf(t3, fmaf(xz, rz, fmaf(xy, ry, __fmul_rn(xx, rx))), sx);
+                    sy = fmaf(t3, fmaf(yz, rz, fmaf(yy, ry, __fmul_rn(xy, rx))), sy);
+                    sz = fmaf(t3, fmaf(zz, rz, fmaf(yz, ry, __fmul_rn(xz, rx))), sz);
                 }
             }
         }
@@ -912,9 +950,9 @@ __device__ __forceinline__ void sweep_b_one(const Dev &d, const Grid &g, const P
     } else {
         const float vf = ph.visc_dynamic ? ph.cF / rho : ph.cF;
         const float sf = ph.cF * by_phase(phi_, I.inv_mass);
-        out.x = -ph.cF * px + vf * vx + sf * sx + ph.gf[0];
-        out.y = -ph.cF * py + vf * vy + sf * sy + ph.gf[1];
-        out.z = DIM == 3 ? -ph.cF * pz + vf * vz + sf * sz + ph.gf[2] : 0.f;
+        out.x = fmaf(sf, sx, fmaf(vf, vx, __fmul_rn(-ph.cF, px))) + ph.gf[0];
+        out.y = fmaf(sf, sy, fmaf(vf, vy, __fmul_rn(-ph.cF, py))) + ph.gf[1];
+        out.z = DIM == 3 ? fmaf(sf, sz, fmaf(vf, vz, __fmul_rn(-ph.cF, pz))) + ph.gf[2] : 0.f;
     }
     d.acc[i] = out;
     if (STAGE == 1) predict_particle<DIM>(d, g, ph, I, i, out, dt * I.dt_scale);
@@ -1027,8 +1065,13 @@ static __global__ void __launch_bounds__(256) k_sweep_a(Dev d, Grid g, Phys ph, 
     sweep_a_one<DIM, true>(d, g, ph, drho_in, renorm, vel_s, i);
 }
 
+// Resident blocks of 256 threads per SM the force sweep is compiled for (4:
+// up to 64 registers a thread).
+#ifndef SPH_SWEEP_B_MIN_BLOCKS
+#define SPH_SWEEP_B_MIN_BLOCKS 4
+#endif
 template <int DIM, int STAGE>
-static __global__ void __launch_bounds__(256, 4) k_sweep_b(Dev d, Grid g, Phys ph, double dt)
+static __global__ void __launch_bounds__(256, SPH_SWEEP_B_MIN_BLOCKS) k_sweep_b(Dev d, Grid g, Phys ph, double dt)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.n) return;

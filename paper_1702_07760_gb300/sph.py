@@ -15,8 +15,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsph.so")
 
 SPH_OK = 0
+SPH_EFALLBACK = -9
 ERRORS = {-1: "SPH_EINVAL", -2: "SPH_ENOMEM", -3: "SPH_ECUDA", -4: "SPH_ENONFINITE",
-          -5: "SPH_ECFL", -6: "SPH_EDOMAIN", -7: "SPH_ECAPACITY", -8: "SPH_ETIMEOUT"}
+          -5: "SPH_ECFL", -6: "SPH_EDOMAIN", -7: "SPH_ECAPACITY", -8: "SPH_ETIMEOUT", -9: "SPH_EFALLBACK"}
 VISC_DYNAMIC, VISC_KINEMATIC = 0, 1
 FIELD = dict(pos=0, vel=1, rho=2, rho_eval=3, pressure=4, acc=5, drho=6, tensor=7, cell=8, order=9)
 
@@ -30,7 +31,7 @@ EXPORTS = ["sph_create", "sph_set_state", "sph_build_cells", "sph_eval_rates", "
            "sph_num_instances", "sph_test_stall_barrier", "sph_mm_bf16", "sph_snapshot", "sph_load_snapshot",
            "sph_surrogate_init", "sph_surrogate_get_weights", "sph_surrogate_predict", "sph_surrogate_advance",
            "sph_surrogate_train_step", "sph_surrogate_run", "sph_create_dev", "sph_set_piston", "sph_get_time",
-           "sph_set_time", "sph_suggest_dt"]
+           "sph_set_time", "sph_suggest_dt", "sph_surrogate_advance_judged"]
 
 
 class SphError(RuntimeError):
@@ -109,6 +110,7 @@ def load(path: str = LIB_PATH):
     L.sph_get_time.argtypes = [H, dp]
     L.sph_set_time.argtypes = [H, C.c_double]
     L.sph_suggest_dt.argtypes = [H, dp]
+    L.sph_surrogate_advance_judged.argtypes = [H, C.c_double, C.c_int, C.c_double, C.c_double, dp]
     _lib = L
     return L
 
@@ -349,6 +351,16 @@ class Simulation:
         _check(load().sph_surrogate_run(self._h, float(dt), int(k_steps), int(n_macro), int(judge_every),
                                         float(tol), float(d_ref), C.byref(a), C.byref(b), C.byref(e)))
         return a.value, b.value, e.value
+
+    def surrogate_advance_judged(self, dt: float, k_steps: int, tol: float, d_ref: float):
+        """One judged macro-step (sph_surrogate_advance_judged): returns
+        (accepted, centroid error / d_ref); the state is the plain result."""
+        e = C.c_double()
+        rc = load().sph_surrogate_advance_judged(self._h, float(dt), int(k_steps), float(tol), float(d_ref),
+                                                 C.byref(e))
+        if rc not in (SPH_OK, SPH_EFALLBACK):
+            _check(rc)
+        return rc == SPH_OK, e.value
 
     # -- output -----------------------------------------------------------
     def read(self, field: str, out: np.ndarray | None = None) -> np.ndarray:

@@ -162,6 +162,27 @@ def test_judged_run_falls_back_to_plain(env):
     assert judged == 2 and rejected == 0 and sim2.step_index == 48
 
 
+def test_judged_single_jump_reports_fallback(env):
+    """sph_surrogate_advance_judged: SPH_EFALLBACK under a strict judge, OK under
+    a lenient one; either way the state is the plain steps' result and the
+    clock and step counter advance by k steps."""
+    torch, sph = env
+    w = WL.drop_tank(2, (24, 30), drop_d_dx=8, seed=84)
+    _, norm, flat = _case(2, 85)
+    dt = WL.stable_dt(w.params)
+    d_ref = 2 * w.meta["drop_radius"]
+    plain = sph.Simulation.from_workload(w)
+    plain.run(dt, 8)
+    for tol, accepted in [(1e-30, False), (1e9, True)]:
+        sim = sph.Simulation.from_workload(w)
+        sim.surrogate_init(flat, norm)
+        ok, err = sim.surrogate_advance_judged(dt, 8, tol, d_ref)
+        assert ok == accepted and err > 0
+        assert sim.step_index == 8
+        assert abs(sim.time - plain.time) < 1e-15
+        assert np.abs(sim.read("pos") - plain.read("pos")).max() < 1e-6 * w.params["dx"]
+
+
 def test_judged_run_rolls_back_a_broken_jump(env):
     """A network whose position corrections are scaled to metres throws
     particles out of the box; the run detects it after the next jump, returns
