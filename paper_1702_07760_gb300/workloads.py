@@ -100,7 +100,7 @@ def _lattice(shape, lo_cells: int):
 def drop_tank(dim: int, shape, dx: float = 2.5e-4, drop_d_dx: float = 16.0,
               drop_centre_frac=None, wall_layers: int = 3, seed: int = 0,
               jitter_dx: float = 1e-3, perturb: bool = False, quantise: int | None = None,
-              lid: bool = True, name: str | None = None, **param_kw) -> Workload:
+              lid: bool = True, name: str | None = None, drop_shape: str = "sphere", **param_kw) -> Workload:
     """A closed box of fluid lattice `shape` (particles per axis) with an oil
     drop of diameter `drop_d_dx` * dx and `wall_layers` layers of dynamic wall
     particles on every side.
@@ -108,19 +108,29 @@ def drop_tank(dim: int, shape, dx: float = 2.5e-4, drop_d_dx: float = 16.0,
     perturb:  add the parity perturbation (u ~ U(-0.01, 0.01) c0 per component
               on fluid particles, rho *= 1 + U(-1e-3, 1e-3)).
     lid:      keep the wall layers above the fluid (closed box); without
-              them the fluid has a free surface at y = H.
+              them the fluid has a free surface at y = H, the side walls rise
+              a quarter of the depth above it and the box half the depth.
     quantise: if given, the jitter is drawn as an integer multiple of
               dx / quantise in [-quantise/4, quantise/4] (grid-quantised test
               positions for exact neighbour-set comparisons).
+    drop_shape: "sphere" (diameter drop_d_dx dx) or "cube" (side drop_d_dx dx).
     """
     shape = tuple(int(s) for s in shape)
     assert len(shape) == dim
     rng = np.random.Generator(np.random.PCG64(seed))
     depth = shape[dim - 1] * dx
     p = fluid_params(dim, dx, depth, **param_kw)
-    ijk, inside = _lattice(shape, wall_layers)
-    if not lid:
-        keep = ijk[:, dim - 1] < shape[dim - 1]
+    if lid:
+        ijk, inside = _lattice(shape, wall_layers)
+    else:
+        # open top: the side walls rise a quarter of the depth above the
+        # surface; no lid layers and no particles in the air above the fluid
+        nh = int(np.ceil(0.25 * shape[dim - 1]))
+        ext = shape[:dim - 1] + (shape[dim - 1] + nh,)
+        ijk, inside = _lattice(ext, wall_layers)
+        z = ijk[:, dim - 1]
+        air = inside & (z >= shape[dim - 1])
+        keep = (z < shape[dim - 1] + nh) & ~air
         ijk, inside = ijk[keep], inside[keep]
     x = (ijk + 0.5) * dx
     wall = (~inside).astype(np.uint8)
@@ -137,7 +147,10 @@ def drop_tank(dim: int, shape, dx: float = 2.5e-4, drop_d_dx: float = 16.0,
     centre = np.array([f * s * dx for f, s in zip(drop_centre_frac, shape)])
     r_drop = 0.5 * drop_d_dx * dx
     lattice_pos = (ijk + 0.5) * dx
-    in_drop = fl & (np.sum((lattice_pos - centre) ** 2, axis=1) < r_drop ** 2)
+    if drop_shape == "cube":
+        in_drop = fl & (np.max(np.abs(lattice_pos - centre), axis=1) < r_drop)
+    else:
+        in_drop = fl & (np.sum((lattice_pos - centre) ** 2, axis=1) < r_drop ** 2)
     phase = np.where(in_drop, OIL, WATER).astype(np.uint8)
     # linearised hydrostatic initial density
     y = x[:, dim - 1]
@@ -152,6 +165,9 @@ def drop_tank(dim: int, shape, dx: float = 2.5e-4, drop_d_dx: float = 16.0,
     for k in range(dim):
         p["box_lo"][k] = lo
         p["box_hi"][k] = shape[k] * dx + wall_layers * dx
+    if not lid:
+        # headroom above an open surface: the side walls' height plus a quarter depth
+        p["box_hi"][dim - 1] = (shape[dim - 1] + 2 * int(np.ceil(0.25 * shape[dim - 1]))) * dx
     meta = dict(shape=shape, drop_centre=centre.tolist(), drop_radius=r_drop, seed=seed,
                 n_fluid=nfl, n_wall=int(wall.sum()), n_oil=int(in_drop.sum()))
     nm = name or f"drop_{dim}d_" + "x".join(map(str, shape))
@@ -166,6 +182,16 @@ def drop_2d(seed: int = 0, perturb: bool = False, **kw) -> Workload:
 def drop_3d(seed: int = 1000, perturb: bool = False, **kw) -> Workload:
     """3-D oil drop rise: 64 x 64 x 128 fluid particles + 3 wall layers (656 600)."""
     return drop_tank(3, (64, 64, 128), seed=seed, perturb=perturb, name="drop_3d_64x64x128", **kw)
+
+
+def paper_drop(shape: str = "sphere", seed: int = 1100, **kw) -> Workload:
+    """The paper's oil-drop examples (Sec. "Numerical examples on oil-water
+    interaction"): a 0.2 m cubic tank filled 0.2 m deep, particle size 5 mm
+    (40 x 40 x 40 fluid particles, 3 wall layers, open top), an oil sphere of
+    diameter 0.04 m or a cube of side 0.04 m centred 0.04 m above the bottom,
+    tension alpha_s = 0.05 N/m."""
+    return drop_tank(3, (40, 40, 40), dx=5e-3, drop_d_dx=8.0, drop_centre_frac=[0.5, 0.5, 0.2],
+                     lid=False, seed=seed, alpha_s=0.05, drop_shape=shape, name=f"paper_drop_{shape}", **kw)
 
 
 def stable_dt(p: dict, cfl: float = 0.25) -> float:
