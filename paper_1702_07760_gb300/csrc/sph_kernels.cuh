@@ -866,8 +866,6 @@ __device__ __forceinline__ void sweep_b_one(const Dev &d, const Grid &g, const P
     const unsigned iface_i = __float_as_uint(oi.w) & 1u;
     typename RO<NC, float4>::type vel_s = STAGE == 2 ? d.velq : d.velp;
     const float4 ui = vel_s[i];              // w: m_i P_i / rho_i^2
-    const float4 Ti = d.T4[i];
-    const float2 Ti2 = DIM == 3 ? d.T2[i] : make_float2(0.f, 0.f);
     float px = 0.f, py = 0.f, pz = 0.f;    // sum m_j (P_i/rho_i^2 + P_j/rho_j^2) t^3 r_ij
     float vx = 0.f, vy = 0.f, vz = 0.f;    // sum k_ij V_j t^3 r^2/(r^2+delta^2) u_ij
     float sx = 0.f, sy = 0.f, sz = 0.f;    // sum (T_i/sigma_i^2 + T_j/sigma_j^2) . t^3 r_ij
@@ -924,6 +922,10 @@ __device__ __forceinline__ void sweep_b_one(const Dev &d, const Grid &g, const P
             if (DIM == 3) ur = fmaf(uz, rz, ur);
             dv = fmaf(vt, ur, dv);
             if ((iface_i | (__float_as_uint(oj.w) & 1u)) != 0u) {
+                // interface pairs are few: the particle's own tensor is re-read
+                // here (an L1 hit) rather than held in six registers
+                const float4 Ti = ld<NC>(T4 + i);
+                const float2 Ti2 = DIM == 3 ? ld<NC>(T2 + i) : make_float2(0.f, 0.f);
                 const float4 Tj = ld<NC>(T4 + j);
                 if (DIM == 2) {
                     const float xx = Ti.x + Tj.x, xy = Ti.y + Tj.y, yy = Ti.z + Tj.z;
