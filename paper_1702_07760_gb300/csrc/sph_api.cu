@@ -8,6 +8,7 @@
 #include "sph_kernels.cuh"
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -165,9 +166,12 @@ struct sph_sim {
         return e;
     }
 
-    // Launch wrapper: brackets the launch with events when timing is enabled.
+    // Launch wrapper: an NVTX range named after the kernel around every
+    // launch (seen by profilers that attach; a no-op otherwise), and events
+    // around it when timing is enabled.
     template <class L>
     void launch(int id, L &&l) {
+        nvtxRangePushA(k_names[id]);
         if (timing) {
             PendingTiming p{id, get_event(), get_event()};
             cudaEventRecord(p.a, stream);
@@ -177,6 +181,7 @@ struct sph_sim {
         } else {
             l();
         }
+        nvtxRangePop();
     }
 
     void collect_timing() {
@@ -340,6 +345,12 @@ namespace sphgb {
 // Records the message returned by sph_last_error() for this thread.
 int set_error(int code, const std::string &msg) { return fail(code, msg); }
 }  // namespace sphgb
+
+// NVTX range for the lifetime of a scope (a no-op when no profiler attaches).
+struct NvtxScope {
+    explicit NvtxScope(const char *name) { nvtxRangePushA(name); }
+    ~NvtxScope() { nvtxRangePop(); }
+};
 
 namespace {
 template <int DIM>
@@ -1096,6 +1107,7 @@ int sph_eval_rates(sph_handle s)
 
 int sph_step(sph_handle s, double dt)
 {
+    NvtxScope nvtx_scope("sph_step");
     if (!s) return fail(SPH_EINVAL, "handle is NULL");
     if (!(dt > 0) || !std::isfinite(dt)) return fail(SPH_EINVAL, "dt must be positive and finite");
     if (s->n > 0) {
@@ -1112,6 +1124,7 @@ int sph_step(sph_handle s, double dt)
 
 int sph_run(sph_handle s, double dt, int64_t nsteps, int graph)
 {
+    NvtxScope nvtx_scope("sph_run");
     if (!s) return fail(SPH_EINVAL, "handle is NULL");
     if (!(dt > 0) || !std::isfinite(dt)) return fail(SPH_EINVAL, "dt must be positive and finite");
     if (nsteps < 0) return fail(SPH_EINVAL, "nsteps must be >= 0");
@@ -1153,6 +1166,7 @@ int sph_run(sph_handle s, double dt, int64_t nsteps, int graph)
 
 int sph_run_persistent(sph_handle s, double dt, int64_t nsteps, int graph)
 {
+    NvtxScope nvtx_scope("sph_run_persistent");
     if (!s) return fail(SPH_EINVAL, "handle is NULL");
     if (!(dt > 0) || !std::isfinite(dt)) return fail(SPH_EINVAL, "dt must be positive and finite");
     if (nsteps < 0 || nsteps > 0x7fffffff) return fail(SPH_EINVAL, "nsteps must be in [0, 2^31)");
