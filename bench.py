@@ -530,16 +530,14 @@ def run_ours(args, ws, rank, local):
         hr[:] = sim.read("rho")
         # one untimed round trip
         sim.set_state(hx, hu, hr)
-        sim.step(dt)
+        sim.run(dt, 1)
         torch.cuda.synchronize()
         barrier(ws)
         t0 = time.perf_counter()
         for _ in range(ke):
             sim.set_state(hx, hu, hr)
-            sim.step(dt)
-            sim.read("pos", out=hx)
-            sim.read("vel", out=hu)
-            sim.read("rho", out=hr)
+            sim.run(dt, 1)
+            sim.read_state(hx, hu, hr)
         sim.sync()
         el = max_over_ranks(ws, time.perf_counter() - t0, dev)
         nb = n * (2 * dim + 1) * 8

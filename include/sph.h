@@ -184,7 +184,8 @@ int sph_suggest_dt(sph_handle h, double *dt);
 int sph_set_dt_scales(sph_handle h, const double *scales);
 
 /* Replaces the state (x, u, rho; same layout as sph_create) of an existing
- * handle with host data, keeping its parameters, phases and walls.  The step
+ * handle with host data, keeping its parameters, phases and walls (device or
+ * managed memory is also accepted and read in place).  The step
  * counter is left as it is.  After a step has run (and with rebuild_every ==
  * 0) the cell order and neighbour list are kept when every particle of the
  * new state is within the corrector's skin test of its position at the last
@@ -262,8 +263,16 @@ int sph_sync(sph_handle h);
 int sph_test_stall_barrier(sph_handle h);
 
 /* Copies a field (SPH_FIELD_*) into host memory in original particle order.
- * bytes must be at least the field's size (see the field list). */
+ * bytes must be at least the field's size (see the field list).  Device or
+ * managed memory is written in place by the kernel that unpermutes the
+ * field; host memory (pinned is fastest) through a staging copy.  Waits for
+ * the stream. */
 int sph_read(sph_handle h, int field, void *host_out, int64_t bytes);
+
+/* x, u (n*dim) and rho (n) in one call with one wait: the state as sph_read
+ * gives it, and the argument sph_set_state takes.  Reports device error
+ * flags like sph_sync. */
+int sph_read_state(sph_handle h, double *x, double *u, double *rho);
 
 /* Neighbour sets at the current positions (rebuilds the cell list, which
  * invalidates the eval fields) as computed by the GPU's own

@@ -201,6 +201,7 @@ struct sph_sim {
 
     void enqueue_build_cells(bool force);
     void enqueue_load(const double *x, const double *u, const double *rho, double check_dt);
+    int enqueue_read(int kind, bool integer, void *out, size_t bytes, size_t staging_offset);
     void enqueue_eval(int stage, const float *drho_in, double dt);
     void enqueue_step(double dt);
     int persistent_shape(int bs, int grid_req, int *grid_out, PersistFn *fn_out);
@@ -379,9 +380,11 @@ template <int DIM>
 __global__ void k_load_state(Dev d, Grid g, Phys ph, const double *x, const double *u, const double *rho,
                              double check_dt)
 {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= d.n) return;
-    const int p = d.pid[k];
+    // one thread per original id: the input is read in order (coalesced), the
+    // sorted state is scattered
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= d.n) return;
+    const int k = d.inv[p];
     const Inst &I = d.inst[d.iid[k]];
     const uint8_t tg = d.tag[k];
     double xa[3] = {0, 0, 0}, ua[3] = {0, 0, 0};
@@ -407,6 +410,41 @@ __global__ void k_load_state(Dev d, Grid g, Phys ph, const double *x, const doub
 }
 
 }  // namespace
+
+// The device address of a caller's buffer when kernels can use it in place
+// (device or managed memory); NULL for host memory, pinned or pageable, which
+// goes through the handle's staging buffers with cudaMemcpyAsync (the copy
+// engines move pinned memory as fast as a kernel over the host link does,
+// and in whole lines).
+template <class T>
+T *device_view(T *p)
+{
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return static_cast<T *>(a.devicePointer);
+    return nullptr;
+}
+
+// Queues the original-order copy of one field into `out`: in place when the
+// kernel can write it (device or managed memory), else through the staging
+// buffer (at staging_offset doubles) and a cudaMemcpyAsync.
+int sph_sim::enqueue_read(int kind, bool integer, void *out, size_t bytes, size_t staging_offset)
+{
+    void *dst = device_view(out);
+    double *fo = integer ? nullptr : (dst ? static_cast<double *>(dst) : read_buf + staging_offset);
+    int *io = integer ? (dst ? static_cast<int *>(dst) : read_ibuf) : read_ibuf;
+    if (dim == 2) k_unpermute<2><<<blocks(n), 256, 0, stream>>>(D(), kind, fo, io);
+    else k_unpermute<3><<<blocks(n), 256, 0, stream>>>(D(), kind, fo, io);
+    CU(cudaGetLastError());
+    if (!dst) {
+        const void *src = integer ? static_cast<const void *>(read_ibuf) : static_cast<const void *>(read_buf + staging_offset);
+        CU(cudaMemcpyAsync(out, src, bytes, cudaMemcpyDeviceToHost, stream));
+    }
+    return SPH_OK;
+}
 
 void sph_sim::enqueue_load(const double *x, const double *u, const double *rho, double check_dt)
 {
@@ -732,6 +770,7 @@ int create_sim(const sph_params *params, int k, const int64_t *counts, const dou
         err |= s->alloc(&d.u, N * dim);
         err |= s->alloc(&d.drho, N);
         err |= s->alloc(&d.pid, N);
+        if (b == 0) err |= s->alloc(&d.inv, N);
         err |= s->alloc(&d.tag, N);
         err |= s->alloc(&d.iid, N);
     }
@@ -790,6 +829,7 @@ int create_sim(const sph_params *params, int k, const int64_t *counts, const dou
     a0.builds = a1.builds = s->dbuilds;
     a0.inst = a1.inst = s->dinst;
     a0.clock = a1.clock = s->clock;
+    a1.inv = a0.inv;
     a0.motion = a1.motion = s->motion;
     for (int c = 0; c < 3; ++c) {
         a0.period[c] = a1.period[c] = s->grid.per[c] ? box_hi[c] - box_lo[c] : 0.0;
@@ -831,6 +871,7 @@ int create_sim(const sph_params *params, int k, const int64_t *counts, const dou
         if ((e = cudaMemcpyAsync(a0.iid, iid.data(), sizeof(uint16_t) * n, cudaMemcpyHostToDevice, st)) != cudaSuccess)
             return cuda_fail(e);
         k_iota<<<s->blocks((int)n), 256, 0, st>>>(a0.pid, (int)n);
+        k_iota<<<s->blocks((int)n), 256, 0, st>>>(a0.inv, (int)n);
     }
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e);
     *out = s;
@@ -955,10 +996,19 @@ int sph_set_state(sph_handle s, const double *x, const double *u, const double *
     if (s->n == 0) return SPH_OK;
     if (!x || !u || !rho) return fail(SPH_EINVAL, "an input array is NULL");
     const size_t n = (size_t)s->n, dim = (size_t)s->dim;
-    double *dx = s->read_buf, *du = s->read_buf + n * dim, *dr = s->read_buf + 2 * n * dim;
-    CU(cudaMemcpyAsync(dx, x, sizeof(double) * n * dim, cudaMemcpyHostToDevice, s->stream));
-    CU(cudaMemcpyAsync(du, u, sizeof(double) * n * dim, cudaMemcpyHostToDevice, s->stream));
-    CU(cudaMemcpyAsync(dr, rho, sizeof(double) * n, cudaMemcpyHostToDevice, s->stream));
+    const double *dx = device_view(x), *du = device_view(u), *dr = device_view(rho);
+    if (!dx) {
+        dx = s->read_buf;
+        CU(cudaMemcpyAsync(s->read_buf, x, sizeof(double) * n * dim, cudaMemcpyHostToDevice, s->stream));
+    }
+    if (!du) {
+        du = s->read_buf + n * dim;
+        CU(cudaMemcpyAsync(s->read_buf + n * dim, u, sizeof(double) * n * dim, cudaMemcpyHostToDevice, s->stream));
+    }
+    if (!dr) {
+        dr = s->read_buf + 2 * n * dim;
+        CU(cudaMemcpyAsync(s->read_buf + 2 * n * dim, rho, sizeof(double) * n, cudaMemcpyHostToDevice, s->stream));
+    }
     // the lists are kept when they still hold the new state (tested against the
     // skin with the last step size; a fixed rebuild cadence or no step yet rebuilds)
     const double check_dt = s->P.rebuild_every == 0 ? s->last_dt : 0.0;
@@ -1374,13 +1424,23 @@ int sph_read(sph_handle s, int field, void *host_out, int64_t bytes)
     }
     if (bytes < (int64_t)need) return fail(SPH_EINVAL, "output buffer too small for the field");
     if (n == 0) return SPH_OK;
-    if (s->dim == 2) k_unpermute<2><<<s->blocks(s->n), 256, 0, s->stream>>>(s->D(), kind, s->read_buf, s->read_ibuf);
-    else k_unpermute<3><<<s->blocks(s->n), 256, 0, s->stream>>>(s->D(), kind, s->read_buf, s->read_ibuf);
-    CU(cudaGetLastError());
-    if (integer) CU(cudaMemcpyAsync(host_out, s->read_ibuf, need, cudaMemcpyDeviceToHost, s->stream));
-    else CU(cudaMemcpyAsync(host_out, s->read_buf, need, cudaMemcpyDeviceToHost, s->stream));
+    if (int rc = s->enqueue_read(kind, integer, host_out, need, 0)) return rc;
     CU(cudaStreamSynchronize(s->stream));
     return SPH_OK;
+}
+
+int sph_read_state(sph_handle s, double *x, double *u, double *rho)
+{
+    if (!s) return fail(SPH_EINVAL, "handle is NULL");
+    if (s->n == 0) return SPH_OK;
+    if (!x || !u || !rho) return fail(SPH_EINVAL, "an output array is NULL");
+    const size_t n = (size_t)s->n, dim = (size_t)s->dim;
+    int rc = s->enqueue_read(RK_X, false, x, n * dim * 8, 0);
+    if (!rc) rc = s->enqueue_read(RK_U, false, u, n * dim * 8, n * dim);
+    if (!rc) rc = s->enqueue_read(RK_RHO, false, rho, n * 8, 2 * n * dim);
+    if (rc) return rc;
+    CU(cudaStreamSynchronize(s->stream));
+    return s->check_flags();
 }
 
 int64_t sph_neighbours(sph_handle s, int64_t *start, int32_t *list, int64_t cap)

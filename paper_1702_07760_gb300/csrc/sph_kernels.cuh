@@ -98,6 +98,7 @@ struct Dev {
     double *u;          // dim * n, SoA
     float *drho;        // n, rho - rho0(phase) of the state
     int *pid;           // n, original particle id
+    int *inv;           // n, by original id: the particle's sorted position (inverse of pid)
     uint8_t *tag;       // n, bit0 oil, bit1 wall
     uint16_t *iid;      // n, instance index
     int *cell;          // n, cell id (sorted order)
@@ -599,6 +600,7 @@ __device__ __forceinline__ void copy_one(const Dev &src, const Dev &dst, int k)
     }
     dst.drho[k] = src.drho[k];
     dst.pid[k] = src.pid[k];
+    dst.inv[src.pid[k]] = k;
     dst.tag[k] = src.tag[k];
     dst.iid[k] = src.iid[k];
 }
@@ -1319,10 +1321,12 @@ enum ReadKind { RK_X, RK_U, RK_RHO, RK_RHO_EVAL, RK_P, RK_ACC, RK_DRHO, RK_T, RK
 template <int DIM>
 static __global__ void __launch_bounds__(256) k_unpermute(Dev d, int kind, double *out, int *iout)
 {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= d.n) return;
+    // one thread per original id: the output is written in order (coalesced),
+    // the sorted state is gathered
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= d.n) return;
     const int n = d.n;
-    const int p = d.pid[k];
+    const int k = d.inv[p];
     const int phs = d.tag[k] & 1;
     const Inst &I = d.inst[d.iid[k]];
     switch (kind) {

@@ -31,7 +31,7 @@ EXPORTS = ["sph_create", "sph_set_state", "sph_build_cells", "sph_eval_rates", "
            "sph_num_instances", "sph_test_stall_barrier", "sph_mm_bf16", "sph_snapshot", "sph_load_snapshot",
            "sph_surrogate_init", "sph_surrogate_get_weights", "sph_surrogate_predict", "sph_surrogate_advance",
            "sph_surrogate_train_step", "sph_surrogate_run", "sph_create_dev", "sph_set_piston", "sph_get_time",
-           "sph_set_time", "sph_suggest_dt", "sph_surrogate_advance_judged"]
+           "sph_set_time", "sph_suggest_dt", "sph_surrogate_advance_judged", "sph_read_state"]
 
 
 class SphError(RuntimeError):
@@ -70,6 +70,7 @@ def load(path: str = LIB_PATH):
     L.sph_step.argtypes = [H, C.c_double]
     L.sph_run.argtypes = [H, C.c_double, C.c_int64, C.c_int]
     L.sph_read.argtypes = [H, C.c_int, vp, C.c_int64]
+    L.sph_read_state.argtypes = [H, dp, dp, dp]
     L.sph_neighbours.argtypes = [H, P(C.c_int64), P(C.c_int32), C.c_int64]
     L.sph_neighbours.restype = C.c_int64
     L.sph_diag.argtypes = [H, dp]
@@ -363,6 +364,15 @@ class Simulation:
         return rc == SPH_OK, e.value
 
     # -- output -----------------------------------------------------------
+    def read_state(self, x: np.ndarray, u: np.ndarray, rho: np.ndarray):
+        """x, u, rho into the given C-contiguous float64 arrays (e.g. pinned)
+        with one call (sph_read_state)."""
+        n, d = self.n, self.dim
+        for a, shape in ((x, (n, d)), (u, (n, d)), (rho, (n,))):
+            if a.shape != shape or a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+                raise ValueError(f"expected a C-contiguous float64 array of shape {shape}")
+        _check(load().sph_read_state(self._h, _dp(x), _dp(u), _dp(rho)))
+
     def read(self, field: str, out: np.ndarray | None = None) -> np.ndarray:
         """Copies a field in original particle order into `out` (a C-contiguous
         array of the field's shape and type, e.g. in pinned host memory) or a
