@@ -109,8 +109,8 @@ struct Dev {
     float *vd;          // n, (m/rho) * drho of the stage input
     float4 *posv;       // n, (offset xyz, +/- m/rho after renormalisation with its lowest
                         //     mantissa bit replaced by the interface flag): sweep A output
-    float4 *velp;       // n, stage 1: (u^n xyz, -cF m P/rho^2 from sweep A)
-    float4 *velq;       // n, stage 2: (u* xyz, -cF m P/rho^2 from sweep A); a separate buffer so
+    float4 *velp;       // n, stage 1: (u^n xyz, P/rho^2 from sweep A)
+    float4 *velq;       // n, stage 2: (u* xyz, P/rho^2 from sweep A); a separate buffer so
                         //     the stage-1 force sweep can write it while neighbours read velp
     float *pres;        // n, P from sweep A
     float *drho_stage;  // n, drho* of the predictor
@@ -847,7 +847,7 @@ __device__ __forceinline__ void sweep_a_one(const Dev &d, const Grid &g, const P
     // rounding of m/rho itself
     const float vs = phi_ ? -vol : vol;
     d.posv[i] = make_float4(oi.x, oi.y, oi.z, __uint_as_float((__float_as_uint(vs) & ~1u) | iface));
-    vel_s[i].w = -ph.cF * by_phase(phi_, I.mass) * P / (rho * rho);  // -cF m_i P_i / rho_i^2
+    vel_s[i].w = by_phase(phi_, I.mass) * P / (rho * rho);  // m_i P_i / rho_i^2
     d.pres[i] = P;
     d.T4[i] = t4;
     if (DIM == 3) d.T2[i] = t2;
@@ -867,26 +867,18 @@ __device__ __forceinline__ void sweep_b_one(const Dev &d, const Grid &g, const P
     const Inst &I = d.inst[d.iid[i]];
     const unsigned iface_i = __float_as_uint(oi.w) & 1u;
     typename RO<NC, float4>::type vel_s = STAGE == 2 ? d.velq : d.velp;
-    const float4 ui = vel_s[i];              // w: -cF m_i P_i / rho_i^2
-    // One set of accumulators for the whole acceleration: each pair term
-    // carries its own factor (grad W = cF t^3 r; the viscous 1/rho_i of
-    // Eq. visc_2; 1/m_i of the tension force), folded into per-particle and
-    // per-record constants, so
-    //   a = sum [-cF m_j (P_i/rho_i^2 + P_j/rho_j^2)] t^3 r_ij
-    //     + sum [f_v k_ij V_j t^3 r^2/(r^2+delta^2)] u_ij
-    //     + sum [cF/m_i t^3] (T_i/sigma_i^2 + T_j/sigma_j^2) . r_ij  + g.
-    float ax = 0.f, ay = 0.f, az = 0.f;
+    const float4 ui = vel_s[i];              // w: m_i P_i / rho_i^2
+    float px = 0.f, py = 0.f, pz = 0.f;    // sum m_j (P_i/rho_i^2 + P_j/rho_j^2) t^3 r_ij
+    float vx = 0.f, vy = 0.f, vz = 0.f;    // sum k_ij V_j t^3 r^2/(r^2+delta^2) u_ij
+    float sx = 0.f, sy = 0.f, sz = 0.f;    // sum (T_i/sigma_i^2 + T_j/sigma_j^2) . t^3 r_ij
     float dv = 0.f;                        // sum V_j t^3 u_ij . r_ij
     const float inv_h = ph.inv_h, cs = g.Es;
     const int n = d.n, cnt = d.ncnt[i];
-    const float rho = by_phase(phi_, I.rho0) + d.drho_eval[i];
-    const float vf = ph.visc_dynamic ? ph.cF / rho : ph.cF;
-    const float sf = ph.cF * by_phase(phi_, I.inv_mass);
     // per-phase constants of the pair terms as registers (selected per pair):
-    // -cF m_j P_i / rho_i^2 for a water and an oil neighbour, and f_v k_ij
+    // m_j P_i / rho_i^2 for a water and an oil neighbour, and the viscous factors
     const float Pi = ui.w * by_phase(phi_, I.inv_mass);
     const float mP_wat = I.mass[0] * Pi, mP_oil = I.mass[1] * Pi;
-    const float kv_wat = vf * (phi_ ? I.kvis[2] : I.kvis[0]), kv_oil = vf * (phi_ ? I.kvis[3] : I.kvis[1]);
+    const float kv_wat = phi_ ? I.kvis[2] : I.kvis[0], kv_oil = phi_ ? I.kvis[3] : I.kvis[1];
     typename RO<NC, unsigned>::type col = d.nbr + i;
     typename RO<NC, float4>::type posv = d.posv;
     typename RO<NC, float4>::type T4 = d.T4;
@@ -916,17 +908,17 @@ __device__ __forceinline__ void sweep_b_one(const Dev &d, const Grid &g, const P
             const float r = r2 * rsqrtf(fmaxf(r2, 1e-30f));
             const float t = fmaxf(fmaf(-0.5f * inv_h, r, 1.f), 0.f);
             const float t3 = t * t * t;
-            // -cF m_j (P_i/rho_i^2 + P_j/rho_j^2) t^3 with the record's -cF m_j P_j / rho_j^2
+            // m_j (P_i/rho_i^2 + P_j/rho_j^2) t^3 with the record's m_j P_j / rho_j^2
             const float pt = ((oil_j ? mP_oil : mP_wat) + uj.w) * t3;
-            ax = fmaf(pt, rx, ax);
-            ay = fmaf(pt, ry, ay);
-            if (DIM == 3) az = fmaf(pt, rz, az);
+            px = fmaf(pt, rx, px);
+            py = fmaf(pt, ry, py);
+            if (DIM == 3) pz = fmaf(pt, rz, pz);
             const float ux = ui.x - uj.x, uy = ui.y - uj.y, uz = DIM == 3 ? ui.z - uj.z : 0.f;
             const float vt = vol_j * t3;
             const float s = (oil_j ? kv_oil : kv_wat) * vt * __fdividef(r2, r2 + ph.delta2);
-            ax = fmaf(s, ux, ax);
-            ay = fmaf(s, uy, ay);
-            if (DIM == 3) az = fmaf(s, uz, az);
+            vx = fmaf(s, ux, vx);
+            vy = fmaf(s, uy, vy);
+            if (DIM == 3) vz = fmaf(s, uz, vz);
             float ur = __fmul_rn(ux, rx);
             ur = fmaf(uy, ry, ur);
             if (DIM == 3) ur = fmaf(uz, rz, ur);
@@ -937,32 +929,34 @@ __device__ __forceinline__ void sweep_b_one(const Dev &d, const Grid &g, const P
                 const float4 Ti = ld<NC>(T4 + i);
                 const float2 Ti2 = DIM == 3 ? ld<NC>(T2 + i) : make_float2(0.f, 0.f);
                 const float4 Tj = ld<NC>(T4 + j);
-                const float st = sf * t3;
                 if (DIM == 2) {
                     const float xx = Ti.x + Tj.x, xy = Ti.y + Tj.y, yy = Ti.z + Tj.z;
-                    ax = fmaf(st, fmaf(xy, ry, __fmul_rn(xx, rx)), ax);
-                    ay = fmaf(st, fmaf(yy, ry, __fmul_rn(xy, rx)), ay);
+                    sx = fmaf(t3, fmaf(xy, ry, __fmul_rn(xx, rx)), sx);
+                    sy = fmaf(t3, fmaf(yy, ry, __fmul_rn(xy, rx)), sy);
                 } else {
                     const float2 Tj2 = ld<NC>(T2 + j);
                     const float xx = Ti.x + Tj.x, xy = Ti.y + Tj.y, xz = Ti.z + Tj.z;
                     const float yy = Ti.w + Tj.w, yz = Ti2.x + Tj2.x, zz = Ti2.y + Tj2.y;
-                    ax = fmaf(st, fmaf(xz, rz, fmaf(xy, ry, __fmul_rn(xx, rx))), ax);
-                    ay = fmaf(st, fmaf(yz, rz, fmaf(yy, ry, __fmul_rn(xy, rx))), ay);
-                    az = fmaf(st, fmaf(zz, rz, fmaf(yz, ry, __fmul_rn(xz, rx))), az);
+                    sx = fmaf(t3, fmaf(xz, rz, fmaf(xy, ry, __fmul_rn(xx, rx))), sx);
+                    sy = fmaf(t3, fmaf(yz, rz, fmaf(yy, ry, __fmul_rn(xy, rx))), sy);
+                    sz = fmaf(t3, fmaf(zz, rz, fmaf(yz, ry, __fmul_rn(xz, rx))), sz);
                 }
             }
         }
 #pragma unroll
         for (int c = 0; c < CH; ++c) ec[c] = en[c];
     }
+    const float rho = by_phase(phi_, I.rho0) + d.drho_eval[i];
     float4 out;
     out.w = rho * ph.cF * dv;
     if (d.tag[i] & 2) {
         out.x = out.y = out.z = 0.f;
     } else {
-        out.x = ax + ph.gf[0];
-        out.y = ay + ph.gf[1];
-        out.z = DIM == 3 ? az + ph.gf[2] : 0.f;
+        const float vf = ph.visc_dynamic ? ph.cF / rho : ph.cF;
+        const float sf = ph.cF * by_phase(phi_, I.inv_mass);
+        out.x = fmaf(sf, sx, fmaf(vf, vx, __fmul_rn(-ph.cF, px))) + ph.gf[0];
+        out.y = fmaf(sf, sy, fmaf(vf, vy, __fmul_rn(-ph.cF, py))) + ph.gf[1];
+        out.z = DIM == 3 ? fmaf(sf, sz, fmaf(vf, vz, __fmul_rn(-ph.cF, pz))) + ph.gf[2] : 0.f;
     }
     d.acc[i] = out;
     if (STAGE == 1) predict_particle<DIM>(d, g, ph, I, i, out, dt * I.dt_scale);
