@@ -759,6 +759,67 @@ __device__ __forceinline__ void correct_particle(const Dev &d, const Grid &g, co
 // over i itself and its same-phase neighbours, both sums Kahan-compensated.
 // The colour gradient uses the density that entered the stage:
 // grad C_i = (1/V_i) sum_{j other phase} V_j^2 grad W_ij, V = m/rho = 1/sigma.
+// The pair loop of sweep A for particle i.  MIXED: the list may hold
+// other-phase particles (colour gradient, phase test per pair); otherwise
+// every entry is same-phase.  The renormalisation sums are compensated per
+// chunk of list entries: the chunk's terms are summed with FMAs, and the
+// chunk sum enters the Kahan sums (s, c).
+template <int DIM, bool NC, bool MIXED>
+__device__ __forceinline__ void sweep_a_pairs(const Dev &d, const Grid &g, const Phys &ph, int i, const float4 &oi,
+                                              int phi_, int renorm, float &s1, float &c1, float &s2, float &c2,
+                                              float &gx, float &gy, float &gz)
+{
+    const float inv_h = ph.inv_h, cs = g.Es;
+    const int n = d.n, cnt = d.ncnt[i];
+    typename RO<NC, unsigned>::type col = d.nbr + i;
+    typename RO<NC, float4>::type pos = d.pos;
+    typename RO<NC, float>::type vd = d.vd;
+    // the list holds whole chunks (padding entries feed zero terms)
+    constexpr int CH = SPH_LIST_CHUNK;
+    unsigned ec[CH];  // the first chunk lies inside the list storage (kmax >= CH) even when empty
+#pragma unroll
+    for (int c = 0; c < CH; ++c) ec[c] = ld<NC>(col + (size_t)c * n);
+    for (int k0 = 0; k0 < cnt; k0 += CH) {
+        unsigned en[CH];
+        const bool more = k0 + CH < cnt;
+#pragma unroll
+        for (int c = 0; c < CH; ++c) en[c] = more ? ld<NC>(col + (size_t)(k0 + CH + c) * n) : 0u;
+        float p1 = 0.f, p2 = 0.f;
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+            const unsigned e = ec[c];
+            const int j = (int)(e & NBR_IDX_MASK);
+            const float4 oj = ld<NC>(pos + j);
+            float rx, ry, rz;
+            const float r2 = entry_vec<DIM>(oi, oj, e, cs, rx, ry, rz);
+            // beyond the support (list entries in the skin) t clamps to 0 and
+            // every kernel term vanishes
+            const float r = r2 * rsqrtf(fmaxf(r2, 1e-30f));
+            const float t = fmaxf(fmaf(-0.5f * inv_h, r, 1.f), 0.f);
+            const float t3 = t * t * t;
+            if (!MIXED || phase_of(oj.w) == phi_) {
+                if (renorm) {
+                    // W / alpha_d = t^4 (2q + 1)
+                    const float w = t3 * t * fmaf(2.f * inv_h, r, 1.f);
+                    p1 = fmaf(fabsf(oj.w), w, p1);
+                    p2 = fmaf(ld<NC>(vd + j), w, p2);
+                }
+            } else {
+                const float cc = oj.w * oj.w * t3;
+                gx = fmaf(cc, rx, gx);
+                gy = fmaf(cc, ry, gy);
+                if (DIM == 3) gz = fmaf(cc, rz, gz);
+            }
+        }
+        if (renorm) {
+            kahan_add(s1, c1, p1);
+            kahan_add(s2, c2, p2);
+        }
+#pragma unroll
+        for (int c = 0; c < CH; ++c) ec[c] = en[c];
+    }
+}
+
 template <int DIM, bool NC>
 __device__ __forceinline__ void sweep_a_one(const Dev &d, const Grid &g, const Phys &ph, const float *drho_in,
                                             int renorm, float4 *vel_s, int i)
@@ -770,52 +831,10 @@ __device__ __forceinline__ void sweep_a_one(const Dev &d, const Grid &g, const P
     float s1 = fabsf(oi.w), c1 = 0.f, s2 = d.vd[i], c2 = 0.f;
     float gx = 0.f, gy = 0.f, gz = 0.f;
     const bool other = d.nflag[i] & 1;
-    if (renorm || other) {
-        const float inv_h = ph.inv_h, cs = g.Es;
-        const int n = d.n, cnt = d.ncnt[i];
-        typename RO<NC, unsigned>::type col = d.nbr + i;
-        typename RO<NC, float4>::type pos = d.pos;
-        typename RO<NC, float>::type vd = d.vd;
-        // the list holds whole chunks (padding entries feed zero terms)
-        constexpr int CH = SPH_LIST_CHUNK;
-        unsigned ec[CH];  // the first chunk lies inside the list storage (kmax >= CH) even when empty
-#pragma unroll
-        for (int c = 0; c < CH; ++c) ec[c] = ld<NC>(col + (size_t)c * n);
-        for (int k0 = 0; k0 < cnt; k0 += CH) {
-            unsigned en[CH];
-            const bool more = k0 + CH < cnt;
-#pragma unroll
-            for (int c = 0; c < CH; ++c) en[c] = more ? ld<NC>(col + (size_t)(k0 + CH + c) * n) : 0u;
-#pragma unroll
-            for (int c = 0; c < CH; ++c) {
-                const unsigned e = ec[c];
-                const int j = (int)(e & NBR_IDX_MASK);
-                const float4 oj = ld<NC>(pos + j);
-                float rx, ry, rz;
-                const float r2 = entry_vec<DIM>(oi, oj, e, cs, rx, ry, rz);
-                // beyond the support (list entries in the skin) t clamps to 0 and
-                // every kernel term vanishes
-                const float r = r2 * rsqrtf(fmaxf(r2, 1e-30f));
-                const float t = fmaxf(fmaf(-0.5f * inv_h, r, 1.f), 0.f);
-                const float t3 = t * t * t;
-                if (phase_of(oj.w) == phi_) {
-                    if (renorm) {
-                        // W / alpha_d = t^4 (2q + 1)
-                        const float w = t3 * t * fmaf(2.f * inv_h, r, 1.f);
-                        kahan_add(s1, c1, __fmul_rn(fabsf(oj.w), w));
-                        kahan_add(s2, c2, __fmul_rn(ld<NC>(vd + j), w));
-                    }
-                } else {
-                    const float cc = oj.w * oj.w * t3;
-                    gx = fmaf(cc, rx, gx);
-                    gy = fmaf(cc, ry, gy);
-                    if (DIM == 3) gz = fmaf(cc, rz, gz);
-                }
-            }
-#pragma unroll
-            for (int c = 0; c < CH; ++c) ec[c] = en[c];
-        }
-    }
+    // particles with no other-phase neighbour (the bulk) take the loop
+    // without the per-pair phase test
+    if (other) sweep_a_pairs<DIM, NC, true>(d, g, ph, i, oi, phi_, renorm, s1, c1, s2, c2, gx, gy, gz);
+    else if (renorm) sweep_a_pairs<DIM, NC, false>(d, g, ph, i, oi, phi_, 1, s1, c1, s2, c2, gx, gy, gz);
     const float drho = renorm ? s2 / s1 : drho_in[i];
     d.drho_eval[i] = drho;
     const float rho = by_phase(phi_, I.rho0) + drho;
