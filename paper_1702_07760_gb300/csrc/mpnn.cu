@@ -139,10 +139,8 @@ int dalloc(Surrogate &S, T **p, size_t count)
 // ---------------------------------------------------------------------------
 // Kernels
 
-// SiLU and its derivative with the fast reciprocal (relative error ~1e-6,
-// far below the BF16 rounding of the network's operands).
-__device__ __forceinline__ float silu(float z) { return __fdividef(z, 1.f + __expf(-z)); }
-
+// Derivative of SiLU with the fast reciprocal (relative error ~1e-6, far
+// below the BF16 rounding of the network's operands).
 __device__ __forceinline__ float dsilu(float z)
 {
     const float s = __fdividef(1.f, 1.f + __expf(-z));
@@ -224,16 +222,6 @@ __device__ __forceinline__ bool edge_features(const Dev &d, const Grid &g, float
     return true;
 }
 
-__device__ __forceinline__ void load4(const bf16 *p, float (&v)[4])
-{
-    const uint2 raw = *(const uint2 *)p;
-    const __nv_bfloat162 a = *(const __nv_bfloat162 *)&raw.x, b = *(const __nv_bfloat162 *)&raw.y;
-    v[0] = __low2float(a);
-    v[1] = __high2float(a);
-    v[2] = __low2float(b);
-    v[3] = __high2float(b);
-}
-
 __device__ __forceinline__ void load4(const __half *p, float (&v)[4])
 {
     const uint2 raw = *(const uint2 *)p;
@@ -253,7 +241,6 @@ __device__ __forceinline__ void store4(bf16 *p, const float (&v)[4])
     *(uint2 *)p = raw;
 }
 
-constexpr int GRP = 2;   // valid edges whose row gathers are in flight together
 
 // Width of a staged entry: 2 DIM + 3 edge features and the sender index,
 // padded to whole 16-byte vectors.
