@@ -104,6 +104,7 @@ struct Surrogate {
     // forward activations (rows: nodes in sorted order, padded to npad, zero beyond n)
     bf16 *X16, *A0, *A1[2], *S[2], *G1[2], *hLb, *A2;
     __half *PQ[2];               // [P | Q] node terms of the edge MLP's first layer, FP16
+    __half *PQf = nullptr;       // the same with the state-difference channels folded in (forward)
     float *Z0, *h[3], *degs, *Z1[2], *Z2, *Y;
     float4 *NF;                  // per node: u / sd_edge_u (xyz), density deviation / sd_edge_rho
     // backward
@@ -222,6 +223,28 @@ __device__ __forceinline__ bool edge_features(const Dev &d, const Grid &g, float
     return true;
 }
 
+// The pair-only part of the edge features: r_ij / 2h (DIM), |r_ij| / 2h,
+// phase_i != phase_j.  The state-difference channels of edge_features are
+// linear in node quantities, so the forward pass folds them into the node
+// terms (k_pq_fold) and the edge phase needs only these.
+template <int DIM>
+__device__ __forceinline__ bool edge_geom(const Dev &d, const Grid &g, float R2, float inv2h, const float4 &oi,
+                                          int phi, unsigned e, int &j, float (&ef)[DIM + 2])
+{
+    j = (int)(e & NBR_IDX_MASK);
+    const float4 oj = d.pos[j];
+    float rx, ry, rz;
+    const float r2 = pair_vec<DIM>(oi, oj, entry_shift(e, 0, g.Es), entry_shift(e, 1, g.Es),
+                                   DIM == 3 ? entry_shift(e, 2, g.Es) : 0.f, rx, ry, rz);
+    if (!(r2 < R2)) return false;
+    ef[0] = rx * inv2h;
+    ef[1] = ry * inv2h;
+    if (DIM == 3) ef[2] = rz * inv2h;
+    ef[DIM] = sqrtf(r2) * inv2h;
+    ef[DIM + 1] = phase_of(oj.w) != phi ? 1.f : 0.f;
+    return true;
+}
+
 __device__ __forceinline__ void load4(const __half *p, float (&v)[4])
 {
     const uint2 raw = *(const uint2 *)p;
@@ -282,34 +305,72 @@ __device__ __forceinline__ void cp_async8(void *smem, const void *gmem)
                  : "memory");
 }
 
-// Lane-parallel decoding as in stage_entries, storing each feature as a
-// duplicated FP16 pair (the operand of the packed arithmetic below) and the
-// sender index after them.
+// Slots of the forward edge phase: the DIM + 2 pair features and the sender.
 template <int DIM>
-__device__ __forceinline__ unsigned stage_entries_h2(const Dev &d, const Grid &g, float R2, float inv2h,
-                                                     const float4 &oi, int phi, const float4 &nfi, const float4 *NF,
-                                                     int i, int k0, int cnt, uint32_t (*slot)[slot_width<DIM>()])
+__host__ __device__ constexpr int geom_slot_width() { return ((DIM + 3) + 3) / 4 * 4; }
+
+// Lane-parallel decoding of up to 32 entries for the forward edge phase: the
+// pair features as duplicated FP16 pairs and the sender index after them.
+template <int DIM>
+__device__ __forceinline__ unsigned stage_geom_h2(const Dev &d, const Grid &g, float R2, float inv2h,
+                                                  const float4 &oi, int phi, int i, int k0, int cnt,
+                                                  uint32_t (*slot)[geom_slot_width<DIM>()])
 {
-    constexpr int NE = 2 * DIM + 3;
+    constexpr int NG = DIM + 2;
     const int lane = threadIdx.x & 31;
     const int k = k0 + lane;
     bool valid = false;
     if (k < cnt) {
         int j;
-        float ef[NE];
-        valid = edge_features<DIM>(d, g, R2, inv2h, oi, phi, nfi, NF, d.nbr[(size_t)k * d.n + i], j, ef);
+        float ef[NG];
+        valid = edge_geom<DIM>(d, g, R2, inv2h, oi, phi, d.nbr[(size_t)k * d.n + i], j, ef);
         if (valid) {
 #pragma unroll
-            for (int c = 0; c < NE; ++c) {
+            for (int c = 0; c < NG; ++c) {
                 const __half2 e2 = __float2half2_rn(ef[c]);
                 slot[lane][c] = *(const uint32_t *)&e2;
             }
-            slot[lane][NE] = (uint32_t)j;
+            slot[lane][NG] = (uint32_t)j;
         }
     }
     const unsigned mask = __ballot_sync(0xffffffffu, valid);
     __syncwarp();
     return mask;
+}
+
+// Folds the state-difference channels of the first edge layer into the node
+// terms: with f_i the node's scaled (u, delta) channels and W3d their columns
+// of W3, W3d (f_i - f_j) = W3d f_i - W3d f_j, so P'_i = P_i + W3d f_i and
+// Q'_j = Q_j - W3d f_j give the same pre-activation P'_i + Q'_j + W3g e_ij.
+// One thread per node and four features; FP32 sums, FP16 results.
+template <int DIM>
+__global__ void __launch_bounds__(256) k_pq_fold(int n, const float4 *NF, const __half *PQ, const float *W3,
+                                                 __half *PQf)
+{
+    constexpr int NE = 2 * DIM + 3;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = (int)(t >> 5);
+    if (i >= n) return;
+    const int f0 = (int)(t & 31) * 4;
+    const float4 f = NF[i];
+    const float fa[3] = {f.x, f.y, f.z};
+    float pv[4], qv[4];
+    load4(PQ + (size_t)i * 2 * H + f0, pv);
+    load4(PQ + (size_t)i * 2 * H + H + f0, qv);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float *w = W3 + (size_t)(f0 + q) * NE;
+        float sdiff = w[2 * DIM + 2] * f.w;
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) sdiff = fmaf(w[DIM + 2 + a], fa[a], sdiff);
+        pv[q] += sdiff;
+        qv[q] -= sdiff;
+    }
+    __half2 *pp = (__half2 *)(PQf + (size_t)i * 2 * H + f0), *qq = (__half2 *)(PQf + (size_t)i * 2 * H + H + f0);
+    pp[0] = __floats2half2_rn(pv[0], pv[1]);
+    pp[1] = __floats2half2_rn(pv[2], pv[3]);
+    qq[0] = __floats2half2_rn(qv[0], qv[1]);
+    qq[1] = __floats2half2_rn(qv[2], qv[3]);
 }
 
 __device__ __forceinline__ __half2 tanh_h2(__half2 x)
@@ -320,8 +381,9 @@ __device__ __forceinline__ __half2 tanh_h2(__half2 x)
 }
 
 // Forward edge phase: one warp per receiver i, four features per lane.
-// S_i = (1/k_ref) sum_j SiLU(P_i + Q_j + W3 e_ij) over list entries with
-// |r_ij| < 2h; degs_i = deg_i / k_ref.  Entries are decoded 32 at a time,
+// S_i = (1/k_ref) sum_j SiLU(P'_i + Q'_j + W3g e_ij) over list entries with
+// |r_ij| < 2h (the folded node terms of k_pq_fold and the pair features);
+// degs_i = deg_i / k_ref.  Entries are decoded 32 at a time,
 // one per lane; the sender rows Q_j of every valid entry of the batch are
 // then copied to shared memory with cp.async (all in flight together).  The
 // pre-activation and SiLU run on feature pairs in FP16 (packed FMA, and
@@ -330,12 +392,12 @@ __device__ __forceinline__ __half2 tanh_h2(__half2 x)
 constexpr int EWF = 128;   // threads of the forward edge kernel (4 warps, one node each)
 
 template <int DIM>
-__global__ void __launch_bounds__(EWF, 4) k_edge_fwd(Dev d, Grid g, float R2, float inv2h, const float4 *NF,
-                                                   const __half *PQ, const float *W3, float inv_kref, bf16 *S,
-                                                   float *degs)
+__global__ void __launch_bounds__(EWF, 4) k_edge_fwd(Dev d, Grid g, float R2, float inv2h, const __half *PQ,
+                                                   const float *W3, float inv_kref, bf16 *S, float *degs)
 {
-    constexpr int NE = 2 * DIM + 3;
-    constexpr int SWD = slot_width<DIM>();
+    constexpr int NE = 2 * DIM + 3;   // columns of W3 (the pair features are its first NG)
+    constexpr int NG = DIM + 2;
+    constexpr int SWD = geom_slot_width<DIM>();
     __shared__ __align__(16) uint32_t slots[EWF / 32][32][SWD];
     __shared__ __align__(16) uint2 qrows[EWF / 32][32][32];   // [warp][entry][lane]: 4 FP16 features
     const int wid = threadIdx.x >> 5;
@@ -343,9 +405,9 @@ __global__ void __launch_bounds__(EWF, 4) k_edge_fwd(Dev d, Grid g, float R2, fl
     const int lane = threadIdx.x & 31;
     if (i >= d.n) return;
     const int f0 = lane * 4;
-    __half2 w2[NE][2];   // W3 column c for features (f0, f0+1) and (f0+2, f0+3)
+    __half2 w2[NG][2];   // W3 column c for features (f0, f0+1) and (f0+2, f0+3)
 #pragma unroll
-    for (int c = 0; c < NE; ++c) {
+    for (int c = 0; c < NG; ++c) {
         w2[c][0] = __floats2half2_rn(W3[f0 * NE + c], W3[(f0 + 1) * NE + c]);
         w2[c][1] = __floats2half2_rn(W3[(f0 + 2) * NE + c], W3[(f0 + 3) * NE + c]);
     }
@@ -355,17 +417,16 @@ __global__ void __launch_bounds__(EWF, 4) k_edge_fwd(Dev d, Grid g, float R2, fl
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
     int deg = 0;
     const float4 oi = d.pos[i];
-    const float4 nfi = NF[i];
     const int phi = phase_of(oi.w);
     const int cnt = d.ncnt[i];
     uint32_t(*slot)[SWD] = slots[wid];
     uint2(*qr)[32] = qrows[wid];
     for (int k0 = 0; k0 < cnt; k0 += 32) {
-        const unsigned valid = stage_entries_h2<DIM>(d, g, R2, inv2h, oi, phi, nfi, NF, i, k0, cnt, slot);
+        const unsigned valid = stage_geom_h2<DIM>(d, g, R2, inv2h, oi, phi, i, k0, cnt, slot);
         deg += __popc(valid);
         for (unsigned m = valid; m; m &= m - 1) {
             const int sl = __ffs(m) - 1;
-            cp_async8(&qr[sl][lane], PQ + (size_t)slot[sl][NE] * 2 * H + H + f0);
+            cp_async8(&qr[sl][lane], PQ + (size_t)slot[sl][NG] * 2 * H + H + f0);
         }
         asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
         __syncwarp();
@@ -385,7 +446,7 @@ __global__ void __launch_bounds__(EWF, 4) k_edge_fwd(Dev d, Grid g, float R2, fl
                 e[4 * v4 + 3] = t4.w;
             }
 #pragma unroll
-            for (int c = 0; c < NE; ++c) {
+            for (int c = 0; c < NG; ++c) {
                 const __half2 ec = *(const __half2 *)&e[c];
                 z0 = __hfma2(w2[c][0], ec, z0);
                 z1 = __hfma2(w2[c][1], ec, z1);
@@ -815,6 +876,7 @@ int alloc_surrogate(Surrogate &S)
         e |= dalloc(S, &S.bpq[r], 2 * H);
         e |= dalloc(S, &S.A1[r], P * 2 * H);
         e |= dalloc(S, &S.PQ[r], P * 2 * H);
+        if (r == 0) e |= dalloc(S, &S.PQf, P * 2 * H);
         e |= dalloc(S, &S.S[r], P * H);
         e |= dalloc(S, &S.G1[r], P * H);
         e |= dalloc(S, &S.Z1[r], P * H);
@@ -907,12 +969,15 @@ int forward(Surrogate &S, const SimView &v, bool training)
             e.ldcb = 2 * H;
             if ((rc = mm(S, st, S.A1[r], 2 * H, S.Wpq[r], H, n, 2 * H, H, e))) return rc;
         }
-        if (v.dim == 2)
-            k_edge_fwd<2><<<nb(n * 32, EWF), EWF, 0, st>>>(v.d, v.g, R2, inv2h, S.NF, S.PQ[r], T + L.w3[r], invk,
-                                                           S.S[r], S.degs);
-        else
-            k_edge_fwd<3><<<nb(n * 32, EWF), EWF, 0, st>>>(v.d, v.g, R2, inv2h, S.NF, S.PQ[r], T + L.w3[r], invk,
-                                                           S.S[r], S.degs);
+        if (v.dim == 2) {
+            k_pq_fold<2><<<nb(n * 32, 256), 256, 0, st>>>(n, S.NF, S.PQ[r], T + L.w3[r], S.PQf);
+            k_edge_fwd<2><<<nb(n * 32, EWF), EWF, 0, st>>>(v.d, v.g, R2, inv2h, S.PQf, T + L.w3[r], invk, S.S[r],
+                                                           S.degs);
+        } else {
+            k_pq_fold<3><<<nb(n * 32, 256), 256, 0, st>>>(n, S.NF, S.PQ[r], T + L.w3[r], S.PQf);
+            k_edge_fwd<3><<<nb(n * 32, EWF), EWF, 0, st>>>(v.d, v.g, R2, inv2h, S.PQf, T + L.w3[r], invk, S.S[r],
+                                                           S.degs);
+        }
         CUR(cudaGetLastError());
         {
             Epi e;
