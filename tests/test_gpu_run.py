@@ -55,3 +55,32 @@ def test_flume_runner_moves_the_piston(runner, tmp_path):
     w = WL.wave_tank_small()
     pis = w.wall == 2
     assert np.abs(c["x"][pis, 0] - w.x[pis, 0]).max() > 0
+
+
+def test_paper_sphere_rises_and_stretches_vertically(runner, tmp_path):
+    """The paper's first drop example (0.2 m tank, d = 0.04 m sphere, d_p =
+    5 mm, alpha_s = 0.05): by t = 0.42 s it has risen and, as the paper
+    describes, lengthened vertically (its oil cloud is taller than wide)."""
+    log = tmp_path / "s.jsonl"
+    assert runner.main(["--workload", "paper_sphere", "--t-end", "0.42", "--every", "100000",
+                        "--log", str(log)]) == 0
+    recs = [json.loads(s) for s in log.read_text().splitlines()]
+    first, last = recs[0], recs[-1]
+    assert abs(last["t"] - 0.42) < 1e-4
+    assert last["centroid"][2] - first["centroid"][2] > 0.01        # risen by more than 2 d_p
+    assert first["oil_aspect"] < 1.02 and last["oil_aspect"] > 1.1   # taller than wide
+    assert last["n_oil"] == first["n_oil"] and abs(last["mass"] / first["mass"] - 1) < 1e-12
+
+
+def test_drop_3d_diagnostics_every_100_steps(runner, tmp_path):
+    """The benchmark workload (656 600 particles) for 300 steps with the
+    diagnostics every 100 steps: the FP64 mass is carried exactly, the oil
+    count is constant and the drop starts to rise."""
+    log = tmp_path / "d.jsonl"
+    assert runner.main(["--workload", "drop_3d", "--steps", "300", "--every", "100", "--log", str(log)]) == 0
+    recs = [json.loads(s) for s in log.read_text().splitlines()]
+    assert [r["step"] for r in recs] == [0, 100, 200, 300]
+    assert all(abs(r["mass"] / recs[0]["mass"] - 1) < 1e-12 for r in recs)
+    assert all(r["n_oil"] == recs[0]["n_oil"] for r in recs)
+    assert recs[-1]["centroid"][2] > recs[0]["centroid"][2]
+    assert all(r["u_max"] < 0.1 * 7.92 for r in recs)   # Mach < 0.1 (c0 = 7.92 m/s)
