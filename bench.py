@@ -385,7 +385,6 @@ def run_surrogate(sph, WL, stream, iters, torch, macro=25, k=8):
     ms_plain = timed(lambda: plain.run(dt, macro * k, graph=True))
     c_plain = plain.diagnostics()["centroid"]
     u_plain = plain.read("vel")
-    plain.close()
     sur = sph.Simulation.from_workload(w_eval, stream=stream.cuda_stream)
     sur.surrogate_init(flat, norm)
     sur.surrogate_advance(k)               # warm-up (allocations), then restart
@@ -423,7 +422,10 @@ def run_surrogate(sph, WL, stream, iters, torch, macro=25, k=8):
     ms_judged = (time.perf_counter() - t2) * 1e3
     c_j = judged.diagnostics()["centroid"]
     u_j = judged.read("vel")
+    _, ierr_judged = judged.surrogate_judge_stats()
+    ierr_final = judged.interface_error(plain)
     judged.close()
+    plain.close()
     return {
         "train": {"workloads": [t.name for t in train_tanks], "particles": int(train_nodes), "iterations": iters,
                   "snapshots": "2 x 40, every k = 8 steps", "record_s": rec_s, "train_s": train_s,
@@ -438,6 +440,8 @@ def run_surrogate(sph, WL, stream, iters, torch, macro=25, k=8):
                    "ms_per_k_steps_host_clock": ms_judged / macro,
                    "speedup_vs_plain": ms_plain / ms_judged,
                    "centroid_err_over_D": float(np.linalg.norm(c_j - c_plain) / D),
+                   "max_interface_err_judged_jumps": ierr_judged,
+                   "interface_err_final": ierr_final,
                    "velocity_rms_err_rel": vel_err(u_j)},
     }
 

@@ -179,6 +179,14 @@ int sph_set_time(sph_handle h, double t);
  * limits of weakly compressible SPH.  Waits for the stream. */
 int sph_suggest_dt(sph_handle h, double *dt);
 
+/* Interface error between the oil of two handles (e.g. a variant of a run and
+ * the plain run): with O the set of cells of a grid of spacing
+ * d_p = (m_oil / rho0_oil)^(1/dim) from box_lo that hold at least one oil
+ * particle, *err = |O_a xor O_b| / |O_b| (0 for identical oil layouts; 1e30
+ * if b has no oil and a has).  Both handles must have the same cell grid and
+ * oil particle volume (SPH_EINVAL otherwise).  Waits for both streams. */
+int sph_oil_occupancy_diff(sph_handle a, sph_handle b, double *err);
+
 /* Per-instance step sizes: instance q advances by dt * scales[q] whenever the
  * handle advances by dt (each scale in (0, 1]).  Default 1. */
 int sph_set_dt_scales(sph_handle h, const double *scales);

@@ -83,20 +83,32 @@ int sph_surrogate_advance(sph_handle h, int k_steps);
 int sph_surrogate_train_step(sph_handle h, const double *x1_dev, const double *u1_dev, const double *rho1_dev,
                              double lr, int update, double *loss_out, double *grad_out, int64_t ngrad);
 
+/* The judge's second criterion: a judged jump whose oil occupancy differs
+ * from the plain steps' by more than tol (|O_jump xor O_plain| / |O_plain|,
+ * as sph_oil_occupancy_diff) is rejected too.  0 (the default) reports the
+ * interface error without using it to reject. */
+int sph_surrogate_set_interface_tol(sph_handle h, double tol);
+
+/* Largest centroid error (over d_ref) and interface error of the judged
+ * macro-steps of the last sph_surrogate_run or sph_surrogate_advance_judged. */
+int sph_surrogate_judge_stats(sph_handle h, double *max_centroid_err, double *max_interface_err);
+
 /* One judged macro-step: the surrogate jump and k_steps plain steps (of size
  * dt, graph-replayed) from the same state; the plain result is kept.  *err
  * (if not NULL) receives |c_jump - c_plain| / d_ref for the oil centroids
  * (1e30 when the jump left a non-finite value, a particle outside the box or
  * an over-full neighbour list).  Returns SPH_OK when err <= tol and
  * SPH_EFALLBACK when the judge rejects the jump (the state is still the
- * plain result).  Waits for the stream. */
+ * plain result); an interface error above the tolerance of
+ * sph_surrogate_set_interface_tol rejects it as well.  Waits for the stream. */
 int sph_surrogate_advance_judged(sph_handle h, double dt, int k_steps, double tol, double d_ref, double *err);
 
 /* n_macro macro-steps of k_steps plain steps each.  A macro-step is one
  * surrogate evaluation, except every judge_every-th (0: never), where both
  * the surrogate and k_steps plain steps (of size dt, graph-replayed) start
  * from the same state: the plain result is kept, and the distance between
- * the two oil centroids over d_ref is the judged error.  An error above tol
+ * the two oil centroids over d_ref is the judged error (the interface error
+ * is judged too, see sph_surrogate_set_interface_tol).  An error above tol
  * rejects the surrogate: plain steps replace it until the next judged
  * macro-step.  After every unjudged jump the device error flags are read; a
  * jump that left a non-finite value, a particle outside the box or an

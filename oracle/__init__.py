@@ -288,6 +288,31 @@ def suggest_dt(p: dict, a=None, wall=None) -> float:
     return float(d)
 
 
+def oil_occupancy(p: dict, x, phase, wall):
+    """Set of cells (integer tuples) of a grid of spacing d_p = (m_oil /
+    rho0_oil)^(1/dim) from box_lo that hold at least one oil particle;
+    periodic coordinates are wrapped into the box first."""
+    d = int(p["dim"])
+    x = np.array(x, np.float64, copy=True)
+    per = int(p.get("periodic", 0))
+    for k in range(d):
+        if (per >> k) & 1:
+            L = p["box_hi"][k] - p["box_lo"][k]
+            x[:, k] -= L * np.floor((x[:, k] - p["box_lo"][k]) / L)
+    dp = (p["mass"][1] / p["rho0"][1]) ** (1.0 / d)
+    oil = (np.asarray(phase) == 1) & (np.asarray(wall) == 0)
+    c = np.floor((x[oil] - np.array(p["box_lo"][:d])) / dp).astype(np.int64)
+    return set(map(tuple, c))
+
+
+def interface_error(p: dict, xa, xb, phase, wall) -> float:
+    """|O_a xor O_b| / |O_b| for the oil occupancies of two states."""
+    A, B = oil_occupancy(p, xa, phase, wall), oil_occupancy(p, xb, phase, wall)
+    if not B:
+        return 0.0 if not A else 1e30
+    return len(A ^ B) / len(B)
+
+
 def set_threads(k: int) -> None:
     lib().or_set_num_threads(int(k))
 

@@ -115,6 +115,10 @@ struct Surrogate {
     // judge snapshots (original order)
     double *sx = nullptr, *su = nullptr, *sr = nullptr;
     double *vx = nullptr, *vu = nullptr, *vr = nullptr;   // last verified state
+    // judge: oil occupancy bitmaps of the jump and of the plain steps, the
+    // interface tolerance (0: not used to reject) and the last run's maxima
+    unsigned *occ_a = nullptr, *occ_b = nullptr;
+    double itol = 0.0, max_cerr = 0.0, max_ierr = 0.0;
     std::vector<void *> allocs;
 
     ~Surrogate()
@@ -1400,12 +1404,14 @@ bool state_error(int rc)
 }
 
 // Snapshot buffers of the judged run (allocated once per surrogate).
-int judge_buffers(Surrogate &S, const SimView &v)
+int judge_buffers(Surrogate &S, const SimView &v, sph_handle h)
 {
     if (S.sx) return SPH_OK;
     const size_t nd = (size_t)v.n * v.dim;
+    const size_t words = (size_t)sim_occupancy_words(h);
     int e = dalloc(S, &S.sx, nd) | dalloc(S, &S.su, nd) | dalloc(S, &S.sr, (size_t)v.n) |
-            dalloc(S, &S.vx, nd) | dalloc(S, &S.vu, nd) | dalloc(S, &S.vr, (size_t)v.n);
+            dalloc(S, &S.vx, nd) | dalloc(S, &S.vu, nd) | dalloc(S, &S.vr, (size_t)v.n) |
+            dalloc(S, &S.occ_a, words) | dalloc(S, &S.occ_b, words);
     if (e) return SPH_ENOMEM;
     CUR(cudaDeviceSynchronize());
     return SPH_OK;
@@ -1413,8 +1419,11 @@ int judge_buffers(Surrogate &S, const SimView &v)
 
 // One judged macro-step: the surrogate jump and k plain steps from the same
 // state; the plain result is kept.  *err = |c_jump - c_plain| / d_ref for the
-// oil centroids (1e30 when the jump broke the state).
-int judged_jump(sph_handle h, Surrogate &S, const SimView &v, double dt, int k_steps, double d_ref, double *err)
+// oil centroids, *ierr = |O_jump xor O_plain| / |O_plain| for the oil
+// occupancies (both 1e30 when the jump broke the state).  Updates the
+// surrogate's maxima; *reject tells whether either tolerance is exceeded.
+int judged_jump(sph_handle h, Surrogate &S, const SimView &v, double dt, int k_steps, double d_ref, double tol,
+                double *err, bool *reject)
 {
     int rc;
     if ((rc = sim_snapshot_device(h, S.sx, S.su, S.sr))) return rc;
@@ -1422,13 +1431,22 @@ int judged_jump(sph_handle h, Surrogate &S, const SimView &v, double dt, int k_s
     double cs[3] = {0, 0, 0}, cp[3];
     const int crc = sim_centroid(h, cs);
     if (crc && !state_error(crc)) return crc;
+    if (!crc && (rc = sim_occupancy(h, S.occ_a))) return rc;
     if ((rc = sim_load_device(h, S.sx, S.su, S.sr))) return rc;
     if ((rc = sim_moved(h, -k_steps, -S.t_jump64))) return rc;
     if ((rc = sph_run(h, dt, k_steps, 1))) return rc;
     if ((rc = sim_centroid(h, cp))) return rc;
+    double ierr = 1.0e30;
+    if (!crc) {
+        if ((rc = sim_occupancy(h, S.occ_b))) return rc;
+        if ((rc = sim_occupancy_error(h, S.occ_a, S.occ_b, &ierr))) return rc;
+    }
     double e2 = 0.0;
     for (int c = 0; c < v.dim; ++c) e2 += (cs[c] - cp[c]) * (cs[c] - cp[c]);
     *err = crc ? 1.0e30 : std::sqrt(e2) / d_ref;
+    S.max_cerr = std::max(S.max_cerr, *err);
+    S.max_ierr = std::max(S.max_ierr, ierr);
+    *reject = *err > tol || (S.itol > 0 && ierr > S.itol);
     return SPH_OK;
 }
 
@@ -1441,15 +1459,35 @@ int sph_surrogate_advance_judged(sph_handle h, double dt, int k_steps, double to
     if (!(dt > 0) || k_steps < 1 || !(tol > 0) || !(d_ref > 0))
         return set_error(SPH_EINVAL, "bad dt, k_steps, tol or d_ref");
     const SimView v = sim_view(h);
-    int rc = judge_buffers(*S, v);
+    int rc = judge_buffers(*S, v, h);
     if (rc) return rc;
     double e = 0.0;
-    if ((rc = judged_jump(h, *S, v, dt, k_steps, d_ref, &e))) return rc;
+    bool reject = false;
+    S->max_cerr = S->max_ierr = 0.0;
+    if ((rc = judged_jump(h, *S, v, dt, k_steps, d_ref, tol, &e, &reject))) return rc;
     if (err) *err = e;
     if ((rc = check_err(*S, v.stream))) return rc;
     if ((rc = sim_check(h))) return rc;
-    return e > tol ? set_error(SPH_EFALLBACK, "the judge rejected the surrogate jump; the state holds the plain steps")
-                   : SPH_OK;
+    return reject ? set_error(SPH_EFALLBACK, "the judge rejected the surrogate jump; the state holds the plain steps")
+                  : SPH_OK;
+}
+
+int sph_surrogate_set_interface_tol(sph_handle h, double tol)
+{
+    Surrogate *S = get(h);
+    if (!S) return set_error(SPH_EINVAL, "no surrogate on this handle");
+    if (!(tol >= 0) || !std::isfinite(tol)) return set_error(SPH_EINVAL, "tol must be >= 0");
+    S->itol = tol;
+    return SPH_OK;
+}
+
+int sph_surrogate_judge_stats(sph_handle h, double *max_centroid_err, double *max_interface_err)
+{
+    Surrogate *S = get(h);
+    if (!S) return set_error(SPH_EINVAL, "no surrogate on this handle");
+    if (max_centroid_err) *max_centroid_err = S->max_cerr;
+    if (max_interface_err) *max_interface_err = S->max_ierr;
+    return SPH_OK;
 }
 
 int sph_surrogate_run(sph_handle h, double dt, int k_steps, int64_t n_macro, int judge_every, double tol,
@@ -1460,7 +1498,8 @@ int sph_surrogate_run(sph_handle h, double dt, int k_steps, int64_t n_macro, int
     if (!(dt > 0) || k_steps < 1 || n_macro < 0 || judge_every < 0 || !(tol > 0) || !(d_ref > 0))
         return set_error(SPH_EINVAL, "bad dt, k_steps, n_macro, judge_every, tol or d_ref");
     const SimView v = sim_view(h);
-    if (int e = judge_buffers(*S, v)) return e;
+    if (int e = judge_buffers(*S, v, h)) return e;
+    S->max_cerr = S->max_ierr = 0.0;
     // a state the plain method produced or accepted, and the macro-step it belongs to
     auto verify = [&](int64_t m, int64_t &mv) {
         mv = m;
@@ -1476,10 +1515,11 @@ int sph_surrogate_run(sph_handle h, double dt, int k_steps, int64_t n_macro, int
         if (judge) {
             // surrogate jump and plain steps from the same state; the plain result is kept
             double err = 0.0;
-            if ((rc = judged_jump(h, *S, v, dt, k_steps, d_ref, &err))) return rc;
+            bool reject = false;
+            if ((rc = judged_jump(h, *S, v, dt, k_steps, d_ref, tol, &err, &reject))) return rc;
             worst = std::max(worst, err);
             ++judged;
-            fallback = err > tol;
+            fallback = reject;
             rejected += fallback ? 1 : 0;
             if ((rc = verify(mstep + 1, mv))) return rc;
         } else if (fallback) {

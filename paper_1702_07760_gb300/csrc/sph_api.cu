@@ -111,6 +111,8 @@ struct sph_sim {
     bool evaluated = false;               // acc holds a rates evaluation
     unsigned *amax = nullptr;             // per instance, max |a|^2 (FP32 bits) for sph_suggest_dt
     std::vector<sph_params> inst_params;  // each instance's parameters as given
+    unsigned *occ = nullptr;              // oil occupancy bitmap (sph_oil_occupancy_diff)
+    unsigned long long *occ_cnt = nullptr;
     GridBarrier *bar = nullptr;
     unsigned long long *pair_tot = nullptr;
     double last_dt = 0.0;
@@ -453,6 +455,48 @@ void sph_sim::enqueue_load(const double *x, const double *u, const double *rho, 
 }
 
 namespace {
+
+// Oil occupancy: the cells of a grid of spacing dx from lo that hold at least
+// one oil particle (periodic coordinates wrapped), as a bitmap.
+template <int DIM>
+__global__ void k_occupancy(Dev d, double3 lo, double dx, int3 dims, unsigned *bm)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= d.n) return;
+    const uint8_t tg = d.tag[k];
+    if (!(tg & 1) || (tg & 2)) return;
+    const double l[3] = {lo.x, lo.y, lo.z};
+    const int nd[3] = {dims.x, dims.y, dims.z};
+    long long lin = 0, stride = 1;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        const double x = wrap_coord(d.x[(size_t)a * d.n + k], d.plo[a], d.period[a]);
+        double c = floor((x - l[a]) / dx);
+        c = c < 0.0 ? 0.0 : (c > nd[a] - 1 ? nd[a] - 1 : c);
+        lin += (long long)c * stride;
+        stride *= nd[a];
+    }
+    atomicOr(bm + (lin >> 5), 1u << (lin & 31));
+}
+
+// out[0] += |a xor b|, out[1] += |b| over `words` bitmap words.
+__global__ void k_occupancy_cmp(const unsigned *a, const unsigned *b, long long words, unsigned long long *out)
+{
+    unsigned long long x = 0, nb = 0;
+    for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < words; w += (long long)gridDim.x * blockDim.x) {
+        x += __popc(a[w] ^ b[w]);
+        nb += __popc(b[w]);
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        x += __shfl_down_sync(0xffffffffu, x, o);
+        nb += __shfl_down_sync(0xffffffffu, nb, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(out, x);
+        atomicAdd(out + 1, nb);
+    }
+}
 
 // Largest |a|^2 over the fluid particles of each instance, from the last
 // rates evaluation (non-negative FP32 values order like their bit patterns).
@@ -955,6 +999,58 @@ int sim_centroid(sph_sim *s, double c[3])
     return rc;
 }
 
+// Occupancy grid of the handle: spacing d_p = (m_oil / rho0_oil)^(1/dim) of
+// instance 0 from the grid's lower corner, covering the cell grid.
+struct OccGrid {
+    double3 lo;
+    double dx;
+    int3 dims;
+    long long words;
+};
+
+OccGrid occ_grid(const sph_sim *s)
+{
+    const sph_params &P = s->inst_params[0];
+    const double dp = std::pow(P.mass[1] / P.rho0[1], 1.0 / s->dim);
+    OccGrid o{};
+    o.lo = make_double3(s->grid.lo[0], s->grid.lo[1], s->grid.lo[2]);
+    o.dx = dp;
+    const int nd[3] = {s->grid.nx, s->grid.ny, s->grid.nz};
+    int m[3] = {1, 1, 1};
+    for (int a = 0; a < s->dim; ++a) m[a] = (int)std::ceil(nd[a] * s->grid.csd / dp);
+    o.dims = make_int3(m[0], m[1], m[2]);
+    o.words = ((long long)m[0] * m[1] * m[2] + 31) / 32;
+    return o;
+}
+
+int64_t sim_occupancy_words(sph_sim *s) { return occ_grid(s).words; }
+
+int sim_occupancy(sph_sim *s, unsigned *bm)
+{
+    const OccGrid o = occ_grid(s);
+    CU(cudaMemsetAsync(bm, 0, sizeof(unsigned) * o.words, s->stream));
+    if (s->n == 0) return SPH_OK;
+    if (s->dim == 2) k_occupancy<2><<<s->blocks(s->n), 256, 0, s->stream>>>(s->D(), o.lo, o.dx, o.dims, bm);
+    else k_occupancy<3><<<s->blocks(s->n), 256, 0, s->stream>>>(s->D(), o.lo, o.dx, o.dims, bm);
+    CU(cudaGetLastError());
+    return SPH_OK;
+}
+
+int sim_occupancy_error(sph_sim *s, const unsigned *a, const unsigned *b, double *err)
+{
+    if (!s->occ_cnt && s->alloc(&s->occ_cnt, 2)) return SPH_ENOMEM;
+    const long long words = occ_grid(s).words;
+    CU(cudaMemsetAsync(s->occ_cnt, 0, 2 * sizeof(unsigned long long), s->stream));
+    const int blocks = (int)std::min<long long>((words + 255) / 256, 1024);
+    k_occupancy_cmp<<<std::max(blocks, 1), 256, 0, s->stream>>>(a, b, words, s->occ_cnt);
+    CU(cudaGetLastError());
+    unsigned long long c[2];
+    CU(cudaMemcpyAsync(c, s->occ_cnt, sizeof(c), cudaMemcpyDeviceToHost, s->stream));
+    CU(cudaStreamSynchronize(s->stream));
+    *err = c[1] > 0 ? (double)c[0] / (double)c[1] : (c[0] > 0 ? 1.0e30 : 0.0);
+    return SPH_OK;
+}
+
 void *sim_ext(sph_sim *s) { return s->ext; }
 
 void sim_set_ext(sph_sim *s, void *p, void (*free_fn)(void *))
@@ -1120,6 +1216,24 @@ int sph_suggest_dt(sph_handle s, double *dt)
     }
     *dt = best;
     return SPH_OK;
+}
+
+int sph_oil_occupancy_diff(sph_handle a, sph_handle b, double *err)
+{
+    if (!a || !b || !err) return fail(SPH_EINVAL, "NULL argument");
+    const OccGrid ga = occ_grid(a), gb = occ_grid(b);
+    if (a->dim != b->dim || ga.dims.x != gb.dims.x || ga.dims.y != gb.dims.y || ga.dims.z != gb.dims.z ||
+        ga.dx != gb.dx || ga.lo.x != gb.lo.x || ga.lo.y != gb.lo.y || ga.lo.z != gb.lo.z)
+        return fail(SPH_EINVAL, "the handles' occupancy grids differ (cell grid and oil particle volume)");
+    if (!a->occ && a->alloc(&a->occ, (size_t)ga.words)) return SPH_ENOMEM;
+    if (!b->occ && b->alloc(&b->occ, (size_t)gb.words)) return SPH_ENOMEM;
+    int rc = sim_occupancy(a, a->occ);
+    if (!rc) rc = sim_occupancy(b, b->occ);
+    if (rc) return rc;
+    CU(cudaStreamSynchronize(b->stream));
+    if ((rc = sim_occupancy_error(a, a->occ, b->occ, err))) return rc;
+    if ((rc = a->check_flags())) return rc;
+    return b->check_flags();
 }
 
 int sph_set_dt_scales(sph_handle s, const double *scales)

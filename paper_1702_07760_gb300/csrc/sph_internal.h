@@ -37,6 +37,11 @@ int sim_snapshot_device(sph_sim *s, double *x, double *u, double *rho);
 int sim_load_device(sph_sim *s, const double *x, const double *u, const double *rho);
 // Oil centroid of instance 0 (FP64), or an error code.
 int sim_centroid(sph_sim *s, double c[3]);
+// Oil occupancy bitmaps (cells of spacing d_p holding oil): the words of one
+// bitmap, queueing one into bm, and |a xor b| / |b| (waits for the stream).
+int64_t sim_occupancy_words(sph_sim *s);
+int sim_occupancy(sph_sim *s, unsigned *bm);
+int sim_occupancy_error(sph_sim *s, const unsigned *a, const unsigned *b, double *err);
 // Slot owned by the surrogate, freed with the handle.
 void *sim_ext(sph_sim *s);
 void sim_set_ext(sph_sim *s, void *p, void (*free_fn)(void *));

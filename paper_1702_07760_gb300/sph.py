@@ -31,7 +31,8 @@ EXPORTS = ["sph_create", "sph_set_state", "sph_build_cells", "sph_eval_rates", "
            "sph_num_instances", "sph_test_stall_barrier", "sph_mm_bf16", "sph_snapshot", "sph_load_snapshot",
            "sph_surrogate_init", "sph_surrogate_get_weights", "sph_surrogate_predict", "sph_surrogate_advance",
            "sph_surrogate_train_step", "sph_surrogate_run", "sph_create_dev", "sph_set_piston", "sph_get_time",
-           "sph_set_time", "sph_suggest_dt", "sph_surrogate_advance_judged", "sph_read_state"]
+           "sph_set_time", "sph_suggest_dt", "sph_surrogate_advance_judged", "sph_read_state",
+           "sph_oil_occupancy_diff", "sph_surrogate_set_interface_tol", "sph_surrogate_judge_stats"]
 
 
 class SphError(RuntimeError):
@@ -71,6 +72,9 @@ def load(path: str = LIB_PATH):
     L.sph_run.argtypes = [H, C.c_double, C.c_int64, C.c_int]
     L.sph_read.argtypes = [H, C.c_int, vp, C.c_int64]
     L.sph_read_state.argtypes = [H, dp, dp, dp]
+    L.sph_oil_occupancy_diff.argtypes = [H, H, dp]
+    L.sph_surrogate_set_interface_tol.argtypes = [H, C.c_double]
+    L.sph_surrogate_judge_stats.argtypes = [H, dp, dp]
     L.sph_neighbours.argtypes = [H, P(C.c_int64), P(C.c_int32), C.c_int64]
     L.sph_neighbours.restype = C.c_int64
     L.sph_diag.argtypes = [H, dp]
@@ -352,6 +356,21 @@ class Simulation:
         _check(load().sph_surrogate_run(self._h, float(dt), int(k_steps), int(n_macro), int(judge_every),
                                         float(tol), float(d_ref), C.byref(a), C.byref(b), C.byref(e)))
         return a.value, b.value, e.value
+
+    def interface_error(self, plain: "Simulation") -> float:
+        """Oil occupancy difference against another handle (sph_oil_occupancy_diff)."""
+        e = C.c_double()
+        _check(load().sph_oil_occupancy_diff(self._h, plain._h, C.byref(e)))
+        return e.value
+
+    def surrogate_set_interface_tol(self, tol: float):
+        _check(load().sph_surrogate_set_interface_tol(self._h, float(tol)))
+
+    def surrogate_judge_stats(self):
+        """(largest centroid error / d_ref, largest interface error) of the last judged run."""
+        a, b = C.c_double(), C.c_double()
+        _check(load().sph_surrogate_judge_stats(self._h, C.byref(a), C.byref(b)))
+        return a.value, b.value
 
     def surrogate_advance_judged(self, dt: float, k_steps: int, tol: float, d_ref: float):
         """One judged macro-step (sph_surrogate_advance_judged): returns

@@ -312,3 +312,24 @@ def test_surrogate_rejects_piston_handles(sphmod):
         sim.surrogate_init(weights, norm)
     assert "piston" in str(e.value)
     sim.close()
+
+
+def test_interface_error_matches_oracle(sphmod):
+    """sph_oil_occupancy_diff: the oil occupancy cells of two states and their
+    symmetric difference, the same as the oracle's count (integer work,
+    FP64 cell decisions on both sides)."""
+    w = WL.drop_tank(3, (20, 20, 30), drop_d_dx=10, seed=91, perturb=True)
+    p = w.params
+    rng = np.random.Generator(np.random.PCG64(92))
+    x2 = w.x.copy()
+    oil = w.phase == 1
+    x2[oil] += rng.uniform(-0.8, 0.8, (oil.sum(), 3)) * p["dx"]
+    a = sphmod.Simulation.from_workload(w)
+    b = sphmod.Simulation(p, x2, w.u, w.rho, w.phase, w.wall)
+    c = sphmod.Simulation.from_workload(w)
+    assert a.interface_error(c) == 0.0
+    e = b.interface_error(a)
+    ref = oracle.interface_error(p, x2, w.x, w.phase, w.wall)
+    assert e == ref and e > 0
+    for s in (a, b, c):
+        s.close()

@@ -250,3 +250,25 @@ def test_training_beats_the_explicit_jump(env):
     assert after["loss"] < 0.7 * before["loss"]
     assert after["du_net"] < after["du_jump"]
     assert after["dr_net"] < 0.25 * after["dr_jump"]
+
+
+def test_judge_reports_and_uses_the_interface_error(env):
+    """The judged macro-step reports the oil occupancy difference between the
+    jump and the plain steps; with an interface tolerance it rejects exactly
+    when that difference exceeds it."""
+    torch, sph = env
+    w = WL.drop_tank(2, (24, 30), drop_d_dx=8, seed=86)
+    _, norm, flat = _case(2, 87)
+    dt = WL.stable_dt(w.params)
+    d_ref = 2 * w.meta["drop_radius"]
+    sim = sph.Simulation.from_workload(w)
+    sim.surrogate_init(flat, norm)
+    ok, err = sim.surrogate_advance_judged(dt, 8, 1e9, d_ref)
+    cerr, ierr = sim.surrogate_judge_stats()
+    assert ok and cerr == err and ierr >= 0
+    sim2 = sph.Simulation.from_workload(w)
+    sim2.surrogate_init(flat, norm)
+    sim2.surrogate_set_interface_tol(1e-12)
+    ok2, _ = sim2.surrogate_advance_judged(dt, 8, 1e9, d_ref)
+    _, ierr2 = sim2.surrogate_judge_stats()
+    assert ierr2 == ierr and ok2 == (ierr2 <= 1e-12)

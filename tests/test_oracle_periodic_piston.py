@@ -261,3 +261,25 @@ def test_suggested_dt_bounds_order():
     assert oracle.suggest_dt(dict(p, alpha_s=1e4)) < base
     assert oracle.suggest_dt(p, a=np.array([[1e9, 0.0]]), wall=np.zeros(1, np.uint8)) < base
     assert oracle.suggest_dt(p, a=np.array([[1e9, 0.0]]), wall=np.ones(1, np.uint8)) == base
+
+
+# --------------------------------------------------------------------------
+# Interface error (oil occupancy), the judge's second criterion
+
+def test_interface_error_closed_forms():
+    """A block of oil on the lattice: identical states give 0; the block moved
+    by one particle spacing along x leaves two slabs of the cross-section:
+    error 2 / (cells along x)."""
+    w = WL.drop_tank(3, (12, 12, 12), drop_d_dx=6.0, seed=2, jitter_dx=0.0, drop_shape="cube")
+    p = w.params
+    assert oracle.interface_error(p, w.x, w.x, w.phase, w.wall) == 0.0
+    O = oracle.oil_occupancy(p, w.x, w.phase, w.wall)
+    nx = len({c[0] for c in O})
+    assert len(O) == nx ** 3            # a cube of cells
+    x2 = w.x.copy()
+    x2[w.phase == 1, 0] += p["dx"]
+    assert abs(oracle.interface_error(p, x2, w.x, w.phase, w.wall) - 2.0 / nx) < 1e-15
+    # moved by half a spacing from the cell centres: the same cells
+    x3 = w.x.copy()
+    x3[w.phase == 1, 1] += 0.4 * p["dx"]
+    assert oracle.interface_error(p, x3, w.x, w.phase, w.wall) == 0.0
