@@ -60,6 +60,8 @@ def parse():
                     help="steps of the 256-instance batched comparison (0 skips it)")
     ap.add_argument("--surrogate-iters", type=int, default=1000,
                     help="training iterations of the learned k-step surrogate (0 skips it)")
+    ap.add_argument("--surrogate-noise", type=float, default=0.3,
+                    help="training input noise, as a fraction of the rms change over one jump")
     ap.add_argument("--flume-steps", type=int, default=200,
                     help="timed steps of the 4.9 M-particle breaking-wave flume (0 skips it)")
     return ap.parse_args()
@@ -301,7 +303,7 @@ def run_flume(sph, WL, stream, steps, torch):
     return out
 
 
-def run_surrogate(sph, WL, stream, iters, torch, macro=25, k=8):
+def run_surrogate(sph, WL, stream, iters, torch, macro=25, k=8, noise_frac=0.0):
     """The learned k-step surrogate: trained on plain trajectories of narrower
     tanks of the same depth (so the same c0, dt and jump T = k dt), then
     advancing the 656 600-particle drop for `macro` jumps of k steps against
@@ -336,6 +338,9 @@ def run_surrogate(sph, WL, stream, iters, torch, macro=25, k=8):
     rec_s = time.perf_counter() - t0
     norm = SUR.fit_norm(train_tanks[0].params, train_tanks[0].phase, train_tanks[0].wall, [sets[0][1]],
                         k_ref=80.0, t_jump=T)
+    # input noise: a fraction of the rms velocity and density change over one jump
+    su, sr = SUR.increment_scales(sets[0][1], train_tanks[0].wall)
+    noise = (noise_frac * su, noise_frac * sr) if noise_frac > 0 else None
     # one handle trains on both trajectories in turn (the weights move between handles)
     flat = SL.init_weights(3, seed=7)
     hist = []
@@ -346,7 +351,7 @@ def run_surrogate(sph, WL, stream, iters, torch, macro=25, k=8):
         s, snaps = sets[rnd % 2]
         s.surrogate_init(flat, norm)
         hist += list(SUR.train(s, [snaps], iters=per, lr=1e-3 * (0.5 ** rnd), lr_final=2e-4 * (0.5 ** rnd),
-                               seed=rnd))
+                               seed=rnd, noise=noise))
         flat = s.surrogate_weights()
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t1
@@ -428,6 +433,8 @@ def run_surrogate(sph, WL, stream, iters, torch, macro=25, k=8):
     plain.close()
     return {
         "train": {"workloads": [t.name for t in train_tanks], "particles": int(train_nodes), "iterations": iters,
+                  "input_noise": {"frac_of_jump_increment": noise_frac, "sigma_u": noise[0] if noise else 0.0,
+                                  "sigma_rho_rel": noise[1] if noise else 0.0},
                   "snapshots": "2 x 40, every k = 8 steps", "record_s": rec_s, "train_s": train_s,
                   "ms_per_iteration": train_s / max(iters, 1) * 1e3,
                   "loss_first_50": float(np.mean(hist[:50])), "loss_last_50": float(np.mean(hist[-50:]))},
@@ -559,7 +566,7 @@ def run_ours(args, ws, rank, local):
         batched = run_batched(sph, WL, stream, args.batch_steps, torch)
     surrogate = None
     if rank == 0 and ws == 1 and args.surrogate_iters > 0:
-        surrogate = run_surrogate(sph, WL, stream, args.surrogate_iters, torch)
+        surrogate = run_surrogate(sph, WL, stream, args.surrogate_iters, torch, noise_frac=args.surrogate_noise)
     flume = None
     if rank == 0 and ws == 1 and args.flume_steps > 0:
         flume = run_flume(sph, WL, stream, args.flume_steps, torch)

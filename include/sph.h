@@ -179,6 +179,16 @@ int sph_set_time(sph_handle h, double t);
  * limits of weakly compressible SPH.  Waits for the stream. */
 int sph_suggest_dt(sph_handle h, double *dt);
 
+/* Perturbs the state in place (no counterpart in the paper: training-data
+ * augmentation for the learned surrogate, and robustness tests): every
+ * velocity component of a fluid particle gets N(0, sigma_u^2) added, its
+ * density a factor 1 + N(0, sigma_rho^2).  The variates come from a
+ * counter-based generator (SplitMix64, Box-Muller) keyed on seed, the
+ * original particle id and the channel, so they do not depend on the
+ * particle order.  The next step or evaluation rebuilds the lists.
+ * Queued on the stream. */
+int sph_perturb_state(sph_handle h, double sigma_u, double sigma_rho, uint64_t seed);
+
 /* Interface error between the oil of two handles (e.g. a variant of a run and
  * the plain run): with O the set of cells of a grid of spacing
  * d_p = (m_oil / rho0_oil)^(1/dim) from box_lo that hold at least one oil

@@ -498,6 +498,45 @@ __global__ void k_occupancy_cmp(const unsigned *a, const unsigned *b, long long 
     }
 }
 
+// SplitMix64 (Steele, Lea and Flood, "Fast splittable pseudorandom number
+// generators", 2014): a counter-based 64-bit mixer.
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long z)
+{
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// A standard normal variate for (seed, particle id, channel): two uniforms
+// from the mixer and the Box-Muller transform.
+__device__ __forceinline__ double gauss(unsigned long long seed, int p, int c)
+{
+    const unsigned long long a = splitmix64(seed ^ splitmix64(((unsigned long long)p << 3) | (unsigned)c));
+    const unsigned long long b = splitmix64(a);
+    const double u1 = ((a >> 11) + 1.0) * 0x1.0p-53, u2 = (b >> 11) * 0x1.0p-53;
+    return sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2);
+}
+
+// Adds N(0, sigma_u^2) to each velocity component and multiplies the density
+// by 1 + N(0, sigma_rho^2), fluid particles only; the variates depend on the
+// original particle id, not on the sorted position.
+template <int DIM>
+__global__ void k_perturb(Dev d, double sigma_u, double sigma_rho, unsigned long long seed)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= d.n) return;
+    const uint8_t tg = d.tag[k];
+    if (tg & 2) return;
+    const int p = d.pid[k];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) d.u[(size_t)c * d.n + k] += sigma_u * gauss(seed, p, c);
+    const Inst &I = d.inst[d.iid[k]];
+    const double rho0 = by_phase(tg & 1, I.rho0);
+    const double rho = (rho0 + (double)d.drho[k]) * (1.0 + sigma_rho * gauss(seed, p, 3));
+    d.drho[k] = (float)(rho - rho0);
+}
+
 // Largest |a|^2 over the fluid particles of each instance, from the last
 // rates evaluation (non-negative FP32 values order like their bit patterns).
 __global__ void k_amax(Dev d, unsigned *amax)
@@ -1215,6 +1254,20 @@ int sph_suggest_dt(sph_handle s, double *dt)
         best = std::min(best, d / s->hinst[q].dt_scale);
     }
     *dt = best;
+    return SPH_OK;
+}
+
+int sph_perturb_state(sph_handle s, double sigma_u, double sigma_rho, uint64_t seed)
+{
+    if (!s) return fail(SPH_EINVAL, "handle is NULL");
+    if (!(sigma_u >= 0) || !(sigma_rho >= 0) || !std::isfinite(sigma_u) || !std::isfinite(sigma_rho))
+        return fail(SPH_EINVAL, "sigma_u and sigma_rho must be finite and >= 0");
+    if (s->n == 0) return SPH_OK;
+    if (s->dim == 2) k_perturb<2><<<s->blocks(s->n), 256, 0, s->stream>>>(s->D(), sigma_u, sigma_rho, seed);
+    else k_perturb<3><<<s->blocks(s->n), 256, 0, s->stream>>>(s->D(), sigma_u, sigma_rho, seed);
+    CU(cudaGetLastError());
+    // the stage records derive from the state: rebuilt with the lists
+    CU(cudaMemsetAsync(s->rebuild, 0xff, sizeof(unsigned), s->stream));
     return SPH_OK;
 }
 

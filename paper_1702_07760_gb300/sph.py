@@ -32,7 +32,8 @@ EXPORTS = ["sph_create", "sph_set_state", "sph_build_cells", "sph_eval_rates", "
            "sph_surrogate_init", "sph_surrogate_get_weights", "sph_surrogate_predict", "sph_surrogate_advance",
            "sph_surrogate_train_step", "sph_surrogate_run", "sph_create_dev", "sph_set_piston", "sph_get_time",
            "sph_set_time", "sph_suggest_dt", "sph_surrogate_advance_judged", "sph_read_state",
-           "sph_oil_occupancy_diff", "sph_surrogate_set_interface_tol", "sph_surrogate_judge_stats"]
+           "sph_oil_occupancy_diff", "sph_surrogate_set_interface_tol", "sph_surrogate_judge_stats",
+           "sph_perturb_state"]
 
 
 class SphError(RuntimeError):
@@ -73,6 +74,7 @@ def load(path: str = LIB_PATH):
     L.sph_read.argtypes = [H, C.c_int, vp, C.c_int64]
     L.sph_read_state.argtypes = [H, dp, dp, dp]
     L.sph_oil_occupancy_diff.argtypes = [H, H, dp]
+    L.sph_perturb_state.argtypes = [H, C.c_double, C.c_double, C.c_uint64]
     L.sph_surrogate_set_interface_tol.argtypes = [H, C.c_double]
     L.sph_surrogate_judge_stats.argtypes = [H, dp, dp]
     L.sph_neighbours.argtypes = [H, P(C.c_int64), P(C.c_int32), C.c_int64]
@@ -356,6 +358,10 @@ class Simulation:
         _check(load().sph_surrogate_run(self._h, float(dt), int(k_steps), int(n_macro), int(judge_every),
                                         float(tol), float(d_ref), C.byref(a), C.byref(b), C.byref(e)))
         return a.value, b.value, e.value
+
+    def perturb(self, sigma_u: float, sigma_rho: float, seed: int):
+        """Gaussian noise on the fluid velocities and densities (sph_perturb_state)."""
+        _check(load().sph_perturb_state(self._h, float(sigma_u), float(sigma_rho), int(seed) & (2 ** 64 - 1)))
 
     def interface_error(self, plain: "Simulation") -> float:
         """Oil occupancy difference against another handle (sph_oil_occupancy_diff)."""

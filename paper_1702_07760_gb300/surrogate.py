@@ -98,10 +98,25 @@ def fit_norm(params: dict, phase, wall, snap_sets, k_ref: float, t_jump: float) 
     return SL.make_norm(dim, mu_in, sd_in, mu_out, sd_out, k_ref, t_jump, sd_eu, sd_er)
 
 
-def train(sim, snap_sets, iters: int, lr: float = 1e-3, lr_final: float = 5e-5, seed: int = 0, log_every: int = 0):
+def increment_scales(snaps: Snapshots, wall) -> tuple[float, float]:
+    """RMS over the fluid particles of the velocity and relative density
+    changes between consecutive snapshots (one jump)."""
+    torch = snaps.torch
+    fl = torch.as_tensor(np.asarray(wall) == 0, device=snaps.u.device)
+    du = snaps.u[1:snaps.count] - snaps.u[:snaps.count - 1]
+    dr = (snaps.r[1:snaps.count] - snaps.r[:snaps.count - 1]) / snaps.r[:snaps.count - 1]
+    return (float(du[:, fl].pow(2).mean().sqrt()), float(dr[:, fl].pow(2).mean().sqrt()))
+
+
+def train(sim, snap_sets, iters: int, lr: float = 1e-3, lr_final: float = 5e-5, seed: int = 0, log_every: int = 0,
+          noise: tuple[float, float] | None = None):
     """Adam on random (state, state k steps later) pairs of the recorded
     trajectories with a cosine learning-rate decay; returns the loss history.
-    Leaves the handle at the last training state."""
+    With noise = (sigma_u, sigma_rho) the input state of every pair is
+    perturbed (sph_perturb_state) while the target stays the recorded one, so
+    the network also learns to correct states a little off the trajectory
+    (the input noise of learned particle simulators).  Leaves the handle at
+    the last training state."""
     rng = np.random.Generator(np.random.PCG64(seed))
     pairs = [(si, t) for si, s in enumerate(snap_sets) for t in range(len(s) - 1)]
     hist = []
@@ -109,6 +124,8 @@ def train(sim, snap_sets, iters: int, lr: float = 1e-3, lr_final: float = 5e-5, 
         si, t = pairs[rng.integers(len(pairs))]
         s = snap_sets[si]
         sim.load_snapshot(*s.ptrs(t))
+        if noise is not None:
+            sim.perturb(noise[0], noise[1], seed * 1_000_003 + it)
         frac = it / max(iters - 1, 1)
         lr_t = lr_final + 0.5 * (lr - lr_final) * (1 + np.cos(np.pi * frac))
         loss, _ = sim.surrogate_train_step(*s.ptrs(t + 1), lr=lr_t, update=True)

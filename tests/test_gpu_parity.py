@@ -355,3 +355,26 @@ def test_pinned_buffers_are_read_and_written_in_place(sphmod):
 
 def p_skin(w):
     return w.params["skin"]
+
+
+def test_perturbation_is_seeded_keyed_on_particle_id_and_fluid_only(sphmod):
+    """sph_perturb_state: the same seed gives the same state whatever the
+    particle order (a handle whose lists were rebuilt in another order), walls
+    are untouched, and the velocity noise has the requested spread."""
+    w = WL.drop_tank(3, (20, 20, 30), drop_d_dx=10, seed=93, perturb=True)
+    a = sphmod.Simulation.from_workload(w)
+    b = sphmod.Simulation.from_workload(w)
+    b.run(WL.stable_dt(w.params), 3)
+    b.set_state(w.x, w.u, w.rho)          # same state, another sorted order
+    a.perturb(0.01, 1e-4, 12345)
+    b.perturb(0.01, 1e-4, 12345)
+    ua, ub = a.read("vel"), b.read("vel")
+    assert np.array_equal(ua, ub) and np.array_equal(a.read("rho"), b.read("rho"))
+    wl = w.wall == 1
+    assert np.array_equal(ua[wl], w.u[wl])
+    du = (ua - w.u)[~wl]
+    assert abs(du.std() / 0.01 - 1) < 0.02 and abs(du.mean()) < 1e-3
+    dr = (a.read("rho") / w.rho - 1)[~wl]
+    assert abs(dr.std() / 1e-4 - 1) < 0.05
+    a.close()
+    b.close()
