@@ -50,6 +50,8 @@ extern "C" {
 #define SPH_ETIMEOUT   -8  /* a grid barrier of the persistent kernel gave up after one second */
 #define SPH_EFALLBACK  -9  /* the judge rejected a surrogate jump; the state holds the plain
                               method's result (sph_surrogate_advance_judged), not a failure */
+#define SPH_EBOUNDS   -10  /* an index read from device data was out of range (reported by the
+                              bounds-checked build only; the access was skipped) */
 
 /* Viscous term forms (Sec. II-C) */
 #define SPH_VISC_DYNAMIC   0  /* Eq. visc_2: (1/rho_i) sum 2 mu_ij (m_j/rho_j) (r.gradW)/(r^2+delta^2) u_ij */

@@ -209,6 +209,7 @@ __device__ __forceinline__ bool edge_features(const Dev &d, const Grid &g, float
                                               float (&ef)[2 * DIM + 3])
 {
     j = (int)(e & NBR_IDX_MASK);
+    if (!SPH_IN_RANGE(d.flags, j, d.n)) return false;
     const float4 oj = d.pos[j];
     float rx, ry, rz;
     const float r2 = pair_vec<DIM>(oi, oj, entry_shift(e, 0, g.Es), entry_shift(e, 1, g.Es),
@@ -236,6 +237,7 @@ __device__ __forceinline__ bool edge_geom(const Dev &d, const Grid &g, float R2,
                                           int phi, unsigned e, int &j, float (&ef)[DIM + 2])
 {
     j = (int)(e & NBR_IDX_MASK);
+    if (!SPH_IN_RANGE(d.flags, j, d.n)) return false;
     const float4 oj = d.pos[j];
     float rx, ry, rz;
     const float r2 = pair_vec<DIM>(oi, oj, entry_shift(e, 0, g.Es), entry_shift(e, 1, g.Es),

@@ -338,6 +338,7 @@ int sph_sim::check_flags()
     // also sends particles out of the box or produces non-finite values
     if (f & FLAG_SKIN) return fail(SPH_ECFL, "a particle moved beyond the cell skin within a step; reduce dt or enlarge cell_size");
     if (f & FLAG_NONFINITE) return fail(SPH_ENONFINITE, "a non-finite value appeared in the particle state");
+    if (f & FLAG_BOUNDS) return fail(SPH_EBOUNDS, "an index read from device data was out of range (bounds-checked build)");
     if (f & FLAG_LIST) return fail(SPH_ECAPACITY, "a particle has more neighbours than max_neighbours");
     return fail(SPH_EDOMAIN, "a particle left the box covered by the cell grid");
 }
@@ -387,6 +388,7 @@ __global__ void k_load_state(Dev d, Grid g, Phys ph, const double *x, const doub
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= d.n) return;
     const int k = d.inv[p];
+    if (!SPH_IN_RANGE(d.flags, k, d.n)) return;
     const Inst &I = d.inst[d.iid[k]];
     const uint8_t tg = d.tag[k];
     double xa[3] = {0, 0, 0}, ua[3] = {0, 0, 0};
@@ -900,6 +902,8 @@ int create_sim(const sph_params *params, int k, const int64_t *counts, const dou
     }
     if (err) return cleanup(SPH_ENOMEM);
     s->sort.ncell = (int)ncell;
+    s->sort.n = (int)n;
+    s->sort.flags = s->flags;
     Dev &a1 = s->buf[1];
     a1.cell = a0.cell; a1.pos0 = a0.pos0;
     a1.pos = a0.pos; a1.vd = a0.vd; a1.posv = a0.posv; a1.velp = a0.velp; a1.velq = a0.velq; a1.pres = a0.pres;

@@ -44,8 +44,20 @@ enum : unsigned {
     FLAG_SKIN = 4u,       // predictor displacement beyond the skin
     FLAG_LIST = 8u,       // a particle has more list neighbours than max_neighbours
     FLAG_TIMEOUT = 16u,   // a grid barrier of the persistent kernel gave up waiting
+    FLAG_BOUNDS = 32u,    // an index out of range (bounds-checked builds only)
 };
-constexpr unsigned FLAG_ERRORS = 31u;
+constexpr unsigned FLAG_ERRORS = 63u;
+
+// Bounds-checked build (-DSPH_CHECKED): every index read from device data
+// (list entries, sort slots, permutations) is tested before it is used; a bad
+// one raises FLAG_BOUNDS and the access is skipped instead of made.  Off in the
+// ordinary build, where the indices are correct by construction.
+#ifdef SPH_CHECKED
+#define SPH_IN_RANGE(flags, i, n) \
+    (((unsigned)(i) < (unsigned)(n)) ? true : (atomicOr((flags), FLAG_BOUNDS), false))
+#else
+#define SPH_IN_RANGE(flags, i, n) true
+#endif
 
 // Constants shared by all instances, FP32 unless they feed an FP64 accumulator.
 struct Phys {
@@ -183,6 +195,8 @@ struct Sort {
     int *perm;          // n, pre-sort index at each sorted position
     int *tile_sums;     // scan tiles
     int ncell;
+    int n;              // particles
+    unsigned *flags;    // the simulation's error word (bounds-checked builds)
 };
 
 // Neighbour-list entries a sweep loads ahead of use (one chunk in flight
@@ -532,7 +546,8 @@ __device__ __forceinline__ void scan_tile_sums(int *tile_sums, int ntiles, int *
 
 __device__ __forceinline__ void scatter_one(const Sort &s, const int *cstart, int k)
 {
-    s.tmp[cstart[s.cell_tmp[k]] + s.slot[k]] = k;
+    const int t = cstart[s.cell_tmp[k]] + s.slot[k];
+    if (SPH_IN_RANGE(s.flags, t, s.n)) s.tmp[t] = k;
 }
 
 // Final position of each particle inside its cell: its rank by original id
@@ -545,7 +560,7 @@ __device__ __forceinline__ void rank_one(const Sort &s, const int *pid, const in
     const int me = pid[k];
     int rank = 0;
     for (int q = b; q < e; ++q) rank += pid[s.tmp[q]] < me;
-    s.perm[b + rank] = k;
+    if (SPH_IN_RANGE(s.flags, b + rank, s.n)) s.perm[b + rank] = k;
 }
 
 // Stage-1 records of particle k from its FP64 state.
@@ -568,6 +583,7 @@ __device__ __forceinline__ void gather_one(const Dev &src, const Dev &dst, const
 {
     const int n = src.n;
     const int o = s.perm[k];
+    if (!SPH_IN_RANGE(src.flags, o, n)) return;
     double xa[3] = {0, 0, 0}, ua[3] = {0, 0, 0};
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
@@ -789,6 +805,7 @@ __device__ __forceinline__ void sweep_a_pairs(const Dev &d, const Grid &g, const
         for (int c = 0; c < CH; ++c) {
             const unsigned e = ec[c];
             const int j = (int)(e & NBR_IDX_MASK);
+            if (!SPH_IN_RANGE(d.flags, j, n)) continue;
             const float4 oj = ld<NC>(pos + j);
             float rx, ry, rz;
             const float r2 = entry_vec<DIM>(oi, oj, e, cs, rx, ry, rz);
@@ -916,6 +933,7 @@ __device__ __forceinline__ void sweep_b_one(const Dev &d, const Grid &g, const P
         for (int c = 0; c < CH; ++c) {
             const unsigned e = ec[c];
             const int j = (int)(e & NBR_IDX_MASK);
+            if (!SPH_IN_RANGE(d.flags, j, n)) continue;
             const float4 oj = ld<NC>(posv + j);
             const float4 uj = ld<NC>(vel_s + j);
             float rx, ry, rz;
@@ -1340,6 +1358,7 @@ static __global__ void __launch_bounds__(256) k_unpermute(Dev d, int kind, doubl
     if (p >= d.n) return;
     const int n = d.n;
     const int k = d.inv[p];
+    if (!SPH_IN_RANGE(d.flags, k, n)) return;
     const int phs = d.tag[k] & 1;
     const Inst &I = d.inst[d.iid[k]];
     switch (kind) {

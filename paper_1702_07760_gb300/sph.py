@@ -17,7 +17,8 @@ LIB_PATH = os.path.join(_HERE, "libsph.so")
 SPH_OK = 0
 SPH_EFALLBACK = -9
 ERRORS = {-1: "SPH_EINVAL", -2: "SPH_ENOMEM", -3: "SPH_ECUDA", -4: "SPH_ENONFINITE",
-          -5: "SPH_ECFL", -6: "SPH_EDOMAIN", -7: "SPH_ECAPACITY", -8: "SPH_ETIMEOUT", -9: "SPH_EFALLBACK"}
+          -5: "SPH_ECFL", -6: "SPH_EDOMAIN", -7: "SPH_ECAPACITY", -8: "SPH_ETIMEOUT", -9: "SPH_EFALLBACK",
+          -10: "SPH_EBOUNDS"}
 VISC_DYNAMIC, VISC_KINEMATIC = 0, 1
 FIELD = dict(pos=0, vel=1, rho=2, rho_eval=3, pressure=4, acc=5, drho=6, tensor=7, cell=8, order=9)
 
