@@ -232,8 +232,12 @@ int sph_eval_rates(sph_handle h);
 int sph_step(sph_handle h, double dt);
 
 /* nsteps steps of size dt, then waits for the stream and reports any device
- * error.  With graph != 0 the per-step launch sequence is captured once into
- * a CUDA graph and replayed. */
+ * error.  With graph != 0 one step is captured once into a CUDA graph and
+ * replayed: a one-thread kernel copies the device rebuild flag into the
+ * condition of a conditional (IF) node whose body is the cell-list chain, so
+ * steps without a list build launch five kernels instead of fourteen.  The
+ * eager form (graph == 0) launches all fourteen, the cell-list kernels
+ * returning at once without a build; both compute the same bits. */
 int sph_run(sph_handle h, double dt, int64_t nsteps, int graph);
 
 /* The same nsteps steps as sph_run in ONE cooperative kernel launch: every

@@ -206,6 +206,7 @@ struct sph_sim {
     int enqueue_read(int kind, bool integer, void *out, size_t bytes, size_t staging_offset);
     void enqueue_eval(int stage, const float *drho_in, double dt);
     void enqueue_step(double dt);
+    int capture_step_graph(double dt);
     int persistent_shape(int bs, int grid_req, int *grid_out, PersistFn *fn_out);
     int launch_persistent(double dt, int nsteps);
     int check_flags();
@@ -276,6 +277,71 @@ void sph_sim::enqueue_step(double dt)
     Dev &d = buf[0];
     enqueue_eval(1, d.drho, dt);
     enqueue_eval(2, d.drho_stage, dt);
+}
+
+namespace {
+__global__ void k_rebuild_cond(cudaGraphConditionalHandle h, const unsigned *rebuild);
+}  // namespace
+
+// The replayed step as a graph: a one-thread kernel reads the rebuild flag
+// into the condition of an IF node whose body is the cell-list chain, then
+// the four sweeps.  On steps without a rebuild the chain is not launched at
+// all (its kernels would return at once, but ten launches of n/256 blocks
+// still cost several microseconds each).  The body's kernels keep their own
+// flag test, so the graph and the eager sequence compute the same.
+int sph_sim::capture_step_graph(double dt)
+{
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t cond_set = nullptr, cond = nullptr;
+    cudaGraphConditionalHandle h;
+    cudaGraphNodeParams cp = {};
+    size_t count = 1;
+    Dev &d = buf[0];
+    cudaError_t e = cudaGraphCreate(&g, 0);
+    if (e != cudaSuccess) return fail(SPH_ECUDA, std::string("graph create: ") + cudaGetErrorString(e));
+    auto bail = [&](const char *what, cudaError_t err) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(stream, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+            cudaGraph_t junk = nullptr;
+            cudaStreamEndCapture(stream, &junk);
+        }
+        cudaGraphDestroy(g);
+        return fail(SPH_ECUDA, std::string(what) + ": " + cudaGetErrorString(err));
+    };
+    if ((e = cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault)) != cudaSuccess)
+        return bail("conditional handle", e);
+    if ((e = cudaStreamBeginCaptureToGraph(stream, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
+        cudaSuccess)
+        return bail("graph capture", e);
+    k_rebuild_cond<<<1, 32, 0, stream>>>(h, rebuild);
+    if ((e = cudaStreamEndCapture(stream, &g)) != cudaSuccess) return bail("graph capture", e);
+    if ((e = cudaGraphGetNodes(g, &cond_set, &count)) != cudaSuccess || count != 1)
+        return bail("graph nodes", e);
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeIf;
+    cp.conditional.size = 1;
+    if ((e = cudaGraphAddNode(&cond, g, &cond_set, nullptr, 1, &cp)) != cudaSuccess)
+        return bail("conditional node", e);
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    if ((e = cudaStreamBeginCaptureToGraph(stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
+        cudaSuccess)
+        return bail("graph capture", e);
+    enqueue_build_cells(false);
+    if ((e = cudaStreamEndCapture(stream, &body)) != cudaSuccess) return bail("graph capture", e);
+    if ((e = cudaStreamBeginCaptureToGraph(stream, g, &cond, nullptr, 1, cudaStreamCaptureModeThreadLocal)) !=
+        cudaSuccess)
+        return bail("graph capture", e);
+    enqueue_eval(1, d.drho, dt);
+    enqueue_eval(2, d.drho_stage, dt);
+    if ((e = cudaStreamEndCapture(stream, &g)) != cudaSuccess) return bail("graph capture", e);
+    if ((e = cudaGraphInstantiate(&exec, g, 0)) != cudaSuccess) return bail("graph instantiate", e);
+    cudaGraphDestroy(g);
+    if (gexec) cudaGraphExecDestroy(gexec);
+    gexec = exec;
+    gdt = dt;
+    return SPH_OK;
 }
 
 // Grid and kernel build of a persistent launch of grid_req blocks of bs
@@ -366,6 +432,12 @@ __global__ void k_add_step(long long *step, long long k, double *clock, double e
         *step += k;
         clock[1] += elapsed;
     }
+}
+// Condition of the step graph's rebuild node: the device rebuild flag (set by
+// the corrector, by a forced build or by a change of dt).
+__global__ void k_rebuild_cond(cudaGraphConditionalHandle h, const unsigned *rebuild)
+{
+    if (threadIdx.x == 0) cudaGraphSetConditional(h, *rebuild != 0u ? 1u : 0u);
 }
 }  // namespace
 
@@ -1358,17 +1430,8 @@ int sph_run(sph_handle s, double dt, int64_t nsteps, int graph)
     s->last_dt = dt;
     if (use_graph) {
         if (!s->gexec || s->gdt != dt) {
-            cudaGraph_t gr = nullptr;
-            CU(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
-            s->enqueue_step(dt);
-            cudaError_t e = cudaStreamEndCapture(s->stream, &gr);
-            if (e != cudaSuccess) return fail(SPH_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-            if (s->gexec) cudaGraphExecDestroy(s->gexec);
-            s->gexec = nullptr;
-            e = cudaGraphInstantiate(&s->gexec, gr, 0);
-            cudaGraphDestroy(gr);
-            if (e != cudaSuccess) return fail(SPH_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
-            s->gdt = dt;
+            const int rc = s->capture_step_graph(dt);
+            if (rc != SPH_OK) return rc;
         }
         for (int64_t k = 0; k < nsteps; ++k) {
             CU(cudaGraphLaunch(s->gexec, s->stream));

@@ -218,6 +218,22 @@ __device__ __forceinline__ T ld(const T *p)
     else return *p;
 }
 
+// Neighbour-list entry load.  The list is streamed once per sweep (each
+// warp reads whole 128-byte lines of it), so in launches where it is
+// read-only its lines bypass L1 and leave the space to the neighbour records
+// that are gathered many times (measured 1 % faster on both sweeps).
+template <bool NC>
+__device__ __forceinline__ unsigned ld_list(const unsigned *p)
+{
+    if constexpr (NC) {
+        unsigned v;
+        asm("ld.global.nc.L1::no_allocate.b32 %0, [%1];" : "=r"(v) : "l"(p));
+        return v;
+    } else {
+        return *p;
+    }
+}
+
 // Read-only pointer, __restrict__ only where the pointee is not written
 // anywhere in the launch (NC): the persistent kernel writes every array in
 // some phase and must not let the compiler route its loads through the
@@ -794,12 +810,12 @@ __device__ __forceinline__ void sweep_a_pairs(const Dev &d, const Grid &g, const
     constexpr int CH = SPH_LIST_CHUNK;
     unsigned ec[CH];  // the first chunk lies inside the list storage (kmax >= CH) even when empty
 #pragma unroll
-    for (int c = 0; c < CH; ++c) ec[c] = ld<NC>(col + (size_t)c * n);
+    for (int c = 0; c < CH; ++c) ec[c] = ld_list<NC>(col + (size_t)c * n);
     for (int k0 = 0; k0 < cnt; k0 += CH) {
         unsigned en[CH];
         const bool more = k0 + CH < cnt;
 #pragma unroll
-        for (int c = 0; c < CH; ++c) en[c] = more ? ld<NC>(col + (size_t)(k0 + CH + c) * n) : 0u;
+        for (int c = 0; c < CH; ++c) en[c] = more ? ld_list<NC>(col + (size_t)(k0 + CH + c) * n) : 0u;
         float p1 = 0.f, p2 = 0.f;
 #pragma unroll
         for (int c = 0; c < CH; ++c) {
@@ -923,12 +939,12 @@ __device__ __forceinline__ void sweep_b_one(const Dev &d, const Grid &g, const P
     constexpr int CH = SPH_LIST_CHUNK;
     unsigned ec[CH];  // the first chunk lies inside the list storage (kmax >= CH) even when empty
 #pragma unroll
-    for (int c = 0; c < CH; ++c) ec[c] = ld<NC>(col + (size_t)c * n);
+    for (int c = 0; c < CH; ++c) ec[c] = ld_list<NC>(col + (size_t)c * n);
     for (int k0 = 0; k0 < cnt; k0 += CH) {
         unsigned en[CH];
         const bool more = k0 + CH < cnt;
 #pragma unroll
-        for (int c = 0; c < CH; ++c) en[c] = more ? ld<NC>(col + (size_t)(k0 + CH + c) * n) : 0u;
+        for (int c = 0; c < CH; ++c) en[c] = more ? ld_list<NC>(col + (size_t)(k0 + CH + c) * n) : 0u;
 #pragma unroll
         for (int c = 0; c < CH; ++c) {
             const unsigned e = ec[c];

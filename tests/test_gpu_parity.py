@@ -136,6 +136,27 @@ def test_graph_replay_is_bit_identical_to_eager(sphmod):
     assert a.step_index == b.step_index == 9
 
 
+@pytest.mark.parametrize("rebuild_every", [0, 3])
+def test_graph_conditional_rebuilds_match_eager(sphmod, rebuild_every):
+    """The replayed graph launches the cell-list chain only through its
+    conditional node: over many steps with several list builds (decided by
+    displacement, or every third step) it matches the eager sequence bit for
+    bit and builds the lists on the same steps."""
+    w = WL.drop_tank(3, (14, 15, 22), drop_d_dx=8, seed=97, perturb=True)
+    p = dict(w.params, rebuild_every=rebuild_every)
+    dt = WL.stable_dt(p)
+    a = sphmod.Simulation(p, w.x, w.u, w.rho, w.phase, w.wall)
+    b = sphmod.Simulation(p, w.x, w.u, w.rho, w.phase, w.wall)
+    for k in (1, 7, 40, 12):
+        a.run(dt, k, graph=False)
+        b.run(dt, k, graph=True)
+        assert a.list_builds == b.list_builds
+    for f in ("pos", "vel", "rho"):
+        assert np.array_equal(a.read(f), b.read(f)), f
+    assert a.step_index == b.step_index == 60
+    assert b.list_builds >= (20 if rebuild_every == 3 else 1)
+
+
 def test_restart_is_bit_exact(sphmod):
     """With a list build every step the particle order after a restart is
     the one the uninterrupted run has, so the runs agree bit for bit."""
