@@ -200,6 +200,7 @@ struct sph_sim {
     }
 
     int blocks(int work, int threads = 256) const { return (work + threads - 1) / threads; }
+    int sms = 0;  // multiprocessors of the device
 
     void enqueue_build_cells(bool force);
     void enqueue_load(const double *x, const double *u, const double *rho, double check_dt);
@@ -255,8 +256,15 @@ void sph_sim::enqueue_eval(int stage, const float *drho_in, double dt)
     float4 *vel_s = stage == 2 ? d.velq : d.velp;
     const int stage1 = stage != 2;
     launch(KI_SWEEP_A, [&] {
-        if (dim == 2) k_sweep_a<2><<<blocks(n), 256, 0, stream>>>(d, grid, phys, drho_in, stage1, vel_s);
-        else k_sweep_a<3><<<blocks(n), 256, 0, stream>>>(d, grid, phys, drho_in, stage1, vel_s);
+        if (stage1) {
+            if (dim == 2) k_sweep_a<2><<<blocks(n), 256, 0, stream>>>(d, grid, phys, drho_in, stage1, vel_s);
+            else k_sweep_a<3><<<blocks(n), 256, 0, stream>>>(d, grid, phys, drho_in, stage1, vel_s);
+        } else {
+            // warps for the mixed particles: up to eight blocks of eight per SM
+            const int mb = std::max(1, std::min(blocks(n), 8 * std::max(sms, 1)));
+            if (dim == 2) k_sweep_a2<2><<<mb + blocks(n), 256, 0, stream>>>(d, grid, phys, drho_in, vel_s, mb);
+            else k_sweep_a2<3><<<mb + blocks(n), 256, 0, stream>>>(d, grid, phys, drho_in, vel_s, mb);
+        }
     });
     launch(KI_SWEEP_B, [&] {
         if (dim == 2) {
@@ -944,6 +952,8 @@ int create_sim(const sph_params *params, int k, const int64_t *counts, const dou
         err |= s->alloc(&a0.nbr, N * (size_t)ph.kmax);
         err |= s->alloc(&a0.ncnt, N);
         err |= s->alloc(&a0.nflag, N);
+        err |= s->alloc(&a0.mixed, N);
+        err |= s->alloc(&a0.nmixed, 1);
         err |= s->alloc(&a0.drho_stage, N);
         err |= s->alloc(&a0.drho_eval, N);
         err |= s->alloc(&a0.T4, N);
@@ -979,7 +989,7 @@ int create_sim(const sph_params *params, int k, const int64_t *counts, const dou
     Dev &a1 = s->buf[1];
     a1.cell = a0.cell; a1.pos0 = a0.pos0;
     a1.pos = a0.pos; a1.vd = a0.vd; a1.posv = a0.posv; a1.velp = a0.velp; a1.velq = a0.velq; a1.pres = a0.pres;
-    a1.nbr = a0.nbr; a1.ncnt = a0.ncnt; a1.nflag = a0.nflag;
+    a1.nbr = a0.nbr; a1.ncnt = a0.ncnt; a1.nflag = a0.nflag; a1.mixed = a0.mixed; a1.nmixed = a0.nmixed;
     a1.drho_stage = a0.drho_stage; a1.drho_eval = a0.drho_eval;
     a1.T4 = a0.T4; a1.T2 = a0.T2; a1.acc = a0.acc; a1.cstart = a0.cstart;
     a0.flags = a1.flags = s->flags;
@@ -1001,6 +1011,12 @@ int create_sim(const sph_params *params, int k, const int64_t *counts, const dou
     if ((e = cudaMemsetAsync(s->flags, 0, sizeof(unsigned), st)) != cudaSuccess) return cuda_fail(e);
     if ((e = cudaMemsetAsync(s->dstep, 0, sizeof(long long), st)) != cudaSuccess) return cuda_fail(e);
     if ((e = cudaMemsetAsync(s->dbuilds, 0, sizeof(long long), st)) != cudaSuccess) return cuda_fail(e);
+    if ((e = cudaMemsetAsync(a0.nmixed, 0, sizeof(int), st)) != cudaSuccess) return cuda_fail(e);
+    {
+        int dev = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return cuda_fail(e);
+        if ((e = cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return cuda_fail(e);
+    }
     if ((e = cudaMemsetAsync(s->bar, 0, sizeof(GridBarrier), st)) != cudaSuccess) return cuda_fail(e);
     if ((e = cudaMemsetAsync(s->clock, 0, 2 * sizeof(double), st)) != cudaSuccess) return cuda_fail(e);
     if ((e = cudaMemsetAsync(s->motion, 0, sizeof(Motion), st)) != cudaSuccess) return cuda_fail(e);

@@ -134,6 +134,8 @@ struct Dev {
     unsigned *nbr;      // kmax * n, entry k of particle i at nbr[k * n + i]
     int *ncnt;          // n, list length
     uint8_t *nflag;     // n, bit0: an other-phase particle lies within the list radius
+    int *mixed;         // n, the particles with nflag bit 0 set, in no particular order
+    int *nmixed;        // 1 word: their number (reset by the hash, appended by the list build)
     // cell list
     int *cstart;        // ncell + 1
     unsigned *flags;    // 1 word
@@ -454,6 +456,7 @@ __device__ __forceinline__ float signed_volume(const Inst &I, int phase, float d
 template <int DIM>
 __device__ __forceinline__ void hash_one(const Dev &d, const Grid &g, const Sort &s, int k)
 {
+    if (k == 0) *d.nmixed = 0;  // the list build that follows appends the mixed particles
     const int dims[3] = {g.nx, g.ny, g.nz};
     int c[3] = {0, 0, 0};
     unsigned bad = 0;
@@ -665,6 +668,7 @@ __device__ __forceinline__ void list_one(const Dev &d, const Grid &g, const Phys
     for (; cnt % SPH_LIST_CHUNK; ++cnt) nbr[(size_t)cnt * n + i] = pad_entry(i);
     d.ncnt[i] = cnt;
     d.nflag[i] = (uint8_t)other;
+    if (other) d.mixed[atomicAdd(d.nmixed, 1)] = i;
 }
 
 // ---------------------------------------------------------------------------
@@ -853,26 +857,81 @@ __device__ __forceinline__ void sweep_a_pairs(const Dev &d, const Grid &g, const
     }
 }
 
+template <int DIM>
+__device__ __forceinline__ void sweep_a_finish(const Dev &d, const Phys &ph, int i, const float4 &oi, int phi_,
+                                               float drho, float gx, float gy, float gz, float4 *vel_s);
+
+// skip_mixed (stage 2): the particles with an other-phase neighbour are left
+// to the warp-per-particle pass (sweep_a_mixed_warp).
 template <int DIM, bool NC>
 __device__ __forceinline__ void sweep_a_one(const Dev &d, const Grid &g, const Phys &ph, const float *drho_in,
-                                            int renorm, float4 *vel_s, int i)
+                                            int renorm, bool skip_mixed, float4 *vel_s, int i)
 {
+    const bool other = d.nflag[i] & 1;
+    if (skip_mixed && other) return;
     const float4 oi = d.pos[i];
     const int phi_ = phase_of(oi.w);
-    const Inst &I = d.inst[d.iid[i]];
     // self term: W(0)/alpha_d = 1
     float s1 = fabsf(oi.w), c1 = 0.f, s2 = d.vd[i], c2 = 0.f;
     float gx = 0.f, gy = 0.f, gz = 0.f;
-    const bool other = d.nflag[i] & 1;
     // particles with no other-phase neighbour (the bulk) take the loop
     // without the per-pair phase test
     if (other) sweep_a_pairs<DIM, NC, true>(d, g, ph, i, oi, phi_, renorm, s1, c1, s2, c2, gx, gy, gz);
     else if (renorm) sweep_a_pairs<DIM, NC, false>(d, g, ph, i, oi, phi_, 1, s1, c1, s2, c2, gx, gy, gz);
-    const float drho = renorm ? s2 / s1 : drho_in[i];
+    sweep_a_finish<DIM>(d, ph, i, oi, phi_, renorm ? s2 / s1 : drho_in[i], gx, gy, gz, vel_s);
+}
+
+// Sweep A at stage 2 (no renormalisation: only the colour gradient) for a
+// particle with an other-phase neighbour, by one whole warp: lane l takes the
+// list entries l, l + 32, ... and the three sums are combined by a butterfly
+// of shuffles (every lane ends with the same bits).  These particles are a
+// thin shell around the interface; a thread each would leave most lanes of
+// their warps idle while one walks a whole list.
+template <int DIM, bool NC>
+__device__ __forceinline__ void sweep_a_mixed_warp(const Dev &d, const Grid &g, const Phys &ph, const float *drho_in,
+                                                   float4 *vel_s, int i, int lane)
+{
+    const float4 oi = d.pos[i];
+    const int phi_ = phase_of(oi.w);
+    const float inv_h = ph.inv_h, cs = g.Es;
+    const int n = d.n, cnt = d.ncnt[i];
+    typename RO<NC, float4>::type pos = d.pos;
+    float gx = 0.f, gy = 0.f, gz = 0.f;
+    for (int k = lane; k < cnt; k += 32) {
+        const unsigned e = ld_list<NC>(d.nbr + (size_t)k * n + i);
+        const int j = (int)(e & NBR_IDX_MASK);
+        if (!SPH_IN_RANGE(d.flags, j, n)) continue;
+        const float4 oj = ld<NC>(pos + j);
+        if (phase_of(oj.w) == phi_) continue;
+        float rx, ry, rz;
+        const float r2 = entry_vec<DIM>(oi, oj, e, cs, rx, ry, rz);
+        const float r = r2 * rsqrtf(fmaxf(r2, 1e-30f));
+        const float t = fmaxf(fmaf(-0.5f * inv_h, r, 1.f), 0.f);
+        const float cc = oj.w * oj.w * (t * t * t);
+        gx = fmaf(cc, rx, gx);
+        gy = fmaf(cc, ry, gy);
+        if (DIM == 3) gz = fmaf(cc, rz, gz);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        gx += __shfl_xor_sync(0xffffffffu, gx, o);
+        gy += __shfl_xor_sync(0xffffffffu, gy, o);
+        if (DIM == 3) gz += __shfl_xor_sync(0xffffffffu, gz, o);
+    }
+    if (lane == 0) sweep_a_finish<DIM>(d, ph, i, oi, phi_, drho_in[i], gx, gy, gz, vel_s);
+}
+
+// Sweep A's per-particle tail: stage density, equation of state, surface
+// tensor, and the records the force sweep gathers.
+template <int DIM>
+__device__ __forceinline__ void sweep_a_finish(const Dev &d, const Phys &ph, int i, const float4 &oi, int phi_,
+                                               float drho, float gx, float gy, float gz, float4 *vel_s)
+{
+    const Inst &I = d.inst[d.iid[i]];
     d.drho_eval[i] = drho;
     const float rho = by_phase(phi_, I.rho0) + drho;
     const float vol = by_phase(phi_, I.mass) / rho;
-    const float P = eos_tait7(by_phase(phi_, I.beta), drho * by_phase(phi_, I.inv_rho0));
+    const float P = eos_tait7(by_phase(phi_, I.beta), __fmul_rn(drho, by_phase(phi_, I.inv_rho0)));
     // grad C_i = sigma_i sum V_j^2 grad W_ij, sigma_i = 1/|V_i| (entry density)
     const float sc = ph.cF / fabsf(oi.w);
     gx *= sc;
@@ -1119,7 +1178,38 @@ static __global__ void __launch_bounds__(256) k_sweep_a(Dev d, Grid g, Phys ph, 
         d.clock[0] += d.clock[1];
         d.clock[1] = 0.0;
     }
-    sweep_a_one<DIM, true>(d, g, ph, drho_in, renorm, vel_s, i);
+    sweep_a_one<DIM, true>(d, g, ph, drho_in, renorm, false, vel_s, i);
+}
+
+// Warps [0, 8 mixed_blocks) of the launch take the mixed particles one at a
+// time (warp-stride over the mixed list).
+template <int DIM, bool NC>
+__device__ __forceinline__ void mixed_pass(const Dev &d, const Grid &g, const Phys &ph, const float *drho_in,
+                                           float4 *vel_s, int warp, int nwarps, int lane)
+{
+    const int nm = min(*d.nmixed, d.n);
+    for (int w = warp; w < nm; w += nwarps) {
+        const int i = d.mixed[w];
+        if (!SPH_IN_RANGE(d.flags, i, d.n)) continue;
+        sweep_a_mixed_warp<DIM, NC>(d, g, ph, drho_in, vel_s, i, lane);
+    }
+}
+
+// Sweep A at stage 2: the first mixed_blocks blocks run the warp-per-particle
+// pass over the mixed particles (launched first, so it overlaps the rest),
+// the others a thread per particle for the remaining ones.
+template <int DIM>
+static __global__ void __launch_bounds__(256) k_sweep_a2(Dev d, Grid g, Phys ph, const float *__restrict__ drho_in,
+                                                  float4 *vel_s, int mixed_blocks)
+{
+    if ((int)blockIdx.x < mixed_blocks) {
+        mixed_pass<DIM, true>(d, g, ph, drho_in, vel_s, (int)(blockIdx.x * blockDim.x + threadIdx.x) >> 5,
+                              (int)(mixed_blocks * blockDim.x) >> 5, (int)threadIdx.x & 31);
+        return;
+    }
+    const int i = (int)(blockIdx.x - mixed_blocks) * blockDim.x + threadIdx.x;
+    if (i >= d.n) return;
+    sweep_a_one<DIM, true>(d, g, ph, drho_in, 0, true, vel_s, i);
 }
 
 // Resident blocks of 256 threads per SM the force sweep is compiled for (4:
@@ -1296,11 +1386,12 @@ __device__ __forceinline__ void persistent_steps(Dev d, Dev scratch, Grid g, Phy
             d.clock[0] += d.clock[1];
             d.clock[1] = 0.0;
         }
-        for_each_particle(bar, n, dyn, [&](int i) { sweep_a_one<DIM, false>(d, g, ph, d.drho, renorm, d.velp, i); });
+        for_each_particle(bar, n, dyn, [&](int i) { sweep_a_one<DIM, false>(d, g, ph, d.drho, renorm, false, d.velp, i); });
         if (grid_sync(bar, d.flags) & FLAG_ERRORS) return;
         for_each_particle(bar, n, dyn, [&](int i) { sweep_b_one<DIM, 1, false>(d, g, ph, dt, i); });
         if (grid_sync(bar, d.flags) & FLAG_ERRORS) return;
-        for_each_particle(bar, n, dyn, [&](int i) { sweep_a_one<DIM, false>(d, g, ph, d.drho_stage, 0, d.velq, i); });
+        for_each_particle(bar, n, dyn, [&](int i) { sweep_a_one<DIM, false>(d, g, ph, d.drho_stage, 0, true, d.velq, i); });
+        mixed_pass<DIM, false>(d, g, ph, d.drho_stage, d.velq, tid >> 5, stride >> 5, (int)threadIdx.x & 31);
         if (grid_sync(bar, d.flags) & FLAG_ERRORS) return;
         for_each_particle(bar, n, dyn, [&](int i) { sweep_b_one<DIM, 2, false>(d, g, ph, dt, i); });
         if (grid_sync(bar, d.flags) & FLAG_ERRORS) return;
