@@ -298,6 +298,18 @@ int sph_read(sph_handle h, int field, void *host_out, int64_t bytes);
  * flags like sph_sync. */
 int sph_read_state(sph_handle h, double *x, double *u, double *rho);
 
+/* Advances a state held by the caller: loads (x, u, rho) as sph_set_state
+ * does, runs nsteps graph-replayed steps of dt as sph_run does, and writes
+ * the resulting state to (x_out, u_out, rho_out) as sph_read_state does — all
+ * queued on the handle's stream with one wait at the end instead of one per
+ * call.  Layouts are those of sph_create (original particle order, x and u
+ * n*dim, rho n); host memory (pinned is fastest) goes through the staging
+ * copies, device or managed memory is used in place.  The outputs may be the
+ * inputs.  Returns SPH_EINVAL for a NULL array, a non-positive or non-finite
+ * dt or a negative nsteps, and reports device error flags like sph_sync. */
+int sph_advance_host(sph_handle h, double dt, int64_t nsteps, const double *x, const double *u, const double *rho,
+                     double *x_out, double *u_out, double *rho_out);
+
 /* Neighbour sets at the current positions (rebuilds the cell list, which
  * invalidates the eval fields) as computed by the GPU's own
  * candidate test (j != i and |r_ij|^2 < (2h)^2 in the kernels' arithmetic),

@@ -208,6 +208,9 @@ struct sph_sim {
     void enqueue_eval(int stage, const float *drho_in, double dt);
     void enqueue_step(double dt);
     int capture_step_graph(double dt);
+    int enqueue_set_state(const double *x, const double *u, const double *rho);
+    int enqueue_run(double dt, int64_t nsteps, bool graph);
+    int enqueue_read_state(double *x, double *u, double *rho);
     int persistent_shape(int bs, int grid_req, int *grid_out, PersistFn *fn_out);
     int launch_persistent(double dt, int nsteps);
     int check_flags();
@@ -1217,31 +1220,39 @@ int sph_create_batch(int k, const sph_params *params, const int64_t *counts, con
     return create_sim(params, k, counts, x, u, rho, phase, wall, stream, out);
 }
 
+// Queues the upload and load of a state (original order) without waiting.
+int sph_sim::enqueue_set_state(const double *x, const double *u, const double *rho)
+{
+    const size_t nn = (size_t)n, dd = (size_t)dim;
+    const double *dx = device_view(x), *du = device_view(u), *dr = device_view(rho);
+    if (!dx) {
+        dx = read_buf;
+        CU(cudaMemcpyAsync(read_buf, x, sizeof(double) * nn * dd, cudaMemcpyHostToDevice, stream));
+    }
+    if (!du) {
+        du = read_buf + nn * dd;
+        CU(cudaMemcpyAsync(read_buf + nn * dd, u, sizeof(double) * nn * dd, cudaMemcpyHostToDevice, stream));
+    }
+    if (!dr) {
+        dr = read_buf + 2 * nn * dd;
+        CU(cudaMemcpyAsync(read_buf + 2 * nn * dd, rho, sizeof(double) * nn, cudaMemcpyHostToDevice, stream));
+    }
+    // the lists are kept when they still hold the new state (tested against the
+    // skin with the last step size; a fixed rebuild cadence or no step yet rebuilds)
+    const double check_dt = P.rebuild_every == 0 ? last_dt : 0.0;
+    enqueue_load(dx, du, dr, check_dt);
+    CU(cudaGetLastError());
+    if (!(check_dt > 0)) CU(cudaMemsetAsync(rebuild, 0xff, sizeof(unsigned), stream));
+    return SPH_OK;
+}
+
 int sph_set_state(sph_handle s, const double *x, const double *u, const double *rho)
 {
     if (!s) return fail(SPH_EINVAL, "handle is NULL");
     if (s->n == 0) return SPH_OK;
     if (!x || !u || !rho) return fail(SPH_EINVAL, "an input array is NULL");
-    const size_t n = (size_t)s->n, dim = (size_t)s->dim;
-    const double *dx = device_view(x), *du = device_view(u), *dr = device_view(rho);
-    if (!dx) {
-        dx = s->read_buf;
-        CU(cudaMemcpyAsync(s->read_buf, x, sizeof(double) * n * dim, cudaMemcpyHostToDevice, s->stream));
-    }
-    if (!du) {
-        du = s->read_buf + n * dim;
-        CU(cudaMemcpyAsync(s->read_buf + n * dim, u, sizeof(double) * n * dim, cudaMemcpyHostToDevice, s->stream));
-    }
-    if (!dr) {
-        dr = s->read_buf + 2 * n * dim;
-        CU(cudaMemcpyAsync(s->read_buf + 2 * n * dim, rho, sizeof(double) * n, cudaMemcpyHostToDevice, s->stream));
-    }
-    // the lists are kept when they still hold the new state (tested against the
-    // skin with the last step size; a fixed rebuild cadence or no step yet rebuilds)
-    const double check_dt = s->P.rebuild_every == 0 ? s->last_dt : 0.0;
-    s->enqueue_load(dx, du, dr, check_dt);
-    CU(cudaGetLastError());
-    if (!(check_dt > 0)) CU(cudaMemsetAsync(s->rebuild, 0xff, sizeof(unsigned), s->stream));
+    const int rc = s->enqueue_set_state(x, u, rho);
+    if (rc != SPH_OK) return rc;
     CU(cudaStreamSynchronize(s->stream));
     return SPH_OK;
 }
@@ -1441,27 +1452,35 @@ int sph_run(sph_handle s, double dt, int64_t nsteps, int graph)
         s->step += nsteps;
         return SPH_OK;
     }
-    const bool use_graph = graph && !s->timing;
-    if (dt != s->last_dt) CU(cudaMemsetAsync(s->rebuild, 0xff, sizeof(unsigned), s->stream));
-    s->last_dt = dt;
+    const int rc = s->enqueue_run(dt, nsteps, graph != 0);
+    if (rc != SPH_OK) return rc;
+    return s->check_flags();
+}
+
+// Queues nsteps steps (graph-replayed when graph) without waiting.
+int sph_sim::enqueue_run(double dt, int64_t nsteps, bool graph)
+{
+    const bool use_graph = graph && !timing;
+    if (dt != last_dt) CU(cudaMemsetAsync(rebuild, 0xff, sizeof(unsigned), stream));
+    last_dt = dt;
     if (use_graph) {
-        if (!s->gexec || s->gdt != dt) {
-            const int rc = s->capture_step_graph(dt);
+        if (!gexec || gdt != dt) {
+            const int rc = capture_step_graph(dt);
             if (rc != SPH_OK) return rc;
         }
         for (int64_t k = 0; k < nsteps; ++k) {
-            CU(cudaGraphLaunch(s->gexec, s->stream));
-            s->step += 1;
+            CU(cudaGraphLaunch(gexec, stream));
+            step += 1;
         }
     } else {
         for (int64_t k = 0; k < nsteps; ++k) {
-            s->enqueue_step(dt);
+            enqueue_step(dt);
             CU(cudaGetLastError());
-            s->step += 1;
+            step += 1;
         }
     }
-    if (nsteps > 0) s->evaluated = true;
-    return s->check_flags();
+    if (nsteps > 0) evaluated = true;
+    return SPH_OK;
 }
 
 int sph_run_persistent(sph_handle s, double dt, int64_t nsteps, int graph)
@@ -1679,17 +1698,46 @@ int sph_read(sph_handle s, int field, void *host_out, int64_t bytes)
     return SPH_OK;
 }
 
+// Queues the unpermuted reads of x, u and rho without waiting.
+int sph_sim::enqueue_read_state(double *x, double *u, double *rho)
+{
+    const size_t nn = (size_t)n, dd = (size_t)dim;
+    int rc = enqueue_read(RK_X, false, x, nn * dd * 8, 0);
+    if (!rc) rc = enqueue_read(RK_U, false, u, nn * dd * 8, nn * dd);
+    if (!rc) rc = enqueue_read(RK_RHO, false, rho, nn * 8, 2 * nn * dd);
+    return rc;
+}
+
 int sph_read_state(sph_handle s, double *x, double *u, double *rho)
 {
     if (!s) return fail(SPH_EINVAL, "handle is NULL");
     if (s->n == 0) return SPH_OK;
     if (!x || !u || !rho) return fail(SPH_EINVAL, "an output array is NULL");
-    const size_t n = (size_t)s->n, dim = (size_t)s->dim;
-    int rc = s->enqueue_read(RK_X, false, x, n * dim * 8, 0);
-    if (!rc) rc = s->enqueue_read(RK_U, false, u, n * dim * 8, n * dim);
-    if (!rc) rc = s->enqueue_read(RK_RHO, false, rho, n * 8, 2 * n * dim);
+    const int rc = s->enqueue_read_state(x, u, rho);
     if (rc) return rc;
-    CU(cudaStreamSynchronize(s->stream));
+    return s->check_flags();
+}
+
+int sph_advance_host(sph_handle s, double dt, int64_t nsteps, const double *x, const double *u, const double *rho,
+                     double *x_out, double *u_out, double *rho_out)
+{
+    NvtxScope nvtx_scope("sph_advance_host");
+    if (!s) return fail(SPH_EINVAL, "handle is NULL");
+    if (!(dt > 0) || !std::isfinite(dt)) return fail(SPH_EINVAL, "dt must be positive and finite");
+    if (nsteps < 0) return fail(SPH_EINVAL, "nsteps must be >= 0");
+    if (!x || !u || !rho) return fail(SPH_EINVAL, "an input array is NULL");
+    if (!x_out || !u_out || !rho_out) return fail(SPH_EINVAL, "an output array is NULL");
+    if (s->n == 0) {
+        s->step += nsteps;
+        return SPH_OK;
+    }
+    int rc = s->enqueue_set_state(x, u, rho);
+    if (rc == SPH_OK) rc = s->enqueue_run(dt, nsteps, true);
+    if (rc == SPH_OK) rc = s->enqueue_read_state(x_out, u_out, rho_out);
+    if (rc != SPH_OK) {
+        cudaStreamSynchronize(s->stream);
+        return rc;
+    }
     return s->check_flags();
 }
 

@@ -32,7 +32,7 @@ EXPORTS = ["sph_create", "sph_set_state", "sph_build_cells", "sph_eval_rates", "
            "sph_num_instances", "sph_test_stall_barrier", "sph_mm_bf16", "sph_snapshot", "sph_load_snapshot",
            "sph_surrogate_init", "sph_surrogate_get_weights", "sph_surrogate_predict", "sph_surrogate_advance",
            "sph_surrogate_train_step", "sph_surrogate_run", "sph_create_dev", "sph_set_piston", "sph_get_time",
-           "sph_set_time", "sph_suggest_dt", "sph_surrogate_advance_judged", "sph_read_state",
+           "sph_set_time", "sph_suggest_dt", "sph_surrogate_advance_judged", "sph_read_state", "sph_advance_host",
            "sph_oil_occupancy_diff", "sph_surrogate_set_interface_tol", "sph_surrogate_judge_stats",
            "sph_perturb_state"]
 
@@ -74,6 +74,7 @@ def load(path: str = LIB_PATH):
     L.sph_run.argtypes = [H, C.c_double, C.c_int64, C.c_int]
     L.sph_read.argtypes = [H, C.c_int, vp, C.c_int64]
     L.sph_read_state.argtypes = [H, dp, dp, dp]
+    L.sph_advance_host.argtypes = [H, C.c_double, C.c_int64, dp, dp, dp, dp, dp, dp]
     L.sph_oil_occupancy_diff.argtypes = [H, H, dp]
     L.sph_perturb_state.argtypes = [H, C.c_double, C.c_double, C.c_uint64]
     L.sph_surrogate_set_interface_tol.argtypes = [H, C.c_double]
@@ -398,6 +399,19 @@ class Simulation:
             if a.shape != shape or a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
                 raise ValueError(f"expected a C-contiguous float64 array of shape {shape}")
         _check(load().sph_read_state(self._h, _dp(x), _dp(u), _dp(rho)))
+
+    def advance_host(self, dt: float, nsteps: int, x: np.ndarray, u: np.ndarray, rho: np.ndarray,
+                     out=None):
+        """Loads (x, u, rho), runs nsteps graph-replayed steps and writes the
+        result into `out` = (x, u, rho) arrays (default: the inputs) with one
+        call and one wait (sph_advance_host)."""
+        n, d = self.n, self.dim
+        xo, uo, ro = (x, u, rho) if out is None else out
+        for a, shape in ((x, (n, d)), (u, (n, d)), (rho, (n,)), (xo, (n, d)), (uo, (n, d)), (ro, (n,))):
+            if a.shape != shape or a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+                raise ValueError(f"expected a C-contiguous float64 array of shape {shape}")
+        _check(load().sph_advance_host(self._h, float(dt), int(nsteps), _dp(x), _dp(u), _dp(rho),
+                                       _dp(xo), _dp(uo), _dp(ro)))
 
     def read(self, field: str, out: np.ndarray | None = None) -> np.ndarray:
         """Copies a field in original particle order into `out` (a C-contiguous

@@ -157,6 +157,39 @@ def test_graph_conditional_rebuilds_match_eager(sphmod, rebuild_every):
     assert b.list_builds >= (20 if rebuild_every == 3 else 1)
 
 
+def test_advance_host_equals_set_run_read(sphmod):
+    """sph_advance_host (upload, steps, read back in one call) gives the bits
+    of sph_set_state + sph_run + sph_read_state, in place and into other
+    arrays, and rejects bad arguments."""
+    w = WL.drop_tank(3, (14, 15, 22), drop_d_dx=8, seed=98, perturb=True)
+    dt = WL.stable_dt(w.params)
+    a = sphmod.Simulation.from_workload(w)
+    b = sphmod.Simulation.from_workload(w)
+    a.run(dt, 3)
+    b.run(dt, 3)
+    x, u, r = a.read("pos"), a.read("vel"), a.read("rho")
+    x[:, 0] += 1e-7  # a small move: the lists are kept
+    xa, ua, ra = x.copy(), u.copy(), r.copy()
+    a.set_state(xa, ua, ra)
+    a.run(dt, 4)
+    a.read_state(xa, ua, ra)
+    xb, ub, rb = x.copy(), u.copy(), r.copy()
+    b.advance_host(dt, 4, xb, ub, rb)  # in place
+    for p, q in ((xa, xb), (ua, ub), (ra, rb)):
+        assert np.array_equal(p, q)
+    assert a.step_index == b.step_index == 7
+    out = (np.empty_like(x), np.empty_like(u), np.empty_like(r))
+    a.advance_host(dt, 2, xa, ua, ra, out=out)
+    b.set_state(xb, ub, rb)
+    b.run(dt, 2)
+    for p, q in zip(out, (b.read("pos"), b.read("vel"), b.read("rho"))):
+        assert np.array_equal(p, q)
+    with pytest.raises(sphmod.SphError):
+        a.advance_host(-dt, 1, xa, ua, ra)
+    with pytest.raises(sphmod.SphError):
+        a.advance_host(dt, -1, xa, ua, ra)
+
+
 def test_restart_is_bit_exact(sphmod):
     """With a list build every step the particle order after a restart is
     the one the uninterrupted run has, so the runs agree bit for bit."""
