@@ -124,6 +124,54 @@ def test_one_step_matches_oracle(sphmod, visc_form):
     sim.close()
 
 
+def _phases(w, kind, seed):
+    """A copy of workload w with its fluid phases replaced: 'water' (one
+    phase: no interface anywhere) or 'mixed' (each fluid particle oil with
+    probability 1/2: every fluid particle has an other-phase neighbour)."""
+    ph = w.phase.copy()
+    fl = w.wall == 0
+    if kind == "water":
+        ph[fl] = 0
+    else:
+        ph[fl] = np.random.Generator(np.random.PCG64(seed)).integers(0, 2, int(fl.sum()))
+    return ph
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("kind", ["water", "mixed"])
+def test_degenerate_phase_layouts_two_steps_match_oracle(sphmod, dim, kind):
+    """Two steps (both stages, renormalisation, list build) with no
+    interface at all, and with every fluid particle next to the other phase
+    (the interface pass then takes every particle, one warp each)."""
+    w = (WL.drop_tank(2, (30, 40), drop_d_dx=10, seed=21, perturb=True) if dim == 2 else
+         WL.drop_tank(3, (12, 13, 16), drop_d_dx=6, seed=22, perturb=True))
+    p = w.params
+    ph = _phases(w, kind, 23 + dim)
+    # the hydrostatic initial density moved to each particle's new phase
+    r0 = np.asarray(p["rho0"], np.float64)
+    rho0 = w.rho - r0[w.phase] + r0[ph]
+    dt = WL.stable_dt(p)
+    sim = sphmod.Simulation(p, w.x, w.u, rho0, ph, w.wall)
+    sim.run(dt, 2)
+    x, u, rho = sim.read("pos"), sim.read("vel"), sim.read("rho")
+    T = sim.read("tensor")
+    xr, ur, rr = oracle.run(p, w.x, w.u, rho0, ph, w.wall, dt, 2)
+    e_x = np.abs(x - xr).max() / p["dx"]
+    e_u = rel_err_field(u - w.u, ur - w.u)
+    e_r = np.abs(rho / rr - 1).max()
+    print(f"\n[{kind} {dim}-D, two steps] |dx|/dx {e_x:.2e} du {e_u:.2e} rho {e_r:.2e}")
+    # the second step's positions carry the first step's FP32 velocity
+    # increment (dt * a with a relative error ~1e-6)
+    assert e_x < 1e-8
+    assert e_u < TOL
+    assert e_r < TOL
+    if kind == "water":
+        assert np.all(T == 0.0)
+    else:
+        assert np.abs(T).max() > 0.0
+    sim.close()
+
+
 def test_graph_replay_is_bit_identical_to_eager(sphmod):
     w = WL.drop_tank(2, (30, 40), drop_d_dx=10, seed=3, perturb=True)
     dt = WL.stable_dt(w.params)
