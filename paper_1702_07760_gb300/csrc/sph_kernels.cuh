@@ -859,7 +859,8 @@ __device__ __forceinline__ void sweep_a_pairs(const Dev &d, const Grid &g, const
 
 template <int DIM>
 __device__ __forceinline__ void sweep_a_finish(const Dev &d, const Phys &ph, int i, const float4 &oi, int phi_,
-                                               float drho, float gx, float gy, float gz, float4 *vel_s);
+                                               float drho, float gx, float gy, float gz, float4 *vel_s,
+                                               bool write_t = true);
 
 // skip_mixed (stage 2): the particles with an other-phase neighbour are left
 // to the warp-per-particle pass (sweep_a_mixed_warp).
@@ -878,7 +879,9 @@ __device__ __forceinline__ void sweep_a_one(const Dev &d, const Grid &g, const P
     // without the per-pair phase test
     if (other) sweep_a_pairs<DIM, NC, true>(d, g, ph, i, oi, phi_, renorm, s1, c1, s2, c2, gx, gy, gz);
     else if (renorm) sweep_a_pairs<DIM, NC, false>(d, g, ph, i, oi, phi_, 1, s1, c1, s2, c2, gx, gy, gz);
-    sweep_a_finish<DIM>(d, ph, i, oi, phi_, renorm ? s2 / s1 : drho_in[i], gx, gy, gz, vel_s);
+    // at stage 2 a particle with no other-phase particle in its list keeps the
+    // zero surface tensor that stage 1 wrote (no colour gradient either time)
+    sweep_a_finish<DIM>(d, ph, i, oi, phi_, renorm ? s2 / s1 : drho_in[i], gx, gy, gz, vel_s, !skip_mixed);
 }
 
 // Sweep A at stage 2 (no renormalisation: only the colour gradient) for a
@@ -925,7 +928,8 @@ __device__ __forceinline__ void sweep_a_mixed_warp(const Dev &d, const Grid &g, 
 // tensor, and the records the force sweep gathers.
 template <int DIM>
 __device__ __forceinline__ void sweep_a_finish(const Dev &d, const Phys &ph, int i, const float4 &oi, int phi_,
-                                               float drho, float gx, float gy, float gz, float4 *vel_s)
+                                               float drho, float gx, float gy, float gz, float4 *vel_s,
+                                               bool write_t)
 {
     const Inst &I = d.inst[d.iid[i]];
     d.drho_eval[i] = drho;
@@ -960,8 +964,10 @@ __device__ __forceinline__ void sweep_a_finish(const Dev &d, const Phys &ph, int
     d.posv[i] = make_float4(oi.x, oi.y, oi.z, __uint_as_float((__float_as_uint(vs) & ~1u) | iface));
     vel_s[i].w = by_phase(phi_, I.mass) * P / (rho * rho);  // m_i P_i / rho_i^2
     d.pres[i] = P;
-    d.T4[i] = t4;
-    if (DIM == 3) d.T2[i] = t2;
+    if (write_t) {
+        d.T4[i] = t4;
+        if (DIM == 3) d.T2[i] = t2;
+    }
 }
 
 // ---------------------------------------------------------------------------
