@@ -3,24 +3,30 @@
 // BF16, FP32 accumulation in tensor memory (TMEM), fused epilogue.
 //
 // Per CTA: one 128-row tile of C and all N <= 256 columns.  K is consumed in
-// chunks of up to 64; each chunk of A and B is copied to shared memory with
-// 16-byte cp.async in the tensor core's K-major layout without swizzle
-// (8-row x 16-byte core matrices: [row group][k group][row][16 B]), double
-// buffered, and contracted by one elected thread issuing tcgen05.mma
-// (M = 128, N, K = 16) into a TMEM accumulator of N columns.  Completion of
-// each chunk's MMAs is signalled through an mbarrier (tcgen05.commit); every
-// wait gives up after one second, raising an error flag, and the CTA still
-// releases its TMEM.  The epilogue reads the accumulator with tcgen05.ld
+// chunks of up to 64; each chunk of A and B is brought to shared memory by the
+// tensor memory accelerator (cp.async.bulk.tensor, one 2-D box of rows x 8
+// elements per 8-wide k group) in the tensor core's K-major layout without
+// swizzle ([k group][row][16 B]: core matrices of 8 rows x 16 bytes, 128 B
+// apart along M and rows x 16 B apart along K), double buffered, and contracted by one thread issuing tcgen05.mma (M = 128, N,
+// K = 16) into a TMEM accumulator of N columns.  The same thread issues the
+// copies: a chunk's arrival and the completion of its MMAs (tcgen05.commit)
+// are each signalled through an mbarrier; every wait gives up after one
+// second, raising an error flag, and the CTA waits (again bounded) for its
+// copies in flight and still releases its TMEM.  The epilogue reads the accumulator with tcgen05.ld
 // (each warp its 32-lane quarter), adds a column bias and an optional
 // row-scaled bias, stores the pre-activation, applies SiLU, adds a residual
 // and writes FP32 and/or BF16 (or FP16) outputs, or adds into FP32 with
 // atomics when K is split across CTAs.
 #pragma once
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <mutex>
 
 namespace umma {
 
@@ -143,15 +149,24 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool valid)
+// Expects `bytes` more transaction bytes on the mbarrier and arrives once.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *mbar, uint32_t bytes)
 {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(smem)), "l"(gmem),
-                 "r"(valid ? 16 : 0)
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes)
                  : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// 2-D tensor copy global -> shared of the box at (x, y) = (k, row) of the
+// tensor map; completion counted in bytes on the mbarrier.  x is a multiple
+// of 8 elements (16 bytes) and dst 128-byte aligned.
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *mbar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+            "r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(mbar))
+        : "memory");
+}
 
 __device__ __forceinline__ float silu(float z) { return z / (1.f + __expf(-z)); }
 
@@ -188,25 +203,6 @@ struct GemmArgs {
     int cb_half;                // 1: Cb holds FP16 (__half) instead of BF16
     unsigned *err;              // error word (ERR_TIMEOUT)
 };
-
-// Copies chunk rows [row0, row0 + R) x k-groups [0, KG) of X (ld elements,
-// columns k0...) into shared memory at dst in the core-matrix layout; rows at
-// or beyond `rows` are zero-filled.
-template <int R>
-__device__ __forceinline__ void load_chunk(uint8_t *dst, const __nv_bfloat16 *X, int ld, int row0, int rows, int k0,
-                                           int KG)
-{
-    const int pieces = R * KG;
-    for (int p = threadIdx.x; p < pieces; p += THREADS) {
-        const int r_lo = p & 7;
-        const int kg = (p >> 3) % KG;
-        const int rg = (p >> 3) / KG;
-        const int row = row0 + rg * 8 + r_lo;
-        const bool ok = row < rows;
-        const __nv_bfloat16 *src = X + (size_t)(ok ? row : 0) * ld + k0 + kg * 8;
-        cp_async16(dst + (size_t)p * 16, src, ok);
-    }
-}
 
 __device__ __forceinline__ bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
@@ -279,8 +275,24 @@ __device__ __forceinline__ void store16_bf16(__nv_bfloat16 *p, const float (&v)[
     }
 }
 
+// Issues the copies of K chunk [k0, k0 + kc) of A (rows row0...) and B into
+// one buffer pair: kc / 8 boxes each, [k group][row][16 B].
 template <int BN>
-__global__ void __launch_bounds__(THREADS, 1) k_gemm(GemmArgs g)
+__device__ __forceinline__ void tma_chunk(uint8_t *a, uint8_t *b, const CUtensorMap *mA, const CUtensorMap *mB,
+                                          int row0, int k0, int kc, uint64_t *bar)
+{
+    const int KG = kc / 8;
+    mbar_arrive_expect_tx(bar, (uint32_t)(KG * (BM + BN) * 16));
+    for (int kg = 0; kg < KG; ++kg) {
+        tma_load_2d(a + kg * BM * 16, mA, k0 + kg * 8, row0, bar);
+        tma_load_2d(b + kg * BN * 16, mB, k0 + kg * 8, 0, bar);
+    }
+}
+
+template <int BN>
+__global__ void __launch_bounds__(THREADS, 1)
+    k_gemm(const __grid_constant__ GemmArgs g, const __grid_constant__ CUtensorMap mapA,
+           const __grid_constant__ CUtensorMap mapB)
 {
     constexpr int NCOLS = BN < 32 ? 32 : BN;
     constexpr int A_BYTES = BM * BK * 2;
@@ -290,7 +302,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_gemm(GemmArgs g)
     // buffer b: A at smem + b * (A_BYTES + B_BYTES), B right after it
     auto bufA = [&](int b) { return smem + b * (A_BYTES + B_BYTES); };
     auto bufB = [&](int b) { return smem + b * (A_BYTES + B_BYTES) + A_BYTES; };
-    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ __align__(8) uint64_t mbar[2];   // MMAs of the chunk in buffer b complete
+    __shared__ __align__(8) uint64_t lbar[2];   // copies into buffer b complete
     __shared__ uint32_t tmem_base;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -306,6 +319,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_gemm(GemmArgs g)
     if (threadIdx.x == 0) {
         mbar_init(&mbar[0], 1);
         mbar_init(&mbar[1], 1);
+        mbar_init(&lbar[0], 1);
+        mbar_init(&lbar[1], 1);
         fence_mbar_init();
     }
     tc_fence_before();
@@ -316,54 +331,58 @@ __global__ void __launch_bounds__(THREADS, 1) k_gemm(GemmArgs g)
 
     bool failed = false;
     if (nchunks > 0) {
-        {
-            const int kc = min(BK, k_end - k_begin);
-            load_chunk<BM>(bufA(0), g.A, g.lda, row0, g.M, k_begin, kc / 8);
-            load_chunk<BN>(bufB(0), g.B, g.ldb, 0, g.N, k_begin, kc / 8);
-            cp_async_commit();
-        }
-        for (int c = 0; c < nchunks; ++c) {
-            const int b = c & 1;
-            if (c + 1 < nchunks) {
-                // buffer b^1 held chunk c-1: its MMAs must be complete before it is overwritten
-                if (c >= 1) failed |= !mbar_wait(&mbar[b ^ 1], ((c - 1) >> 1) & 1);
-                if (__syncthreads_or(failed)) {
+        if (threadIdx.x == 0) {
+            // copies issued into each buffer (their arrivals are waited on by
+            // phase parity (uses - 1) & 1)
+            int issued[2] = {0, 0}, landed[2] = {0, 0};
+            int committed = -1;  // last chunk whose MMAs were committed
+            tma_chunk<BN>(bufA(0), bufB(0), &mapA, &mapB, row0, k_begin, min(BK, k_end - k_begin), &lbar[0]);
+            issued[0] = 1;
+            for (int c = 0; c < nchunks; ++c) {
+                const int b = c & 1;
+                if (c + 1 < nchunks) {
+                    // buffer b^1 held chunk c-1: its MMAs must be complete before it is overwritten
+                    if (c >= 1 && !mbar_wait(&mbar[b ^ 1], ((c - 1) >> 1) & 1)) {
+                        failed = true;
+                        break;
+                    }
+                    const int k0 = k_begin + (c + 1) * BK;
+                    tma_chunk<BN>(bufA(b ^ 1), bufB(b ^ 1), &mapA, &mapB, row0, k0, min(BK, k_end - k0), &lbar[b ^ 1]);
+                    issued[b ^ 1] += 1;
+                }
+                if (!mbar_wait(&lbar[b], (c >> 1) & 1)) {
                     failed = true;
                     break;
                 }
-                const int k0 = k_begin + (c + 1) * BK;
-                const int kc = min(BK, k_end - k0);
-                load_chunk<BM>(bufA(b ^ 1), g.A, g.lda, row0, g.M, k0, kc / 8);
-                load_chunk<BN>(bufB(b ^ 1), g.B, g.ldb, 0, g.N, k0, kc / 8);
-                cp_async_commit();
-                cp_async_wait<1>();
-            } else {
-                cp_async_wait<0>();
-            }
-            fence_proxy_async();
-            __syncthreads();
-            if (threadIdx.x == 0) {
+                landed[b] += 1;
                 tc_fence_after();
                 const int k0 = k_begin + c * BK;
                 const int kc = min(BK, k_end - k0);
-                const int KG = kc / 8;
                 const uint32_t a0 = smem_u32(bufA(b)), b0 = smem_u32(bufB(b));
                 for (int kk = 0; kk < kc / 16; ++kk) {
-                    const uint64_t ad = desc_kmajor(a0 + kk * 256, 128, KG * 128);
-                    const uint64_t bd = desc_kmajor(b0 + kk * 256, 128, KG * 128);
+                    const uint64_t ad = desc_kmajor(a0 + kk * 2 * BM * 16, BM * 16, 128);
+                    const uint64_t bd = desc_kmajor(b0 + kk * 2 * BN * 16, BN * 16, 128);
                     mma_bf16(taddr, ad, bd, idesc, (c > 0 || kk > 0) ? 1u : 0u);
                 }
                 mma_commit(&mbar[b]);
+                committed = c;
+            }
+            if (failed) {
+                // copies still in flight write this CTA's shared memory and
+                // MMAs in flight its TMEM: wait for them (bounded) before the
+                // CTA releases either (the last commit covers every MMA)
+                for (int bb = 0; bb < 2; ++bb)
+                    for (int u = landed[bb]; u < issued[bb]; ++u) mbar_wait(&lbar[bb], u & 1);
+                if (committed >= 0) mbar_wait(&mbar[committed & 1], (committed >> 1) & 1);
             }
         }
-        if (!failed) {
+        if (!__syncthreads_or(failed)) {
             const int last = nchunks - 1;
-            failed |= !mbar_wait(&mbar[last & 1], (last >> 1) & 1);
+            failed = !mbar_wait(&mbar[last & 1], (last >> 1) & 1);
         }
         failed = __syncthreads_or(failed);
     }
     if (failed) {
-        cp_async_wait<0>();
         if (threadIdx.x == 0) atomicOr(g.err, ERR_TIMEOUT);
     } else {
         tc_fence_after();
@@ -435,6 +454,39 @@ __global__ void __launch_bounds__(THREADS, 1) k_gemm(GemmArgs g)
 
 inline size_t gemm_smem_bytes(int BN) { return 2 * (size_t)(BM * BK * 2 + BN * BK * 2) + 1024; }
 
+// cuTensorMapEncodeTiled of the driver, looked up once through the runtime.
+inline PFN_cuTensorMapEncodeTiled_v12000 encode_tiled()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    });
+    return fn;
+}
+
+// Tensor map of a row-major BF16 matrix (rows x cols, ld elements between
+// rows) read in boxes of box_rows rows x 8 elements; rows beyond `rows` and
+// columns beyond `cols` read as zero.  False when the base is not 16-byte
+// aligned, ld not a multiple of 8, or the driver refuses the map.
+inline bool make_map(CUtensorMap *m, const __nv_bfloat16 *base, int rows, int cols, int ld, int box_rows)
+{
+    const PFN_cuTensorMapEncodeTiled_v12000 fn = encode_tiled();
+    if (!fn || ((uintptr_t)base & 15u) || ld % 8 != 0 || rows <= 0 || cols <= 0) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    const cuuint32_t box[2] = {8, (cuuint32_t)box_rows};
+    const cuuint32_t step[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)base, dims, strides, box, step,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // Launches C = A B^T (+ epilogue) on `stream`; returns a cudaError_t.
 inline cudaError_t gemm(const GemmArgs &g, cudaStream_t stream)
 {
@@ -443,13 +495,16 @@ inline cudaError_t gemm(const GemmArgs &g, cudaStream_t stream)
         return cudaErrorInvalidValue;
     const dim3 grid((g.M + BM - 1) / BM, (g.K + g.k_split - 1) / g.k_split);
     const size_t smem = gemm_smem_bytes(g.N);
+    CUtensorMap mapA{}, mapB{};
+    if (g.K > 0 && (!make_map(&mapA, g.A, g.M, g.K, g.lda, BM) || !make_map(&mapB, g.B, g.N, g.K, g.ldb, g.N)))
+        return cudaErrorInvalidValue;
     cudaError_t e = cudaSuccess;
     switch (g.N) {
 #define SPH_GEMM_CASE(BN)                                                                                  \
     case BN:                                                                                              \
         e = cudaFuncSetAttribute(k_gemm<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);    \
         if (e != cudaSuccess) return e;                                                                   \
-        k_gemm<BN><<<grid, THREADS, smem, stream>>>(g);                                                   \
+        k_gemm<BN><<<grid, THREADS, smem, stream>>>(g, mapA, mapB);                                       \
         break;
         SPH_GEMM_CASE(16)
         SPH_GEMM_CASE(32)
