@@ -238,6 +238,48 @@ def test_advance_host_equals_set_run_read(sphmod):
         a.advance_host(dt, -1, xa, ua, ra)
 
 
+def test_host_round_trip_matches_device_arrays(sphmod):
+    """State uploads and reads through pinned or pageable host memory (staged
+    copies) give the bits of the same calls on device arrays (read and written
+    in place), for sph_set_state / sph_read_state and sph_advance_host, at a
+    size of several thousand 256-thread blocks."""
+    import ctypes as C
+    import torch
+    w = WL.drop_tank(3, (40, 40, 48), drop_d_dx=12, seed=99, perturb=True)
+    dt = WL.stable_dt(w.params)
+    L = sphmod.load()
+    dp = lambda t: C.cast(t.data_ptr(), C.POINTER(C.c_double))
+    a = sphmod.Simulation.from_workload(w)
+    b = sphmod.Simulation.from_workload(w)
+    a.run(dt, 2)
+    b.run(dt, 2)
+    x, u, r = a.read("pos"), a.read("vel"), a.read("rho")
+    x[:, 0] += 1e-7
+    pin = lambda v: torch.from_numpy(v).pin_memory().numpy()
+    hx, hu, hr = pin(x), pin(u), pin(r)
+    a.set_state(hx, hu, hr)
+    a.run(dt, 3)
+    a.read_state(hx, hu, hr)
+    dx, du, dr = (torch.from_numpy(v).cuda() for v in (x, u, r))
+    torch.cuda.synchronize()
+    sphmod._check(L.sph_set_state(b._h, dp(dx), dp(du), dp(dr)))
+    b.run(dt, 3)
+    ox, ou, orho = torch.empty_like(dx), torch.empty_like(du), torch.empty_like(dr)
+    sphmod._check(L.sph_read_state(b._h, dp(ox), dp(ou), dp(orho)))
+    torch.cuda.synchronize()
+    for p, q in ((hx, ox), (hu, ou), (hr, orho)):
+        assert np.array_equal(p, q.cpu().numpy())
+    # the one-call round trip from pageable memory against device arrays
+    px, pu, pr = hx.copy(), hu.copy(), hr.copy()
+    a.advance_host(dt, 2, px, pu, pr)
+    sphmod._check(L.sph_advance_host(b._h, dt, 2, dp(ox), dp(ou), dp(orho), dp(ox), dp(ou), dp(orho)))
+    torch.cuda.synchronize()
+    for p, q in ((px, ox), (pu, ou), (pr, orho)):
+        assert np.array_equal(p, q.cpu().numpy())
+    a.close()
+    b.close()
+
+
 def test_restart_is_bit_exact(sphmod):
     """With a list build every step the particle order after a restart is
     the one the uninterrupted run has, so the runs agree bit for bit."""
