@@ -150,7 +150,9 @@ class ClockSampler:
 
 
 def cpu_oracle_rate(w, budget_s=15.0, max_steps=8):
-    """Times the FP64 oracle on the host cores; returns (particle-steps/s, cores, steps)."""
+    """Times the FP64 oracle on the host cores (OpenMP over particles on
+    every core), then one step on a single thread; returns (particle-steps/s
+    on all cores, cores, steps, particle-steps/s on one thread)."""
     import oracle
     from paper_1702_07760_gb300 import workloads as WL
     cores = os.cpu_count() or 1
@@ -165,7 +167,13 @@ def cpu_oracle_rate(w, budget_s=15.0, max_steps=8):
         if time.perf_counter() - t0 > budget_s:
             break
     el = time.perf_counter() - t0
-    return w.n * steps / el, oracle.num_threads(), steps
+    used = oracle.num_threads()
+    oracle.set_threads(1)
+    t1 = time.perf_counter()
+    oracle.run(w.params, x, u, rho, w.phase, w.wall, dt, 1, first_step=steps)
+    el1 = time.perf_counter() - t1
+    oracle.set_threads(cores)
+    return w.n * steps / el, used, steps, w.n / el1
 
 
 def run_reference(args, ws, rank):
@@ -558,9 +566,10 @@ def run_ours(args, ws, rank, local):
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        rate, cores, steps = cpu_oracle_rate(w)
+        rate, cores, steps, rate1 = cpu_oracle_rate(w)
         cpu = {"value": rate, "unit": "particle-steps/s", "cores": cores, "kind": "oracle",
-               "sample": f"{steps} FP64 oracle step(s) of the full {n}-particle workload"}
+               "sample": f"{steps} FP64 oracle step(s) of the full {n}-particle workload",
+               "value_1thread": rate1, "sample_1thread": "one more full-size step on a single thread"}
 
     batched = None
     if rank == 0 and ws == 1 and args.batch_steps > 0:
