@@ -24,7 +24,10 @@
  *   - dynamic boundary particles are phase 0 (water) everywhere.
  *   - the per-phase renormalisation (Eq. ct_dist_3) is a Jacobi update over
  *     same-phase neighbours including i itself, applied at stage 1 of every
- *     renorm_every-th step; the colour gradient of the same stage uses the
+ *     renorm_every-th step, to fluid particles only: the dynamic boundary
+ *     particles share the fluid's continuity and state equations (Sec. III)
+ *     and keep the density continuity gives them, while still entering the
+ *     fluid's sums as water; the colour gradient of the same stage uses the
  *     density that entered the stage (before renormalisation), everything
  *     after it uses the renormalised density.
  *   - T = 0 exactly when grad C = 0 (no threshold: |T| <= alpha_s |grad C|
@@ -423,10 +426,12 @@ int or_eval(const or_params *p, int64_t n, const double *x, const double *u,
     if (rc != 0) return rc;
 
     /* Eq. ct_dist_3: rho_i = sum_{same phase} m_j W_ij / sum_{same phase} (m_j/rho_j) W_ij,
-     * the sums running over i itself and its same-phase neighbours. */
+     * the sums running over i itself and its same-phase neighbours; boundary
+     * particles (wall != 0) keep their density (Sec. III: continuity and state
+     * only). */
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) {
-        if (!renorm) { rho[i] = rho_in[i]; continue; }
+        if (!renorm || wall[i]) { rho[i] = rho_in[i]; continue; }
         int ph = phase[i];
         double num = p->mass[ph] * or_W(d, p->h, 0.0);
         double den = p->mass[ph] / rho_in[i] * or_W(d, p->h, 0.0);

@@ -872,16 +872,20 @@ __device__ __forceinline__ void sweep_a_one(const Dev &d, const Grid &g, const P
     if (skip_mixed && other) return;
     const float4 oi = d.pos[i];
     const int phi_ = phase_of(oi.w);
+    // boundary particles keep the density continuity gives them (Sec. III:
+    // they share the fluid's continuity and state equations); they still
+    // enter the fluid's sums as water
+    const int renorm_i = renorm && !(d.tag[i] & 2);
     // self term: W(0)/alpha_d = 1
     float s1 = fabsf(oi.w), c1 = 0.f, s2 = d.vd[i], c2 = 0.f;
     float gx = 0.f, gy = 0.f, gz = 0.f;
     // particles with no other-phase neighbour (the bulk) take the loop
     // without the per-pair phase test
-    if (other) sweep_a_pairs<DIM, NC, true>(d, g, ph, i, oi, phi_, renorm, s1, c1, s2, c2, gx, gy, gz);
-    else if (renorm) sweep_a_pairs<DIM, NC, false>(d, g, ph, i, oi, phi_, 1, s1, c1, s2, c2, gx, gy, gz);
+    if (other) sweep_a_pairs<DIM, NC, true>(d, g, ph, i, oi, phi_, renorm_i, s1, c1, s2, c2, gx, gy, gz);
+    else if (renorm_i) sweep_a_pairs<DIM, NC, false>(d, g, ph, i, oi, phi_, 1, s1, c1, s2, c2, gx, gy, gz);
     // at stage 2 a particle with no other-phase particle in its list keeps the
     // zero surface tensor that stage 1 wrote (no colour gradient either time)
-    sweep_a_finish<DIM>(d, ph, i, oi, phi_, renorm ? s2 / s1 : drho_in[i], gx, gy, gz, vel_s, !skip_mixed);
+    sweep_a_finish<DIM>(d, ph, i, oi, phi_, renorm_i ? s2 / s1 : drho_in[i], gx, gy, gz, vel_s, !skip_mixed);
 }
 
 // Sweep A at stage 2 (no renormalisation: only the colour gradient) for a

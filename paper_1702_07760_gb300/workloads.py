@@ -316,7 +316,8 @@ def wave_tank(dx: float = 5e-3, length: float = 4.0, width: float = 0.3, depth: 
     """3-D flume (x along the tank, y across, z up), periodic in y.
 
     Fluid: the lattice of length x width x depth (cells of dx) above the slope.
-    Boundary particles (wall_layers each): the bed below z = 0, the end wall
+    Boundary particles (wall_layers each): the bed below z = 0 (running on
+    behind the piston as far as its stroke can take it), the end wall
     beyond x = length, and a plane slope z = slope (x - slope_toe) for
     x > slope_toe (the layers just under it).  The wall layers before x = 0
     are the piston (wall = 2), driven by ``meta["piston"]`` (a focused group,
@@ -332,12 +333,17 @@ def wave_tank(dx: float = 5e-3, length: float = 4.0, width: float = 0.3, depth: 
     msc = int(np.floor(width / RL))
     p["cell_size"] = width / msc / 2.0
     p["periodic"] = 2
-    i, j, k = np.meshgrid(np.arange(-L, nx + L), np.arange(ny), np.arange(-L, nzw), indexing="ij")
+    motion = focused_group(seed + 1, depth, x_focus)
+    reach = 2.0 * float(np.sum(np.abs(motion["amp"])))      # bound on |X(t)|
+    # the bed runs on behind the piston for its whole backward stroke (the
+    # water follows the piston face there)
+    nb = int(np.ceil(reach / dx)) + 1
+    i, j, k = np.meshgrid(np.arange(-L - nb, nx + L), np.arange(ny), np.arange(-L, nzw), indexing="ij")
     i, j, k = i.ravel(order="F"), j.ravel(order="F"), k.ravel(order="F")
     xc, zc = (i + 0.5) * dx, (k + 0.5) * dx
     zs = np.where(xc > slope_toe, slope * (xc - slope_toe), -np.inf)
     bed = k < 0
-    piston = (i < 0) & (k >= 0)
+    piston = (i >= -L) & (i < 0) & (k >= 0)
     endw = (i >= nx) & (k >= 0)
     inside = (i >= 0) & (i < nx) & (k >= 0)
     slope_layer = inside & (zc < zs) & (zc >= zs - L * dx)
@@ -360,9 +366,7 @@ def wave_tank(dx: float = 5e-3, length: float = 4.0, width: float = 0.3, depth: 
     rho = np.where(wall > 0, p["rho0"][WATER] + p["rho0"][WATER] * g * np.maximum(depth - x[:, 2], 0.0)
                    / p["c0"] ** 2, rho)
     u = np.zeros_like(x)
-    motion = focused_group(seed + 1, depth, x_focus)
-    reach = 2.0 * float(np.sum(np.abs(motion["amp"])))      # bound on |X(t)|
-    p["box_lo"] = [-L * dx - reach - dx, 0.0, -L * dx]
+    p["box_lo"] = [-(L + nb + 1) * dx, 0.0, -L * dx]
     p["box_hi"] = [length + L * dx + dx, width, height + 0.4 * depth]
     meta = dict(piston=motion, n_fluid=nfl, n_wall=int((wall == 1).sum()), n_piston=int((wall == 2).sum()),
                 n_oil=int(oil.sum()), depth=depth, length=length, width=width, seed=seed)

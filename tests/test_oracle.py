@@ -173,6 +173,27 @@ def test_renormalisation_isolated_particle_keeps_density():
     assert abs(out["rho"][centre] - 905.5) < 1e-12
 
 
+def test_renormalisation_leaves_boundary_particles_alone():
+    """Dynamic boundary particles share the fluid's continuity and state
+    equations (Sec. III) but are not renormalised: their density passes
+    through unchanged, while a fluid particle within 2h of a wall still counts
+    the wall particles (water) in its Shepard sums."""
+    w = WL.drop_tank(2, (12, 12), drop_d_dx=4, seed=31)
+    p = w.params
+    ph = np.zeros(w.n, np.uint8)            # one phase: only the walls matter
+    walls = w.wall > 0
+    rho = np.where(walls, 1010.0, 1000.0)
+    out = oracle.evaluate(p, w.x, w.u, rho, ph, w.wall, renorm=True)
+    assert np.array_equal(out["rho"][walls], rho[walls])
+    # distance of each fluid particle to the nearest wall particle
+    d = np.sqrt(((w.x[~walls, None, :] - w.x[None, walls, :]) ** 2).sum(-1)).min(1)
+    near, far = d < 2 * p["h"] * (1 - 1e-9), d >= 2 * p["h"] * (1 + 1e-9)
+    r = out["rho"][~walls]
+    assert far.any() and near.any()
+    assert np.abs(r[far] / 1000.0 - 1).max() < 1e-14
+    assert np.all(r[near] > 1000.0) and np.all(r[near] < 1010.0)
+
+
 # --------------------------------------------------------------------------
 # Continuity (Eqs. ct_dist_1, ct_dist_2)
 
