@@ -65,6 +65,19 @@ def test_invalid_parameters_are_rejected_without_a_gpu(lib):
         sph.Simulation(w.params, w.x, w.u, w.rho, ph, wl)
 
 
+def test_null_handles_are_rejected_without_a_gpu(lib):
+    """Entry points taking a handle return SPH_EINVAL for NULL before any
+    CUDA call."""
+    import ctypes as C
+    dp = C.POINTER(C.c_double)
+    buf = (C.c_double * 8)()
+    p = C.cast(buf, dp)
+    assert lib.sph_advance_host(None, 1e-5, 1, p, p, p, p, p, p) == -1
+    assert lib.sph_read_state(None, p, p, p) == -1
+    assert lib.sph_set_state(None, p, p, p) == -1
+    assert lib.sph_run(None, 1e-5, 1, 1) == -1
+
+
 def test_kernels_compile_for_sm103a_without_spills():
     out = subprocess.run(B.nvcc_command("/tmp/libsph_probe.so", ("-Xptxas", "-v")),
                          capture_output=True, text=True)
