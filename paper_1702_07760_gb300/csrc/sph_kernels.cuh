@@ -873,7 +873,7 @@ __device__ __forceinline__ void sweep_a_one(const Dev &d, const Grid &g, const P
     const float4 oi = d.pos[i];
     const int phi_ = phase_of(oi.w);
     // boundary particles keep the density continuity gives them (Sec. III:
-    // they share the fluid's continuity and state equations); they still
+    // they obey the fluid's mass-conservation law and EOS); they still
     // enter the fluid's sums as water
     const int renorm_i = renorm && !(d.tag[i] & 2);
     // self term: W(0)/alpha_d = 1

@@ -174,8 +174,8 @@ def test_renormalisation_isolated_particle_keeps_density():
 
 
 def test_renormalisation_leaves_boundary_particles_alone():
-    """Dynamic boundary particles share the fluid's continuity and state
-    equations (Sec. III) but are not renormalised: their density passes
+    """Dynamic boundary particles obey the fluid's mass-conservation law and
+    EOS (Sec. III) but are not renormalised: their density passes
     through unchanged, while a fluid particle within 2h of a wall still counts
     the wall particles (water) in its Shepard sums."""
     w = WL.drop_tank(2, (12, 12), drop_d_dx=4, seed=31)
