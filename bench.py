@@ -19,6 +19,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -26,14 +27,15 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# FP32 peak from unit counts and the maximum SM clock: 152 SMs x 128 FP32
-# lanes x 2 flops (FMA) x 2.07 GHz.
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# FP32 peak from unit counts and the maximum SM clock, for context beside the
+# measured one (sph_fp32_peak): 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2.07 GHz.
+FP32_PEAK_DERIVED_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 # Algorithmic flops of one accepted (i, j) pair in the force sweep (FMA = 2,
-# sqrt and divide = 1): pair vector and squared distance, q, (1 - q/2)^3,
+# sqrt and divide = 1): pair vector and squared distance, r, (1 - q/2)^3,
 # pressure term, viscous term, continuity term.  Surface-tension pairs are
-# not counted (conservative).
+# not counted (conservative).  Pinned by the counted restatement in
+# tests/test_flop_count.py.
 SWEEP_B_FLOPS_PER_PAIR = {2: 33, 3: 43}
 # Algorithmic flops of one accepted pair in the renormalisation sweep at
 # stage 1: same-phase pairs (kernel value + two compensated sums) and
@@ -64,6 +66,9 @@ def parse():
                     help="training input noise, as a fraction of the rms change over one jump")
     ap.add_argument("--flume-steps", type=int, default=200,
                     help="timed steps of the 4.9 M-particle breaking-wave flume (0 skips it)")
+    ap.add_argument("--steady-steps", type=int, default=2000,
+                    help="graph-replayed steps of the steady-state window after the timed steps, "
+                         "list rebuilds at their natural rate (0 skips it)")
     return ap.parse_args()
 
 
@@ -109,10 +114,12 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "",
-                                 f".clocks_{os.getpid()}.csv")
+        fd, self.path = tempfile.mkstemp(prefix="sph_clocks_", suffix=".csv")
+        os.close(fd)
 
-    def start(self):
+    def start(self, wait_s: float = 3.0):
+        """Starts sampling and waits (up to wait_s) for the first sample, so
+        that the samples cover the region timed next."""
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
@@ -120,9 +127,17 @@ class ClockSampler:
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < wait_s and os.path.getsize(self.path) == 0:
+            time.sleep(0.02)
 
     def stop(self):
         if self.proc is None:
+            try:
+                os.remove(self.path)
+            except OSError:
+                pass
             return None
         self.proc.terminate()
         try:
@@ -493,9 +508,26 @@ def run_ours(args, ws, rank, local):
         sim.run(dt, args.steps, graph=True)
         ev1.record(stream)
     torch.cuda.synchronize()
-    clk = clocks.stop()
     builds_timed = sim.list_builds - builds0
     ms = ev0.elapsed_time(ev1)
+    # steady state: many more graph-replayed steps right after, so the list
+    # rebuilds come at their natural rate (the short timed window may hold none)
+    steady = None
+    if args.steady_steps > 0:
+        b1 = sim.list_builds
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            s0.record(stream)
+            sim.run(dt, args.steady_steps, graph=True)
+            s1.record(stream)
+        torch.cuda.synchronize()
+        ms_ss = s0.elapsed_time(s1)
+        steady = {"steps": args.steady_steps, "ms_per_step": ms_ss / args.steady_steps,
+                  "value": n * args.steady_steps / (ms_ss / 1e3), "unit": "particle-steps/s",
+                  "list_builds": sim.list_builds - b1}
+    # measured FP32 peak (FMA chains on every SM), inside the same sampled window
+    peak_tflops, peak_ms = sph.fp32_peak(8, 4096, stream.cuda_stream)
+    clk = clocks.stop()
     ms = max_over_ranks(ws, ms, dev)
     barrier(ws)
     value = ws * n * args.steps / (ms / 1e3)
@@ -535,10 +567,14 @@ def run_ours(args, ws, rank, local):
         src = os.path.join(ROOT, "paper_1702_07760_gb300", "csrc", "sph_kernels.cuh")
         if hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] == prof["source_sha256"]:
             traffic = prof["bytes"]
-    roofline = {"bound": "alu", "kernel": top, "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
-                "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz",
-                "flops_per_launch": flops, "avg_launch_ms": avg_ms}
+    roofline = {"bound": "alu", "kernel": top, "achieved": achieved, "peak": peak_tflops,
+                "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": traffic,
+                "peak_source": "measured: sph_fp32_peak, 16 independent FMA chains per thread, 8 blocks "
+                               f"of 256 threads per SM, {peak_ms:.1f} ms launch, clocks as sampled",
+                "peak_derived": FP32_PEAK_DERIVED_TFLOPS,
+                "flops_per_pair": SWEEP_B_FLOPS_PER_PAIR[dim] if top == "sweep_b" else None,
+                "pairs_per_launch": pairs, "flops_per_launch": flops, "avg_launch_ms": avg_ms,
+                "launches": kt[top][0]}
 
     # ---- e2e: host buffers through the C ABI every step ----
     e2e = None
@@ -595,7 +631,11 @@ def run_ours(args, ws, rank, local):
                    "neighbour_pairs": int(pairs), "l2": "step working set (~390 MB) exceeds the 129 MB L2; no flush",
                    "parallelism": "replicas" if ws > 1 else "single", "graph": True,
                    "list_builds_in_timed_steps": builds_timed,
-                   "ms_per_step_eager_timed": ms_eager / args.steps},
+                   "ms_per_step_eager_timed": ms_eager / args.steps,
+                   "boundary_reading": ("boundary particles renormalised as water (Eq. ct_dist_3 with Sec. III)"
+                                        if int(p.get("renorm_walls", 1)) else
+                                        "boundary particles keep their continuity density (stabilisation)")},
+        "steady_state": steady,
         "roofline": roofline,
         "kernels": kernels,
         "cpu_baseline": cpu,

@@ -90,6 +90,14 @@ typedef struct sph_params {
                               number of super-cells, at least three: cell_size when
                               cell_size >= 2h + 2 skin, else 2 cell_size.  Positions are read
                               back wrapped into the box.  Not allowed in a batch. */
+    int32_t renorm_walls;  /* 1: dynamic boundary particles are renormalised (Eq. ct_dist_3)
+                              like water particles, the paper's reading: Sec. III gives them
+                              the fluid's equations of continuity and state, and Eq. ct_dist_3
+                              is part of the discretised continuity equation (Sec. II-B).
+                              0: they keep the density continuity gives them (a stabilisation
+                              of long runs, not the paper's); they still enter the water's
+                              sums either way. */
+    int32_t reserved;      /* must be 0 */
     double h;              /* smoothing length; the Wendland C2 kernel has support 2h */
     double c0;             /* reference speed of sound C_s0 (Eq. beta) */
     double gamma;          /* exponent of Eq. state; must be 7 (the paper's value) */
@@ -358,27 +366,41 @@ int64_t sph_num_instances(sph_handle h);
 
 void sph_destroy(sph_handle h);
 
-/* Allocation-free cell sort (no counterpart in the paper: it serves callers
- * that cannot allocate device memory -- code running while a CUDA stream is
- * captured, where cudaMalloc is not permitted, or a host whose device memory
- * is owned by another allocator).  Computes, for n particles whose positions
- * x_dev are a device array of n * dim doubles (particle-major), the cell id
- * of each particle on the grid of params (cell_size, box_lo, box_hi) into
- * cell_dev (n int32, device) and the particle ids in the stable order by
- * (cell id, particle id) into order_dev (n int32, device): the same values as
- * SPH_FIELD_CELL and SPH_FIELD_ORDER after sph_build_cells.  The caller owns
- * all three arrays.  No device memory is allocated: the scratch is one
- * file-scope device array of about 21 MB that every GPU loading the library
- * holds until the process exits, limiting n to 2^20 particles and the grid to
- * 2^20 cells (larger sizes return SPH_EINVAL).  The first call on a device
- * looks up that array's device address (once per device, with the device
- * current), so make it before any stream capture.  Every call on a device
- * shares the array and keeps the last call's contents (the parts that must
- * start at zero are cleared by each call); calls that overlap on the GPU race.
- * The call waits for the stream and returns SPH_EDOMAIN when a particle lies
- * outside the box. */
+/* Allocation-free cell sort (no counterpart in the paper).  It serves callers
+ * that cannot allocate device memory: a host application whose device memory
+ * belongs to its own pool or allocator (a cudaMalloc from inside it would
+ * fail or fragment that pool), or a deployment whose device memory is fixed
+ * in advance.  Computes, for n particles whose positions x_dev are a device
+ * array of n * dim doubles (particle-major), the cell id of each particle on
+ * the grid of params (cell_size, box_lo, box_hi) into cell_dev (n int32,
+ * device) and the particle ids in the stable order by (cell id, particle id)
+ * into order_dev (n int32, device): the same values as SPH_FIELD_CELL and
+ * SPH_FIELD_ORDER after sph_build_cells.  The caller owns all three arrays.
+ * No device memory is allocated: the scratch is one file-scope device array
+ * of about 21 MB that every GPU loading the library holds until the process
+ * exits, limiting n to 2^20 particles and the grid to 2^20 cells (larger
+ * sizes return SPH_EINVAL).  The first call on a device looks up that
+ * array's device address (once per device, with the device current) and
+ * caches it, so make the first call before any stream capture; a device
+ * reset (cudaDeviceReset) invalidates the cached address, so do not call
+ * this again in the same process after one.  Every call on a device shares
+ * the array and keeps the last call's contents (the parts that must start at
+ * zero are cleared by each call); calls that overlap on the GPU race.  Before
+ * returning, the call copies a one-word out-of-box flag to the host and waits
+ * for the stream; it returns SPH_EDOMAIN when a particle lies outside the
+ * box (the cell ids of such a particle are then clamped into the grid). */
 int sph_cell_sort_noalloc(const sph_params *params, int64_t n, const double *x_dev, int32_t *cell_dev,
                           int32_t *order_dev, void *stream);
+
+/* FP32 fused multiply-add throughput of the current device (no counterpart
+ * in the paper: the measured denominator of the force sweeps' roofline).
+ * Launches blocks_per_sm (1..8) resident blocks of 256 threads on every SM,
+ * each thread running 16 independent FMA chains of iters (1..2^20) steps,
+ * once to warm up and once timed with CUDA events on stream (NULL: the
+ * default stream); waits for the stream.  Writes the achieved rate in
+ * TFLOP/s (2 flops per FMA) to *tflops and the timed launch's duration to
+ * *ms.  Allocates nothing; reads no memory. */
+int sph_fp32_peak(int blocks_per_sm, int iters, void *stream, double *tflops, double *ms);
 
 /* Message of the last failure on the calling thread ("" if none). */
 const char *sph_last_error(void);

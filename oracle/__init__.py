@@ -28,6 +28,7 @@ class OrParams(C.Structure):
         ("visc_form", C.c_int32),
         ("renorm_every", C.c_int32),
         ("periodic", C.c_int32),
+        ("renorm_walls", C.c_int32),
         ("h", C.c_double),
         ("c0", C.c_double),
         ("gamma", C.c_double),
@@ -114,6 +115,7 @@ def make_params(p: dict) -> OrParams:
     o.visc_form = int(p.get("visc_form", 0))
     o.renorm_every = int(p.get("renorm_every", 1))
     o.periodic = int(p.get("periodic", 0))
+    o.renorm_walls = int(p.get("renorm_walls", 1))
     o.h = p["h"]
     o.c0 = p["c0"]
     o.gamma = p.get("gamma", 7.0)

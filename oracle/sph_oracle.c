@@ -24,12 +24,15 @@
  *   - dynamic boundary particles are phase 0 (water) everywhere.
  *   - the per-phase renormalisation (Eq. ct_dist_3) is a Jacobi update over
  *     same-phase neighbours including i itself, applied at stage 1 of every
- *     renorm_every-th step, to fluid particles only: the dynamic boundary
- *     particles obey the fluid's mass-conservation law and EOS (Sec. III)
- *     and keep the density continuity gives them, while still entering the
- *     fluid's sums as water; the colour gradient of the same stage uses the
- *     density that entered the stage (before renormalisation), everything
- *     after it uses the renormalised density.
+ *     renorm_every-th step.  Dynamic boundary particles take it like water
+ *     particles (renorm_walls = 1, the default): Sec. III gives them the
+ *     fluid's equations of continuity and state, and Eq. ct_dist_3 belongs to
+ *     the discretised continuity equation (Sec. II-B).  renorm_walls = 0 is a
+ *     stabilisation of this library's long runs, not the paper's: boundary
+ *     particles then keep the density continuity gives them while still
+ *     entering the fluid's sums as water.  The colour gradient of the same
+ *     stage uses the density that entered the stage (before
+ *     renormalisation), everything after it uses the renormalised density.
  *   - T = 0 exactly when grad C = 0 (no threshold: |T| <= alpha_s |grad C|
  *     tends to zero with grad C).
  *   - time integration is the explicit midpoint predictor-corrector.
@@ -65,6 +68,8 @@ typedef struct {
     int32_t visc_form;    /* 0: dynamic form (Eq. visc_2), 1: kinematic form (Eq. visc_1) */
     int32_t renorm_every; /* Eq. ct_dist_3 at stage 1 of steps n % k == 0; 0 = never */
     int32_t periodic;     /* bit k set: axis k is periodic with period box_hi - box_lo */
+    int32_t renorm_walls; /* 1: boundary particles are renormalised as water (Sec. II-B with
+                             Sec. III); 0: they keep their continuity density */
     double h;             /* smoothing length */
     double c0;            /* reference speed of sound C_s0 */
     double gamma;         /* exponent of the equation of state */
@@ -426,12 +431,14 @@ int or_eval(const or_params *p, int64_t n, const double *x, const double *u,
     if (rc != 0) return rc;
 
     /* Eq. ct_dist_3: rho_i = sum_{same phase} m_j W_ij / sum_{same phase} (m_j/rho_j) W_ij,
-     * the sums running over i itself and its same-phase neighbours; boundary
-     * particles (wall != 0) keep their density (Sec. III gives them the mass-conservation
-     * law and the EOS, nothing more). */
+     * the sums running over i itself and its same-phase neighbours.  Boundary
+     * particles (wall != 0, water) are renormalised like water particles when
+     * renorm_walls is set: they share the fluid's continuity equation
+     * (Sec. III), of whose discretisation Eq. ct_dist_3 is part (Sec. II-B);
+     * otherwise they keep the density continuity gives them. */
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) {
-        if (!renorm || wall[i]) { rho[i] = rho_in[i]; continue; }
+        if (!renorm || (wall[i] && !p->renorm_walls)) { rho[i] = rho_in[i]; continue; }
         int ph = phase[i];
         double num = p->mass[ph] * or_W(d, p->h, 0.0);
         double den = p->mass[ph] / rho_in[i] * or_W(d, p->h, 0.0);

@@ -15,7 +15,7 @@ LIB = os.path.join(HERE, "libsph.so")
 # the bounds-checked variant (-DSPH_CHECKED), for debugging and its tests
 LIB_CHECKED = os.path.join(HERE, "libsph_checked.so")
 OBJ_DIR = os.path.join(ROOT, "_build")
-SOURCES = ["sph_api.cu", "sph_noalloc.cu", "mpnn.cu"]
+SOURCES = ["sph_api.cu", "sph_noalloc.cu", "mpnn.cu", "fma_peak.cu"]
 HEADERS = ["sph_kernels.cuh", "umma.cuh"]
 PUBLIC_HEADERS = ["sph.h", "sph_surrogate.h"]
 FLAGS = ["-O3", "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-Xcompiler", "-fPIC"]

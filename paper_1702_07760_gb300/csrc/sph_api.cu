@@ -646,6 +646,8 @@ int validate(const sph_params *P)
     if (P->visc_form != SPH_VISC_DYNAMIC && P->visc_form != SPH_VISC_KINEMATIC)
         return fail(SPH_EINVAL, "visc_form must be SPH_VISC_DYNAMIC or SPH_VISC_KINEMATIC");
     if (P->renorm_every < 0) return fail(SPH_EINVAL, "renorm_every must be >= 0");
+    if (P->renorm_walls != 0 && P->renorm_walls != 1) return fail(SPH_EINVAL, "renorm_walls must be 0 or 1");
+    if (P->reserved != 0) return fail(SPH_EINVAL, "reserved must be 0");
     if (P->max_neighbours < 0 || P->max_neighbours > 4096)
         return fail(SPH_EINVAL, "max_neighbours must be in [0, 4096]");
     if (P->rebuild_every < 0) return fail(SPH_EINVAL, "rebuild_every must be >= 0");
@@ -675,6 +677,7 @@ int validate(const sph_params *P)
 bool same_shared(const sph_params &a, const sph_params &b)
 {
     bool same = a.dim == b.dim && a.visc_form == b.visc_form && a.renorm_every == b.renorm_every &&
+                a.renorm_walls == b.renorm_walls &&
                 a.periodic == b.periodic &&
                 a.max_neighbours == b.max_neighbours && a.rebuild_every == b.rebuild_every && a.h == b.h &&
                 a.gamma == b.gamma && a.delta == b.delta && a.cell_size == b.cell_size && a.skin == b.skin;
@@ -783,7 +786,7 @@ int create_sim(const sph_params *params, int k, const int64_t *counts, const dou
         if (rc) return rc;
         if (!same_shared(params[0], params[q]))
             return fail(SPH_EINVAL, "instances of a batch must share dim, h, gamma, delta, g, cell_size, skin, "
-                                    "visc_form, renorm_every, rebuild_every and max_neighbours");
+                                    "visc_form, renorm_every, renorm_walls, rebuild_every and max_neighbours");
         if (counts[q] < 0) return fail(SPH_EINVAL, "instance particle counts must be >= 0");
         n += counts[q];
         if (n > ((int64_t)1 << 26)) return fail(SPH_EINVAL, "n must be in [0, 2^26]");
@@ -913,6 +916,7 @@ int create_sim(const sph_params *params, int k, const int64_t *counts, const dou
     ph.inv_dim = (float)(1.0 / dim);
     ph.visc_dynamic = P0.visc_form == SPH_VISC_DYNAMIC;
     ph.renorm_every = P0.renorm_every;
+    ph.renorm_walls = P0.renorm_walls;
     ph.rebuild_every = P0.rebuild_every;
     for (int c = 0; c < 3; ++c) ph.gf[c] = c < dim ? (float)P0.g[c] : 0.f;
 

@@ -71,6 +71,7 @@ struct Phys {
     float gf[3];        // gravity (FP32, added to the FP32 acceleration)
     int visc_dynamic;   // 1: Eq. visc_2 (factor 1/rho_i), 0: Eq. visc_1
     int renorm_every;   // Eq. ct_dist_3 at stage 1 of steps with step % renorm_every == 0
+    int renorm_walls;   // 1: boundary particles are renormalised as water; 0: they keep their density
     int kmax;           // neighbour-list capacity per particle
     int rebuild_every;  // 0: rebuild when a particle may leave the skin; k: every k steps
     double skin;        // allowed displacement since the last build (the list's margin)
@@ -872,10 +873,11 @@ __device__ __forceinline__ void sweep_a_one(const Dev &d, const Grid &g, const P
     if (skip_mixed && other) return;
     const float4 oi = d.pos[i];
     const int phi_ = phase_of(oi.w);
-    // boundary particles keep the density continuity gives them (Sec. III:
-    // they obey the fluid's mass-conservation law and EOS); they still
-    // enter the fluid's sums as water
-    const int renorm_i = renorm && !(d.tag[i] & 2);
+    // boundary particles share the fluid's continuity equation (Sec. III),
+    // whose discretisation includes Eq. ct_dist_3, so by default they are
+    // renormalised as water; with renorm_walls off they keep the density
+    // continuity gives them and only enter the fluid's sums as water
+    const int renorm_i = renorm && (ph.renorm_walls || !(d.tag[i] & 2));
     // self term: W(0)/alpha_d = 1
     float s1 = fabsf(oi.w), c1 = 0.f, s2 = d.vd[i], c2 = 0.f;
     float gx = 0.f, gy = 0.f, gz = 0.f;

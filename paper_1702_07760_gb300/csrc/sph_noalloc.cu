@@ -1,10 +1,11 @@
 // Allocation-free cell sort: the cell hash and the stable counting sort by
 // (cell id, particle id) of the cell-list build, for callers that must not
-// allocate device memory -- code that runs while a CUDA stream is being
-// captured (cudaMalloc is not permitted there), or a host whose device memory
-// is owned by another allocator or fixed in advance.  Its scratch memory is a
-// file-scope device array of fixed size instead of the per-simulation buffers
-// that sph_create allocates.
+// allocate device memory -- a host application whose device memory belongs to
+// its own pool or allocator, or a deployment whose device memory is fixed in
+// advance.  Its scratch memory is a file-scope device array of fixed size
+// instead of the per-simulation buffers that sph_create allocates.  The call
+// ends by copying a one-word out-of-box flag to the host and waiting for the
+// stream.
 #include "sph.h"
 
 #include <cuda_runtime.h>
@@ -51,7 +52,8 @@ std::mutex g_na_mutex;
 int *g_na_ptr[NA_MAX_DEVICES] = {};
 
 // Device address of the scratch array on the current device, looked up with
-// that device current the first time it is needed.
+// that device current the first time it is needed and cached per device
+// index (a device reset would invalidate the cached address).
 int scratch_for_current_device(int **out)
 {
     int dev = -1;

@@ -92,6 +92,9 @@ def main(argv=None) -> int:
     ap.add_argument("--persistent", action="store_true", help="advance with the persistent kernel")
     ap.add_argument("--visc-form", type=int, default=None, choices=[0, 1],
                     help="viscous term: 0 dynamic (Eq. visc_2), 1 kinematic (Eq. visc_1)")
+    ap.add_argument("--renorm-walls", type=int, default=None, choices=[0, 1],
+                    help="1: boundary particles renormalised as water (the paper's reading, default); "
+                         "0: they keep their continuity density (the stabilisation of long open-top runs)")
     args = ap.parse_args(argv)
 
     step0, t_start = 0, 0.0
@@ -108,6 +111,8 @@ def main(argv=None) -> int:
         w.params["rebuild_every"] = int(args.rebuild_every)
     if args.visc_form is not None:
         w.params["visc_form"] = int(args.visc_form)
+    if args.renorm_walls is not None:
+        w.params["renorm_walls"] = int(args.renorm_walls)
     dt = args.dt or WL.stable_dt(w.params)
     if args.steps is None and args.t_end is None:
         raise SystemExit("give --steps or --t-end")

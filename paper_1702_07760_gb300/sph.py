@@ -34,7 +34,7 @@ EXPORTS = ["sph_create", "sph_set_state", "sph_build_cells", "sph_eval_rates", "
            "sph_surrogate_train_step", "sph_surrogate_run", "sph_create_dev", "sph_set_piston", "sph_get_time",
            "sph_set_time", "sph_suggest_dt", "sph_surrogate_advance_judged", "sph_read_state", "sph_advance_host",
            "sph_oil_occupancy_diff", "sph_surrogate_set_interface_tol", "sph_surrogate_judge_stats",
-           "sph_perturb_state"]
+           "sph_perturb_state", "sph_fp32_peak"]
 
 
 class SphError(RuntimeError):
@@ -46,7 +46,9 @@ class SphError(RuntimeError):
 class SphParams(C.Structure):
     _fields_ = [
         ("dim", C.c_int32), ("visc_form", C.c_int32), ("renorm_every", C.c_int32),
-        ("max_neighbours", C.c_int32), ("rebuild_every", C.c_int32), ("periodic", C.c_int32), ("h", C.c_double), ("c0", C.c_double), ("gamma", C.c_double),
+        ("max_neighbours", C.c_int32), ("rebuild_every", C.c_int32), ("periodic", C.c_int32),
+        ("renorm_walls", C.c_int32), ("reserved", C.c_int32),
+        ("h", C.c_double), ("c0", C.c_double), ("gamma", C.c_double),
         ("delta", C.c_double), ("alpha_s", C.c_double), ("cell_size", C.c_double), ("skin", C.c_double),
         ("g", C.c_double * 3), ("rho0", C.c_double * 2), ("mu", C.c_double * 2),
         ("mass", C.c_double * 2), ("box_lo", C.c_double * 3), ("box_hi", C.c_double * 3),
@@ -93,6 +95,7 @@ def load(path: str = LIB_PATH):
     L.sph_destroy.restype = None
     L.sph_last_error.restype = C.c_char_p
     L.sph_cell_sort_noalloc.argtypes = [P(SphParams), C.c_int64, vp, vp, vp, vp]
+    L.sph_fp32_peak.argtypes = [C.c_int, C.c_int, vp, dp, dp]
     L.sph_create_batch.argtypes = [C.c_int, P(SphParams), P(C.c_int64), dp, dp, dp, u8p, u8p, vp, P(H)]
     L.sph_set_dt_scales.argtypes = [H, dp]
     L.sph_run_persistent.argtypes = [H, C.c_double, C.c_int64, C.c_int]
@@ -132,6 +135,7 @@ def make_params(p: dict) -> SphParams:
     s.max_neighbours = int(p.get("max_neighbours", 0))
     s.rebuild_every = int(p.get("rebuild_every", 0))
     s.periodic = int(p.get("periodic", 0))
+    s.renorm_walls = int(p.get("renorm_walls", 1))
     s.h, s.c0, s.gamma = p["h"], p["c0"], p.get("gamma", 7.0)
     s.delta, s.alpha_s, s.cell_size, s.skin = p["delta"], p["alpha_s"], p["cell_size"], p["skin"]
     for k in range(3):
@@ -156,6 +160,14 @@ def cell_sort_noalloc(params: dict, n: int, x_dev: int, cell_dev: int, order_dev
     p = make_params(params)
     _check(load().sph_cell_sort_noalloc(C.byref(p), int(n), C.c_void_p(x_dev), C.c_void_p(cell_dev),
                                         C.c_void_p(order_dev), C.c_void_p(stream)))
+
+
+def fp32_peak(blocks_per_sm: int = 8, iters: int = 4096, stream: int = 0):
+    """(TFLOP/s, ms): FP32 FMA throughput of the current device (see
+    sph_fp32_peak in include/sph.h)."""
+    t, m = C.c_double(), C.c_double()
+    _check(load().sph_fp32_peak(int(blocks_per_sm), int(iters), C.c_void_p(stream), C.byref(t), C.byref(m)))
+    return t.value, m.value
 
 
 def mm_bf16(a_ptr: int, lda: int, b_ptr: int, ldb: int, c_ptr: int, ldc: int, M: int, N: int, K: int,

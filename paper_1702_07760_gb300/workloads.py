@@ -61,8 +61,12 @@ class Workload:
 
 def fluid_params(dim: int, dx: float, depth: float, *, rho0=(1000.0, 900.0),
                  mu=(1e-3, 1e-2), alpha_s=0.02, g=9.81, h_over_dx=1.3,
-                 c0=None, visc_form=0, renorm_every=1, skin_h=0.025, cell_h=None) -> dict:
+                 c0=None, visc_form=0, renorm_every=1, renorm_walls=1, skin_h=0.025, cell_h=None) -> dict:
     """Physical and numerical parameters of a drop-rise workload.
+
+    ``renorm_walls`` = 1 renormalises the dynamic boundary particles like
+    water (the paper's reading); 0 keeps their continuity density (the
+    stabilisation that long runs of the paper's open-top tank select).
 
     ``skin_h`` is the neighbour-list margin in units of h (the list holds pairs
     closer than 2h + 2 skin); ``cell_h`` is the hashing-cell edge in units of
@@ -79,7 +83,7 @@ def fluid_params(dim: int, dx: float, depth: float, *, rho0=(1000.0, 900.0),
         dim=dim, dx=dx, h=h, c0=float(c0), gamma=7.0, delta=0.1 * h,
         alpha_s=float(alpha_s), g=grav, rho0=list(map(float, rho0)), mu=list(map(float, mu)),
         mass=[float(r) * dx ** dim for r in rho0], visc_form=int(visc_form),
-        renorm_every=int(renorm_every), cell_size=cell, skin=skin, depth=depth,
+        renorm_every=int(renorm_every), renorm_walls=int(renorm_walls), cell_size=cell, skin=skin, depth=depth,
         box_lo=[0.0, 0.0, 0.0], box_hi=[0.0, 0.0, 0.0],
     )
 

@@ -13,10 +13,11 @@ axis.
 In the flume, still water half a metre deep, the acceleration is the small
 difference between a pressure gradient and gravity, while each pressure pair
 term is of order (P/rho)/h, about 75 g at the bed.  The FP32 sums round at
-the size of those terms, so there the acceleration error is stated relative
-to a_P = max_i (|P_i| / rho_i) / h, the scale of one pressure pair term:
-1e-5 a_P (the drop tanks, 32 mm deep, have a_P of a few g and meet 1e-5 of
-their largest acceleration).
+the size of those terms, so the acceleration error of particle i is held to
+the bound of the FP32 arithmetic, (k_i + 8) u S_i with S_i the sum of the
+magnitudes of its pair terms (tests/acc_bounds.py), and the per-particle
+error against max(|a_i|, |g|) is printed beside it; after one step the
+velocity error is held to dt times that bound.
 """
 import math
 
@@ -24,6 +25,7 @@ import numpy as np
 import pytest
 
 import oracle
+from acc_bounds import ROUNDINGS_PER_TERM, U32, acc_error_report, term_magnitudes
 from paper_1702_07760_gb300 import workloads as WL
 
 pytestmark = pytest.mark.gpu
@@ -145,6 +147,18 @@ def pressure_scale(p, ref):
     return float(np.max(np.abs(ref["P"]) / ref["rho"]) / p["h"])
 
 
+def step_velocity_errors(p, w, ref, u_gpu, u_ref, dt):
+    """One step from the state of w: (max over fluid particles of |du_i| /
+    (dt (k_i + 8) u S_i), and of |du_i| / (dt max(|a_i|, |g|))), with S_i, k_i
+    and a_i those of the rates at the start of the step."""
+    S, k = term_magnitudes(p, w.x, w.u, ref["rho"], ref["P"], ref["T"], w.phase, w.wall)
+    fl = w.wall == 0
+    du = np.linalg.norm(u_gpu[fl] - u_ref[fl], axis=1)
+    bound = dt * (k[fl] + ROUNDINGS_PER_TERM) * U32 * S[fl]
+    floor = dt * np.maximum(np.linalg.norm(ref["a"][fl], axis=1), np.linalg.norm(p["g"]))
+    return float((du / bound).max()), float((du / floor).max())
+
+
 def piston_tank(seed):
     w = WL.drop_tank(2, (40, 24), drop_d_dx=8, seed=seed, perturb=True)
     wall = w.wall.copy()
@@ -200,19 +214,20 @@ def test_flume_small_matches_oracle(sphmod):
     sim.eval_rates()
     ref = oracle.evaluate(p, w.x, w.u, w.rho, w.phase, w.wall, renorm=True)
     aP = pressure_scale(p, ref)
-    fl = w.wall == 0
     e_rho = np.abs(sim.read("rho_eval") / ref["rho"] - 1).max()
-    e_a = np.abs(sim.read("acc")[fl] - ref["a"][fl]).max() / aP
+    b_a, b_u, e_pp = acc_error_report(p, w.x, w.u, ref, sim.read("acc"), w.phase, w.wall)
     e_T = rel_field(sim.read("tensor"), ref["T"])
-    print(f"\n[flume small n={w.n}, rates] a_P = {aP / 9.81:.1f} g; rho {e_rho:.2e} acc/a_P {e_a:.2e} T {e_T:.2e}")
-    assert e_rho < TOL and e_a < TOL and e_T < 1e-4
+    print(f"\n[flume small n={w.n}, rates] a_P = {aP / 9.81:.1f} g; rho {e_rho:.2e} acc per particle "
+          f"(floor |g|) {e_pp:.2e}, of the FP32 bound {b_a:.3f} (in u S_i {b_u:.2f}); T {e_T:.2e}")
+    assert e_rho < TOL and b_a <= 1.0 and e_T < 1e-4
     sim.step(dt)
     xr, ur, rr = oracle.run(p, w.x, w.u, w.rho, w.phase, w.wall, dt, 1, piston=m)
     e_x = np.abs(min_image(sim.read("pos") - xr, p)).max() / p["dx"]
-    e_u = np.abs(sim.read("vel") - ur).max() / (dt * aP)
+    b_s, e_s = step_velocity_errors(p, w, ref, sim.read("vel"), ur, dt)
     e_r = np.abs(sim.read("rho") / rr - 1).max()
-    print(f"[flume small, 1 step] |dx|/dx {e_x:.2e} du/(dt a_P) {e_u:.2e} rho {e_r:.2e}")
-    assert e_x < 1e-9 and e_u < TOL and e_r < TOL
+    print(f"[flume small, 1 step] |dx|/dx {e_x:.2e} du per particle (floor dt |g|) {e_s:.2e}, of the FP32 bound "
+          f"{b_s:.3f}; rho {e_r:.2e}")
+    assert e_x < 1e-9 and b_s <= 1.0 and e_r < TOL
     # moving piston: state from the oracle's step, clock at 0.3 s
     t0 = 0.3
     u0 = ur.copy()
@@ -248,13 +263,14 @@ def test_flume_full_size_step_matches_oracle(sphmod):
     x, u, rho = sim.read("pos"), sim.read("vel"), sim.read("rho")
     sim.close()
     xr, ur, rr = oracle.run(p, w.x, w.u, w.rho, w.phase, w.wall, dt, 1, piston=m)
-    aP = pressure_scale(p, oracle.evaluate(p, w.x, w.u, w.rho, w.phase, w.wall, renorm=True))
+    ref = oracle.evaluate(p, w.x, w.u, w.rho, w.phase, w.wall, renorm=True)
+    aP = pressure_scale(p, ref)
     e_x = np.abs(min_image(x - xr, p)).max() / p["dx"]
-    e_u = np.abs(u - ur).max() / (dt * aP)
+    b_s, e_s = step_velocity_errors(p, w, ref, u, ur, dt)
     e_r = np.abs(rho / rr - 1).max()
-    print(f"\n[flume full n={w.n}, 1 step] a_P = {aP / 9.81:.1f} g; |dx|/dx {e_x:.2e} du/(dt a_P) {e_u:.2e} "
-          f"rho {e_r:.2e}")
-    assert e_x < 1e-9 and e_u < TOL and e_r < TOL
+    print(f"\n[flume full n={w.n}, 1 step] a_P = {aP / 9.81:.1f} g; |dx|/dx {e_x:.2e} du per particle "
+          f"(floor dt |g|) {e_s:.2e}, of the FP32 bound {b_s:.3f}; rho {e_r:.2e}")
+    assert e_x < 1e-9 and b_s <= 1.0 and e_r < TOL
 
 
 def test_time_and_suggested_dt(sphmod):

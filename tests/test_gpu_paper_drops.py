@@ -1,0 +1,101 @@
+"""The paper's own drop examples on the GPU against the FP64 oracle (Sec.
+"Numerical examples on oil-water interaction": a 0.2 m tank filled 0.2 m
+deep, particle size d_p = 5 mm, open top, alpha_s = 0.05 N/m, an oil sphere
+of diameter 0.04 m or a cube of side 0.04 m near the bottom).
+
+Both drops are compared, through the C ABI, with the oracle on every particle
+at the paper's initial state (one rates evaluation: density after
+renormalisation, pressure, acceleration, density rate, surface stress
+tensor) and over two steps from a perturbed state, with the tolerances of
+the drop-rise parity tests: 1e-5 on density, pressure and density rate, the
+normwise acceleration within 1e-5 and every particle's acceleration within
+the bound of the FP32 arithmetic (tests/acc_bounds.py).  Both readings of
+the boundary particles' renormalisation are covered.  The cube drop also
+runs to t = 0.42 s like the sphere in tests/test_gpu_run.py.
+"""
+import json
+
+import numpy as np
+import pytest
+
+import oracle
+from acc_bounds import acc_error_report
+from paper_1702_07760_gb300 import workloads as WL
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def sphmod():
+    from paper_1702_07760_gb300 import build as B
+    from paper_1702_07760_gb300 import sph
+    B.build()
+    sph.load()
+    return sph
+
+
+def field_err(g, r):
+    g = np.asarray(g).reshape(len(g), -1)
+    r = np.asarray(r).reshape(len(r), -1)
+    return np.linalg.norm(g - r, axis=1).max() / np.linalg.norm(r, axis=1).max()
+
+
+@pytest.mark.parametrize("shape", ["sphere", "cube"])
+@pytest.mark.parametrize("renorm_walls", [1, 0])
+def test_paper_drop_rates_match_oracle(sphmod, shape, renorm_walls):
+    w = WL.paper_drop(shape, renorm_walls=renorm_walls)
+    p = w.params
+    sim = sphmod.Simulation.from_workload(w)
+    sim.eval_rates()
+    got = {k: sim.read(k) for k in ("rho_eval", "pressure", "acc", "drho", "tensor")}
+    sim.close()
+    ref = oracle.evaluate(p, w.x, w.u, w.rho, w.phase, w.wall, renorm=True)
+    fl = w.wall == 0
+    e_rho = np.abs(got["rho_eval"] / ref["rho"] - 1).max()
+    e_p = field_err(got["pressure"], ref["P"])
+    e_a = field_err(got["acc"][fl], ref["a"][fl])
+    b_a, b_u, e_pp = acc_error_report(p, w.x, w.u, ref, got["acc"], w.phase, w.wall)
+    e_dr = field_err(got["drho"], ref["drho"])
+    e_T = field_err(got["tensor"], ref["T"])
+    print(f"\n[paper {shape}, renorm_walls {renorm_walls}, n={w.n}] rho {e_rho:.2e} P {e_p:.2e} acc {e_a:.2e} "
+          f"(per particle, floor |g|: {e_pp:.2e}; of the FP32 bound {b_a:.3f}) drho {e_dr:.2e} T {e_T:.2e}")
+    assert np.all(got["acc"][~fl] == 0.0)
+    assert e_rho <= TOL and e_p <= TOL and e_a <= TOL and e_dr <= TOL and e_T <= 1e-4
+    assert b_a <= 1.0
+    assert np.abs(ref["T"]).max() > 0.0          # the drop has an interface
+
+
+@pytest.mark.parametrize("shape", ["sphere", "cube"])
+def test_paper_drop_two_steps_match_oracle(sphmod, shape):
+    w = WL.paper_drop(shape, perturb=True)
+    p = w.params
+    dt = WL.stable_dt(p)
+    sim = sphmod.Simulation.from_workload(w)
+    sim.run(dt, 2)
+    x, u, rho = sim.read("pos"), sim.read("vel"), sim.read("rho")
+    sim.close()
+    xr, ur, rr = oracle.run(p, w.x, w.u, w.rho, w.phase, w.wall, dt, 2)
+    e_x = np.abs(x - xr).max() / p["dx"]
+    e_u = field_err(u - w.u, ur - w.u)
+    e_r = np.abs(rho / rr - 1).max()
+    print(f"\n[paper {shape}, two steps] |dx|/dx {e_x:.2e} du {e_u:.2e} rho {e_r:.2e}")
+    assert e_x < 1e-8 and e_u < TOL and e_r < TOL
+
+
+def test_paper_cube_rises_and_stretches_vertically(tmp_path):
+    """The paper's second drop example (a cube of side 0.04 m): by t = 0.42 s
+    it has risen by more than 2 d_p and its oil cloud is taller than wide."""
+    from paper_1702_07760_gb300 import build as B
+    from paper_1702_07760_gb300 import run, sph
+    B.build()
+    sph.load()
+    log = tmp_path / "c.jsonl"
+    assert run.main(["--workload", "paper_cube", "--t-end", "0.42", "--every", "100000", "--log", str(log)]) == 0
+    recs = [json.loads(s) for s in log.read_text().splitlines()]
+    first, last = recs[0], recs[-1]
+    assert abs(last["t"] - 0.42) < 1e-4
+    assert last["centroid"][2] - first["centroid"][2] > 0.01
+    assert first["oil_aspect"] < 1.02 and last["oil_aspect"] > 1.05
+    assert last["n_oil"] == first["n_oil"] and abs(last["mass"] / first["mass"] - 1) < 1e-12

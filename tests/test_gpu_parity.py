@@ -8,13 +8,19 @@ Tolerances (FP32 interactions against an FP64 oracle):
   |x_gpu - x_ref| / |x_ref| <= 1e-5 (density), and <= 1e-5 of the field's
   largest magnitude (density rate);
 * acceleration: max_i |a_gpu,i - a_ref,i| / max_i |a_ref,i| <= 1e-5 (the
-  normwise relative error), and the per-particle error is reported against
-  max(|a_ref,i|, |g|).
+  normwise relative error), and per particle the bound of the FP32
+  arithmetic, |a_gpu,i - a_ref,i| <= (k_i + 8) u S_i with S_i the sum of the
+  magnitudes of particle i's pair terms and u = 2^-24 (tests/acc_bounds.py).
+  The per-particle error against max(|a_ref,i|, |g|) is printed: it exceeds
+  1e-5 because the pressure sums cancel 50 to 400 times; storing positions
+  as int cell + FP32 offset alone (everything else exact) already gives
+  1.8e-5 on the 2-D parity state.
 """
 import numpy as np
 import pytest
 
 import oracle
+from acc_bounds import acc_error_report
 from paper_1702_07760_gb300 import workloads as WL
 
 pytestmark = pytest.mark.gpu
@@ -55,6 +61,9 @@ CASES = {
     # kinematic viscosity form (Eq. visc_1): nu = mu / rho0 per phase
     "2d_kinematic": lambda: WL.drop_tank(2, (40, 60), drop_d_dx=12, seed=8, perturb=True, visc_form=1),
     "3d_kinematic": lambda: WL.drop_tank(3, (20, 20, 36), drop_d_dx=10, seed=9, perturb=True, visc_form=1),
+    # boundary particles keep their continuity density (the long runs' stabilisation)
+    "2d_walls_kept": lambda: WL.drop_tank(2, (40, 60), drop_d_dx=12, seed=5, perturb=True, renorm_walls=0),
+    "3d_walls_kept": lambda: WL.drop_tank(3, (20, 20, 36), drop_d_dx=10, seed=7, perturb=True, renorm_walls=0),
 }
 
 
@@ -89,23 +98,24 @@ def test_single_evaluation_matches_oracle(sphmod, case):
     e_rho = np.abs(got["rho_eval"] / ref["rho"] - 1).max()
     e_p = rel_err_field(got["pressure"], ref["P"])
     e_a = rel_err_field(got["acc"][fl], ref["a"][fl])
-    e_a_pp = rel_err_particle(got["acc"][fl], ref["a"][fl], np.linalg.norm(p["g"]))
+    b_a, b_u, e_a_pp = acc_error_report(p, w.x, w.u, ref, got["acc"], w.phase, w.wall)
     e_dr = rel_err_field(got["drho"], ref["drho"])
     e_T = rel_err_field(got["tensor"], ref["T"])
     print(f"\n[{case}] n={w.n} rho {e_rho:.2e} P {e_p:.2e} acc {e_a:.2e} (per particle, floor |g|: "
-          f"{e_a_pp:.2e}) drho {e_dr:.2e} T {e_T:.2e}")
+          f"{e_a_pp:.2e}; of the FP32 bound {b_a:.3f}, in u S_i {b_u:.2f}) drho {e_dr:.2e} T {e_T:.2e}")
     assert np.all(got["acc"][~fl] == 0.0)
     assert e_rho <= TOL
     assert e_p <= TOL
     assert e_a <= TOL
+    assert b_a <= 1.0
     assert e_dr <= TOL
     assert e_T <= 1e-4
     sim.close()
 
 
-@pytest.mark.parametrize("visc_form", [0, 1])
-def test_one_step_matches_oracle(sphmod, visc_form):
-    w = WL.drop_2d(seed=2, perturb=True, visc_form=visc_form)
+@pytest.mark.parametrize("visc_form,renorm_walls", [(0, 1), (1, 1), (0, 0)])
+def test_one_step_matches_oracle(sphmod, visc_form, renorm_walls):
+    w = WL.drop_2d(seed=2, perturb=True, visc_form=visc_form, renorm_walls=renorm_walls)
     p = w.params
     dt = WL.stable_dt(p)
     sim = sphmod.Simulation.from_workload(w)
@@ -117,7 +127,8 @@ def test_one_step_matches_oracle(sphmod, visc_form):
     e_x = np.abs(x - xr).max() / dx
     e_u = rel_err_field(u - w.u, ur - w.u)        # velocity increment dt * a*
     e_r = np.abs(rho / rr - 1).max()
-    print(f"\n[one step, visc_form {visc_form}] |dx|/dx {e_x:.2e} du {e_u:.2e} rho {e_r:.2e}")
+    print(f"\n[one step, visc_form {visc_form}, renorm_walls {renorm_walls}] |dx|/dx {e_x:.2e} du {e_u:.2e} "
+          f"rho {e_r:.2e}")
     assert e_x < 1e-9
     assert e_u < TOL
     assert e_r < TOL
@@ -454,10 +465,11 @@ def test_full_size_3d_evaluation(sphmod):
     fl = w.wall == 0
     e_rho = np.abs(got_r / ref["rho"] - 1).max()
     e_a = rel_err_field(got_a[fl], ref["a"][fl])
-    e_a_pp = rel_err_particle(got_a[fl], ref["a"][fl], np.linalg.norm(p["g"]))
+    b_a, b_u, e_a_pp = acc_error_report(p, w.x, w.u, ref, got_a, w.phase, w.wall)
     e_dr = rel_err_field(got_d, ref["drho"])
-    print(f"\n[3d full n={w.n}] rho {e_rho:.2e} acc {e_a:.2e} (per particle {e_a_pp:.2e}) drho {e_dr:.2e}")
-    assert e_rho <= TOL and e_a <= TOL and e_dr <= TOL
+    print(f"\n[3d full n={w.n}] rho {e_rho:.2e} acc {e_a:.2e} (per particle {e_a_pp:.2e}; of the FP32 bound "
+          f"{b_a:.3f}, in u S_i {b_u:.2f}) drho {e_dr:.2e}")
+    assert e_rho <= TOL and e_a <= TOL and e_dr <= TOL and b_a <= 1.0
 
 
 def test_pinned_buffers_are_read_and_written_in_place(sphmod):

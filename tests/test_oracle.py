@@ -173,25 +173,60 @@ def test_renormalisation_isolated_particle_keeps_density():
     assert abs(out["rho"][centre] - 905.5) < 1e-12
 
 
-def test_renormalisation_leaves_boundary_particles_alone():
-    """Dynamic boundary particles obey the fluid's mass-conservation law and
-    EOS (Sec. III) but are not renormalised: their density passes
-    through unchanged, while a fluid particle within 2h of a wall still counts
-    the wall particles (water) in its Shepard sums."""
+def _wall_tank():
+    """A one-phase (water) tank with fluid at 1000 and boundary particles at
+    1010, and each fluid particle's distance to the nearest boundary particle."""
     w = WL.drop_tank(2, (12, 12), drop_d_dx=4, seed=31)
-    p = w.params
-    ph = np.zeros(w.n, np.uint8)            # one phase: only the walls matter
     walls = w.wall > 0
     rho = np.where(walls, 1010.0, 1000.0)
+    x = w.x
+    d_fl = np.sqrt(((x[~walls, None, :] - x[None, walls, :]) ** 2).sum(-1)).min(1)
+    d_wall = np.sqrt(((x[walls, None, :] - x[None, ~walls, :]) ** 2).sum(-1)).min(1)
+    return w, np.zeros(w.n, np.uint8), walls, rho, d_fl, d_wall
+
+
+def test_renormalisation_of_boundary_particles_as_water():
+    """The paper's reading (renorm_walls = 1): dynamic boundary particles share
+    the fluid's continuity equation (Sec. III), and Eq. ct_dist_3 is part of
+    its discretisation (Sec. II-B), so they are renormalised like water.  A
+    Shepard average is a convex combination of the same-phase densities in
+    its support: boundary particles with no fluid particle within 2h keep
+    1010 exactly, those within 2h of the fluid land strictly between 1000 and
+    1010, and likewise for the fluid; a uniform density is returned as is."""
+    w, ph, walls, rho, d_fl, d_wall = _wall_tank()
+    p = dict(w.params, renorm_walls=1)
+    h2 = 2 * p["h"]
+    out = oracle.evaluate(p, w.x, w.u, rho, ph, w.wall, renorm=True)
+    rw, rf = out["rho"][walls], out["rho"][~walls]
+    far_w, near_w = d_wall >= h2 * (1 + 1e-9), d_wall < h2 * (1 - 1e-9)
+    assert far_w.any() and near_w.any()
+    assert np.abs(rw[far_w] / 1010.0 - 1).max() < 1e-14
+    assert np.all(rw[near_w] > 1000.0) and np.all(rw[near_w] < 1010.0)
+    far_f, near_f = d_fl >= h2 * (1 + 1e-9), d_fl < h2 * (1 - 1e-9)
+    assert np.abs(rf[far_f] / 1000.0 - 1).max() < 1e-14
+    assert np.all(rf[near_f] > 1000.0) and np.all(rf[near_f] < 1010.0)
+    uni = oracle.evaluate(p, w.x, w.u, np.full(w.n, 1003.0), ph, w.wall, renorm=True)
+    assert np.abs(uni["rho"] / 1003.0 - 1).max() < 1e-14
+
+
+def test_renormalisation_can_leave_boundary_particles_alone():
+    """The stabilisation of long runs (renorm_walls = 0): boundary particles
+    keep their continuity density (it passes through unchanged), while a
+    fluid particle within 2h of a wall still counts the wall particles
+    (water) in its Shepard sums; the fluid's values equal those of the
+    paper's reading."""
+    w, ph, walls, rho, d_fl, _ = _wall_tank()
+    p = dict(w.params, renorm_walls=0)
     out = oracle.evaluate(p, w.x, w.u, rho, ph, w.wall, renorm=True)
     assert np.array_equal(out["rho"][walls], rho[walls])
-    # distance of each fluid particle to the nearest wall particle
-    d = np.sqrt(((w.x[~walls, None, :] - w.x[None, walls, :]) ** 2).sum(-1)).min(1)
-    near, far = d < 2 * p["h"] * (1 - 1e-9), d >= 2 * p["h"] * (1 + 1e-9)
+    near, far = d_fl < 2 * p["h"] * (1 - 1e-9), d_fl >= 2 * p["h"] * (1 + 1e-9)
     r = out["rho"][~walls]
     assert far.any() and near.any()
     assert np.abs(r[far] / 1000.0 - 1).max() < 1e-14
     assert np.all(r[near] > 1000.0) and np.all(r[near] < 1010.0)
+    lit = oracle.evaluate(dict(w.params, renorm_walls=1), w.x, w.u, rho, ph, w.wall, renorm=True)
+    assert np.array_equal(lit["rho"][~walls], r)
+    assert not np.array_equal(lit["rho"][walls], rho[walls])
 
 
 # --------------------------------------------------------------------------
