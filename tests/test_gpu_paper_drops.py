@@ -4,10 +4,11 @@ deep, particle size d_p = 5 mm, open top, alpha_s = 0.05 N/m, an oil sphere
 of diameter 0.04 m or a cube of side 0.04 m near the bottom).
 
 Both drops are compared, through the C ABI, with the oracle on every particle
-at the paper's initial state (one rates evaluation: density after
-renormalisation, pressure, acceleration, density rate, surface stress
-tensor) and over two steps from a perturbed state, with the tolerances of
-the drop-rise parity tests: 1e-5 on density, pressure and density rate, the
+in one rates evaluation (density after renormalisation, pressure,
+acceleration, density rate, surface stress tensor) from the parity state
+(seeded velocities and densities) and from the paper's initial state at
+rest, and over two steps from the parity state, with the tolerances of the
+drop-rise parity tests: 1e-5 on density, pressure and density rate, the
 normwise acceleration within 1e-5 and every particle's acceleration within
 the bound of the FP32 arithmetic (tests/acc_bounds.py).  Both readings of
 the boundary particles' renormalisation are covered.  The cube drop also
@@ -45,7 +46,9 @@ def field_err(g, r):
 @pytest.mark.parametrize("shape", ["sphere", "cube"])
 @pytest.mark.parametrize("renorm_walls", [1, 0])
 def test_paper_drop_rates_match_oracle(sphmod, shape, renorm_walls):
-    w = WL.paper_drop(shape, renorm_walls=renorm_walls)
+    """One rates evaluation from the parity state of the paper's tank (seeded
+    velocities and densities) against the oracle on every particle."""
+    w = WL.paper_drop(shape, renorm_walls=renorm_walls, perturb=True)
     p = w.params
     sim = sphmod.Simulation.from_workload(w)
     sim.eval_rates()
@@ -65,6 +68,30 @@ def test_paper_drop_rates_match_oracle(sphmod, shape, renorm_walls):
     assert e_rho <= TOL and e_p <= TOL and e_a <= TOL and e_dr <= TOL and e_T <= 1e-4
     assert b_a <= 1.0
     assert np.abs(ref["T"]).max() > 0.0          # the drop has an interface
+
+
+@pytest.mark.parametrize("shape", ["sphere", "cube"])
+def test_paper_drop_at_rest_matches_oracle(sphmod, shape):
+    """The paper's initial state itself: water at hydrostatic rest, so the
+    density rate is exactly zero and the fluid accelerations nearly cancel
+    (gravity against the pressure gradient; the drop's buoyancy and surface
+    tension remain).  The density rate must be exactly zero on the GPU too,
+    density and pressure within 1e-5, and every acceleration within the
+    bound of the FP32 arithmetic."""
+    w = WL.paper_drop(shape)
+    p = w.params
+    sim = sphmod.Simulation.from_workload(w)
+    sim.eval_rates()
+    got = {k: sim.read(k) for k in ("rho_eval", "pressure", "acc", "drho")}
+    sim.close()
+    ref = oracle.evaluate(p, w.x, w.u, w.rho, w.phase, w.wall, renorm=True)
+    e_rho = np.abs(got["rho_eval"] / ref["rho"] - 1).max()
+    e_p = field_err(got["pressure"], ref["P"])
+    b_a, b_u, e_pp = acc_error_report(p, w.x, w.u, ref, got["acc"], w.phase, w.wall)
+    print(f"\n[paper {shape} at rest, n={w.n}] rho {e_rho:.2e} P {e_p:.2e} acc per particle (floor |g|) "
+          f"{e_pp:.2e}, of the FP32 bound {b_a:.3f}")
+    assert np.all(ref["drho"] == 0.0) and np.all(got["drho"] == 0.0)
+    assert e_rho <= TOL and e_p <= TOL and b_a <= 1.0
 
 
 @pytest.mark.parametrize("shape", ["sphere", "cube"])
