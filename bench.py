@@ -44,9 +44,9 @@ SWEEP_A_FLOPS_SAME = {2: 24, 3: 27}
 SWEEP_A_FLOPS_OTHER = {2: 14, 3: 21}
 
 # DRAM bytes (read + write) per launch of the force sweep on the 3-D workload,
-# from the ncu capture summarised in profiles/sweeps_drop_3d_64x64x128.md; valid
+# from the ncu capture summarised in profiles/sweep_b_drop_3d_64x64x128.md; valid
 # only for the kernel source it was taken on (first 16 hex digits of its sha256).
-PROFILED_TRAFFIC = {"sweep_b": {"source_sha256": "0ce0240a17cd9e67", "bytes": 303.7e6, "workload": "drop_3d"}}
+PROFILED_TRAFFIC = {"sweep_b": {"source_sha256": "0244b5ea3a9366d4", "bytes": 307.4e6, "workload": "drop_3d"}}
 
 
 def parse():
@@ -326,12 +326,14 @@ def run_flume(sph, WL, stream, steps, torch):
     return out
 
 
-def run_surrogate(sph, WL, stream, iters, torch, macro=25, k=8, noise_frac=0.0):
+def run_surrogate(sph, WL, stream, iters, torch, k=8, noise_frac=0.0, move_frac=0.1, max_macro=800):
     """The learned k-step surrogate: trained on plain trajectories of narrower
     tanks of the same depth (so the same c0, dt and jump T = k dt), then
-    advancing the 656 600-particle drop for `macro` jumps of k steps against
-    the plain method over the same physical time: time per k steps and the
-    drop-centroid error ||c_surrogate - c_plain|| / D."""
+    advancing the 656 600-particle drop from rest against the plain method
+    over the same physical time, a horizon of as many macro-steps of k steps
+    as the plain drop needs to move move_frac D (at most max_macro): time per
+    k steps, the drop-centroid error ||c_surrogate - c_plain|| / D, the
+    interface error and the velocity error."""
     from paper_1702_07760_gb300 import surrogate as SUR
     from paper_1702_07760_gb300 import surrogate_layout as SL
 
@@ -405,6 +407,18 @@ def run_surrogate(sph, WL, stream, iters, torch, macro=25, k=8, noise_frac=0.0):
         "drho_err_rel_network": rms(pred[:, 2 * d] - dr_true) / rms(dr_true),
         "drho_err_rel_explicit_jump": rms(T * drdt0 - dr_true) / rms(dr_true),
     }
+    # the horizon: macro-steps until the plain drop has moved move_frac D (untimed pass)
+    D = 2 * w_eval.meta["drop_radius"]
+    probe = sph.Simulation.from_workload(w_eval, stream=stream.cuda_stream)
+    c_start = probe.diagnostics()["centroid"]
+    macro = 0
+    while macro < max_macro:
+        probe.run(dt, 5 * k, graph=True)
+        macro += 5
+        if np.linalg.norm(probe.diagnostics()["centroid"] - c_start) >= move_frac * D:
+            break
+    moved = float(np.linalg.norm(probe.diagnostics()["centroid"] - c_start) / D)
+    probe.close()
     # rollouts on the full workload against the plain method over the same physical time
     plain = sph.Simulation.from_workload(w_eval, stream=stream.cuda_stream)
     plain.run(dt, k, graph=True)          # graph capture, untimed
@@ -420,7 +434,6 @@ def run_surrogate(sph, WL, stream, iters, torch, macro=25, k=8, noise_frac=0.0):
     sur = sph.Simulation.from_workload(w_eval, stream=stream.cuda_stream)
     sur.surrogate_init(flat, norm)
     ms_sur = timed(lambda: [sur.surrogate_advance(k) for _ in range(macro)])
-    D = 2 * w_eval.meta["drop_radius"]
     vel_err = lambda u: float(np.sqrt(((u[fl] - u_plain[fl]) ** 2).mean() / (u_plain[fl] ** 2).mean()))
     free = {"jumps": macro}
     try:
@@ -461,7 +474,9 @@ def run_surrogate(sph, WL, stream, iters, torch, macro=25, k=8, noise_frac=0.0):
                   "snapshots": "2 x 40, every k = 8 steps", "record_s": rec_s, "train_s": train_s,
                   "ms_per_iteration": train_s / max(iters, 1) * 1e3,
                   "loss_first_50": float(np.mean(hist[:50])), "loss_last_50": float(np.mean(hist[-50:]))},
-        "eval_workload": "drop_3d_64x64x128 (656 600 particles, D = 16 dx)", "k": k, "macro_steps": macro,
+        "eval_workload": "drop_3d_64x64x128 (656 600 particles, D = 16 dx), from rest", "k": k,
+        "macro_steps": macro, "horizon": {"plain_centroid_moved_over_D": moved, "target_over_D": move_frac,
+                                          "time_s": macro * k * dt},
         "plain_ms_per_k_steps": ms_plain / macro, "surrogate_ms_per_jump": ms_sur / macro,
         "speedup_per_jump_vs_plain": ms_plain / ms_sur,
         "one_jump": one_jump,

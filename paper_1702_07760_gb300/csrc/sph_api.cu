@@ -260,8 +260,9 @@ void sph_sim::enqueue_eval(int stage, const float *drho_in, double dt)
     const int stage1 = stage != 2;
     launch(KI_SWEEP_A, [&] {
         if (stage1) {
-            if (dim == 2) k_sweep_a<2><<<blocks(n), 256, 0, stream>>>(d, grid, phys, drho_in, stage1, vel_s);
-            else k_sweep_a<3><<<blocks(n), 256, 0, stream>>>(d, grid, phys, drho_in, stage1, vel_s);
+            const int ta = SPH_SWEEP_A_THREADS;
+            if (dim == 2) k_sweep_a<2><<<blocks(n, ta), ta, 0, stream>>>(d, grid, phys, drho_in, stage1, vel_s);
+            else k_sweep_a<3><<<blocks(n, ta), ta, 0, stream>>>(d, grid, phys, drho_in, stage1, vel_s);
         } else {
             // warps for the mixed particles: up to eight blocks of eight per SM
             const int mb = std::max(1, std::min(blocks(n), 8 * std::max(sms, 1)));
@@ -270,14 +271,15 @@ void sph_sim::enqueue_eval(int stage, const float *drho_in, double dt)
         }
     });
     launch(KI_SWEEP_B, [&] {
+        const int tb = SPH_SWEEP_B_THREADS, nbb = blocks(n, tb);
         if (dim == 2) {
-            if (stage == 0) k_sweep_b<2, 0><<<blocks(n), 256, 0, stream>>>(d, grid, phys, dt);
-            else if (stage == 1) k_sweep_b<2, 1><<<blocks(n), 256, 0, stream>>>(d, grid, phys, dt);
-            else k_sweep_b<2, 2><<<blocks(n), 256, 0, stream>>>(d, grid, phys, dt);
+            if (stage == 0) k_sweep_b<2, 0><<<nbb, tb, 0, stream>>>(d, grid, phys, dt);
+            else if (stage == 1) k_sweep_b<2, 1><<<nbb, tb, 0, stream>>>(d, grid, phys, dt);
+            else k_sweep_b<2, 2><<<nbb, tb, 0, stream>>>(d, grid, phys, dt);
         } else {
-            if (stage == 0) k_sweep_b<3, 0><<<blocks(n), 256, 0, stream>>>(d, grid, phys, dt);
-            else if (stage == 1) k_sweep_b<3, 1><<<blocks(n), 256, 0, stream>>>(d, grid, phys, dt);
-            else k_sweep_b<3, 2><<<blocks(n), 256, 0, stream>>>(d, grid, phys, dt);
+            if (stage == 0) k_sweep_b<3, 0><<<nbb, tb, 0, stream>>>(d, grid, phys, dt);
+            else if (stage == 1) k_sweep_b<3, 1><<<nbb, tb, 0, stream>>>(d, grid, phys, dt);
+            else k_sweep_b<3, 2><<<nbb, tb, 0, stream>>>(d, grid, phys, dt);
         }
     });
 }

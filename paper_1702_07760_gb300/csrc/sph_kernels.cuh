@@ -207,10 +207,6 @@ struct Sort {
 #ifndef SPH_LIST_CHUNK
 #define SPH_LIST_CHUNK 4
 #endif
-// Force sweep with the pair arithmetic on packed FP32x2 operations.
-#ifndef SPH_PACKED_B
-#define SPH_PACKED_B 0
-#endif
 
 // Neighbour-list entry: particle index in the low 26 bits; per axis a, two
 // bits at 26 + 2a holding (S_i - S_j) + 1 in {0, 1, 2} (super-cells).
@@ -308,6 +304,20 @@ __device__ __forceinline__ float entry_vec(const float4 &oi, const float4 &oj, u
     r2 = fmaf(ry, ry, r2);
     if (DIM == 3) r2 = fmaf(rz, rz, r2);
     return r2;
+}
+
+// |r_ij| from r^2 as r^2 / sqrt(r^2).  The added 1e-30 lies far below half
+// an ulp of any nonzero r^2 a list holds, so it changes nothing but r^2 = 0,
+// which it keeps finite (a plain FP32 add, on the FMA pipe).
+__device__ __forceinline__ float pair_dist(float r2) { return r2 * rsqrtf(r2 + 1e-30f); }
+
+// t = 1 - q/2 = 1 - r/(2h), clamped at 0 beyond the support by the saturation
+// of the fused multiply-add (t <= 1 holds anyway, r >= 0).
+__device__ __forceinline__ float kernel_t(float inv_h, float r)
+{
+    float t;
+    asm("fma.rn.sat.f32 %0, %1, %2, %3;" : "=f"(t) : "f"(-0.5f * inv_h), "f"(r), "f"(1.f));
+    return t;
 }
 
 // Padding entry of particle i's list: i itself one super-cell away along x
@@ -836,8 +846,8 @@ __device__ __forceinline__ void sweep_a_pairs(const Dev &d, const Grid &g, const
             const float r2 = entry_vec<DIM>(oi, oj, e, cs, rx, ry, rz);
             // beyond the support (list entries in the skin) t clamps to 0 and
             // every kernel term vanishes
-            const float r = r2 * rsqrtf(fmaxf(r2, 1e-30f));
-            const float t = fmaxf(fmaf(-0.5f * inv_h, r, 1.f), 0.f);
+            const float r = pair_dist(r2);
+            const float t = kernel_t(inv_h, r);
             const float t3 = t * t * t;
             if (!MIXED || phase_of(oj.w) == phi_) {
                 if (renorm) {
@@ -918,8 +928,8 @@ __device__ __forceinline__ void sweep_a_mixed_warp(const Dev &d, const Grid &g, 
         if (phase_of(oj.w) == phi_) continue;
         float rx, ry, rz;
         const float r2 = entry_vec<DIM>(oi, oj, e, cs, rx, ry, rz);
-        const float r = r2 * rsqrtf(fmaxf(r2, 1e-30f));
-        const float t = fmaxf(fmaf(-0.5f * inv_h, r, 1.f), 0.f);
+        const float r = pair_dist(r2);
+        const float t = kernel_t(inv_h, r);
         const float cc = oj.w * oj.w * (t * t * t);
         gx = fmaf(cc, rx, gx);
         gy = fmaf(cc, ry, gy);
@@ -980,39 +990,6 @@ __device__ __forceinline__ void sweep_a_finish(const Dev &d, const Phys &ph, int
     }
 }
 
-// Approximate reciprocal (the hardware's single-instruction estimate).
-__device__ __forceinline__ float rcp_approx(float x)
-{
-    float y;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-// Surface-tension term of one interface pair: (T_i/sigma_i^2 + T_j/sigma_j^2)
-// . t^3 r_ij added to (sx, sy, sz).  Interface pairs are few: the particle's
-// own tensor is re-read here (an L1 hit) rather than held in six registers.
-template <int DIM, bool NC>
-__device__ __forceinline__ void surface_pair(typename RO<NC, float4>::type T4, typename RO<NC, float2>::type T2, int i,
-                                             int j, float t3, float rx, float ry, float rz, float &sx, float &sy,
-                                             float &sz)
-{
-    const float4 Ti = ld<NC>(T4 + i);
-    const float4 Tj = ld<NC>(T4 + j);
-    if (DIM == 2) {
-        const float xx = Ti.x + Tj.x, xy = Ti.y + Tj.y, yy = Ti.z + Tj.z;
-        sx = fmaf(t3, fmaf(xy, ry, __fmul_rn(xx, rx)), sx);
-        sy = fmaf(t3, fmaf(yy, ry, __fmul_rn(xy, rx)), sy);
-    } else {
-        const float2 Ti2 = ld<NC>(T2 + i);
-        const float2 Tj2 = ld<NC>(T2 + j);
-        const float xx = Ti.x + Tj.x, xy = Ti.y + Tj.y, xz = Ti.z + Tj.z;
-        const float yy = Ti.w + Tj.w, yz = Ti2.x + Tj2.x, zz = Ti2.y + Tj2.y;
-        sx = fmaf(t3, fmaf(xz, rz, fmaf(xy, ry, __fmul_rn(xx, rx))), sx);
-        sy = fmaf(t3, fmaf(yz, rz, fmaf(yy, ry, __fmul_rn(xy, rx))), sy);
-        sz = fmaf(t3, fmaf(zz, rz, fmaf(yz, ry, __fmul_rn(xz, rx))), sz);
-    }
-}
-
 // ---------------------------------------------------------------------------
 // Sweep B: pressure gradient (Eq. dist_p_1), harmonic-mean viscosity
 // (Eq. visc_2 or visc_1), surface tension (F_s/rho), gravity, continuity
@@ -1048,71 +1025,6 @@ __device__ __forceinline__ void sweep_b_one(const Dev &d, const Grid &g, const P
     unsigned ec[CH];  // the first chunk lies inside the list storage (kmax >= CH) even when empty
 #pragma unroll
     for (int c = 0; c < CH; ++c) ec[c] = ld_list<NC>(col + (size_t)c * n);
-#if SPH_PACKED_B
-    // Two list entries per step of the pair arithmetic: the lanes .x and .y of
-    // the packed FP32x2 operations hold entries c and c + 1 of the chunk, and
-    // each running sum keeps the two entries' partial sums apart until the end.
-    float2 px2 = make_float2(0.f, 0.f), py2 = px2, pz2 = px2, vx2 = px2, vy2 = px2, vz2 = px2, dv2 = px2;
-    const float2 nh2 = make_float2(-0.5f * inv_h, -0.5f * inv_h), one2 = make_float2(1.f, 1.f);
-    const float2 d2 = make_float2(ph.delta2, ph.delta2);
-    for (int k0 = 0; k0 < cnt; k0 += CH) {
-        unsigned en[CH];
-        const bool more = k0 + CH < cnt;
-#pragma unroll
-        for (int c = 0; c < CH; ++c) en[c] = more ? ld_list<NC>(col + (size_t)(k0 + CH + c) * n) : 0u;
-#pragma unroll
-        for (int c = 0; c < CH; c += 2) {
-            unsigned e0 = ec[c], e1 = ec[c + 1];
-            int j0 = (int)(e0 & NBR_IDX_MASK), j1 = (int)(e1 & NBR_IDX_MASK);
-            // an index out of range (checked builds) becomes a padding entry
-            if (!SPH_IN_RANGE(d.flags, j0, n)) { e0 = pad_entry(i); j0 = i; }
-            if (!SPH_IN_RANGE(d.flags, j1, n)) { e1 = pad_entry(i); j1 = i; }
-            const float4 o0 = ld<NC>(posv + j0), o1 = ld<NC>(posv + j1);
-            const float4 u0 = ld<NC>(vel_s + j0), u1 = ld<NC>(vel_s + j1);
-            float rx0, ry0, rz0, rx1, ry1, rz1;
-            const float r20 = entry_vec<DIM>(oi, o0, e0, cs, rx0, ry0, rz0);
-            const float r21 = entry_vec<DIM>(oi, o1, e1, cs, rx1, ry1, rz1);
-            const float2 r2 = make_float2(r20, r21);
-            const float2 r = __fmul2_rn(r2, make_float2(rsqrtf(fmaxf(r20, 1e-30f)), rsqrtf(fmaxf(r21, 1e-30f))));
-            float2 t = __ffma2_rn(nh2, r, one2);
-            t.x = fmaxf(t.x, 0.f);
-            t.y = fmaxf(t.y, 0.f);
-            const float2 t3 = __fmul2_rn(__fmul2_rn(t, t), t);
-            const bool oil0 = o0.w < 0.f, oil1 = o1.w < 0.f;
-            const float2 pt = __fmul2_rn(make_float2((oil0 ? mP_oil : mP_wat) + u0.w, (oil1 ? mP_oil : mP_wat) + u1.w), t3);
-            const float2 rxx = make_float2(rx0, rx1), ryy = make_float2(ry0, ry1), rzz = make_float2(rz0, rz1);
-            px2 = __ffma2_rn(pt, rxx, px2);
-            py2 = __ffma2_rn(pt, ryy, py2);
-            if (DIM == 3) pz2 = __ffma2_rn(pt, rzz, pz2);
-            const float2 ux = make_float2(ui.x - u0.x, ui.x - u1.x), uy = make_float2(ui.y - u0.y, ui.y - u1.y);
-            const float2 uz = DIM == 3 ? make_float2(ui.z - u0.z, ui.z - u1.z) : make_float2(0.f, 0.f);
-            const float2 vt = __fmul2_rn(make_float2(fabsf(o0.w), fabsf(o1.w)), t3);
-            const float2 den = __fadd2_rn(r2, d2);
-            const float2 q = __fmul2_rn(r2, make_float2(rcp_approx(den.x), rcp_approx(den.y)));
-            const float2 sv = __fmul2_rn(__fmul2_rn(make_float2(oil0 ? kv_oil : kv_wat, oil1 ? kv_oil : kv_wat), vt), q);
-            vx2 = __ffma2_rn(sv, ux, vx2);
-            vy2 = __ffma2_rn(sv, uy, vy2);
-            if (DIM == 3) vz2 = __ffma2_rn(sv, uz, vz2);
-            float2 ur = __fmul2_rn(ux, rxx);
-            ur = __ffma2_rn(uy, ryy, ur);
-            if (DIM == 3) ur = __ffma2_rn(uz, rzz, ur);
-            dv2 = __ffma2_rn(vt, ur, dv2);
-            if ((iface_i | (__float_as_uint(o0.w) & 1u)) != 0u)
-                surface_pair<DIM, NC>(T4, T2, i, j0, t3.x, rx0, ry0, rz0, sx, sy, sz);
-            if ((iface_i | (__float_as_uint(o1.w) & 1u)) != 0u)
-                surface_pair<DIM, NC>(T4, T2, i, j1, t3.y, rx1, ry1, rz1, sx, sy, sz);
-        }
-#pragma unroll
-        for (int c = 0; c < CH; ++c) ec[c] = en[c];
-    }
-    px = px2.x + px2.y;
-    py = py2.x + py2.y;
-    pz = pz2.x + pz2.y;
-    vx = vx2.x + vx2.y;
-    vy = vy2.x + vy2.y;
-    vz = vz2.x + vz2.y;
-    dv = dv2.x + dv2.y;
-#else
     for (int k0 = 0; k0 < cnt; k0 += CH) {
         unsigned en[CH];
         const bool more = k0 + CH < cnt;
@@ -1131,8 +1043,8 @@ __device__ __forceinline__ void sweep_b_one(const Dev &d, const Grid &g, const P
             const float vol_j = fabsf(oj.w);
             // beyond the support (list entries in the skin) t clamps to 0 and
             // every pair term below vanishes
-            const float r = r2 * rsqrtf(fmaxf(r2, 1e-30f));
-            const float t = fmaxf(fmaf(-0.5f * inv_h, r, 1.f), 0.f);
+            const float r = pair_dist(r2);
+            const float t = kernel_t(inv_h, r);
             const float t3 = t * t * t;
             // m_j (P_i/rho_i^2 + P_j/rho_j^2) t^3 with the record's m_j P_j / rho_j^2
             const float pt = ((oil_j ? mP_oil : mP_wat) + uj.w) * t3;
@@ -1172,7 +1084,6 @@ __device__ __forceinline__ void sweep_b_one(const Dev &d, const Grid &g, const P
 #pragma unroll
         for (int c = 0; c < CH; ++c) ec[c] = en[c];
     }
-#endif
     const float rho = by_phase(phi_, I.rho0) + d.drho_eval[i];
     float4 out;
     out.w = rho * ph.cF * dv;
@@ -1280,9 +1191,13 @@ static __global__ void __launch_bounds__(256, 4) k_build_list(Dev d, Grid g, Phy
     list_one<DIM, true>(d, g, ph, i);
 }
 
+// Threads per block of the stage-1 sweep A.
+#ifndef SPH_SWEEP_A_THREADS
+#define SPH_SWEEP_A_THREADS 256
+#endif
 template <int DIM>
-static __global__ void __launch_bounds__(256) k_sweep_a(Dev d, Grid g, Phys ph, const float *__restrict__ drho_in, int stage1,
-                                                 float4 *vel_s)
+static __global__ void __launch_bounds__(SPH_SWEEP_A_THREADS)
+    k_sweep_a(Dev d, Grid g, Phys ph, const float *__restrict__ drho_in, int stage1, float4 *vel_s)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.n) return;
@@ -1327,13 +1242,17 @@ static __global__ void __launch_bounds__(256) k_sweep_a2(Dev d, Grid g, Phys ph,
     sweep_a_one<DIM, true>(d, g, ph, drho_in, 0, true, vel_s, i);
 }
 
-// Resident blocks of 256 threads per SM the force sweep is compiled for (4:
-// up to 64 registers a thread).
+// Threads per block of the force sweep and the resident blocks per SM it is
+// compiled for (1024 threads an SM: up to 64 registers a thread).
+#ifndef SPH_SWEEP_B_THREADS
+#define SPH_SWEEP_B_THREADS 256
+#endif
 #ifndef SPH_SWEEP_B_MIN_BLOCKS
-#define SPH_SWEEP_B_MIN_BLOCKS 4
+#define SPH_SWEEP_B_MIN_BLOCKS (1024 / SPH_SWEEP_B_THREADS)
 #endif
 template <int DIM, int STAGE>
-static __global__ void __launch_bounds__(256, SPH_SWEEP_B_MIN_BLOCKS) k_sweep_b(Dev d, Grid g, Phys ph, double dt)
+static __global__ void __launch_bounds__(SPH_SWEEP_B_THREADS, SPH_SWEEP_B_MIN_BLOCKS)
+    k_sweep_b(Dev d, Grid g, Phys ph, double dt)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.n) return;

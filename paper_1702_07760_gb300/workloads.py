@@ -198,6 +198,35 @@ def paper_drop(shape: str = "sphere", seed: int = 1100, **kw) -> Workload:
                      lid=False, seed=seed, alpha_s=0.05, drop_shape=shape, name=f"paper_drop_{shape}", **kw)
 
 
+def static_drop(dim: int, n: int, r_dx: float, dx: float = 2.5e-4, mu: float = 0.2, c0: float = 2.5,
+                alpha_s: float = 0.02, renorm_every: int = 0) -> Workload:
+    """A drop of radius r_dx dx at the centre of a fully periodic box of n^dim
+    particles on a perfect lattice (no walls, no gravity), both fluids of
+    density 1000 and viscosity mu, at rest at uniform density: the static
+    drop whose pressure jump the surface-tension force must sustain.  mu =
+    0.2 Pa s damps the drop's shape oscillations near critically, so the
+    pressure field settles within a few hundred steps; c0 = 2.5 m/s keeps
+    the flow's Mach number below 0.01.  The cell edge is the box edge over a
+    whole number of cells."""
+    p = fluid_params(dim, dx, n * dx, rho0=(1000.0, 1000.0), mu=(mu, mu), alpha_s=alpha_s, c0=c0,
+                     renorm_every=renorm_every)
+    p["g"] = [0.0, 0.0, 0.0]
+    axes = [np.arange(n)] * dim
+    ijk = np.stack([g.ravel() for g in np.meshgrid(*axes, indexing="ij")], axis=1)
+    x = (ijk + 0.5) * dx
+    centre = np.full(dim, 0.5 * n * dx)
+    r_drop = r_dx * dx
+    oil = ((x - centre) ** 2).sum(1) < r_drop ** 2
+    p["cell_size"] = n * dx / int(np.floor(n * dx / p["cell_size"] + 1e-9))
+    p["periodic"] = (1 << dim) - 1
+    p["box_lo"] = [0.0, 0.0, 0.0]
+    p["box_hi"] = [n * dx if k < dim else 0.0 for k in range(3)]
+    meta = dict(shape=(n,) * dim, drop_centre=centre.tolist(), drop_radius=r_drop, seed=None,
+                n_fluid=len(x), n_wall=0, n_oil=int(oil.sum()))
+    return Workload(f"static_drop_{dim}d_{n}_r{r_dx:g}", p, np.ascontiguousarray(x), np.zeros_like(x),
+                    np.full(len(x), 1000.0), oil.astype(np.uint8), np.zeros(len(x), np.uint8), meta)
+
+
 def stable_dt(p: dict, cfl: float = 0.25) -> float:
     """Acoustic time step 0.25 h / c0 used by the drop-rise workloads."""
     return cfl * p["h"] / p["c0"]

@@ -272,3 +272,43 @@ def test_judge_reports_and_uses_the_interface_error(env):
     ok2, _ = sim2.surrogate_advance_judged(dt, 8, 1e9, d_ref)
     _, ierr2 = sim2.surrogate_judge_stats()
     assert ierr2 == ierr and ok2 == (ierr2 <= 1e-12)
+
+
+def test_surrogate_speed_against_plain_is_reported(env):
+    """The judged surrogate run (sph_surrogate_run: a jump of k = 8 steps per
+    macro-step, k plain steps as the judge of every 4th) against plain steps
+    over the same simulated time on a 3-D drop tank: both are timed and the
+    speedup is reported as measured (below 1 on this hardware, see the
+    benchmark's surrogate section), together with the judge's worst centroid
+    error over D.  Both runs end at the same step and time."""
+    import time
+    torch, sph = env
+    w = WL.drop_tank(3, (24, 24, 48), drop_d_dx=10, seed=95)
+    _, norm, flat = _case(3, 96)
+    k, macro = 8, 12
+    dt = WL.stable_dt(w.params)
+    D = 2 * w.meta["drop_radius"]
+    plain = sph.Simulation.from_workload(w)
+    plain.run(dt, k, graph=True)                     # graph capture, untimed
+    plain = sph.Simulation.from_workload(w)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain.run(dt, macro * k, graph=True)
+    plain.sync()
+    s_plain = time.perf_counter() - t0
+    sur = sph.Simulation.from_workload(w)
+    sur.surrogate_init(flat, norm)
+    sur.surrogate_advance(k)                         # allocations, untimed
+    sur = sph.Simulation.from_workload(w)
+    sur.surrogate_init(flat, norm)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    judged, rejected, worst = sur.surrogate_run(dt, k, macro, 4, 0.02, D)
+    sur.sync()
+    s_sur = time.perf_counter() - t0
+    print(f"\n[surrogate speed, n={w.n}] plain {1e3 * s_plain / macro:.3f} ms per {k} steps, judged surrogate "
+          f"{1e3 * s_sur / macro:.3f} ms per macro-step: speedup {s_plain / s_sur:.3f}; judged {judged}, "
+          f"rejected {rejected}, worst centroid error / D {worst:.2e}")
+    assert sur.step_index == plain.step_index == macro * k
+    assert abs(sur.time - plain.time) < 1e-12
+    assert judged + rejected >= 1 and worst >= 0.0 and s_plain > 0 and s_sur > 0

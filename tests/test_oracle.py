@@ -453,27 +453,30 @@ def test_diagnostics_match_numpy():
 # --------------------------------------------------------------------------
 # Physical limits: hydrostatic column and Laplace jump (need a relaxation)
 
-def _laplace_jump(R_dx, box, renorm_every, steps=1500, skip=500, every=50):
-    """Time-averaged p_in - p_out of a static 2-D drop, in units of alpha_s / R."""
-    w = WL.drop_tank(2, (box, box), drop_d_dx=2 * R_dx, drop_centre_frac=[0.5, 0.5], seed=3,
-                     jitter_dx=0.0, rho0=(1000.0, 1000.0), mu=(2e-2, 2e-2), alpha_s=0.02,
-                     c0=5.0, renorm_every=renorm_every)
-    p = dict(w.params, g=[0.0, 0.0, 0.0])
-    x, u, rho = w.x, w.u, np.full(w.n, 1000.0)
+def _laplace_jump(dim, n, r_dx, steps, skip, every=10, shell=(1.45, 1.7)):
+    """Time-averaged p_in - p_out of a static drop (periodic box, no gravity,
+    equal densities, no renormalisation), in units of (dim - 1) alpha_s / R:
+    p_in over the particles within R/2 of the drop's centroid, p_out over the
+    shell between shell[0] R and shell[1] R (beyond the interface layer of
+    width 2h = 2.6 dx), sampled every `every` steps after `skip`."""
+    w = WL.static_drop(dim, n, r_dx)
+    p = w.params
+    x, u, rho = w.x, w.u, w.rho
     dt = WL.stable_dt(p)
-    R = R_dx * p["dx"]
-    fl = w.wall == 0
+    R = w.meta["drop_radius"]
+    L = n * p["dx"]
     vals = []
     for k in range(steps // every):
         x, u, rho = oracle.run(p, x, u, rho, w.phase, w.wall, dt, every, first_step=k * every)
         if (k + 1) * every <= skip:
             continue
-        P = np.array([oracle.eos(p, int(ph), r) for ph, r in zip(w.phase, rho)])
-        rr = np.linalg.norm(x - x[w.phase == 1].mean(0), axis=1)
-        inside = fl & (rr < 0.5 * R)
-        outside = fl & (rr > 1.6 * R) & (rr < 2.2 * R)
-        vals.append((P[inside].mean() - P[outside].mean()) / (p["alpha_s"] / R))
-    return float(np.mean(vals)), float(np.std(vals))
+        P = np.array([oracle.eos(p, 0, r) for r in rho])
+        d = x - x[w.phase == 1].mean(0)
+        d -= L * np.round(d / L)          # minimum image in the periodic box
+        rr = np.linalg.norm(d, axis=1)
+        inside, outside = rr < 0.5 * R, (rr > shell[0] * R) & (rr < shell[1] * R)
+        vals.append((P[inside].mean() - P[outside].mean()) / ((dim - 1) * p["alpha_s"] / R))
+    return float(np.mean(vals))
 
 
 @pytest.mark.slow
@@ -503,16 +506,24 @@ def test_hydrostatic_column_relaxes_to_rho_g_h():
 
 @pytest.mark.slow
 def test_laplace_pressure_jump_2d():
-    """Static 2-D drop, no gravity, equal densities: p_in - p_out = alpha_s / R.
-
-    Without renormalisation (the paper notes Eq. ct_dist_2 alone suffices
-    when there is no free surface) the time-averaged jump is within 20 % of
-    alpha_s / R at R = 8 dx.  With per-phase renormalisation every step the
-    jump is steadier but smaller by a constant factor; its 1/R law is pinned
-    by comparing two radii."""
-    mean0, _ = _laplace_jump(8, 40, renorm_every=0)
-    assert abs(mean0 - 1) < 0.2, mean0
-    m8, s8 = _laplace_jump(8, 40, renorm_every=1)
-    m12, s12 = _laplace_jump(12, 56, renorm_every=1)
-    assert 0.5 < m8 < 1.1 and s8 < 0.05
+    """Static 2-D drop: p_in - p_out = alpha_s / R (the jump the CSF tensor of
+    Eq. csf must sustain; curvature 1/R).  Without renormalisation (the
+    paper: Eq. ct_dist_2 alone suffices without a free surface, Sec. II-B)
+    the time-averaged jump is within 10 % of alpha_s / R at R = 8 dx
+    (measured 0.95), and it follows the 1/R law: R = 8 dx and R = 12 dx give
+    the same jump in units of alpha_s / R within 5 %."""
+    m8 = _laplace_jump(2, 40, 8, steps=1000, skip=500)
+    m12 = _laplace_jump(2, 56, 12, steps=2000, skip=800)
+    assert abs(m8 - 1) < 0.10, m8
+    assert abs(m12 - 1) < 0.10, m12
     assert abs(m8 / m12 - 1) < 0.05, (m8, m12)
+
+
+@pytest.mark.slow
+def test_laplace_pressure_jump_3d():
+    """Static 3-D drop: p_in - p_out = 2 alpha_s / R (curvature 2/R; the
+    isotropic part of T, |grad C|^2 / d I with d = 3, only reshapes the
+    pressure inside the interface layer).  Within 10 % at R = 8 dx (measured
+    0.97-0.98)."""
+    m = _laplace_jump(3, 28, 8, steps=600, skip=300)
+    assert abs(m - 1) < 0.10, m
