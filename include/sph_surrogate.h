@@ -100,7 +100,9 @@ int sph_surrogate_judge_stats(sph_handle h, double *max_centroid_err, double *ma
  * an over-full neighbour list).  Returns SPH_OK when err <= tol and
  * SPH_EFALLBACK when the judge rejects the jump (the state is still the
  * plain result); an interface error above the tolerance of
- * sph_surrogate_set_interface_tol rejects it as well.  Waits for the stream. */
+ * sph_surrogate_set_interface_tol rejects it as well.  k_steps * dt must equal
+ * the network's jump span (t_jump of its normalisation block, to 1e-9
+ * relative), else SPH_EINVAL.  Waits for the stream. */
 int sph_surrogate_advance_judged(sph_handle h, double dt, int k_steps, double tol, double d_ref, double *err);
 
 /* n_macro macro-steps of k_steps plain steps each.  A macro-step is one
@@ -117,8 +119,9 @@ int sph_surrogate_advance_judged(sph_handle h, double dt, int k_steps, double to
  * stretch), the macro-steps since then are redone with plain steps, and
  * plain steps continue until the next judged macro-step.  Reports the
  * judged count, the rejected count (both kinds) and the largest judged
- * error (1e30 for a judged jump that broke the state).  Waits for the
- * stream. */
+ * error (1e30 for a judged jump that broke the state).  k_steps * dt must
+ * equal the network's jump span (t_jump of its normalisation block, to 1e-9
+ * relative), else SPH_EINVAL.  Waits for the stream. */
 int sph_surrogate_run(sph_handle h, double dt, int k_steps, int64_t n_macro, int judge_every, double tol,
                       double d_ref, int64_t *n_judged, int64_t *n_rejected, double *max_err);
 

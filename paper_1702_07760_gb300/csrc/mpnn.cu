@@ -1405,6 +1405,21 @@ bool state_error(int rc)
     return rc == SPH_ENONFINITE || rc == SPH_EDOMAIN || rc == SPH_ECAPACITY || rc == SPH_ECFL;
 }
 
+// The plain steps that judge or replace a jump must span the time the network
+// jumps (its normalisation block's t_jump): k_steps * dt = t_jump, up to the
+// rounding of either.
+int check_jump_span(const Surrogate &S, double dt, int k_steps)
+{
+    const double span = (double)k_steps * dt;
+    if (!(std::fabs(span - S.t_jump64) <= 1e-9 * S.t_jump64)) {
+        char m[200];
+        snprintf(m, sizeof m, "k_steps * dt = %.9g s differs from the network's jump span t_jump = %.9g s", span,
+                 S.t_jump64);
+        return set_error(SPH_EINVAL, m);
+    }
+    return SPH_OK;
+}
+
 // Snapshot buffers of the judged run (allocated once per surrogate).
 int judge_buffers(Surrogate &S, const SimView &v, sph_handle h)
 {
@@ -1460,6 +1475,7 @@ int sph_surrogate_advance_judged(sph_handle h, double dt, int k_steps, double to
     if (!S) return set_error(SPH_EINVAL, "no surrogate on this handle");
     if (!(dt > 0) || k_steps < 1 || !(tol > 0) || !(d_ref > 0))
         return set_error(SPH_EINVAL, "bad dt, k_steps, tol or d_ref");
+    if (int e = check_jump_span(*S, dt, k_steps)) return e;
     const SimView v = sim_view(h);
     int rc = judge_buffers(*S, v, h);
     if (rc) return rc;
@@ -1499,6 +1515,7 @@ int sph_surrogate_run(sph_handle h, double dt, int k_steps, int64_t n_macro, int
     if (!S) return set_error(SPH_EINVAL, "no surrogate on this handle");
     if (!(dt > 0) || k_steps < 1 || n_macro < 0 || judge_every < 0 || !(tol > 0) || !(d_ref > 0))
         return set_error(SPH_EINVAL, "bad dt, k_steps, n_macro, judge_every, tol or d_ref");
+    if (int e = check_jump_span(*S, dt, k_steps)) return e;
     const SimView v = sim_view(h);
     if (int e = judge_buffers(*S, v, h)) return e;
     S->max_cerr = S->max_ierr = 0.0;

@@ -29,7 +29,9 @@ def env():
     return torch, sph
 
 
-def _case(dim, seed):
+def _case(dim, seed, dt=None):
+    """A small grid-quantised tank, a normalisation block and seeded weights;
+    the network's jump spans 8 steps of dt (default: the tank's own step)."""
     if dim == 2:
         w = WL.drop_tank(2, (26, 30), drop_d_dx=10, seed=seed, perturb=True, quantise=16)
     else:
@@ -41,7 +43,7 @@ def _case(dim, seed):
     sd_in = np.concatenate([np.full(dim, 0.006 * c0), [1e-3], [1, 1], np.full(dim, 0.05), [1e-3]])
     mu_out = rng.normal(0, 1e-9, n_out)
     sd_out = np.concatenate([np.full(dim, 1e-6), np.full(dim, 1e-2), [1e-4]])
-    T = 8 * WL.stable_dt(w.params)
+    T = 8 * (dt if dt is not None else WL.stable_dt(w.params))
     norm = SL.make_norm(dim, mu_in, sd_in, mu_out, sd_out, k_ref=20.0 if dim == 2 else 80.0, t_jump=T,
                         sd_edge_u=0.008 * c0, sd_edge_rho=1.5e-3)
     flat = SL.init_weights(dim, seed=seed + 1, out_scale=1.0)
@@ -284,9 +286,9 @@ def test_surrogate_speed_against_plain_is_reported(env):
     import time
     torch, sph = env
     w = WL.drop_tank(3, (24, 24, 48), drop_d_dx=10, seed=95)
-    _, norm, flat = _case(3, 96)
     k, macro = 8, 12
     dt = WL.stable_dt(w.params)
+    _, norm, flat = _case(3, 96, dt=dt)
     D = 2 * w.meta["drop_radius"]
     plain = sph.Simulation.from_workload(w)
     plain.run(dt, k, graph=True)                     # graph capture, untimed
@@ -312,3 +314,7 @@ def test_surrogate_speed_against_plain_is_reported(env):
     assert sur.step_index == plain.step_index == macro * k
     assert abs(sur.time - plain.time) < 1e-12
     assert judged + rejected >= 1 and worst >= 0.0 and s_plain > 0 and s_sur > 0
+    # plain steps that do not span the network's jump are refused
+    with pytest.raises(sph.SphError) as e:
+        sur.surrogate_run(1.5 * dt, k, 1, 1, 0.02, D)
+    assert e.value.code == -1 and "jump span" in str(e.value)
