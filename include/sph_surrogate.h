@@ -117,7 +117,11 @@ int sph_surrogate_advance_judged(sph_handle h, double dt, int k_steps, double to
  * over-full neighbour list is rejected too: the state returns to the last
  * verified one (the start, or the result of the last judged or plain
  * stretch), the macro-steps since then are redone with plain steps, and
- * plain steps continue until the next judged macro-step.  Reports the
+ * plain steps continue until the next judged macro-step.  The same happens
+ * when the plain steps of a judged macro-step fail from the state the
+ * unjudged jumps before it left (a non-finite value, a particle outside the
+ * box, an over-full list, a step beyond the skin): that judged error counts
+ * as 1e30 and the jump as rejected.  Reports the
  * judged count, the rejected count (both kinds) and the largest judged
  * error (1e30 for a judged jump that broke the state).  k_steps * dt must
  * equal the network's jump span (t_jump of its normalisation block, to 1e-9

@@ -1535,7 +1535,19 @@ int sph_surrogate_run(sph_handle h, double dt, int k_steps, int64_t n_macro, int
             // surrogate jump and plain steps from the same state; the plain result is kept
             double err = 0.0;
             bool reject = false;
-            if ((rc = judged_jump(h, *S, v, dt, k_steps, d_ref, tol, &err, &reject))) return rc;
+            rc = judged_jump(h, *S, v, dt, k_steps, d_ref, tol, &err, &reject);
+            if (rc && !state_error(rc)) return rc;
+            if (rc) {
+                // the plain steps failed from the state the unjudged jumps left: back to
+                // the last verified state, plain steps from there
+                const int64_t redo = (mstep + 1 - mv) * k_steps;
+                if ((rc = sim_load_device(h, S->vx, S->vu, S->vr))) return rc;
+                if ((rc = sim_moved(h, -redo, -(double)(mstep + 1 - mv) * S->t_jump64))) return rc;
+                if ((rc = sph_run(h, dt, redo, 1))) return rc;
+                err = 1.0e30;
+                reject = true;
+                S->max_cerr = std::max(S->max_cerr, err);
+            }
             worst = std::max(worst, err);
             ++judged;
             fallback = reject;
