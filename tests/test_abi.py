@@ -1,6 +1,7 @@
 """CPU checks of the C ABI: the library builds, loads without a GPU, and
 exports every entry point that include/sph.h declares; the binding names the
 same set."""
+import ctypes as C
 import os
 import re
 import subprocess
@@ -63,6 +64,25 @@ def test_invalid_parameters_are_rejected_without_a_gpu(lib):
     ph[wl == 1] = 1
     with pytest.raises(sph.SphError):
         sph.Simulation(w.params, w.x, w.u, w.rho, ph, wl)
+    # the boundary-reading switch is 0 or 1, the reserved word 0
+    with pytest.raises(sph.SphError) as e:
+        sph.Simulation(dict(w.params, renorm_walls=2), w.x, w.u, w.rho, w.phase, w.wall)
+    assert e.value.code == -1 and "renorm_walls" in str(e.value)
+    prm = sph.make_params(w.params)
+    prm.reserved = 1
+    h = C.c_void_p()
+    rc = lib.sph_create(C.byref(prm), w.n, sph._dp(w.x), sph._dp(w.u), sph._dp(w.rho),
+                        w.phase.ctypes.data_as(C.POINTER(C.c_uint8)), w.wall.ctypes.data_as(C.POINTER(C.c_uint8)),
+                        None, C.byref(h))
+    assert rc == -1 and "reserved" in lib.sph_last_error().decode() and not h.value
+
+
+def test_fp32_peak_rejects_bad_arguments_without_a_gpu(lib):
+    t, m = C.c_double(), C.c_double()
+    assert lib.sph_fp32_peak(0, 16, None, C.byref(t), C.byref(m)) == -1
+    assert lib.sph_fp32_peak(9, 16, None, C.byref(t), C.byref(m)) == -1
+    assert lib.sph_fp32_peak(8, 0, None, C.byref(t), C.byref(m)) == -1
+    assert lib.sph_fp32_peak(8, 16, None, None, C.byref(m)) == -1
 
 
 def test_null_handles_are_rejected_without_a_gpu(lib):

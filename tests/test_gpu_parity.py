@@ -534,3 +534,18 @@ def test_perturbation_is_seeded_keyed_on_particle_id_and_fluid_only(sphmod):
     assert abs(dr.std() / 1e-4 - 1) < 0.05
     a.close()
     b.close()
+
+
+def test_fp32_peak_measurement_is_plausible(sphmod):
+    """sph_fp32_peak (the force sweep's roofline denominator): FMA chains on
+    every SM reach a rate between a quarter of and just above the unit-count
+    bound (number of SMs x 128 lanes x 2 flops x the maximum SM clock), and
+    longer chains give the same rate."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    bound = sms * 128 * 2 * 2.2e9 / 1e12
+    t1, ms1 = sphmod.fp32_peak(8, 2048)
+    t2, ms2 = sphmod.fp32_peak(8, 4096)
+    print(f"\n[fp32 peak] {t1:.1f} TFLOP/s ({ms1:.3f} ms), {t2:.1f} TFLOP/s ({ms2:.3f} ms); bound {bound:.1f}")
+    assert 0.25 * bound < t1 < bound and 0.25 * bound < t2 < bound
+    assert abs(t2 / t1 - 1) < 0.1 and ms2 > 1.5 * ms1
