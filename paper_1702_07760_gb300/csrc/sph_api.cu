@@ -494,7 +494,7 @@ __global__ void k_load_state(Dev d, Grid g, Phys ph, const double *x, const doub
     const float hx = __fmul_rn(hdt, (float)ua[0]), hy = __fmul_rn(hdt, (float)ua[1]), hz = __fmul_rn(hdt, (float)ua[2]);
     const float d1 = sq3(ex, ey, ez);
     const float d2 = sq3(ex + hx, ey + hy, ez + hz);
-    const float lim = (float)(0.98 * ph.skin);
+    const float lim = ph.skin98f;
     if (!(d1 <= lim * lim) || !(d2 <= lim * lim)) atomicOr(d.rebuild, 1u);
 }
 
@@ -911,6 +911,8 @@ int create_sim(const sph_params *params, int k, const int64_t *counts, const dou
     ph.RL2 = (float)(RL * RL);
     ph.RP = (float)(RL * (1.0 + 1e-4));
     ph.skin = P0.skin;
+    ph.skin2f = (float)(P0.skin * P0.skin);
+    ph.skin98f = (float)(0.98 * P0.skin);
     ph.kmax = P0.max_neighbours > 0 ? P0.max_neighbours : (dim == 2 ? 48 : 128);
     ph.kmax = (ph.kmax + SPH_LIST_CHUNK - 1) / SPH_LIST_CHUNK * SPH_LIST_CHUNK;  // lists hold whole chunks
     ph.cF = (float)(-5.0 * alpha_d / (h * h));

@@ -75,6 +75,8 @@ struct Phys {
     int kmax;           // neighbour-list capacity per particle
     int rebuild_every;  // 0: rebuild when a particle may leave the skin; k: every k steps
     double skin;        // allowed displacement since the last build (the list's margin)
+    float skin2f;       // (float)(skin * skin): the predictor's skin test
+    float skin98f;      // (float)(0.98 * skin): the corrector's rebuild test
 };
 
 // Constants of one instance.
@@ -458,6 +460,13 @@ __device__ __forceinline__ float4 cell_offset(const Grid &g, int c, const double
     return make_float4(o[0], o[1], o[2], 0.f);
 }
 
+// Every component of v finite (FP32 tests on the FMA/ALU pipes: the FP64
+// pipe of this part runs at 1/64 of the FP32 rate).
+__device__ __forceinline__ bool finite4(const float4 &v)
+{
+    return isfinite(v.x) && isfinite(v.y) && isfinite(v.z) && isfinite(v.w);
+}
+
 // Signed specific volume m/rho, negative for oil.
 __device__ __forceinline__ float signed_volume(const Inst &I, int phase, float drho, float &vol)
 {
@@ -597,17 +606,25 @@ __device__ __forceinline__ void rank_one(const Sort &s, const int *pid, const in
     if (SPH_IN_RANGE(s.flags, b + rank, s.n)) s.perm[b + rank] = k;
 }
 
-// Stage-1 records of particle k from its FP64 state.
+// Stage-1 records of particle k from its FP64 state; returns whether every
+// FP32 value of the records is finite (a non-finite FP64 position or
+// velocity gives a non-finite record), and the position and velocity
+// records through p_out and v_out.
 template <int DIM>
-__device__ __forceinline__ void stage_records(const Dev &d, const Grid &g, const Inst &I, int k, int c,
-                                              const double xa[3], const double ua[3], float dr, int oil)
+__device__ __forceinline__ bool stage_records(const Dev &d, const Grid &g, const Inst &I, int k, int c,
+                                              const double xa[3], const double ua[3], float dr, int oil,
+                                              float4 *p_out = nullptr, float4 *v_out = nullptr)
 {
     float4 p = cell_offset<DIM>(g, c, xa);
     float vol;
     p.w = signed_volume(I, oil, dr, vol);
+    const float4 v = make_float4((float)ua[0], (float)ua[1], (float)ua[2], 0.f);
     d.pos[k] = p;
     d.vd[k] = vol * dr;
-    d.velp[k] = make_float4((float)ua[0], (float)ua[1], (float)ua[2], 0.f);
+    d.velp[k] = v;
+    if (p_out) *p_out = p;
+    if (v_out) *v_out = v;
+    return finite4(p) && finite4(v);
 }
 
 // Gathers the state of sorted position k into the scratch set `dst` and
@@ -692,49 +709,62 @@ __device__ __forceinline__ void list_one(const Dev &d, const Grid &g, const Phys
 
 // Predictor: x* = x^n + dt/2 u^n, u* = u^n + dt/2 a^n, rho* = rho^n + dt/2 Drho^n;
 // the renormalised density becomes the state rho^n.  Writes the stage-2
-// records (pos, vd, velq).
+// records (pos, vd, velq).  o1 and u1 are the particle's stage-1 records
+// (the FP32 offset of x^n from its super-cell centre and the FP32 u^n): the
+// stage-2 offset is o1 + dt/2 u1 in one FP32 FMA per axis, within one
+// rounding of the offset of the FP64 x*, and x* itself is not needed (the
+// corrector integrates from x^n).  Only the velocity, which the stage keeps
+// to integrate x, goes through FP64 (the FP64 pipe of this part runs at 1/64
+// of the FP32 rate); the pistons' prescribed motion is evaluated in FP64.
 template <int DIM>
 __device__ __forceinline__ void predict_particle(const Dev &d, const Grid &g, const Phys &ph, const Inst &I, int k,
-                                                 float4 a, double dt)
+                                                 float4 a, double dt, const float4 &o1, const float4 &u1)
 {
     const uint8_t tg = d.tag[k];
     const float dr = d.drho_eval[k];
     d.drho[k] = dr;
-    const float drs = fmaf(0.5f * (float)dt, a.w, dr);
+    const float hdt = 0.5f * (float)dt;
+    const float drs = fmaf(hdt, a.w, dr);
     d.drho_stage[k] = drs;
-    double xs[3] = {0, 0, 0}, us[3] = {0, 0, 0};
+    double us[3] = {0, 0, 0};
     const double af[3] = {a.x, a.y, a.z};
-    bool finite = isfinite(drs);
 #pragma unroll
     for (int c = 0; c < DIM; ++c) {
-        const double x = d.x[(size_t)c * d.n + k], u = d.u[(size_t)c * d.n + k];
-        xs[c] = (tg & 2) ? x : fma(0.5 * dt, u, x);
+        const double u = d.u[(size_t)c * d.n + k];
         us[c] = (tg & 2) ? u : fma(0.5 * dt, af[c], u);
-        finite = finite && isfinite(us[c]) && isfinite(xs[c]);
     }
+    float4 p;
     if (tg & 4) {
         // piston: at X(t + dt/2) with velocity X'(t + dt/2) along its axis
         const Motion &m = *d.motion;
         const double t = d.clock[0];
         const double dX = motion_disp(m, t + 0.5 * dt) - motion_disp(m, t), U = motion_vel(m, t + 0.5 * dt);
+        double xs[3] = {0, 0, 0};
 #pragma unroll
         for (int c = 0; c < DIM; ++c) {
+            xs[c] = d.x[(size_t)c * d.n + k];
             if (c == m.axis) xs[c] += dX;
             us[c] = c == m.axis ? U : 0.0;
         }
+        p = cell_offset<DIM>(g, d.cell[k], xs);
+    } else if (tg & 2) {
+        p = make_float4(o1.x, o1.y, o1.z, 0.f);
+    } else {
+        p = make_float4(fmaf(hdt, u1.x, o1.x), fmaf(hdt, u1.y, o1.y), DIM == 3 ? fmaf(hdt, u1.z, o1.z) : 0.f, 0.f);
     }
-    float4 p = cell_offset<DIM>(g, d.cell[k], xs);
     // the neighbour list stays complete while no particle is farther than the
     // skin from where it was at the build
     const float4 p0 = d.pos0[k];
     const float ex = p.x - p0.x, ey = p.y - p0.y, ez = p.z - p0.z;
-    if (sq3(ex, ey, ez) > (float)(ph.skin * ph.skin)) atomicOr(d.flags, FLAG_SKIN);
+    if (sq3(ex, ey, ez) > ph.skin2f) atomicOr(d.flags, FLAG_SKIN);
     float vol;
     p.w = signed_volume(I, tg & 1, drs, vol);
+    const float4 v = make_float4((float)us[0], (float)us[1], (float)us[2], 0.f);
     d.pos[k] = p;
     d.vd[k] = vol * drs;
-    d.velq[k] = make_float4((float)us[0], (float)us[1], (float)us[2], 0.f);
-    if (!finite) atomicOr(d.flags, FLAG_NONFINITE);
+    d.velq[k] = v;
+    // a non-finite FP64 state gives non-finite FP32 records
+    if (!(isfinite(drs) && finite4(p) && finite4(v))) atomicOr(d.flags, FLAG_NONFINITE);
 }
 
 // Corrector: x^{n+1} = x^n + dt u*, u^{n+1} = u^n + dt a*, rho^{n+1} = rho^n +
@@ -752,7 +782,6 @@ __device__ __forceinline__ void correct_particle(const Dev &d, const Grid &g, co
     const uint8_t tg = d.tag[k];
     const float dr = fmaf((float)dt, a.w, d.drho[k]);
     d.drho[k] = dr;
-    bool finite = isfinite(dr);
     double xa[3] = {0, 0, 0}, ua[3] = {0, 0, 0};
     const float4 us = d.velq[k];
     const double usa[3] = {us.x, us.y, us.z};
@@ -767,7 +796,6 @@ __device__ __forceinline__ void correct_particle(const Dev &d, const Grid &g, co
             d.x[(size_t)c * d.n + k] = xa[c];
             d.u[(size_t)c * d.n + k] = ua[c];
         }
-        finite = finite && isfinite(xa[c]) && isfinite(ua[c]);
     }
     if (tg & 4) {
         // piston: at X(t + dt) with velocity X'(t + dt) along its axis
@@ -782,20 +810,21 @@ __device__ __forceinline__ void correct_particle(const Dev &d, const Grid &g, co
             d.u[(size_t)c * d.n + k] = ua[c];
         }
     }
-    if (!finite) atomicOr(d.flags, FLAG_NONFINITE);
-    // stage-1 records of the next step (replaced by the gather if it rebuilds)
-    stage_records<DIM>(d, g, I, k, d.cell[k], xa, ua, dr, tg & 1);
+    // stage-1 records of the next step (replaced by the gather if it rebuilds);
+    // a non-finite FP64 state gives non-finite FP32 records
+    float4 p, v;
+    const bool finite = stage_records<DIM>(d, g, I, k, d.cell[k], xa, ua, dr, tg & 1, &p, &v);
+    if (!(finite && isfinite(dr))) atomicOr(d.flags, FLAG_NONFINITE);
     if (ph.rebuild_every == 0 && (!(tg & 2) || (tg & 4))) {
         // next step's stage positions: x^{n+1} and x^{n+1} + dt/2 u^{n+1};
         // rebuild before either can be farther than the skin from the build
-        const float4 p = d.pos[k], p0 = d.pos0[k];
+        const float4 p0 = d.pos0[k];
         const float hdt = 0.5f * (float)dt;
-        const float hx = __fmul_rn(hdt, (float)ua[0]), hy = __fmul_rn(hdt, (float)ua[1]),
-                    hz = __fmul_rn(hdt, (float)ua[2]);
+        const float hx = __fmul_rn(hdt, v.x), hy = __fmul_rn(hdt, v.y), hz = __fmul_rn(hdt, v.z);
         const float ex = p.x - p0.x, ey = p.y - p0.y, ez = p.z - p0.z;
         const float d1 = sq3(ex, ey, ez);
         const float d2 = sq3(ex + hx, ey + hy, ez + hz);
-        const float lim = (float)(0.98 * ph.skin);
+        const float lim = ph.skin98f;
         if (fmaxf(d1, d2) > lim * lim) atomicOr(d.rebuild, 1u);
     }
 }
@@ -1097,7 +1126,7 @@ __device__ __forceinline__ void sweep_b_one(const Dev &d, const Grid &g, const P
         out.z = DIM == 3 ? fmaf(sf, sz, fmaf(vf, vz, __fmul_rn(-ph.cF, pz))) + ph.gf[2] : 0.f;
     }
     d.acc[i] = out;
-    if (STAGE == 1) predict_particle<DIM>(d, g, ph, I, i, out, dt * I.dt_scale);
+    if (STAGE == 1) predict_particle<DIM>(d, g, ph, I, i, out, dt * I.dt_scale, oi, ui);
     if (STAGE == 2) {
         correct_particle<DIM>(d, g, ph, I, i, out, dt * I.dt_scale);
         // the clock advances when the next step starts (every particle of
