@@ -1028,6 +1028,22 @@ int create_sim(const sph_params *params, int k, const int64_t *counts, const dou
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return cuda_fail(e);
         if ((e = cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return cuda_fail(e);
     }
+    {
+        // super-cell centres per axis (the FP64 offsets' origins)
+        std::vector<double> cen;
+        const int dims3[3] = {s->grid.nx, s->grid.ny, s->grid.nz};
+        for (int a = 0; a < 3; ++a) {
+            s->grid.cen_off[a] = (int)cen.size();
+            const int ns = dims3[a] / s->grid.f + 2;
+            for (int S = 0; S < ns; ++S) cen.push_back(std::fma((double)S + 0.5, s->grid.Ed, s->grid.lo[a]));
+        }
+        double *dcen = nullptr;
+        if (s->alloc(&dcen, cen.size())) return cleanup(SPH_ENOMEM);
+        if ((e = cudaMemcpyAsync(dcen, cen.data(), sizeof(double) * cen.size(), cudaMemcpyHostToDevice, st)) !=
+            cudaSuccess)
+            return cuda_fail(e);
+        s->grid.cen = dcen;
+    }
     if ((e = cudaMemsetAsync(s->bar, 0, sizeof(GridBarrier), st)) != cudaSuccess) return cuda_fail(e);
     if ((e = cudaMemsetAsync(s->clock, 0, 2 * sizeof(double), st)) != cudaSuccess) return cuda_fail(e);
     if ((e = cudaMemsetAsync(s->motion, 0, sizeof(Motion), st)) != cudaSuccess) return cuda_fail(e);
