@@ -897,6 +897,7 @@ int create_sim(const sph_params *params, int k, const int64_t *counts, const dou
     s->grid.f = P0.cell_size >= RL ? 1 : 2;
     s->grid.csd = P0.cell_size;
     s->grid.cs = (float)P0.cell_size;
+    s->grid.inv_cs = 1.0f / s->grid.cs;
     s->grid.Ed = s->grid.f * P0.cell_size;
     s->grid.Es = (float)s->grid.Ed;
     for (int c = 0; c < 3; ++c) s->grid.lo[c] = box_lo[c];

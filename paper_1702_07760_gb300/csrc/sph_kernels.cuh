@@ -98,6 +98,7 @@ struct Grid {
     int nx, ny, nz;     // cells per axis (nz = 1 in 2-D)
     int f;              // cells per super-cell edge: 1 or 2 (also the stencil half-width)
     float cs;           // cell edge (FP32)
+    float inv_cs;       // 1 / cs (FP32): row pruning and the hash's estimate
     float Es;           // super-cell edge (FP32): pair vectors
     double csd;         // cell edge (FP64): hashing
     double Ed;          // super-cell edge (FP64): offsets
@@ -389,9 +390,14 @@ __device__ __forceinline__ void for_each_candidate(const Grid &g, typename RO<NC
             const int dSy = Sy - (y >> fm);
             const int yw = y < 0 ? y + g.ny : (y >= g.ny ? y - g.ny : y);
             const float sy = (float)dSy * E;
-            const float xr = sqrtf(rem);
-            int xlo = max(cx + (int)floorf((px - xr) / e), cx - hw);
-            int xhi = min(cx + (int)floorf((px + xr) / e), cx + hw);
+            // the row's cells that reach the sphere of radius Rp; Rp exceeds
+            // every search radius by 1e-4 of the list radius, far more than
+            // the few-ulp error of the fast root and of the reciprocal
+            // (1e-6 of a cell), so no cell holding a particle within the
+            // search radius is left out
+            const float xr = rem * rsqrtf(rem + 1e-30f);
+            int xlo = max(cx + (int)floorf((px - xr) * g.inv_cs), cx - hw);
+            int xhi = min(cx + (int)floorf((px + xr) * g.inv_cs), cx + hw);
             if (!g.per[0]) {
                 xlo = max(xlo, 0);
                 xhi = min(xhi, g.nx - 1);
@@ -400,13 +406,8 @@ __device__ __forceinline__ void for_each_candidate(const Grid &g, typename RO<NC
             const int row = (zw * g.ny + yw) * g.nx;
             const unsigned cyz = ((unsigned)(dSy + 1) << (NBR_IDX_BITS + 2)) |
                                  ((unsigned)(dSz + 1) << (NBR_IDX_BITS + 4));
-            // the unwrapped range xlo..xhi in pieces of one image each (one
-            // piece unless x is periodic); the cells of a piece are
-            // contiguous in the sorted order
-            for (int img = -1; img <= 1; ++img) {
-                const int off = img * g.nx;
-                const int a = max(xlo, off), b = min(xhi, off + g.nx - 1);
-                if (a > b) continue;
+            // the particles of cells a..b of the row (one image)
+            auto piece = [&](int a, int b, int off) {
                 const int jb = ld<NC>(cstart + row + a - off), je = ld<NC>(cstart + row + b - off + 1);
                 // super-cell Sx covers the unwrapped cells [Sx*f, Sx*f + f)
                 const int b1 = ld<NC>(cstart + row + min(max(Sx * hw, a), b + 1) - off);
@@ -420,6 +421,17 @@ __device__ __forceinline__ void for_each_candidate(const Grid &g, typename RO<NC
                     float rx, ry, rz;
                     const float r2 = pair_vec<DIM>(oi, oj, sx, sy, sz, rx, ry, rz);
                     if (r2 < R2) fn(j, oj, rx, ry, rz, r2, cyz | (ex << NBR_IDX_BITS));
+                }
+            };
+            if (!g.per[0]) {
+                piece(xlo, xhi, 0);
+            } else {
+                // the unwrapped range xlo..xhi in pieces of one image each;
+                // the cells of a piece are contiguous in the sorted order
+                for (int img = -1; img <= 1; ++img) {
+                    const int off = img * g.nx;
+                    const int a = max(xlo, off), b = min(xhi, off + g.nx - 1);
+                    if (a <= b) piece(a, b, off);
                 }
             }
         }
@@ -494,7 +506,18 @@ __device__ __forceinline__ void hash_one(const Dev &d, const Grid &g, const Sort
             xa = wrap_coord(xa, g.lo[a], d.period[a]);
             d.x[(size_t)a * d.n + k] = xa;
         }
-        double sc = floor((xa - g.lo[a]) / g.csd);
+        // floor((x - lo) / cs) of the FP64 quotient, from an FP32 estimate
+        // where that is decisive: q32 = fl32(t) * fl32(1 / fl32(cs)) lies
+        // within 2.4e-7 |q| of t / cs (four FP32 roundings of at most 2^-24
+        // relative: cs, its reciprocal, t and the product), so when its
+        // fractional part keeps 4e-7 |q| + 1e-30 away from 0 and 1 both floors
+        // agree; otherwise (near a cell face, or not finite) the FP64
+        // division decides, as before
+        const double t = xa - g.lo[a];
+        const float q32 = __fmul_rn((float)t, g.inv_cs);
+        const float fl = floorf(q32), fr = q32 - fl, m = fmaf(4e-7f, fabsf(q32), 1e-30f);
+        double sc = (double)fl;
+        if (!(fr > m && fr < 1.f - m)) sc = floor(t / g.csd);
         if (g.per[a] && sc >= (double)dims[a]) sc = dims[a] - 1;  // rounding at the upper side
         if (isnan(xa)) {
             bad |= FLAG_NONFINITE;
