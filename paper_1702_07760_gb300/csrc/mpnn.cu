@@ -219,7 +219,7 @@ __device__ __forceinline__ bool edge_features(const Dev &d, const Grid &g, float
     ef[1] = ry * inv2h;
     if (DIM == 3) ef[2] = rz * inv2h;
     ef[DIM] = sqrtf(r2) * inv2h;
-    ef[DIM + 1] = phase_of(oj.w) != phi ? 1.f : 0.f;
+    ef[DIM + 1] = rec_phase(oj.w) != phi ? 1.f : 0.f;
     const float4 nfj = NF[j];
     ef[DIM + 2] = nfi.x - nfj.x;
     ef[DIM + 3] = nfi.y - nfj.y;
@@ -247,7 +247,7 @@ __device__ __forceinline__ bool edge_geom(const Dev &d, const Grid &g, float R2,
     ef[1] = ry * inv2h;
     if (DIM == 3) ef[2] = rz * inv2h;
     ef[DIM] = sqrtf(r2) * inv2h;
-    ef[DIM + 1] = phase_of(oj.w) != phi ? 1.f : 0.f;
+    ef[DIM + 1] = rec_phase(oj.w) != phi ? 1.f : 0.f;
     return true;
 }
 
@@ -423,7 +423,7 @@ __global__ void __launch_bounds__(EWF, 4) k_edge_fwd(Dev d, Grid g, float R2, fl
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
     int deg = 0;
     const float4 oi = d.pos[i];
-    const int phi = phase_of(oi.w);
+    const int phi = rec_phase(oi.w);
     const int cnt = d.ncnt[i];
     uint32_t(*slot)[SWD] = slots[wid];
     uint2(*qr)[32] = qrows[wid];
@@ -515,7 +515,7 @@ __global__ void __launch_bounds__(EW, 2) k_edge_bwd(Dev d, Grid g, float R2, flo
         dSi[3] = ds4.w * inv_kref;
         const float4 oi = d.pos[i];
         const float4 nfi = NF[i];
-        const int phi = phase_of(oi.w);
+        const int phi = rec_phase(oi.w);
         const int cnt = d.ncnt[i];
         float(*slot)[SWD] = slots[wid];
         for (int k0 = 0; k0 < cnt; k0 += 32) {

@@ -701,6 +701,7 @@ Inst make_inst(const sph_params &P)
         I.inv_mass[k] = (float)(1.0 / P.mass[k]);
         I.rho0[k] = (float)P.rho0[k];
         I.inv_rho0[k] = (float)(1.0 / P.rho0[k]);
+        I.vol0[k] = (float)(P.mass[k] / P.rho0[k]);
         I.beta[k] = (float)(P.rho0[k] * P.c0 * P.c0 / P.gamma);
     }
     for (int a = 0; a < 2; ++a)
@@ -956,7 +957,6 @@ int create_sim(const sph_params *params, int k, const int64_t *counts, const dou
         err |= s->alloc(&a0.cell, N);
         err |= s->alloc(&a0.pos0, N);
         err |= s->alloc(&a0.pos, N);
-        err |= s->alloc(&a0.vd, N);
         err |= s->alloc(&a0.posv, N);
         err |= s->alloc(&a0.velp, N);
         err |= s->alloc(&a0.velq, N);
@@ -1000,7 +1000,7 @@ int create_sim(const sph_params *params, int k, const int64_t *counts, const dou
     s->sort.flags = s->flags;
     Dev &a1 = s->buf[1];
     a1.cell = a0.cell; a1.pos0 = a0.pos0;
-    a1.pos = a0.pos; a1.vd = a0.vd; a1.posv = a0.posv; a1.velp = a0.velp; a1.velq = a0.velq; a1.pres = a0.pres;
+    a1.pos = a0.pos; a1.posv = a0.posv; a1.velp = a0.velp; a1.velq = a0.velq; a1.pres = a0.pres;
     a1.nbr = a0.nbr; a1.ncnt = a0.ncnt; a1.nflag = a0.nflag; a1.mixed = a0.mixed; a1.nmixed = a0.nmixed;
     a1.drho_stage = a0.drho_stage; a1.drho_eval = a0.drho_eval;
     a1.T4 = a0.T4; a1.T2 = a0.T2; a1.acc = a0.acc; a1.cstart = a0.cstart;

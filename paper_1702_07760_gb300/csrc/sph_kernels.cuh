@@ -87,6 +87,7 @@ struct Inst {
     float inv_rho0[2];
     float beta[2];      // rho0 c0^2 / gamma
     float kvis[4];      // [2*ph_i + ph_j]: 2 mu_ij (dynamic form) or 2 nu_ij (kinematic form)
+    float vol0[2];      // per-phase m / rho0: the volume at the reference density
     float alpha_s;      // surface tension coefficient
     float pad;
     double dt_scale;    // this instance's step is dt * dt_scale
@@ -122,9 +123,9 @@ struct Dev {
     int *cell;          // n, cell id (sorted order)
     const Inst *inst;   // instance table
     // stage arrays
-    float4 *pos;        // n, (offset from the super-cell centre xyz, +/- m/rho of the stage input; sign = phase)
+    float4 *pos;        // n, (offset from the super-cell centre xyz, w: (m/rho) * drho of the stage
+                        //     input with its lowest mantissa bit replaced by the phase; pack_vd)
     float4 *pos0;       // n, offset at the last list build (xyz): displacement since the build
-    float *vd;          // n, (m/rho) * drho of the stage input
     float4 *posv;       // n, (offset xyz, +/- m/rho after renormalisation with its lowest
                         //     mantissa bit replaced by the interface flag): sweep A output
     float4 *velp;       // n, stage 1: (u^n xyz, P/rho^2 from sweep A)
@@ -258,6 +259,20 @@ struct RO<false, T> {
 __device__ __forceinline__ int phase_of(float w) { return __float_as_uint(w) >> 31; }
 
 __device__ __forceinline__ float by_phase(int phase, const float (&a)[2]) { return phase ? a[1] : a[0]; }
+
+// w of a stage-input record (pos): vd = (m/rho) drho, the volume times the
+// density deviation, with its lowest mantissa bit replaced by the phase (1:
+// oil; a change of at most one unit in the last place of vd).  Within a
+// phase vd = V (rho - rho0) = m - rho0 V, so the record gives the volume too,
+// V = m/rho0 - vd/rho0, and the renormalisation sweep reads one 16-byte
+// record per neighbour.
+__device__ __forceinline__ float pack_vd(float vd, int oil)
+{
+    return __uint_as_float((__float_as_uint(vd) & ~1u) | (unsigned)oil);
+}
+__device__ __forceinline__ int rec_phase(float w) { return (int)(__float_as_uint(w) & 1u); }
+__device__ __forceinline__ float rec_vd(float w) { return __uint_as_float(__float_as_uint(w) & ~1u); }
+__device__ __forceinline__ float rec_vol(float vd, float vol0, float inv_rho0) { return fmaf(-inv_rho0, vd, vol0); }
 
 // (S_i - S_j) * E for axis a of an entry, exact: the code e in {0, 1, 2}
 // becomes the float e - 1 through the 2^23 + 2^22 mantissa trick.
@@ -481,11 +496,12 @@ __device__ __forceinline__ bool finite4(const float4 &v)
     return isfinite(v.x) && isfinite(v.y) && isfinite(v.z) && isfinite(v.w);
 }
 
-// Signed specific volume m/rho, negative for oil.
-__device__ __forceinline__ float signed_volume(const Inst &I, int phase, float drho, float &vol)
+// w of the stage-input record of a particle of the given phase and density
+// deviation: (m/rho) drho with the phase bit (pack_vd).
+__device__ __forceinline__ float record_w(const Inst &I, int phase, float drho)
 {
-    vol = by_phase(phase, I.mass) / (by_phase(phase, I.rho0) + drho);
-    return phase ? -vol : vol;
+    const float vol = by_phase(phase, I.mass) / (by_phase(phase, I.rho0) + drho);
+    return pack_vd(vol * drho, phase);
 }
 
 // ---------------------------------------------------------------------------
@@ -641,11 +657,9 @@ __device__ __forceinline__ bool stage_records(const Dev &d, const Grid &g, const
                                               float4 *p_out = nullptr, float4 *v_out = nullptr)
 {
     float4 p = cell_offset<DIM>(g, c, xa);
-    float vol;
-    p.w = signed_volume(I, oil, dr, vol);
+    p.w = record_w(I, oil, dr);
     const float4 v = make_float4((float)ua[0], (float)ua[1], (float)ua[2], 0.f);
     d.pos[k] = p;
-    d.vd[k] = vol * dr;
     d.velp[k] = v;
     if (p_out) *p_out = p;
     if (v_out) *v_out = v;
@@ -704,7 +718,7 @@ template <int DIM, bool NC>
 __device__ __forceinline__ void list_one(const Dev &d, const Grid &g, const Phys &ph, int i)
 {
     const float4 oi = d.pos[i];
-    const int phi_ = phase_of(oi.w);
+    const int phi_ = rec_phase(oi.w);
     int cnt = 0;
     int other = 0;
     const int n = d.n, kmax = ph.kmax;
@@ -714,7 +728,7 @@ __device__ __forceinline__ void list_one(const Dev &d, const Grid &g, const Phys
             if (j == i) return;
             if (cnt < kmax) nbr[(size_t)cnt * n + i] = (unsigned)j | code;
             ++cnt;
-            other |= phase_of(oj.w) != phi_;
+            other |= rec_phase(oj.w) != phi_;
         });
     if (cnt > kmax) {
         atomicOr(d.flags, FLAG_LIST);
@@ -734,7 +748,7 @@ __device__ __forceinline__ void list_one(const Dev &d, const Grid &g, const Phys
 
 // Predictor: x* = x^n + dt/2 u^n, u* = u^n + dt/2 a^n, rho* = rho^n + dt/2 Drho^n;
 // the renormalised density becomes the state rho^n.  Writes the stage-2
-// records (pos, vd, velq).  o1 and u1 are the particle's stage-1 records
+// records (pos, velq).  o1 and u1 are the particle's stage-1 records
 // (the FP32 offset of x^n from its super-cell centre and the FP32 u^n): the
 // stage-2 offset is o1 + dt/2 u1 in one FP32 FMA per axis, within one
 // rounding of the offset of the FP64 x*, and x* itself is not needed (the
@@ -782,11 +796,9 @@ __device__ __forceinline__ void predict_particle(const Dev &d, const Grid &g, co
     const float4 p0 = d.pos0[k];
     const float ex = p.x - p0.x, ey = p.y - p0.y, ez = p.z - p0.z;
     if (sq3(ex, ey, ez) > ph.skin2f) atomicOr(d.flags, FLAG_SKIN);
-    float vol;
-    p.w = signed_volume(I, tg & 1, drs, vol);
+    p.w = record_w(I, tg & 1, drs);
     const float4 v = make_float4((float)us[0], (float)us[1], (float)us[2], 0.f);
     d.pos[k] = p;
-    d.vd[k] = vol * drs;
     d.velq[k] = v;
     // a non-finite FP64 state gives non-finite FP32 records
     if (!(isfinite(drs) && finite4(p) && finite4(v))) atomicOr(d.flags, FLAG_NONFINITE);
@@ -869,16 +881,20 @@ __device__ __forceinline__ void correct_particle(const Dev &d, const Grid &g, co
 // every entry is same-phase.  The renormalisation sums are compensated per
 // chunk of list entries: the chunk's terms are summed with FMAs, and the
 // chunk sum enters the Kahan sums (s, c).
+// The pair sums of sweep A over particle i's list.  Each neighbour's volume
+// comes from its record (rec_vol) with the constants of its phase: own
+// (vol0, irho0) for the renormalisation, the other phase's (vol0_o,
+// irho0_o) for the colour gradient.
 template <int DIM, bool NC, bool MIXED>
 __device__ __forceinline__ void sweep_a_pairs(const Dev &d, const Grid &g, const Phys &ph, int i, const float4 &oi,
-                                              int phi_, int renorm, float &s1, float &c1, float &s2, float &c2,
+                                              int phi_, int renorm, float vol0, float irho0, float vol0_o,
+                                              float irho0_o, float &s1, float &c1, float &s2, float &c2,
                                               float &gx, float &gy, float &gz)
 {
     const float inv_h = ph.inv_h, cs = g.Es;
     const int n = d.n, cnt = d.ncnt[i];
     typename RO<NC, unsigned>::type col = d.nbr + i;
     typename RO<NC, float4>::type pos = d.pos;
-    typename RO<NC, float>::type vd = d.vd;
     // the list holds whole chunks (padding entries feed zero terms)
     constexpr int CH = SPH_LIST_CHUNK;
     unsigned ec[CH];  // the first chunk lies inside the list storage (kmax >= CH) even when empty
@@ -903,15 +919,17 @@ __device__ __forceinline__ void sweep_a_pairs(const Dev &d, const Grid &g, const
             const float r = pair_dist(r2);
             const float t = kernel_t(inv_h, r);
             const float t3 = t * t * t;
-            if (!MIXED || phase_of(oj.w) == phi_) {
+            const float vdj = rec_vd(oj.w);
+            if (!MIXED || rec_phase(oj.w) == phi_) {
                 if (renorm) {
                     // W / alpha_d = t^4 (2q + 1)
                     const float w = t3 * t * fmaf(2.f * inv_h, r, 1.f);
-                    p1 = fmaf(fabsf(oj.w), w, p1);
-                    p2 = fmaf(ld<NC>(vd + j), w, p2);
+                    p1 = fmaf(rec_vol(vdj, vol0, irho0), w, p1);
+                    p2 = fmaf(vdj, w, p2);
                 }
             } else {
-                const float cc = oj.w * oj.w * t3;
+                const float vj = rec_vol(vdj, vol0_o, irho0_o);
+                const float cc = vj * vj * t3;
                 gx = fmaf(cc, rx, gx);
                 gy = fmaf(cc, ry, gy);
                 if (DIM == 3) gz = fmaf(cc, rz, gz);
@@ -927,9 +945,9 @@ __device__ __forceinline__ void sweep_a_pairs(const Dev &d, const Grid &g, const
 }
 
 template <int DIM>
-__device__ __forceinline__ void sweep_a_finish(const Dev &d, const Phys &ph, int i, const float4 &oi, int phi_,
-                                               float drho, float gx, float gy, float gz, float4 *vel_s,
-                                               bool write_t = true);
+__device__ __forceinline__ void sweep_a_finish(const Dev &d, const Phys &ph, const Inst &I, int i, const float4 &oi,
+                                               int phi_, float vol_in, float drho, float gx, float gy, float gz,
+                                               float4 *vel_s, bool write_t = true);
 
 // skip_mixed (stage 2): the particles with an other-phase neighbour are left
 // to the warp-per-particle pass (sweep_a_mixed_warp).
@@ -940,22 +958,30 @@ __device__ __forceinline__ void sweep_a_one(const Dev &d, const Grid &g, const P
     const bool other = d.nflag[i] & 1;
     if (skip_mixed && other) return;
     const float4 oi = d.pos[i];
-    const int phi_ = phase_of(oi.w);
+    const int phi_ = rec_phase(oi.w);
+    const Inst &I = d.inst[d.iid[i]];
     // boundary particles share the fluid's continuity equation (Sec. III),
     // whose discretisation includes Eq. ct_dist_3, so by default they are
     // renormalised as water; with renorm_walls off they keep the density
     // continuity gives them and only enter the fluid's sums as water
     const int renorm_i = renorm && (ph.renorm_walls || !(d.tag[i] & 2));
+    const float vol0 = by_phase(phi_, I.vol0), irho0 = by_phase(phi_, I.inv_rho0);
+    const float vol0_o = by_phase(phi_ ^ 1, I.vol0), irho0_o = by_phase(phi_ ^ 1, I.inv_rho0);
     // self term: W(0)/alpha_d = 1
-    float s1 = fabsf(oi.w), c1 = 0.f, s2 = d.vd[i], c2 = 0.f;
+    const float vdi = rec_vd(oi.w), vi = rec_vol(vdi, vol0, irho0);
+    float s1 = vi, c1 = 0.f, s2 = vdi, c2 = 0.f;
     float gx = 0.f, gy = 0.f, gz = 0.f;
     // particles with no other-phase neighbour (the bulk) take the loop
     // without the per-pair phase test
-    if (other) sweep_a_pairs<DIM, NC, true>(d, g, ph, i, oi, phi_, renorm_i, s1, c1, s2, c2, gx, gy, gz);
-    else if (renorm_i) sweep_a_pairs<DIM, NC, false>(d, g, ph, i, oi, phi_, 1, s1, c1, s2, c2, gx, gy, gz);
+    if (other)
+        sweep_a_pairs<DIM, NC, true>(d, g, ph, i, oi, phi_, renorm_i, vol0, irho0, vol0_o, irho0_o, s1, c1, s2, c2,
+                                     gx, gy, gz);
+    else if (renorm_i)
+        sweep_a_pairs<DIM, NC, false>(d, g, ph, i, oi, phi_, 1, vol0, irho0, vol0_o, irho0_o, s1, c1, s2, c2, gx,
+                                      gy, gz);
     // at stage 2 a particle with no other-phase particle in its list keeps the
     // zero surface tensor that stage 1 wrote (no colour gradient either time)
-    sweep_a_finish<DIM>(d, ph, i, oi, phi_, renorm_i ? s2 / s1 : drho_in[i], gx, gy, gz, vel_s, !skip_mixed);
+    sweep_a_finish<DIM>(d, ph, I, i, oi, phi_, vi, renorm_i ? s2 / s1 : drho_in[i], gx, gy, gz, vel_s, !skip_mixed);
 }
 
 // Sweep A at stage 2 (no renormalisation: only the colour gradient) for a
@@ -969,7 +995,9 @@ __device__ __forceinline__ void sweep_a_mixed_warp(const Dev &d, const Grid &g, 
                                                    float4 *vel_s, int i, int lane)
 {
     const float4 oi = d.pos[i];
-    const int phi_ = phase_of(oi.w);
+    const int phi_ = rec_phase(oi.w);
+    const Inst &I = d.inst[d.iid[i]];
+    const float vol0_o = by_phase(phi_ ^ 1, I.vol0), irho0_o = by_phase(phi_ ^ 1, I.inv_rho0);
     const float inv_h = ph.inv_h, cs = g.Es;
     const int n = d.n, cnt = d.ncnt[i];
     typename RO<NC, float4>::type pos = d.pos;
@@ -979,12 +1007,13 @@ __device__ __forceinline__ void sweep_a_mixed_warp(const Dev &d, const Grid &g, 
         const int j = (int)(e & NBR_IDX_MASK);
         if (!SPH_IN_RANGE(d.flags, j, n)) continue;
         const float4 oj = ld<NC>(pos + j);
-        if (phase_of(oj.w) == phi_) continue;
+        if (rec_phase(oj.w) == phi_) continue;
         float rx, ry, rz;
         const float r2 = entry_vec<DIM>(oi, oj, e, cs, rx, ry, rz);
         const float r = pair_dist(r2);
         const float t = kernel_t(inv_h, r);
-        const float cc = oj.w * oj.w * (t * t * t);
+        const float vj = rec_vol(rec_vd(oj.w), vol0_o, irho0_o);
+        const float cc = vj * vj * (t * t * t);
         gx = fmaf(cc, rx, gx);
         gy = fmaf(cc, ry, gy);
         if (DIM == 3) gz = fmaf(cc, rz, gz);
@@ -995,23 +1024,24 @@ __device__ __forceinline__ void sweep_a_mixed_warp(const Dev &d, const Grid &g, 
         gy += __shfl_xor_sync(0xffffffffu, gy, o);
         if (DIM == 3) gz += __shfl_xor_sync(0xffffffffu, gz, o);
     }
-    if (lane == 0) sweep_a_finish<DIM>(d, ph, i, oi, phi_, drho_in[i], gx, gy, gz, vel_s);
+    if (lane == 0)
+        sweep_a_finish<DIM>(d, ph, I, i, oi, phi_, rec_vol(rec_vd(oi.w), by_phase(phi_, I.vol0), by_phase(phi_, I.inv_rho0)),
+                            drho_in[i], gx, gy, gz, vel_s);
 }
 
 // Sweep A's per-particle tail: stage density, equation of state, surface
 // tensor, and the records the force sweep gathers.
 template <int DIM>
-__device__ __forceinline__ void sweep_a_finish(const Dev &d, const Phys &ph, int i, const float4 &oi, int phi_,
-                                               float drho, float gx, float gy, float gz, float4 *vel_s,
-                                               bool write_t)
+__device__ __forceinline__ void sweep_a_finish(const Dev &d, const Phys &ph, const Inst &I, int i, const float4 &oi,
+                                               int phi_, float vol_in, float drho, float gx, float gy, float gz,
+                                               float4 *vel_s, bool write_t)
 {
-    const Inst &I = d.inst[d.iid[i]];
     d.drho_eval[i] = drho;
     const float rho = by_phase(phi_, I.rho0) + drho;
     const float vol = by_phase(phi_, I.mass) / rho;
     const float P = eos_tait7(by_phase(phi_, I.beta), __fmul_rn(drho, by_phase(phi_, I.inv_rho0)));
-    // grad C_i = sigma_i sum V_j^2 grad W_ij, sigma_i = 1/|V_i| (entry density)
-    const float sc = ph.cF / fabsf(oi.w);
+    // grad C_i = sigma_i sum V_j^2 grad W_ij, sigma_i = 1/V_i (entry density)
+    const float sc = ph.cF / vol_in;
     gx *= sc;
     gy *= sc;
     gz *= sc;
@@ -1552,11 +1582,11 @@ static __global__ void __launch_bounds__(256) k_pair_stats(Dev d, Grid g, Phys p
     int all = 0, other = 0;
     if (i < d.n) {
         const float4 oi = d.pos[i];
-        const int phi_ = phase_of(oi.w);
+        const int phi_ = rec_phase(oi.w);
         for_each_candidate<DIM, true>(g, d.cstart, d.pos, d.cell[i], oi, ph.R2, ph.RP,
                                       [&](int j, const float4 &oj, float, float, float, float, unsigned) {
                                           all += j != i;
-                                          other += phase_of(oj.w) != phi_;
+                                          other += rec_phase(oj.w) != phi_;
                                       });
     }
     for (int o = 16; o > 0; o >>= 1) {
