@@ -486,6 +486,9 @@ __global__ void k_load_state(Dev d, Grid g, Phys ph, const double *x, const doub
     }
     const float dr = (float)(rho[p] - (double)by_phase(tg & 1, I.rho0));
     d.drho[k] = dr;
+    // static boundary particles keep their velocity: one that is not at rest
+    // gives the force sweep its whole lists
+    if (static_wall(tg) && !(ua[0] == 0.0 && ua[1] == 0.0 && ua[2] == 0.0)) atomicOr(d.walls_moving, 1u);
     if (!(check_dt > 0)) return;
     stage_records<DIM>(d, g, I, k, d.cell[k], xa, ua, dr, tg & 1);
     const float4 q = d.pos[k], q0 = d.pos0[k];
@@ -537,6 +540,8 @@ int sph_sim::enqueue_read(int kind, bool integer, void *out, size_t bytes, size_
 
 void sph_sim::enqueue_load(const double *x, const double *u, const double *rho, double check_dt)
 {
+    // the load raises the flag again if a static boundary particle moves
+    cudaMemsetAsync(D().walls_moving, 0, sizeof(unsigned), stream);
     if (dim == 2) k_load_state<2><<<blocks(n), 256, 0, stream>>>(D(), grid, phys, x, u, rho, check_dt);
     else k_load_state<3><<<blocks(n), 256, 0, stream>>>(D(), grid, phys, x, u, rho, check_dt);
 }
@@ -963,6 +968,8 @@ int create_sim(const sph_params *params, int k, const int64_t *counts, const dou
         err |= s->alloc(&a0.pres, N);
         err |= s->alloc(&a0.nbr, N * (size_t)ph.kmax);
         err |= s->alloc(&a0.ncnt, N);
+        err |= s->alloc(&a0.nfcnt, N);
+        err |= s->alloc(&a0.walls_moving, 1);
         err |= s->alloc(&a0.nflag, N);
         err |= s->alloc(&a0.mixed, N);
         err |= s->alloc(&a0.nmixed, 1);
@@ -1001,7 +1008,7 @@ int create_sim(const sph_params *params, int k, const int64_t *counts, const dou
     Dev &a1 = s->buf[1];
     a1.cell = a0.cell; a1.pos0 = a0.pos0;
     a1.pos = a0.pos; a1.posv = a0.posv; a1.velp = a0.velp; a1.velq = a0.velq; a1.pres = a0.pres;
-    a1.nbr = a0.nbr; a1.ncnt = a0.ncnt; a1.nflag = a0.nflag; a1.mixed = a0.mixed; a1.nmixed = a0.nmixed;
+    a1.nbr = a0.nbr; a1.ncnt = a0.ncnt; a1.nfcnt = a0.nfcnt; a1.walls_moving = a0.walls_moving; a1.nflag = a0.nflag; a1.mixed = a0.mixed; a1.nmixed = a0.nmixed;
     a1.drho_stage = a0.drho_stage; a1.drho_eval = a0.drho_eval;
     a1.T4 = a0.T4; a1.T2 = a0.T2; a1.acc = a0.acc; a1.cstart = a0.cstart;
     a0.flags = a1.flags = s->flags;

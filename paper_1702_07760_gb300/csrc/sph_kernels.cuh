@@ -140,6 +140,11 @@ struct Dev {
     // neighbour list
     unsigned *nbr;      // kmax * n, entry k of particle i at nbr[k * n + i]
     int *ncnt;          // n, list length
+    int *nfcnt;         // n, the part of the list the force sweep visits while *walls_moving is 0
+                        //     (static boundary particles: the leading part without static
+                        //     boundary neighbours; everyone else: the whole list)
+    unsigned *walls_moving;  // 1 word: nonzero when a static boundary particle has a nonzero
+                        //     velocity (set by the load of a state; boundary particles keep u)
     uint8_t *nflag;     // n, bit0: an other-phase particle lies within the list radius
     int *mixed;         // n, the particles with nflag bit 0 set, in no particular order
     int *nmixed;        // 1 word: their number (reset by the hash, appended by the list build)
@@ -257,6 +262,9 @@ struct RO<false, T> {
 };
 
 __device__ __forceinline__ int phase_of(float w) { return __float_as_uint(w) >> 31; }
+
+// Boundary particle that is not a piston (tag bit 1 without bit 2).
+__device__ __forceinline__ bool static_wall(unsigned tag) { return (tag & 6u) == 2u; }
 
 __device__ __forceinline__ float by_phase(int phase, const float (&a)[2]) { return phase ? a[1] : a[0]; }
 
@@ -719,25 +727,46 @@ __device__ __forceinline__ void list_one(const Dev &d, const Grid &g, const Phys
 {
     const float4 oi = d.pos[i];
     const int phi_ = rec_phase(oi.w);
-    int cnt = 0;
+    int cf = 0, cs = 0;  // entries at the front; static boundary entries at the back
     int other = 0;
     const int n = d.n, kmax = ph.kmax;
     unsigned *__restrict__ nbr = d.nbr;
+    typename RO<NC, uint8_t>::type tag = d.tag;
+    // a static boundary particle while every static boundary particle is at
+    // rest: its pairs with the others feed the force sweep nothing (u_ij = 0,
+    // and its own acceleration is not used), so they are written from the end
+    // of its column backwards and then moved behind the rest of its list,
+    // which the force sweep visits alone
+    const bool split = static_wall(d.tag[i]) && *(volatile unsigned *)d.walls_moving == 0u;
     for_each_candidate<DIM, NC>(g, d.cstart, d.pos, d.cell[i], oi, ph.RL2, ph.RP,
         [&](int j, const float4 &oj, float, float, float, float, unsigned code) {
             if (j == i) return;
-            if (cnt < kmax) nbr[(size_t)cnt * n + i] = (unsigned)j | code;
-            ++cnt;
+            const bool back = split && static_wall(ld<NC>(tag + j));
+            // entries past kmax are counted, not stored (the overflow is reported)
+            if (cf + cs < kmax) nbr[(size_t)(back ? kmax - 1 - cs : cf) * n + i] = (unsigned)j | code;
+            cf += !back;
+            cs += back;
             other |= rec_phase(oj.w) != phi_;
         });
+    // lists hold whole chunks (kmax is a multiple of the chunk), so the
+    // sweeps need no per-entry bound test
+    int nf = cf;
+    for (; nf % SPH_LIST_CHUNK; ++nf)
+        if (nf + cs < kmax) nbr[(size_t)nf * n + i] = pad_entry(i);
+    int cnt = nf + cs;
     if (cnt > kmax) {
         atomicOr(d.flags, FLAG_LIST);
         cnt = kmax;
+        nf = min(nf, kmax);
+    } else if (cs > 0) {
+        // the back entries (in reverse scan order) move down to follow the
+        // front part; every move goes to a lower or equal slot, in ascending
+        // order, so no entry is overwritten before it is read
+        for (int q = 0; q < cs; ++q) nbr[(size_t)(nf + q) * n + i] = nbr[(size_t)(kmax - cs + q) * n + i];
     }
-    // whole chunks (kmax is a multiple of the chunk), so the sweeps need no
-    // per-entry bound test
     for (; cnt % SPH_LIST_CHUNK; ++cnt) nbr[(size_t)cnt * n + i] = pad_entry(i);
     d.ncnt[i] = cnt;
+    d.nfcnt[i] = split ? nf : cnt;
     d.nflag[i] = (uint8_t)other;
     if (other) d.mixed[atomicAdd(d.nmixed, 1)] = i;
 }
@@ -1123,7 +1152,10 @@ __device__ __forceinline__ void sweep_b_one(const Dev &d, const Grid &g, const P
     float sx = 0.f, sy = 0.f, sz = 0.f;    // sum (T_i/sigma_i^2 + T_j/sigma_j^2) . t^3 r_ij
     float dv = 0.f;                        // sum V_j t^3 u_ij . r_ij
     const float inv_h = ph.inv_h, cs = g.Es;
-    const int n = d.n, cnt = d.ncnt[i];
+    // a static boundary particle's pairs with the others (at the end of its
+    // list) add exact zeros while those are at rest: u_ij = 0 in the
+    // continuity term, and the acceleration of a boundary particle is not used
+    const int n = d.n, cnt = ld<NC>(d.walls_moving) ? d.ncnt[i] : d.nfcnt[i];
     if (STAGE != 0) prefetch_epilogue<DIM, STAGE>(d, i);
     // per-phase constants of the pair terms as registers (selected per pair):
     // m_j P_i / rho_i^2 for a water and an oil neighbour, and the viscous factors

@@ -309,6 +309,64 @@ def test_restart_is_bit_exact(sphmod):
     assert a.list_builds == 20
 
 
+def _static_walls_moving(w, seed):
+    """Velocities of the workload with its static boundary particles given
+    seeded values, which they keep (boundary particles do not integrate)."""
+    rng = np.random.default_rng(seed)
+    u = w.u.copy()
+    st = w.wall == 1
+    u[st] = rng.uniform(-0.01, 0.01, size=(int(st.sum()), u.shape[1])) * w.params["c0"]
+    return u
+
+
+@pytest.mark.parametrize("case", ["2d_small", "3d_small"])
+def test_static_walls_in_motion_take_whole_lists(sphmod, case):
+    """While every static boundary particle is at rest, its static boundary
+    neighbours sit at the end of its list and the force sweep stops before
+    them (their pairs add exact zeros: u_ij = 0, and a boundary particle's
+    acceleration is not used); the parity tests above cover that form.  Once
+    one moves, those pairs carry u_ij != 0 and the sweep takes whole lists:
+    the boundary particles' density rates against the oracle with moving
+    walls from the start, and after a state with moving walls is loaded onto
+    lists built while they were at rest (set_state keeps the lists), one step
+    against the oracle."""
+    w = CASES[case]()
+    p = w.params
+    st = w.wall == 1
+    um = _static_walls_moving(w, 11)
+    sim = sphmod.Simulation(p, w.x, um, w.rho, w.phase, w.wall)
+    sim.eval_rates()
+    drho = sim.read("drho")
+    sim.close()
+    ref = oracle.evaluate(p, w.x, um, w.rho, w.phase, w.wall, renorm=True)
+    ref_rest = oracle.evaluate(p, w.x, w.u, w.rho, w.phase, w.wall, renorm=True)
+    e_w = rel_err_field(drho[st], ref["drho"][st])
+    moved = rel_err_field(ref_rest["drho"][st], ref["drho"][st])   # what the wall-wall pairs add
+    dt = WL.stable_dt(p)
+    sim = sphmod.Simulation.from_workload(w)
+    sim.step(dt)
+    b0 = sim.list_builds
+    x, u, r = sim.read("pos"), sim.read("vel"), sim.read("rho")
+    u[st] = um[st]
+    sim.set_state(x, u, r)
+    sim.step(dt)
+    kept = sim.list_builds == b0
+    x1, u1, r1 = sim.read("pos"), sim.read("vel"), sim.read("rho")
+    sim.close()
+    xr, ur, rr = oracle.run(p, x, u, r, w.phase, w.wall, dt, 1)
+    e_x = np.abs(x1 - xr).max() / p["dx"]
+    e_u = rel_err_field(u1 - u, ur - u)
+    e_r = np.abs(r1 / rr - 1).max()
+    e_rw = np.abs(r1[st] - rr[st]).max() / np.abs(rr[st] - r[st]).max()
+    print(f"\n[{case}, static walls moving] wall drho {e_w:.2e} (the wall-wall pairs change it by {moved:.2e}); "
+          f"after set_state (lists kept: {kept}) |dx|/dx {e_x:.2e} du {e_u:.2e} rho {e_r:.2e}, "
+          f"wall density change {e_rw:.2e}")
+    assert moved > 1e-2
+    assert e_w <= TOL
+    assert kept
+    assert e_x < 1e-8 and e_u < TOL and e_r < TOL and e_rw < 1e-4
+
+
 def test_set_state_keeps_valid_lists(sphmod):
     """Loading back the state a handle holds keeps its cell order and list
     (no rebuild) and leaves the trajectory bit for bit unchanged."""
