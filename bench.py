@@ -37,6 +37,12 @@ FP32_PEAK_DERIVED_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # not counted (conservative).  Pinned by the counted restatement in
 # tests/test_flop_count.py.
 SWEEP_B_FLOPS_PER_PAIR = {2: 33, 3: 43}
+# Of those, the continuity term alone (pair vector, r, (1 - q/2)^3, u_ij,
+# u_ij . r_ij and the sum): all a static boundary particle needs from a pair
+# with a particle that is not one (its acceleration is not used); pairs of
+# two static boundary particles at rest need nothing (u_ij = 0).  Pinned the
+# same way.
+SWEEP_B_FLOPS_CONTINUITY = {2: 18, 3: 24}
 # Algorithmic flops of one accepted pair in the renormalisation sweep at
 # stage 1: same-phase pairs (kernel value + two compensated sums) and
 # other-phase pairs (colour gradient).
@@ -534,7 +540,7 @@ def run_ours(args, ws, rank, local):
     dt = WL.stable_dt(p)
     n = w.n
     sim = sph.Simulation.from_workload(w, stream=stream.cuda_stream)
-    pairs0, other0 = sim.pair_stats()
+    cls0 = sim.pair_classes()
 
     # ---- timed region A: graph-replayed steps, state resident in HBM ----
     sim.run(dt, args.warmup, graph=True)
@@ -569,7 +575,7 @@ def run_ours(args, ws, rank, local):
     ms_eager = e0.elapsed_time(e1)
     kt = sim.timing_read()
     sim.timing(False)
-    pairs1, other1 = sim.pair_stats()
+    cls1 = sim.pair_classes()
     # steady state: many more graph-replayed steps right after, so the list
     # rebuilds come at their natural rate (the short timed window may hold none)
     steady = None
@@ -591,10 +597,16 @@ def run_ours(args, ws, rank, local):
     tot = sum(v[1] for v in kt.values())
     kernels = {k: {"launches": v[0], "ms": round(v[1], 4), "share": round(v[1] / tot, 4)} for k, v in kt.items() if v[0]}
     top = max(kt, key=lambda k: kt[k][1])
-    pairs = 0.5 * (pairs0 + pairs1)
-    other = 0.5 * (other0 + other1)
+    # ordered pairs within 2h: all, across phases, two static boundary
+    # particles, a static boundary particle with another (mean of the counts
+    # before and after the timed steps)
+    pairs, other, pairs_ss, pairs_sw = (0.5 * (a + b) for a, b in zip(cls0, cls1))
     if top == "sweep_b":
-        flops = pairs * SWEEP_B_FLOPS_PER_PAIR[dim]
+        # the pairs the method needs: all but those of two static boundary
+        # particles at rest; a static boundary particle's pairs with the
+        # others need only the continuity term
+        flops = ((pairs - pairs_ss - pairs_sw) * SWEEP_B_FLOPS_PER_PAIR[dim]
+                 + pairs_sw * SWEEP_B_FLOPS_CONTINUITY[dim])
     elif top == "sweep_a":
         # two launches per step: stage 1 (renormalisation + colour) and stage 2 (colour only)
         flops = 0.5 * ((pairs - other) * SWEEP_A_FLOPS_SAME[dim] + 2 * other * SWEEP_A_FLOPS_OTHER[dim])
@@ -615,7 +627,10 @@ def run_ours(args, ws, rank, local):
                                f"of 256 threads per SM, {peak_ms:.1f} ms launch, clocks as sampled",
                 "peak_derived": FP32_PEAK_DERIVED_TFLOPS,
                 "flops_per_pair": SWEEP_B_FLOPS_PER_PAIR[dim] if top == "sweep_b" else None,
-                "pairs_per_launch": pairs, "flops_per_launch": flops, "avg_launch_ms": avg_ms,
+                "flops_per_boundary_pair": SWEEP_B_FLOPS_CONTINUITY[dim] if top == "sweep_b" else None,
+                "pairs_per_launch": pairs - pairs_ss if top == "sweep_b" else pairs,
+                "boundary_pairs_per_launch": pairs_sw if top == "sweep_b" else None,
+                "flops_per_launch": flops, "avg_launch_ms": avg_ms,
                 "launches": kt[top][0]}
 
     # ---- e2e: host buffers through the C ABI every step ----

@@ -332,6 +332,16 @@ int64_t sph_neighbours(sph_handle h, int64_t *start, int32_t *list, int64_t cap)
  * the pair counts the interaction sweeps evaluate. */
 int sph_pair_stats(sph_handle h, int64_t out[2]);
 
+/* The same count by classes (rebuilds the cell list): out[0] and out[1] as
+ * in sph_pair_stats; out[2] = ordered pairs of two static boundary particles
+ * (wall flag 1); out[3] = ordered pairs (i, j) of a static boundary particle
+ * i with a particle j that is not one.  While every static boundary particle
+ * is at rest the force sweep (Eq. dist_p_1, visc_2, ct_dist_2) leaves out the
+ * out[2] pairs, whose terms are zero (u_ij = 0 in the continuity term; a
+ * boundary particle's acceleration is not used), and of the out[3] pairs only
+ * the continuity term is needed.  Errors: SPH_EINVAL for a NULL argument. */
+int sph_pair_classes(sph_handle h, int64_t out[4]);
+
 /* FP64 diagnostics over the fluid particles (walls excluded):
  *   out[0] mass, out[1..3] momentum sum m u, out[4] kinetic energy,
  *   out[5] potential energy -sum m g.x, out[6..8] oil centroid,

@@ -984,7 +984,7 @@ int create_sim(const sph_params *params, int k, const int64_t *counts, const dou
         err |= s->alloc(&s->dstep, 1);
         err |= s->alloc(&s->dbuilds, 1);
         err |= s->alloc(&s->bar, 1);
-        err |= s->alloc(&s->pair_tot, 2);
+        err |= s->alloc(&s->pair_tot, 4);
         err |= s->alloc(&s->dinst, (size_t)k);
         err |= s->alloc(&s->dfirst, (size_t)k + 1);
         err |= s->alloc(&s->sort.cell_tmp, N);
@@ -1824,22 +1824,31 @@ int64_t sph_neighbours(sph_handle s, int64_t *start, int32_t *list, int64_t cap)
     return total;
 }
 
-int sph_pair_stats(sph_handle s, int64_t out[2])
+int sph_pair_classes(sph_handle s, int64_t out[4])
 {
     if (!s || !out) return fail(SPH_EINVAL, "NULL argument");
-    out[0] = out[1] = 0;
+    out[0] = out[1] = out[2] = out[3] = 0;
     if (s->n == 0) return SPH_OK;
     s->enqueue_build_cells(true);
-    CU(cudaMemsetAsync(s->pair_tot, 0, 2 * sizeof(unsigned long long), s->stream));
+    CU(cudaMemsetAsync(s->pair_tot, 0, 4 * sizeof(unsigned long long), s->stream));
     if (s->dim == 2) k_pair_stats<2><<<s->blocks(s->n), 256, 0, s->stream>>>(s->D(), s->grid, s->phys, s->pair_tot);
     else k_pair_stats<3><<<s->blocks(s->n), 256, 0, s->stream>>>(s->D(), s->grid, s->phys, s->pair_tot);
     CU(cudaGetLastError());
-    unsigned long long h[2];
+    unsigned long long h[4];
     CU(cudaMemcpyAsync(h, s->pair_tot, sizeof(h), cudaMemcpyDeviceToHost, s->stream));
     CU(cudaStreamSynchronize(s->stream));
-    out[0] = (int64_t)h[0];
-    out[1] = (int64_t)h[1];
+    for (int q = 0; q < 4; ++q) out[q] = (int64_t)h[q];
     return s->check_flags();
+}
+
+int sph_pair_stats(sph_handle s, int64_t out[2])
+{
+    if (!s || !out) return fail(SPH_EINVAL, "NULL argument");
+    int64_t c[4];
+    const int rc = sph_pair_classes(s, c);
+    out[0] = c[0];
+    out[1] = c[1];
+    return rc;
 }
 
 int sph_diag_instances(sph_handle s, double *out)

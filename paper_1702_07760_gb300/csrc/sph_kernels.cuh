@@ -1611,23 +1611,27 @@ template <int DIM>
 static __global__ void __launch_bounds__(256) k_pair_stats(Dev d, Grid g, Phys ph, unsigned long long *tot)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    int all = 0, other = 0;
+    // ordered pairs: all, across phases, both static boundary particles, a
+    // static boundary particle i with any other j
+    int c[4] = {0, 0, 0, 0};
     if (i < d.n) {
         const float4 oi = d.pos[i];
         const int phi_ = rec_phase(oi.w);
+        const bool si = static_wall(d.tag[i]);
         for_each_candidate<DIM, true>(g, d.cstart, d.pos, d.cell[i], oi, ph.R2, ph.RP,
                                       [&](int j, const float4 &oj, float, float, float, float, unsigned) {
-                                          all += j != i;
-                                          other += rec_phase(oj.w) != phi_;
+                                          if (j == i) return;
+                                          const bool sj = static_wall(d.tag[j]);
+                                          c[0] += 1;
+                                          c[1] += rec_phase(oj.w) != phi_;
+                                          c[2] += si && sj;
+                                          c[3] += si && !sj;
                                       });
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        all += __shfl_down_sync(0xffffffffu, all, o);
-        other += __shfl_down_sync(0xffffffffu, other, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        atomicAdd(tot, (unsigned long long)all);
-        atomicAdd(tot + 1, (unsigned long long)other);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        for (int o = 16; o > 0; o >>= 1) c[q] += __shfl_down_sync(0xffffffffu, c[q], o);
+        if ((threadIdx.x & 31) == 0) atomicAdd(tot + q, (unsigned long long)c[q]);
     }
 }
 

@@ -24,7 +24,7 @@ FIELD = dict(pos=0, vel=1, rho=2, rho_eval=3, pressure=4, acc=5, drho=6, tensor=
 
 # entry points declared in include/sph.h and include/sph_surrogate.h
 EXPORTS = ["sph_create", "sph_set_state", "sph_build_cells", "sph_eval_rates", "sph_step", "sph_run",
-           "sph_sync", "sph_read", "sph_neighbours", "sph_pair_stats", "sph_diag", "sph_timing_enable",
+           "sph_sync", "sph_read", "sph_neighbours", "sph_pair_stats", "sph_pair_classes", "sph_diag", "sph_timing_enable",
            "sph_timing_reset", "sph_timing_count", "sph_timing_read", "sph_num_particles",
            "sph_step_index", "sph_num_cells", "sph_list_builds", "sph_destroy", "sph_last_error",
            "sph_cell_sort_noalloc", "sph_create_batch", "sph_set_dt_scales", "sph_run_persistent",
@@ -85,6 +85,7 @@ def load(path: str = LIB_PATH):
     L.sph_neighbours.restype = C.c_int64
     L.sph_diag.argtypes = [H, dp]
     L.sph_pair_stats.argtypes = [H, P(C.c_int64)]
+    L.sph_pair_classes.argtypes = [H, P(C.c_int64)]
     L.sph_timing_enable.argtypes = [H, C.c_int]
     L.sph_timing_count.argtypes = []
     L.sph_timing_read.argtypes = [H, C.c_int, P(C.c_char_p), P(C.c_int64), P(C.c_double)]
@@ -457,6 +458,14 @@ class Simulation:
         out = np.zeros(2, np.int64)
         _check(load().sph_pair_stats(self._h, out.ctypes.data_as(C.POINTER(C.c_int64))))
         return int(out[0]), int(out[1])
+
+    def pair_classes(self):
+        """(ordered neighbour pairs, across phases, between two static boundary
+        particles, of a static boundary particle with another) at the current
+        positions (sph_pair_classes)."""
+        out = np.zeros(4, np.int64)
+        _check(load().sph_pair_classes(self._h, out.ctypes.data_as(C.POINTER(C.c_int64))))
+        return tuple(int(v) for v in out)
 
     @staticmethod
     def _diag_dict(out, d):

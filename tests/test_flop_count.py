@@ -72,6 +72,33 @@ def pair_terms(dim, xi, xj, ui, uj, Q_i, Q_j, m_j, V_j, k_ij, inv_2h, delta2, ac
     return div + vt * ur
 
 
+def continuity_terms(dim, xi, xj, ui, uj, V_j, inv_2h, div):
+    """The continuity term alone, V_j u_ij . grad W (what a boundary particle
+    takes from a pair with a moving particle)."""
+    r = [xi[c] - xj[c] for c in range(dim)]
+    r2 = r[0] * r[0]
+    for c in range(1, dim):
+        r2 = r2 + r[c] * r[c]
+    rr = r2.sqrt()
+    t = 1.0 - rr * inv_2h
+    t3 = t * t * t
+    vt = V_j * t3
+    u = [ui[c] - uj[c] for c in range(dim)]
+    ur = u[0] * r[0]
+    for c in range(1, dim):
+        ur = ur + u[c] * r[c]
+    return div + vt * ur
+
+
+def count_continuity(dim):
+    C = Counted
+    xi, xj = [C(0.1 * (c + 1)) for c in range(dim)], [C(0.05 * c) for c in range(dim)]
+    ui, uj = [C(0.0)] * dim, [C(-0.02 * c) for c in range(dim)]
+    Counted.ops = 0
+    continuity_terms(dim, xi, xj, ui, uj, 1e-11, 1.0 / 0.65, C(0.0))
+    return Counted.ops
+
+
 def count(dim):
     C = Counted
     xi, xj = [C(0.1 * (c + 1)) for c in range(dim)], [C(0.05 * c) for c in range(dim)]
@@ -85,3 +112,8 @@ def count(dim):
 def test_force_sweep_flops_per_pair_match_bench():
     for dim in (2, 3):
         assert count(dim) == bench.SWEEP_B_FLOPS_PER_PAIR[dim], (dim, count(dim))
+
+
+def test_continuity_only_flops_per_pair_match_bench():
+    for dim in (2, 3):
+        assert count_continuity(dim) == bench.SWEEP_B_FLOPS_CONTINUITY[dim], (dim, count_continuity(dim))

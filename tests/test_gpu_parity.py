@@ -83,6 +83,16 @@ def test_cells_order_and_neighbours_bit_exact(sphmod, case):
     s_ref, l_ref = oracle.neighbours(w.params, w.x, "brute")
     assert np.array_equal(s_gpu, s_ref)
     assert np.array_equal(l_gpu, l_ref)
+    # the same pairs by class: across phases, two static boundary particles,
+    # a static boundary particle with another
+    I = np.repeat(np.arange(w.n), np.diff(s_ref))
+    J = l_ref.astype(np.int64)
+    st = w.wall == 1
+    ref_classes = (len(J), int((w.phase[I] != w.phase[J]).sum()), int((st[I] & st[J]).sum()),
+                   int((st[I] & ~st[J]).sum()))
+    assert sim.pair_classes() == ref_classes
+    assert sim.pair_stats() == ref_classes[:2]
+    assert ref_classes[2] > 0 and ref_classes[3] > 0
     sim.close()
 
 
