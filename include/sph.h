@@ -124,7 +124,11 @@ typedef struct sph_sim *sph_handle;
  *   phase  : n bytes, 0 = water, 1 = oil
  *   wall   : n bytes, 0 = fluid, 1 = dynamic boundary particle, 2 = piston
  *            particle (a boundary particle moved by sph_set_piston); boundary
- *            and piston particles must be phase 0
+ *            and piston particles must be phase 0.  Boundary particles keep
+ *            the position and velocity they are given (Sec. III); while every
+ *            wall == 1 particle has zero velocity (the intended use) the force
+ *            sweep skips their mutual pairs, whose terms are zero, and a state
+ *            in which one moves is computed in full (same results)
  *   stream : a cudaStream_t, or NULL for the default stream
  * Every position must lie inside [box_lo, box_hi].  On success *out holds the
  * handle; on failure *out is NULL and nothing is leaked. */
