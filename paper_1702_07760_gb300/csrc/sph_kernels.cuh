@@ -540,8 +540,14 @@ __device__ __forceinline__ void hash_one(const Dev &d, const Grid &g, const Sort
         const double t = xa - g.lo[a];
         const float q32 = __fmul_rn((float)t, g.inv_cs);
         const float fl = floorf(q32), fr = q32 - fl, m = fmaf(4e-7f, fabsf(q32), 1e-30f);
-        double sc = (double)fl;
-        if (!(fr > m && fr < 1.f - m)) sc = floor(t / g.csd);
+        if (fr > m && fr < 1.f - m) {
+            // decided by the estimate (finite, away from a face): the bounds
+            // test on the FP32 cell index, off the FP64 pipe (1/64 rate)
+            if (fl >= 0.f && fl < (float)dims[a]) c[a] = (int)fl;
+            else bad |= FLAG_DOMAIN;
+            continue;
+        }
+        double sc = floor(t / g.csd);
         if (g.per[a] && sc >= (double)dims[a]) sc = dims[a] - 1;  // rounding at the upper side
         if (isnan(xa)) {
             bad |= FLAG_NONFINITE;
