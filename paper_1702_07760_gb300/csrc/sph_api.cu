@@ -505,9 +505,8 @@ __global__ void k_load_state(Dev d, Grid g, Phys ph, const double *x, const doub
 
 // The device address of a caller's buffer when kernels can use it in place
 // (device or managed memory); NULL for host memory, pinned or pageable, which
-// goes through the handle's staging buffers with cudaMemcpyAsync (the copy
-// engines move pinned memory as fast as a kernel over the host link does,
-// and in whole lines).
+// goes through the handle's staging buffers with cudaMemcpyAsync unless a
+// path below reads or writes it in place.
 template <class T>
 T *device_view(T *p)
 {
@@ -517,6 +516,21 @@ T *device_view(T *p)
         return nullptr;
     }
     if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return static_cast<T *>(a.devicePointer);
+    return nullptr;
+}
+
+// The device address of pinned host memory the GPU can address (mapped);
+// NULL for anything else.  The state is read back into such memory in place,
+// in whole lines (k_read_state_lines).
+template <class T>
+T *pinned_view(T *p)
+{
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type == cudaMemoryTypeHost && a.devicePointer) return static_cast<T *>(a.devicePointer);
     return nullptr;
 }
 
@@ -1256,6 +1270,10 @@ int sph_create_batch(int k, const sph_params *params, const int64_t *counts, con
 int sph_sim::enqueue_set_state(const double *x, const double *u, const double *rho)
 {
     const size_t nn = (size_t)n, dd = (size_t)dim;
+    // device arrays are read in place by the load kernel; host arrays are
+    // staged by the copy engines (a load kernel reading pinned memory in place
+    // measured slower: its per-particle work and scattered writes leave too
+    // few reads in flight to fill the host link)
     const double *dx = device_view(x), *du = device_view(u), *dr = device_view(rho);
     if (!dx) {
         dx = read_buf;
@@ -1734,6 +1752,16 @@ int sph_read(sph_handle s, int field, void *host_out, int64_t bytes)
 int sph_sim::enqueue_read_state(double *x, double *u, double *rho)
 {
     const size_t nn = (size_t)n, dd = (size_t)dim;
+    // pinned outputs (x and u on 16-byte boundaries): one kernel writes all
+    // three in place, in whole lines
+    double *px = pinned_view(x), *pu = pinned_view(u), *pr = pinned_view(rho);
+    if (px && pu && pr && ((uintptr_t)px % 16) == 0 && ((uintptr_t)pu % 16) == 0) {
+        const int nb = blocks(n, RS_TILE);
+        if (dim == 2) k_read_state_lines<2><<<nb, RS_TILE, 0, stream>>>(D(), px, pu, pr);
+        else k_read_state_lines<3><<<nb, RS_TILE, 0, stream>>>(D(), px, pu, pr);
+        CU(cudaGetLastError());
+        return SPH_OK;
+    }
     int rc = enqueue_read(RK_X, false, x, nn * dd * 8, 0);
     if (!rc) rc = enqueue_read(RK_U, false, u, nn * dd * 8, nn * dd);
     if (!rc) rc = enqueue_read(RK_RHO, false, rho, nn * 8, 2 * nn * dd);

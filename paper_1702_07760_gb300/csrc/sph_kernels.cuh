@@ -1715,6 +1715,53 @@ static __global__ void __launch_bounds__(256) k_unpermute(Dev d, int kind, doubl
     }
 }
 
+// The state (x, u, rho) in original order written straight into host memory
+// the GPU can address (pinned, mapped), in whole lines: a block takes 256
+// consecutive particles, gathers their values from the sorted state into
+// shared memory in the output's particle-major layout, and writes each
+// field's contiguous stretch with 16-byte stores (x and u must start on a
+// 16-byte boundary); rho, one double a particle, is contiguous across a warp
+// already.  Scattered 8-byte stores at a 24-byte stride, as k_unpermute
+// makes, reach a third of the host link's rate; whole-line stores reach the
+// copy engines' rate, with no staging copy after the kernel.
+constexpr int RS_TILE = 256;
+template <int DIM>
+static __global__ void __launch_bounds__(RS_TILE) k_read_state_lines(Dev d, double *x, double *u, double *rho)
+{
+    __shared__ double sx[RS_TILE * DIM], su[RS_TILE * DIM];
+    const int n = d.n;
+    const int p0 = blockIdx.x * RS_TILE, t = threadIdx.x;
+    const int cnt = min(RS_TILE, n - p0);
+    if (t < cnt) {
+        const int p = p0 + t;
+        const int k = d.inv[p];
+        if (SPH_IN_RANGE(d.flags, k, n)) {
+            const Inst &I = d.inst[d.iid[k]];
+#pragma unroll
+            for (int c = 0; c < DIM; ++c) {
+                sx[t * DIM + c] = wrap_coord(d.x[(size_t)c * n + k], d.plo[c], d.period[c]) - I.offset[c];
+                su[t * DIM + c] = d.u[(size_t)c * n + k];
+            }
+            rho[p] = (double)by_phase(d.tag[k] & 1, I.rho0) + (double)d.drho[k];
+        } else {
+#pragma unroll
+            for (int c = 0; c < DIM; ++c) sx[t * DIM + c] = su[t * DIM + c] = 0.0;
+        }
+    }
+    __syncthreads();
+    const int m = cnt * DIM;  // doubles of the tile in each of x and u
+    double2 *x2 = reinterpret_cast<double2 *>(x + (size_t)p0 * DIM);
+    double2 *u2 = reinterpret_cast<double2 *>(u + (size_t)p0 * DIM);
+    for (int q = t; q < m / 2; q += RS_TILE) {
+        x2[q] = make_double2(sx[2 * q], sx[2 * q + 1]);
+        u2[q] = make_double2(su[2 * q], su[2 * q + 1]);
+    }
+    if ((m & 1) && t == 0) {
+        x[(size_t)p0 * DIM + m - 1] = sx[m - 1];
+        u[(size_t)p0 * DIM + m - 1] = su[m - 1];
+    }
+}
+
 // ---------------------------------------------------------------------------
 // FP64 diagnostics of each instance: one block per instance reduces, in a
 // fixed tree order, over the instance's fluid particles taken in original

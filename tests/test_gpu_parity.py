@@ -577,6 +577,49 @@ def test_pinned_buffers_are_read_and_written_in_place(sphmod):
     b.close()
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+def test_pinned_state_reads_in_whole_lines_match_staged_reads(sphmod, dim):
+    """Reading the state into pinned host memory (one kernel writes x, u and
+    rho in place, x and u in whole lines through shared memory) gives the
+    bits of the staged read into pageable arrays: at a particle count whose
+    last 256-particle tile is ragged and holds an odd number of doubles, and
+    with a pinned x that starts off a 16-byte boundary (which takes the
+    staged path).  Loading from pinned memory matches loading from pageable
+    copies."""
+    import torch
+    w = (WL.drop_tank(2, (37, 53), drop_d_dx=10, seed=21, perturb=True) if dim == 2
+         else WL.drop_tank(3, (13, 17, 19), drop_d_dx=8, seed=22, perturb=True))
+    n = w.n
+    assert n % 2 == 1 and n % 256 != 0
+    dt = WL.stable_dt(w.params)
+    a = sphmod.Simulation.from_workload(w)
+    b = sphmod.Simulation.from_workload(w)
+    a.run(dt, 3)
+    b.run(dt, 3)
+    pin = lambda *s: torch.empty(s, dtype=torch.float64, pin_memory=True).numpy()
+    x, u, r = pin(n, dim), pin(n, dim), pin(n)
+    a.read_state(x, u, r)
+    xs, us, rs = np.empty((n, dim)), np.empty((n, dim)), np.empty(n)
+    a.read_state(xs, us, rs)
+    assert np.array_equal(x, xs) and np.array_equal(u, us) and np.array_equal(r, rs)
+    assert np.array_equal(xs, b.read("pos")) and np.array_equal(rs, b.read("rho"))
+    big = pin(n * dim + 1)
+    xm = big[1:].reshape(n, dim)                  # 8 bytes off a 16-byte boundary
+    assert xm.ctypes.data % 16 == 8
+    a.read_state(xm, u, r)
+    assert np.array_equal(xm, xs)
+    # load from pinned memory (a) and from pageable copies (b), then step both
+    x[:, 0] += 0.3 * p_skin(w)
+    a.set_state(x, u, r)
+    b.set_state(np.array(x), np.array(u), np.array(r))
+    a.run(dt, 2)
+    b.run(dt, 2)
+    for f in ("pos", "vel", "rho"):
+        assert np.array_equal(a.read(f), b.read(f)), f
+    a.close()
+    b.close()
+
+
 def p_skin(w):
     return w.params["skin"]
 
