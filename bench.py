@@ -52,7 +52,7 @@ SWEEP_A_FLOPS_OTHER = {2: 14, 3: 21}
 # DRAM bytes (read + write) per launch of the force sweep on the 3-D workload,
 # from the ncu capture summarised in profiles/sweep_b_drop_3d_64x64x128.md; valid
 # only for the kernel source it was taken on (first 16 hex digits of its sha256).
-PROFILED_TRAFFIC = {"sweep_b": {"source_sha256": "872a7502129550e9", "bytes": 275.9e6, "workload": "drop_3d"}}
+PROFILED_TRAFFIC = {"sweep_b": {"source_sha256": "80374495e7553f0d", "bytes": 275.9e6, "workload": "drop_3d"}}
 
 
 def parse():
