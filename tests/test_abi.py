@@ -96,6 +96,9 @@ def test_null_handles_are_rejected_without_a_gpu(lib):
     assert lib.sph_read_state(None, p, p, p) == -1
     assert lib.sph_set_state(None, p, p, p) == -1
     assert lib.sph_run(None, 1e-5, 1, 1) == -1
+    counts = (C.c_int64 * 4)()
+    assert lib.sph_pair_classes(None, counts) == -1
+    assert lib.sph_pair_stats(None, counts) == -1
 
 
 def test_kernels_compile_for_sm103a_without_spills():
